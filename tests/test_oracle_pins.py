@@ -1,0 +1,481 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle function against something other than itself: a
+closed form, an invariant stated in the paper, a textbook routine written
+independently here (integral-image guided filter, ridge regression), a library
+routine (scipy max-flow) or brute force on tiny inputs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.conftest import TINY_PARAMS
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- random draws -------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    """SplitMix64 (Steele et al. 2014) from state 0: the published first outputs."""
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.startswith("0x")]
+    assert oracle.splitmix64(0, len(vals)) == vals
+
+
+# --- preprocessing --------------------------------------------------------------
+
+def _gray_ramp(H, W, k):
+    # R = G = B so the BT.601 gray value equals the channel value
+    u = np.arange(W, dtype=np.float64)
+    img = np.repeat((20.0 + k * u)[None, :, None], 3, axis=2)
+    return np.repeat(img, H, axis=0)
+
+
+def test_gradient_kernel_on_ramp():
+    """[-0.5 0 0.5] on a ramp of slope k: k inside, k/2 at the replicated border (Sec. 3.2)."""
+    H, W, k = 6, 12, 3.5
+    img = _gray_ramp(H, W, k)
+    o = oracle.Oracle(img, img, gf_radius=1)
+    g = o.planes()["L"][..., 3]
+    assert np.allclose(g[:, 1:-1], k, atol=1e-12)
+    assert np.allclose(g[:, [0, -1]], k / 2, atol=1e-12)
+
+
+def test_guide_stats_against_numpy(tiny_pair):
+    """mu_k and (Sigma_k + eU)^-1 over the clipped window, vs numpy mean/cov/inv."""
+    r = 2
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=r)
+    pl = o.planes()
+    I = tiny_pair["left"].astype(np.float64) / 255.0
+    H, W = I.shape[:2]
+    for (y, x) in [(0, 0), (5, 7), (71, 95), (30, 0), (40, 60)]:
+        win = I[max(0, y - r):y + r + 1, max(0, x - r):x + r + 1].reshape(-1, 3)
+        mu = win.mean(0)
+        S = np.cov(win.T, bias=True) + 1e-4 * np.eye(3)
+        assert np.allclose(pl["mu"][y, x], mu, rtol=0, atol=1e-14)
+        assert np.allclose(pl["A"][y, x], np.linalg.inv(S), rtol=1e-9)
+
+
+def test_contrast_weight_closed_form():
+    """w_pq = exp(-|I_p - I_q|_1 / gamma) with the lower bound eps (Eq. smweight)."""
+    H, W = 4, 5
+    img = np.full((H, W, 3), 100.0)
+    img[:, 3:, :] += np.array([4.0, 3.0, 2.0])   # step of L1 = 9 between columns 2 and 3
+    img[2:, :, 0] += 60.0                          # step of 60 between rows 1 and 2 (weight floor)
+    o = oracle.Oracle(img, img, gf_radius=1, gamma=10.0, eps_w=0.01)
+    w = o.planes()["w"]
+    assert w[0, 0, 0] == pytest.approx(1.0)                 # flat
+    assert w[0, 2, 0] == pytest.approx(np.exp(-0.9))        # right across the colour step
+    assert w[1, 0, 2] == pytest.approx(0.01)                # down across the 60 step: exp(-6) < eps
+    assert w[0, 4, 0] == 0.0                                # right neighbour outside the image
+
+
+# --- raw cost rho ---------------------------------------------------------------
+
+def test_rho_zero_for_integer_fronto_parallel_shift(tiny_pair):
+    """Noise-free right view = left shifted by an integer d: rho(s|(0,0,d)) = 0 exactly."""
+    L = tiny_pair["left"].astype(np.float64)
+    d = 6
+    R = np.empty_like(L)
+    R[:, :-d] = L[:, d:]
+    R[:, -d:] = L[:, -1:]
+    o = oracle.Oracle(L, R, gf_radius=2)
+    H, W = L.shape[:2]
+    for v in range(0, H, 7):
+        for u in range(d + 1, W - 1, 5):
+            assert o.rho((0, 0, d), u, v) == 0.0
+
+
+def test_rho_zero_on_slanted_plane_with_affine_texture():
+    """Slanted plane, texture affine in u with constant gray: the exact right view gives rho = 0."""
+    H, W = 20, 64
+    a, b, c = 0.12, -0.05, 9.0
+    rng = np.random.default_rng(3)
+    base = rng.uniform(60, 160, size=(H, 1, 3))
+    # per-row colour slopes whose BT.601 gray slope is zero, so both gradients vanish
+    sR = rng.uniform(-1, 1, size=(H, 1))
+    sB = rng.uniform(-1, 1, size=(H, 1))
+    sG = -(0.299 * sR + 0.114 * sB) / 0.587
+    slope = np.concatenate([sR, sG, sB], axis=1)[:, None, :]
+    u = np.arange(W, dtype=np.float64)[None, :, None]
+    L = base + slope * u
+    v = np.arange(H, dtype=np.float64)[:, None, None]
+    ul = (u + b * v + c) / (1.0 - a)           # left position seen by right pixel u
+    R = base + slope * ul
+    o = oracle.Oracle(L, R, gf_radius=2)
+    for vv in range(H):
+        for uu in range(W):
+            up = uu - (a * uu + b * vv + c)
+            if 0.0 <= up <= W - 1:
+                assert abs(o.rho(np.float32([a, b, c]), uu, vv)) < 1e-5   # labels are float32
+    # with the float32-rounded label the residual is the label rounding only
+    lab = np.float32([a, b, c])
+    o2 = oracle.Oracle(L, base + slope * ((u + float(lab[1]) * v + float(lab[2])) / (1.0 - float(lab[0]))),
+                       gf_radius=2)
+    assert max(abs(o2.rho(lab, uu, 10)) for uu in range(W // 2, W)) < 1e-10
+
+
+def test_rho_bounded_by_linear_interpolation_error():
+    """Smooth sinusoid, non-integer shift: rho <= the linear-interpolation error bound h^2/8 max|f''|."""
+    H, W = 3, 80
+    A, om, ph = 40.0, 0.3, 0.4
+    delta = 3.37
+    u = np.arange(W, dtype=np.float64)
+    f = lambda x: 120.0 + A * np.sin(om * x + ph)
+    L = np.repeat(np.repeat(f(u)[None, :, None], 3, axis=2), H, axis=0)
+    R = np.repeat(np.repeat(f(u + delta)[None, :, None], 3, axis=2), H, axis=0)
+    o = oracle.Oracle(L, R, gf_radius=1)
+    # colour: 3 channels, each |f - lerp f| <= A om^2 / 8; gradient: central difference
+    # of a sinusoid is A sin(om) cos(.), whose lerp error is <= A om^2 sin(om) / 8
+    bound = 0.1 * 3 * A * om ** 2 / 8 + 0.9 * A * om ** 2 * np.sin(om) / 8
+    worst = max(o.rho((0, 0, delta), uu, 1) for uu in range(6, W - 2))
+    assert worst <= bound + 1e-9
+    assert worst > 0.05 * bound           # and the bound is not vacuous
+
+
+# --- data term: guided-filter aggregation ---------------------------------------
+
+def _box_mean(x, r):
+    """Count-normalised box mean over (2r+1)^2 windows clipped to the image, by integral images."""
+    H, W = x.shape[:2]
+    ii = np.zeros((H + 1, W + 1) + x.shape[2:])
+    ii[1:, 1:] = x.cumsum(0).cumsum(1)
+    ys = np.arange(H); xs = np.arange(W)
+    y0 = np.clip(ys - r, 0, H); y1 = np.clip(ys + r + 1, 0, H)
+    x0 = np.clip(xs - r, 0, W); x1 = np.clip(xs + r + 1, 0, W)
+    s = ii[y1][:, x1] - ii[y0][:, x1] - ii[y1][:, x0] + ii[y0][:, x0]
+    n = (y1 - y0)[:, None] * (x1 - x0)[None, :]
+    return s / n.reshape(n.shape + (1,) * (x.ndim - 2))
+
+
+def _guided_filter(I, p, r, eps):
+    """He et al. (TPAMI 2013) guided filter, colour guide, box means by integral images."""
+    mI = _box_mean(I, r)
+    mp = _box_mean(p, r)
+    mIp = _box_mean(I * p[..., None], r)
+    cov_Ip = mIp - mI * mp[..., None]
+    II = I[..., :, None] * I[..., None, :]
+    var = _box_mean(II.reshape(I.shape[:2] + (9,)), r).reshape(I.shape[:2] + (3, 3)) \
+        - mI[..., :, None] * mI[..., None, :]
+    a = np.linalg.solve(var + eps * np.eye(3), cov_Ip[..., None])[..., 0]
+    b = mp - (a * mI).sum(-1)
+    return (_box_mean(a, r) * I).sum(-1) + _box_mean(b[..., None], r)[..., 0]
+
+
+@pytest.mark.parametrize("c", [4.0, 6.63])
+def test_fronto_parallel_region_cost_is_cost_volume_filtering(tiny_pair, c):
+    """alpha = (0,0,c): phi over a region equals the guided-filtered cost-volume slice."""
+    r = 2
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=r)
+    H, W = o.H, o.W
+    slice_ = np.array([[o.rho((0, 0, c), u, v) for u in range(W)] for v in range(H)])
+    I = tiny_pair["left"].astype(np.float64) / 255.0
+    ref = _guided_filter(I, slice_, r, 1e-4)
+    for (x0, y0, w, h) in [(0, 0, 15, 15), (40, 30, 15, 15), (81, 57, 15, 15), (20, 60, 9, 12)]:
+        reg = o.region_cost(x0, y0, w, h, (0, 0, c))
+        assert np.allclose(reg, ref[y0:y0 + h, x0:x0 + w], rtol=0, atol=1e-9)
+
+
+def test_gf_coefficients_are_the_ridge_regression(tiny_pair):
+    """a_k, b_k minimise sum_s (a.I_s + b - rho_s)^2 + e |W'_k| |a|^2 (He et al. 2013)."""
+    r = 2
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=r)
+    I = tiny_pair["left"].astype(np.float64) / 255.0
+    lab = np.float32([0.07, -0.03, 5.2])
+    for (kx, ky) in [(0, 0), (10, 10), (95, 71), (50, 3)]:
+        xs = range(max(0, kx - r), min(o.W, kx + r + 1))
+        ys = range(max(0, ky - r), min(o.H, ky + r + 1))
+        X, y = [], []
+        for v in ys:
+            for u in xs:
+                X.append([*I[v, u], 1.0])
+                y.append(o.rho(lab, u, v))
+        X = np.array(X); y = np.array(y); n = len(y)
+        Pen = np.diag([1e-4 * n] * 3 + [0.0])
+        sol = np.linalg.solve(X.T @ X + Pen, X.T @ y)
+        assert np.allclose(o.gf_coeffs(lab, kx, ky), sol, rtol=1e-7, atol=1e-9)
+
+
+def test_region_cost_equals_definition_brute_force(tiny_pair):
+    """The region scheme over M reproduces phi_p(alpha) by definition at every p, borders included."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2)
+    lab = np.float32([0.05, 0.02, 8.4])
+    for (x0, y0, w, h) in [(0, 0, 10, 10), (86, 62, 10, 10), (37, 21, 15, 15), (90, 0, 6, 4)]:
+        reg = o.region_cost(x0, y0, w, h, lab)
+        d = np.array([[o.phi_def(lab, x0 + x, y0 + y) for x in range(w)] for y in range(h)])
+        assert np.abs(reg - d).max() < 1e-12
+
+
+def test_definition_equals_explicit_weights_of_eq_gf(tiny_pair):
+    """Interior p: phi_p = sum_s omega_ps rho(s) with omega from Eq. gf, and the weights sum to 1."""
+    r = 2
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=r)
+    lab = np.float32([-0.04, 0.06, 7.1])
+    for (u, v) in [(20, 20), (50, 33), (80, 60)]:
+        w = o.phi_weights(u, v)
+        rho = np.array([[o.rho(lab, u + dx, v + dy) for dx in range(-2 * r, 2 * r + 1)]
+                        for dy in range(-2 * r, 2 * r + 1)])
+        assert w.sum() == pytest.approx(1.0, abs=1e-12)
+        assert (w * rho).sum() == pytest.approx(o.phi_def(lab, u, v), abs=1e-12)
+
+
+# --- smoothness term --------------------------------------------------------------
+
+def _rand_label(rng):
+    return np.float32([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(-30, 60)])
+
+
+def test_psi_lemma1_and_special_cases(tiny_pair):
+    """Lemma 1 (psi(a,a) + psi(b,g) <= psi(b,a) + psi(a,g)), psi(f,f) = 0, and a=b=0 -> 2|c_p - c_q|."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2, tau_dis=1e9, eps_w=1.0)
+    o_t = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2)
+    rng = np.random.default_rng(5)
+    for _ in range(400):
+        u, v, d = int(rng.integers(1, 90)), int(rng.integers(0, 70)), int(rng.integers(0, 4))
+        al, be, ga = (_rand_label(rng) for _ in range(3))
+        for oo in (o, o_t):
+            lhs = oo.psi(u, v, d, al, al) + oo.psi(u, v, d, be, ga)
+            rhs = oo.psi(u, v, d, be, al) + oo.psi(u, v, d, al, ga)
+            assert lhs <= rhs + 1e-9
+            assert oo.psi(u, v, d, be, be) == 0.0
+        cp, cq = rng.uniform(0, 60, 2)
+        # untruncated, unit weight: psi-bar = 2 |c_p - c_q|
+        assert o.psi(u, v, d, (0, 0, cp), (0, 0, cq)) == pytest.approx(
+            2 * abs(np.float32(cp) - np.float32(cq)), rel=1e-12)
+
+
+# --- the binary move ---------------------------------------------------------------
+
+def _random_state(o, rng, spread=0.6):
+    H, W = o.H, o.W
+    lab = np.empty((H, W, 3), np.float32)
+    base = [_rand_label(rng) for _ in range(4)]
+    for y in range(H):
+        for x in range(W):
+            f = base[rng.integers(0, 4)].astype(np.float64)
+            f = f + rng.normal(0, [0.02, 0.02, spread])
+            lab[y, x] = f
+    return lab
+
+
+def test_move_graph_encodes_the_energy_exactly(tiny_pair):
+    """|R| = 16: for all 2^16 moves x, const + cut(x) equals the quantised energy of f (+) x summed
+    term by term from the definitions (phi by definition, psi of Eq. smooth_phi), except one unit
+    less for each pair that was lowered to B + C (submodularity after rounding) and stays at (0,0)."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2)
+    S, lam = 65536.0, o.p["lam"]
+    rng = np.random.default_rng(9)
+    lab = _random_state(o, rng)
+    x0, y0, w, h = 34, 24, 4, 4
+    cost = np.zeros((o.H, o.W))
+    for y in range(y0, y0 + h):
+        for x in range(x0, x0 + w):
+            cost[y, x] = o.phi_def(lab[y, x], x, y)
+    alpha = lab[y0 + 1, x0 + 1].copy()
+    alpha[2] += 0.3
+    alpha[0] += 0.01
+    phiA = np.array([[o.phi_def(alpha, x0 + x, y0 + y) for x in range(w)] for y in range(h)])
+    g = o.build_graph(x0, y0, w, h, alpha, lab, cost, phiA)
+    tcap, ncap = g["tcap"].reshape(-1, 2).astype(np.int64), g["ncap"].reshape(-1, 4).astype(np.int64)
+    Q = lambda z: int(np.rint(S * z))
+    fdx, fdy = [1, -1, 0, 1], [0, 1, 1, 1]
+    n = w * h
+    X = ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)   # all moves
+    idx = lambda x, y: (y - y0) * w + (x - x0)
+    inR = lambda x, y: x0 <= x < x0 + w and y0 <= y < y0 + h
+    # energy of f (+) x from the definitions, restricted to the terms that touch R
+    E = np.zeros(1 << n, np.int64)
+    for y in range(y0, y0 + h):
+        for x in range(x0, x0 + w):
+            i = idx(x, y)
+            E += np.where(X[:, i] == 1, Q(phiA[y - y0, x - x0]), Q(cost[y, x]))
+    for y in range(y0 - 1, y0 + h + 1):
+        for x in range(x0 - 1, x0 + w + 1):
+            for d in range(4):
+                qx, qy = x + fdx[d], y + fdy[d]
+                if not (inR(x, y) or inR(qx, qy)):
+                    continue
+                lp = [lab[y, x], alpha] if inR(x, y) else [lab[y, x], lab[y, x]]
+                lq = [lab[qy, qx], alpha] if inR(qx, qy) else [lab[qy, qx], lab[qy, qx]]
+                xp = X[:, idx(x, y)] if inR(x, y) else np.zeros(1 << n, np.int64)
+                xq = X[:, idx(qx, qy)] if inR(qx, qy) else np.zeros(1 << n, np.int64)
+                for bp in (0, 1):
+                    for bq in (0, 1):
+                        term = Q(lam * o.psi(x, y, d, lp[bp], lq[bq]))
+                        E += np.where((xp == bp) & (xq == bq), term, 0)
+    # cut of every move
+    cut = np.where(X == 1, tcap[None, :, 0], tcap[None, :, 1]).sum(1)
+    lowered = np.zeros(1 << n, np.int64)
+    clamp = g["clamp_mask"].reshape(-1)
+    for i in range(n):
+        iy, ix = divmod(i, w)
+        for d in range(4):
+            jx, jy = ix + fdx[d], iy + fdy[d]
+            if 0 <= jx < w and jy < h:
+                j = jy * w + jx
+                cut += np.where((X[:, i] == 0) & (X[:, j] == 1), ncap[i, d], 0)
+                if (clamp[i] >> d) & 1:
+                    lowered += (X[:, i] == 0) & (X[:, j] == 0)
+    assert (g["const"] + cut == E - lowered).all()
+    # and the min-cut solvers find the minimum of this energy
+    f, c = oracle.maxflow(w, h, g["tcap"], g["ncap"], "dinic")
+    assert f == cut.min()
+
+
+def _random_grid(rng, w, h, cap=2000, tmax=5000):
+    tcap = rng.integers(0, tmax, size=(h, w, 2)).astype(np.int32)
+    tcap[rng.random((h, w)) < 0.5, 0] = 0
+    tcap[tcap[..., 0] > 0, 1] = 0
+    ncap = rng.integers(0, cap, size=(h, w, 4)).astype(np.int32)
+    ncap[rng.random((h, w, 4)) < 0.3] = 0
+    return tcap, ncap
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_mincut_small_exhaustive(seed):
+    """<= 16 nodes: Dinic, Edmonds-Karp and enumeration agree on the value and the minimal cut."""
+    rng = np.random.default_rng(seed)
+    w, h = [(4, 4), (3, 5), (5, 3), (1, 16), (16, 1), (2, 2)][seed % 6]
+    tcap, ncap = _random_grid(rng, w, h, cap=int(rng.integers(1, 3000)))
+    f1, c1 = oracle.maxflow(w, h, tcap, ncap, "dinic")
+    f2, c2 = oracle.maxflow(w, h, tcap, ncap, "ek")
+    f3, c3 = oracle.maxflow(w, h, tcap, ncap, "enum")
+    assert f1 == f2 == f3
+    assert (c1 == c3).all() and (c2 == c3).all()
+
+
+def _scipy_maxflow(w, h, tcap, ncap):
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    n = w * h
+    rows, cols, caps = [], [], []
+    fdx, fdy = [1, -1, 0, 1], [0, 1, 1, 1]
+    for y in range(h):
+        for x in range(w):
+            i = y * w + x
+            if tcap[y, x, 0]:
+                rows.append(n); cols.append(i); caps.append(tcap[y, x, 0])
+            if tcap[y, x, 1]:
+                rows.append(i); cols.append(n + 1); caps.append(tcap[y, x, 1])
+            for d in range(4):
+                jx, jy = x + fdx[d], y + fdy[d]
+                if 0 <= jx < w and jy < h and ncap[y, x, d]:
+                    rows.append(i); cols.append(jy * w + jx); caps.append(ncap[y, x, d])
+    m = sp.csr_matrix((np.array(caps, np.int32), (rows, cols)), shape=(n + 2, n + 2))
+    return csg.maximum_flow(m, n, n + 1).flow_value
+
+
+@pytest.mark.parametrize("w,h,seed", [(15, 15, 0), (45, 45, 1), (75, 75, 2), (33, 7, 3)])
+def test_mincut_large_against_ek_and_scipy(w, h, seed):
+    """Random grid graphs up to 75x75: Dinic = Edmonds-Karp (value and cut) = scipy max-flow value."""
+    rng = np.random.default_rng(100 + seed)
+    tcap, ncap = _random_grid(rng, w, h)
+    f1, c1 = oracle.maxflow(w, h, tcap, ncap, "dinic")
+    f2, c2 = oracle.maxflow(w, h, tcap, ncap, "ek")
+    assert f1 == f2
+    assert (c1 == c2).all()
+    assert f1 == _scipy_maxflow(w, h, tcap, ncap)
+
+
+# --- the method: Algorithms 1 and 2 -------------------------------------------------
+
+def test_groups_are_disjoint_with_one_cell_gaps():
+    """Eq. groupindex: the 16 groups partition the cells; regions of one group are separated by >= 1 cell."""
+    for (H, W, s) in [(72, 96, 5), (375, 450, 15), (375, 450, 25), (40, 41, 5)]:
+        nx, ny = -(-W // s), -(-H // s)
+        seen = np.zeros((ny, nx), int)
+        for g in range(16):
+            cells = oracle.group_cells(H, W, s, g)
+            for (i, j) in cells:
+                seen[j, i] += 1
+                assert 4 * (j % 4) + (i % 4) == g
+            rects = [oracle.region_of(H, W, s, i, j)[0] for (i, j) in cells]
+            for a in range(len(rects)):
+                for b in range(a + 1, len(rects)):
+                    (ax, ay, aw, ah), (bx, by, bw, bh) = rects[a], rects[b]
+                    gapx = max(bx - (ax + aw), ax - (bx + bw))
+                    gapy = max(by - (ay + ah), ay - (by + bh))
+                    assert max(gapx, gapy) >= s
+        assert (seen == 1).all()
+
+
+def test_init_labels_pass_through_a_disparity_in_range():
+    """Random init (Sec. 3.4): the plane passes through (u, v, z0), z0 in [dmin, dmax]."""
+    for (u, v) in [(0, 0), (17, 3), (449, 374), (200, 100)]:
+        f = oracle.init_label(7, 450, u, v, 0.0, 60.0).astype(np.float64)
+        d = f[0] * u + f[1] * v + f[2]
+        assert -1e-3 <= d <= 60.0 + 1e-3
+
+
+def test_proposals_propagation_and_perturbation(tiny_pair):
+    """Propagation returns the label of a pixel r of the centre cell (Algorithm 2); perturbation
+    (Sec. 3.4) moves the disparity at r by at most r_d (then clamps it to the range) and tilts the
+    normal by at most asin(r_n)."""
+    rng = np.random.default_rng(2)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    lab = _random_state(o, rng)
+    cell = (10, 15, 5, 5)
+    where = {tuple(lab[y, x]): (x, y) for y in range(15, 20) for x in range(10, 15)}
+    rd, rn = 2.0, 0.5
+    for k in range(40):
+        st = oracle.proposal_stream(11, 0, 0, 2, 3, k)
+        a = oracle.propose(lab, st, cell, 0, 0, 0, 0.0, 15.0)
+        assert tuple(a) in where
+        x, y = where[tuple(a)]            # the same stream draws the same pixel first
+        b = oracle.propose(lab, st, cell, 1, rd, rn, 0.0, 15.0).astype(np.float64)
+        a = a.astype(np.float64)
+        d0 = a[0] * x + a[1] * y + a[2]
+        d1 = b[0] * x + b[1] * y + b[2]
+        lo, hi = min(max(d0 - rd, 0.0), 15.0), min(max(d0 + rd, 0.0), 15.0)
+        assert lo - 1e-3 <= d1 <= hi + 1e-3
+        n0 = np.array([-a[0], -a[1], 1.0]); n0 /= np.linalg.norm(n0)
+        n1 = np.array([-b[0], -b[1], 1.0]); n1 /= np.linalg.norm(n1)
+        ang = np.arccos(np.clip(abs(n0 @ n1), -1, 1))
+        assert ang <= np.arcsin(rn) + 1e-4
+
+
+def test_energy_never_increases_and_group_order_is_irrelevant(tiny_pair):
+    """Subproblem optimality (Sec. 3.3): E never increases over the moves of Algorithm 1;
+    independence (Lemma 3): reversing the order of the regions of a group changes nothing."""
+    kw = dict(TINY_PARAMS)
+    o1 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **kw)
+    o2 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], reverse_order=1, n_threads=1,
+                       **{k: v for k, v in kw.items()})
+    o1.init_state(); o2.init_state()
+    e_prev, q_prev = o1.energy()
+    for it in range(2):
+        for g in range(16):
+            o1.expand_group(it, 0, g)
+            o2.expand_group(it, 0, g)
+            e, q = o1.energy()
+            assert q <= q_prev
+            assert e <= e_prev + 1e-9
+            e_prev, q_prev = e, q
+    l1, c1 = o1.state(); l2, c2 = o2.state()
+    assert (l1 == l2).all() and (c1 == c2).all()
+
+
+def test_cost_cache_matches_definition_after_moves(tiny_pair):
+    """The cached phi_p(f_p) equals phi_p by definition for the current labels."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    o.init_state()
+    o.iterate(0)
+    lab, cost = o.state()
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        y, x = int(rng.integers(0, o.H)), int(rng.integers(0, o.W))
+        assert cost[y, x] == pytest.approx(o.phi_def(lab[y, x], x, y), abs=1e-11)
+
+
+def test_method_recovers_ground_truth_disparity(tiny_pair):
+    """After 4 iterations on the tiny scene most pixels are within 1 px of the rendered disparity."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    o.init_state()
+    for it in range(4):
+        o.iterate(it)
+    lab, _ = o.state()
+    v, u = np.mgrid[0:o.H, 0:o.W]
+    d = lab[..., 0] * u + lab[..., 1] * v + lab[..., 2]
+    assert (np.abs(d - tiny_pair["disp"]) > 1.0).mean() < 0.2
