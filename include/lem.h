@@ -1,0 +1,227 @@
+/*
+ * lem.h -- C ABI of the GB300 (sm_103a) local-expansion-move stereo library.
+ *
+ * Method: Taniai, Matsushita, Sato, Naemura, "Continuous 3D Label Stereo
+ * Matching using Local Expansion Moves" (arXiv 1603.08328).  Every pixel p of
+ * the left image carries a disparity plane f_p = (a, b, c), d_p = a u + b v + c
+ * (Sec. 3.2), and the energy E(f) = sum_p phi_p(f_p) + lambda sum_pq psi_pq
+ * (Eq. mrf) is lowered by local alpha-expansions on 3x3-cell regions
+ * (Sec. 3.3, Algorithms 1-2).
+ *
+ * Conventions for every entry point:
+ *  - All functions return an int status (LEM_OK = 0, negative on error) and
+ *    never throw, trap or abort.  lem_last_error() gives the text of the last
+ *    failure on a handle.
+ *  - Work is ordered on the CUDA stream given in lem_params.stream (NULL: the
+ *    legacy default stream).  Outputs written to device memory are valid once
+ *    that stream has been synchronised; the library does not synchronise unless
+ *    a function says so.
+ *  - Pointers documented as "device" must be device (or managed) memory owned
+ *    by the caller; "host" pointers are read before the call returns.  The
+ *    handle owns all memory it allocates and frees it in lem_destroy().
+ *  - Images are 8-bit RGB, rows of `width` interleaved R,G,B triples.
+ *  - Labels are float32 triples (a, b, c); pixel coordinates are 0-based pixel
+ *    centres, u = column, v = row; a left pixel u matches right pixel u - d.
+ */
+#ifndef LEM_H
+#define LEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LEM_OK 0
+#define LEM_ERR_ARG (-1)           /* bad argument (null pointer, value out of range) */
+#define LEM_ERR_SHAPE (-2)         /* image or region shape mismatch / too large        */
+#define LEM_ERR_CUDA (-3)          /* a CUDA call failed (text in lem_last_error)        */
+#define LEM_ERR_MAXFLOW_LIMIT (-4) /* a min-cut hit its round limit (labels kept)        */
+#define LEM_ERR_OOM (-5)           /* device allocation failed                           */
+
+/* internal storage of the packed images */
+#define LEM_STORE_F32 0
+#define LEM_STORE_F16 1
+#define LEM_STORE_BF16 2
+
+/* largest expansion region (nodes) a single CTA min-cut holds in shared memory:
+ * 75 x 75, i.e. 3x3 cells of 25 px */
+#define LEM_MAX_REGION_NODES 5625
+
+typedef struct {
+    const uint8_t *data; /* H x W x 3 RGB                                  */
+    int height, width;
+    int64_t stride_row;  /* bytes between rows (>= 3*width)                */
+    int on_device;       /* 1: `data` is device memory, 0: host memory     */
+} lem_image;
+
+/* Parameters.  lem_default_params() fills the values of the paper's
+ * experiments (Sec. 4, settings): e = 0.01^2, tau_col = 10, tau_grad = 2,
+ * alpha = 0.9, 41x41 matching windows (r' = 10), lambda = 1, tau_dis = 1,
+ * eps = 0.01, gamma = 10, 8-neighbourhood, cells 5/15/25 px with
+ * {K_prop, K_rand} = {1,7}, {2,0}, {2,0}. */
+typedef struct {
+    int gf_radius;        /* r': regression window (2r'+1)^2, matching window (4r'+1)^2 */
+    double gf_eps;        /* e in (Sigma_k + e U)^-1 (guide scaled to [0,1])            */
+    double tau_col;       /* truncation of the colour L1 term (0..255 scale)            */
+    double tau_grad;      /* truncation of the gradient term                            */
+    double alpha_grad;    /* alpha: weight of the gradient term                         */
+    double lambda;        /* smoothness weight                                          */
+    double tau_dis;       /* truncation of psi-bar                                      */
+    double eps_w;         /* lower bound of the contrast weight w_pq                    */
+    double gamma;         /* contrast weight scale                                      */
+    double disp_min;      /* disparity range of the random init / perturbation          */
+    double disp_max;
+    int n_levels;         /* number of grid levels (<= 3)                               */
+    int cell[3];          /* cell size in pixels per level                              */
+    int k_prop[3];        /* propagation proposals per region visit, per level          */
+    int k_rand[3];        /* perturbation proposals per region visit, per level         */
+    double quant_scale;   /* S: every energy term is quantised as rne(S x)              */
+    int store_dtype;      /* LEM_STORE_F32 (default), _F16, _BF16                        */
+    double cond_fp64;     /* 3x3 inverses with a larger condition estimate use FP64     */
+    uint64_t seed;        /* seed of all random draws                                   */
+    void *stream;         /* cudaStream_t                                               */
+    int max_rounds;       /* push-relabel round limit per cut                           */
+    int gr_interval;      /* push-relabel rounds between global relabels                */
+    int strip_rows;       /* rows per strip of the cost-aggregation pipeline            */
+    int threads;          /* threads per CTA of the expansion kernels                   */
+} lem_params;
+
+/* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
+typedef struct {
+    int x0, y0, w, h;
+} lem_region;
+
+typedef struct {
+    int64_t energy_q;      /* sum_p Q(phi_p) + sum_pq Q(lambda psi_pq), Q(x) = rne(S x) */
+    double energy;         /* energy_q / S                                             */
+    int64_t evals;         /* pixel-label cost evaluations done                        */
+    int64_t accepted;      /* pixels that switched to a candidate label                */
+    int64_t maxflow_limit; /* cuts that hit the round limit                            */
+    int32_t fp64_inverses; /* guide-covariance inverses taken in FP64 (lem_create)     */
+    int32_t iterations;    /* outer iterations done so far on this handle              */
+} lem_stats;
+
+typedef struct lem_handle lem_handle;
+
+/* Fills `p` with the paper's parameter values (see lem_params).  disp_max is
+ * set to 60; callers set it to their range. */
+void lem_default_params(lem_params *p);
+
+/* Creates a handle for one rectified pair.  Copies both images to the device,
+ * packs (R, G, B, x-gradient of gray) per pixel (Sec. 3.2, data term: gradient
+ * kernel [-0.5 0 0.5], BT.601 gray, edge pixels replicated), computes the
+ * guide statistics mu_k and (Sigma_k + eU)^-1 over every clipped window W'_k
+ * (Eq. gf), the contrast weights lambda*max(w_pq, eps) of the 4 forward
+ * neighbours (Eq. smweight), draws the random initial labels (Sec. 3.4:
+ * random disparity in [disp_min, disp_max] and random unit normal) and fills
+ * the cost cache phi_p(f_p).  left/right: same height and width.
+ * Errors: LEM_ERR_ARG (null pointers, bad parameters), LEM_ERR_SHAPE,
+ * LEM_ERR_OOM, LEM_ERR_CUDA.  On error *out is NULL. */
+int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out);
+
+/* Frees the handle and everything it owns.  NULL is accepted. */
+int lem_destroy(lem_handle *h);
+
+/* Text of the last error on `h` (or of the last failed lem_create when h is
+ * NULL).  The pointer stays valid until the next call on the same handle. */
+const char *lem_last_error(const lem_handle *h);
+
+/* Data term phi_p(alpha) (Eq. unary_term with the guided-filter weights of
+ * Eq. gf, count-normalised at the image border) for every p of each region and
+ * each of its K candidate labels, computed per region through the filtering
+ * region M (Sec. 3.5): raw costs rho(s|alpha) (Eqs. warp, photofunc; linear
+ * interpolation along u, u' clamped to [0, W-1]) over R grown by 2r', guided-
+ * filter coefficients over R grown by r', their window means over R.
+ *   regions : host, n_regions entries, each inside the image, w*h >= 1
+ *   labels  : device float32, n_regions*K*3: candidate k of region i at (i*K+k)*3
+ *   costs   : device float32, packed region-major: region i starts at
+ *             K * sum_{j<i} w_j*h_j; within it candidate k occupies w_i*h_i
+ *             values, row-major over R.
+ * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE (region outside the image), LEM_ERR_CUDA. */
+int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *labels, int K,
+                    float *costs);
+
+/* Binary expansion-move graph of each region against the handle's current
+ * labels and cost cache (Sec. 3.3; footnote to Lemma 2: neighbours outside R
+ * fold into the unaries; pairs inside R use the A + (C-A)x_p + (D-C)x_q +
+ * (B+C-A-D)(1-x_p)x_q decomposition with D = 0, valid by Lemma 1).  Every term
+ * is quantised as rne(S x); a quantised A above B + C is lowered to B + C.
+ * x_p = 1 (take alpha) puts p on the sink side.
+ *   regions     : host, n_regions entries (at most LEM_MAX_REGION_NODES nodes each)
+ *   alpha       : device float32, n_regions*3
+ *   costs_alpha : device float32, phi_p(alpha) packed as lem_unary_batch with K = 1
+ *   tcaps       : device int32, 2 per node {s->p: U_p(1)-m, p->t: U_p(0)-m}, packed like costs_alpha
+ *   ncaps       : device int32, 4 per node: capacity of p->q for the forward
+ *                 neighbours q = p+(1,0), p+(-1,1), p+(0,1), p+(1,1) inside R, else 0
+ *   const_term  : device int64, n_regions: energy of the terms touching R minus the cut
+ * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE, LEM_ERR_CUDA. */
+int lem_pairwise_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *alpha,
+                       const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *const_term);
+
+/* Minimum s-t cut of each region graph (layout of lem_pairwise_batch) by
+ * push-relabel with global relabelling, one CTA per region, in shared memory.
+ * take_alpha[p] = 1 iff p can reach the sink in the residual graph of the
+ * maximum preflow: the unique minimal sink side among all minimum cuts.
+ *   take_alpha : device uint8, 1 per node, packed like costs_alpha
+ *   flow       : device int64, n_regions: max-flow value (= min-cut value)
+ *   status     : device int32, n_regions: LEM_OK or LEM_ERR_MAXFLOW_LIMIT
+ * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE, LEM_ERR_CUDA.  A region that hits the
+ * round limit only sets its status; the call still returns LEM_OK. */
+int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, const int32_t *tcaps,
+                     const int32_t *ncaps, uint8_t *take_alpha, int64_t *flow, int32_t *status);
+
+/* All alpha_ij-expansions of one disjoint group k = 4 (j mod 4) + (i mod 4)
+ * (Eq. groupindex) at grid level `level` of outer iteration `iter`, in one
+ * launch (one CTA per region, Lemma 3): each region runs Algorithm 2
+ * (K_prop propagation proposals, then K_rand perturbation proposals with the
+ * perturbation size halved after each; outer sizes r_d = (disp_max-disp_min)/2
+ * and r_n = 1 halved per iteration), each proposal evaluated, cut and committed
+ * in turn.  Updates the handle's labels and cost cache.  Does not advance the
+ * handle's iteration counter.  stats may be NULL (no synchronisation); when
+ * given, the call synchronises the stream and fills evals/accepted/maxflow_limit
+ * for this launch.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *stats);
+
+/* n_iters outer iterations of Algorithm 1 (every level, all 16 groups),
+ * continuing from the handle's iteration counter.  stats may be NULL (no
+ * synchronisation); when given, the call synchronises and fills all fields
+ * (energy after the last iteration).  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats);
+
+/* Current labels and cost cache.  abc: float32 H*W*3, disp: float32 H*W
+ * (d_p = a u + b v + c), cost: float32 H*W; any may be NULL; `on_device`
+ * says whether the pointers are device (1) or host (0) memory.  Host copies
+ * synchronise the stream.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_get_labels(lem_handle *h, float *abc, float *disp, float *cost, int on_device);
+
+/* Replaces the labels (float32 H*W*3) and, when `cost` is not NULL, the cost
+ * cache (float32 H*W, taken as phi_p(f_p) for the new labels); with cost NULL
+ * the cache is recomputed by the data term.  on_device as in lem_get_labels.
+ * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_device);
+
+/* Quantised energy of the current labels (Eq. mrf, each unordered
+ * 8-neighbour pair once): *energy_q = sum_p Q(phi_p) + sum Q(lambda psi_pq),
+ * *energy = *energy_q / S.  Synchronises the stream.  Either pointer may be
+ * NULL.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_energy(lem_handle *h, double *energy, int64_t *energy_q);
+
+/* Device views of the handle's packed planes (for tests): left/right packed
+ * pixels (4 floats: R, G, B, gradient) as float32 H*W*4, guide statistics as
+ * float32 H*W*9 {mu_r, mu_g, mu_b, A00, A01, A02, A11, A12, A22}, and
+ * lambda*max(w, eps) for the 4 forward neighbours as float32 H*W*4.  Copies
+ * into caller device buffers; any may be NULL.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float *weights);
+
+/* Number of pixel-label cost evaluations in one outer iteration (sum over all
+ * region visits of |R| x proposals).  Host only. */
+int64_t lem_evals_per_iteration(const lem_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEM_H */

@@ -1,0 +1,491 @@
+// C ABI of the local-expansion-move library: handle management, argument
+// checking and the host-side schedule of Algorithm 1.  All device work is in
+// lem_kernels.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lem.h"
+#include "lem_internal.h"
+
+struct lem_handle {
+    int H = 0, W = 0;
+    lem_params p{};
+    cudaStream_t st = nullptr;
+    float4 *L = nullptr, *R = nullptr, *gst = nullptr, *wfw = nullptr, *lab = nullptr;
+    float *phiA = nullptr;
+    long long *e_part = nullptr, *e_out = nullptr;
+    lem::Counters *ctr = nullptr;
+    int *n_fp64 = nullptr;
+    int4 *d_regions = nullptr;
+    int64_t *d_offsets = nullptr;
+    size_t cap_regions = 0;
+    int iter = 0;
+    int fp64_inverses = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(lem_handle *h, int code, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(lem_handle *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? LEM_ERR_OOM : LEM_ERR_CUDA, m);
+}
+
+#define LEM_CUDA(h, call)                                      \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+lem::DevPlanes planes(const lem_handle *h) {
+    lem::DevPlanes P;
+    P.H = h->H;
+    P.W = h->W;
+    P.L = h->L;
+    P.R = h->R;
+    P.gst = h->gst;
+    P.wfw = h->wfw;
+    return P;
+}
+
+lem::KParams kparams(const lem_handle *h) {
+    const lem_params &p = h->p;
+    lem::KParams k;
+    k.r = p.gf_radius;
+    k.tau_col = (float)p.tau_col;
+    k.tau_grad = (float)p.tau_grad;
+    k.alpha_grad = (float)p.alpha_grad;
+    k.tau_dis = (float)p.tau_dis;
+    k.S = (float)p.quant_scale;
+    k.disp_min = p.disp_min;
+    k.disp_max = p.disp_max;
+    k.seed = p.seed;
+    k.max_rounds = p.max_rounds;
+    k.gr_interval = p.gr_interval;
+    k.T = p.strip_rows;
+    return k;
+}
+
+int check_params(const lem_params *p) {
+    if (!p) return fail(nullptr, LEM_ERR_ARG, "params is NULL");
+    if (p->gf_radius < 0 || p->gf_radius > 32) return fail(nullptr, LEM_ERR_ARG, "gf_radius out of range [0, 32]");
+    if (!(p->gf_eps > 0)) return fail(nullptr, LEM_ERR_ARG, "gf_eps must be > 0");
+    if (p->n_levels < 1 || p->n_levels > 3) return fail(nullptr, LEM_ERR_ARG, "n_levels must be 1..3");
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->cell[l] < 1) return fail(nullptr, LEM_ERR_ARG, "cell size must be >= 1");
+        if (9 * p->cell[l] * p->cell[l] > LEM_MAX_REGION_NODES)
+            return fail(nullptr, LEM_ERR_ARG, "cell size too large: a 3x3-cell region exceeds LEM_MAX_REGION_NODES");
+        if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_prop[l] + p->k_rand[l] < 1)
+            return fail(nullptr, LEM_ERR_ARG, "each level needs at least one proposal");
+    }
+    if (!(p->disp_max >= p->disp_min)) return fail(nullptr, LEM_ERR_ARG, "disp_max < disp_min");
+    if (!(p->quant_scale > 0) || p->quant_scale > 1048576.0)
+        return fail(nullptr, LEM_ERR_ARG, "quant_scale must be in (0, 2^20]");
+    if (p->store_dtype != LEM_STORE_F32) return fail(nullptr, LEM_ERR_ARG, "store_dtype: only LEM_STORE_F32 is built");
+    if (p->max_rounds < 1 || p->gr_interval < 1) return fail(nullptr, LEM_ERR_ARG, "max_rounds/gr_interval must be >= 1");
+    if (p->strip_rows < 1 || p->strip_rows > 64) return fail(nullptr, LEM_ERR_ARG, "strip_rows must be 1..64");
+    if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
+        return fail(nullptr, LEM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+    return LEM_OK;
+}
+
+int check_image(const lem_image *im, const char *name) {
+    if (!im || !im->data) return fail(nullptr, LEM_ERR_ARG, std::string(name) + " image is NULL");
+    if (im->height < 1 || im->width < 2) return fail(nullptr, LEM_ERR_SHAPE, std::string(name) + " image too small");
+    if (im->stride_row < 3LL * im->width) return fail(nullptr, LEM_ERR_SHAPE, std::string(name) + " stride_row < 3*width");
+    if ((int64_t)im->height * im->width > (1LL << 30)) return fail(nullptr, LEM_ERR_SHAPE, "image too large");
+    return LEM_OK;
+}
+
+void free_handle(lem_handle *h) {
+    if (!h) return;
+    cudaFree(h->L);
+    cudaFree(h->R);
+    cudaFree(h->gst);
+    cudaFree(h->wfw);
+    cudaFree(h->lab);
+    cudaFree(h->phiA);
+    cudaFree(h->e_part);
+    cudaFree(h->e_out);
+    cudaFree(h->ctr);
+    cudaFree(h->n_fp64);
+    cudaFree(h->d_regions);
+    cudaFree(h->d_offsets);
+    delete h;
+}
+
+// Uploads regions (host) and their packed offsets (K values per pixel).
+int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_t *total, int *max_w, int *max_h,
+                  int *max_n) {
+    if (!regions || n < 1) return fail(h, LEM_ERR_ARG, "regions is NULL or n_regions < 1");
+    std::vector<int4> rg(n);
+    std::vector<int64_t> off(n);
+    int64_t acc = 0;
+    int mw = 0, mh = 0, mn = 0;
+    for (int i = 0; i < n; ++i) {
+        const lem_region &r = regions[i];
+        if (r.w < 1 || r.h < 1 || r.x0 < 0 || r.y0 < 0 || r.x0 + r.w > h->W || r.y0 + r.h > h->H)
+            return fail(h, LEM_ERR_SHAPE, "region " + std::to_string(i) + " is empty or outside the image");
+        rg[i] = make_int4(r.x0, r.y0, r.w, r.h);
+        off[i] = acc;
+        acc += (int64_t)K * r.w * r.h;
+        mw = std::max(mw, r.w);
+        mh = std::max(mh, r.h);
+        mn = std::max(mn, r.w * r.h);
+    }
+    if ((size_t)n > h->cap_regions) {
+        cudaFree(h->d_regions);
+        cudaFree(h->d_offsets);
+        h->d_regions = nullptr;
+        h->d_offsets = nullptr;
+        LEM_CUDA(h, cudaMalloc(&h->d_regions, sizeof(int4) * n));
+        LEM_CUDA(h, cudaMalloc(&h->d_offsets, sizeof(int64_t) * n));
+        h->cap_regions = n;
+    }
+    LEM_CUDA(h, cudaMemcpyAsync(h->d_regions, rg.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, h->st));
+    LEM_CUDA(h, cudaMemcpyAsync(h->d_offsets, off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->st));
+    // the staging vectors die on return: make sure the copies have read them
+    LEM_CUDA(h, cudaStreamSynchronize(h->st));
+    *total = acc;
+    *max_w = mw;
+    *max_h = mh;
+    *max_n = mn;
+    return LEM_OK;
+}
+
+int run_energy(lem_handle *h, long long *eq) {
+    lem::KParams kp = kparams(h);
+    LEM_CUDA(h, lem::launch_energy(planes(h), kp, h->lab, h->e_part, h->e_out, h->st));
+    LEM_CUDA(h, cudaMemcpyAsync(eq, h->e_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st));
+    LEM_CUDA(h, cudaStreamSynchronize(h->st));
+    return LEM_OK;
+}
+
+int threads_for_level(const lem_handle *h, int s) {
+    (void)s;
+    return h->p.threads;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lem_default_params(lem_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->gf_radius = 10;
+    p->gf_eps = 1e-4;
+    p->tau_col = 10.0;
+    p->tau_grad = 2.0;
+    p->alpha_grad = 0.9;
+    p->lambda = 1.0;
+    p->tau_dis = 1.0;
+    p->eps_w = 0.01;
+    p->gamma = 10.0;
+    p->disp_min = 0.0;
+    p->disp_max = 60.0;
+    p->n_levels = 3;
+    p->cell[0] = 5;
+    p->cell[1] = 15;
+    p->cell[2] = 25;
+    p->k_prop[0] = 1;
+    p->k_prop[1] = 2;
+    p->k_prop[2] = 2;
+    p->k_rand[0] = 7;
+    p->k_rand[1] = 0;
+    p->k_rand[2] = 0;
+    p->quant_scale = 65536.0;
+    p->store_dtype = LEM_STORE_F32;
+    p->cond_fp64 = 1e3;
+    p->seed = 1;
+    p->stream = nullptr;
+    p->max_rounds = 200000;
+    p->gr_interval = 16;
+    p->strip_rows = 8;
+    p->threads = 256;
+}
+
+const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out) {
+    if (!out) return fail(nullptr, LEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc;
+    if ((rc = check_params(p)) != LEM_OK) return rc;
+    if ((rc = check_image(left, "left")) != LEM_OK) return rc;
+    if ((rc = check_image(right, "right")) != LEM_OK) return rc;
+    if (left->height != right->height || left->width != right->width)
+        return fail(nullptr, LEM_ERR_SHAPE, "left and right images differ in size");
+    const int H = left->height, W = left->width;
+    if (W < 2 * p->gf_radius + 1 || H < 2 * p->gf_radius + 1)
+        return fail(nullptr, LEM_ERR_SHAPE, "image smaller than one regression window");
+    lem_handle *h = new lem_handle();
+    h->H = H;
+    h->W = W;
+    h->p = *p;
+    h->st = (cudaStream_t)p->stream;
+    const size_t n = (size_t)H * W;
+    auto bail = [&](int code) {
+        g_create_err = h->err;
+        free_handle(h);
+        return code;
+    };
+#define CREATE_CUDA(call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
+    } while (0)
+    CREATE_CUDA(cudaMalloc(&h->L, sizeof(float4) * n));
+    CREATE_CUDA(cudaMalloc(&h->R, sizeof(float4) * n));
+    CREATE_CUDA(cudaMalloc(&h->gst, sizeof(float4) * 3 * n));
+    CREATE_CUDA(cudaMalloc(&h->wfw, sizeof(float4) * n));
+    CREATE_CUDA(cudaMalloc(&h->lab, sizeof(float4) * n));
+    CREATE_CUDA(cudaMalloc(&h->phiA, sizeof(float) * n));
+    CREATE_CUDA(cudaMalloc(&h->e_part, sizeof(long long) * lem::energy_partials(H, W)));
+    CREATE_CUDA(cudaMalloc(&h->e_out, sizeof(long long)));
+    CREATE_CUDA(cudaMalloc(&h->ctr, sizeof(lem::Counters)));
+    CREATE_CUDA(cudaMalloc(&h->n_fp64, sizeof(int)));
+    CREATE_CUDA(cudaMemsetAsync(h->n_fp64, 0, sizeof(int), h->st));
+    CREATE_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
+    // images on the device (copied from the host when needed)
+    const uint8_t *dl = left->data, *dr = right->data;
+    int64_t ls = left->stride_row, rs = right->stride_row;
+    uint8_t *tmp = nullptr;
+    if (!left->on_device || !right->on_device) {
+        CREATE_CUDA(cudaMalloc(&tmp, 2 * n * 3));
+        if (!left->on_device) {
+            CREATE_CUDA(cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H,
+                                          cudaMemcpyHostToDevice, h->st));
+            dl = tmp;
+            ls = 3 * W;
+        }
+        if (!right->on_device) {
+            CREATE_CUDA(cudaMemcpy2DAsync(tmp + 3 * n, 3 * W, right->data, right->stride_row, 3 * W, H,
+                                          cudaMemcpyHostToDevice, h->st));
+            dr = tmp + 3 * n;
+            rs = 3 * W;
+        }
+    }
+    cudaError_t e = lem::launch_preprocess(dl, ls, dr, rs, H, W, (float)p->lambda, (float)p->eps_w,
+                                           (float)p->gamma, h->L, h->R, h->wfw, h->st);
+    if (e == cudaSuccess)
+        e = lem::launch_guide_stats(dl, ls, H, W, p->gf_radius, p->gf_eps, p->cond_fp64, h->gst, h->n_fp64, h->st);
+    if (e == cudaSuccess) e = lem::launch_init_labels(H, W, p->seed, p->disp_min, p->disp_max, h->lab, h->st);
+    if (e == cudaSuccess) e = lem::launch_pixel_costs(planes(h), kparams(h), h->lab, std::min(p->threads, 128), h->st);
+    int nf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nf, h->n_fp64, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "lem_create kernels"));
+#undef CREATE_CUDA
+    h->fp64_inverses = nf;
+    *out = h;
+    return LEM_OK;
+}
+
+int lem_destroy(lem_handle *h) {
+    if (h && h->st) cudaStreamSynchronize(h->st);
+    free_handle(h);
+    return LEM_OK;
+}
+
+int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *labels, int K,
+                    float *costs) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!labels || !costs || K < 1) return fail(h, LEM_ERR_ARG, "labels/costs NULL or K < 1");
+    int64_t total;
+    int mw, mh, mn, rc;
+    if ((rc = stage_regions(h, regions, n_regions, K, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
+    if ((int64_t)n_regions * K > (1LL << 31) - 1) return fail(h, LEM_ERR_ARG, "too many region-label pairs");
+    LEM_CUDA(h, lem::launch_unary_batch(planes(h), kparams(h), h->d_regions, h->d_offsets, n_regions, K, mw, mh,
+                                        labels, costs, h->p.threads, h->st));
+    return LEM_OK;
+}
+
+int lem_pairwise_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *alpha,
+                       const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *const_term) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!alpha || !costs_alpha || !tcaps || !ncaps || !const_term) return fail(h, LEM_ERR_ARG, "NULL pointer");
+    int64_t total;
+    int mw, mh, mn, rc;
+    if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
+    if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
+    LEM_CUDA(h, lem::launch_pairwise_batch(planes(h), kparams(h), h->d_regions, h->d_offsets, n_regions, h->lab,
+                                           alpha, costs_alpha, tcaps, ncaps, const_term, h->p.threads, h->st));
+    return LEM_OK;
+}
+
+int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, const int32_t *tcaps,
+                     const int32_t *ncaps, uint8_t *take_alpha, int64_t *flow, int32_t *status) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!tcaps || !ncaps || !take_alpha || !flow || !status) return fail(h, LEM_ERR_ARG, "NULL pointer");
+    int64_t total;
+    int mw, mh, mn, rc;
+    if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
+    if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
+    LEM_CUDA(h, lem::launch_mincut_batch(kparams(h), h->d_regions, h->d_offsets, n_regions, mn, tcaps, ncaps,
+                                         take_alpha, flow, status, h->p.threads, h->st));
+    return LEM_OK;
+}
+
+static int expand_group_impl(lem_handle *h, int iter, int level, int group) {
+    lem::Level lv;
+    lv.s = h->p.cell[level];
+    lv.k_prop = h->p.k_prop[level];
+    lv.k_rand = h->p.k_rand[level];
+    LEM_CUDA(h, lem::launch_expand_group(planes(h), kparams(h), lv, level, iter, group, h->lab, h->phiA, h->ctr,
+                                         threads_for_level(h, lv.s), h->st));
+    return LEM_OK;
+}
+
+int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *stats) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (iter < 0 || level < 0 || level >= h->p.n_levels || group < 0 || group > 15)
+        return fail(h, LEM_ERR_ARG, "iter/level/group out of range");
+    if (stats) LEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
+    int rc = expand_group_impl(h, iter, level, group);
+    if (rc != LEM_OK) return rc;
+    if (stats) {
+        lem::Counters c;
+        LEM_CUDA(h, cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, h->st));
+        LEM_CUDA(h, cudaStreamSynchronize(h->st));
+        std::memset(stats, 0, sizeof(*stats));
+        stats->evals = (int64_t)c.evals;
+        stats->accepted = (int64_t)c.accepted;
+        stats->maxflow_limit = (int64_t)c.limit_hits;
+        stats->fp64_inverses = h->fp64_inverses;
+        stats->iterations = h->iter;
+    }
+    return LEM_OK;
+}
+
+int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (n_iters < 0) return fail(h, LEM_ERR_ARG, "n_iters < 0");
+    if (stats) LEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
+    for (int it = 0; it < n_iters; ++it) {
+        for (int l = 0; l < h->p.n_levels; ++l)
+            for (int g = 0; g < 16; ++g) {
+                int rc = expand_group_impl(h, h->iter, l, g);
+                if (rc != LEM_OK) return rc;
+            }
+        ++h->iter;
+    }
+    if (stats) {
+        lem::Counters c;
+        LEM_CUDA(h, cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, h->st));
+        long long eq = 0;
+        int rc = run_energy(h, &eq);
+        if (rc != LEM_OK) return rc;
+        stats->energy_q = eq;
+        stats->energy = (double)eq / h->p.quant_scale;
+        stats->evals = (int64_t)c.evals;
+        stats->accepted = (int64_t)c.accepted;
+        stats->maxflow_limit = (int64_t)c.limit_hits;
+        stats->fp64_inverses = h->fp64_inverses;
+        stats->iterations = h->iter;
+    }
+    return LEM_OK;
+}
+
+int lem_get_labels(lem_handle *h, float *abc, float *disp, float *cost, int on_device) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    const size_t n = (size_t)h->H * h->W;
+    if (on_device) {
+        LEM_CUDA(h, lem::launch_labels_out(h->H, h->W, h->lab, abc, disp, cost, h->st));
+        return LEM_OK;
+    }
+    float *d = nullptr;
+    LEM_CUDA(h, cudaMalloc(&d, sizeof(float) * n * 5));
+    cudaError_t e = lem::launch_labels_out(h->H, h->W, h->lab, d, d + 3 * n, d + 4 * n, h->st);
+    if (e == cudaSuccess && abc) e = cudaMemcpyAsync(abc, d, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && disp)
+        e = cudaMemcpyAsync(disp, d + 3 * n, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && cost)
+        e = cudaMemcpyAsync(cost, d + 4 * n, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lem_get_labels");
+    return LEM_OK;
+}
+
+int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_device) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!abc) return fail(h, LEM_ERR_ARG, "abc is NULL");
+    const size_t n = (size_t)h->H * h->W;
+    const float *dabc = abc, *dcost = cost;
+    float *tmp = nullptr;
+    if (!on_device) {
+        LEM_CUDA(h, cudaMalloc(&tmp, sizeof(float) * n * 4));
+        cudaError_t e = cudaMemcpyAsync(tmp, abc, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess && cost)
+            e = cudaMemcpyAsync(tmp + 3 * n, cost, sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(h, e, "lem_set_labels copy");
+        }
+        dabc = tmp;
+        dcost = cost ? tmp + 3 * n : nullptr;
+    }
+    cudaError_t e = lem::launch_labels_in(h->H, h->W, dabc, dcost, h->lab, h->st);
+    if (e == cudaSuccess && !cost)
+        e = lem::launch_pixel_costs(planes(h), kparams(h), h->lab, std::min(h->p.threads, 128), h->st);
+    if (tmp) {
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "lem_set_labels");
+    return LEM_OK;
+}
+
+int lem_energy(lem_handle *h, double *energy, int64_t *energy_q) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    long long eq = 0;
+    int rc = run_energy(h, &eq);
+    if (rc != LEM_OK) return rc;
+    if (energy_q) *energy_q = eq;
+    if (energy) *energy = (double)eq / h->p.quant_scale;
+    return LEM_OK;
+}
+
+int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float *weights) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    LEM_CUDA(h, lem::launch_planes_out(h->H, h->W, planes(h), left, right, guide, weights, h->st));
+    return LEM_OK;
+}
+
+int64_t lem_evals_per_iteration(const lem_handle *h) {
+    if (!h) return -1;
+    int64_t tot = 0;
+    for (int l = 0; l < h->p.n_levels; ++l) {
+        const int s = h->p.cell[l];
+        const int nx = (h->W + s - 1) / s, ny = (h->H + s - 1) / s;
+        const int np = h->p.k_prop[l] + h->p.k_rand[l];
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int x0 = std::max(0, (i - 1) * s), x1 = std::min(h->W, (i + 2) * s);
+                const int y0 = std::max(0, (j - 1) * s), y1 = std::min(h->H, (j + 2) * s);
+                tot += (int64_t)(x1 - x0) * (y1 - y0) * np;
+            }
+    }
+    return tot;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the host API (lem_api.cu) and the kernels
+// (lem_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lem.h"
+
+namespace lem {
+
+// Device views of one pair's packed planes.
+struct DevPlanes {
+    int H, W;
+    const float4 *L;    // left:  (R, G, B, x-gradient of gray), 0..255 scale
+    const float4 *R;    // right: same
+    const float4 *gst;  // 3 float4 per pixel: {mu_r, mu_g, mu_b, A00}, {A01, A02, A11, A12}, {A22, 0, 0, 0}
+    const float4 *wfw;  // lambda * max(w_pq, eps) for the forward neighbours (1,0), (-1,1), (0,1), (1,1)
+};
+
+// Scalar parameters as the kernels use them.
+struct KParams {
+    int r;              // guided-filter radius r'
+    float tau_col, tau_grad, alpha_grad;
+    float tau_dis;
+    float S;            // quantisation scale
+    double disp_min, disp_max;
+    unsigned long long seed;
+    int max_rounds;     // push-relabel round limit
+    int gr_interval;    // rounds between global relabels
+    int T;              // strip rows of the aggregation pipeline
+};
+
+// One grid level of Algorithm 1.
+struct Level {
+    int s;              // cell size
+    int k_prop, k_rand;
+};
+
+// Per-launch counters written by the expansion kernels.
+struct Counters {
+    unsigned long long accepted;
+    unsigned long long limit_hits;
+    unsigned long long evals;
+    unsigned long long pad;
+};
+
+// Shared-memory bytes the region cost pipeline needs for regions up to
+// rw x rh pixels.
+size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh);
+// Shared-memory bytes of the CTA min-cut for n nodes.
+size_t cut_smem_bytes(int n);
+
+cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
+                              int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
+                              cudaStream_t st);
+cudaError_t launch_guide_stats(const uint8_t *left, int64_t lstride, int H, int W, int r, double eps,
+                               double cond_fp64, float4 *gst, int *n_fp64, cudaStream_t st);
+cudaError_t launch_init_labels(int H, int W, unsigned long long seed, double dmin, double dmax, float4 *lab,
+                               cudaStream_t st);
+// phi_p(f_p) for every pixel with its own label (1x1 regions).
+cudaError_t launch_pixel_costs(const DevPlanes &P, const KParams &kp, float4 *lab, int threads, cudaStream_t st);
+cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
+                               int n_regions, int K, int max_w, int max_h, const float *labels, float *costs,
+                               int threads, cudaStream_t st);
+cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const int4 *regions,
+                                  const int64_t *offsets, int n_regions, const float4 *lab, const float *alpha,
+                                  const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *cterm,
+                                  int threads, cudaStream_t st);
+cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
+                                int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                int64_t *flow, int32_t *status, int threads, cudaStream_t st);
+cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                                int group, float4 *lab, float *phiA, Counters *ctr, int threads, cudaStream_t st);
+cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
+                          long long *out, cudaStream_t st);
+cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,
+                              cudaStream_t st);
+cudaError_t launch_labels_in(int H, int W, const float *abc, const float *cost, float4 *lab, cudaStream_t st);
+cudaError_t launch_planes_out(int H, int W, const DevPlanes &P, float *left, float *right, float *guide,
+                              float *weights, cudaStream_t st);
+int energy_partials(int H, int W);
+
+}  // namespace lem

@@ -1,0 +1,1032 @@
+// CUDA kernels of local-expansion-move stereo (arXiv 1603.08328) for sm_103a.
+//
+// Layout in device memory (one pair):
+//   L, R  : float4 per pixel (R, G, B, x-gradient of gray), 0..255 scale
+//   gst   : 3 float4 per pixel, guide mean mu_k and (Sigma_k + eU)^-1 (sym.)
+//   wfw   : float4 per pixel, lambda * max(w_pq, eps), forward neighbours
+//   lab   : float4 per pixel (a, b, c, phi_p(f_p)): label and cost cache
+//   phiA  : float per pixel, phi_p(alpha) of the candidate being evaluated
+//           (expansion regions of one group are disjoint, so one plane serves)
+//
+// One CTA evaluates, cuts and commits one expansion region.  The data term is
+// computed through the filtering region M as a strip pipeline in shared
+// memory (raw cost rows -> vertical window sums -> horizontal window sums ->
+// guided-filter coefficients -> their window means), then the move graph is
+// built in shared memory and cut by push-relabel with global relabelling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "lem_internal.h"
+
+namespace lem {
+namespace {
+
+constexpr uint16_t kInf = 0xFFFF;
+
+// 8-neighbourhood: k < 4 are the forward neighbours (1,0), (-1,1), (0,1), (1,1)
+// (each unordered pair once); k >= 4 the opposite offsets.  Reverse of k is k^4.
+__device__ __forceinline__ int dir_dx(int k) {
+    const int d = k & 3;
+    const int dx = (d == 0 || d == 3) ? 1 : (d == 1 ? -1 : 0);
+    return k < 4 ? dx : -dx;
+}
+__device__ __forceinline__ int dir_dy(int k) {
+    const int d = k & 3;
+    const int dy = d == 0 ? 0 : 1;
+    return k < 4 ? dy : -dy;
+}
+__device__ __forceinline__ float comp(const float4 &v, int d) {
+    return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+}
+
+// ---------------------------------------------------------------------------
+// error-free transformations (never contracted into FMA: explicit _rn ops)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+__device__ __forceinline__ float two_prod(float a, float b, float &err) {
+    const float p = __fmul_rn(a, b);
+    err = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// d_(u,v)(f1) - d_(u,v)(f2) with d_p(f) = a u + b v + c, in float-float so the
+// result is accurate even for steep planes with large |c|.  Antisymmetric
+// bit for bit: dd(f2, f1) == -dd(f1, f2).
+__device__ __forceinline__ float disp_diff(const float4 &f1, const float4 &f2, float u, float v) {
+    float al, bl, cl, e1, e2, e3, e4;
+    const float ah = two_sum(f1.x, -f2.x, al);
+    const float bh = two_sum(f1.y, -f2.y, bl);
+    const float ch = two_sum(f1.z, -f2.z, cl);
+    const float x1 = two_prod(ah, u, e1);
+    const float x2 = two_prod(bh, v, e2);
+    const float s1 = two_sum(x1, x2, e3);
+    const float s2 = two_sum(s1, ch, e4);
+    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4));
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fmul_rn(al, u), __fmul_rn(bl, v)), cl));
+    return __fadd_rn(s2, lo);
+}
+
+// Q(lambda psi_pq(f1, f2)) for the pair (p = (u1,v1), q = (u2,v2)) with weight
+// wl = lambda max(w_pq, eps): psi-bar = |d_p(f1) - d_p(f2)| + |d_q(f2) - d_q(f1)|
+// (Eq. smooth), truncated at tau_dis (Eq. smooth_phi); Q(x) = rne(S x).
+// Symmetric bit for bit under swapping (f1 at p) <-> (f2 at q).
+__device__ __forceinline__ int q_psi(float wl, float tau, float S, const float4 &f1, const float4 &f2, int u1,
+                                     int v1, int u2, int v2) {
+    const float D1 = disp_diff(f1, f2, (float)u1, (float)v1);
+    const float D2 = disp_diff(f1, f2, (float)u2, (float)v2);
+    const float pb = __fadd_rn(fabsf(D1), fabsf(D2));
+    const float psi = __fmul_rn(wl, fminf(pb, tau));
+    return __float2int_rn(__fmul_rn(psi, S));
+}
+
+__device__ __forceinline__ int q_cost(float phi, float S) { return __float2int_rn(__fmul_rn(phi, S)); }
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood 2014) and the random label arithmetic of the
+// proposals, in FP64 with explicitly rounded operations so the candidate
+// labels are bit-identical to a CPU evaluation of the same steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sm_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+struct Rng {
+    unsigned long long s;
+    __device__ double u01() {
+        s += 0x9E3779B97F4A7C15ull;
+        return __dmul_rn(__ull2double_rn(sm_mix(s) >> 11), 0x1.0p-53);
+    }
+};
+__device__ __forceinline__ unsigned long long proposal_stream(unsigned long long seed, int iter, int level, int ci,
+                                                              int cj, int prop) {
+    unsigned long long s = sm_mix(seed);
+    s = sm_mix(s ^ (unsigned long long)iter);
+    s = sm_mix(s ^ (unsigned long long)level);
+    s = sm_mix(s ^ (((unsigned long long)(unsigned)cj << 32) | (unsigned long long)(unsigned)ci));
+    s = sm_mix(s ^ (unsigned long long)prop);
+    return s;
+}
+__device__ __forceinline__ double dsq3(double x, double y, double z) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+}
+// uniform unit vector by rejection from the cube; (0,0,1) after 1000 misses
+__device__ void unit_vec(Rng &g, double &x, double &y, double &z) {
+    for (int t = 0; t < 1000; ++t) {
+        const double a = __dsub_rn(__dmul_rn(2.0, g.u01()), 1.0);
+        const double b = __dsub_rn(__dmul_rn(2.0, g.u01()), 1.0);
+        const double c = __dsub_rn(__dmul_rn(2.0, g.u01()), 1.0);
+        const double s = dsq3(a, b, c);
+        if (s > 1.0 || s == 0.0) continue;
+        const double l = __dsqrt_rn(s);
+        x = __ddiv_rn(a, l);
+        y = __ddiv_rn(b, l);
+        z = __ddiv_rn(c, l);
+        return;
+    }
+    x = 0.0;
+    y = 0.0;
+    z = 1.0;
+}
+// plane through (u, v, z0) with unit normal n: a = -nx/nz, b = -ny/nz,
+// c = (nx u + ny v + nz z0)/nz
+__device__ __forceinline__ float4 plane_from(double nx, double ny, double nz, int u, int v, double z0) {
+    const double c = __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(nx, (double)u), __dmul_rn(ny, (double)v)),
+                                         __dmul_rn(nz, z0)),
+                               nz);
+    return make_float4(__double2float_rn(__ddiv_rn(-nx, nz)), __double2float_rn(__ddiv_rn(-ny, nz)),
+                       __double2float_rn(c), 0.f);
+}
+
+// Candidate of one proposal of Algorithm 2 from the current label map.
+__device__ float4 propose(const float4 *lab, int W, unsigned long long stream, int cx0, int cy0, int cw, int chh,
+                          bool perturb, double rd, double rn, double dmin, double dmax) {
+    Rng g{stream};
+    const int n = cw * chh;
+    int k = (int)__dmul_rn(g.u01(), (double)n);
+    if (k >= n) k = n - 1;
+    const int ru = cx0 + k % cw, rv = cy0 + k / cw;
+    const float4 f = lab[(size_t)rv * W + ru];
+    if (!perturb) return make_float4(f.x, f.y, f.z, 0.f);
+    const double a = f.x, b = f.y, c = f.z;
+    const double d = __dadd_rn(__dadd_rn(__dmul_rn(a, (double)ru), __dmul_rn(b, (double)rv)), c);
+    const double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), 1.0));
+    const double n0 = __ddiv_rn(-a, len), n1 = __ddiv_rn(-b, len), n2 = __ddiv_rn(1.0, len);
+    double dp = __dadd_rn(d, __dmul_rn(rd, __dsub_rn(__dmul_rn(2.0, g.u01()), 1.0)));
+    if (dp < dmin) dp = dmin;
+    if (dp > dmax) dp = dmax;
+    double m0 = n0, m1 = n1, m2 = n2;
+    for (int t = 0; t < 64; ++t) {
+        double vx, vy, vz;
+        unit_vec(g, vx, vy, vz);
+        double q0 = __dadd_rn(n0, __dmul_rn(rn, vx));
+        double q1 = __dadd_rn(n1, __dmul_rn(rn, vy));
+        double q2 = __dadd_rn(n2, __dmul_rn(rn, vz));
+        const double ql = __dsqrt_rn(dsq3(q0, q1, q2));
+        if (ql == 0.0) continue;
+        q0 = __ddiv_rn(q0, ql);
+        q1 = __ddiv_rn(q1, ql);
+        q2 = __ddiv_rn(q2, ql);
+        if (fabs(q2) < 1e-3) continue;
+        m0 = q0;
+        m1 = q1;
+        m2 = q2;
+        break;
+    }
+    return plane_from(m0, m1, m2, ru, rv, dp);
+}
+
+// ---------------------------------------------------------------------------
+// K0: packing, contrast weights, guide statistics, random init
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int gray1000(const uint8_t *c) { return 299 * c[0] + 587 * c[1] + 114 * c[2]; }
+
+__global__ void k_preprocess(const uint8_t *left, int64_t ls, const uint8_t *right, int64_t rs, int H, int W,
+                             float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const uint8_t *lr = left + (size_t)y * ls, *rr = right + (size_t)y * rs;
+    const int xm = max(x - 1, 0), xp = min(x + 1, W - 1);
+    // BT.601 gray x 1000 is an exact integer; the [-0.5 0 0.5] gradient is
+    // then one correctly rounded division
+    const float gl = (float)(gray1000(lr + 3 * xp) - gray1000(lr + 3 * xm)) / 2000.0f;
+    const float gr = (float)(gray1000(rr + 3 * xp) - gray1000(rr + 3 * xm)) / 2000.0f;
+    const size_t p = (size_t)y * W + x;
+    Lp[p] = make_float4(lr[3 * x], lr[3 * x + 1], lr[3 * x + 2], gl);
+    Rp[p] = make_float4(rr[3 * x], rr[3 * x + 1], rr[3 * x + 2], gr);
+    float w[4];
+    for (int d = 0; d < 4; ++d) {
+        const int qx = x + dir_dx(d), qy = y + dir_dy(d);
+        w[d] = 0.f;
+        if (qx < 0 || qx >= W || qy >= H) continue;
+        const uint8_t *a = lr + 3 * x, *b = left + (size_t)qy * ls + 3 * qx;
+        const int l1 = abs((int)a[0] - (int)b[0]) + abs((int)a[1] - (int)b[1]) + abs((int)a[2] - (int)b[2]);
+        const float wv = expf(-(float)l1 / gamma);
+        w[d] = lambda * fmaxf(wv, eps_w);
+    }
+    wfw[p] = make_float4(w[0], w[1], w[2], w[3]);
+}
+
+// Guide statistics over the clipped window W'_k: exact integer window sums of
+// the 8-bit colours, so N^2 255^2 Sigma_k = N S2 - S1 S1^T is exact in int64.
+// (Sigma_k + eU)^-1 by the adjugate in FP32; when the Frobenius condition
+// estimate exceeds cond_fp64 the inverse is redone in FP64 from the exact sums.
+__global__ void k_guide_stats(const uint8_t *left, int64_t ls, int H, int W, int r, double eps, double cond_fp64,
+                              float4 *gst, int *n_fp64) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const int x0 = max(0, x - r), x1 = min(W - 1, x + r), y0 = max(0, y - r), y1 = min(H - 1, y + r);
+    int s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
+    for (int yy = y0; yy <= y1; ++yy) {
+        const uint8_t *row = left + (size_t)yy * ls;
+        for (int xx = x0; xx <= x1; ++xx) {
+            const int r0 = row[3 * xx], g0 = row[3 * xx + 1], b0 = row[3 * xx + 2];
+            s1[0] += r0;
+            s1[1] += g0;
+            s1[2] += b0;
+            s2[0] += r0 * r0;
+            s2[1] += r0 * g0;
+            s2[2] += r0 * b0;
+            s2[3] += g0 * g0;
+            s2[4] += g0 * b0;
+            s2[5] += b0 * b0;
+        }
+    }
+    const long long N = (long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+    long long num[6];
+    for (int k = 0; k < 6; ++k) num[k] = N * (long long)s2[k] - (long long)s1[ii[k]] * (long long)s1[jj[k]];
+    const float den = (float)((double)N * (double)N * 65025.0);
+    float m[6];
+    for (int k = 0; k < 6; ++k) m[k] = (float)num[k] / den;
+    m[0] += (float)eps;
+    m[3] += (float)eps;
+    m[5] += (float)eps;
+    // adjugate of [[m0 m1 m2] [m1 m3 m4] [m2 m4 m5]]
+    float c00 = m[3] * m[5] - m[4] * m[4], c01 = m[2] * m[4] - m[1] * m[5], c02 = m[1] * m[4] - m[2] * m[3];
+    float c11 = m[0] * m[5] - m[2] * m[2], c12 = m[1] * m[2] - m[0] * m[4], c22 = m[0] * m[3] - m[1] * m[1];
+    float det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    float inv[6] = {c00 / det, c01 / det, c02 / det, c11 / det, c12 / det, c22 / det};
+    float nm = 0.f, ni = 0.f;
+    for (int k = 0; k < 6; ++k) {
+        const float wgt = (k == 0 || k == 3 || k == 5) ? 1.f : 2.f;
+        nm += wgt * m[k] * m[k];
+        ni += wgt * inv[k] * inv[k];
+    }
+    const float cond = sqrtf(nm) * sqrtf(ni);
+    if (!(cond <= (float)cond_fp64)) {
+        double d[6];
+        const double dd = (double)N * (double)N * 65025.0;
+        for (int k = 0; k < 6; ++k) d[k] = (double)num[k] / dd;
+        d[0] += eps;
+        d[3] += eps;
+        d[5] += eps;
+        const double e00 = d[3] * d[5] - d[4] * d[4], e01 = d[2] * d[4] - d[1] * d[5],
+                     e02 = d[1] * d[4] - d[2] * d[3];
+        const double e11 = d[0] * d[5] - d[2] * d[2], e12 = d[1] * d[2] - d[0] * d[4],
+                     e22 = d[0] * d[3] - d[1] * d[1];
+        const double dt = d[0] * e00 + d[1] * e01 + d[2] * e02;
+        inv[0] = (float)(e00 / dt);
+        inv[1] = (float)(e01 / dt);
+        inv[2] = (float)(e02 / dt);
+        inv[3] = (float)(e11 / dt);
+        inv[4] = (float)(e12 / dt);
+        inv[5] = (float)(e22 / dt);
+        atomicAdd(n_fp64, 1);
+    }
+    const float n255 = 255.f * (float)N;
+    const size_t p = (size_t)y * W + x;
+    gst[3 * p + 0] = make_float4((float)s1[0] / n255, (float)s1[1] / n255, (float)s1[2] / n255, inv[0]);
+    gst[3 * p + 1] = make_float4(inv[1], inv[2], inv[3], inv[4]);
+    gst[3 * p + 2] = make_float4(inv[5], 0.f, 0.f, 0.f);
+}
+
+// Random initial labels (Sec. 3.4): z0 uniform in [dmin, dmax], unit normal by
+// rejection (redrawn while |n_z| < 1e-3, at most 64 tries, else (0,0,1)).
+__global__ void k_init_labels(int H, int W, unsigned long long seed, double dmin, double dmax, float4 *lab) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    Rng g{sm_mix(sm_mix(seed ^ 0x5851F42D4C957F2Dull) ^ (unsigned long long)((long long)y * W + x))};
+    const double z0 = __dadd_rn(dmin, __dmul_rn(__dsub_rn(dmax, dmin), g.u01()));
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    for (int t = 0; t < 64; ++t) {
+        double a, b, c;
+        unit_vec(g, a, b, c);
+        if (fabs(c) < 1e-3) continue;
+        nx = a;
+        ny = b;
+        nz = c;
+        break;
+    }
+    lab[(size_t)y * W + x] = plane_from(nx, ny, nz, x, y, z0);
+}
+
+// ---------------------------------------------------------------------------
+// A3 + A4: data term of one label over one region, through M
+// ---------------------------------------------------------------------------
+// phi_p(f) for p in [Rx0, Rx0+Rw) x [Ry0, Ry0+Rh); out[(py-Ry0)*pitch + px-Rx0].
+// Guided-filter aggregation (Eq. gf): mean over the windows W'_k containing p
+// of a_k . I_p + b_k, a_k = (Sigma_k+eU)^-1 (mean(I rho) - mu_k mean(rho)),
+// b_k = mean(rho) - a_k . mu_k, every window clipped to the image and
+// normalised by its pixel count.  The guide is centred on the colour at the
+// region centre (the filter is invariant to a constant shift of the guide),
+// which keeps the covariance differences small in flat areas.
+__device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
+                             float lb, float lc, float *sm, float *out, int pitch) {
+    const int H = P.H, W = P.W, r = kp.r, T = kp.T;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int Mx0 = max(0, Rx0 - 2 * r), Mx1 = min(W, Rx0 + Rw + 2 * r);
+    const int My0 = max(0, Ry0 - 2 * r), My1 = min(H, Ry0 + Rh + 2 * r);
+    const int Kx0 = max(0, Rx0 - r), Kx1 = min(W, Rx0 + Rw + r);
+    const int Ky0 = max(0, Ry0 - r), Ky1 = min(H, Ry0 + Rh + r);
+    const int Mw = Mx1 - Mx0, Kw = Kx1 - Kx0;
+    const int RS = T + 2 * r;
+    float *Xr = sm;                          // [RS][4][Mw]  raw-cost channels of M rows (ring)
+    float *Vb = Xr + (size_t)RS * 4 * Mw;    // [T][4][Mw]   vertical sums (also [T][4][Kw])
+    float *Bb = Vb + (size_t)T * 4 * Mw;     // [T][4][Kw]   box sums      (also [T][4][Rw])
+    float *ABr = Bb + (size_t)T * 4 * Kw;    // [RS][4][Kw]  a_k, b_k of K rows (ring)
+    int *rowI = (int *)(ABr + (size_t)RS * 4 * Kw);  // [RS] integer part of the row warp offset
+    float *rowF = (float *)(rowI + RS);              // [RS] fractional part
+
+    const float4 cen4 = P.L[(size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2)];
+    const float inv255 = 1.0f / 255.0f;
+    const float cr = cen4.x * inv255, cg = cen4.y * inv255, cb = cen4.z * inv255;
+    // warp s' = s - (a s_u + b s_v + c): u' = x - d = Q(y) + (1-a)(x - Rx0) with
+    // Q(y) = (1-a) Rx0 - b y - c kept as integer + fraction in float-float
+    float sl;
+    const float sh = two_sum(1.0f, -la, sl);
+    const float oma = 1.0f - kp.alpha_grad;
+
+    int mNext = My0, kNext = Ky0;
+    for (int p0 = Ry0; p0 < Ry0 + Rh; p0 += T) {
+        const int p1 = min(Ry0 + Rh, p0 + T);
+        const int kNeed = min(Ky1, p1 + r);
+        while (kNext < kNeed) {
+            const int k0 = kNext, k1 = min(kNeed, k0 + T);
+            const int mNeed = min(My1, k1 + r);
+            if (mNext < mNeed) {
+                for (int i = tid; i < mNeed - mNext; i += nt) {
+                    const int y = mNext + i;
+                    float e1, e2, e3, e4;
+                    const float p = two_prod(sh, (float)Rx0, e1);
+                    const float q = two_prod(lb, (float)y, e2);
+                    const float t1 = two_sum(p, -q, e3);
+                    const float t2 = two_sum(t1, -lc, e4);
+                    const float lo = __fadd_rn(__fadd_rn(__fsub_rn(e1, e2), __fadd_rn(e3, e4)),
+                                               __fmul_rn(sl, (float)Rx0));
+                    float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
+                    const float fl = floorf(th);
+                    float F = __fadd_rn(__fsub_rn(th, fl), lo);
+                    int I = (int)fl;
+                    if (F < 0.f) {
+                        F += 1.f;
+                        I -= 1;
+                    } else if (F >= 1.f) {
+                        F -= 1.f;
+                        I += 1;
+                    }
+                    const int slot = (y - My0) % RS;
+                    rowI[slot] = I;
+                    rowF[slot] = F;
+                }
+                __syncthreads();
+                const int nitem = (mNeed - mNext) * Mw;
+                for (int it = tid; it < nitem; it += nt) {
+                    const int y = mNext + it / Mw, xc = it % Mw, x = Mx0 + xc;
+                    const int slot = (y - My0) % RS;
+                    const float4 l = P.L[(size_t)y * W + x];
+                    const float dx = (float)(x - Rx0);
+                    const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, rowF[slot]));
+                    const float gf = floorf(g);
+                    float t = g - gf;
+                    int i0 = rowI[slot] + (int)gf;
+                    if (i0 < 0) {
+                        i0 = 0;
+                        t = 0.f;
+                    } else if (i0 >= W - 1) {
+                        i0 = W - 1;
+                        t = 0.f;
+                    }
+                    const int i1 = min(i0 + 1, W - 1);
+                    const float4 r0 = P.R[(size_t)y * W + i0], r1 = P.R[(size_t)y * W + i1];
+                    const float rr = fmaf(t, r1.x - r0.x, r0.x);
+                    const float rg = fmaf(t, r1.y - r0.y, r0.y);
+                    const float rb = fmaf(t, r1.z - r0.z, r0.z);
+                    const float rd = fmaf(t, r1.w - r0.w, r0.w);
+                    const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
+                    const float gd = fabsf(l.w - rd);
+                    const float rho = oma * fminf(col, kp.tau_col) + kp.alpha_grad * fminf(gd, kp.tau_grad);
+                    float *o = Xr + (size_t)slot * 4 * Mw + xc;
+                    o[0] = rho;
+                    o[Mw] = (l.x * inv255 - cr) * rho;
+                    o[2 * Mw] = (l.y * inv255 - cg) * rho;
+                    o[3 * Mw] = (l.z * inv255 - cb) * rho;
+                }
+                mNext = mNeed;
+                __syncthreads();
+            }
+            // vertical window sums of the 4 channels for K rows [k0, k1), every M column
+            for (int it = tid; it < 4 * Mw; it += nt) {
+                const int col = it % Mw, ch = it / Mw;
+                const float *X = Xr + (size_t)ch * Mw + col;
+                const size_t rs = (size_t)4 * Mw;
+                float s = 0.f;
+                for (int y = max(0, k0 - r); y <= min(H - 1, k0 + r); ++y) s += X[((y - My0) % RS) * rs];
+                Vb[(size_t)ch * Mw + col] = s;
+                for (int ky = k0 + 1; ky < k1; ++ky) {
+                    const int yin = ky + r, yout = ky - r - 1;
+                    if (yin <= H - 1) s += X[((yin - My0) % RS) * rs];
+                    if (yout >= 0) s -= X[((yout - My0) % RS) * rs];
+                    Vb[(size_t)(ky - k0) * rs + (size_t)ch * Mw + col] = s;
+                }
+            }
+            __syncthreads();
+            // horizontal window sums at K columns, chunks of 16 outputs
+            {
+                const int nch = (Kw + 15) >> 4;
+                const int nitem = (k1 - k0) * 4 * nch;
+                for (int it = tid; it < nitem; it += nt) {
+                    const int chunk = it % nch, rest = it / nch, ch = rest & 3, row = rest >> 2;
+                    const float *V = Vb + (size_t)row * 4 * Mw + (size_t)ch * Mw;
+                    float *B = Bb + (size_t)row * 4 * Kw + (size_t)ch * Kw;
+                    const int kx0 = Kx0 + chunk * 16, kx1 = min(Kx1, kx0 + 16);
+                    float s = 0.f;
+                    for (int x = max(0, kx0 - r); x <= min(W - 1, kx0 + r); ++x) s += V[x - Mx0];
+                    B[kx0 - Kx0] = s;
+                    for (int kx = kx0 + 1; kx < kx1; ++kx) {
+                        const int xin = kx + r, xout = kx - r - 1;
+                        if (xin <= W - 1) s += V[xin - Mx0];
+                        if (xout >= 0) s -= V[xout - Mx0];
+                        B[kx - Kx0] = s;
+                    }
+                }
+            }
+            __syncthreads();
+            // guided-filter coefficients a_k, b_k for K rows [k0, k1)
+            for (int it = tid; it < (k1 - k0) * Kw; it += nt) {
+                const int row = it / Kw, col = it % Kw;
+                const int ky = k0 + row, kx = Kx0 + col;
+                const float n = (float)((min(W - 1, kx + r) - max(0, kx - r) + 1) *
+                                        (min(H - 1, ky + r) - max(0, ky - r) + 1));
+                const float inv = 1.0f / n;
+                const float *B = Bb + (size_t)row * 4 * Kw + col;
+                const float mr = B[0] * inv;
+                const size_t k = (size_t)ky * W + kx;
+                const float4 g0 = P.gst[3 * k], g1 = P.gst[3 * k + 1], g2 = P.gst[3 * k + 2];
+                const float u0 = g0.x - cr, u1 = g0.y - cg, u2 = g0.z - cb;
+                const float v0 = B[Kw] * inv - u0 * mr;
+                const float v1 = B[2 * Kw] * inv - u1 * mr;
+                const float v2 = B[3 * Kw] * inv - u2 * mr;
+                const float a0 = g0.w * v0 + g1.x * v1 + g1.y * v2;
+                const float a1 = g1.x * v0 + g1.z * v1 + g1.w * v2;
+                const float a2 = g1.y * v0 + g1.w * v1 + g2.x * v2;
+                const float bk = mr - (a0 * u0 + a1 * u1 + a2 * u2);
+                float *A = ABr + (size_t)((ky - Ky0) % RS) * 4 * Kw + col;
+                A[0] = a0;
+                A[Kw] = a1;
+                A[2 * Kw] = a2;
+                A[3 * Kw] = bk;
+            }
+            kNext = k1;
+            __syncthreads();
+        }
+        // window means of a_k, b_k at p: vertical sums over K rows, every K column
+        for (int it = tid; it < 4 * Kw; it += nt) {
+            const int col = it % Kw, ch = it / Kw;
+            const float *A = ABr + (size_t)ch * Kw + col;
+            const size_t rs = (size_t)4 * Kw;
+            float s = 0.f;
+            for (int y = max(0, p0 - r); y <= min(H - 1, p0 + r); ++y) s += A[((y - Ky0) % RS) * rs];
+            Vb[(size_t)ch * Kw + col] = s;
+            for (int py = p0 + 1; py < p1; ++py) {
+                const int yin = py + r, yout = py - r - 1;
+                if (yin <= H - 1) s += A[((yin - Ky0) % RS) * rs];
+                if (yout >= 0) s -= A[((yout - Ky0) % RS) * rs];
+                Vb[(size_t)(py - p0) * rs + (size_t)ch * Kw + col] = s;
+            }
+        }
+        __syncthreads();
+        {
+            const int nch = (Rw + 15) >> 4;
+            const int nitem = (p1 - p0) * 4 * nch;
+            for (int it = tid; it < nitem; it += nt) {
+                const int chunk = it % nch, rest = it / nch, ch = rest & 3, row = rest >> 2;
+                const float *V = Vb + (size_t)row * 4 * Kw + (size_t)ch * Kw;
+                float *B = Bb + (size_t)row * 4 * Rw + (size_t)ch * Rw;
+                const int px0 = Rx0 + chunk * 16, px1 = min(Rx0 + Rw, px0 + 16);
+                float s = 0.f;
+                for (int x = max(0, px0 - r); x <= min(W - 1, px0 + r); ++x) s += V[x - Kx0];
+                B[px0 - Rx0] = s;
+                for (int px = px0 + 1; px < px1; ++px) {
+                    const int xin = px + r, xout = px - r - 1;
+                    if (xin <= W - 1) s += V[xin - Kx0];
+                    if (xout >= 0) s -= V[xout - Kx0];
+                    B[px - Rx0] = s;
+                }
+            }
+        }
+        __syncthreads();
+        for (int it = tid; it < (p1 - p0) * Rw; it += nt) {
+            const int row = it / Rw, col = it % Rw;
+            const int py = p0 + row, px = Rx0 + col;
+            const float n = (float)((min(W - 1, px + r) - max(0, px - r) + 1) *
+                                    (min(H - 1, py + r) - max(0, py - r) + 1));
+            const float *B = Bb + (size_t)row * 4 * Rw + col;
+            const float4 l = P.L[(size_t)py * W + px];
+            const float phi = (B[0] * (l.x * inv255 - cr) + B[Rw] * (l.y * inv255 - cg) +
+                               B[2 * Rw] * (l.z * inv255 - cb) + B[3 * Rw]) /
+                              n;
+            out[(size_t)(py - Ry0) * pitch + (px - Rx0)] = phi;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5: expansion-move graph of one node
+// ---------------------------------------------------------------------------
+struct NodeCaps {
+    int cap_s, cap_t;  // s->p (taken when x_p = 1), p->t (taken when x_p = 0)
+    int k[4];          // p -> forward neighbour inside R
+    long long cst;     // constant: lowered A's of the forward pairs + min(U0, U1)
+    int nclamp;
+};
+
+// Node p = (x0+ix, y0+iy) of region [x0,x0+w) x [y0,y0+h); al = candidate,
+// phi_al = phi_p(alpha); lab holds the current labels and cost cache.
+__device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *lab, const float4 &al,
+                           float phi_al, int x0, int y0, int w, int h, int ix, int iy, NodeCaps &o) {
+    const int H = P.H, W = P.W;
+    const int pu = x0 + ix, pv = y0 + iy;
+    const float4 fp = lab[(size_t)pv * W + pu];
+    int U0 = q_cost(fp.w, kp.S), U1 = q_cost(phi_al, kp.S);
+    long long cst = 0;
+    int ncl = 0;
+    const float4 wp = P.wfw[(size_t)pv * W + pu];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int d = k & 3;
+        const bool fwd = k < 4;
+        if (fwd) o.k[d] = 0;
+        const int qu = pu + dir_dx(k), qv = pv + dir_dy(k);
+        if (qu < 0 || qu >= W || qv < 0 || qv >= H) continue;
+        const float wl = fwd ? comp(wp, d) : comp(P.wfw[(size_t)qv * W + qu], d);
+        const float4 fq = lab[(size_t)qv * W + qu];
+        const bool qin = qu >= x0 && qu < x0 + w && qv >= y0 && qv < y0 + h;
+        if (!qin) {
+            U0 += q_psi(wl, kp.tau_dis, kp.S, fp, fq, pu, pv, qu, qv);
+            U1 += q_psi(wl, kp.tau_dis, kp.S, al, fq, pu, pv, qu, qv);
+        } else if (fwd) {
+            int A = q_psi(wl, kp.tau_dis, kp.S, fp, fq, pu, pv, qu, qv);
+            const int B = q_psi(wl, kp.tau_dis, kp.S, fp, al, pu, pv, qu, qv);
+            const int C = q_psi(wl, kp.tau_dis, kp.S, al, fq, pu, pv, qu, qv);
+            if (A > B + C) {
+                A = B + C;
+                ++ncl;
+            }
+            cst += A;
+            U1 += C - A;
+            o.k[d] = B + C - A;
+        } else {
+            // backward neighbour q: the pair (q, p) is forward from q, whose C
+            // term psi(alpha at q, f_p at p) lands on p's unary with a minus sign
+            U1 -= q_psi(wl, kp.tau_dis, kp.S, al, fp, qu, qv, pu, pv);
+        }
+    }
+    const int m = min(U0, U1);
+    o.cap_s = U1 - m;
+    o.cap_t = U0 - m;
+    o.cst = cst + m;
+    o.nclamp = ncl;
+}
+
+// block-wide sum of a long long (all threads get the result)
+__device__ long long block_sum_ll(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int i = 0; i < nw; ++i) s += red[i];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// ---------------------------------------------------------------------------
+// A6: CTA push-relabel on a w x h grid region held in shared memory
+//   res[k*n + i] : residual capacity of i -> neighbour k (8 directions)
+//   v[i]         : excess minus residual sink capacity (excess = max(v,0),
+//                  residual p->t = max(-v,0)); excess reaching a node with
+//                  residual sink capacity is pushed to the sink at once
+//   hh[i]        : height (kInf = cannot reach the sink)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dir_off(int k, int w) { return dir_dx(k) + dir_dy(k) * w; }
+
+// Exact distances to the sink in the residual graph (level-synchronous BFS);
+// returns whether some node with excess can still reach the sink.
+__device__ bool global_relabel(int n, int w, const int *res, const int *v, uint16_t *hh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < n; i += nt) hh[i] = v[i] < 0 ? 1 : kInf;
+    __syncthreads();
+    for (int level = 1; level <= n; ++level) {
+        int changed = 0;
+        for (int i = tid; i < n; i += nt) {
+            if (hh[i] != kInf) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (res[k * n + i] > 0 && hh[i + dir_off(k, w)] == level) {
+                    hh[i] = (uint16_t)(level + 1);
+                    changed = 1;
+                    break;
+                }
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    int act = 0;
+    for (int i = tid; i < n; i += nt) act |= (v[i] > 0 && hh[i] != kInf);
+    return __syncthreads_or(act) != 0;
+}
+
+// Maximum preflow.  On return (LEM_OK) hh[i] != kInf exactly for the nodes that
+// reach the sink in the residual graph: the minimal sink side of the cut.
+__device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, int max_rounds, int gr_interval) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    bool act = global_relabel(n, w, res, v, hh);
+    int rounds = 0;
+    while (act) {
+        if (rounds >= max_rounds) return LEM_ERR_MAXFLOW_LIMIT;
+        int mine = 0;
+        for (int i = tid; i < n; i += nt) {
+            const int e = v[i];
+            if (e <= 0) continue;
+            const int hu = hh[i];
+            if (hu == kInf) continue;
+            int left = e;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (left == 0) break;
+                const int rk = res[k * n + i];
+                if (rk <= 0) continue;
+                const int j = i + dir_off(k, w);
+                if ((int)hh[j] + 1 == hu) {
+                    const int d = min(left, rk);
+                    atomicSub(&res[k * n + i], d);
+                    atomicAdd(&res[(k ^ 4) * n + j], d);
+                    atomicAdd(&v[j], d);
+                    left -= d;
+                }
+            }
+            if (left != e) atomicSub(&v[i], e - left);
+            if (left > 0) {
+                int mh = kInf;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (res[k * n + i] > 0) mh = min(mh, (int)hh[i + dir_off(k, w)]);
+                hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
+            }
+            mine = 1;
+        }
+        ++rounds;
+        // a round in which no thread found an active node (so nothing moved),
+        // or the periodic point, hands over to an exact global relabel
+        const int any = __syncthreads_or(mine);
+        if (!any || rounds % gr_interval == 0) act = global_relabel(n, w, res, v, hh);
+    }
+    return LEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// phi_p(f_p) for every pixel, one CTA per pixel (1x1 region)
+__global__ void k_pixel_costs(DevPlanes P, KParams kp, float4 *lab) {
+    extern __shared__ __align__(16) float smf[];
+    const int p = blockIdx.x;
+    const int x = p % P.W, y = p / P.W;
+    const float4 f = lab[p];
+    region_unary(P, kp, x, y, 1, 1, f.x, f.y, f.z, smf, &lab[p].w, 1);
+}
+
+__global__ void k_unary_batch(DevPlanes P, KParams kp, const int4 *regions, const int64_t *offsets, int K,
+                              const float *labels, float *costs) {
+    extern __shared__ __align__(16) float smf[];
+    const int i = blockIdx.x / K, k = blockIdx.x % K;
+    const int4 R = regions[i];
+    const float *l = labels + ((size_t)i * K + k) * 3;
+    float *out = costs + offsets[i] + (int64_t)k * R.z * R.w;
+    region_unary(P, kp, R.x, R.y, R.z, R.w, l[0], l[1], l[2], smf, out, R.z);
+}
+
+__global__ void k_pairwise_batch(DevPlanes P, KParams kp, const int4 *regions, const int64_t *offsets,
+                                 const float4 *lab, const float *alpha, const float *costs_alpha, int32_t *tcaps,
+                                 int32_t *ncaps, int64_t *cterm) {
+    __shared__ long long red[33];
+    const int i = blockIdx.x;
+    const int4 R = regions[i];
+    const float4 al = make_float4(alpha[3 * i], alpha[3 * i + 1], alpha[3 * i + 2], 0.f);
+    const int n = R.z * R.w;
+    const int64_t off = offsets[i];
+    long long cst = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        NodeCaps o;
+        build_node(P, kp, lab, al, costs_alpha[off + j], R.x, R.y, R.z, R.w, j % R.z, j / R.z, o);
+        tcaps[2 * (off + j)] = o.cap_s;
+        tcaps[2 * (off + j) + 1] = o.cap_t;
+        for (int d = 0; d < 4; ++d) ncaps[4 * (off + j) + d] = o.k[d];
+        cst += o.cst;
+    }
+    cst = block_sum_ll(cst, red);
+    if (threadIdx.x == 0) cterm[i] = cst;
+}
+
+__global__ void k_mincut_batch(KParams kp, const int4 *regions, const int64_t *offsets, const int32_t *tcaps,
+                               const int32_t *ncaps, uint8_t *take, int64_t *flow, int32_t *status) {
+    extern __shared__ __align__(16) int smi[];
+    __shared__ long long red[33];
+    const int i = blockIdx.x;
+    const int4 R = regions[i];
+    const int n = R.z * R.w, w = R.z, h = R.w;
+    const int64_t off = offsets[i];
+    int *res = smi;
+    int *v = res + 8 * n;
+    uint16_t *hh = (uint16_t *)(v + n);
+    long long capt = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int ix = j % w, iy = j / w;
+        const int cs = tcaps[2 * (off + j)], ct = tcaps[2 * (off + j) + 1];
+        v[j] = cs - ct;
+        capt += ct;
+        for (int k = 0; k < 8; ++k) {
+            int c = 0;
+            const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
+            if (k < 4 && jx >= 0 && jx < w && jy >= 0 && jy < h) c = max(0, (int)ncaps[4 * (off + j) + k]);
+            res[k * n + j] = c;
+        }
+    }
+    capt = block_sum_ll(capt, red);
+    const int st = cta_maxflow(n, w, res, v, hh, kp.max_rounds, kp.gr_interval);
+    long long rt = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        take[off + j] = (st == LEM_OK && hh[j] != kInf) ? 1 : 0;
+        rt += max(0, -v[j]);
+    }
+    rt = block_sum_ll(rt, red);
+    if (threadIdx.x == 0) {
+        flow[i] = capt - rt;
+        status[i] = st;
+    }
+}
+
+// All expansions of one group at one level: one CTA per region, Algorithm 2.
+__global__ void k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, int group, float4 *lab,
+                               float *phiA, Counters *ctr) {
+    extern __shared__ __align__(16) float smf[];
+    __shared__ float4 s_alpha;
+    __shared__ long long red[33];
+    const int H = P.H, W = P.W, s = lv.s;
+    const int nx = (W + s - 1) / s;
+    const int gi = group & 3, gj = group >> 2;
+    const int cx = (nx - gi + 3) / 4;
+    const int ci = gi + 4 * (blockIdx.x % cx), cj = gj + 4 * (blockIdx.x / cx);
+    const int x0 = max(0, (ci - 1) * s), x1 = min(W, (ci + 2) * s);
+    const int y0 = max(0, (cj - 1) * s), y1 = min(H, (cj + 2) * s);
+    const int w = x1 - x0, h = y1 - y0, n = w * h;
+    const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
+    int *res = (int *)smf;
+    int *v = res + 8 * n;
+    uint16_t *hh = (uint16_t *)(v + n);
+    // outer perturbation sizes of this iteration, copied into Algorithm 2
+    double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
+    double rn = ldexp(1.0, -iter);
+    long long acc = 0, hits = 0;
+    const int nprop = lv.k_prop + lv.k_rand;
+    for (int t = 0; t < nprop; ++t) {
+        const bool perturb = t >= lv.k_prop;
+        if (threadIdx.x == 0) {
+            s_alpha = propose(lab, W, proposal_stream(kp.seed, iter, level, ci, cj, t), cx0, cy0, cw, chh, perturb,
+                              rd, rn, kp.disp_min, kp.disp_max);
+        }
+        if (perturb) {
+            rd *= 0.5;
+            rn *= 0.5;
+        }
+        __syncthreads();
+        const float4 al = s_alpha;
+        region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
+        // (region_unary ends with a barrier; its shared memory is reused below)
+        long long base_t = 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int ix = j % w, iy = j / w;
+            NodeCaps o;
+            build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
+            v[j] = o.cap_s - o.cap_t;
+            for (int d = 0; d < 4; ++d) res[d * n + j] = o.k[d];
+            for (int d = 4; d < 8; ++d) res[d * n + j] = 0;
+            base_t += o.cap_t;
+        }
+        (void)base_t;
+        __syncthreads();
+        const int st = cta_maxflow(n, w, res, v, hh, kp.max_rounds, kp.gr_interval);
+        if (st == LEM_OK) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                if (hh[j] == kInf) continue;
+                const size_t p = (size_t)(y0 + j / w) * W + x0 + j % w;
+                lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
+                ++acc;
+            }
+        } else if (threadIdx.x == 0) {
+            ++hits;
+        }
+        __syncthreads();
+    }
+    acc = block_sum_ll(acc, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctr->accepted, (unsigned long long)acc);
+        atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
+        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop);
+    }
+}
+
+// A9: quantised energy, per-block partial sums
+__global__ void k_energy(DevPlanes P, KParams kp, const float4 *lab, long long *partials) {
+    __shared__ long long red[33];
+    const int H = P.H, W = P.W;
+    long long e = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < H * W; p += gridDim.x * blockDim.x) {
+        const int x = p % W, y = p / W;
+        const float4 f = lab[p];
+        e += q_cost(f.w, kp.S);
+        const float4 wp = P.wfw[p];
+        for (int d = 0; d < 4; ++d) {
+            const int qx = x + dir_dx(d), qy = y + dir_dy(d);
+            if (qx < 0 || qx >= W || qy >= H) continue;
+            e += q_psi(comp(wp, d), kp.tau_dis, kp.S, f, lab[(size_t)qy * W + qx], x, y, qx, qy);
+        }
+    }
+    e = block_sum_ll(e, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = e;
+}
+
+__global__ void k_sum_partials(const long long *partials, int n, long long *out) {
+    __shared__ long long red[33];
+    long long s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    s = block_sum_ll(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    const float4 f = lab[p];
+    if (abc) {
+        abc[3 * p] = f.x;
+        abc[3 * p + 1] = f.y;
+        abc[3 * p + 2] = f.z;
+    }
+    if (disp) disp[p] = fmaf(f.x, (float)(p % W), fmaf(f.y, (float)(p / W), f.z));
+    if (cost) cost[p] = f.w;
+}
+
+__global__ void k_labels_in(int H, int W, const float *abc, const float *cost, float4 *lab) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    lab[p] = make_float4(abc[3 * p], abc[3 * p + 1], abc[3 * p + 2], cost ? cost[p] : 0.f);
+}
+
+__global__ void k_planes_out(int H, int W, DevPlanes P, float *left, float *right, float *guide, float *weights) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    if (left) reinterpret_cast<float4 *>(left)[p] = P.L[p];
+    if (right) reinterpret_cast<float4 *>(right)[p] = P.R[p];
+    if (weights) reinterpret_cast<float4 *>(weights)[p] = P.wfw[p];
+    if (guide) {
+        const float4 a = P.gst[3 * p], b = P.gst[3 * p + 1], c = P.gst[3 * p + 2];
+        float *g = guide + 9 * (size_t)p;
+        g[0] = a.x;
+        g[1] = a.y;
+        g[2] = a.z;
+        g[3] = a.w;
+        g[4] = b.x;
+        g[5] = b.y;
+        g[6] = b.z;
+        g[7] = b.w;
+        g[8] = c.x;
+    }
+}
+
+size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
+    const int r = kp.r, T = kp.T;
+    const int Mw = std::min(W, rw + 4 * r), Kw = std::min(W, rw + 2 * r);
+    (void)rh;
+    const int RS = T + 2 * r;
+    return sizeof(float) * ((size_t)RS * 4 * Mw + (size_t)T * 4 * Mw + (size_t)T * 4 * Kw + (size_t)RS * 4 * Kw +
+                            2 * (size_t)RS);
+}
+
+cudaError_t set_smem(const void *fn, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh) { return unary_bytes_host(kp, H, W, rw, rh); }
+size_t cut_smem_bytes(int n) { return (size_t)9 * n * sizeof(int) + (size_t)((n + 1) & ~1) * sizeof(uint16_t); }
+
+cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
+                              int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
+                              cudaStream_t st) {
+    dim3 grid((W + 127) / 128, H);
+    k_preprocess<<<grid, 128, 0, st>>>(left, lstride, right, rstride, H, W, lambda, eps_w, gamma, Lp, Rp, wfw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guide_stats(const uint8_t *left, int64_t lstride, int H, int W, int r, double eps,
+                               double cond_fp64, float4 *gst, int *n_fp64, cudaStream_t st) {
+    dim3 grid((W + 127) / 128, H);
+    k_guide_stats<<<grid, 128, 0, st>>>(left, lstride, H, W, r, eps, cond_fp64, gst, n_fp64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_labels(int H, int W, unsigned long long seed, double dmin, double dmax, float4 *lab,
+                               cudaStream_t st) {
+    dim3 grid((W + 127) / 128, H);
+    k_init_labels<<<grid, 128, 0, st>>>(H, W, seed, dmin, dmax, lab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pixel_costs(const DevPlanes &P, const KParams &kp, float4 *lab, int threads, cudaStream_t st) {
+    const size_t sm = unary_bytes_host(kp, P.H, P.W, 1, 1);
+    cudaError_t e = set_smem((const void *)k_pixel_costs, sm);
+    if (e != cudaSuccess) return e;
+    k_pixel_costs<<<P.H * P.W, threads, sm, st>>>(P, kp, lab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
+                               int n_regions, int K, int max_w, int max_h, const float *labels, float *costs,
+                               int threads, cudaStream_t st) {
+    const size_t sm = unary_bytes_host(kp, P.H, P.W, max_w, max_h);
+    cudaError_t e = set_smem((const void *)k_unary_batch, sm);
+    if (e != cudaSuccess) return e;
+    k_unary_batch<<<n_regions * K, threads, sm, st>>>(P, kp, regions, offsets, K, labels, costs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const int4 *regions,
+                                  const int64_t *offsets, int n_regions, const float4 *lab, const float *alpha,
+                                  const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *cterm,
+                                  int threads, cudaStream_t st) {
+    k_pairwise_batch<<<n_regions, threads, 0, st>>>(P, kp, regions, offsets, lab, alpha, costs_alpha, tcaps, ncaps,
+                                                    cterm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
+                                int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                int64_t *flow, int32_t *status, int threads, cudaStream_t st) {
+    const size_t sm = cut_smem_bytes(max_nodes);
+    cudaError_t e = set_smem((const void *)k_mincut_batch, sm);
+    if (e != cudaSuccess) return e;
+    k_mincut_batch<<<n_regions, threads, sm, st>>>(kp, regions, offsets, tcaps, ncaps, take, flow, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                                int group, float4 *lab, float *phiA, Counters *ctr, int threads, cudaStream_t st) {
+    const int s = lv.s;
+    const int nx = (P.W + s - 1) / s, ny = (P.H + s - 1) / s;
+    const int gi = group & 3, gj = group >> 2;
+    const int cx = gi < nx ? (nx - gi + 3) / 4 : 0;
+    const int cy = gj < ny ? (ny - gj + 3) / 4 : 0;
+    if (cx * cy == 0) return cudaSuccess;
+    const int rw = std::min(P.W, 3 * s), rh = std::min(P.H, 3 * s);
+    const size_t sm = std::max(unary_bytes_host(kp, P.H, P.W, rw, rh), cut_smem_bytes(rw * rh));
+    cudaError_t e = set_smem((const void *)k_expand_group, sm);
+    if (e != cudaSuccess) return e;
+    k_expand_group<<<cx * cy, threads, sm, st>>>(P, kp, lv, level, iter, group, lab, phiA, ctr);
+    return cudaGetLastError();
+}
+
+int energy_partials(int H, int W) { return std::min(1024, (H * W + 255) / 256); }
+
+cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
+                          long long *out, cudaStream_t st) {
+    const int nb = energy_partials(P.H, P.W);
+    k_energy<<<nb, 256, 0, st>>>(P, kp, lab, partials);
+    k_sum_partials<<<1, 256, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,
+                              cudaStream_t st) {
+    k_labels_out<<<(H * W + 255) / 256, 256, 0, st>>>(H, W, lab, abc, disp, cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_in(int H, int W, const float *abc, const float *cost, float4 *lab, cudaStream_t st) {
+    k_labels_in<<<(H * W + 255) / 256, 256, 0, st>>>(H, W, abc, cost, lab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes_out(int H, int W, const DevPlanes &P, float *left, float *right, float *guide,
+                              float *weights, cudaStream_t st) {
+    k_planes_out<<<(H * W + 255) / 256, 256, 0, st>>>(H, W, P, left, right, guide, weights);
+    return cudaGetLastError();
+}
+
+}  // namespace lem

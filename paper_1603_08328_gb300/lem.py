@@ -1,0 +1,312 @@
+"""Python binding of the C ABI in ``include/lem.h`` (ctypes, argument marshalling only).
+
+Every function of the header is exposed under the same name.  ``Stereo`` is a
+thin convenience wrapper that keeps one handle and allocates the device
+buffers of the batch calls as torch tensors; every step of the computation
+runs in the CUDA library.  There is no CPU fallback: without the built library
+or without a CUDA device these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblem.so")
+
+LEM_OK = 0
+LEM_ERR_ARG = -1
+LEM_ERR_SHAPE = -2
+LEM_ERR_CUDA = -3
+LEM_ERR_MAXFLOW_LIMIT = -4
+LEM_ERR_OOM = -5
+LEM_STORE_F32, LEM_STORE_F16, LEM_STORE_BF16 = 0, 1, 2
+LEM_MAX_REGION_NODES = 5625
+
+
+class lem_image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("height", C.c_int), ("width", C.c_int), ("stride_row", C.c_int64),
+                ("on_device", C.c_int)]
+
+
+class lem_params(C.Structure):
+    _fields_ = [
+        ("gf_radius", C.c_int), ("gf_eps", C.c_double), ("tau_col", C.c_double), ("tau_grad", C.c_double),
+        ("alpha_grad", C.c_double), ("lam", C.c_double), ("tau_dis", C.c_double), ("eps_w", C.c_double),
+        ("gamma", C.c_double), ("disp_min", C.c_double), ("disp_max", C.c_double), ("n_levels", C.c_int),
+        ("cell", C.c_int * 3), ("k_prop", C.c_int * 3), ("k_rand", C.c_int * 3), ("quant_scale", C.c_double),
+        ("store_dtype", C.c_int), ("cond_fp64", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p),
+        ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
+    ]
+
+
+class lem_region(C.Structure):
+    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("w", C.c_int), ("h", C.c_int)]
+
+
+class lem_stats(C.Structure):
+    _fields_ = [("energy_q", C.c_int64), ("energy", C.c_double), ("evals", C.c_int64), ("accepted", C.c_int64),
+                ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        P, vp, H = C.POINTER, C.c_void_p, C.c_void_p
+        L.lem_default_params.argtypes = [P(lem_params)]
+        L.lem_default_params.restype = None
+        L.lem_create.argtypes = [P(lem_image), P(lem_image), P(lem_params), P(H)]
+        L.lem_destroy.argtypes = [H]
+        L.lem_last_error.argtypes = [H]
+        L.lem_last_error.restype = C.c_char_p
+        L.lem_unary_batch.argtypes = [H, P(lem_region), C.c_int, vp, C.c_int, vp]
+        L.lem_pairwise_batch.argtypes = [H, P(lem_region), C.c_int, vp, vp, vp, vp, vp]
+        L.lem_mincut_batch.argtypes = [H, P(lem_region), C.c_int, vp, vp, vp, vp, vp]
+        L.lem_expand_group.argtypes = [H, C.c_int, C.c_int, C.c_int, P(lem_stats)]
+        L.lem_expand_iteration.argtypes = [H, C.c_int, P(lem_stats)]
+        L.lem_get_labels.argtypes = [H, vp, vp, vp, C.c_int]
+        L.lem_set_labels.argtypes = [H, vp, vp, C.c_int]
+        L.lem_energy.argtypes = [H, P(C.c_double), P(C.c_int64)]
+        L.lem_get_planes.argtypes = [H, vp, vp, vp, vp]
+        L.lem_evals_per_iteration.argtypes = [H]
+        L.lem_evals_per_iteration.restype = C.c_int64
+        for name in ("lem_create", "lem_destroy", "lem_unary_batch", "lem_pairwise_batch", "lem_mincut_batch",
+                     "lem_expand_group", "lem_expand_iteration", "lem_get_labels", "lem_set_labels", "lem_energy",
+                     "lem_get_planes"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class LemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lem error {code}: {msg}")
+        self.code = code
+
+
+# --- same-name wrappers of the C functions ------------------------------------
+
+def lem_default_params(**overrides) -> lem_params:
+    p = lem_params()
+    lib().lem_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if k == "lambda":
+            k = "lam"
+        if k in ("cell", "k_prop", "k_rand"):
+            v = list(v) + [0] * (3 - len(v))
+            v = (C.c_int * 3)(*v)
+        setattr(p, k, v)
+    return p
+
+
+def lem_last_error(h) -> str:
+    s = lib().lem_last_error(h)
+    return s.decode() if s else ""
+
+
+def _check(rc, h=None):
+    if rc != LEM_OK:
+        raise LemError(rc, lem_last_error(h))
+    return rc
+
+
+def lem_create(left: lem_image, right: lem_image, params: lem_params):
+    h = C.c_void_p()
+    rc = lib().lem_create(C.byref(left), C.byref(right), C.byref(params), C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def lem_destroy(h):
+    return lib().lem_destroy(h)
+
+
+def _regions(regions):
+    arr = (lem_region * len(regions))()
+    for i, r in enumerate(regions):
+        arr[i] = lem_region(*[int(x) for x in r])
+    return arr
+
+
+def lem_unary_batch(h, regions, labels_ptr, K, costs_ptr):
+    return lib().lem_unary_batch(h, _regions(regions), len(regions), labels_ptr, K, costs_ptr)
+
+
+def lem_pairwise_batch(h, regions, alpha_ptr, costs_alpha_ptr, tcaps_ptr, ncaps_ptr, const_ptr):
+    return lib().lem_pairwise_batch(h, _regions(regions), len(regions), alpha_ptr, costs_alpha_ptr, tcaps_ptr,
+                                    ncaps_ptr, const_ptr)
+
+
+def lem_mincut_batch(h, regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, status_ptr):
+    return lib().lem_mincut_batch(h, _regions(regions), len(regions), tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr,
+                                  status_ptr)
+
+
+def lem_expand_group(h, it, level, group, stats=None):
+    return lib().lem_expand_group(h, it, level, group, C.byref(stats) if stats is not None else None)
+
+
+def lem_expand_iteration(h, n_iters, stats=None):
+    return lib().lem_expand_iteration(h, n_iters, C.byref(stats) if stats is not None else None)
+
+
+def lem_get_labels(h, abc_ptr, disp_ptr, cost_ptr, on_device):
+    return lib().lem_get_labels(h, abc_ptr, disp_ptr, cost_ptr, on_device)
+
+
+def lem_set_labels(h, abc_ptr, cost_ptr, on_device):
+    return lib().lem_set_labels(h, abc_ptr, cost_ptr, on_device)
+
+
+def lem_energy(h):
+    e = C.c_double()
+    q = C.c_int64()
+    rc = lib().lem_energy(h, C.byref(e), C.byref(q))
+    return rc, e.value, q.value
+
+
+def lem_get_planes(h, left_ptr, right_ptr, guide_ptr, weights_ptr):
+    return lib().lem_get_planes(h, left_ptr, right_ptr, guide_ptr, weights_ptr)
+
+
+def lem_evals_per_iteration(h) -> int:
+    return lib().lem_evals_per_iteration(h)
+
+
+# --- convenience wrapper ------------------------------------------------------
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Stereo:
+    """One handle on one pair.  Images are numpy uint8 (H, W, 3) host arrays or
+    CUDA uint8 tensors; batch outputs are CUDA tensors."""
+
+    def __init__(self, left, right, stream=None, **params):
+        import torch
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the library has no CPU path")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = lem_default_params(**params)
+        self.params.stream = C.c_void_p(stream.cuda_stream)
+        self._keep = []
+        li, ri = self._image(left), self._image(right)
+        self.h = lem_create(li, ri, self.params)
+        self.H, self.W = li.height, li.width
+
+    def _image(self, img):
+        torch = self.torch
+        if isinstance(img, torch.Tensor):
+            assert img.dtype == torch.uint8 and img.is_cuda and img.is_contiguous()
+            self._keep.append(img)
+            return lem_image(img.data_ptr(), img.shape[0], img.shape[1], 3 * img.shape[1], 1)
+        a = np.ascontiguousarray(img, dtype=np.uint8)
+        self._keep.append(a)
+        return lem_image(a.ctypes.data, a.shape[0], a.shape[1], 3 * a.shape[1], 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        return _check(rc, self.h)
+
+    # batch calls ------------------------------------------------------------
+    def unary(self, regions, labels):
+        """labels: (n_regions, K, 3) float32 -> list of (K, h, w) cost tensors."""
+        torch = self.torch
+        lab = torch.as_tensor(np.ascontiguousarray(labels, np.float32)).cuda()
+        n, K = lab.shape[0], lab.shape[1]
+        sizes = [r[2] * r[3] for r in regions]
+        out = torch.empty(K * sum(sizes), dtype=torch.float32, device="cuda")
+        self.check(lem_unary_batch(self.h, regions, _ptr(lab), K, _ptr(out)))
+        res, off = [], 0
+        for r, s in zip(regions, sizes):
+            res.append(out[off:off + K * s].view(K, r[3], r[2]))
+            off += K * s
+        return res
+
+    def pairwise(self, regions, alpha, costs_alpha):
+        torch = self.torch
+        al = torch.as_tensor(np.ascontiguousarray(alpha, np.float32)).cuda()
+        ca = torch.cat([torch.as_tensor(c, dtype=torch.float32).reshape(-1).cuda() for c in costs_alpha])
+        n = sum(r[2] * r[3] for r in regions)
+        tc = torch.empty(2 * n, dtype=torch.int32, device="cuda")
+        nc = torch.empty(4 * n, dtype=torch.int32, device="cuda")
+        ct = torch.empty(len(regions), dtype=torch.int64, device="cuda")
+        self.check(lem_pairwise_batch(self.h, regions, _ptr(al), _ptr(ca), _ptr(tc), _ptr(nc), _ptr(ct)))
+        return tc, nc, ct
+
+    def mincut(self, regions, tcaps, ncaps):
+        torch = self.torch
+        n = sum(r[2] * r[3] for r in regions)
+        tc = torch.as_tensor(tcaps, dtype=torch.int32).reshape(-1).cuda().contiguous()
+        nc = torch.as_tensor(ncaps, dtype=torch.int32).reshape(-1).cuda().contiguous()
+        take = torch.empty(n, dtype=torch.uint8, device="cuda")
+        flow = torch.empty(len(regions), dtype=torch.int64, device="cuda")
+        st = torch.empty(len(regions), dtype=torch.int32, device="cuda")
+        self.check(lem_mincut_batch(self.h, regions, _ptr(tc), _ptr(nc), _ptr(take), _ptr(flow), _ptr(st)))
+        return take, flow, st
+
+    # method ---------------------------------------------------------------------
+    def expand_group(self, it, level, group):
+        s = lem_stats()
+        self.check(lem_expand_group(self.h, it, level, group, s))
+        return s
+
+    def iterate(self, n=1, stats=True):
+        s = lem_stats() if stats else None
+        self.check(lem_expand_iteration(self.h, n, s))
+        return s
+
+    def labels(self):
+        torch = self.torch
+        abc = torch.empty(self.H, self.W, 3, dtype=torch.float32, device="cuda")
+        disp = torch.empty(self.H, self.W, dtype=torch.float32, device="cuda")
+        cost = torch.empty(self.H, self.W, dtype=torch.float32, device="cuda")
+        self.check(lem_get_labels(self.h, _ptr(abc), _ptr(disp), _ptr(cost), 1))
+        return abc, disp, cost
+
+    def set_labels(self, abc, cost=None):
+        torch = self.torch
+        a = torch.as_tensor(np.ascontiguousarray(abc, np.float32)).cuda()
+        c = torch.as_tensor(np.ascontiguousarray(cost, np.float32)).cuda() if cost is not None else None
+        self.check(lem_set_labels(self.h, _ptr(a), _ptr(c), 1))
+
+    def energy(self):
+        rc, e, q = lem_energy(self.h)
+        self.check(rc)
+        return e, q
+
+    def planes(self):
+        torch = self.torch
+        H, W = self.H, self.W
+        L = torch.empty(H, W, 4, device="cuda")
+        R = torch.empty(H, W, 4, device="cuda")
+        G = torch.empty(H, W, 9, device="cuda")
+        Wt = torch.empty(H, W, 4, device="cuda")
+        self.check(lem_get_planes(self.h, _ptr(L), _ptr(R), _ptr(G), _ptr(Wt)))
+        return L, R, G, Wt
+
+    def evals_per_iteration(self):
+        return lem_evals_per_iteration(self.h)

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/lem.h declares;
+argument checks that need no GPU return the documented status codes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1603_08328_gb300 import build as b
+    b.build()
+    from paper_1603_08328_gb300 import lem
+    return lem
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lem_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_symbols_are_exported(L):
+    names = _declared()
+    assert len(names) >= 14
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+        assert hasattr(L, n), f"binding lacks {n}"
+
+
+def test_struct_sizes_match_header(L):
+    # lem_params / lem_stats layouts are mirrored by the binding; a size check
+    # against the C compiler's view catches a dropped or reordered field
+    import subprocess
+    import tempfile
+    code = '#include "lem.h"\n#include <stdio.h>\nint main(){printf("%zu %zu %zu %zu\\n", sizeof(lem_params), ' \
+           'sizeof(lem_stats), sizeof(lem_image), sizeof(lem_region));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "s.c")
+        open(src, "w").write(code)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert sizes == [C.sizeof(L.lem_params), C.sizeof(L.lem_stats), C.sizeof(L.lem_image), C.sizeof(L.lem_region)]
+
+
+def test_default_params_are_the_papers(L):
+    p = L.lem_default_params()
+    assert (p.gf_radius, p.gf_eps, p.tau_col, p.tau_grad, p.alpha_grad) == (10, 1e-4, 10.0, 2.0, 0.9)
+    assert (p.lam, p.tau_dis, p.eps_w, p.gamma) == (1.0, 1.0, 0.01, 10.0)
+    assert list(p.cell) == [5, 15, 25] and list(p.k_prop) == [1, 2, 2] and list(p.k_rand) == [7, 0, 0]
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(L):
+    lib = L.lib()
+    a = np.zeros((32, 40, 3), np.uint8)
+    b = np.zeros((32, 41, 3), np.uint8)
+    im_a = L.lem_image(a.ctypes.data, 32, 40, 120, 0)
+    im_b = L.lem_image(b.ctypes.data, 32, 41, 123, 0)
+    p = L.lem_default_params(gf_radius=2)
+    h = C.c_void_p()
+    assert lib.lem_create(None, C.byref(im_a), C.byref(p), C.byref(h)) == L.LEM_ERR_ARG
+    assert lib.lem_create(C.byref(im_a), C.byref(im_b), C.byref(p), C.byref(h)) == L.LEM_ERR_SHAPE
+    assert "differ" in L.lem_last_error(None)
+    bad = L.lem_default_params(gf_radius=2, cell=(30, 15, 25))
+    assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
+    bad = L.lem_default_params(gf_radius=2, threads=100)
+    assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
+    bad = L.lem_default_params(gf_radius=2, disp_min=5.0, disp_max=1.0)
+    assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
+    short = L.lem_image(a.ctypes.data, 32, 40, 100, 0)
+    assert lib.lem_create(C.byref(short), C.byref(short), C.byref(p), C.byref(h)) == L.LEM_ERR_SHAPE
+    assert not h.value
+    # NULL handles
+    assert lib.lem_expand_iteration(None, 1, None) == L.LEM_ERR_ARG
+    assert lib.lem_destroy(None) == L.LEM_OK
+    assert lib.lem_evals_per_iteration(None) == -1

@@ -1,0 +1,257 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against the FP64 oracle.
+
+Tolerances (derived in the design doc from the FP32 arithmetic of the kernels):
+  data term phi          |gpu - oracle| <= 1e-4 * max(1, |oracle|)
+  quantised capacities   each quantised term within 1 unit; sums of up to 9 terms within 12
+  min-cut                bit-exact flow and cut on the same int32 graph
+  random labels          bit-exact
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import random_labels, workload_pair
+from tests.conftest import TINY_PARAMS
+
+pytestmark = pytest.mark.gpu
+
+PHI_TOL = 1e-4
+
+
+def _rel_err(gpu, ref):
+    gpu = np.asarray(gpu, np.float64)
+    return np.abs(gpu - ref) / np.maximum(1.0, np.abs(ref))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def tiny(torch_cuda, tiny_pair):
+    from paper_1603_08328_gb300.lem import Stereo
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    return g, o
+
+
+@pytest.fixture(scope="module")
+def mid(torch_cuda):
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 0)
+    params = dict(disp_max=60.0, seed=5)
+    g = Stereo(pair["left"], pair["right"], **params)
+    o = oracle.Oracle(pair["left"], pair["right"], **params)
+    return g, o, pair
+
+
+def test_packed_planes_match_the_oracle(tiny):
+    g, o = tiny
+    L, R, G, Wt = (t.cpu().numpy().astype(np.float64) for t in g.planes())
+    pl = o.planes()
+    assert (L[..., :3] == pl["L"][..., :3]).all() and (R[..., :3] == pl["R"][..., :3]).all()
+    assert np.abs(L[..., 3] - pl["L"][..., 3]).max() <= 1e-5
+    assert np.abs(R[..., 3] - pl["R"][..., 3]).max() <= 1e-5
+    assert np.abs(G[..., :3] - pl["mu"]).max() <= 1e-6
+    A = pl["A"]
+    Ag = np.stack([G[..., 3], G[..., 4], G[..., 5], G[..., 4], G[..., 6], G[..., 7], G[..., 5], G[..., 7], G[..., 8]],
+                  -1).reshape(A.shape)
+    rel = np.abs(Ag - A).max(axis=(-1, -2)) / np.abs(A).max(axis=(-1, -2))
+    assert rel.max() <= 5e-4, rel.max()
+    assert np.allclose(Wt, pl["w"] * o.p["lam"], rtol=1e-6, atol=0)
+
+
+def test_random_init_is_bit_identical(tiny_pair, torch_cuda):
+    from paper_1603_08328_gb300.lem import Stereo
+    for seed in (1, 77):
+        params = dict(TINY_PARAMS, seed=seed)
+        g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+        o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **params)
+        o.init_state()
+        abc, _, cost = g.labels()
+        lab, ocost = o.state()
+        assert (abc.cpu().numpy() == lab).all()
+        err = _rel_err(cost.cpu().numpy(), ocost)
+        assert err.max() <= PHI_TOL, err.max()
+
+
+TINY_REGIONS = [(40, 30, 15, 15), (0, 0, 10, 10), (86, 62, 10, 10), (90, 0, 6, 15), (0, 57, 15, 15),
+                (33, 20, 7, 3), (50, 40, 1, 1), (0, 10, 96, 5), (20, 0, 13, 72)]
+
+
+def test_unary_batch_tiny_all_regions(tiny):
+    g, o = tiny
+    K = 3
+    labs = random_labels(3, len(TINY_REGIONS) * K, 72, 96, 15.0).reshape(len(TINY_REGIONS), K, 3)
+    labs[0, 2] = [0.0, 0.0, 6.0]                 # fronto-parallel, integer disparity
+    labs[1, 1] = [0.0, 0.0, 2.5]                 # fronto-parallel, half-pixel
+    labs[2, 0] = [1.7, -0.8, -40.0]              # steep plane, warps mostly out of the image
+    costs = g.unary(TINY_REGIONS, labs)
+    worst = 0.0
+    for r, lab, c in zip(TINY_REGIONS, labs, costs):
+        c = c.cpu().numpy()
+        for k in range(K):
+            ref = o.region_cost(*r, lab[k])
+            worst = max(worst, _rel_err(c[k], ref).max())
+    assert worst <= PHI_TOL, worst
+
+
+def test_unary_batch_middlebury_shapes(mid):
+    """r' = 10 (41x41 windows) on 450x375: 75x75, 45x45, 15x15 regions, interior and clipped."""
+    g, o, _ = mid
+    regions = [(150, 120, 75, 75), (0, 0, 50, 50), (400, 300, 50, 75), (200, 45, 45, 45), (435, 360, 15, 15),
+               (100, 200, 15, 15)]
+    K = 2
+    labs = random_labels(9, len(regions) * K, 375, 450, 60.0).reshape(len(regions), K, 3)
+    costs = g.unary(regions, labs)
+    worst, errs = 0.0, []
+    for r, lab, c in zip(regions, labs, costs):
+        c = c.cpu().numpy()
+        for k in range(K):
+            ref = o.region_cost(*r, lab[k])
+            e = _rel_err(c[k], ref)
+            errs.append(e.ravel())
+            worst = max(worst, e.max())
+    allerr = np.concatenate(errs)
+    print(f"phi rel err: max {worst:.3e}, p99 {np.quantile(allerr, 0.99):.3e}, median {np.median(allerr):.3e}")
+    assert worst <= PHI_TOL, worst
+
+
+def _gpu_state_to_oracle(g, o):
+    abc, _, cost = g.labels()
+    o.put_state(abc.cpu().numpy(), cost.cpu().numpy().astype(np.float64))
+    return abc.cpu().numpy(), cost.cpu().numpy().astype(np.float64)
+
+
+def test_pairwise_batch_matches_oracle_graph(tiny):
+    g, o = tiny
+    g.iterate(1)                                   # realistic current labels
+    lab, cost = _gpu_state_to_oracle(g, o)
+    regions = [(35, 25, 15, 15), (0, 0, 10, 10), (86, 67, 10, 5), (60, 10, 4, 4)]
+    rng = np.random.default_rng(4)
+    alpha = np.stack([lab[r[1] + 1, r[0] + 1] + np.float32([0.01, -0.01, 0.4]) * rng.standard_normal(3)
+                      for r in regions]).astype(np.float32)
+    ca = [c[0] for c in g.unary(regions, alpha[:, None, :])]
+    tc, nc, ct = g.pairwise(regions, alpha, ca)
+    tc, nc, ct = tc.cpu().numpy(), nc.cpu().numpy(), ct.cpu().numpy()
+    off = 0
+    exact = total = 0
+    for i, r in enumerate(regions):
+        n = r[2] * r[3]
+        gref = o.build_graph(*r, alpha[i], lab, cost, ca[i].cpu().numpy().astype(np.float64))
+        gt = tc[2 * off:2 * (off + n)].reshape(r[3], r[2], 2)
+        gn = nc[4 * off:4 * (off + n)].reshape(r[3], r[2], 4)
+        assert np.abs(gn - gref["ncap"]).max() <= 3
+        du = (gt[..., 0] - gt[..., 1]) - (gref["tcap"][..., 0] - gref["tcap"][..., 1])
+        assert np.abs(du).max() <= 12
+        assert abs(int(ct[i]) - gref["const"]) <= 12 * n
+        exact += (gn == gref["ncap"]).sum() + (du == 0).sum()
+        total += gn.size + du.size
+        off += n
+    assert exact / total > 0.9, exact / total
+
+
+def _random_graph(rng, w, h, tmax=200000, cap=131072):
+    tcap = rng.integers(0, tmax, size=(h, w, 2)).astype(np.int32)
+    tcap[rng.random((h, w)) < 0.5, 0] = 0
+    tcap[tcap[..., 0] > 0, 1] = 0
+    ncap = rng.integers(0, cap, size=(h, w, 4)).astype(np.int32)
+    ncap[rng.random((h, w, 4)) < 0.3] = 0
+    # capacities toward neighbours outside the region are zero by the layout
+    ncap[:, -1, 0] = 0
+    ncap[:, 0, 1] = 0
+    ncap[-1, :, 1:] = 0
+    ncap[:, -1, 3] = 0
+    return tcap, ncap
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (16, 1), (1, 16), (4, 4), (15, 15), (45, 45), (75, 75), (75, 13)])
+def test_mincut_batch_random_graphs_bit_exact(mid, shape):
+    g, _, _ = mid
+    w, h = shape
+    rng = np.random.default_rng(w * 1000 + h)
+    graphs = [_random_graph(rng, w, h) for _ in range(3)]
+    graphs.append((np.zeros((h, w, 2), np.int32), np.zeros((h, w, 4), np.int32)))   # degenerate: no edges
+    regions = [(0, 0, w, h)] * len(graphs)
+    tc = np.concatenate([t.reshape(-1) for t, _ in graphs])
+    nc = np.concatenate([c.reshape(-1) for _, c in graphs])
+    take, flow, st = g.mincut(regions, tc, nc)
+    take, flow, st = take.cpu().numpy(), flow.cpu().numpy(), st.cpu().numpy()
+    for i, (t, c) in enumerate(graphs):
+        f, cut = oracle.maxflow(w, h, t, c, "dinic")
+        assert st[i] == 0
+        assert flow[i] == f
+        assert (take[i * w * h:(i + 1) * w * h].reshape(h, w) == cut).all()
+
+
+def test_mincut_batch_on_move_graphs(tiny):
+    """Graphs built by lem_pairwise_batch: the GPU cut equals Dinic's on the same int32 graph."""
+    g, o = tiny
+    lab, cost = _gpu_state_to_oracle(g, o)
+    regions = [(35, 25, 15, 15), (0, 0, 10, 10), (81, 57, 15, 15), (20, 30, 15, 15)]
+    alpha = np.stack([lab[r[1] + 7 if r[3] > 7 else r[1], r[0] + 2] for r in regions]).astype(np.float32)
+    ca = [c[0] for c in g.unary(regions, alpha[:, None, :])]
+    tc, nc, ct = g.pairwise(regions, alpha, ca)
+    take, flow, st = g.mincut(regions, tc, nc)
+    tc, nc, take, flow = tc.cpu().numpy(), nc.cpu().numpy(), take.cpu().numpy(), flow.cpu().numpy()
+    off = 0
+    for i, r in enumerate(regions):
+        n = r[2] * r[3]
+        f, cut = oracle.maxflow(r[2], r[3], tc[2 * off:2 * (off + n)], nc[4 * off:4 * (off + n)], "dinic")
+        assert flow[i] == f and (take[off:off + n].reshape(r[3], r[2]) == cut).all()
+        off += n
+
+
+def test_energy_matches_oracle(tiny):
+    g, o = tiny
+    lab, cost = _gpu_state_to_oracle(g, o)
+    e, q = g.energy()
+    eo, qo = o.energy()
+    assert abs(q - qo) <= 2 * lab.shape[0] * lab.shape[1] * 5, (q, qo)   # <= 2 units per term
+    assert abs(e - eo) / abs(eo) <= 1e-5
+
+
+def test_expand_groups_in_lockstep_with_oracle(tiny_pair, torch_cuda):
+    """Algorithm 1 on the tiny scene, group by group: the GPU and the oracle start from
+    the same labels, draw the same candidates and take the same moves; any pixel where
+    the FP32 and FP64 costs decide a near-tie differently is counted, then the oracle is
+    re-synchronised to the GPU labels.  The GPU energy never increases."""
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(TINY_PARAMS, seed=23)
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **params)
+    o.init_state()
+    q_prev = g.energy()[1]
+    flips = switched = 0
+    for it in range(4):
+        for grp in range(16):
+            st = g.expand_group(it, 0, grp)
+            acc, _ = o.expand_group(it, 0, grp)
+            assert st.maxflow_limit == 0
+            abc = g.labels()[0].cpu().numpy()
+            lab, _ = o.state()
+            flips += int((abc != lab).any(axis=-1).sum())
+            switched += acc
+            o.set_labels(abc)
+            q = g.energy()[1]
+            assert q <= q_prev
+            q_prev = q
+    print(f"lockstep: {flips} differing pixels over {switched} switches")
+    assert flips <= max(10, 0.002 * switched)
+
+
+def test_full_iteration_middlebury(mid):
+    g, o, pair = mid
+    e0, q0 = g.energy()
+    st = g.iterate(1)
+    assert st.maxflow_limit == 0
+    assert st.evals == g.evals_per_iteration()
+    assert st.energy_q < q0
+    st2 = g.iterate(1)
+    assert st2.energy_q <= st.energy_q
