@@ -1,0 +1,407 @@
+"""Benchmark: pixel-label cost evaluations per second of local-expansion-move stereo.
+
+One step = one outer iteration of Algorithm 1 (3 grid levels x 16 disjoint
+groups, every alpha_ij-expansion evaluated, cut and committed) on the
+Middlebury-V2-shaped synthetic pair (450 x 375, disparities 0-60, cells
+5/15/25 px, 41 x 41 matching windows, FP32).  Steps continue one run from the
+random initialisation; warm-up steps run on a separate handle.  L2 is flushed
+between timed steps; each step is timed with CUDA events on the library's
+stream.
+
+Prints one JSON line.  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "middlebury_450x375"
+PARAMS = dict(disp_max=60.0)          # everything else: the paper's values (lem_default_params)
+METRIC = "pixel-label cost evals/s"
+FP32_LANES_PER_SM = 128               # FP32 FMA lanes per SM (Blackwell)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lem", choices=["lem", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    return ap.parse_args()
+
+
+# --- distributed plumbing (replicas: every rank solves its own pair) -------------
+
+def dist_init(n):
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    world = int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return rank, world, dist
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# --- clocks during the timed region ---------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --- algorithmic work ------------------------------------------------------------
+
+def region_geometry(H, W, s):
+    """(x0, y0, w, h) of every expansion region at cell size s, by group."""
+    nx, ny = -(-W // s), -(-H // s)
+    groups = {g: [] for g in range(16)}
+    for j in range(ny):
+        for i in range(nx):
+            x0, x1 = max(0, (i - 1) * s), min(W, (i + 2) * s)
+            y0, y1 = max(0, (j - 1) * s), min(H, (j + 2) * s)
+            groups[4 * (j % 4) + (i % 4)].append((x0, y0, x1 - x0, y1 - y0))
+    return groups
+
+
+def algorithmic_flops(H, W, r, x0, y0, w, h):
+    """FP32 operations the data term of one candidate on region R needs: about 30 per
+    raw cost over M, 44 per regression window over R grown by r' (4 box means and the
+    3x3 solve) and 24 per output pixel (4 box means and the output)."""
+    mw = min(W, x0 + w + 2 * r) - max(0, x0 - 2 * r)
+    mh = min(H, y0 + h + 2 * r) - max(0, y0 - 2 * r)
+    kw = min(W, x0 + w + r) - max(0, x0 - r)
+    kh = min(H, y0 + h + r) - max(0, y0 - r)
+    return 30 * mw * mh + 44 * kw * kh + 24 * w * h
+
+
+def launches_and_work(H, W, p):
+    r = p["gf_radius"]
+    out = []
+    for l in range(p["n_levels"]):
+        s = p["cell"][l]
+        nprop = p["k_prop"][l] + p["k_rand"][l]
+        groups = region_geometry(H, W, s)
+        for g in range(16):
+            regs = groups[g]
+            if not regs:
+                continue
+            evals = sum(w * h for (_, _, w, h) in regs) * nprop
+            flops = sum(algorithmic_flops(H, W, r, *R) for R in regs) * nprop
+            out.append(dict(level=l, group=g, evals=evals, flops=flops, regions=len(regs)))
+    return out
+
+
+def kernel_source_sha():
+    with open(os.path.join(ROOT, "paper_1603_08328_gb300", "csrc", "lem_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def traffic_from_profile(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha256") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# --- CPU oracle ------------------------------------------------------------------
+
+def cpu_oracle_baseline(pair, p, seed):
+    """The oracle, as it stands, on the host cores: one full outer iteration (iteration
+    0 from the random initialisation) of the same workload."""
+    import oracle
+    o = oracle.Oracle(pair["left"], pair["right"], seed=seed, **PARAMS)
+    o.init_state()
+    t = time.perf_counter()
+    _, evals = o.iterate(0)
+    dt = time.perf_counter() - t
+    return {"value": evals / dt, "unit": METRIC, "cores": oracle.openmp_threads(), "kind": "oracle",
+            "sample": f"outer iteration 0 of {WORKLOAD} (all 48 level-group launches, {evals} evals), "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores, one (level, group)
+    expansion per step, cycling through the 48 of an outer iteration."""
+    rank, world, dist = dist_init(args.gpus)
+    if rank != 0:
+        return
+    import oracle
+    from synth import workload_pair
+    pair = workload_pair(WORKLOAD, args.seed)
+    o = oracle.Oracle(pair["left"], pair["right"], seed=args.seed + 1, **PARAMS)
+    o.init_state()
+    nl = len(oracle.PAPER_DEFAULTS["cell"])
+    seq = [(it, l, g) for it in range(1000) for l in range(nl) for g in range(16)]
+    k = 0
+    for _ in range(args.warmup):
+        o.expand_group(*seq[k])
+        k += 1
+    evals = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, e = o.expand_group(*seq[k])
+        evals += e
+        k += 1
+    dt = time.perf_counter() - t0
+    v = evals / dt
+    cores = oracle.openmp_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "height": 375, "width": 450, "disp_max": 60, "cells": [5, 15, 25],
+                       "window": 41, "step": "one (level, group) expansion of the CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} (level, group) expansions of outer iteration 0.."},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --- GPU -------------------------------------------------------------------------
+
+def run_lem(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    rank, world, dist = dist_init(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    dev = torch.cuda.current_device()
+    if rank == 0 or dist is None:
+        __graft_entry__.build()
+    barrier(dist)
+    from paper_1603_08328_gb300 import lem
+    from synth import workload_pair
+
+    pair = workload_pair(WORKLOAD, args.seed + rank)
+    stream = torch.cuda.current_stream()
+    H, W = pair["left"].shape[:2]
+
+    # warm-up: a separate handle, W outer iterations
+    warm = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1000 + rank, **PARAMS)
+    warm.iterate(max(1, args.warmup), stats=False)
+    torch.cuda.synchronize()
+    warm.close()
+
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **PARAMS)
+    p = dict(gf_radius=g.params.gf_radius, n_levels=g.params.n_levels, cell=list(g.params.cell),
+             k_prop=list(g.params.k_prop), k_rand=list(g.params.k_rand))
+    work = launches_and_work(H, W, p)
+    evals_per_step = g.evals_per_iteration()
+    assert evals_per_step == sum(x["evals"] for x in work)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    e0, q0 = g.energy()
+    g.iterate(0)                       # stats baseline: counters restart here
+    times = []
+    torch.cuda.synchronize()
+    barrier(dist)
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.check(lem.lem_expand_iteration(g.h, 1, None))
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+    torch.cuda.synchronize()
+    t_total = sum(times)
+    t_max = max_over_ranks(t_total, dist)
+    e1, q1 = g.energy()
+    st = g.iterate(0)
+    assert st.maxflow_limit == 0, "a cut hit its round limit"
+
+    # per-launch durations of the expansion kernel (one launch per lem_expand_group call),
+    # on a fresh handle over one outer iteration, L2 flushed before every launch
+    g2 = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **PARAMS)
+    per, cut = [], []
+    for wk in work:
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        sts = lem.lem_stats()
+        a.record(stream)
+        g2.check(lem.lem_expand_group(g2.h, 0, wk["level"], wk["group"], None))
+        b.record(stream)
+        b.synchronize()
+        per.append(a.elapsed_time(b) / 1e3)
+        lem.lib().lem_expand_iteration(g2.h, 0, lem.C.byref(sts))
+        cut.append((sts.pr_rounds, sts.pr_global_relabels, sts.pr_bfs_levels))
+    g2.close()
+    flops = sum(wk["flops"] for wk in work)
+    launch_avg = sum(per) / len(per)
+    achieved = flops / len(work) / launch_avg / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    by_level = {}
+    for wk, t, c in zip(work, per, cut):
+        d = by_level.setdefault(wk["level"], {"ms": 0.0, "evals": 0, "flops": 0, "launches": 0, "cuts": 0,
+                                              "rounds": 0, "relabels": 0, "bfs_levels": 0})
+        d["ms"] += 1e3 * t
+        d["evals"] += wk["evals"]
+        d["flops"] += wk["flops"]
+        d["launches"] += 1
+        lv = wk["level"]
+        d["cuts"] += wk["regions"] * (p["k_prop"][lv] + p["k_rand"][lv])
+        d["rounds"] += c[0]
+        d["relabels"] += c[1]
+        d["bfs_levels"] += c[2]
+
+    # end to end through the C ABI: pinned host images in, disparity map out,
+    # one job = create + 10 outer iterations
+    n_iters_job = 10
+    hl = torch.from_numpy(pair["left"]).pin_memory()
+    hr = torch.from_numpy(pair["right"]).pin_memory()
+    hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for j in range(args.e2e_jobs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prm = lem.lem_default_params(seed=7 + j, **PARAMS)
+        prm.stream = stream.cuda_stream
+        li = lem.lem_image(hl.data_ptr(), H, W, 3 * W, 0)
+        ri = lem.lem_image(hr.data_ptr(), H, W, 3 * W, 0)
+        h = lem.lem_create(li, ri, prm)
+        lem._check(lem.lem_expand_iteration(h, n_iters_job, None), h)
+        lem._check(lem.lem_get_labels(h, None, lem.C.c_void_p(hd.data_ptr()), None, 0), h)
+        e2e_t.append(time.perf_counter() - t0)
+        lem.lem_destroy(h)
+    e2e_job = max_over_ranks(sum(e2e_t) / len(e2e_t), dist)
+    e2e_v = world * n_iters_job * evals_per_step / e2e_job
+
+    if rank != 0:
+        return
+    value = world * evals_per_step * args.steps / t_max
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "height": H, "width": W, "disp_max": 60, "cells": p["cell"],
+                   "window": 4 * p["gf_radius"] + 1, "step": "one outer iteration (48 level-group launches)",
+                   "schedule": "sequential proposals (Algorithm 2)", "l2": "flushed between timed steps",
+                   "parallelism": f"replicas x{world}", "evals_per_step": evals_per_step},
+        "e2e": {"value": e2e_v, "unit": METRIC, "h2d_bytes_per_step": 2 * H * W * 3, "d2h_bytes_per_step": H * W * 4,
+                "step": f"one job: host images -> lem_create -> {n_iters_job} iterations -> host disparity",
+                "jobs": args.e2e_jobs, "ms_per_job": 1e3 * e2e_job},
+        "gpu_launches": len(work) * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic_from_profile("k_expand_group"), "kernel": "k_expand_group",
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                     "launch_avg_ms": 1e3 * launch_avg},
+        "clocks": clk.summary(),
+        "energy": {"before": e0, "after": e1},
+        "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
+                            "evals_per_s": v["evals"] / (v["ms"] / 1e3),
+                            "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
+                            "rounds_per_cut": v["rounds"] / max(1, v["cuts"]),
+                            "relabels_per_cut": v["relabels"] / max(1, v["cuts"]),
+                            "bfs_levels_per_relabel": v["bfs_levels"] / max(1, v["relabels"])}
+                   for k, v in by_level.items()},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_baseline(pair, p, seed=1)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_lem(args)
+
+
+if __name__ == "__main__":
+    main()

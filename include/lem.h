@@ -94,6 +94,8 @@ typedef struct {
     int x0, y0, w, h;
 } lem_region;
 
+/* Counters (evals, accepted, maxflow_limit) cover the work done since the
+ * previous call on the same handle that returned stats (or since lem_create). */
 typedef struct {
     int64_t energy_q;      /* sum_p Q(phi_p) + sum_pq Q(lambda psi_pq), Q(x) = rne(S x) */
     double energy;         /* energy_q / S                                             */
@@ -102,6 +104,9 @@ typedef struct {
     int64_t maxflow_limit; /* cuts that hit the round limit                            */
     int32_t fp64_inverses; /* guide-covariance inverses taken in FP64 (lem_create)     */
     int32_t iterations;    /* outer iterations done so far on this handle              */
+    int64_t pr_rounds;     /* push-relabel rounds (all cuts)                           */
+    int64_t pr_global_relabels; /* global relabels (all cuts)                          */
+    int64_t pr_bfs_levels; /* BFS frontiers processed by the global relabels           */
 } lem_stats;
 
 typedef struct lem_handle lem_handle;
@@ -182,7 +187,7 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
  * in turn.  Updates the handle's labels and cost cache.  Does not advance the
  * handle's iteration counter.  stats may be NULL (no synchronisation); when
  * given, the call synchronises the stream and fills evals/accepted/maxflow_limit
- * for this launch.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+ * (energy fields are left 0).  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *stats);
 
 /* n_iters outer iterations of Algorithm 1 (every level, all 16 groups),

@@ -28,6 +28,7 @@ struct lem_handle {
     size_t cap_regions = 0;
     int iter = 0;
     int fp64_inverses = 0;
+    lem::Counters last{};  // device counters at the previous stats read
     std::string err;
 };
 
@@ -178,9 +179,21 @@ int run_energy(lem_handle *h, long long *eq) {
     return LEM_OK;
 }
 
-int threads_for_level(const lem_handle *h, int s) {
-    (void)s;
-    return h->p.threads;
+// Reads the cumulative device counters; fills the deltas since the previous read.
+int read_counters(lem_handle *h, lem_stats *stats) {
+    lem::Counters c;
+    LEM_CUDA(h, cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, h->st));
+    LEM_CUDA(h, cudaStreamSynchronize(h->st));
+    stats->evals = (int64_t)(c.evals - h->last.evals);
+    stats->accepted = (int64_t)(c.accepted - h->last.accepted);
+    stats->maxflow_limit = (int64_t)(c.limit_hits - h->last.limit_hits);
+    stats->pr_rounds = (int64_t)(c.rounds - h->last.rounds);
+    stats->pr_global_relabels = (int64_t)(c.relabels - h->last.relabels);
+    stats->pr_bfs_levels = (int64_t)(c.bfs_levels - h->last.bfs_levels);
+    stats->fp64_inverses = h->fp64_inverses;
+    stats->iterations = h->iter;
+    h->last = c;
+    return LEM_OK;
 }
 
 }  // namespace
@@ -218,7 +231,7 @@ void lem_default_params(lem_params *p) {
     p->stream = nullptr;
     p->max_rounds = 200000;
     p->gr_interval = 16;
-    p->strip_rows = 8;
+    p->strip_rows = 16;
     p->threads = 256;
 }
 
@@ -341,7 +354,7 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
     if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
     if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
     LEM_CUDA(h, lem::launch_mincut_batch(kparams(h), h->d_regions, h->d_offsets, n_regions, mn, tcaps, ncaps,
-                                         take_alpha, flow, status, h->p.threads, h->st));
+                                         take_alpha, flow, status, h->ctr, h->st));
     return LEM_OK;
 }
 
@@ -351,7 +364,7 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group) {
     lv.k_prop = h->p.k_prop[level];
     lv.k_rand = h->p.k_rand[level];
     LEM_CUDA(h, lem::launch_expand_group(planes(h), kparams(h), lv, level, iter, group, h->lab, h->phiA, h->ctr,
-                                         threads_for_level(h, lv.s), h->st));
+                                         h->st));
     return LEM_OK;
 }
 
@@ -359,19 +372,11 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (iter < 0 || level < 0 || level >= h->p.n_levels || group < 0 || group > 15)
         return fail(h, LEM_ERR_ARG, "iter/level/group out of range");
-    if (stats) LEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
     int rc = expand_group_impl(h, iter, level, group);
     if (rc != LEM_OK) return rc;
     if (stats) {
-        lem::Counters c;
-        LEM_CUDA(h, cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, h->st));
-        LEM_CUDA(h, cudaStreamSynchronize(h->st));
         std::memset(stats, 0, sizeof(*stats));
-        stats->evals = (int64_t)c.evals;
-        stats->accepted = (int64_t)c.accepted;
-        stats->maxflow_limit = (int64_t)c.limit_hits;
-        stats->fp64_inverses = h->fp64_inverses;
-        stats->iterations = h->iter;
+        return read_counters(h, stats);
     }
     return LEM_OK;
 }
@@ -379,7 +384,6 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (n_iters < 0) return fail(h, LEM_ERR_ARG, "n_iters < 0");
-    if (stats) LEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
     for (int it = 0; it < n_iters; ++it) {
         for (int l = 0; l < h->p.n_levels; ++l)
             for (int g = 0; g < 16; ++g) {
@@ -389,18 +393,12 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
         ++h->iter;
     }
     if (stats) {
-        lem::Counters c;
-        LEM_CUDA(h, cudaMemcpyAsync(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost, h->st));
         long long eq = 0;
         int rc = run_energy(h, &eq);
         if (rc != LEM_OK) return rc;
+        if ((rc = read_counters(h, stats)) != LEM_OK) return rc;
         stats->energy_q = eq;
         stats->energy = (double)eq / h->p.quant_scale;
-        stats->evals = (int64_t)c.evals;
-        stats->accepted = (int64_t)c.accepted;
-        stats->maxflow_limit = (int64_t)c.limit_hits;
-        stats->fp64_inverses = h->fp64_inverses;
-        stats->iterations = h->iter;
     }
     return LEM_OK;
 }

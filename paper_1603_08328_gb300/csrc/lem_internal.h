@@ -42,7 +42,9 @@ struct Counters {
     unsigned long long accepted;
     unsigned long long limit_hits;
     unsigned long long evals;
-    unsigned long long pad;
+    unsigned long long rounds;      // push-relabel rounds
+    unsigned long long relabels;    // global relabels
+    unsigned long long bfs_levels;  // BFS frontiers summed over global relabels
 };
 
 // Shared-memory bytes the region cost pipeline needs for regions up to
@@ -69,9 +71,9 @@ cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const i
                                   int threads, cudaStream_t st);
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
                                 int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
-                                int64_t *flow, int32_t *status, int threads, cudaStream_t st);
+                                int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st);
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
-                                int group, float4 *lab, float *phiA, Counters *ctr, int threads, cudaStream_t st);
+                                int group, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st);
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st);
 cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,

@@ -613,40 +613,70 @@ __device__ long long block_sum_ll(long long v, long long *red) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int dir_off(int k, int w) { return dir_dx(k) + dir_dy(k) * w; }
 
-// Exact distances to the sink in the residual graph (level-synchronous BFS);
-// returns whether some node with excess can still reach the sink.
-__device__ bool global_relabel(int n, int w, const int *res, const int *v, uint16_t *hh) {
+// Exact distances to the sink in the residual graph: BFS backwards from the
+// nodes with residual sink capacity, frontier by frontier through a queue in
+// shared memory (each node enters once).  Returns whether some node with
+// excess can still reach the sink; *levels gets the BFS depth.
+__device__ bool global_relabel(int n, int w, const int *res, const int *v, uint16_t *hh, uint16_t *queue,
+                               int *qtail, int *levels) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < n; i += nt) hh[i] = v[i] < 0 ? 1 : kInf;
+    const int h = n / w;
+    if (tid == 0) *qtail = 0;
     __syncthreads();
-    for (int level = 1; level <= n; ++level) {
-        int changed = 0;
-        for (int i = tid; i < n; i += nt) {
-            if (hh[i] != kInf) continue;
+    for (int i = tid; i < n; i += nt) {
+        if (v[i] < 0) {
+            hh[i] = 1;
+            queue[atomicAdd(qtail, 1)] = (uint16_t)i;
+        } else {
+            hh[i] = kInf;
+        }
+    }
+    __syncthreads();
+    int head = 0, tail = *qtail, level = 1;
+    while (head < tail) {
+        for (int q = head + tid; q < tail; q += nt) {
+            const int j = queue[q];
+            const int jx = j % w, jy = j / w;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                if (res[k * n + i] > 0 && hh[i + dir_off(k, w)] == level) {
-                    hh[i] = (uint16_t)(level + 1);
-                    changed = 1;
-                    break;
-                }
+                const int ix = jx + dir_dx(k), iy = jy + dir_dy(k);
+                if (ix < 0 || ix >= w || iy < 0 || iy >= h) continue;
+                const int i = iy * w + ix;
+                // edge i -> j runs in direction k^4 from i
+                if (hh[i] == kInf && res[(k ^ 4) * n + i] > 0 &&
+                    atomicCAS(&hh[i], (unsigned short)kInf, (unsigned short)(level + 1)) == kInf)
+                    queue[atomicAdd(qtail, 1)] = (uint16_t)i;
             }
         }
-        if (!__syncthreads_or(changed)) break;
+        __syncthreads();
+        head = tail;
+        tail = *qtail;
+        ++level;
+        __syncthreads();
     }
+    *levels += level;
     int act = 0;
     for (int i = tid; i < n; i += nt) act |= (v[i] > 0 && hh[i] != kInf);
     return __syncthreads_or(act) != 0;
 }
 
+struct CutCount {
+    int rounds, relabels, levels;
+};
+
 // Maximum preflow.  On return (LEM_OK) hh[i] != kInf exactly for the nodes that
 // reach the sink in the residual graph: the minimal sink side of the cut.
-__device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, int max_rounds, int gr_interval) {
+__device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, uint16_t *queue, int *qtail,
+                           int max_rounds, int gr_interval, CutCount &cc) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    bool act = global_relabel(n, w, res, v, hh);
+    bool act = global_relabel(n, w, res, v, hh, queue, qtail, &cc.levels);
+    ++cc.relabels;
     int rounds = 0;
     while (act) {
-        if (rounds >= max_rounds) return LEM_ERR_MAXFLOW_LIMIT;
+        if (rounds >= max_rounds) {
+            cc.rounds += rounds;
+            return LEM_ERR_MAXFLOW_LIMIT;
+        }
         int mine = 0;
         for (int i = tid; i < n; i += nt) {
             const int e = v[i];
@@ -682,9 +712,29 @@ __device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, int max
         // a round in which no thread found an active node (so nothing moved),
         // or the periodic point, hands over to an exact global relabel
         const int any = __syncthreads_or(mine);
-        if (!any || rounds % gr_interval == 0) act = global_relabel(n, w, res, v, hh);
+        if (!any || rounds % gr_interval == 0) {
+            act = global_relabel(n, w, res, v, hh, queue, qtail, &cc.levels);
+            ++cc.relabels;
+        }
     }
+    cc.rounds += rounds;
     return LEM_OK;
+}
+
+// shared-memory layout of the CTA min-cut for n nodes
+struct CutSmem {
+    int *res;
+    int *v;
+    uint16_t *hh;
+    uint16_t *queue;
+};
+__device__ __forceinline__ CutSmem cut_layout(void *base, int n) {
+    CutSmem c;
+    c.res = (int *)base;
+    c.v = c.res + 8 * n;
+    c.hh = (uint16_t *)(c.v + n);
+    c.queue = c.hh + n;
+    return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -732,50 +782,58 @@ __global__ void k_pairwise_batch(DevPlanes P, KParams kp, const int4 *regions, c
     if (threadIdx.x == 0) cterm[i] = cst;
 }
 
-__global__ void k_mincut_batch(KParams kp, const int4 *regions, const int64_t *offsets, const int32_t *tcaps,
-                               const int32_t *ncaps, uint8_t *take, int64_t *flow, int32_t *status) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *regions, const int64_t *offsets,
+                                                       const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                                       int64_t *flow, int32_t *status, Counters *ctr) {
     extern __shared__ __align__(16) int smi[];
     __shared__ long long red[33];
+    __shared__ int qtail;
     const int i = blockIdx.x;
     const int4 R = regions[i];
     const int n = R.z * R.w, w = R.z, h = R.w;
     const int64_t off = offsets[i];
-    int *res = smi;
-    int *v = res + 8 * n;
-    uint16_t *hh = (uint16_t *)(v + n);
+    CutSmem cs = cut_layout(smi, n);
     long long capt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int ix = j % w, iy = j / w;
-        const int cs = tcaps[2 * (off + j)], ct = tcaps[2 * (off + j) + 1];
-        v[j] = cs - ct;
-        capt += ct;
+        const int c_s = tcaps[2 * (off + j)], c_t = tcaps[2 * (off + j) + 1];
+        cs.v[j] = c_s - c_t;
+        capt += c_t;
         for (int k = 0; k < 8; ++k) {
             int c = 0;
             const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
             if (k < 4 && jx >= 0 && jx < w && jy >= 0 && jy < h) c = max(0, (int)ncaps[4 * (off + j) + k]);
-            res[k * n + j] = c;
+            cs.res[k * n + j] = c;
         }
     }
     capt = block_sum_ll(capt, red);
-    const int st = cta_maxflow(n, w, res, v, hh, kp.max_rounds, kp.gr_interval);
+    CutCount cc{0, 0, 0};
+    const int st = cta_maxflow(n, w, cs.res, cs.v, cs.hh, cs.queue, &qtail, kp.max_rounds, kp.gr_interval, cc);
     long long rt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        take[off + j] = (st == LEM_OK && hh[j] != kInf) ? 1 : 0;
-        rt += max(0, -v[j]);
+        take[off + j] = (st == LEM_OK && cs.hh[j] != kInf) ? 1 : 0;
+        rt += max(0, -cs.v[j]);
     }
     rt = block_sum_ll(rt, red);
     if (threadIdx.x == 0) {
         flow[i] = capt - rt;
         status[i] = st;
+        atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
+        atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
+        atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
     }
 }
 
 // All expansions of one group at one level: one CTA per region, Algorithm 2.
-__global__ void k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, int group, float4 *lab,
-                               float *phiA, Counters *ctr) {
+template <int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
+    k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, int group, float4 *lab, float *phiA,
+                   Counters *ctr) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha;
     __shared__ long long red[33];
+    __shared__ int qtail;
     const int H = P.H, W = P.W, s = lv.s;
     const int nx = (W + s - 1) / s;
     const int gi = group & 3, gj = group >> 2;
@@ -785,13 +843,12 @@ __global__ void k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int
     const int y0 = max(0, (cj - 1) * s), y1 = min(H, (cj + 2) * s);
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
-    int *res = (int *)smf;
-    int *v = res + 8 * n;
-    uint16_t *hh = (uint16_t *)(v + n);
+    CutSmem cs = cut_layout(smf, n);
     // outer perturbation sizes of this iteration, copied into Algorithm 2
     double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
     double rn = ldexp(1.0, -iter);
     long long acc = 0, hits = 0;
+    CutCount cc{0, 0, 0};
     const int nprop = lv.k_prop + lv.k_rand;
     for (int t = 0; t < nprop; ++t) {
         const bool perturb = t >= lv.k_prop;
@@ -807,22 +864,19 @@ __global__ void k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int
         const float4 al = s_alpha;
         region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
         // (region_unary ends with a barrier; its shared memory is reused below)
-        long long base_t = 0;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const int ix = j % w, iy = j / w;
             NodeCaps o;
             build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
-            v[j] = o.cap_s - o.cap_t;
-            for (int d = 0; d < 4; ++d) res[d * n + j] = o.k[d];
-            for (int d = 4; d < 8; ++d) res[d * n + j] = 0;
-            base_t += o.cap_t;
+            cs.v[j] = o.cap_s - o.cap_t;
+            for (int d = 0; d < 4; ++d) cs.res[d * n + j] = o.k[d];
+            for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
         }
-        (void)base_t;
         __syncthreads();
-        const int st = cta_maxflow(n, w, res, v, hh, kp.max_rounds, kp.gr_interval);
+        const int st = cta_maxflow(n, w, cs.res, cs.v, cs.hh, cs.queue, &qtail, kp.max_rounds, kp.gr_interval, cc);
         if (st == LEM_OK) {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                if (hh[j] == kInf) continue;
+                if (cs.hh[j] == kInf) continue;
                 const size_t p = (size_t)(y0 + j / w) * W + x0 + j % w;
                 lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
                 ++acc;
@@ -837,6 +891,9 @@ __global__ void k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int
         atomicAdd(&ctr->accepted, (unsigned long long)acc);
         atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
         atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop);
+        atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
+        atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
+        atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
     }
 }
 
@@ -917,6 +974,9 @@ size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
                             2 * (size_t)RS);
 }
 
+// threads per CTA for a region of n nodes: about 4-8 nodes per thread
+int threads_for_nodes(int n) { return n <= 400 ? 256 : (n <= 2500 ? 512 : 1024); }
+
 cudaError_t set_smem(const void *fn, size_t bytes) {
     if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return cudaSuccess;
@@ -925,7 +985,7 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 }  // namespace
 
 size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh) { return unary_bytes_host(kp, H, W, rw, rh); }
-size_t cut_smem_bytes(int n) { return (size_t)9 * n * sizeof(int) + (size_t)((n + 1) & ~1) * sizeof(uint16_t); }
+size_t cut_smem_bytes(int n) { return (size_t)9 * n * sizeof(int) + (size_t)2 * n * sizeof(uint16_t) + 16; }
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
                               int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
@@ -976,18 +1036,37 @@ cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const i
     return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t mincut_nt(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions, size_t sm,
+                      const int32_t *tcaps, const int32_t *ncaps, uint8_t *take, int64_t *flow, int32_t *status,
+                      Counters *ctr, cudaStream_t st) {
+    cudaError_t e = set_smem((const void *)k_mincut_batch<NT>, sm);
+    if (e != cudaSuccess) return e;
+    k_mincut_batch<NT><<<n_regions, NT, sm, st>>>(kp, regions, offsets, tcaps, ncaps, take, flow, status, ctr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
                                 int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
-                                int64_t *flow, int32_t *status, int threads, cudaStream_t st) {
+                                int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st) {
     const size_t sm = cut_smem_bytes(max_nodes);
-    cudaError_t e = set_smem((const void *)k_mincut_batch, sm);
+    const int nt = threads_for_nodes(max_nodes);
+    if (nt == 256) return mincut_nt<256>(kp, regions, offsets, n_regions, sm, tcaps, ncaps, take, flow, status, ctr, st);
+    if (nt == 512) return mincut_nt<512>(kp, regions, offsets, n_regions, sm, tcaps, ncaps, take, flow, status, ctr, st);
+    return mincut_nt<1024>(kp, regions, offsets, n_regions, sm, tcaps, ncaps, take, flow, status, ctr, st);
+}
+
+template <int NT>
+cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, int group,
+                      float4 *lab, float *phiA, Counters *ctr, int nblocks, size_t sm, cudaStream_t st) {
+    cudaError_t e = set_smem((const void *)k_expand_group<NT>, sm);
     if (e != cudaSuccess) return e;
-    k_mincut_batch<<<n_regions, threads, sm, st>>>(kp, regions, offsets, tcaps, ncaps, take, flow, status);
+    k_expand_group<NT><<<nblocks, NT, sm, st>>>(P, kp, lv, level, iter, group, lab, phiA, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
-                                int group, float4 *lab, float *phiA, Counters *ctr, int threads, cudaStream_t st) {
+                                int group, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st) {
     const int s = lv.s;
     const int nx = (P.W + s - 1) / s, ny = (P.H + s - 1) / s;
     const int gi = group & 3, gj = group >> 2;
@@ -996,10 +1075,10 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     if (cx * cy == 0) return cudaSuccess;
     const int rw = std::min(P.W, 3 * s), rh = std::min(P.H, 3 * s);
     const size_t sm = std::max(unary_bytes_host(kp, P.H, P.W, rw, rh), cut_smem_bytes(rw * rh));
-    cudaError_t e = set_smem((const void *)k_expand_group, sm);
-    if (e != cudaSuccess) return e;
-    k_expand_group<<<cx * cy, threads, sm, st>>>(P, kp, lv, level, iter, group, lab, phiA, ctr);
-    return cudaGetLastError();
+    const int nt = threads_for_nodes(rw * rh);
+    if (nt == 256) return expand_nt<256>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
+    if (nt == 512) return expand_nt<512>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
+    return expand_nt<1024>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
 }
 
 int energy_partials(int H, int W) { return std::min(1024, (H * W + 255) / 256); }

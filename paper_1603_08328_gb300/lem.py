@@ -48,7 +48,8 @@ class lem_region(C.Structure):
 
 class lem_stats(C.Structure):
     _fields_ = [("energy_q", C.c_int64), ("energy", C.c_double), ("evals", C.c_int64), ("accepted", C.c_int64),
-                ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32)]
+                ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32),
+                ("pr_rounds", C.c_int64), ("pr_global_relabels", C.c_int64), ("pr_bfs_levels", C.c_int64)]
 
 
 _lib = None
