@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "lem_internal.h"
@@ -613,6 +615,16 @@ __device__ long long block_sum_ll(long long v, long long *red) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int dir_off(int k, int w) { return dir_dx(k) + dir_dy(k) * w; }
 
+// Appends `val` to the shared queue: one atomic per group of converged lanes.
+__device__ __forceinline__ void queue_push(uint16_t *queue, int *qtail, int val) {
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(qtail, (int)g.size());
+    base = g.shfl(base, 0);
+    queue[base + g.thread_rank()] = (uint16_t)val;
+}
+
 // Exact distances to the sink in the residual graph: BFS backwards from the
 // nodes with residual sink capacity, frontier by frontier through a queue in
 // shared memory (each node enters once).  Returns whether some node with
@@ -626,7 +638,7 @@ __device__ bool global_relabel(int n, int w, const int *res, const int *v, uint1
     for (int i = tid; i < n; i += nt) {
         if (v[i] < 0) {
             hh[i] = 1;
-            queue[atomicAdd(qtail, 1)] = (uint16_t)i;
+            queue_push(queue, qtail, i);
         } else {
             hh[i] = kInf;
         }
@@ -645,7 +657,7 @@ __device__ bool global_relabel(int n, int w, const int *res, const int *v, uint1
                 // edge i -> j runs in direction k^4 from i
                 if (hh[i] == kInf && res[(k ^ 4) * n + i] > 0 &&
                     atomicCAS(&hh[i], (unsigned short)kInf, (unsigned short)(level + 1)) == kInf)
-                    queue[atomicAdd(qtail, 1)] = (uint16_t)i;
+                    queue_push(queue, qtail, i);
             }
         }
         __syncthreads();
