@@ -134,7 +134,7 @@ void free_handle(lem_handle *h) {
 
 // Uploads regions (host) and their packed offsets (K values per pixel).
 int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_t *total, int *max_w, int *max_h,
-                  int *max_n) {
+                  int *max_n, size_t *max_cut_smem = nullptr) {
     if (!regions || n < 1) return fail(h, LEM_ERR_ARG, "regions is NULL or n_regions < 1");
     std::vector<int4> rg(n);
     std::vector<int64_t> off(n);
@@ -150,6 +150,7 @@ int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_
         mw = std::max(mw, r.w);
         mh = std::max(mh, r.h);
         mn = std::max(mn, r.w * r.h);
+        if (max_cut_smem) *max_cut_smem = std::max(*max_cut_smem, lem::cut_smem_bytes(r.w, r.h));
     }
     if ((size_t)n > h->cap_regions) {
         cudaFree(h->d_regions);
@@ -351,9 +352,11 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
     if (!tcaps || !ncaps || !take_alpha || !flow || !status) return fail(h, LEM_ERR_ARG, "NULL pointer");
     int64_t total;
     int mw, mh, mn, rc;
-    if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
+    size_t smem = 0;
+    if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn, &smem)) != LEM_OK) return rc;
     if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
-    LEM_CUDA(h, lem::launch_mincut_batch(kparams(h), h->d_regions, h->d_offsets, n_regions, mn, tcaps, ncaps,
+    if (smem > 227 * 1024) return fail(h, LEM_ERR_SHAPE, "region shape needs more shared memory than a CTA has");
+    LEM_CUDA(h, lem::launch_mincut_batch(kparams(h), h->d_regions, h->d_offsets, n_regions, mn, smem, tcaps, ncaps,
                                          take_alpha, flow, status, h->ctr, h->st));
     return LEM_OK;
 }

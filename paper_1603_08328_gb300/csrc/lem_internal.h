@@ -50,8 +50,8 @@ struct Counters {
 // Shared-memory bytes the region cost pipeline needs for regions up to
 // rw x rh pixels.
 size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh);
-// Shared-memory bytes of the CTA min-cut for n nodes.
-size_t cut_smem_bytes(int n);
+// Shared-memory bytes of the CTA min-cut for a w x h region.
+size_t cut_smem_bytes(int w, int h);
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
                               int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
@@ -70,7 +70,7 @@ cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const i
                                   const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *cterm,
                                   int threads, cudaStream_t st);
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
-                                int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                int max_nodes, size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
                                 int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st);
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 int group, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st);

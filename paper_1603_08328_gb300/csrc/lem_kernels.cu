@@ -313,6 +313,38 @@ __global__ void k_init_labels(int H, int W, unsigned long long seed, double dmin
 // ---------------------------------------------------------------------------
 // A3 + A4: data term of one label over one region, through M
 // ---------------------------------------------------------------------------
+// sum of count values base[0], base[stride], ... with four independent partial sums
+__device__ __forceinline__ float strided_sum(const float *base, int stride, int count) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int i = 0;
+    for (; i + 4 <= count; i += 4) {
+        a0 += base[i * stride];
+        a1 += base[(i + 1) * stride];
+        a2 += base[(i + 2) * stride];
+        a3 += base[(i + 3) * stride];
+    }
+    for (; i < count; ++i) a0 += base[i * stride];
+    return (a0 + a1) + (a2 + a3);
+}
+// the same over `count` consecutive rows of a ring of RS rows (row pitch rs) from slot s0
+__device__ __forceinline__ float ring_sum(const float *base, int rs, int RS, int s0, int count) {
+    const int c1 = min(count, RS - s0);
+    return strided_sum(base + s0 * rs, rs, c1) + strided_sum(base, rs, count - c1);
+}
+__device__ __forceinline__ int ring_next(int s, int RS) { return s + 1 == RS ? 0 : s + 1; }
+
+// Thread layout of one pipeline stage over an R x C item grid: threads form
+// rows of min(C, nt) columns; the (single) division happens once per stage.
+struct Grid2 {
+    int tc, tr, cpr, rpp;
+    __device__ Grid2(int C) {
+        cpr = min(C, (int)blockDim.x);
+        rpp = blockDim.x / cpr;
+        tc = threadIdx.x % cpr;
+        tr = threadIdx.x / cpr;
+    }
+};
+
 // phi_p(f) for p in [Rx0, Rx0+Rw) x [Ry0, Ry0+Rh); out[(py-Ry0)*pitch + px-Rx0].
 // Guided-filter aggregation (Eq. gf): mean over the windows W'_k containing p
 // of a_k . I_p + b_k, a_k = (Sigma_k+eU)^-1 (mean(I rho) - mu_k mean(rho)),
@@ -320,6 +352,11 @@ __global__ void k_init_labels(int H, int W, unsigned long long seed, double dmin
 // normalised by its pixel count.  The guide is centred on the colour at the
 // region centre (the filter is invariant to a constant shift of the guide),
 // which keeps the covariance differences small in flat areas.
+//
+// Strip pipeline: M rows enter a ring of T + 2r' rows of the four channels
+// (rho, (I - c) rho); every T rows of K (R grown by r') get vertical then
+// horizontal window sums and their a_k, b_k, which enter a second ring; every
+// T rows of R get the window means of a_k, b_k and phi.
 __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                              float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, r = kp.r, T = kp.T;
@@ -346,7 +383,14 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
     const float sh = two_sum(1.0f, -la, sl);
     const float oma = 1.0f - kp.alpha_grad;
 
+    // stage layouts (fixed for the call)
+    const Grid2 gM(Mw), gK(Kw), gR(Rw), gV(4 * Mw), gV2(4 * Kw);
+    const int nchK = (Kw + 3) >> 2, nchR = (Rw + 3) >> 2;
+    const Grid2 gH(4 * nchK), gH2(4 * nchR);
+
     int mNext = My0, kNext = Ky0;
+    int mSlot = 0;  // ring slot of row mNext in Xr
+    int kSlot = 0;  // ring slot of row kNext in ABr
     for (int p0 = Ry0; p0 < Ry0 + Rh; p0 += T) {
         const int p1 = min(Ry0 + Rh, p0 + T);
         const int kNeed = min(Ky1, p1 + r);
@@ -354,7 +398,8 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
             const int k0 = kNext, k1 = min(kNeed, k0 + T);
             const int mNeed = min(My1, k1 + r);
             if (mNext < mNeed) {
-                for (int i = tid; i < mNeed - mNext; i += nt) {
+                const int nrow = mNeed - mNext;
+                for (int i = tid; i < nrow; i += nt) {
                     const int y = mNext + i;
                     float e1, e2, e3, e4;
                     const float p = two_prod(sh, (float)Rx0, e1);
@@ -363,7 +408,7 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                     const float t2 = two_sum(t1, -lc, e4);
                     const float lo = __fadd_rn(__fadd_rn(__fsub_rn(e1, e2), __fadd_rn(e3, e4)),
                                                __fmul_rn(sl, (float)Rx0));
-                    float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
+                    const float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
                     const float fl = floorf(th);
                     float F = __fadd_rn(__fsub_rn(th, fl), lo);
                     int I = (int)fl;
@@ -374,158 +419,219 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                         F -= 1.f;
                         I += 1;
                     }
-                    const int slot = (y - My0) % RS;
+                    int slot = mSlot + i;
+                    if (slot >= RS) slot -= RS;
                     rowI[slot] = I;
                     rowF[slot] = F;
                 }
                 __syncthreads();
-                const int nitem = (mNeed - mNext) * Mw;
-                for (int it = tid; it < nitem; it += nt) {
-                    const int y = mNext + it / Mw, xc = it % Mw, x = Mx0 + xc;
-                    const int slot = (y - My0) % RS;
-                    const float4 l = P.L[(size_t)y * W + x];
-                    const float dx = (float)(x - Rx0);
-                    const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, rowF[slot]));
-                    const float gf = floorf(g);
-                    float t = g - gf;
-                    int i0 = rowI[slot] + (int)gf;
-                    if (i0 < 0) {
-                        i0 = 0;
-                        t = 0.f;
-                    } else if (i0 >= W - 1) {
-                        i0 = W - 1;
-                        t = 0.f;
+                if (gM.tr < gM.rpp) {
+                    for (int i = gM.tr; i < nrow; i += gM.rpp) {
+                        const int y = mNext + i;
+                        int slot = mSlot + i;
+                        if (slot >= RS) slot -= RS;
+                        const int Ib = rowI[slot];
+                        const float Fb = rowF[slot];
+                        const float4 *Lrow = P.L + (size_t)y * W;
+                        const float4 *Rrow = P.R + (size_t)y * W;
+                        float *o = Xr + (size_t)slot * 4 * Mw;
+                        for (int xc = gM.tc; xc < Mw; xc += gM.cpr) {
+                            const int x = Mx0 + xc;
+                            const float4 l = Lrow[x];
+                            const float dx = (float)(x - Rx0);
+                            const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, Fb));
+                            const float gf = floorf(g);
+                            float t = g - gf;
+                            int i0 = Ib + (int)gf;
+                            if (i0 < 0) {
+                                i0 = 0;
+                                t = 0.f;
+                            } else if (i0 >= W - 1) {
+                                i0 = W - 1;
+                                t = 0.f;
+                            }
+                            const int i1 = min(i0 + 1, W - 1);
+                            const float4 r0 = Rrow[i0], r1 = Rrow[i1];
+                            const float rr = fmaf(t, r1.x - r0.x, r0.x);
+                            const float rg = fmaf(t, r1.y - r0.y, r0.y);
+                            const float rb = fmaf(t, r1.z - r0.z, r0.z);
+                            const float rd = fmaf(t, r1.w - r0.w, r0.w);
+                            const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
+                            const float gd = fabsf(l.w - rd);
+                            const float rho = oma * fminf(col, kp.tau_col) + kp.alpha_grad * fminf(gd, kp.tau_grad);
+                            o[xc] = rho;
+                            o[Mw + xc] = (l.x * inv255 - cr) * rho;
+                            o[2 * Mw + xc] = (l.y * inv255 - cg) * rho;
+                            o[3 * Mw + xc] = (l.z * inv255 - cb) * rho;
+                        }
                     }
-                    const int i1 = min(i0 + 1, W - 1);
-                    const float4 r0 = P.R[(size_t)y * W + i0], r1 = P.R[(size_t)y * W + i1];
-                    const float rr = fmaf(t, r1.x - r0.x, r0.x);
-                    const float rg = fmaf(t, r1.y - r0.y, r0.y);
-                    const float rb = fmaf(t, r1.z - r0.z, r0.z);
-                    const float rd = fmaf(t, r1.w - r0.w, r0.w);
-                    const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
-                    const float gd = fabsf(l.w - rd);
-                    const float rho = oma * fminf(col, kp.tau_col) + kp.alpha_grad * fminf(gd, kp.tau_grad);
-                    float *o = Xr + (size_t)slot * 4 * Mw + xc;
-                    o[0] = rho;
-                    o[Mw] = (l.x * inv255 - cr) * rho;
-                    o[2 * Mw] = (l.y * inv255 - cg) * rho;
-                    o[3 * Mw] = (l.z * inv255 - cb) * rho;
                 }
+                mSlot += nrow;
+                if (mSlot >= RS) mSlot -= RS;
                 mNext = mNeed;
                 __syncthreads();
             }
-            // vertical window sums of the 4 channels for K rows [k0, k1), every M column
-            for (int it = tid; it < 4 * Mw; it += nt) {
-                const int col = it % Mw, ch = it / Mw;
-                const float *X = Xr + (size_t)ch * Mw + col;
-                const size_t rs = (size_t)4 * Mw;
-                float s = 0.f;
-                for (int y = max(0, k0 - r); y <= min(H - 1, k0 + r); ++y) s += X[((y - My0) % RS) * rs];
-                Vb[(size_t)ch * Mw + col] = s;
-                for (int ky = k0 + 1; ky < k1; ++ky) {
-                    const int yin = ky + r, yout = ky - r - 1;
-                    if (yin <= H - 1) s += X[((yin - My0) % RS) * rs];
-                    if (yout >= 0) s -= X[((yout - My0) % RS) * rs];
-                    Vb[(size_t)(ky - k0) * rs + (size_t)ch * Mw + col] = s;
+            // vertical window sums of the 4 channels for K rows [k0, k1): item =
+            // (channel x M column) by group of 4 consecutive output rows
+            {
+                const int ng = (k1 - k0 + 3) >> 2;
+                const int rs = 4 * Mw;
+                if (gV.tr < gV.rpp) {
+                    for (int cc = gV.tc; cc < 4 * Mw; cc += gV.cpr) {
+                        const float *X = Xr + cc;  // cc = ch * Mw + col
+                        float *V = Vb + cc;
+                        for (int grp = gV.tr; grp < ng; grp += gV.rpp) {
+                            const int ky0 = k0 + 4 * grp, ky1 = min(k1, ky0 + 4);
+                            const int ylo = max(0, ky0 - r), yhi = min(H - 1, ky0 + r);
+                            // slot of row ylo: rows mNext - RS .. mNext - 1 are in the ring
+                            int sIn = mSlot - (mNext - ylo);
+                            if (sIn < 0) sIn += RS;
+                            float sm = ring_sum(X, rs, RS, sIn, yhi - ylo + 1);
+                            V[(ky0 - k0) * rs] = sm;
+                            int sA = sIn + (yhi - ylo + 1);  // slot of row yhi + 1
+                            if (sA >= RS) sA -= RS;
+                            int sO = sIn;                    // slot of row ylo
+                            for (int ky = ky0 + 1; ky < ky1; ++ky) {
+                                if (ky + r <= H - 1) {
+                                    sm += X[sA * rs];
+                                    sA = ring_next(sA, RS);
+                                }
+                                if (ky - r - 1 >= 0) {
+                                    sm -= X[sO * rs];
+                                    sO = ring_next(sO, RS);
+                                }
+                                V[(ky - k0) * rs] = sm;
+                            }
+                        }
+                    }
                 }
             }
             __syncthreads();
-            // horizontal window sums at K columns, chunks of 16 outputs
-            {
-                const int nch = (Kw + 15) >> 4;
-                const int nitem = (k1 - k0) * 4 * nch;
-                for (int it = tid; it < nitem; it += nt) {
-                    const int chunk = it % nch, rest = it / nch, ch = rest & 3, row = rest >> 2;
-                    const float *V = Vb + (size_t)row * 4 * Mw + (size_t)ch * Mw;
-                    float *B = Bb + (size_t)row * 4 * Kw + (size_t)ch * Kw;
-                    const int kx0 = Kx0 + chunk * 16, kx1 = min(Kx1, kx0 + 16);
-                    float s = 0.f;
-                    for (int x = max(0, kx0 - r); x <= min(W - 1, kx0 + r); ++x) s += V[x - Mx0];
-                    B[kx0 - Kx0] = s;
-                    for (int kx = kx0 + 1; kx < kx1; ++kx) {
-                        const int xin = kx + r, xout = kx - r - 1;
-                        if (xin <= W - 1) s += V[xin - Mx0];
-                        if (xout >= 0) s -= V[xout - Mx0];
-                        B[kx - Kx0] = s;
+            // horizontal window sums at K columns, 4 outputs per item
+            if (gH.tr < gH.rpp) {
+                for (int cc = gH.tc; cc < 4 * nchK; cc += gH.cpr) {
+                    const int ch = cc / nchK, chunk = cc - ch * nchK;
+                    const int kx0 = Kx0 + chunk * 4, kx1 = min(Kx1, kx0 + 4);
+                    const int xlo = max(0, kx0 - r), xhi = min(W - 1, kx0 + r);
+                    for (int row = gH.tr; row < k1 - k0; row += gH.rpp) {
+                        const float *V = Vb + row * 4 * Mw + ch * Mw - Mx0;
+                        float *B = Bb + row * 4 * Kw + ch * Kw - Kx0;
+                        float sm = strided_sum(V + xlo, 1, xhi - xlo + 1);
+                        B[kx0] = sm;
+                        for (int kx = kx0 + 1; kx < kx1; ++kx) {
+                            if (kx + r <= W - 1) sm += V[kx + r];
+                            if (kx - r - 1 >= 0) sm -= V[kx - r - 1];
+                            B[kx] = sm;
+                        }
                     }
                 }
             }
             __syncthreads();
             // guided-filter coefficients a_k, b_k for K rows [k0, k1)
-            for (int it = tid; it < (k1 - k0) * Kw; it += nt) {
-                const int row = it / Kw, col = it % Kw;
-                const int ky = k0 + row, kx = Kx0 + col;
-                const float n = (float)((min(W - 1, kx + r) - max(0, kx - r) + 1) *
-                                        (min(H - 1, ky + r) - max(0, ky - r) + 1));
-                const float inv = 1.0f / n;
-                const float *B = Bb + (size_t)row * 4 * Kw + col;
-                const float mr = B[0] * inv;
-                const size_t k = (size_t)ky * W + kx;
-                const float4 g0 = P.gst[3 * k], g1 = P.gst[3 * k + 1], g2 = P.gst[3 * k + 2];
-                const float u0 = g0.x - cr, u1 = g0.y - cg, u2 = g0.z - cb;
-                const float v0 = B[Kw] * inv - u0 * mr;
-                const float v1 = B[2 * Kw] * inv - u1 * mr;
-                const float v2 = B[3 * Kw] * inv - u2 * mr;
-                const float a0 = g0.w * v0 + g1.x * v1 + g1.y * v2;
-                const float a1 = g1.x * v0 + g1.z * v1 + g1.w * v2;
-                const float a2 = g1.y * v0 + g1.w * v1 + g2.x * v2;
-                const float bk = mr - (a0 * u0 + a1 * u1 + a2 * u2);
-                float *A = ABr + (size_t)((ky - Ky0) % RS) * 4 * Kw + col;
-                A[0] = a0;
-                A[Kw] = a1;
-                A[2 * Kw] = a2;
-                A[3 * Kw] = bk;
+            if (gK.tr < gK.rpp) {
+                for (int row = gK.tr; row < k1 - k0; row += gK.rpp) {
+                    const int ky = k0 + row;
+                    const int ny = min(H - 1, ky + r) - max(0, ky - r) + 1;
+                    int slot = kSlot + row;
+                    if (slot >= RS) slot -= RS;
+                    float *A = ABr + slot * 4 * Kw;
+                    const float *B = Bb + row * 4 * Kw;
+                    const float4 *G = P.gst + 3 * ((size_t)ky * W + Kx0);
+                    for (int col = gK.tc; col < Kw; col += gK.cpr) {
+                        const int kx = Kx0 + col;
+                        const float n = (float)((min(W - 1, kx + r) - max(0, kx - r) + 1) * ny);
+                        const float inv = 1.0f / n;
+                        const float mr = B[col] * inv;
+                        const float4 g0 = G[3 * col], g1 = G[3 * col + 1], g2 = G[3 * col + 2];
+                        const float u0 = g0.x - cr, u1 = g0.y - cg, u2 = g0.z - cb;
+                        const float v0 = B[Kw + col] * inv - u0 * mr;
+                        const float v1 = B[2 * Kw + col] * inv - u1 * mr;
+                        const float v2 = B[3 * Kw + col] * inv - u2 * mr;
+                        const float a0 = g0.w * v0 + g1.x * v1 + g1.y * v2;
+                        const float a1 = g1.x * v0 + g1.z * v1 + g1.w * v2;
+                        const float a2 = g1.y * v0 + g1.w * v1 + g2.x * v2;
+                        const float bk = mr - (a0 * u0 + a1 * u1 + a2 * u2);
+                        A[col] = a0;
+                        A[Kw + col] = a1;
+                        A[2 * Kw + col] = a2;
+                        A[3 * Kw + col] = bk;
+                    }
+                }
             }
+            kSlot += k1 - k0;
+            if (kSlot >= RS) kSlot -= RS;
             kNext = k1;
             __syncthreads();
         }
         // window means of a_k, b_k at p: vertical sums over K rows, every K column
-        for (int it = tid; it < 4 * Kw; it += nt) {
-            const int col = it % Kw, ch = it / Kw;
-            const float *A = ABr + (size_t)ch * Kw + col;
-            const size_t rs = (size_t)4 * Kw;
-            float s = 0.f;
-            for (int y = max(0, p0 - r); y <= min(H - 1, p0 + r); ++y) s += A[((y - Ky0) % RS) * rs];
-            Vb[(size_t)ch * Kw + col] = s;
-            for (int py = p0 + 1; py < p1; ++py) {
-                const int yin = py + r, yout = py - r - 1;
-                if (yin <= H - 1) s += A[((yin - Ky0) % RS) * rs];
-                if (yout >= 0) s -= A[((yout - Ky0) % RS) * rs];
-                Vb[(size_t)(py - p0) * rs + (size_t)ch * Kw + col] = s;
-            }
-        }
-        __syncthreads();
         {
-            const int nch = (Rw + 15) >> 4;
-            const int nitem = (p1 - p0) * 4 * nch;
-            for (int it = tid; it < nitem; it += nt) {
-                const int chunk = it % nch, rest = it / nch, ch = rest & 3, row = rest >> 2;
-                const float *V = Vb + (size_t)row * 4 * Kw + (size_t)ch * Kw;
-                float *B = Bb + (size_t)row * 4 * Rw + (size_t)ch * Rw;
-                const int px0 = Rx0 + chunk * 16, px1 = min(Rx0 + Rw, px0 + 16);
-                float s = 0.f;
-                for (int x = max(0, px0 - r); x <= min(W - 1, px0 + r); ++x) s += V[x - Kx0];
-                B[px0 - Rx0] = s;
-                for (int px = px0 + 1; px < px1; ++px) {
-                    const int xin = px + r, xout = px - r - 1;
-                    if (xin <= W - 1) s += V[xin - Kx0];
-                    if (xout >= 0) s -= V[xout - Kx0];
-                    B[px - Rx0] = s;
+            const int ng = (p1 - p0 + 3) >> 2;
+            const int rs = 4 * Kw;
+            if (gV2.tr < gV2.rpp) {
+                for (int cc = gV2.tc; cc < 4 * Kw; cc += gV2.cpr) {
+                    const float *A = ABr + cc;
+                    float *V = Vb + cc;
+                    for (int grp = gV2.tr; grp < ng; grp += gV2.rpp) {
+                        const int py0 = p0 + 4 * grp, py1 = min(p1, py0 + 4);
+                        const int ylo = max(0, py0 - r), yhi = min(H - 1, py0 + r);
+                        int sIn = kSlot - (kNext - ylo);
+                        if (sIn < 0) sIn += RS;
+                        float sm = ring_sum(A, rs, RS, sIn, yhi - ylo + 1);
+                        V[(py0 - p0) * rs] = sm;
+                        int sA = sIn + (yhi - ylo + 1);
+                        if (sA >= RS) sA -= RS;
+                        int sO = sIn;
+                        for (int py = py0 + 1; py < py1; ++py) {
+                            if (py + r <= H - 1) {
+                                sm += A[sA * rs];
+                                sA = ring_next(sA, RS);
+                            }
+                            if (py - r - 1 >= 0) {
+                                sm -= A[sO * rs];
+                                sO = ring_next(sO, RS);
+                            }
+                            V[(py - p0) * rs] = sm;
+                        }
+                    }
                 }
             }
         }
         __syncthreads();
-        for (int it = tid; it < (p1 - p0) * Rw; it += nt) {
-            const int row = it / Rw, col = it % Rw;
-            const int py = p0 + row, px = Rx0 + col;
-            const float n = (float)((min(W - 1, px + r) - max(0, px - r) + 1) *
-                                    (min(H - 1, py + r) - max(0, py - r) + 1));
-            const float *B = Bb + (size_t)row * 4 * Rw + col;
-            const float4 l = P.L[(size_t)py * W + px];
-            const float phi = (B[0] * (l.x * inv255 - cr) + B[Rw] * (l.y * inv255 - cg) +
-                               B[2 * Rw] * (l.z * inv255 - cb) + B[3 * Rw]) /
-                              n;
-            out[(size_t)(py - Ry0) * pitch + (px - Rx0)] = phi;
+        if (gH2.tr < gH2.rpp) {
+            for (int cc = gH2.tc; cc < 4 * nchR; cc += gH2.cpr) {
+                const int ch = cc / nchR, chunk = cc - ch * nchR;
+                const int px0 = Rx0 + chunk * 4, px1 = min(Rx0 + Rw, px0 + 4);
+                const int xlo = max(0, px0 - r), xhi = min(W - 1, px0 + r);
+                for (int row = gH2.tr; row < p1 - p0; row += gH2.rpp) {
+                    const float *V = Vb + row * 4 * Kw + ch * Kw - Kx0;
+                    float *B = Bb + row * 4 * Rw + ch * Rw - Rx0;
+                    float sm = strided_sum(V + xlo, 1, xhi - xlo + 1);
+                    B[px0] = sm;
+                    for (int px = px0 + 1; px < px1; ++px) {
+                        if (px + r <= W - 1) sm += V[px + r];
+                        if (px - r - 1 >= 0) sm -= V[px - r - 1];
+                        B[px] = sm;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (gR.tr < gR.rpp) {
+            for (int row = gR.tr; row < p1 - p0; row += gR.rpp) {
+                const int py = p0 + row;
+                const int ny = min(H - 1, py + r) - max(0, py - r) + 1;
+                const float *B = Bb + row * 4 * Rw;
+                const float4 *Lrow = P.L + (size_t)py * W;
+                for (int col = gR.tc; col < Rw; col += gR.cpr) {
+                    const int px = Rx0 + col;
+                    const float n = (float)((min(W - 1, px + r) - max(0, px - r) + 1) * ny);
+                    const float4 l = Lrow[px];
+                    const float phi = (B[col] * (l.x * inv255 - cr) + B[Rw + col] * (l.y * inv255 - cg) +
+                                       B[2 * Rw + col] * (l.z * inv255 - cb) + B[3 * Rw + col]) /
+                                      n;
+                    out[(size_t)row * pitch + (p0 - Ry0) * (size_t)pitch + col] = phi;
+                }
+            }
         }
         __syncthreads();
     }
@@ -615,61 +721,131 @@ __device__ long long block_sum_ll(long long v, long long *red) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int dir_off(int k, int w) { return dir_dx(k) + dir_dy(k) * w; }
 
-// Appends `val` to the shared queue: one atomic per group of converged lanes.
-__device__ __forceinline__ void queue_push(uint16_t *queue, int *qtail, int val) {
-    namespace cg = cooperative_groups;
-    cg::coalesced_group g = cg::coalesced_threads();
-    int base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(qtail, (int)g.size());
-    base = g.shfl(base, 0);
-    queue[base + g.thread_rank()] = (uint16_t)val;
-}
+// j / d for 0 <= j, d < 2^16 by one 64-bit multiply: floor(j * ceil(2^32 / d) / 2^32)
+struct FastDiv {
+    unsigned long long m;
+    int d;
+    __device__ explicit FastDiv(int d_) : m(((1ull << 32) + (unsigned)d_ - 1) / (unsigned)d_), d(d_) {}
+    __device__ __forceinline__ int div(int j) const { return (int)(((unsigned long long)j * m) >> 32); }
+};
 
-// Exact distances to the sink in the residual graph: BFS backwards from the
-// nodes with residual sink capacity, frontier by frontier through a queue in
-// shared memory (each node enters once).  Returns whether some node with
-// excess can still reach the sink; *levels gets the BFS depth.
-__device__ bool global_relabel(int n, int w, const int *res, const int *v, uint16_t *hh, uint16_t *queue,
-                               int *qtail, int *levels) {
+// Exact distances to the sink in the residual graph, by a bit-parallel BFS
+// backwards from the nodes with residual sink capacity.  Rows of the region
+// are bit strings of WPR 32-bit words; for each direction k a bitplane marks
+// the nodes with residual capacity toward neighbour k.  One BFS level is, per
+// word, the OR over k of (plane_k AND frontier shifted by the offset of k),
+// minus the visited set.  Returns whether some node with excess can still
+// reach the sink; *levels gets the BFS depth.
+//   bits: 8 planes + 2 frontiers + visited, each h * WPR words
+__device__ bool global_relabel(int n, int w, int h, const int *res, const int *v, uint16_t *hh, uint32_t *bits,
+                               int *levels) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int h = n / w;
-    if (tid == 0) *qtail = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-        if (v[i] < 0) {
-            hh[i] = 1;
-            queue_push(queue, qtail, i);
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    const int WPR = (w + 31) >> 5, NW = h * WPR;
+    uint32_t *M = bits, *Fa = bits + 8 * NW, *Fb = Fa + NW, *VIS = Fb + NW;
+    const FastDiv fwpr(WPR);
+    // planes and seeds: one warp per (plane, row word), lane = bit
+    for (int t = warp; t < 9 * NW; t += nwarp) {
+        const int k = t / NW;  // uniform per warp
+        const int word = t - k * NW;
+        const int y = fwpr.div(word), wi = word - y * WPR;
+        const int x = wi * 32 + lane;
+        const int i = y * w + x;
+        bool pred = false;
+        if (x < w) pred = (k < 8) ? (res[k * n + i] > 0) : (v[i] < 0);
+        const uint32_t m = __ballot_sync(0xffffffffu, pred);
+        if (k < 8) {
+            if (lane == 0) M[k * NW + word] = m;
         } else {
-            hh[i] = kInf;
+            if (lane == 0) {
+                Fa[word] = m;
+                VIS[word] = m;
+            }
+            if (x < w) hh[i] = pred ? 1 : kInf;
         }
     }
     __syncthreads();
-    int head = 0, tail = *qtail, level = 1;
-    while (head < tail) {
-        for (int q = head + tid; q < tail; q += nt) {
-            const int j = queue[q];
-            const int jx = j % w, jy = j / w;
+    uint32_t *Fc = Fa, *Fn = Fb;
+    int level = 1;
+    for (;;) {
+        int any = 0;
+        for (int word = tid; word < NW; word += nt) {
+            const int y = fwpr.div(word), wi = word - y * WPR;
+            const uint32_t vis = VIS[word];
+            uint32_t cand = 0;
+            if (~vis) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int ix = jx + dir_dx(k), iy = jy + dir_dy(k);
-                if (ix < 0 || ix >= w || iy < 0 || iy >= h) continue;
-                const int i = iy * w + ix;
-                // edge i -> j runs in direction k^4 from i
-                if (hh[i] == kInf && res[(k ^ 4) * n + i] > 0 &&
-                    atomicCAS(&hh[i], (unsigned short)kInf, (unsigned short)(level + 1)) == kInf)
-                    queue_push(queue, qtail, i);
+                for (int k = 0; k < 8; ++k) {
+                    const int yy = y + dir_dy(k);
+                    if (yy < 0 || yy >= h) continue;
+                    const uint32_t *F = Fc + yy * WPR;
+                    const uint32_t f = F[wi];
+                    uint32_t sh;
+                    const int dx = dir_dx(k);
+                    if (dx > 0)
+                        sh = (f >> 1) | (wi + 1 < WPR ? F[wi + 1] << 31 : 0u);
+                    else if (dx < 0)
+                        sh = (f << 1) | (wi > 0 ? F[wi - 1] >> 31 : 0u);
+                    else
+                        sh = f;
+                    cand |= M[k * NW + word] & sh;
+                }
+                cand &= ~vis;
+            }
+            Fn[word] = cand;
+            if (cand) {
+                VIS[word] = vis | cand;
+                any = 1;
+                uint32_t c = cand;
+                const int base = y * w + wi * 32;
+                while (c) {
+                    const int b = __ffs(c) - 1;
+                    c &= c - 1;
+                    hh[base + b] = (uint16_t)(level + 1);
+                }
             }
         }
-        __syncthreads();
-        head = tail;
-        tail = *qtail;
+        if (!__syncthreads_or(any)) break;
+        uint32_t *t = Fc;
+        Fc = Fn;
+        Fn = t;
         ++level;
-        __syncthreads();
     }
     *levels += level;
     int act = 0;
     for (int i = tid; i < n; i += nt) act |= (v[i] > 0 && hh[i] != kInf);
     return __syncthreads_or(act) != 0;
+}
+
+// Terminal reduction before the max-flow: a node's excess beyond what its
+// outgoing n-links can carry can never leave it, and a node's sink capacity
+// beyond what its incoming n-links can bring is never used.  Clamping
+// v = cap_s - cap_t to [-(in + 1), out + 1] keeps the max-flow value and the
+// minimal sink side unchanged: a node with cap_s > out lies on the source side
+// of every minimum cut and one with cap_t > in on the sink side, and the slack
+// of one unit keeps these strict.  Needs res (initial capacities) and v.
+__device__ void clamp_terminals(int n, int w, int h, const int *res, int *v) {
+    const FastDiv fw(w);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int e = v[i];
+        if (e > 0) {
+            int out = 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out += res[k * n + i];
+            v[i] = min(e, out);
+        } else if (e < 0) {
+            const int iy = fw.div(i), ix = i - iy * w;
+            int in = 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
+                if (jx < 0 || jx >= w || jy < 0 || jy >= h) continue;
+                // the edge from neighbour j back to i runs in direction k^4 at j
+                in += res[(k ^ 4) * n + i + dir_off(k, w)];
+            }
+            v[i] = max(e, -in);
+        }
+    }
 }
 
 struct CutCount {
@@ -678,10 +854,10 @@ struct CutCount {
 
 // Maximum preflow.  On return (LEM_OK) hh[i] != kInf exactly for the nodes that
 // reach the sink in the residual graph: the minimal sink side of the cut.
-__device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, uint16_t *queue, int *qtail,
-                           int max_rounds, int gr_interval, CutCount &cc) {
+__device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
+                           int gr_interval, CutCount &cc) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    bool act = global_relabel(n, w, res, v, hh, queue, qtail, &cc.levels);
+    bool act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
     ++cc.relabels;
     int rounds = 0;
     while (act) {
@@ -695,29 +871,37 @@ __device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, uint16_
             if (e <= 0) continue;
             const int hu = hh[i];
             if (hu == kInf) continue;
-            int left = e;
+            // all loads first (independent), then the pushes decided in
+            // registers, then fire-and-forget atomics
+            int r[8], hn[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = res[k * n + i];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? (int)hh[i + dir_off(k, w)] : (int)kInf;
+            int left = e, mh = kInf;
+            int d[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                if (left == 0) break;
-                const int rk = res[k * n + i];
-                if (rk <= 0) continue;
-                const int j = i + dir_off(k, w);
-                if ((int)hh[j] + 1 == hu) {
-                    const int d = min(left, rk);
-                    atomicSub(&res[k * n + i], d);
-                    atomicAdd(&res[(k ^ 4) * n + j], d);
-                    atomicAdd(&v[j], d);
-                    left -= d;
+                d[k] = 0;
+                if (r[k] > 0 && hn[k] + 1 == hu && left > 0) {
+                    d[k] = min(left, r[k]);
+                    left -= d[k];
                 }
+                if (r[k] - d[k] > 0) mh = min(mh, hn[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (d[k] == 0) continue;
+                const int j = i + dir_off(k, w);
+                atomicSub(&res[k * n + i], d[k]);
+                atomicAdd(&res[(k ^ 4) * n + j], d[k]);
+                atomicAdd(&v[j], d[k]);
             }
             if (left != e) atomicSub(&v[i], e - left);
-            if (left > 0) {
-                int mh = kInf;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (res[k * n + i] > 0) mh = min(mh, (int)hh[i + dir_off(k, w)]);
-                hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
-            }
+            // excess left and no admissible edge: relabel from the heights read
+            // above (a stale read only costs extra rounds; the global relabel
+            // restores exact heights)
+            if (left > 0) hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
             mine = 1;
         }
         ++rounds;
@@ -725,7 +909,7 @@ __device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, uint16_
         // or the periodic point, hands over to an exact global relabel
         const int any = __syncthreads_or(mine);
         if (!any || rounds % gr_interval == 0) {
-            act = global_relabel(n, w, res, v, hh, queue, qtail, &cc.levels);
+            act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
             ++cc.relabels;
         }
     }
@@ -733,19 +917,19 @@ __device__ int cta_maxflow(int n, int w, int *res, int *v, uint16_t *hh, uint16_
     return LEM_OK;
 }
 
-// shared-memory layout of the CTA min-cut for n nodes
+// shared-memory layout of the CTA min-cut for a w x h region (n = w h nodes)
 struct CutSmem {
     int *res;
     int *v;
     uint16_t *hh;
-    uint16_t *queue;
+    uint32_t *bits;
 };
 __device__ __forceinline__ CutSmem cut_layout(void *base, int n) {
     CutSmem c;
     c.res = (int *)base;
     c.v = c.res + 8 * n;
     c.hh = (uint16_t *)(c.v + n);
-    c.queue = c.hh + n;
+    c.bits = (uint32_t *)(c.hh + ((n + 1) & ~1));
     return c;
 }
 
@@ -800,18 +984,15 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
                                                        int64_t *flow, int32_t *status, Counters *ctr) {
     extern __shared__ __align__(16) int smi[];
     __shared__ long long red[33];
-    __shared__ int qtail;
     const int i = blockIdx.x;
     const int4 R = regions[i];
     const int n = R.z * R.w, w = R.z, h = R.w;
     const int64_t off = offsets[i];
     CutSmem cs = cut_layout(smi, n);
-    long long capt = 0;
+    const FastDiv fw(w);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int ix = j % w, iy = j / w;
-        const int c_s = tcaps[2 * (off + j)], c_t = tcaps[2 * (off + j) + 1];
-        cs.v[j] = c_s - c_t;
-        capt += c_t;
+        const int iy = fw.div(j), ix = j - iy * w;
+        cs.v[j] = tcaps[2 * (off + j)] - tcaps[2 * (off + j) + 1];
         for (int k = 0; k < 8; ++k) {
             int c = 0;
             const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
@@ -819,9 +1000,15 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
             cs.res[k * n + j] = c;
         }
     }
+    __syncthreads();
+    clamp_terminals(n, w, h, cs.res, cs.v);
+    __syncthreads();
+    // flow into the sink = initial sink capacity - residual sink capacity at the end
+    long long capt = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) capt += max(0, -cs.v[j]);
     capt = block_sum_ll(capt, red);
     CutCount cc{0, 0, 0};
-    const int st = cta_maxflow(n, w, cs.res, cs.v, cs.hh, cs.queue, &qtail, kp.max_rounds, kp.gr_interval, cc);
+    const int st = cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
     long long rt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         take[off + j] = (st == LEM_OK && cs.hh[j] != kInf) ? 1 : 0;
@@ -845,7 +1032,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha;
     __shared__ long long red[33];
-    __shared__ int qtail;
     const int H = P.H, W = P.W, s = lv.s;
     const int nx = (W + s - 1) / s;
     const int gi = group & 3, gj = group >> 2;
@@ -856,6 +1042,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     CutSmem cs = cut_layout(smf, n);
+    const FastDiv fw(w);
     // outer perturbation sizes of this iteration, copied into Algorithm 2
     double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
     double rn = ldexp(1.0, -iter);
@@ -877,7 +1064,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
         region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
         // (region_unary ends with a barrier; its shared memory is reused below)
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const int ix = j % w, iy = j / w;
+            const int iy = fw.div(j), ix = j - iy * w;
             NodeCaps o;
             build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
             cs.v[j] = o.cap_s - o.cap_t;
@@ -885,11 +1072,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
             for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
         }
         __syncthreads();
-        const int st = cta_maxflow(n, w, cs.res, cs.v, cs.hh, cs.queue, &qtail, kp.max_rounds, kp.gr_interval, cc);
+        clamp_terminals(n, w, h, cs.res, cs.v);
+        __syncthreads();
+        const int st = cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
         if (st == LEM_OK) {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
                 if (cs.hh[j] == kInf) continue;
-                const size_t p = (size_t)(y0 + j / w) * W + x0 + j % w;
+                const int iy = fw.div(j);
+                const size_t p = (size_t)(y0 + iy) * W + x0 + (j - iy * w);
                 lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
                 ++acc;
             }
@@ -997,7 +1187,11 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 }  // namespace
 
 size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh) { return unary_bytes_host(kp, H, W, rw, rh); }
-size_t cut_smem_bytes(int n) { return (size_t)9 * n * sizeof(int) + (size_t)2 * n * sizeof(uint16_t) + 16; }
+size_t cut_smem_bytes(int w, int h) {
+    const size_t n = (size_t)w * h;
+    return 9 * n * sizeof(int) + ((n + 1) & ~(size_t)1) * sizeof(uint16_t) +
+           (size_t)11 * h * ((w + 31) / 32) * sizeof(uint32_t);
+}
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
                               int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
@@ -1059,9 +1253,9 @@ cudaError_t mincut_nt(const KParams &kp, const int4 *regions, const int64_t *off
 }
 
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
-                                int max_nodes, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                int max_nodes, size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
                                 int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st) {
-    const size_t sm = cut_smem_bytes(max_nodes);
+    const size_t sm = smem;
     const int nt = threads_for_nodes(max_nodes);
     if (nt == 256) return mincut_nt<256>(kp, regions, offsets, n_regions, sm, tcaps, ncaps, take, flow, status, ctr, st);
     if (nt == 512) return mincut_nt<512>(kp, regions, offsets, n_regions, sm, tcaps, ncaps, take, flow, status, ctr, st);
@@ -1086,7 +1280,7 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     const int cy = gj < ny ? (ny - gj + 3) / 4 : 0;
     if (cx * cy == 0) return cudaSuccess;
     const int rw = std::min(P.W, 3 * s), rh = std::min(P.H, 3 * s);
-    const size_t sm = std::max(unary_bytes_host(kp, P.H, P.W, rw, rh), cut_smem_bytes(rw * rh));
+    const size_t sm = std::max(unary_bytes_host(kp, P.H, P.W, rw, rh), cut_smem_bytes(rw, rh));
     const int nt = threads_for_nodes(rw * rh);
     if (nt == 256) return expand_nt<256>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
     if (nt == 512) return expand_nt<512>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
