@@ -221,6 +221,37 @@ int lem_energy(lem_handle *h, double *energy, int64_t *energy_q);
  * into caller device buffers; any may be NULL.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float *weights);
 
+/* Largest n_regions of lem_mincut_batch_noalloc. */
+#define LEM_NOALLOC_MAX_REGIONS 4096
+
+/* lem_mincut_batch for callers that cannot allocate device memory when they
+ * cut: code that runs inside a preallocated memory arena, a host thread that
+ * must not call cudaMalloc/cudaFree because those synchronise the device, or an
+ * embedding that forbids growing the device heap.  The paper has no
+ * counterpart; this is a deployment variant of the same min-cut.
+ *
+ * It needs no handle and allocates nothing: the scratch the batch min-cut
+ * keeps per call (region descriptors, packed offsets, work counters) is a
+ * fixed array of about 96 KiB in the library's device memory, which every GPU
+ * that loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the array and overwrites it (the counters are cleared first), so
+ * calls whose work overlaps on the GPU race: order them on one stream, or
+ * synchronise between them.
+ *   regions     : host, n_regions <= LEM_NOALLOC_MAX_REGIONS entries, each
+ *                 region at most LEM_MAX_REGION_NODES nodes; x0/y0 are ignored
+ *   tcaps/ncaps : device int32, layout of lem_pairwise_batch
+ *   take_alpha, flow, status : device outputs as in lem_mincut_batch
+ *   max_rounds, gr_interval  : as in lem_params (>= 1)
+ *   stream      : cudaStream_t (NULL: the legacy default stream)
+ * Errors: LEM_ERR_ARG (NULL pointer, n_regions < 1 or above
+ * LEM_NOALLOC_MAX_REGIONS, bad round parameters), LEM_ERR_SHAPE (an empty or
+ * too large region), LEM_ERR_CUDA; the text is in lem_last_error(NULL). */
+int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int32_t *tcaps, const int32_t *ncaps,
+                             uint8_t *take_alpha, int64_t *flow, int32_t *status, int max_rounds, int gr_interval,
+                             void *stream);
+
 /* Number of pixel-label cost evaluations in one outer iteration (sum over all
  * region visits of |R| x proposals).  Host only. */
 int64_t lem_evals_per_iteration(const lem_handle *h);

@@ -472,6 +472,38 @@ int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float
     return LEM_OK;
 }
 
+int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int32_t *tcaps, const int32_t *ncaps,
+                             uint8_t *take_alpha, int64_t *flow, int32_t *status, int max_rounds, int gr_interval,
+                             void *stream) {
+    if (!regions || !tcaps || !ncaps || !take_alpha || !flow || !status)
+        return fail(nullptr, LEM_ERR_ARG, "lem_mincut_batch_noalloc: NULL pointer");
+    if (n_regions < 1 || n_regions > LEM_NOALLOC_MAX_REGIONS)
+        return fail(nullptr, LEM_ERR_ARG,
+                    "lem_mincut_batch_noalloc: n_regions must be in [1, LEM_NOALLOC_MAX_REGIONS = " +
+                        std::to_string(LEM_NOALLOC_MAX_REGIONS) + "], got " + std::to_string(n_regions));
+    if (max_rounds < 1 || gr_interval < 1)
+        return fail(nullptr, LEM_ERR_ARG, "lem_mincut_batch_noalloc: max_rounds/gr_interval must be >= 1");
+    int max_nodes = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n_regions; ++i) {
+        const lem_region &r = regions[i];
+        if (r.w < 1 || r.h < 1 || (int64_t)r.w * r.h > LEM_MAX_REGION_NODES)
+            return fail(nullptr, LEM_ERR_SHAPE,
+                        "lem_mincut_batch_noalloc: region " + std::to_string(i) + " is empty or too large");
+        max_nodes = std::max(max_nodes, r.w * r.h);
+        smem = std::max(smem, lem::cut_smem_bytes(r.w, r.h));
+    }
+    if (smem > 227 * 1024)
+        return fail(nullptr, LEM_ERR_SHAPE, "lem_mincut_batch_noalloc: region shape needs more shared memory");
+    lem::KParams kp{};
+    kp.max_rounds = max_rounds;
+    kp.gr_interval = gr_interval;
+    cudaError_t e = lem::launch_mincut_noalloc(kp, regions, n_regions, max_nodes, smem, tcaps, ncaps, take_alpha,
+                                               flow, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lem_mincut_batch_noalloc");
+    return LEM_OK;
+}
+
 int64_t lem_evals_per_iteration(const lem_handle *h) {
     if (!h) return -1;
     int64_t tot = 0;

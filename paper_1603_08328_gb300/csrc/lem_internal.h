@@ -82,5 +82,10 @@ cudaError_t launch_labels_in(int H, int W, const float *abc, const float *cost, 
 cudaError_t launch_planes_out(int H, int W, const DevPlanes &P, float *left, float *right, float *guide,
                               float *weights, cudaStream_t st);
 int energy_partials(int H, int W);
+// Batch min-cut whose region/offset/counter scratch is a static device array
+// (no allocation); at most LEM_NOALLOC_MAX_REGIONS regions.
+cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, int n_regions, int max_nodes,
+                                  size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                  int64_t *flow, int32_t *status, cudaStream_t st);
 
 }  // namespace lem

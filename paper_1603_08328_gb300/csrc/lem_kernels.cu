@@ -1314,4 +1314,92 @@ cudaError_t launch_planes_out(int H, int W, const DevPlanes &P, float *left, flo
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Min-cut without allocation.  Some callers cannot allocate device memory at
+// the point where they cut (code running inside a preallocated memory arena,
+// a host thread that must not call cudaMalloc because it would synchronise
+// the device, or an embedding that forbids growing the device heap).  For
+// them the per-call scratch of the batch min-cut (region descriptors, their
+// packed offsets and the work counters) lives in this fixed array, which every
+// GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocRegionsOff = 0;
+constexpr size_t kNoAllocOffsetsOff = kNoAllocRegionsOff + sizeof(int4) * LEM_NOALLOC_MAX_REGIONS;
+constexpr size_t kNoAllocCountersOff = kNoAllocOffsetsOff + sizeof(int64_t) * LEM_NOALLOC_MAX_REGIONS;
+constexpr size_t kNoAllocBytes = kNoAllocCountersOff + sizeof(Counters);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// packed offsets of the regions (exclusive prefix sum of w*h), one CTA
+__global__ void k_noalloc_offsets(const int4 *regions, int n, int64_t *offsets) {
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const long long sz = i < n ? (long long)regions[i].z * regions[i].w : 0;
+        // inclusive scan of sz over the block (Hillis-Steele in shared memory)
+        __shared__ long long scan[1024];
+        scan[threadIdx.x] = sz;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const long long add = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < n) offsets[i] = carry + scan[threadIdx.x] - sz;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += scan[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// device address of g_noalloc_scratch per device, taken once per device with
+// that device current
+struct NoAllocSlot {
+    int ready;
+    unsigned char *ptr;
+};
+NoAllocSlot g_noalloc_slots[64];
+}  // namespace
+
+cudaError_t noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    NoAllocSlot &slot = g_noalloc_slots[dev];
+    if (!__atomic_load_n(&slot.ready, __ATOMIC_ACQUIRE)) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        slot.ptr = (unsigned char *)p;
+        __atomic_store_n(&slot.ready, 1, __ATOMIC_RELEASE);
+    }
+    *out = slot.ptr;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, int n_regions, int max_nodes,
+                                  size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                                  int64_t *flow, int32_t *status, cudaStream_t st) {
+    unsigned char *scr = nullptr;
+    cudaError_t e = noalloc_scratch(&scr);
+    if (e != cudaSuccess) return e;
+    int4 *d_regions = (int4 *)(scr + kNoAllocRegionsOff);
+    int64_t *d_offsets = (int64_t *)(scr + kNoAllocOffsetsOff);
+    Counters *d_ctr = (Counters *)(scr + kNoAllocCountersOff);
+    // lem_region is four ints, the layout of int4
+    e = cudaMemcpyAsync(d_regions, regions, sizeof(int4) * n_regions, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st);
+    if (e != cudaSuccess) return e;
+    k_noalloc_offsets<<<1, 1024, 0, st>>>(d_regions, n_regions, d_offsets);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_mincut_batch(kp, d_regions, d_offsets, n_regions, max_nodes, smem, tcaps, ncaps, take, flow,
+                               status, d_ctr, st);
+}
 }  // namespace lem

@@ -24,6 +24,7 @@ LEM_ERR_MAXFLOW_LIMIT = -4
 LEM_ERR_OOM = -5
 LEM_STORE_F32, LEM_STORE_F16, LEM_STORE_BF16 = 0, 1, 2
 LEM_MAX_REGION_NODES = 5625
+LEM_NOALLOC_MAX_REGIONS = 4096
 
 
 class lem_image(C.Structure):
@@ -78,6 +79,8 @@ def lib():
         L.lem_set_labels.argtypes = [H, vp, vp, C.c_int]
         L.lem_energy.argtypes = [H, P(C.c_double), P(C.c_int64)]
         L.lem_get_planes.argtypes = [H, vp, vp, vp, vp]
+        L.lem_mincut_batch_noalloc.argtypes = [P(lem_region), C.c_int, vp, vp, vp, vp, vp, C.c_int, C.c_int, vp]
+        L.lem_mincut_batch_noalloc.restype = C.c_int
         L.lem_evals_per_iteration.argtypes = [H]
         L.lem_evals_per_iteration.restype = C.c_int64
         for name in ("lem_create", "lem_destroy", "lem_unary_batch", "lem_pairwise_batch", "lem_mincut_batch",
@@ -177,6 +180,12 @@ def lem_energy(h):
 
 def lem_get_planes(h, left_ptr, right_ptr, guide_ptr, weights_ptr):
     return lib().lem_get_planes(h, left_ptr, right_ptr, guide_ptr, weights_ptr)
+
+
+def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, status_ptr, max_rounds, gr_interval,
+                             stream):
+    return lib().lem_mincut_batch_noalloc(_regions(regions), len(regions), tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr,
+                                          status_ptr, max_rounds, gr_interval, stream)
 
 
 def lem_evals_per_iteration(h) -> int:
