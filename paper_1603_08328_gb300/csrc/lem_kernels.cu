@@ -854,9 +854,14 @@ struct CutCount {
 
 // Maximum preflow.  On return (LEM_OK) hh[i] != kInf exactly for the nodes that
 // reach the sink in the residual graph: the minimal sink side of the cut.
+// Each round first compacts the active nodes (excess, finite height) into a
+// list, so warps only run the push path for nodes that have work.
+//   list: n 16-bit entries; shares storage with the relabel's bitplanes
 __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
                            int gr_interval, CutCount &cc) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_cnt;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    uint16_t *list = (uint16_t *)bits;
     bool act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
     ++cc.relabels;
     int rounds = 0;
@@ -865,12 +870,25 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
             cc.rounds += rounds;
             return LEM_ERR_MAXFLOW_LIMIT;
         }
-        int mine = 0;
-        for (int i = tid; i < n; i += nt) {
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        for (int base = 0; base < n; base += nt) {
+            const int i = base + tid;
+            const bool a = i < n && v[i] > 0 && hh[i] != kInf;
+            const uint32_t m = __ballot_sync(0xffffffffu, a);
+            if (m) {
+                int pos = 0;
+                if (lane == 0) pos = atomicAdd(&s_cnt, __popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                if (a) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+            }
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        for (int q = tid; q < cnt; q += nt) {
+            const int i = list[q];
             const int e = v[i];
-            if (e <= 0) continue;
             const int hu = hh[i];
-            if (hu == kInf) continue;
             // all loads first (independent), then the pushes decided in
             // registers, then fire-and-forget atomics
             int r[8], hn[8];
@@ -902,13 +920,12 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
             // above (a stale read only costs extra rounds; the global relabel
             // restores exact heights)
             if (left > 0) hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
-            mine = 1;
         }
         ++rounds;
-        // a round in which no thread found an active node (so nothing moved),
-        // or the periodic point, hands over to an exact global relabel
-        const int any = __syncthreads_or(mine);
-        if (!any || rounds % gr_interval == 0) {
+        __syncthreads();
+        // a round with no active node, or the periodic point, hands over to an
+        // exact global relabel (which also decides termination)
+        if (cnt == 0 || rounds % gr_interval == 0) {
             act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
             ++cc.relabels;
         }
@@ -1189,8 +1206,9 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh) { return unary_bytes_host(kp, H, W, rw, rh); }
 size_t cut_smem_bytes(int w, int h) {
     const size_t n = (size_t)w * h;
-    return 9 * n * sizeof(int) + ((n + 1) & ~(size_t)1) * sizeof(uint16_t) +
-           (size_t)11 * h * ((w + 31) / 32) * sizeof(uint32_t);
+    const size_t planes = (size_t)11 * h * ((w + 31) / 32) * sizeof(uint32_t);
+    const size_t list = ((n + 1) & ~(size_t)1) * sizeof(uint16_t);
+    return 9 * n * sizeof(int) + ((n + 1) & ~(size_t)1) * sizeof(uint16_t) + std::max(planes, list);
 }
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
