@@ -231,7 +231,7 @@ void lem_default_params(lem_params *p) {
     p->seed = 1;
     p->stream = nullptr;
     p->max_rounds = 200000;
-    p->gr_interval = 16;
+    p->gr_interval = 32;
     p->strip_rows = 16;
     p->threads = 256;
 }
