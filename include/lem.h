@@ -86,7 +86,8 @@ typedef struct {
     int max_rounds;       /* push-relabel round limit per cut                           */
     int gr_interval;      /* push-relabel rounds between global relabels                */
     int strip_rows;       /* rows per strip of the cost-aggregation pipeline            */
-    int threads;          /* threads per CTA of the expansion kernels                   */
+    int threads;          /* threads per CTA of the batch data-term/graph kernels       */
+    int use_graph;        /* 1: lem_expand_iteration replays outer iterations as a CUDA graph */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -126,6 +127,30 @@ void lem_default_params(lem_params *p);
  * Errors: LEM_ERR_ARG (null pointers, bad parameters), LEM_ERR_SHAPE,
  * LEM_ERR_OOM, LEM_ERR_CUDA.  On error *out is NULL. */
 int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out);
+
+/* A handle for n_pairs independent pairs (sizes may differ), solved together:
+ * each (level, group) launch of lem_expand_group / lem_expand_iteration runs
+ * the regions of every pair (pairs are independent, so their regions never
+ * interact).  Pair b draws its random numbers from seed + b * 0x9E3779B97F4A7C15,
+ * so pair 0 of a batch reproduces lem_create with the same parameters.  The
+ * label, cost and plane arrays of lem_get_labels, lem_set_labels and
+ * lem_get_planes hold the pairs in order, each row-major (see lem_pair_info);
+ * lem_energy sums over the pairs.  The batch entry points (lem_unary_batch,
+ * lem_pairwise_batch, lem_mincut_batch) work on pair 0.
+ * Errors as lem_create; n_pairs must be in [1, 4096]. */
+int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pairs, const lem_params *p,
+                     lem_handle **out);
+
+/* Number of pairs of a handle (-1 for NULL). */
+int lem_pair_count(const lem_handle *h);
+
+/* Height, width and first pixel index (in the concatenated per-pixel arrays)
+ * of pair `pair`.  Any output may be NULL.  Errors: LEM_ERR_ARG. */
+int lem_pair_info(const lem_handle *h, int pair, int *height, int *width, int64_t *pixel_offset);
+
+/* Quantised energy of one pair (see lem_energy).  Synchronises the stream.
+ * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_energy_pair(lem_handle *h, int pair, double *energy, int64_t *energy_q);
 
 /* Frees the handle and everything it owns.  NULL is accepted. */
 int lem_destroy(lem_handle *h);
@@ -191,9 +216,13 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
 int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *stats);
 
 /* n_iters outer iterations of Algorithm 1 (every level, all 16 groups),
- * continuing from the handle's iteration counter.  stats may be NULL (no
- * synchronisation); when given, the call synchronises and fills all fields
- * (energy after the last iteration).  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+ * continuing from the handle's iteration counter.  With params.use_graph the
+ * first call runs one iteration directly and captures one iteration (48
+ * launches and the increment of a device-side iteration index) as a CUDA
+ * graph on a private stream; later iterations replay that graph on the
+ * handle's stream.  stats may be NULL (no synchronisation); when given, the
+ * call synchronises and fills all fields (energy after the last iteration).
+ * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats);
 
 /* Current labels and cost cache.  abc: float32 H*W*3, disp: float32 H*W

@@ -15,7 +15,12 @@
 #include "lem_internal.h"
 
 struct lem_handle {
-    int H = 0, W = 0;
+    int B = 1;                          // pairs in the batch
+    std::vector<lem::PairDesc> pairs;   // host copy
+    lem::PairDesc *d_pairs = nullptr;
+    int H = 0, W = 0;                   // pair 0 (the batch entry points work on pair 0)
+    int maxH = 0, maxW = 0;
+    long long total = 0;                // pixels over all pairs
     lem_params p{};
     cudaStream_t st = nullptr;
     float4 *L = nullptr, *R = nullptr, *gst = nullptr, *wfw = nullptr, *lab = nullptr;
@@ -26,6 +31,15 @@ struct lem_handle {
     int4 *d_regions = nullptr;
     int64_t *d_offsets = nullptr;
     size_t cap_regions = 0;
+    // work items (pair, cell i, cell j) of every (level, group), concatenated
+    int4 *d_items = nullptr;
+    int item_off[3][16] = {};
+    int item_cnt[3][16] = {};
+    // one outer iteration as a CUDA graph; the iteration index lives on the device
+    int *d_iter = nullptr;
+    cudaStream_t cap_st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     int iter = 0;
     int fp64_inverses = 0;
     lem::Counters last{};  // device counters at the previous stats read
@@ -55,10 +69,24 @@ int cuda_fail(lem_handle *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-lem::DevPlanes planes(const lem_handle *h) {
+// planes of pair b (pointers offset to its pixels)
+lem::DevPlanes planes(const lem_handle *h, int b = 0) {
+    const lem::PairDesc &pd = h->pairs[b];
     lem::DevPlanes P;
-    P.H = h->H;
-    P.W = h->W;
+    P.H = pd.H;
+    P.W = pd.W;
+    P.L = h->L + pd.off;
+    P.R = h->R + pd.off;
+    P.gst = h->gst + 3 * pd.off;
+    P.wfw = h->wfw + pd.off;
+    return P;
+}
+
+// base planes of the whole batch (the expansion kernel offsets per pair)
+lem::DevPlanes planes_base(const lem_handle *h) {
+    lem::DevPlanes P;
+    P.H = h->maxH;
+    P.W = h->maxW;
     P.L = h->L;
     P.R = h->R;
     P.gst = h->gst;
@@ -129,6 +157,12 @@ void free_handle(lem_handle *h) {
     cudaFree(h->n_fp64);
     cudaFree(h->d_regions);
     cudaFree(h->d_offsets);
+    cudaFree(h->d_pairs);
+    cudaFree(h->d_items);
+    cudaFree(h->d_iter);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
     delete h;
 }
 
@@ -172,11 +206,19 @@ int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_
     return LEM_OK;
 }
 
-int run_energy(lem_handle *h, long long *eq) {
+// quantised energy of pair b, or of all pairs (b < 0)
+int run_energy(lem_handle *h, long long *eq, int b = -1) {
     lem::KParams kp = kparams(h);
-    LEM_CUDA(h, lem::launch_energy(planes(h), kp, h->lab, h->e_part, h->e_out, h->st));
-    LEM_CUDA(h, cudaMemcpyAsync(eq, h->e_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st));
-    LEM_CUDA(h, cudaStreamSynchronize(h->st));
+    long long tot = 0;
+    for (int i = 0; i < h->B; ++i) {
+        if (b >= 0 && i != b) continue;
+        long long e = 0;
+        LEM_CUDA(h, lem::launch_energy(planes(h, i), kp, h->lab + h->pairs[i].off, h->e_part, h->e_out, h->st));
+        LEM_CUDA(h, cudaMemcpyAsync(&e, h->e_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st));
+        LEM_CUDA(h, cudaStreamSynchronize(h->st));
+        tot += e;
+    }
+    *eq = tot;
     return LEM_OK;
 }
 
@@ -234,36 +276,56 @@ void lem_default_params(lem_params *p) {
     p->gr_interval = 32;
     p->strip_rows = 16;
     p->threads = 256;
+    p->use_graph = 1;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
-int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out) {
+int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pairs, const lem_params *p,
+                     lem_handle **out) {
     if (!out) return fail(nullptr, LEM_ERR_ARG, "out is NULL");
     *out = nullptr;
     int rc;
     if ((rc = check_params(p)) != LEM_OK) return rc;
-    if ((rc = check_image(left, "left")) != LEM_OK) return rc;
-    if ((rc = check_image(right, "right")) != LEM_OK) return rc;
-    if (left->height != right->height || left->width != right->width)
-        return fail(nullptr, LEM_ERR_SHAPE, "left and right images differ in size");
-    const int H = left->height, W = left->width;
-    if (W < 2 * p->gf_radius + 1 || H < 2 * p->gf_radius + 1)
-        return fail(nullptr, LEM_ERR_SHAPE, "image smaller than one regression window");
+    if (!lefts || !rights || n_pairs < 1 || n_pairs > 4096)
+        return fail(nullptr, LEM_ERR_ARG, "lefts/rights NULL or n_pairs outside [1, 4096]");
+    for (int b = 0; b < n_pairs; ++b) {
+        if ((rc = check_image(&lefts[b], "left")) != LEM_OK) return rc;
+        if ((rc = check_image(&rights[b], "right")) != LEM_OK) return rc;
+        if (lefts[b].height != rights[b].height || lefts[b].width != rights[b].width)
+            return fail(nullptr, LEM_ERR_SHAPE, "left and right images differ in size (pair " + std::to_string(b) + ")");
+        if (lefts[b].width < 2 * p->gf_radius + 1 || lefts[b].height < 2 * p->gf_radius + 1)
+            return fail(nullptr, LEM_ERR_SHAPE, "image smaller than one regression window");
+    }
     lem_handle *h = new lem_handle();
-    h->H = H;
-    h->W = W;
+    h->B = n_pairs;
     h->p = *p;
     h->st = (cudaStream_t)p->stream;
-    const size_t n = (size_t)H * W;
+    long long off = 0;
+    for (int b = 0; b < n_pairs; ++b) {
+        lem::PairDesc pd;
+        pd.H = lefts[b].height;
+        pd.W = lefts[b].width;
+        pd.off = off;
+        // pair 0 keeps the seed, so a batch of one reproduces lem_create
+        pd.seed = p->seed + 0x9E3779B97F4A7C15ull * (unsigned long long)b;
+        off += (long long)pd.H * pd.W;
+        h->pairs.push_back(pd);
+        h->maxH = std::max(h->maxH, pd.H);
+        h->maxW = std::max(h->maxW, pd.W);
+    }
+    h->total = off;
+    h->H = h->pairs[0].H;
+    h->W = h->pairs[0].W;
+    const size_t n = (size_t)h->total;
     auto bail = [&](int code) {
         g_create_err = h->err;
         free_handle(h);
         return code;
     };
-#define CREATE_CUDA(call)                                   \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
+#define CREATE_CUDA(call)                                            \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
     } while (0)
     CREATE_CUDA(cudaMalloc(&h->L, sizeof(float4) * n));
@@ -272,45 +334,101 @@ int lem_create(const lem_image *left, const lem_image *right, const lem_params *
     CREATE_CUDA(cudaMalloc(&h->wfw, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->lab, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->phiA, sizeof(float) * n));
-    CREATE_CUDA(cudaMalloc(&h->e_part, sizeof(long long) * lem::energy_partials(H, W)));
+    CREATE_CUDA(cudaMalloc(&h->e_part, sizeof(long long) * lem::energy_partials(h->maxH, h->maxW)));
     CREATE_CUDA(cudaMalloc(&h->e_out, sizeof(long long)));
     CREATE_CUDA(cudaMalloc(&h->ctr, sizeof(lem::Counters)));
     CREATE_CUDA(cudaMalloc(&h->n_fp64, sizeof(int)));
+    CREATE_CUDA(cudaMalloc(&h->d_pairs, sizeof(lem::PairDesc) * n_pairs));
+    CREATE_CUDA(cudaMalloc(&h->d_iter, sizeof(int)));
     CREATE_CUDA(cudaMemsetAsync(h->n_fp64, 0, sizeof(int), h->st));
     CREATE_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
-    // images on the device (copied from the host when needed)
-    const uint8_t *dl = left->data, *dr = right->data;
-    int64_t ls = left->stride_row, rs = right->stride_row;
-    uint8_t *tmp = nullptr;
-    if (!left->on_device || !right->on_device) {
-        CREATE_CUDA(cudaMalloc(&tmp, 2 * n * 3));
-        if (!left->on_device) {
-            CREATE_CUDA(cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H,
-                                          cudaMemcpyHostToDevice, h->st));
-            dl = tmp;
-            ls = 3 * W;
+    CREATE_CUDA(cudaMemcpyAsync(h->d_pairs, h->pairs.data(), sizeof(lem::PairDesc) * n_pairs, cudaMemcpyHostToDevice,
+                                h->st));
+    // work items of every (level, group): (pair, cell i, cell j)
+    {
+        std::vector<int4> items;
+        for (int l = 0; l < p->n_levels; ++l) {
+            const int s = p->cell[l];
+            for (int g = 0; g < 16; ++g) {
+                h->item_off[l][g] = (int)items.size();
+                const int gi = g & 3, gj = g >> 2;
+                for (int b = 0; b < n_pairs; ++b) {
+                    const int nx = (h->pairs[b].W + s - 1) / s, ny = (h->pairs[b].H + s - 1) / s;
+                    for (int cj = gj; cj < ny; cj += 4)
+                        for (int ci = gi; ci < nx; ci += 4) items.push_back(make_int4(b, ci, cj, 0));
+                }
+                h->item_cnt[l][g] = (int)items.size() - h->item_off[l][g];
+            }
         }
-        if (!right->on_device) {
-            CREATE_CUDA(cudaMemcpy2DAsync(tmp + 3 * n, 3 * W, right->data, right->stride_row, 3 * W, H,
-                                          cudaMemcpyHostToDevice, h->st));
-            dr = tmp + 3 * n;
-            rs = 3 * W;
-        }
+        CREATE_CUDA(cudaMalloc(&h->d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
+        CREATE_CUDA(cudaMemcpy(h->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     }
-    cudaError_t e = lem::launch_preprocess(dl, ls, dr, rs, H, W, (float)p->lambda, (float)p->eps_w,
-                                           (float)p->gamma, h->L, h->R, h->wfw, h->st);
-    if (e == cudaSuccess)
-        e = lem::launch_guide_stats(dl, ls, H, W, p->gf_radius, p->gf_eps, p->cond_fp64, h->gst, h->n_fp64, h->st);
-    if (e == cudaSuccess) e = lem::launch_init_labels(H, W, p->seed, p->disp_min, p->disp_max, h->lab, h->st);
-    if (e == cudaSuccess) e = lem::launch_pixel_costs(planes(h), kparams(h), h->lab, std::min(p->threads, 128), h->st);
+    // per pair: images on the device, packing, guide statistics, random labels, costs
+    for (int b = 0; b < n_pairs; ++b) {
+        const lem_image *left = &lefts[b], *right = &rights[b];
+        const lem::PairDesc &pd = h->pairs[b];
+        const int H = pd.H, W = pd.W;
+        const size_t np = (size_t)H * W;
+        const uint8_t *dl = left->data, *dr = right->data;
+        int64_t ls = left->stride_row, rs = right->stride_row;
+        uint8_t *tmp = nullptr;
+        if (!left->on_device || !right->on_device) {
+            CREATE_CUDA(cudaMalloc(&tmp, 2 * np * 3));
+            if (!left->on_device) {
+                CREATE_CUDA(cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H,
+                                              cudaMemcpyHostToDevice, h->st));
+                dl = tmp;
+                ls = 3 * W;
+            }
+            if (!right->on_device) {
+                CREATE_CUDA(cudaMemcpy2DAsync(tmp + 3 * np, 3 * W, right->data, right->stride_row, 3 * W, H,
+                                              cudaMemcpyHostToDevice, h->st));
+                dr = tmp + 3 * np;
+                rs = 3 * W;
+            }
+        }
+        lem::DevPlanes P = planes(h, b);
+        lem::KParams kp = kparams(h);
+        kp.seed = pd.seed;
+        cudaError_t e = lem::launch_preprocess(dl, ls, dr, rs, H, W, (float)p->lambda, (float)p->eps_w,
+                                               (float)p->gamma, (float4 *)P.L, (float4 *)P.R, (float4 *)P.wfw, h->st);
+        if (e == cudaSuccess)
+            e = lem::launch_guide_stats(dl, ls, H, W, p->gf_radius, p->gf_eps, p->cond_fp64, (float4 *)P.gst,
+                                        h->n_fp64, h->st);
+        if (e == cudaSuccess)
+            e = lem::launch_init_labels(H, W, pd.seed, p->disp_min, p->disp_max, h->lab + pd.off, h->st);
+        if (e == cudaSuccess) e = lem::launch_pixel_costs(P, kp, h->lab + pd.off, std::min(p->threads, 128), h->st);
+        // the temporary upload buffer must outlive the kernels that read it
+        if (tmp) {
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            cudaFree(tmp);
+        }
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "lem_create kernels"));
+    }
     int nf = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nf, h->n_fp64, sizeof(int), cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    if (tmp) cudaFree(tmp);
-    if (e != cudaSuccess) return bail(cuda_fail(h, e, "lem_create kernels"));
+    CREATE_CUDA(cudaMemcpyAsync(&nf, h->n_fp64, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CREATE_CUDA(cudaStreamSynchronize(h->st));
 #undef CREATE_CUDA
     h->fp64_inverses = nf;
     *out = h;
+    return LEM_OK;
+}
+
+int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out) {
+    if (!left || !right) {
+        if (out) *out = nullptr;
+        return fail(nullptr, LEM_ERR_ARG, "left image is NULL");
+    }
+    return lem_create_batch(left, right, 1, p, out);
+}
+
+int lem_pair_count(const lem_handle *h) { return h ? h->B : -1; }
+
+int lem_pair_info(const lem_handle *h, int pair, int *height, int *width, int64_t *pixel_offset) {
+    if (!h || pair < 0 || pair >= h->B) return fail(nullptr, LEM_ERR_ARG, "lem_pair_info: bad handle or pair");
+    if (height) *height = h->pairs[pair].H;
+    if (width) *width = h->pairs[pair].W;
+    if (pixel_offset) *pixel_offset = h->pairs[pair].off;
     return LEM_OK;
 }
 
@@ -361,13 +479,37 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
     return LEM_OK;
 }
 
-static int expand_group_impl(lem_handle *h, int iter, int level, int group) {
+// one (level, group) launch over every pair; iter < 0: read from h->d_iter
+static int expand_group_impl(lem_handle *h, int iter, int level, int group, cudaStream_t st) {
     lem::Level lv;
     lv.s = h->p.cell[level];
     lv.k_prop = h->p.k_prop[level];
     lv.k_rand = h->p.k_rand[level];
-    LEM_CUDA(h, lem::launch_expand_group(planes(h), kparams(h), lv, level, iter, group, h->lab, h->phiA, h->ctr,
-                                         h->st));
+    LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kparams(h), lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
+                                         h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
+                                         h->lab, h->phiA, h->ctr, st));
+    return LEM_OK;
+}
+
+// Captures one outer iteration (every level and group, then the increment of
+// the device iteration index) as a CUDA graph on a private stream.
+static int build_graph(lem_handle *h) {
+    if (!h->cap_st) LEM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    LEM_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+    int rc = LEM_OK;
+    for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
+        for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, -1, l, g, h->cap_st);
+    cudaError_t e = rc == LEM_OK ? lem::launch_increment(h->d_iter, h->cap_st) : cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
+    if (rc != LEM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    h->graph = graph;
+    LEM_CUDA(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
     return LEM_OK;
 }
 
@@ -375,7 +517,7 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (iter < 0 || level < 0 || level >= h->p.n_levels || group < 0 || group > 15)
         return fail(h, LEM_ERR_ARG, "iter/level/group out of range");
-    int rc = expand_group_impl(h, iter, level, group);
+    int rc = expand_group_impl(h, iter, level, group, h->st);
     if (rc != LEM_OK) return rc;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -387,10 +529,32 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (n_iters < 0) return fail(h, LEM_ERR_ARG, "n_iters < 0");
-    for (int it = 0; it < n_iters; ++it) {
+    int done = 0;
+    if (n_iters > 0 && h->p.use_graph && !h->gexec) {
+        // the first iteration runs directly (it also sets the kernels' shared
+        // memory limits), the graph is captured for the following ones
         for (int l = 0; l < h->p.n_levels; ++l)
             for (int g = 0; g < 16; ++g) {
-                int rc = expand_group_impl(h, h->iter, l, g);
+                int rc = expand_group_impl(h, h->iter, l, g, h->st);
+                if (rc != LEM_OK) return rc;
+            }
+        ++h->iter;
+        ++done;
+        int rc = build_graph(h);
+        if (rc != LEM_OK) return rc;
+    }
+    if (done < n_iters && h->gexec) {
+        // the device iteration index follows the host one
+        LEM_CUDA(h, cudaMemcpyAsync(h->d_iter, &h->iter, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        for (; done < n_iters; ++done) {
+            LEM_CUDA(h, cudaGraphLaunch(h->gexec, h->st));
+            ++h->iter;
+        }
+    }
+    for (; done < n_iters; ++done) {
+        for (int l = 0; l < h->p.n_levels; ++l)
+            for (int g = 0; g < 16; ++g) {
+                int rc = expand_group_impl(h, h->iter, l, g, h->st);
                 if (rc != LEM_OK) return rc;
             }
         ++h->iter;
@@ -406,16 +570,27 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     return LEM_OK;
 }
 
+// labels of every pair into device buffers (pairs in order, each row-major)
+static cudaError_t labels_out_all(lem_handle *h, float *abc, float *disp, float *cost) {
+    for (int b = 0; b < h->B; ++b) {
+        const lem::PairDesc &pd = h->pairs[b];
+        cudaError_t e = lem::launch_labels_out(pd.H, pd.W, h->lab + pd.off, abc ? abc + 3 * pd.off : nullptr,
+                                               disp ? disp + pd.off : nullptr, cost ? cost + pd.off : nullptr, h->st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int lem_get_labels(lem_handle *h, float *abc, float *disp, float *cost, int on_device) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
-    const size_t n = (size_t)h->H * h->W;
+    const size_t n = (size_t)h->total;
     if (on_device) {
-        LEM_CUDA(h, lem::launch_labels_out(h->H, h->W, h->lab, abc, disp, cost, h->st));
+        LEM_CUDA(h, labels_out_all(h, abc, disp, cost));
         return LEM_OK;
     }
     float *d = nullptr;
     LEM_CUDA(h, cudaMalloc(&d, sizeof(float) * n * 5));
-    cudaError_t e = lem::launch_labels_out(h->H, h->W, h->lab, d, d + 3 * n, d + 4 * n, h->st);
+    cudaError_t e = labels_out_all(h, d, d + 3 * n, d + 4 * n);
     if (e == cudaSuccess && abc) e = cudaMemcpyAsync(abc, d, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess && disp)
         e = cudaMemcpyAsync(disp, d + 3 * n, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st);
@@ -430,7 +605,7 @@ int lem_get_labels(lem_handle *h, float *abc, float *disp, float *cost, int on_d
 int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_device) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (!abc) return fail(h, LEM_ERR_ARG, "abc is NULL");
-    const size_t n = (size_t)h->H * h->W;
+    const size_t n = (size_t)h->total;
     const float *dabc = abc, *dcost = cost;
     float *tmp = nullptr;
     if (!on_device) {
@@ -445,9 +620,16 @@ int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_de
         dabc = tmp;
         dcost = cost ? tmp + 3 * n : nullptr;
     }
-    cudaError_t e = lem::launch_labels_in(h->H, h->W, dabc, dcost, h->lab, h->st);
-    if (e == cudaSuccess && !cost)
-        e = lem::launch_pixel_costs(planes(h), kparams(h), h->lab, std::min(h->p.threads, 128), h->st);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < h->B && e == cudaSuccess; ++b) {
+        const lem::PairDesc &pd = h->pairs[b];
+        e = lem::launch_labels_in(pd.H, pd.W, dabc + 3 * pd.off, dcost ? dcost + pd.off : nullptr, h->lab + pd.off,
+                                  h->st);
+        if (e == cudaSuccess && !dcost) {
+            lem::KParams kp = kparams(h);
+            e = lem::launch_pixel_costs(planes(h, b), kp, h->lab + pd.off, std::min(h->p.threads, 128), h->st);
+        }
+    }
     if (tmp) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
         cudaFree(tmp);
@@ -466,9 +648,25 @@ int lem_energy(lem_handle *h, double *energy, int64_t *energy_q) {
     return LEM_OK;
 }
 
+int lem_energy_pair(lem_handle *h, int pair, double *energy, int64_t *energy_q) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "pair out of range");
+    long long eq = 0;
+    int rc = run_energy(h, &eq, pair);
+    if (rc != LEM_OK) return rc;
+    if (energy_q) *energy_q = eq;
+    if (energy) *energy = (double)eq / h->p.quant_scale;
+    return LEM_OK;
+}
+
 int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float *weights) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
-    LEM_CUDA(h, lem::launch_planes_out(h->H, h->W, planes(h), left, right, guide, weights, h->st));
+    for (int b = 0; b < h->B; ++b) {
+        const long long o = h->pairs[b].off;
+        LEM_CUDA(h, lem::launch_planes_out(h->pairs[b].H, h->pairs[b].W, planes(h, b), left ? left + 4 * o : nullptr,
+                                           right ? right + 4 * o : nullptr, guide ? guide + 9 * o : nullptr,
+                                           weights ? weights + 4 * o : nullptr, h->st));
+    }
     return LEM_OK;
 }
 
@@ -507,17 +705,18 @@ int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int
 int64_t lem_evals_per_iteration(const lem_handle *h) {
     if (!h) return -1;
     int64_t tot = 0;
-    for (int l = 0; l < h->p.n_levels; ++l) {
-        const int s = h->p.cell[l];
-        const int nx = (h->W + s - 1) / s, ny = (h->H + s - 1) / s;
-        const int np = h->p.k_prop[l] + h->p.k_rand[l];
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                const int x0 = std::max(0, (i - 1) * s), x1 = std::min(h->W, (i + 2) * s);
-                const int y0 = std::max(0, (j - 1) * s), y1 = std::min(h->H, (j + 2) * s);
-                tot += (int64_t)(x1 - x0) * (y1 - y0) * np;
-            }
-    }
+    for (const lem::PairDesc &pd : h->pairs)
+        for (int l = 0; l < h->p.n_levels; ++l) {
+            const int s = h->p.cell[l];
+            const int nx = (pd.W + s - 1) / s, ny = (pd.H + s - 1) / s;
+            const int np = h->p.k_prop[l] + h->p.k_rand[l];
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const int x0 = std::max(0, (i - 1) * s), x1 = std::min(pd.W, (i + 2) * s);
+                    const int y0 = std::max(0, (j - 1) * s), y1 = std::min(pd.H, (j + 2) * s);
+                    tot += (int64_t)(x1 - x0) * (y1 - y0) * np;
+                }
+        }
     return tot;
 }
 

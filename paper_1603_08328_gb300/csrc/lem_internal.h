@@ -31,6 +31,14 @@ struct KParams {
     int T;              // strip rows of the aggregation pipeline
 };
 
+// One stereo pair inside a batch handle: its size, the pixel offset of its
+// planes in the concatenated arrays, and the seed of its random draws.
+struct PairDesc {
+    int H, W;
+    long long off;
+    unsigned long long seed;
+};
+
 // One grid level of Algorithm 1.
 struct Level {
     int s;              // cell size
@@ -72,8 +80,12 @@ cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const i
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
                                 int max_nodes, size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
                                 int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st);
+// All expansions of one (level, group) over every pair of the batch: items
+// lists (pair, cell i, cell j); iter < 0 reads the iteration from *iter_dev.
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
-                                int group, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st);
+                                const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
+                                int n_items, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st);
+cudaError_t launch_increment(int *x, cudaStream_t st);
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st);
 cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,

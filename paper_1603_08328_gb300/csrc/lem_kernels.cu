@@ -1042,18 +1042,31 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
 }
 
 // All expansions of one group at one level: one CTA per region, Algorithm 2.
+//   P      : base planes of all pairs (H/W unused); pair b's planes start at
+//            pixel pairs[b].off
+//   items  : one (pair, cell i, cell j) per CTA
+//   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
 template <int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
-    k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, int group, float4 *lab, float *phiA,
-                   Counters *ctr) {
+    k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
+                   const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all, Counters *ctr) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha;
     __shared__ long long red[33];
+    const int4 item = items[blockIdx.x];
+    const PairDesc pd = pairs[item.x];
+    P.H = pd.H;
+    P.W = pd.W;
+    P.L += pd.off;
+    P.R += pd.off;
+    P.gst += 3 * pd.off;
+    P.wfw += pd.off;
+    kp.seed = pd.seed;
+    float4 *lab = lab_all + pd.off;
+    float *phiA = phiA_all + pd.off;
+    if (iter < 0) iter = *iter_dev;
     const int H = P.H, W = P.W, s = lv.s;
-    const int nx = (W + s - 1) / s;
-    const int gi = group & 3, gj = group >> 2;
-    const int cx = (nx - gi + 3) / 4;
-    const int ci = gi + 4 * (blockIdx.x % cx), cj = gj + 4 * (blockIdx.x / cx);
+    const int ci = item.y, cj = item.z;
     const int x0 = max(0, (ci - 1) * s), x1 = min(W, (ci + 2) * s);
     const int y0 = max(0, (cj - 1) * s), y1 = min(H, (cj + 2) * s);
     const int w = x1 - x0, h = y1 - y0, n = w * h;
@@ -1281,28 +1294,35 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 }
 
 template <int NT>
-cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, int group,
-                      float4 *lab, float *phiA, Counters *ctr, int nblocks, size_t sm, cudaStream_t st) {
+cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, const int *iter_dev,
+                      const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA, Counters *ctr,
+                      size_t sm, cudaStream_t st) {
     cudaError_t e = set_smem((const void *)k_expand_group<NT>, sm);
     if (e != cudaSuccess) return e;
-    k_expand_group<NT><<<nblocks, NT, sm, st>>>(P, kp, lv, level, iter, group, lab, phiA, ctr);
+    k_expand_group<NT><<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
-                                int group, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st) {
+                                const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
+                                int n_items, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
     const int s = lv.s;
-    const int nx = (P.W + s - 1) / s, ny = (P.H + s - 1) / s;
-    const int gi = group & 3, gj = group >> 2;
-    const int cx = gi < nx ? (nx - gi + 3) / 4 : 0;
-    const int cy = gj < ny ? (ny - gj + 3) / 4 : 0;
-    if (cx * cy == 0) return cudaSuccess;
-    const int rw = std::min(P.W, 3 * s), rh = std::min(P.H, 3 * s);
-    const size_t sm = std::max(unary_bytes_host(kp, P.H, P.W, rw, rh), cut_smem_bytes(rw, rh));
+    const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
+    const size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
     const int nt = threads_for_nodes(rw * rh);
-    if (nt == 256) return expand_nt<256>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
-    if (nt == 512) return expand_nt<512>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
-    return expand_nt<1024>(P, kp, lv, level, iter, group, lab, phiA, ctr, cx * cy, sm, st);
+    if (nt == 256)
+        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
+    if (nt == 512)
+        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
+    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
+}
+
+__global__ void k_increment(int *x) { *x += 1; }
+
+cudaError_t launch_increment(int *x, cudaStream_t st) {
+    k_increment<<<1, 1, 0, st>>>(x);
+    return cudaGetLastError();
 }
 
 int energy_partials(int H, int W) { return std::min(1024, (H * W + 255) / 256); }

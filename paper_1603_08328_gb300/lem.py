@@ -40,6 +40,7 @@ class lem_params(C.Structure):
         ("cell", C.c_int * 3), ("k_prop", C.c_int * 3), ("k_rand", C.c_int * 3), ("quant_scale", C.c_double),
         ("store_dtype", C.c_int), ("cond_fp64", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p),
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
+        ("use_graph", C.c_int),
     ]
 
 
@@ -67,6 +68,10 @@ def lib():
         L.lem_default_params.argtypes = [P(lem_params)]
         L.lem_default_params.restype = None
         L.lem_create.argtypes = [P(lem_image), P(lem_image), P(lem_params), P(H)]
+        L.lem_create_batch.argtypes = [P(lem_image), P(lem_image), C.c_int, P(lem_params), P(H)]
+        L.lem_pair_count.argtypes = [H]
+        L.lem_pair_info.argtypes = [H, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int64)]
+        L.lem_energy_pair.argtypes = [H, C.c_int, P(C.c_double), P(C.c_int64)]
         L.lem_destroy.argtypes = [H]
         L.lem_last_error.argtypes = [H]
         L.lem_last_error.restype = C.c_char_p
@@ -83,7 +88,8 @@ def lib():
         L.lem_mincut_batch_noalloc.restype = C.c_int
         L.lem_evals_per_iteration.argtypes = [H]
         L.lem_evals_per_iteration.restype = C.c_int64
-        for name in ("lem_create", "lem_destroy", "lem_unary_batch", "lem_pairwise_batch", "lem_mincut_batch",
+        for name in ("lem_create", "lem_create_batch", "lem_pair_count", "lem_pair_info", "lem_energy_pair",
+                     "lem_destroy", "lem_unary_batch", "lem_pairwise_batch", "lem_mincut_batch",
                      "lem_expand_group", "lem_expand_iteration", "lem_get_labels", "lem_set_labels", "lem_energy",
                      "lem_get_planes"):
             getattr(L, name).restype = C.c_int
@@ -128,6 +134,33 @@ def lem_create(left: lem_image, right: lem_image, params: lem_params):
     rc = lib().lem_create(C.byref(left), C.byref(right), C.byref(params), C.byref(h))
     _check(rc, None)
     return h
+
+
+def lem_create_batch(lefts, rights, params: lem_params):
+    n = len(lefts)
+    la = (lem_image * n)(*lefts)
+    ra = (lem_image * n)(*rights)
+    h = C.c_void_p()
+    rc = lib().lem_create_batch(la, ra, n, C.byref(params), C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def lem_pair_count(h) -> int:
+    return lib().lem_pair_count(h)
+
+
+def lem_pair_info(h, pair):
+    hh, ww, off = C.c_int(), C.c_int(), C.c_int64()
+    rc = lib().lem_pair_info(h, pair, C.byref(hh), C.byref(ww), C.byref(off))
+    return rc, hh.value, ww.value, off.value
+
+
+def lem_energy_pair(h, pair):
+    e = C.c_double()
+    q = C.c_int64()
+    rc = lib().lem_energy_pair(h, pair, C.byref(e), C.byref(q))
+    return rc, e.value, q.value
 
 
 def lem_destroy(h):
@@ -203,6 +236,7 @@ class Stereo:
     CUDA uint8 tensors; batch outputs are CUDA tensors."""
 
     def __init__(self, left, right, stream=None, **params):
+        """left/right: one image each, or lists of images (a batch of pairs)."""
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -213,9 +247,17 @@ class Stereo:
         self.params = lem_default_params(**params)
         self.params.stream = C.c_void_p(stream.cuda_stream)
         self._keep = []
-        li, ri = self._image(left), self._image(right)
-        self.h = lem_create(li, ri, self.params)
+        if isinstance(left, (list, tuple)):
+            lis = [self._image(x) for x in left]
+            ris = [self._image(x) for x in right]
+            self.h = lem_create_batch(lis, ris, self.params)
+            li = lis[0]
+        else:
+            li, ri = self._image(left), self._image(right)
+            self.h = lem_create(li, ri, self.params)
         self.H, self.W = li.height, li.width
+        self.pairs = [lem_pair_info(self.h, b)[1:] for b in range(lem_pair_count(self.h))]
+        self.total = sum(hh * ww for hh, ww, _ in self.pairs)
 
     def _image(self, img):
         torch = self.torch
@@ -289,13 +331,19 @@ class Stereo:
         self.check(lem_expand_iteration(self.h, n, s))
         return s
 
-    def labels(self):
+    def labels(self, pair=None):
+        """(abc, disp, cost) of pair 0 (single pair) or of `pair`; pair='all' gives flat arrays."""
         torch = self.torch
-        abc = torch.empty(self.H, self.W, 3, dtype=torch.float32, device="cuda")
-        disp = torch.empty(self.H, self.W, dtype=torch.float32, device="cuda")
-        cost = torch.empty(self.H, self.W, dtype=torch.float32, device="cuda")
+        abc = torch.empty(self.total, 3, dtype=torch.float32, device="cuda")
+        disp = torch.empty(self.total, dtype=torch.float32, device="cuda")
+        cost = torch.empty(self.total, dtype=torch.float32, device="cuda")
         self.check(lem_get_labels(self.h, _ptr(abc), _ptr(disp), _ptr(cost), 1))
-        return abc, disp, cost
+        if pair == "all":
+            return abc, disp, cost
+        b = 0 if pair is None else pair
+        hh, ww, off = self.pairs[b]
+        n = hh * ww
+        return abc[off:off + n].view(hh, ww, 3), disp[off:off + n].view(hh, ww), cost[off:off + n].view(hh, ww)
 
     def set_labels(self, abc, cost=None):
         torch = self.torch
@@ -303,19 +351,22 @@ class Stereo:
         c = torch.as_tensor(np.ascontiguousarray(cost, np.float32)).cuda() if cost is not None else None
         self.check(lem_set_labels(self.h, _ptr(a), _ptr(c), 1))
 
-    def energy(self):
-        rc, e, q = lem_energy(self.h)
+    def energy(self, pair=None):
+        rc, e, q = lem_energy(self.h) if pair is None else lem_energy_pair(self.h, pair)
         self.check(rc)
         return e, q
 
     def planes(self):
         torch = self.torch
-        H, W = self.H, self.W
-        L = torch.empty(H, W, 4, device="cuda")
-        R = torch.empty(H, W, 4, device="cuda")
-        G = torch.empty(H, W, 9, device="cuda")
-        Wt = torch.empty(H, W, 4, device="cuda")
+        n = self.total
+        L = torch.empty(n, 4, device="cuda")
+        R = torch.empty(n, 4, device="cuda")
+        G = torch.empty(n, 9, device="cuda")
+        Wt = torch.empty(n, 4, device="cuda")
         self.check(lem_get_planes(self.h, _ptr(L), _ptr(R), _ptr(G), _ptr(Wt)))
+        if len(self.pairs) == 1:
+            H, W = self.H, self.W
+            return L.view(H, W, 4), R.view(H, W, 4), G.view(H, W, 9), Wt.view(H, W, 4)
         return L, R, G, Wt
 
     def evals_per_iteration(self):

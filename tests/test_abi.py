@@ -76,6 +76,9 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(L):
     short = L.lem_image(a.ctypes.data, 32, 40, 100, 0)
     assert lib.lem_create(C.byref(short), C.byref(short), C.byref(p), C.byref(h)) == L.LEM_ERR_SHAPE
     assert not h.value
+    im_c = L.lem_image(a.ctypes.data, 32, 40, 120, 0)
+    assert lib.lem_create_batch(C.byref(im_c), C.byref(im_c), 0, C.byref(p), C.byref(h)) == L.LEM_ERR_ARG
+    assert lib.lem_pair_count(None) == -1
     # NULL handles
     assert lib.lem_expand_iteration(None, 1, None) == L.LEM_ERR_ARG
     assert lib.lem_destroy(None) == L.LEM_OK

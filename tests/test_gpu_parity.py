@@ -255,3 +255,38 @@ def test_full_iteration_middlebury(mid):
     assert st.energy_q < q0
     st2 = g.iterate(1)
     assert st2.energy_q <= st.energy_q
+
+
+def test_batch_of_pairs_equals_separate_handles(torch_cuda):
+    """A batch handle solves its pairs exactly as separate handles would (pairs are independent;
+    pair b draws from seed + b * 0x9E3779B97F4A7C15)."""
+    from paper_1603_08328_gb300.lem import Stereo
+    from synth import make_pair
+    p0 = workload_pair("tiny_96x72", 0)
+    p1 = make_pair(5, 60, 110, 15.0, n_planes=2, n_quadrics=1)
+    params = dict(TINY_PARAMS, seed=31)
+    batch = Stereo([p0["left"], p1["left"]], [p0["right"], p1["right"]], **params)
+    st = batch.iterate(2)
+    assert st.maxflow_limit == 0
+    s0 = Stereo(p0["left"], p0["right"], **params)
+    s1 = Stereo(p1["left"], p1["right"], **dict(params, seed=(31 + 0x9E3779B97F4A7C15) % (1 << 64)))
+    s0.iterate(2)
+    s1.iterate(2)
+    for b, single in ((0, s0), (1, s1)):
+        ab, _, cb = batch.labels(b)
+        a1, _, c1 = single.labels()
+        assert (ab.cpu().numpy() == a1.cpu().numpy()).all()
+        assert (cb.cpu().numpy() == c1.cpu().numpy()).all()
+    assert batch.energy()[1] == s0.energy()[1] + s1.energy()[1]
+
+
+def test_graph_replay_equals_direct_launches(torch_cuda, tiny_pair):
+    """Outer iterations replayed as a CUDA graph give the labels of direct launches."""
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(TINY_PARAMS, seed=8)
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], use_graph=1, **params)
+    d = Stereo(tiny_pair["left"], tiny_pair["right"], use_graph=0, **params)
+    g.iterate(3)
+    d.iterate(3)
+    assert (g.labels()[0].cpu().numpy() == d.labels()[0].cpu().numpy()).all()
+    assert g.energy() == d.energy()
