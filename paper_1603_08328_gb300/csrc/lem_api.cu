@@ -23,7 +23,8 @@ struct lem_handle {
     long long total = 0;                // pixels over all pairs
     lem_params p{};
     cudaStream_t st = nullptr;
-    float4 *L = nullptr, *R = nullptr, *gst = nullptr, *wfw = nullptr, *lab = nullptr;
+    void *L = nullptr, *R = nullptr;  // packed images, lem::px_bytes(p.store_dtype) per pixel
+    float4 *gst = nullptr, *wfw = nullptr, *lab = nullptr;
     float *phiA = nullptr;
     long long *e_part = nullptr, *e_out = nullptr;
     lem::Counters *ctr = nullptr;
@@ -75,8 +76,10 @@ lem::DevPlanes planes(const lem_handle *h, int b = 0) {
     lem::DevPlanes P;
     P.H = pd.H;
     P.W = pd.W;
-    P.L = h->L + pd.off;
-    P.R = h->R + pd.off;
+    const size_t pb = lem::px_bytes(h->p.store_dtype);
+    P.L = (const char *)h->L + pd.off * pb;
+    P.R = (const char *)h->R + pd.off * pb;
+    P.fmt = h->p.store_dtype;
     P.gst = h->gst + 3 * pd.off;
     P.wfw = h->wfw + pd.off;
     return P;
@@ -89,6 +92,7 @@ lem::DevPlanes planes_base(const lem_handle *h) {
     P.W = h->maxW;
     P.L = h->L;
     P.R = h->R;
+    P.fmt = h->p.store_dtype;
     P.gst = h->gst;
     P.wfw = h->wfw;
     return P;
@@ -127,7 +131,8 @@ int check_params(const lem_params *p) {
     if (!(p->disp_max >= p->disp_min)) return fail(nullptr, LEM_ERR_ARG, "disp_max < disp_min");
     if (!(p->quant_scale > 0) || p->quant_scale > 1048576.0)
         return fail(nullptr, LEM_ERR_ARG, "quant_scale must be in (0, 2^20]");
-    if (p->store_dtype != LEM_STORE_F32) return fail(nullptr, LEM_ERR_ARG, "store_dtype: only LEM_STORE_F32 is built");
+    if (p->store_dtype != LEM_STORE_F32 && p->store_dtype != LEM_STORE_F16 && p->store_dtype != LEM_STORE_BF16)
+        return fail(nullptr, LEM_ERR_ARG, "store_dtype must be LEM_STORE_F32, LEM_STORE_F16 or LEM_STORE_BF16");
     if (p->max_rounds < 1 || p->gr_interval < 1) return fail(nullptr, LEM_ERR_ARG, "max_rounds/gr_interval must be >= 1");
     if (p->strip_rows < 1 || p->strip_rows > 64) return fail(nullptr, LEM_ERR_ARG, "strip_rows must be 1..64");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
@@ -328,8 +333,8 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
     } while (0)
-    CREATE_CUDA(cudaMalloc(&h->L, sizeof(float4) * n));
-    CREATE_CUDA(cudaMalloc(&h->R, sizeof(float4) * n));
+    CREATE_CUDA(cudaMalloc(&h->L, lem::px_bytes(p->store_dtype) * n));
+    CREATE_CUDA(cudaMalloc(&h->R, lem::px_bytes(p->store_dtype) * n));
     CREATE_CUDA(cudaMalloc(&h->gst, sizeof(float4) * 3 * n));
     CREATE_CUDA(cudaMalloc(&h->wfw, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->lab, sizeof(float4) * n));
@@ -391,7 +396,8 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
         lem::KParams kp = kparams(h);
         kp.seed = pd.seed;
         cudaError_t e = lem::launch_preprocess(dl, ls, dr, rs, H, W, (float)p->lambda, (float)p->eps_w,
-                                               (float)p->gamma, (float4 *)P.L, (float4 *)P.R, (float4 *)P.wfw, h->st);
+                                               (float)p->gamma, (void *)P.L, (void *)P.R, p->store_dtype,
+                                               (float4 *)P.wfw, h->st);
         if (e == cudaSuccess)
             e = lem::launch_guide_stats(dl, ls, H, W, p->gf_radius, p->gf_eps, p->cond_fp64, (float4 *)P.gst,
                                         h->n_fp64, h->st);

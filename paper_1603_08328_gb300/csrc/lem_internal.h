@@ -12,8 +12,9 @@ namespace lem {
 // Device views of one pair's packed planes.
 struct DevPlanes {
     int H, W;
-    const float4 *L;    // left:  (R, G, B, x-gradient of gray), 0..255 scale
-    const float4 *R;    // right: same
+    const void *L;      // left:  (R, G, B, x-gradient of gray), 0..255 scale, in format fmt
+    const void *R;      // right: same
+    int fmt;            // LEM_STORE_F32 (float4), LEM_STORE_F16 / LEM_STORE_BF16 (4 x 16 bit)
     const float4 *gst;  // 3 float4 per pixel: {mu_r, mu_g, mu_b, A00}, {A01, A02, A11, A12}, {A22, 0, 0, 0}
     const float4 *wfw;  // lambda * max(w_pq, eps) for the forward neighbours (1,0), (-1,1), (0,1), (1,1)
 };
@@ -61,9 +62,11 @@ size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh);
 // Shared-memory bytes of the CTA min-cut for a w x h region.
 size_t cut_smem_bytes(int w, int h);
 
+// bytes per packed image pixel in format fmt
+inline size_t px_bytes(int fmt) { return fmt == LEM_STORE_F32 ? 16 : 8; }
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
-                              int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
-                              cudaStream_t st);
+                              int W, float lambda, float eps_w, float gamma, void *Lp, void *Rp, int fmt,
+                              float4 *wfw, cudaStream_t st);
 cudaError_t launch_guide_stats(const uint8_t *left, int64_t lstride, int H, int W, int r, double eps,
                                double cond_fp64, float4 *gst, int *n_fp64, cudaStream_t st);
 cudaError_t launch_init_labels(int H, int W, unsigned long long seed, double dmin, double dmax, float4 *lab,

@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -41,6 +43,44 @@ __device__ __forceinline__ int dir_dy(int k) {
 }
 __device__ __forceinline__ float comp(const float4 &v, int d) {
     return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+}
+
+// ---------------------------------------------------------------------------
+// packed image pixels: float4, or four 16-bit floats (FP16 / BF16) converted
+// to FP32 on load; all arithmetic is FP32
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 load_px(const void *base, size_t i, int fmt) {
+    if (fmt == LEM_STORE_F32) return static_cast<const float4 *>(base)[i];
+    const uint2 u = static_cast<const uint2 *>(base)[i];
+    float2 a, b;
+    if (fmt == LEM_STORE_F16) {
+        a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    } else {
+        a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+        b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    }
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_px(void *base, size_t i, int fmt, float4 v) {
+    if (fmt == LEM_STORE_F32) {
+        static_cast<float4 *>(base)[i] = v;
+        return;
+    }
+    uint2 u;
+    if (fmt == LEM_STORE_F16) {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        u.x = *reinterpret_cast<unsigned *>(&a);
+        u.y = *reinterpret_cast<unsigned *>(&b);
+    } else {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        u.x = *reinterpret_cast<unsigned *>(&a);
+        u.y = *reinterpret_cast<unsigned *>(&b);
+    }
+    static_cast<uint2 *>(base)[i] = u;
+}
+__device__ __forceinline__ const void *px_offset(const void *base, long long off, int fmt) {
+    return static_cast<const char *>(base) + off * (fmt == LEM_STORE_F32 ? 16 : 8);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,7 +231,7 @@ __device__ float4 propose(const float4 *lab, int W, unsigned long long stream, i
 __device__ __forceinline__ int gray1000(const uint8_t *c) { return 299 * c[0] + 587 * c[1] + 114 * c[2]; }
 
 __global__ void k_preprocess(const uint8_t *left, int64_t ls, const uint8_t *right, int64_t rs, int H, int W,
-                             float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw) {
+                             float lambda, float eps_w, float gamma, void *Lp, void *Rp, int fmt, float4 *wfw) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= W || y >= H) return;
     const uint8_t *lr = left + (size_t)y * ls, *rr = right + (size_t)y * rs;
@@ -201,8 +241,8 @@ __global__ void k_preprocess(const uint8_t *left, int64_t ls, const uint8_t *rig
     const float gl = (float)(gray1000(lr + 3 * xp) - gray1000(lr + 3 * xm)) / 2000.0f;
     const float gr = (float)(gray1000(rr + 3 * xp) - gray1000(rr + 3 * xm)) / 2000.0f;
     const size_t p = (size_t)y * W + x;
-    Lp[p] = make_float4(lr[3 * x], lr[3 * x + 1], lr[3 * x + 2], gl);
-    Rp[p] = make_float4(rr[3 * x], rr[3 * x + 1], rr[3 * x + 2], gr);
+    store_px(Lp, p, fmt, make_float4(lr[3 * x], lr[3 * x + 1], lr[3 * x + 2], gl));
+    store_px(Rp, p, fmt, make_float4(rr[3 * x], rr[3 * x + 1], rr[3 * x + 2], gr));
     float w[4];
     for (int d = 0; d < 4; ++d) {
         const int qx = x + dir_dx(d), qy = y + dir_dy(d);
@@ -374,7 +414,8 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
     int *rowI = (int *)(ABr + (size_t)RS * 4 * Kw);  // [RS] integer part of the row warp offset
     float *rowF = (float *)(rowI + RS);              // [RS] fractional part
 
-    const float4 cen4 = P.L[(size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2)];
+    const int fmt = P.fmt;
+    const float4 cen4 = load_px(P.L, (size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2), fmt);
     const float inv255 = 1.0f / 255.0f;
     const float cr = cen4.x * inv255, cg = cen4.y * inv255, cb = cen4.z * inv255;
     // warp s' = s - (a s_u + b s_v + c): u' = x - d = Q(y) + (1-a)(x - Rx0) with
@@ -432,12 +473,11 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                         if (slot >= RS) slot -= RS;
                         const int Ib = rowI[slot];
                         const float Fb = rowF[slot];
-                        const float4 *Lrow = P.L + (size_t)y * W;
-                        const float4 *Rrow = P.R + (size_t)y * W;
+                        const size_t rowb = (size_t)y * W;
                         float *o = Xr + (size_t)slot * 4 * Mw;
                         for (int xc = gM.tc; xc < Mw; xc += gM.cpr) {
                             const int x = Mx0 + xc;
-                            const float4 l = Lrow[x];
+                            const float4 l = load_px(P.L, rowb + x, fmt);
                             const float dx = (float)(x - Rx0);
                             const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, Fb));
                             const float gf = floorf(g);
@@ -451,7 +491,7 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                                 t = 0.f;
                             }
                             const int i1 = min(i0 + 1, W - 1);
-                            const float4 r0 = Rrow[i0], r1 = Rrow[i1];
+                            const float4 r0 = load_px(P.R, rowb + i0, fmt), r1 = load_px(P.R, rowb + i1, fmt);
                             const float rr = fmaf(t, r1.x - r0.x, r0.x);
                             const float rg = fmaf(t, r1.y - r0.y, r0.y);
                             const float rb = fmaf(t, r1.z - r0.z, r0.z);
@@ -621,11 +661,11 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                 const int py = p0 + row;
                 const int ny = min(H - 1, py + r) - max(0, py - r) + 1;
                 const float *B = Bb + row * 4 * Rw;
-                const float4 *Lrow = P.L + (size_t)py * W;
+                const size_t rowb = (size_t)py * W;
                 for (int col = gR.tc; col < Rw; col += gR.cpr) {
                     const int px = Rx0 + col;
                     const float n = (float)((min(W - 1, px + r) - max(0, px - r) + 1) * ny);
-                    const float4 l = Lrow[px];
+                    const float4 l = load_px(P.L, rowb + px, fmt);
                     const float phi = (B[col] * (l.x * inv255 - cr) + B[Rw + col] * (l.y * inv255 - cg) +
                                        B[2 * Rw + col] * (l.z * inv255 - cb) + B[3 * Rw + col]) /
                                       n;
@@ -1057,8 +1097,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     const PairDesc pd = pairs[item.x];
     P.H = pd.H;
     P.W = pd.W;
-    P.L += pd.off;
-    P.R += pd.off;
+    P.L = px_offset(P.L, pd.off, P.fmt);
+    P.R = px_offset(P.R, pd.off, P.fmt);
     P.gst += 3 * pd.off;
     P.wfw += pd.off;
     kp.seed = pd.seed;
@@ -1179,8 +1219,8 @@ __global__ void k_labels_in(int H, int W, const float *abc, const float *cost, f
 __global__ void k_planes_out(int H, int W, DevPlanes P, float *left, float *right, float *guide, float *weights) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= H * W) return;
-    if (left) reinterpret_cast<float4 *>(left)[p] = P.L[p];
-    if (right) reinterpret_cast<float4 *>(right)[p] = P.R[p];
+    if (left) reinterpret_cast<float4 *>(left)[p] = load_px(P.L, p, P.fmt);
+    if (right) reinterpret_cast<float4 *>(right)[p] = load_px(P.R, p, P.fmt);
     if (weights) reinterpret_cast<float4 *>(weights)[p] = P.wfw[p];
     if (guide) {
         const float4 a = P.gst[3 * p], b = P.gst[3 * p + 1], c = P.gst[3 * p + 2];
@@ -1225,10 +1265,10 @@ size_t cut_smem_bytes(int w, int h) {
 }
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
-                              int W, float lambda, float eps_w, float gamma, float4 *Lp, float4 *Rp, float4 *wfw,
-                              cudaStream_t st) {
+                              int W, float lambda, float eps_w, float gamma, void *Lp, void *Rp, int fmt,
+                              float4 *wfw, cudaStream_t st) {
     dim3 grid((W + 127) / 128, H);
-    k_preprocess<<<grid, 128, 0, st>>>(left, lstride, right, rstride, H, W, lambda, eps_w, gamma, Lp, Rp, wfw);
+    k_preprocess<<<grid, 128, 0, st>>>(left, lstride, right, rstride, H, W, lambda, eps_w, gamma, Lp, Rp, fmt, wfw);
     return cudaGetLastError();
 }
 

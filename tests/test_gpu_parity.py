@@ -290,3 +290,29 @@ def test_graph_replay_equals_direct_launches(torch_cuda, tiny_pair):
     d.iterate(3)
     assert (g.labels()[0].cpu().numpy() == d.labels()[0].cpu().numpy()).all()
     assert g.energy() == d.energy()
+
+
+@pytest.mark.parametrize("store", [1, 2])   # LEM_STORE_F16, LEM_STORE_BF16
+def test_16bit_image_storage_data_term(torch_cuda, store):
+    """Images stored in 16 bits (colours exact, gradient rounded): the data term stays within
+    2e-3 of the FP64 oracle, and an outer iteration runs and lowers the energy."""
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 1)
+    params = dict(disp_max=60.0, seed=3)
+    g = Stereo(pair["left"], pair["right"], store_dtype=store, **params)
+    o = oracle.Oracle(pair["left"], pair["right"], **params)
+    L, R, _, _ = (t.cpu().numpy() for t in g.planes())
+    pl = o.planes()
+    assert (L[..., :3] == pl["L"][..., :3]).all() and (R[..., :3] == pl["R"][..., :3]).all()
+    regions = [(150, 120, 75, 75), (0, 0, 50, 50), (200, 45, 45, 45), (435, 360, 15, 15)]
+    labs = random_labels(21, len(regions) * 2, 375, 450, 60.0).reshape(len(regions), 2, 3)
+    costs = g.unary(regions, labs)
+    worst = 0.0
+    for r, lab, c in zip(regions, labs, costs):
+        for k in range(2):
+            worst = max(worst, _rel_err(c[k].cpu().numpy(), o.region_cost(*r, lab[k])).max())
+    print(f"store {store}: phi rel err max {worst:.3e}")
+    assert worst <= 2e-3, worst
+    q0 = g.energy()[1]
+    st = g.iterate(1)
+    assert st.maxflow_limit == 0 and st.energy_q < q0
