@@ -54,6 +54,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("n_threads", C.c_int),
         ("reverse_order", C.c_int),
+        ("visit", C.c_int),
     ]
 
 
@@ -61,7 +62,7 @@ class Params(C.Structure):
 PAPER_DEFAULTS = dict(gf_radius=10, gf_eps=1e-4, tau_col=10.0, tau_grad=2.0, alpha_grad=0.9,
                       lam=1.0, tau_dis=1.0, eps_w=0.01, gamma=10.0, disp_min=0.0, disp_max=60.0,
                       n_levels=3, cell=(5, 15, 25), k_prop=(1, 2, 2), k_rand=(7, 0, 0),
-                      quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0)
+                      quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0, visit=1)
 
 
 def make_params(**kw) -> Params:

@@ -65,6 +65,7 @@ typedef struct {
     uint64_t seed;
     int n_threads;        /* 0: OpenMP default                                    */
     int reverse_order;    /* visit the regions of a group in reverse order        */
+    int visit;            /* candidates drawn per region visit (1: Algorithm 2)   */
 } lo_params;
 
 typedef struct {
@@ -1187,28 +1188,35 @@ void lo_region_of(int H, int W, int s, int ci, int cj, int *R, int *C) {
 
 /* Algorithm 2 at cell (i, j): K_prop propagation proposals, then K_rand
  * perturbation proposals with the perturbation size halved after each.  The
- * perturbation sizes are this call's own copies of the outer ones. */
+ * perturbation sizes are this call's own copies of the outer ones.
+ * With visit = K > 1 (the batched schedule variant) the candidates of each run
+ * of K consecutive proposals are all drawn from the labels at the start of
+ * that run; their moves are then made one after the other, each against the
+ * labels left by the previous one.  visit = 1 is Algorithm 2 as printed. */
 static void iterative_expansion(lo_ctx *c, int iter, int level, int ci, int cj, double rd, double rn,
                                 long long *accepted, long long *evals) {
     const int H = c->H, W = c->W, s = c->p.cell[level];
     int R[4], C[4];
     lo_region_of(H, W, s, ci, cj, R, C);
-    int prop = 0;
-    for (int t = 0; t < c->p.k_prop[level]; t++, prop++) {
-        float alpha[3];
-        lo_propose(c->lab, W, lo_proposal_stream(c->p.seed, iter, level, ci, cj, prop), C[0], C[1], C[2], C[3], 0,
-                   0.0, 0.0, c->p.disp_min, c->p.disp_max, alpha);
-        *accepted += expand_move(c, R[0], R[1], R[2], R[3], alpha, NULL);
-        *evals += (long long)R[2] * R[3];
-    }
-    for (int t = 0; t < c->p.k_rand[level]; t++, prop++) {
-        float alpha[3];
-        lo_propose(c->lab, W, lo_proposal_stream(c->p.seed, iter, level, ci, cj, prop), C[0], C[1], C[2], C[3], 1,
-                   rd, rn, c->p.disp_min, c->p.disp_max, alpha);
-        *accepted += expand_move(c, R[0], R[1], R[2], R[3], alpha, NULL);
-        *evals += (long long)R[2] * R[3];
-        rd *= 0.5;
-        rn *= 0.5;
+    const int kp = c->p.k_prop[level], nprop = kp + c->p.k_rand[level];
+    const int K = c->p.visit < 1 ? 1 : (c->p.visit > 64 ? 64 : c->p.visit);
+    float alpha[64][3];
+    for (int t0 = 0; t0 < nprop; t0 += K) {
+        const int t1 = t0 + K < nprop ? t0 + K : nprop;
+        for (int t = t0; t < t1; t++) {
+            const int perturb = t >= kp;
+            lo_propose(c->lab, W, lo_proposal_stream(c->p.seed, iter, level, ci, cj, t), C[0], C[1], C[2], C[3],
+                       perturb, perturb ? rd : 0.0, perturb ? rn : 0.0, c->p.disp_min, c->p.disp_max,
+                       alpha[t - t0]);
+            if (perturb) {
+                rd *= 0.5;
+                rn *= 0.5;
+            }
+        }
+        for (int t = t0; t < t1; t++) {
+            *accepted += expand_move(c, R[0], R[1], R[2], R[3], alpha[t - t0], NULL);
+            *evals += (long long)R[2] * R[3];
+        }
     }
 }
 

@@ -479,3 +479,30 @@ def test_method_recovers_ground_truth_disparity(tiny_pair):
     v, u = np.mgrid[0:o.H, 0:o.W]
     d = lab[..., 0] * u + lab[..., 1] * v + lab[..., 2]
     assert (np.abs(d - tiny_pair["disp"]) > 1.0).mean() < 0.2
+
+
+def test_batched_visits_are_exact_moves(tiny_pair):
+    """Batched schedule (candidates of a visit drawn from the visit-start labels): every move
+    is still an exact expansion, so the energy never increases and the cost cache stays exact;
+    with visit = 1 it is Algorithm 2 as printed (bit-identical to the default)."""
+    kw = dict(TINY_PARAMS)
+    o4 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], visit=4, **kw)
+    o1 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], visit=1, **kw)
+    o0 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **kw)
+    for o in (o4, o1, o0):
+        o.init_state()
+    q_prev = o4.energy()[1]
+    for g in range(16):
+        o4.expand_group(0, 0, g)
+        q = o4.energy()[1]
+        assert q <= q_prev
+        q_prev = q
+    o1.iterate(0)
+    o0.iterate(0)
+    l1, c1 = o1.state(); l0, c0 = o0.state()
+    assert (l1 == l0).all() and (c1 == c0).all()
+    lab, cost = o4.state()
+    rng = np.random.default_rng(1)
+    for _ in range(30):
+        y, x = int(rng.integers(0, o4.H)), int(rng.integers(0, o4.W))
+        assert cost[y, x] == pytest.approx(o4.phi_def(lab[y, x], x, y), abs=1e-11)
