@@ -88,6 +88,11 @@ typedef struct {
     int strip_rows;       /* rows per strip of the cost-aggregation pipeline            */
     int threads;          /* threads per CTA of the batch data-term/graph kernels       */
     int use_graph;        /* 1: lem_expand_iteration replays outer iterations as a CUDA graph */
+    int candidates_per_visit; /* 1 (default): Algorithm 2 as printed, each proposal drawn from the
+                                 labels left by the previous move.  K in 2..8: batched schedule, the
+                                 candidates of each run of K proposals are drawn from the labels at
+                                 the start of the run (perturbation size still halved per
+                                 candidate), then cut in order, each against the updated labels. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */

@@ -113,6 +113,7 @@ lem::KParams kparams(const lem_handle *h) {
     k.max_rounds = p.max_rounds;
     k.gr_interval = p.gr_interval;
     k.T = p.strip_rows;
+    k.visit = p.candidates_per_visit;
     return k;
 }
 
@@ -135,6 +136,8 @@ int check_params(const lem_params *p) {
         return fail(nullptr, LEM_ERR_ARG, "store_dtype must be LEM_STORE_F32, LEM_STORE_F16 or LEM_STORE_BF16");
     if (p->max_rounds < 1 || p->gr_interval < 1) return fail(nullptr, LEM_ERR_ARG, "max_rounds/gr_interval must be >= 1");
     if (p->strip_rows < 1 || p->strip_rows > 64) return fail(nullptr, LEM_ERR_ARG, "strip_rows must be 1..64");
+    if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
+        return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
         return fail(nullptr, LEM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
     return LEM_OK;
@@ -282,6 +285,7 @@ void lem_default_params(lem_params *p) {
     p->strip_rows = 16;
     p->threads = 256;
     p->use_graph = 1;
+    p->candidates_per_visit = 1;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }

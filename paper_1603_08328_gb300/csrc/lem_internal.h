@@ -30,6 +30,7 @@ struct KParams {
     int max_rounds;     // push-relabel round limit
     int gr_interval;    // rounds between global relabels
     int T;              // strip rows of the aggregation pipeline
+    int visit;          // candidates drawn per region visit (1: Algorithm 2)
 };
 
 // One stereo pair inside a batch handle: its size, the pixel offset of its

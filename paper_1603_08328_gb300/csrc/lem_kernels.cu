@@ -28,6 +28,7 @@ namespace lem {
 namespace {
 
 constexpr uint16_t kInf = 0xFFFF;
+constexpr int kMaxVisit = 8;  // candidates per region visit held in shared memory
 
 // 8-neighbourhood: k < 4 are the forward neighbours (1,0), (-1,1), (0,1), (1,1)
 // (each unordered pair once); k >= 4 the opposite offsets.  Reverse of k is k^4.
@@ -1091,7 +1092,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
                    const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all, Counters *ctr) {
     extern __shared__ __align__(16) float smf[];
-    __shared__ float4 s_alpha;
+    __shared__ float4 s_alpha[kMaxVisit];
     __shared__ long long red[33];
     const int4 item = items[blockIdx.x];
     const PairDesc pd = pairs[item.x];
@@ -1119,44 +1120,54 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     long long acc = 0, hits = 0;
     CutCount cc{0, 0, 0};
     const int nprop = lv.k_prop + lv.k_rand;
-    for (int t = 0; t < nprop; ++t) {
-        const bool perturb = t >= lv.k_prop;
+    const int K = kp.visit;
+    for (int t0 = 0; t0 < nprop; t0 += K) {
+        const int t1 = min(nprop, t0 + K);
+        // the candidates of one visit, all drawn from the labels at its start
+        // (K = 1: Algorithm 2 as printed)
         if (threadIdx.x == 0) {
-            s_alpha = propose(lab, W, proposal_stream(kp.seed, iter, level, ci, cj, t), cx0, cy0, cw, chh, perturb,
-                              rd, rn, kp.disp_min, kp.disp_max);
-        }
-        if (perturb) {
-            rd *= 0.5;
-            rn *= 0.5;
-        }
-        __syncthreads();
-        const float4 al = s_alpha;
-        region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
-        // (region_unary ends with a barrier; its shared memory is reused below)
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const int iy = fw.div(j), ix = j - iy * w;
-            NodeCaps o;
-            build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
-            cs.v[j] = o.cap_s - o.cap_t;
-            for (int d = 0; d < 4; ++d) cs.res[d * n + j] = o.k[d];
-            for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
-        }
-        __syncthreads();
-        clamp_terminals(n, w, h, cs.res, cs.v);
-        __syncthreads();
-        const int st = cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
-        if (st == LEM_OK) {
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                if (cs.hh[j] == kInf) continue;
-                const int iy = fw.div(j);
-                const size_t p = (size_t)(y0 + iy) * W + x0 + (j - iy * w);
-                lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
-                ++acc;
+            for (int t = t0; t < t1; ++t) {
+                const bool perturb = t >= lv.k_prop;
+                s_alpha[t - t0] = propose(lab, W, proposal_stream(kp.seed, iter, level, ci, cj, t), cx0, cy0, cw,
+                                          chh, perturb, perturb ? rd : 0.0, perturb ? rn : 0.0, kp.disp_min,
+                                          kp.disp_max);
+                if (perturb) {
+                    rd *= 0.5;
+                    rn *= 0.5;
+                }
             }
-        } else if (threadIdx.x == 0) {
-            ++hits;
         }
         __syncthreads();
+        for (int t = t0; t < t1; ++t) {
+            const float4 al = s_alpha[t - t0];
+            region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
+            // (region_unary ends with a barrier; its shared memory is reused below)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const int iy = fw.div(j), ix = j - iy * w;
+                NodeCaps o;
+                build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
+                cs.v[j] = o.cap_s - o.cap_t;
+                for (int d = 0; d < 4; ++d) cs.res[d * n + j] = o.k[d];
+                for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
+            }
+            __syncthreads();
+            clamp_terminals(n, w, h, cs.res, cs.v);
+            __syncthreads();
+            const int st =
+                cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
+            if (st == LEM_OK) {
+                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                    if (cs.hh[j] == kInf) continue;
+                    const int iy = fw.div(j);
+                    const size_t p = (size_t)(y0 + iy) * W + x0 + (j - iy * w);
+                    lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
+                    ++acc;
+                }
+            } else if (threadIdx.x == 0) {
+                ++hits;
+            }
+            __syncthreads();
+        }
     }
     acc = block_sum_ll(acc, red);
     if (threadIdx.x == 0) {

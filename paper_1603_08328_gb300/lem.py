@@ -40,7 +40,7 @@ class lem_params(C.Structure):
         ("cell", C.c_int * 3), ("k_prop", C.c_int * 3), ("k_rand", C.c_int * 3), ("quant_scale", C.c_double),
         ("store_dtype", C.c_int), ("cond_fp64", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p),
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
-        ("use_graph", C.c_int),
+        ("use_graph", C.c_int), ("candidates_per_visit", C.c_int),
     ]
 
 

@@ -217,15 +217,17 @@ def test_energy_matches_oracle(tiny):
     assert abs(e - eo) / abs(eo) <= 1e-5
 
 
-def test_expand_groups_in_lockstep_with_oracle(tiny_pair, torch_cuda):
+@pytest.mark.parametrize("visit", [1, 4])
+def test_expand_groups_in_lockstep_with_oracle(tiny_pair, torch_cuda, visit):
     """Algorithm 1 on the tiny scene, group by group: the GPU and the oracle start from
     the same labels, draw the same candidates and take the same moves; any pixel where
     the FP32 and FP64 costs decide a near-tie differently is counted, then the oracle is
-    re-synchronised to the GPU labels.  The GPU energy never increases."""
+    re-synchronised to the GPU labels.  The GPU energy never increases.  visit = 4 runs
+    the batched schedule (candidates of a visit drawn from the visit-start labels)."""
     from paper_1603_08328_gb300.lem import Stereo
     params = dict(TINY_PARAMS, seed=23)
-    g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
-    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **params)
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], candidates_per_visit=visit, **params)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], visit=visit, **params)
     o.init_state()
     q_prev = g.energy()[1]
     flips = switched = 0
