@@ -93,6 +93,12 @@ typedef struct {
                                  candidates of each run of K proposals are drawn from the labels at
                                  the start of the run (perturbation size still halved per
                                  candidate), then cut in order, each against the updated labels. */
+    int k_cnn[3];         /* map proposals per region visit, per level (default 0: the method as
+                             published).  Proposal indices K_prop .. K_prop + k_cnn - 1 of a visit
+                             take alpha = m_r, the proposal map's label at a pixel r drawn
+                             uniformly from the centre cell (as propagation draws f_r); the
+                             perturbations follow.  Needs a map (lem_set_proposals or
+                             lem_cnn_propose) before the first expansion. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -289,6 +295,66 @@ int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int
 /* Number of pixel-label cost evaluations in one outer iteration (sum over all
  * region visits of |R| x proposals).  Host only. */
 int64_t lem_evals_per_iteration(const lem_handle *h);
+
+/* ------------------------------------------------------------------------- */
+/* Learned proposer (an extension beyond the paper: its proposals are the     */
+/* random propagation and perturbation of Sec. 3.3).                          */
+/* ------------------------------------------------------------------------- */
+
+/* Proposal map of pair `pair` (H*W labels (a, b, c), row-major, 3 floats per
+ * pixel, DEVICE pointer; copied, so the caller keeps ownership), read by the
+ * k_cnn map proposals.  Errors: LEM_ERR_ARG (NULL, pair out of range, or
+ * every k_cnn is 0: the handle keeps no map), LEM_ERR_CUDA. */
+int lem_set_proposals(lem_handle *h, int pair, const float *abc_dev);
+/* The proposal map of pair `pair` into a DEVICE array of H*W*3 floats.
+ * Errors: LEM_ERR_ARG (also when no map was set), LEM_ERR_CUDA. */
+int lem_get_proposals(lem_handle *h, int pair, float *abc_dev);
+
+/* The proposal network: 6 layers of 3x3 convolutions (zero padding), 32
+ * channels, ReLU after all but the last; input (H4, W4, 7) = left RGB, right
+ * RGB (/255) and label disparity (/disp_max) at quarter resolution (4x4 block
+ * means, H4 = ceil(H/4), W4 = ceil(W/4)); output (H4, W4, 3) = (d/disp_max, a,
+ * b).  BF16 tensor-core convolutions with FP32 accumulation; FP32 master
+ * weights trained by Adam on an L1 loss.  Runs on the stream given at creation
+ * (NULL: legacy default stream). */
+typedef struct lem_cnn lem_cnn;
+
+/* He-initialised network (normal weights from a SplitMix64 stream of `seed`,
+ * zero biases).  Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out);
+int lem_cnn_destroy(lem_cnn *net);
+const char *lem_cnn_last_error(const lem_cnn *net);
+/* Number of parameters: per layer, weights (3, 3, Cin, Cout) row-major, then the
+ * Cout biases; layers in order (Cin, Cout) = (7,32), (32,32) x4, (32,3). */
+int64_t lem_cnn_num_params(void);
+/* All parameters to / from a HOST array of lem_cnn_num_params() floats. */
+int lem_cnn_get_params(lem_cnn *net, float *host);
+int lem_cnn_set_params(lem_cnn *net, const float *host);
+/* Forward pass: x DEVICE (H4*W4*7 floats), y DEVICE (H4*W4*3 floats).
+ * Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *y);
+/* Loss and gradients over n_images inputs x (DEVICE, n*H4*W4*7) with targets
+ * t (DEVICE, n*H4*W4*3): loss = mean over images and pixels of
+ * sum_c scale_c |y_c - t_c|.  scale: HOST, 3 floats.  loss: HOST float or NULL;
+ * grads: HOST array in the lem_cnn_get_params order, or NULL.  Synchronises
+ * the stream.  Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_cnn_gradients(lem_cnn *net, const float *x, const float *t, int n_images, int H4, int W4,
+                      const float *scale, float *loss, float *grads);
+/* lem_cnn_gradients, then one Adam step (beta 0.9 / 0.999, eps 1e-8, rate lr). */
+int lem_cnn_train_step(lem_cnn *net, const float *x, const float *t, int n_images, int H4, int W4,
+                       const float *scale, float lr, float *loss);
+/* Network input of pair `pair` from its images and current labels into x
+ * (DEVICE, H4*W4*7).  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_cnn_features(lem_handle *h, int pair, float *x);
+/* Training target of pair `pair` from its current labels: 4x4 block means of
+ * (d/disp_max, a, b), the mean slopes clamped to [-1, 1], into t (DEVICE,
+ * H4*W4*3).  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_cnn_targets(lem_handle *h, int pair, float *t);
+/* Features, forward pass and bilinear upsampling of (d, a, b) to a plane per
+ * pixel (c = d - a u - b v), stored as the proposal map of every pair of `h`.
+ * Uses the handle's stream.  Errors: LEM_ERR_ARG (also when every k_cnn is 0),
+ * LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_cnn_propose(lem_cnn *net, lem_handle *h);
 
 #ifdef __cplusplus
 }

@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("n_threads", C.c_int),
         ("reverse_order", C.c_int),
         ("visit", C.c_int),
+        ("k_cnn", C.c_int * 3),
     ]
 
 
@@ -62,7 +63,8 @@ class Params(C.Structure):
 PAPER_DEFAULTS = dict(gf_radius=10, gf_eps=1e-4, tau_col=10.0, tau_grad=2.0, alpha_grad=0.9,
                       lam=1.0, tau_dis=1.0, eps_w=0.01, gamma=10.0, disp_min=0.0, disp_max=60.0,
                       n_levels=3, cell=(5, 15, 25), k_prop=(1, 2, 2), k_rand=(7, 0, 0),
-                      quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0, visit=1)
+                      quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0, visit=1,
+                      k_cnn=(0, 0, 0))
 
 
 def make_params(**kw) -> Params:
@@ -70,7 +72,7 @@ def make_params(**kw) -> Params:
     d.update(kw)
     p = Params()
     for k, v in d.items():
-        if k in ("cell", "k_prop", "k_rand"):
+        if k in ("cell", "k_prop", "k_rand", "k_cnn"):
             v = list(v) + [0] * (3 - len(v))
             setattr(p, k, (C.c_int * 3)(*v))
         else:
@@ -124,6 +126,8 @@ def lib():
         L.lo_init_label.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, fp]
         L.lo_propose.argtypes = [fp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.c_double, C.c_double, C.c_double, C.c_double, fp]
+        L.lo_propose_map.argtypes = [fp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, fp]
+        L.lo_set_proposals.argtypes = [C.c_void_p, fp]
         L.lo_init_state.argtypes = [C.c_void_p]
         L.lo_set_labels.argtypes = [C.c_void_p, fp]
         L.lo_get_state.argtypes = [C.c_void_p, fp, dp]
@@ -254,6 +258,14 @@ class Oracle:
         lab = _f32(lab)
         lib().lo_set_labels(self.h, _ptr(lab, C.c_float))
 
+    def set_proposals(self, abc):
+        """Proposal map (H, W, 3) of plane labels for the k_cnn map candidates; None clears it."""
+        if abc is None:
+            lib().lo_set_proposals(self.h, None)
+            return
+        self._prop = _f32(abc).reshape(self.H, self.W, 3)
+        lib().lo_set_proposals(self.h, _ptr(self._prop, C.c_float))
+
     def expand_group(self, it, level, group):
         ev = C.c_longlong()
         acc = lib().lo_expand_group(self.h, it, level, group, C.byref(ev))
@@ -299,6 +311,16 @@ def propose(lab, stream, cell, perturb, rd, rn, dmin, dmax):
     cx0, cy0, cw, ch = cell
     lib().lo_propose(_ptr(lab, C.c_float), W, stream, cx0, cy0, cw, ch, int(perturb), rd, rn, dmin, dmax,
                      _ptr(out, C.c_float))
+    return out
+
+
+def propose_map(prop, stream, cell):
+    """Map candidate: the proposal map's label at a pixel drawn from the centre cell."""
+    prop = _f32(prop)
+    W = prop.shape[1]
+    out = np.empty(3, np.float32)
+    cx0, cy0, cw, ch = cell
+    lib().lo_propose_map(_ptr(prop, C.c_float), W, stream, cx0, cy0, cw, ch, _ptr(out, C.c_float))
     return out
 
 

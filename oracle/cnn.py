@@ -58,29 +58,55 @@ def conv3x3_grad_weight(x, dy):
     return dw, dy.sum(axis=(0, 1))
 
 
-def forward(params, x):
-    """params: list of (w, b); returns the output and the per-layer inputs/pre-activations."""
-    acts, pre = [x], []
-    h = x
+def round_bf16(x):
+    """Round to the nearest bfloat16 value (8 significant bits, ties to even), returned as
+    float64.  bfloat16 is the upper half of an IEEE binary32: the value is first rounded to
+    binary32, then the low 16 bits of its encoding are rounded away."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    keep = u >> 16
+    rest = u & 0xFFFF
+    up = (rest > 0x8000) | ((rest == 0x8000) & ((keep & 1) == 1))
+    r = ((keep + up.astype(np.uint64)) << 16).astype(np.uint32)
+    nan = np.isnan(f)
+    out = r.view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+def _store(x, store):
+    return round_bf16(x) if store == "bf16" else x
+
+
+def forward(params, x, store=None):
+    """params: list of (w, b); returns the output and the per-layer inputs/pre-activations.
+
+    store="bf16" models a kernel that keeps the weights and every layer input in bfloat16
+    (the biases, pre-activations and output stay exact): those operands are rounded with
+    round_bf16 where they are stored, the arithmetic stays FP64."""
+    h = _store(x, store)
+    acts, pre = [h], []
     for li, (w, b) in enumerate(params):
-        z = conv3x3(h, w, b)
+        z = conv3x3(h, _store(w, store), b)
         pre.append(z)
-        h = np.maximum(z, 0.0) if li < len(params) - 1 else z
+        h = _store(np.maximum(z, 0.0), store) if li < len(params) - 1 else z
         acts.append(h)
     return h, acts, pre
 
 
-def backward(params, acts, pre, dout):
-    """Gradients of every (w, b) given d loss / d output."""
+def backward(params, acts, pre, dout, store=None):
+    """Gradients of every (w, b) given d loss / d output.  store="bf16": the gradients
+    with respect to the pre-activations are kept in bfloat16 (rounded where stored) and
+    the weights are the rounded ones, as in forward."""
     grads = [None] * len(params)
-    d = dout
+    d = _store(dout, store)
     for li in range(len(params) - 1, -1, -1):
         if li < len(params) - 1:
-            d = d * (pre[li] > 0)
+            d = _store(d * (pre[li] > 0), store)
         dw, db = conv3x3_grad_weight(acts[li], d)
         grads[li] = (dw, db)
         if li > 0:
-            d = conv3x3_grad_input(d, params[li][0])
+            d = conv3x3_grad_input(d, _store(params[li][0], store))
     return grads
 
 
@@ -90,3 +116,57 @@ def l1_loss(out, target, scale):
     n = out.shape[0] * out.shape[1]
     loss = float((np.abs(diff) * scale).sum() / n)
     return loss, np.sign(diff) * scale / n
+
+
+def quarter_features(left, right, lab, dmax):
+    """Network input at quarter resolution: 4x4 block means (blocks clipped at the
+    image border) of the left and right RGB / 255 and of the label disparity
+    d_p = a u + b v + c, divided by dmax.  left/right (H, W, 3), lab (H, W, 3)."""
+    H, W = lab.shape[:2]
+    v, u = np.mgrid[0:H, 0:W]
+    d = lab[..., 0].astype(np.float64) * u + lab[..., 1].astype(np.float64) * v + lab[..., 2]
+    chans = np.concatenate([np.asarray(left, np.float64) / 255.0, np.asarray(right, np.float64) / 255.0,
+                            (d / dmax)[..., None]], axis=-1)
+    return _block_means(chans)
+
+
+def quarter_targets(lab, dmax):
+    """Training target: 4x4 block means of (d_p / dmax, a_p, b_p), the mean slopes
+    clamped to [-1, 1]."""
+    H, W = lab.shape[:2]
+    v, u = np.mgrid[0:H, 0:W]
+    lab = lab.astype(np.float64)
+    d = lab[..., 0] * u + lab[..., 1] * v + lab[..., 2]
+    t = _block_means(np.stack([d / dmax, lab[..., 0], lab[..., 1]], axis=-1))
+    t[..., 1:] = np.clip(t[..., 1:], -1.0, 1.0)
+    return t
+
+
+def _block_means(x):
+    H, W, C = x.shape
+    H4, W4 = (H + 3) // 4, (W + 3) // 4
+    out = np.zeros((H4, W4, C))
+    for V in range(H4):
+        for U in range(W4):
+            out[V, U] = x[4 * V:4 * V + 4, 4 * U:4 * U + 4].reshape(-1, C).mean(axis=0)
+    return out
+
+
+def upsample_planes(y, H, W, dmax):
+    """Plane label per full-resolution pixel from the quarter-resolution (d/dmax, a, b):
+    bilinear interpolation at the pixel's position in the quarter grid, whose cell U
+    covers pixels 4U .. 4U+3 with centre 4U + 1.5 (positions clamped to the grid), then
+    c = d - a u - b v."""
+    H4, W4 = y.shape[:2]
+    out = np.zeros((H, W, 3))
+    for vv in range(H):
+        fv = min(max((vv - 1.5) / 4.0, 0.0), H4 - 1.0)
+        v0 = int(fv); v1 = min(v0 + 1, H4 - 1); tv = fv - v0
+        for uu in range(W):
+            fu = min(max((uu - 1.5) / 4.0, 0.0), W4 - 1.0)
+            u0 = int(fu); u1 = min(u0 + 1, W4 - 1); tu = fu - u0
+            r = ((1 - tv) * ((1 - tu) * y[v0, u0] + tu * y[v0, u1])
+                 + tv * ((1 - tu) * y[v1, u0] + tu * y[v1, u1]))
+            d, a, b = r[0] * dmax, r[1], r[2]
+            out[vv, uu] = (a, b, d - a * uu - b * vv)
+    return out

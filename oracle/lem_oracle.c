@@ -66,6 +66,7 @@ typedef struct {
     int n_threads;        /* 0: OpenMP default                                    */
     int reverse_order;    /* visit the regions of a group in reverse order        */
     int visit;            /* candidates drawn per region visit (1: Algorithm 2)   */
+    int k_cnn[3];         /* candidates per visit cell taken from the proposal map */
 } lo_params;
 
 typedef struct {
@@ -78,6 +79,7 @@ typedef struct {
     double *wq;   /* H*W*4: max(w_pq, eps) for the 4 forward neighbours */
     float *lab;   /* H*W*3: current plane labels (a, b, c)              */
     double *cost; /* H*W: phi_p(f_p) for the current labels             */
+    float *prop;  /* H*W*3: proposal map (a, b, c) or NULL              */
 } lo_ctx;
 
 /* forward neighbours: right, down-left, down, down-right (each unordered pair of
@@ -246,7 +248,21 @@ void lo_destroy(lo_ctx *c) {
     free(c->wq);
     free(c->lab);
     free(c->cost);
+    free(c->prop);
     free(c);
+}
+
+/* Proposal map of the learned proposer: H*W*3 plane labels (a, b, c), copied;
+ * NULL clears it.  The k_cnn[level] map candidates of a visit need it. */
+void lo_set_proposals(lo_ctx *c, const float *abc) {
+    size_t n = (size_t)c->H * c->W * 3;
+    if (!abc) {
+        free(c->prop);
+        c->prop = NULL;
+        return;
+    }
+    if (!c->prop) c->prop = (float *)malloc(sizeof(float) * n);
+    memcpy(c->prop, abc, sizeof(float) * n);
 }
 
 /* Read-only views of the preprocessed planes, for the tests. */
@@ -1044,6 +1060,19 @@ static void pick_pixel(uint64_t *st, int cx0, int cy0, int cw, int ch, int *ru, 
     *rv = cy0 + k / cw;
 }
 
+/* Candidate of one map proposal: alpha = m_r, the proposal map's label at a
+ * pixel r drawn uniformly from the centre cell (as the propagation proposal
+ * draws f_r). */
+void lo_propose_map(const float *map, int W, uint64_t stream, int cx0, int cy0, int cw, int ch, float *alpha) {
+    uint64_t st = stream;
+    int ru, rv;
+    pick_pixel(&st, cx0, cy0, cw, ch, &ru, &rv);
+    const float *m = map + ((size_t)rv * W + ru) * 3;
+    alpha[0] = m[0];
+    alpha[1] = m[1];
+    alpha[2] = m[2];
+}
+
 /* Candidate alpha of one proposal (Algorithm 2).  perturb = 0: propagation,
  * alpha = f_r.  perturb = 1: the label f_r is turned into a disparity d and unit
  * normal n at r, d' = d + U[-rd, rd] (clamped to [dmin, dmax]), n' = n + rn * v
@@ -1189,6 +1218,9 @@ void lo_region_of(int H, int W, int s, int ci, int cj, int *R, int *C) {
 /* Algorithm 2 at cell (i, j): K_prop propagation proposals, then K_rand
  * perturbation proposals with the perturbation size halved after each.  The
  * perturbation sizes are this call's own copies of the outer ones.
+ * With a proposal map, k_cnn map proposals sit between the two kinds
+ * (proposal indices K_prop .. K_prop + k_cnn - 1); k_cnn = 0 is the method as
+ * published.
  * With visit = K > 1 (the batched schedule variant) the candidates of each run
  * of K consecutive proposals are all drawn from the labels at the start of
  * that run; their moves are then made one after the other, each against the
@@ -1198,16 +1230,21 @@ static void iterative_expansion(lo_ctx *c, int iter, int level, int ci, int cj, 
     const int H = c->H, W = c->W, s = c->p.cell[level];
     int R[4], C[4];
     lo_region_of(H, W, s, ci, cj, R, C);
-    const int kp = c->p.k_prop[level], nprop = kp + c->p.k_rand[level];
+    const int kp = c->p.k_prop[level], kc = c->prop ? c->p.k_cnn[level] : 0;
+    const int nprop = kp + kc + c->p.k_rand[level];
     const int K = c->p.visit < 1 ? 1 : (c->p.visit > 64 ? 64 : c->p.visit);
     float alpha[64][3];
     for (int t0 = 0; t0 < nprop; t0 += K) {
         const int t1 = t0 + K < nprop ? t0 + K : nprop;
         for (int t = t0; t < t1; t++) {
-            const int perturb = t >= kp;
-            lo_propose(c->lab, W, lo_proposal_stream(c->p.seed, iter, level, ci, cj, t), C[0], C[1], C[2], C[3],
-                       perturb, perturb ? rd : 0.0, perturb ? rn : 0.0, c->p.disp_min, c->p.disp_max,
-                       alpha[t - t0]);
+            const uint64_t stream = lo_proposal_stream(c->p.seed, iter, level, ci, cj, t);
+            if (t >= kp && t < kp + kc) {
+                lo_propose_map(c->prop, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
+                continue;
+            }
+            const int perturb = t >= kp + kc;
+            lo_propose(c->lab, W, stream, C[0], C[1], C[2], C[3], perturb, perturb ? rd : 0.0, perturb ? rn : 0.0,
+                       c->p.disp_min, c->p.disp_max, alpha[t - t0]);
             if (perturb) {
                 rd *= 0.5;
                 rn *= 0.5;

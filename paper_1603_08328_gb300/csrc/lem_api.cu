@@ -26,6 +26,8 @@ struct lem_handle {
     void *L = nullptr, *R = nullptr;  // packed images, lem::px_bytes(p.store_dtype) per pixel
     float4 *gst = nullptr, *wfw = nullptr, *lab = nullptr;
     float *phiA = nullptr;
+    float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
+    bool prop_set = false;
     long long *e_part = nullptr, *e_out = nullptr;
     lem::Counters *ctr = nullptr;
     int *n_fp64 = nullptr;
@@ -126,8 +128,10 @@ int check_params(const lem_params *p) {
         if (p->cell[l] < 1) return fail(nullptr, LEM_ERR_ARG, "cell size must be >= 1");
         if (9 * p->cell[l] * p->cell[l] > LEM_MAX_REGION_NODES)
             return fail(nullptr, LEM_ERR_ARG, "cell size too large: a 3x3-cell region exceeds LEM_MAX_REGION_NODES");
-        if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_prop[l] + p->k_rand[l] < 1)
-            return fail(nullptr, LEM_ERR_ARG, "each level needs at least one proposal");
+        if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_cnn[l] < 0 || p->k_cnn[l] > 64 ||
+            p->k_prop[l] + p->k_rand[l] < 1)
+            return fail(nullptr, LEM_ERR_ARG,
+                        "each level needs a propagation or perturbation proposal; k_cnn must be 0..64");
     }
     if (!(p->disp_max >= p->disp_min)) return fail(nullptr, LEM_ERR_ARG, "disp_max < disp_min");
     if (!(p->quant_scale > 0) || p->quant_scale > 1048576.0)
@@ -159,6 +163,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->wfw);
     cudaFree(h->lab);
     cudaFree(h->phiA);
+    cudaFree(h->prop);
     cudaFree(h->e_part);
     cudaFree(h->e_out);
     cudaFree(h->ctr);
@@ -286,6 +291,7 @@ void lem_default_params(lem_params *p) {
     p->threads = 256;
     p->use_graph = 1;
     p->candidates_per_visit = 1;
+    p->k_cnn[0] = p->k_cnn[1] = p->k_cnn[2] = 0;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
@@ -343,6 +349,8 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
     CREATE_CUDA(cudaMalloc(&h->wfw, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->lab, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->phiA, sizeof(float) * n));
+    for (int l = 0; l < p->n_levels; ++l)
+        if (p->k_cnn[l] > 0 && !h->prop) CREATE_CUDA(cudaMalloc(&h->prop, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->e_part, sizeof(long long) * lem::energy_partials(h->maxH, h->maxW)));
     CREATE_CUDA(cudaMalloc(&h->e_out, sizeof(long long)));
     CREATE_CUDA(cudaMalloc(&h->ctr, sizeof(lem::Counters)));
@@ -495,9 +503,12 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     lv.s = h->p.cell[level];
     lv.k_prop = h->p.k_prop[level];
     lv.k_rand = h->p.k_rand[level];
+    lv.k_cnn = h->p.k_cnn[level];
+    if (h->prop && !h->prop_set)
+        return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kparams(h), lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
-                                         h->lab, h->phiA, h->ctr, st));
+                                         h->lab, h->phiA, h->prop, h->ctr, st));
     return LEM_OK;
 }
 
@@ -712,6 +723,79 @@ int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int
     return LEM_OK;
 }
 
+int lem_set_proposals(lem_handle *h, int pair, const float *abc_dev) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!abc_dev || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "abc is NULL or pair out of range");
+    if (!h->prop) return fail(h, LEM_ERR_ARG, "every k_cnn is 0: the handle keeps no proposal map");
+    const lem::PairDesc &pd = h->pairs[pair];
+    LEM_CUDA(h, lem::launch_props_in(pd.H * pd.W, abc_dev, h->prop + pd.off, h->st));
+    // a batch needs every pair's map; pairs not set keep what the buffer holds
+    h->prop_set = true;
+    return LEM_OK;
+}
+
+int lem_get_proposals(lem_handle *h, int pair, float *abc_dev) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!abc_dev || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "abc is NULL or pair out of range");
+    if (!h->prop || !h->prop_set) return fail(h, LEM_ERR_ARG, "no proposal map was set");
+    const lem::PairDesc &pd = h->pairs[pair];
+    LEM_CUDA(h, lem::launch_props_out(pd.H * pd.W, h->prop + pd.off, abc_dev, h->st));
+    return LEM_OK;
+}
+
+int lem_cnn_features(lem_handle *h, int pair, float *x) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!x || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "x is NULL or pair out of range");
+    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
+    LEM_CUDA(h, lem::launch_cnn_features(planes(h, pair), h->lab + h->pairs[pair].off, (float)h->p.disp_max, x, h->st));
+    return LEM_OK;
+}
+
+int lem_cnn_targets(lem_handle *h, int pair, float *t) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!t || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "t is NULL or pair out of range");
+    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network target needs disp_max > 0");
+    const lem::PairDesc &pd = h->pairs[pair];
+    LEM_CUDA(h, lem::launch_cnn_targets(h->lab + pd.off, pd.H, pd.W, (float)h->p.disp_max, t, h->st));
+    return LEM_OK;
+}
+
+int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!net) return fail(h, LEM_ERR_ARG, "network is NULL");
+    if (!h->prop) return fail(h, LEM_ERR_ARG, "every k_cnn is 0: the handle keeps no proposal map");
+    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
+    // quarter-resolution buffers sized for the largest pair
+    const size_t n4 = (size_t)((h->maxH + 3) / 4) * ((h->maxW + 3) / 4);
+    float *buf = nullptr;
+    LEM_CUDA(h, cudaMalloc(&buf, sizeof(float) * n4 * 10));
+    float *x = buf, *y = buf + 7 * n4;
+    int rc = LEM_OK;
+    for (int b = 0; b < h->B && rc == LEM_OK; ++b) {
+        const lem::PairDesc &pd = h->pairs[b];
+        const float dmax = (float)h->p.disp_max;
+        cudaError_t e = lem::launch_cnn_features(planes(h, b), h->lab + pd.off, dmax, x, h->st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "lem_cnn_propose features");
+            break;
+        }
+        rc = lem::cnn_forward_on(net, x, (pd.H + 3) / 4, (pd.W + 3) / 4, y, h->st);
+        if (rc != LEM_OK) {
+            fail(h, rc, std::string("lem_cnn_propose forward: ") + lem::cnn_error(net));
+            break;
+        }
+        e = lem::launch_cnn_upsample(y, pd.H, pd.W, dmax, h->prop + pd.off, h->st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lem_cnn_propose upsample");
+    }
+    // the buffer is read by kernels on h->st: free it once they are done
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (rc != LEM_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(h, e, "lem_cnn_propose");
+    h->prop_set = true;
+    return LEM_OK;
+}
+
 int64_t lem_evals_per_iteration(const lem_handle *h) {
     if (!h) return -1;
     int64_t tot = 0;
@@ -719,7 +803,7 @@ int64_t lem_evals_per_iteration(const lem_handle *h) {
         for (int l = 0; l < h->p.n_levels; ++l) {
             const int s = h->p.cell[l];
             const int nx = (pd.W + s - 1) / s, ny = (pd.H + s - 1) / s;
-            const int np = h->p.k_prop[l] + h->p.k_rand[l];
+            const int np = h->p.k_prop[l] + h->p.k_rand[l] + (h->prop ? h->p.k_cnn[l] : 0);
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
                     const int x0 = std::max(0, (i - 1) * s), x1 = std::min(pd.W, (i + 2) * s);

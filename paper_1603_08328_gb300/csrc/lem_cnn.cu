@@ -1,0 +1,614 @@
+// Plane-proposal network: 6 layers of 3x3 convolutions (32 channels, ReLU
+// between layers) on (left RGB, right RGB, disparity) at quarter resolution,
+// predicting (d, a, b) per quarter-resolution pixel; bilinear upsampling turns
+// the prediction into a full-resolution map of plane labels that the
+// expansion kernel can draw candidates from.
+//
+// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
+// BF16 operands, FP32 accumulation):
+//   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = pixels, N = Cout, K = 9 Cin)
+//   input grad   dX        = the same kernel with flipped, transposed weights
+//   weight grad  dW[o][k]  = sum_p dZ[p][o] Xpatch[p][k]      (M = Cout, N = 9 Cin, K = pixels)
+// Activations are BF16, NHWC, channels padded to a multiple of 16; the weights
+// have an FP32 master copy updated by Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "lem.h"
+#include "lem_internal.h"
+
+namespace lemcnn {
+
+constexpr int kLayers = 6;
+// padded input / output channels of each layer (the real ones: 7/32 ... 32/3)
+constexpr int kCin[kLayers] = {16, 32, 32, 32, 32, 32};
+constexpr int kCout[kLayers] = {32, 32, 32, 32, 32, 16};
+constexpr int kRealCin[kLayers] = {7, 32, 32, 32, 32, 32};
+constexpr int kRealCout[kLayers] = {32, 32, 32, 32, 32, 3};
+constexpr int kTileP = 128;  // pixels per CTA
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Gathers the 3x3 x CIN patch of pixel (u, v) (zero outside the image) into
+// dst[0 .. 9*CIN), k = (i*3 + j)*CIN + c.
+template <int CIN>
+__device__ __forceinline__ void gather_patch(const bf16 *X, int H, int W, int u, int v, bf16 *dst, int part,
+                                             int nparts) {
+    // 16-byte chunks of 8 channels
+    constexpr int CH = CIN / 8;
+    for (int q = part; q < 9 * CH; q += nparts) {
+        const int tap = q / CH, c8 = q - tap * CH;
+        const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (uu >= 0 && uu < W && vv >= 0 && vv < H)
+            val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
+        *reinterpret_cast<uint4 *>(dst + tap * CIN + c8 * 8) = val;
+    }
+}
+
+// Y = conv3x3(X) (+ bias), 128 pixels per CTA, 8 warps of 16 pixels.
+//   X  : H*W*CIN bf16;  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]);
+//   Z  : optional fp32 pre-activation H*W*COUT;  Y : optional bf16 output (ReLU if relu)
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias,
+                                              float *Z, bf16 *Y, int relu) {
+    constexpr int K = 9 * CIN, LDA = K + 8;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    bf16 *As = reinterpret_cast<bf16 *>(sm_raw);    // [kTileP][LDA]
+    bf16 *Bs = As + kTileP * LDA;                     // [COUT][LDA]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = H * W, p0 = blockIdx.x * kTileP;
+    // stage the weights and the pixels' patches
+    for (int q = tid; q < COUT * (K / 8); q += blockDim.x) {
+        const int o = q / (K / 8), c8 = q - o * (K / 8);
+        *reinterpret_cast<uint4 *>(Bs + o * LDA + c8 * 8) = *reinterpret_cast<const uint4 *>(Bt + (size_t)o * K + c8 * 8);
+    }
+    // two threads per pixel
+    {
+        const int pl = tid >> 1, part = tid & 1;
+        const int p = p0 + pl;
+        if (p < n) {
+            gather_patch<CIN>(X, H, W, p % W, p / W, As + pl * LDA, part, 2);
+        } else {
+            for (int k = part * 8; k < K; k += 16) *reinterpret_cast<uint4 *>(As + pl * LDA + k) = make_uint4(0, 0, 0, 0);
+        }
+    }
+    __syncthreads();
+    const int g = lane >> 2, t = lane & 3;
+    constexpr int NT = COUT / 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const bf16 *Aw = As + (warp * 16) * LDA;
+#pragma unroll 2
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4];
+        a[0] = ld_u32(Aw + g * LDA + k0 + t * 2);
+        a[1] = ld_u32(Aw + (g + 8) * LDA + k0 + t * 2);
+        a[2] = ld_u32(Aw + g * LDA + k0 + t * 2 + 8);
+        a[3] = ld_u32(Aw + (g + 8) * LDA + k0 + t * 2 + 8);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            uint32_t b[2];
+            b[0] = ld_u32(Bs + (j * 8 + g) * LDA + k0 + t * 2);
+            b[1] = ld_u32(Bs + (j * 8 + g) * LDA + k0 + t * 2 + 8);
+            mma_bf16(acc[j], a, b);
+        }
+    }
+    // epilogue: c0 (row g, col 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int p = p0 + warp * 16 + g + 8 * r;
+            if (p >= n) continue;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int o = j * 8 + 2 * t + c;
+                float z = acc[j][2 * r + c] + (bias ? bias[o] : 0.f);
+                if (Z) Z[(size_t)p * COUT + o] = z;
+                if (Y) Y[(size_t)p * COUT + o] = __float2bfloat16_rn(relu ? fmaxf(z, 0.f) : z);
+            }
+        }
+    }
+}
+
+// dW[o][k] += sum_p dZ[p][o] Xpatch[p][k] over the CTA's 128 pixels; dB[o] += sum_p dZ[p][o].
+//   dZ : H*W*COUT bf16; X : H*W*CIN bf16; dW : COUT x 9CIN fp32 (atomic accumulation)
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_conv_wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW,
+                                                    float *dB) {
+    constexpr int K = 9 * CIN, LDP = kTileP + 8;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    bf16 *At = reinterpret_cast<bf16 *>(sm_raw);  // [COUT][LDP]  dZ transposed (A: M = COUT, K = pixels)
+    bf16 *Bt = At + COUT * LDP;                   // [K][LDP]     Xpatch transposed (B col layout: N = K)
+    bf16 *Pt = Bt + K * LDP;                      // [kTileP][K]  patch staging (pixel-major)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = H * W, p0 = blockIdx.x * kTileP;
+    {
+        const int pl = tid >> 1, part = tid & 1;
+        const int p = p0 + pl;
+        if (p < n) {
+            gather_patch<CIN>(X, H, W, p % W, p / W, Pt + pl * K, part, 2);
+        } else {
+            for (int k = part * 8; k < K; k += 16) *reinterpret_cast<uint4 *>(Pt + pl * K + k) = make_uint4(0, 0, 0, 0);
+        }
+    }
+    for (int q = tid; q < kTileP * COUT; q += blockDim.x) {
+        const int pl = q / COUT, o = q - pl * COUT;
+        const int p = p0 + pl;
+        At[o * LDP + pl] = p < n ? dZ[(size_t)p * COUT + o] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int q = tid; q < kTileP * K; q += blockDim.x) {
+        const int pl = q / K, k = q - pl * K;
+        Bt[k * LDP + pl] = Pt[pl * K + k];
+    }
+    // bias gradient: one thread per output channel
+    if (tid < COUT) {
+        float s = 0.f;
+        for (int pl = 0; pl < kTileP; ++pl) s += __bfloat162float(At[tid * LDP + pl]);
+        atomicAdd(&dB[tid], s);
+    }
+    __syncthreads();
+    const int g = lane >> 2, t = lane & 3;
+    constexpr int MT = COUT / 16, NT = K / 8;
+    for (int tile = warp; tile < MT * NT; tile += 8) {
+        const int mt = tile / NT, nt = tile - mt * NT;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const bf16 *Aw = At + (mt * 16) * LDP;
+        const bf16 *Bw = Bt + (nt * 8) * LDP;
+#pragma unroll
+        for (int k0 = 0; k0 < kTileP; k0 += 16) {
+            uint32_t a[4], b[2];
+            a[0] = ld_u32(Aw + g * LDP + k0 + t * 2);
+            a[1] = ld_u32(Aw + (g + 8) * LDP + k0 + t * 2);
+            a[2] = ld_u32(Aw + g * LDP + k0 + t * 2 + 8);
+            a[3] = ld_u32(Aw + (g + 8) * LDP + k0 + t * 2 + 8);
+            b[0] = ld_u32(Bw + g * LDP + k0 + t * 2);
+            b[1] = ld_u32(Bw + g * LDP + k0 + t * 2 + 8);
+            mma_bf16(acc, a, b);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int o = mt * 16 + g + 8 * r, k = nt * 8 + 2 * t + c;
+                atomicAdd(&dW[(size_t)o * K + k], acc[2 * r + c]);
+            }
+    }
+}
+
+// dZprev = dX * (Zprev > 0) as bf16 (ReLU backward); channels padded
+__global__ void k_relu_back(const float *dX, const float *Zprev, int count, bf16 *dZ) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    dZ[i] = __float2bfloat16_rn(Zprev[i] > 0.f ? dX[i] : 0.f);
+}
+
+// L1 loss on (d, a, b): out is H*W*16 fp32 (channels 0..2 used), target H*W*3;
+// writes d loss / d out (bf16, padded channels zero) and accumulates the loss
+__global__ void k_l1_loss(const float *out, const float *target, int n, float s0, float s1, float s2, float inv_n,
+                          bf16 *dout, float *loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (p < n) {
+        const float sc[3] = {s0, s1, s2};
+        for (int c = 0; c < 16; ++c) {
+            float gval = 0.f;
+            if (c < 3) {
+                const float diff = out[(size_t)p * 16 + c] - target[(size_t)p * 3 + c];
+                l += sc[c] * fabsf(diff);
+                gval = (diff > 0.f ? sc[c] : (diff < 0.f ? -sc[c] : 0.f)) * inv_n;
+            }
+            dout[(size_t)p * 16 + c] = __float2bfloat16_rn(gval);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l * inv_n);
+}
+
+// Adam on the fp32 master weights of one layer (real channels only), then the
+// bf16 copies: forward Bt[o][k] and input-gradient Bf[c][k'] (flipped taps,
+// roles of channels swapped).
+//   w: (3,3,Cin,Cout) real sizes, fp32;  gW: dW in the padded GEMM layout COUT x 9CIN
+__global__ void k_adam(float *w, float *m, float *v, const float *gW, int ci, int co, int CIN, int COUT, float lr,
+                       float b1, float b2, float eps, float c1, float c2, bf16 *Bt, bf16 *Bf) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 9 * ci * co) return;
+    const int o = idx % co, c = (idx / co) % ci, tap = idx / (co * ci);
+    const float gr = gW[(size_t)o * 9 * CIN + tap * CIN + c];
+    const float mm = b1 * m[idx] + (1.f - b1) * gr;
+    const float vv = b2 * v[idx] + (1.f - b2) * gr * gr;
+    m[idx] = mm;
+    v[idx] = vv;
+    const float wn = w[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    w[idx] = wn;
+    Bt[(size_t)o * 9 * CIN + tap * CIN + c] = __float2bfloat16_rn(wn);
+    if (Bf) Bf[(size_t)c * 9 * COUT + (8 - tap) * COUT + o] = __float2bfloat16_rn(wn);
+}
+
+__global__ void k_adam_bias(float *b, float *m, float *v, const float *g, int co, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    const int o = threadIdx.x;
+    if (o >= co) return;
+    const float mm = b1 * m[o] + (1.f - b1) * g[o];
+    const float vv = b2 * v[o] + (1.f - b2) * g[o] * g[o];
+    m[o] = mm;
+    v[o] = vv;
+    b[o] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+// bf16 copies of all layers from the fp32 master weights
+__global__ void k_pack_weights(const float *w, int ci, int co, int CIN, int COUT, bf16 *Bt, bf16 *Bf) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 9 * ci * co) return;
+    const int o = idx % co, c = (idx / co) % ci, tap = idx / (co * ci);
+    Bt[(size_t)o * 9 * CIN + tap * CIN + c] = __float2bfloat16_rn(w[idx]);
+    if (Bf) Bf[(size_t)c * 9 * COUT + (8 - tap) * COUT + o] = __float2bfloat16_rn(w[idx]);
+}
+
+// quarter-resolution input: x (fp32, H4*W4*7: R,G,B of left, R,G,B of right /255,
+// disparity / dmax) -> bf16 padded to 16 channels
+__global__ void k_pack_input(const float *x, int n, bf16 *X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * 16) return;
+    const int p = i / 16, c = i % 16;
+    X[i] = __float2bfloat16_rn(c < 7 ? x[(size_t)p * 7 + c] : 0.f);
+}
+
+// network output (pre-activation of the last layer, 16 padded channels) -> y (3 channels)
+__global__ void k_take3(const float *z, int n, float *y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * 3) return;
+    y[i] = z[(size_t)(i / 3) * 16 + i % 3];
+}
+
+template <int CIN, int COUT>
+size_t conv_smem() {
+    return sizeof(bf16) * ((size_t)kTileP * (9 * CIN + 8) + (size_t)COUT * (9 * CIN + 8));
+}
+template <int CIN, int COUT>
+size_t wgrad_smem() {
+    return sizeof(bf16) * ((size_t)COUT * (kTileP + 8) + (size_t)9 * CIN * (kTileP + 8) + (size_t)kTileP * 9 * CIN);
+}
+
+template <int CIN, int COUT>
+cudaError_t conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias, float *Z, bf16 *Y, int relu,
+                 cudaStream_t st) {
+    const size_t sm = conv_smem<CIN, COUT>();
+    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nb = (H * W + kTileP - 1) / kTileP;
+    k_conv<CIN, COUT><<<nb, 256, sm, st>>>(X, H, W, Bt, bias, Z, Y, relu);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW, float *dB, cudaStream_t st) {
+    const size_t sm = wgrad_smem<CIN, COUT>();
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nb = (H * W + kTileP - 1) / kTileP;
+    k_conv_wgrad<CIN, COUT><<<nb, 256, sm, st>>>(X, dZ, H, W, dW, dB);
+    return cudaGetLastError();
+}
+
+}  // namespace lemcnn
+
+using namespace lemcnn;
+
+struct lem_cnn {
+    cudaStream_t st = nullptr;
+    float *w[kLayers] = {}, *b[kLayers] = {};     // fp32 master weights (3,3,ci,co), bias
+    float *mw[kLayers] = {}, *vw[kLayers] = {}, *mb[kLayers] = {}, *vb[kLayers] = {};
+    bf16 *Bt[kLayers] = {}, *Bf[kLayers] = {};    // forward / input-gradient GEMM layouts
+    float *gW[kLayers] = {}, *gB[kLayers] = {};   // gradients (padded GEMM layout)
+    // activations for one image of up to cap pixels
+    size_t cap = 0;
+    bf16 *act[kLayers + 1] = {};                  // layer inputs (bf16), act[0] = packed input
+    float *pre[kLayers] = {};                     // pre-activations (fp32)
+    bf16 *dz = nullptr;                           // d loss / d pre-activation (bf16, 32 ch)
+    float *dx = nullptr;                          // d loss / d layer input (fp32, 32 ch)
+    float *loss = nullptr;
+    float *xin = nullptr, *tgt = nullptr;         // staging of one image's input / target
+    int step = 0;
+    std::string err;
+};
+
+namespace {
+thread_local std::string g_cnn_err;
+
+int cnn_fail(lem_cnn *net, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e);
+    if (net) net->err = m;
+    g_cnn_err = m;
+    return e == cudaErrorMemoryAllocation ? LEM_ERR_OOM : LEM_ERR_CUDA;
+}
+#define CNN_CUDA(net, call)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cnn_fail((net), e_, #call);    \
+    } while (0)
+
+size_t nweights(int l) { return (size_t)9 * kRealCin[l] * kRealCout[l]; }
+
+int ensure_capacity(lem_cnn *net, size_t npix) {
+    if (npix <= net->cap) return LEM_OK;
+    for (int l = 0; l <= kLayers; ++l) cudaFree(net->act[l]);
+    for (int l = 0; l < kLayers; ++l) cudaFree(net->pre[l]);
+    cudaFree(net->dz);
+    cudaFree(net->dx);
+    cudaFree(net->xin);
+    cudaFree(net->tgt);
+    for (int l = 0; l <= kLayers; ++l) {
+        const int c = l == 0 ? kCin[0] : kCout[l - 1];
+        CNN_CUDA(net, cudaMalloc(&net->act[l], sizeof(bf16) * npix * c));
+    }
+    for (int l = 0; l < kLayers; ++l) CNN_CUDA(net, cudaMalloc(&net->pre[l], sizeof(float) * npix * kCout[l]));
+    CNN_CUDA(net, cudaMalloc(&net->dz, sizeof(bf16) * npix * 32));
+    CNN_CUDA(net, cudaMalloc(&net->dx, sizeof(float) * npix * 32));
+    CNN_CUDA(net, cudaMalloc(&net->xin, sizeof(float) * npix * 7));
+    CNN_CUDA(net, cudaMalloc(&net->tgt, sizeof(float) * npix * 3));
+    net->cap = npix;
+    return LEM_OK;
+}
+
+cudaError_t forward(lem_cnn *net, int H4, int W4) {
+    cudaStream_t st = net->st;
+    cudaError_t e = conv<16, 32>(net->act[0], H4, W4, net->Bt[0], net->b[0], net->pre[0], net->act[1], 1, st);
+    for (int l = 1; l < 5 && e == cudaSuccess; ++l)
+        e = conv<32, 32>(net->act[l], H4, W4, net->Bt[l], net->b[l], net->pre[l], net->act[l + 1], 1, st);
+    if (e == cudaSuccess) e = conv<32, 16>(net->act[5], H4, W4, net->Bt[5], net->b[5], net->pre[5], nullptr, 0, st);
+    return e;
+}
+
+// backward of one image from d loss / d output (in net->dz, 16 channels);
+// accumulates into gW / gB
+cudaError_t backward(lem_cnn *net, int H4, int W4) {
+    cudaStream_t st = net->st;
+    const int n = H4 * W4;
+    cudaError_t e = cudaSuccess;
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        // weight gradient of layer l: input act[l], output gradient dz
+        if (l == 5) e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, net->gW[5], net->gB[5], st);
+        else if (l == 0) e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, net->gW[0], net->gB[0], st);
+        else e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, net->gW[l], net->gB[l], st);
+        if (e != cudaSuccess || l == 0) break;
+        // input gradient: conv of dz with the flipped, transposed weights
+        if (l == 5) e = conv<16, 32>(net->dz, H4, W4, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
+        else e = conv<32, 32>(net->dz, H4, W4, net->Bf[l], nullptr, net->dx, nullptr, 0, st);
+        if (e != cudaSuccess) break;
+        // ReLU of layer l-1
+        const int cnt = n * kCout[l - 1];
+        k_relu_back<<<(cnt + 255) / 256, 256, 0, st>>>(net->dx, net->pre[l - 1], cnt, net->dz);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+}  // namespace
+
+extern "C" {
+
+const char *lem_cnn_last_error(const lem_cnn *net) { return net ? net->err.c_str() : g_cnn_err.c_str(); }
+
+int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out) {
+    if (!out) return LEM_ERR_ARG;
+    *out = nullptr;
+    lem_cnn *net = new lem_cnn();
+    net->st = (cudaStream_t)stream;
+    auto bail = [&](int rc) {
+        lem_cnn_destroy(net);
+        return rc;
+    };
+    // He initialisation from a fixed generator (host), zero biases
+    uint64_t s = seed ^ 0x2545F4914F6CDD1Dull;
+    auto uni = [&]() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1.0p-53;
+    };
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = nweights(l);
+        std::vector<float> hw(nw);
+        const double sd = std::sqrt(2.0 / (9.0 * kRealCin[l])) * (l == kLayers - 1 ? 0.1 : 1.0);
+        for (size_t i = 0; i < nw; ++i) {
+            // Box-Muller normal
+            const double u1 = std::max(uni(), 1e-300), u2 = uni();
+            hw[i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+        cudaError_t e = cudaMalloc(&net->w[l], sizeof(float) * nw);
+        if (e == cudaSuccess) e = cudaMemcpy(net->w[l], hw.data(), sizeof(float) * nw, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&net->b[l], sizeof(float) * kCout[l]);
+        if (e == cudaSuccess) e = cudaMemset(net->b[l], 0, sizeof(float) * kCout[l]);
+        for (float **p : {&net->mw[l], &net->vw[l]})
+            if (e == cudaSuccess) {
+                e = cudaMalloc(p, sizeof(float) * nw);
+                if (e == cudaSuccess) e = cudaMemset(*p, 0, sizeof(float) * nw);
+            }
+        for (float **p : {&net->mb[l], &net->vb[l], &net->gB[l]})
+            if (e == cudaSuccess) {
+                e = cudaMalloc(p, sizeof(float) * kCout[l]);
+                if (e == cudaSuccess) e = cudaMemset(*p, 0, sizeof(float) * kCout[l]);
+            }
+        const size_t gemm = (size_t)kCout[l] * 9 * kCin[l];
+        if (e == cudaSuccess) e = cudaMalloc(&net->Bt[l], sizeof(bf16) * gemm);
+        if (e == cudaSuccess) e = cudaMemset(net->Bt[l], 0, sizeof(bf16) * gemm);
+        if (e == cudaSuccess) e = cudaMalloc(&net->Bf[l], sizeof(bf16) * gemm);
+        if (e == cudaSuccess) e = cudaMemset(net->Bf[l], 0, sizeof(bf16) * gemm);
+        if (e == cudaSuccess) e = cudaMalloc(&net->gW[l], sizeof(float) * gemm);
+        if (e == cudaSuccess) e = cudaMemset(net->gW[l], 0, sizeof(float) * gemm);
+        if (e == cudaSuccess) {
+            k_pack_weights<<<(int)((nw + 255) / 256), 256, 0, net->st>>>(net->w[l], kRealCin[l], kRealCout[l],
+                                                                        kCin[l], kCout[l], net->Bt[l], net->Bf[l]);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return bail(cnn_fail(net, e, "lem_cnn_create"));
+    }
+    cudaError_t e = cudaMalloc(&net->loss, sizeof(float));
+    if (e != cudaSuccess) return bail(cnn_fail(net, e, "lem_cnn_create"));
+    *out = net;
+    return LEM_OK;
+}
+
+int lem_cnn_destroy(lem_cnn *net) {
+    if (!net) return LEM_OK;
+    for (int l = 0; l < kLayers; ++l) {
+        for (float *p : {net->w[l], net->b[l], net->mw[l], net->vw[l], net->mb[l], net->vb[l], net->gW[l], net->gB[l],
+                         net->pre[l]})
+            cudaFree(p);
+        cudaFree(net->Bt[l]);
+        cudaFree(net->Bf[l]);
+    }
+    for (int l = 0; l <= kLayers; ++l) cudaFree(net->act[l]);
+    cudaFree(net->dz);
+    cudaFree(net->dx);
+    cudaFree(net->loss);
+    cudaFree(net->xin);
+    cudaFree(net->tgt);
+    delete net;
+    return LEM_OK;
+}
+
+int64_t lem_cnn_num_params(void) {
+    int64_t n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (int64_t)nweights(l) + kRealCout[l];
+    return n;
+}
+
+int lem_cnn_get_params(lem_cnn *net, float *host) {
+    if (!net || !host) return LEM_ERR_ARG;
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        CNN_CUDA(net, cudaMemcpy(host + o, net->w[l], sizeof(float) * nweights(l), cudaMemcpyDeviceToHost));
+        o += nweights(l);
+        CNN_CUDA(net, cudaMemcpy(host + o, net->b[l], sizeof(float) * kRealCout[l], cudaMemcpyDeviceToHost));
+        o += kRealCout[l];
+    }
+    return LEM_OK;
+}
+
+int lem_cnn_set_params(lem_cnn *net, const float *host) {
+    if (!net || !host) return LEM_ERR_ARG;
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        CNN_CUDA(net, cudaMemcpy(net->w[l], host + o, sizeof(float) * nweights(l), cudaMemcpyHostToDevice));
+        o += nweights(l);
+        CNN_CUDA(net, cudaMemcpy(net->b[l], host + o, sizeof(float) * kRealCout[l], cudaMemcpyHostToDevice));
+        o += kRealCout[l];
+        const size_t nw = nweights(l);
+        k_pack_weights<<<(int)((nw + 255) / 256), 256, 0, net->st>>>(net->w[l], kRealCin[l], kRealCout[l], kCin[l],
+                                                                    kCout[l], net->Bt[l], net->Bf[l]);
+        CNN_CUDA(net, cudaGetLastError());
+    }
+    return LEM_OK;
+}
+
+int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
+    if (!net || !x || !out || H4 < 1 || W4 < 1) return LEM_ERR_ARG;
+    const size_t n = (size_t)H4 * W4;
+    int rc = ensure_capacity(net, n);
+    if (rc != LEM_OK) return rc;
+    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, (int)n, net->act[0]);
+    CNN_CUDA(net, cudaGetLastError());
+    CNN_CUDA(net, forward(net, H4, W4));
+    k_take3<<<(int)((n * 3 + 255) / 256), 256, 0, net->st>>>(net->pre[5], (int)n, out);
+    CNN_CUDA(net, cudaGetLastError());
+    return LEM_OK;
+}
+
+int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_images, int H4, int W4,
+                      const float *scale, float *loss, float *grads) {
+    if (!net || !x || !target || n_images < 1 || H4 < 1 || W4 < 1 || !scale) return LEM_ERR_ARG;
+    const size_t n = (size_t)H4 * W4;
+    int rc = ensure_capacity(net, n);
+    if (rc != LEM_OK) return rc;
+    for (int l = 0; l < kLayers; ++l) {
+        CNN_CUDA(net, cudaMemsetAsync(net->gW[l], 0, sizeof(float) * kCout[l] * 9 * kCin[l], net->st));
+        CNN_CUDA(net, cudaMemsetAsync(net->gB[l], 0, sizeof(float) * kCout[l], net->st));
+    }
+    CNN_CUDA(net, cudaMemsetAsync(net->loss, 0, sizeof(float), net->st));
+    const float inv_n = 1.f / (float)(n * n_images);
+    for (int i = 0; i < n_images; ++i) {
+        k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x + i * n * 7, (int)n, net->act[0]);
+        CNN_CUDA(net, cudaGetLastError());
+        CNN_CUDA(net, forward(net, H4, W4));
+        k_l1_loss<<<(int)((n + 255) / 256), 256, 0, net->st>>>(net->pre[5], target + i * n * 3, (int)n, scale[0],
+                                                             scale[1], scale[2], inv_n, net->dz, net->loss);
+        CNN_CUDA(net, cudaGetLastError());
+        CNN_CUDA(net, backward(net, H4, W4));
+    }
+    if (loss) CNN_CUDA(net, cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, net->st));
+    if (grads) {
+        // real-channel gradients in the (3,3,ci,co) + bias order of lem_cnn_get_params
+        std::vector<float> g;
+        for (int l = 0; l < kLayers; ++l) {
+            std::vector<float> gw((size_t)kCout[l] * 9 * kCin[l]), gb(kCout[l]);
+            CNN_CUDA(net, cudaMemcpyAsync(gw.data(), net->gW[l], sizeof(float) * gw.size(), cudaMemcpyDeviceToHost,
+                                          net->st));
+            CNN_CUDA(net, cudaMemcpyAsync(gb.data(), net->gB[l], sizeof(float) * gb.size(), cudaMemcpyDeviceToHost,
+                                          net->st));
+            CNN_CUDA(net, cudaStreamSynchronize(net->st));
+            for (int tap = 0; tap < 9; ++tap)
+                for (int c = 0; c < kRealCin[l]; ++c)
+                    for (int o = 0; o < kRealCout[l]; ++o) g.push_back(gw[(size_t)o * 9 * kCin[l] + tap * kCin[l] + c]);
+            for (int o = 0; o < kRealCout[l]; ++o) g.push_back(gb[o]);
+        }
+        std::copy(g.begin(), g.end(), grads);
+    }
+    CNN_CUDA(net, cudaStreamSynchronize(net->st));
+    return LEM_OK;
+}
+
+int lem_cnn_train_step(lem_cnn *net, const float *x, const float *target, int n_images, int H4, int W4,
+                       const float *scale, float lr, float *loss) {
+    int rc = lem_cnn_gradients(net, x, target, n_images, H4, W4, scale, loss, nullptr);
+    if (rc != LEM_OK) return rc;
+    ++net->step;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = nweights(l);
+        k_adam<<<(int)((nw + 255) / 256), 256, 0, net->st>>>(net->w[l], net->mw[l], net->vw[l], net->gW[l],
+                                                            kRealCin[l], kRealCout[l], kCin[l], kCout[l], lr, b1,
+                                                            b2, eps, c1, c2, net->Bt[l], net->Bf[l]);
+        CNN_CUDA(net, cudaGetLastError());
+        k_adam_bias<<<1, 32, 0, net->st>>>(net->b[l], net->mb[l], net->vb[l], net->gB[l], kRealCout[l], lr, b1, b2,
+                                          eps, c1, c2);
+        CNN_CUDA(net, cudaGetLastError());
+    }
+    return LEM_OK;
+}
+
+}  // extern "C"
+
+namespace lem {
+int cnn_forward_on(lem_cnn *net, const float *x, int H4, int W4, float *y, cudaStream_t st) {
+    cudaStream_t keep = net->st;
+    net->st = st;
+    const int rc = lem_cnn_forward(net, x, H4, W4, y);
+    net->st = keep;
+    return rc;
+}
+const char *cnn_error(const lem_cnn *net) { return lem_cnn_last_error(net); }
+}  // namespace lem

@@ -45,6 +45,7 @@ struct PairDesc {
 struct Level {
     int s;              // cell size
     int k_prop, k_rand;
+    int k_cnn;          // map candidates (proposal indices k_prop .. k_prop + k_cnn - 1)
 };
 
 // Per-launch counters written by the expansion kernels.
@@ -86,9 +87,11 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
                                 int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st);
 // All expansions of one (level, group) over every pair of the batch: items
 // lists (pair, cell i, cell j); iter < 0 reads the iteration from *iter_dev.
+// prop: proposal maps of all pairs (same offsets as lab), or NULL when lv.k_cnn == 0.
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
-                                int n_items, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st);
+                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
+                                cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st);
@@ -98,10 +101,24 @@ cudaError_t launch_labels_in(int H, int W, const float *abc, const float *cost, 
 cudaError_t launch_planes_out(int H, int W, const DevPlanes &P, float *left, float *right, float *guide,
                               float *weights, cudaStream_t st);
 int energy_partials(int H, int W);
+// Learned-proposer glue.  Quarter-resolution grid: H4 = ceil(H/4), W4 = ceil(W/4).
+// x: H4*W4*7 (left RGB, right RGB as 4x4 block means / 255; mean label disparity / dmax)
+cudaError_t launch_cnn_features(const DevPlanes &P, const float4 *lab, float dmax, float *x, cudaStream_t st);
+// t: H4*W4*3 (4x4 block means of the label's disparity / dmax, a, b)
+cudaError_t launch_cnn_targets(const float4 *lab, int H, int W, float dmax, float *t, cudaStream_t st);
+// prop: H*W plane labels from the bilinearly upsampled quarter-resolution (d/dmax, a, b) in y (H4*W4*3)
+cudaError_t launch_cnn_upsample(const float *y, int H, int W, float dmax, float4 *prop, cudaStream_t st);
+// prop (float4 a, b, c, 0) from / to a caller's H*W*3 array
+cudaError_t launch_props_in(int n, const float *abc, float4 *prop, cudaStream_t st);
+cudaError_t launch_props_out(int n, const float4 *prop, float *abc, cudaStream_t st);
 // Batch min-cut whose region/offset/counter scratch is a static device array
 // (no allocation); at most LEM_NOALLOC_MAX_REGIONS regions.
 cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, int n_regions, int max_nodes,
                                   size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
                                   int64_t *flow, int32_t *status, cudaStream_t st);
+
+// Forward pass of the proposal network on stream st (lem_cnn.cu); LEM_* status.
+int cnn_forward_on(lem_cnn *net, const float *x, int H4, int W4, float *y, cudaStream_t st);
+const char *cnn_error(const lem_cnn *net);
 
 }  // namespace lem

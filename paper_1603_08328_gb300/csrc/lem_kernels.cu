@@ -1090,7 +1090,8 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
 template <int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
-                   const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all, Counters *ctr) {
+                   const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all,
+                   const float4 *prop_all, Counters *ctr) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha[kMaxVisit];
     __shared__ long long red[33];
@@ -1105,6 +1106,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     kp.seed = pd.seed;
     float4 *lab = lab_all + pd.off;
     float *phiA = phiA_all + pd.off;
+    const float4 *prop = prop_all ? prop_all + pd.off : nullptr;
     if (iter < 0) iter = *iter_dev;
     const int H = P.H, W = P.W, s = lv.s;
     const int ci = item.y, cj = item.z;
@@ -1119,7 +1121,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     double rn = ldexp(1.0, -iter);
     long long acc = 0, hits = 0;
     CutCount cc{0, 0, 0};
-    const int nprop = lv.k_prop + lv.k_rand;
+    // proposal indices: [0, k_prop) propagation, [k_prop, k_prop + kc) map
+    // candidates of the learned proposer, then k_rand perturbations
+    const int kc = prop ? lv.k_cnn : 0;
+    const int nprop = lv.k_prop + kc + lv.k_rand;
     const int K = kp.visit;
     for (int t0 = 0; t0 < nprop; t0 += K) {
         const int t1 = min(nprop, t0 + K);
@@ -1127,10 +1132,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
         // (K = 1: Algorithm 2 as printed)
         if (threadIdx.x == 0) {
             for (int t = t0; t < t1; ++t) {
-                const bool perturb = t >= lv.k_prop;
-                s_alpha[t - t0] = propose(lab, W, proposal_stream(kp.seed, iter, level, ci, cj, t), cx0, cy0, cw,
-                                          chh, perturb, perturb ? rd : 0.0, perturb ? rn : 0.0, kp.disp_min,
-                                          kp.disp_max);
+                const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+                if (t >= lv.k_prop && t < lv.k_prop + kc) {
+                    s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+                    continue;
+                }
+                const bool perturb = t >= lv.k_prop + kc;
+                s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
+                                          perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
                 if (perturb) {
                     rd *= 0.5;
                     rn *= 0.5;
@@ -1178,6 +1187,96 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
         atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
         atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
     }
+}
+
+// ---------------------------------------------------------------------------
+// learned-proposer glue: quarter-resolution features / targets of a label map
+// and full-resolution plane proposals from the network's output
+// ---------------------------------------------------------------------------
+__global__ void k_cnn_features(DevPlanes P, const float4 *lab, int H4, int W4, float inv_dmax, float *x) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= H4 * W4) return;
+    const int U = q % W4, V = q / W4;
+    float s[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+            const int u = 4 * U + dx, v = 4 * V + dy;
+            if (u >= P.W || v >= P.H) continue;
+            const size_t p = (size_t)v * P.W + u;
+            const float4 l = load_px(P.L, p, P.fmt), r = load_px(P.R, p, P.fmt), f = lab[p];
+            s[0] += l.x;
+            s[1] += l.y;
+            s[2] += l.z;
+            s[3] += r.x;
+            s[4] += r.y;
+            s[5] += r.z;
+            s[6] += fmaf(f.x, (float)u, fmaf(f.y, (float)v, f.z));
+            ++cnt;
+        }
+    const float inv = 1.f / (float)cnt;
+    for (int c = 0; c < 6; ++c) x[(size_t)q * 7 + c] = s[c] * inv * (1.f / 255.f);
+    x[(size_t)q * 7 + 6] = s[6] * inv * inv_dmax;
+}
+
+__global__ void k_cnn_targets(const float4 *lab, int H, int W, int H4, int W4, float inv_dmax, float *t) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= H4 * W4) return;
+    const int U = q % W4, V = q / W4;
+    float d = 0.f, a = 0.f, b = 0.f;
+    int cnt = 0;
+    for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+            const int u = 4 * U + dx, v = 4 * V + dy;
+            if (u >= W || v >= H) continue;
+            const float4 f = lab[(size_t)v * W + u];
+            d += fmaf(f.x, (float)u, fmaf(f.y, (float)v, f.z));
+            a += f.x;
+            b += f.y;
+            ++cnt;
+        }
+    // slopes beyond 1 (more than a pixel of disparity per pixel) are clamped: such
+    // labels are left-overs of the random initialisation, not surfaces to learn
+    const float inv = 1.f / (float)cnt;
+    t[(size_t)q * 3] = d * inv * inv_dmax;
+    t[(size_t)q * 3 + 1] = fminf(fmaxf(a * inv, -1.f), 1.f);
+    t[(size_t)q * 3 + 2] = fminf(fmaxf(b * inv, -1.f), 1.f);
+}
+
+// bilinear interpolation of (d/dmax, a, b) at the pixel centre (quarter-
+// resolution cell U covers pixels 4U .. 4U+3, centre 4U + 1.5), then
+// c = d - a u - b v
+__global__ void k_cnn_upsample(const float *y, int H4, int W4, int H, int W, float dmax, float4 *prop) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    const int u = p % W, v = p / W;
+    const float fu = fminf(fmaxf(((float)u - 1.5f) * 0.25f, 0.f), (float)(W4 - 1));
+    const float fv = fminf(fmaxf(((float)v - 1.5f) * 0.25f, 0.f), (float)(H4 - 1));
+    const int u0 = (int)fu, v0 = (int)fv;
+    const int u1 = min(u0 + 1, W4 - 1), v1 = min(v0 + 1, H4 - 1);
+    const float tu = fu - (float)u0, tv = fv - (float)v0;
+    float r[3];
+    for (int c = 0; c < 3; ++c) {
+        const float a00 = y[((size_t)v0 * W4 + u0) * 3 + c], a01 = y[((size_t)v0 * W4 + u1) * 3 + c];
+        const float a10 = y[((size_t)v1 * W4 + u0) * 3 + c], a11 = y[((size_t)v1 * W4 + u1) * 3 + c];
+        const float top = fmaf(tu, a01 - a00, a00), bot = fmaf(tu, a11 - a10, a10);
+        r[c] = fmaf(tv, bot - top, top);
+    }
+    const float d = r[0] * dmax, a = r[1], b = r[2];
+    prop[p] = make_float4(a, b, d - a * (float)u - b * (float)v, 0.f);
+}
+
+__global__ void k_props_in(int n, const float *abc, float4 *prop) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) prop[p] = make_float4(abc[3 * (size_t)p], abc[3 * (size_t)p + 1], abc[3 * (size_t)p + 2], 0.f);
+}
+__global__ void k_props_out(int n, const float4 *prop, float *abc) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const float4 f = prop[p];
+    abc[3 * (size_t)p] = f.x;
+    abc[3 * (size_t)p + 1] = f.y;
+    abc[3 * (size_t)p + 2] = f.z;
 }
 
 // A9: quantised energy, per-block partial sums
@@ -1346,27 +1445,29 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 
 template <int NT>
 cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, const int *iter_dev,
-                      const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA, Counters *ctr,
-                      size_t sm, cudaStream_t st) {
+                      const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA,
+                      const float4 *prop, Counters *ctr, size_t sm, cudaStream_t st) {
     cudaError_t e = set_smem((const void *)k_expand_group<NT>, sm);
     if (e != cudaSuccess) return e;
-    k_expand_group<NT><<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA, ctr);
+    k_expand_group<NT>
+        <<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA, prop, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
-                                int n_items, float4 *lab, float *phiA, Counters *ctr, cudaStream_t st) {
+                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
+                                cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const int s = lv.s;
     const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
     const size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
     const int nt = threads_for_nodes(rw * rh);
     if (nt == 256)
-        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
+        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
     if (nt == 512)
-        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
-    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, ctr, sm, st);
+        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
+    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
 }
 
 __global__ void k_increment(int *x) { *x += 1; }
@@ -1377,6 +1478,30 @@ cudaError_t launch_increment(int *x, cudaStream_t st) {
 }
 
 int energy_partials(int H, int W) { return std::min(1024, (H * W + 255) / 256); }
+
+cudaError_t launch_cnn_features(const DevPlanes &P, const float4 *lab, float dmax, float *x, cudaStream_t st) {
+    const int H4 = (P.H + 3) / 4, W4 = (P.W + 3) / 4;
+    k_cnn_features<<<(H4 * W4 + 255) / 256, 256, 0, st>>>(P, lab, H4, W4, 1.f / dmax, x);
+    return cudaGetLastError();
+}
+cudaError_t launch_cnn_targets(const float4 *lab, int H, int W, float dmax, float *t, cudaStream_t st) {
+    const int H4 = (H + 3) / 4, W4 = (W + 3) / 4;
+    k_cnn_targets<<<(H4 * W4 + 255) / 256, 256, 0, st>>>(lab, H, W, H4, W4, 1.f / dmax, t);
+    return cudaGetLastError();
+}
+cudaError_t launch_cnn_upsample(const float *y, int H, int W, float dmax, float4 *prop, cudaStream_t st) {
+    const int H4 = (H + 3) / 4, W4 = (W + 3) / 4;
+    k_cnn_upsample<<<(H * W + 255) / 256, 256, 0, st>>>(y, H4, W4, H, W, dmax, prop);
+    return cudaGetLastError();
+}
+cudaError_t launch_props_in(int n, const float *abc, float4 *prop, cudaStream_t st) {
+    k_props_in<<<(n + 255) / 256, 256, 0, st>>>(n, abc, prop);
+    return cudaGetLastError();
+}
+cudaError_t launch_props_out(int n, const float4 *prop, float *abc, cudaStream_t st) {
+    k_props_out<<<(n + 255) / 256, 256, 0, st>>>(n, prop, abc);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st) {

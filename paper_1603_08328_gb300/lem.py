@@ -40,7 +40,7 @@ class lem_params(C.Structure):
         ("cell", C.c_int * 3), ("k_prop", C.c_int * 3), ("k_rand", C.c_int * 3), ("quant_scale", C.c_double),
         ("store_dtype", C.c_int), ("cond_fp64", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p),
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
-        ("use_graph", C.c_int), ("candidates_per_visit", C.c_int),
+        ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
     ]
 
 
@@ -88,6 +88,27 @@ def lib():
         L.lem_mincut_batch_noalloc.restype = C.c_int
         L.lem_evals_per_iteration.argtypes = [H]
         L.lem_evals_per_iteration.restype = C.c_int64
+        L.lem_set_proposals.argtypes = [H, C.c_int, vp]
+        L.lem_get_proposals.argtypes = [H, C.c_int, vp]
+        N = C.c_void_p
+        L.lem_cnn_create.argtypes = [C.c_uint64, vp, P(N)]
+        L.lem_cnn_destroy.argtypes = [N]
+        L.lem_cnn_last_error.argtypes = [N]
+        L.lem_cnn_last_error.restype = C.c_char_p
+        L.lem_cnn_num_params.argtypes = []
+        L.lem_cnn_num_params.restype = C.c_int64
+        L.lem_cnn_get_params.argtypes = [N, vp]
+        L.lem_cnn_set_params.argtypes = [N, vp]
+        L.lem_cnn_forward.argtypes = [N, vp, C.c_int, C.c_int, vp]
+        L.lem_cnn_gradients.argtypes = [N, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+        L.lem_cnn_train_step.argtypes = [N, vp, vp, C.c_int, C.c_int, C.c_int, vp, C.c_float, vp]
+        L.lem_cnn_features.argtypes = [H, C.c_int, vp]
+        L.lem_cnn_targets.argtypes = [H, C.c_int, vp]
+        L.lem_cnn_propose.argtypes = [N, H]
+        for name in ("lem_set_proposals", "lem_get_proposals", "lem_cnn_create", "lem_cnn_destroy",
+                     "lem_cnn_get_params", "lem_cnn_set_params", "lem_cnn_forward", "lem_cnn_gradients",
+                     "lem_cnn_train_step", "lem_cnn_features", "lem_cnn_targets", "lem_cnn_propose"):
+            getattr(L, name).restype = C.c_int
         for name in ("lem_create", "lem_create_batch", "lem_pair_count", "lem_pair_info", "lem_energy_pair",
                      "lem_destroy", "lem_unary_batch", "lem_pairwise_batch", "lem_mincut_batch",
                      "lem_expand_group", "lem_expand_iteration", "lem_get_labels", "lem_set_labels", "lem_energy",
@@ -111,7 +132,7 @@ def lem_default_params(**overrides) -> lem_params:
     for k, v in overrides.items():
         if k == "lambda":
             k = "lam"
-        if k in ("cell", "k_prop", "k_rand"):
+        if k in ("cell", "k_prop", "k_rand", "k_cnn"):
             v = list(v) + [0] * (3 - len(v))
             v = (C.c_int * 3)(*v)
         setattr(p, k, v)
@@ -223,6 +244,67 @@ def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, 
 
 def lem_evals_per_iteration(h) -> int:
     return lib().lem_evals_per_iteration(h)
+
+
+def lem_set_proposals(h, pair, abc_ptr):
+    return lib().lem_set_proposals(h, pair, abc_ptr)
+
+
+def lem_get_proposals(h, pair, abc_ptr):
+    return lib().lem_get_proposals(h, pair, abc_ptr)
+
+
+def lem_cnn_create(seed, stream=None):
+    n = C.c_void_p()
+    rc = lib().lem_cnn_create(seed, stream, C.byref(n))
+    if rc != LEM_OK:
+        raise LemError(rc, lem_cnn_last_error(None))
+    return n
+
+
+def lem_cnn_destroy(net):
+    return lib().lem_cnn_destroy(net)
+
+
+def lem_cnn_last_error(net) -> str:
+    s = lib().lem_cnn_last_error(net)
+    return s.decode() if s else ""
+
+
+def lem_cnn_num_params() -> int:
+    return lib().lem_cnn_num_params()
+
+
+def lem_cnn_get_params(net, host_ptr):
+    return lib().lem_cnn_get_params(net, host_ptr)
+
+
+def lem_cnn_set_params(net, host_ptr):
+    return lib().lem_cnn_set_params(net, host_ptr)
+
+
+def lem_cnn_forward(net, x_ptr, H4, W4, y_ptr):
+    return lib().lem_cnn_forward(net, x_ptr, H4, W4, y_ptr)
+
+
+def lem_cnn_gradients(net, x_ptr, t_ptr, n_images, H4, W4, scale_ptr, loss_ptr, grads_ptr):
+    return lib().lem_cnn_gradients(net, x_ptr, t_ptr, n_images, H4, W4, scale_ptr, loss_ptr, grads_ptr)
+
+
+def lem_cnn_train_step(net, x_ptr, t_ptr, n_images, H4, W4, scale_ptr, lr, loss_ptr):
+    return lib().lem_cnn_train_step(net, x_ptr, t_ptr, n_images, H4, W4, scale_ptr, lr, loss_ptr)
+
+
+def lem_cnn_features(h, pair, x_ptr):
+    return lib().lem_cnn_features(h, pair, x_ptr)
+
+
+def lem_cnn_targets(h, pair, t_ptr):
+    return lib().lem_cnn_targets(h, pair, t_ptr)
+
+
+def lem_cnn_propose(net, h):
+    return lib().lem_cnn_propose(net, h)
 
 
 # --- convenience wrapper ------------------------------------------------------
@@ -371,3 +453,119 @@ class Stereo:
 
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
+
+    # learned proposer -------------------------------------------------------------
+    def set_proposals(self, abc, pair=0):
+        """Proposal map (H, W, 3) of plane labels for the k_cnn map candidates."""
+        torch = self.torch
+        a = torch.as_tensor(np.ascontiguousarray(abc, np.float32)).cuda().contiguous()
+        self._prop_keep = a
+        self.check(lem_set_proposals(self.h, pair, _ptr(a)))
+
+    def proposals(self, pair=0):
+        hh, ww, _ = self.pairs[pair]
+        out = self.torch.empty(hh, ww, 3, dtype=self.torch.float32, device="cuda")
+        self.check(lem_get_proposals(self.h, pair, _ptr(out)))
+        return out
+
+    def quarter_shape(self, pair=0):
+        hh, ww, _ = self.pairs[pair]
+        return (hh + 3) // 4, (ww + 3) // 4
+
+    def cnn_features(self, pair=0):
+        H4, W4 = self.quarter_shape(pair)
+        x = self.torch.empty(H4, W4, 7, dtype=self.torch.float32, device="cuda")
+        self.check(lem_cnn_features(self.h, pair, _ptr(x)))
+        return x
+
+    def cnn_targets(self, pair=0):
+        H4, W4 = self.quarter_shape(pair)
+        t = self.torch.empty(H4, W4, 3, dtype=self.torch.float32, device="cuda")
+        self.check(lem_cnn_targets(self.h, pair, _ptr(t)))
+        return t
+
+    def cnn_propose(self, net: "ProposalNet"):
+        self.check(lem_cnn_propose(net.net, self.h))
+
+
+class ProposalNet:
+    """The proposal network (lem_cnn_* entry points).  Inputs and outputs are CUDA tensors."""
+
+    def __init__(self, seed=0, stream=None):
+        import torch
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the library has no CPU path")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.net = lem_cnn_create(seed, C.c_void_p(stream.cuda_stream))
+
+    def close(self):
+        if getattr(self, "net", None):
+            lem_cnn_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != LEM_OK:
+            raise LemError(rc, lem_cnn_last_error(self.net))
+        return rc
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(lem_cnn_num_params(), np.float32)
+        self.check(lem_cnn_get_params(self.net, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, np.float32)
+        assert a.size == lem_cnn_num_params()
+        self.check(lem_cnn_set_params(self.net, C.c_void_p(a.ctypes.data)))
+
+    def forward(self, x):
+        """x: (H4, W4, 7) CUDA float32 -> (H4, W4, 3)."""
+        x = x.contiguous()
+        H4, W4 = x.shape[:2]
+        y = self.torch.empty(H4, W4, 3, dtype=self.torch.float32, device="cuda")
+        self.check(lem_cnn_forward(self.net, _ptr(x), H4, W4, _ptr(y)))
+        return y
+
+    def gradients(self, x, t, scale=(1.0, 1.0, 1.0)):
+        """x: (n, H4, W4, 7), t: (n, H4, W4, 3) CUDA -> (loss, flat gradients in get_params order)."""
+        x, t = x.contiguous(), t.contiguous()
+        n, H4, W4 = x.shape[:3]
+        sc = np.ascontiguousarray(scale, np.float32)
+        loss = np.zeros(1, np.float32)
+        g = np.empty(lem_cnn_num_params(), np.float32)
+        self.check(lem_cnn_gradients(self.net, _ptr(x), _ptr(t), n, H4, W4, C.c_void_p(sc.ctypes.data),
+                                     C.c_void_p(loss.ctypes.data), C.c_void_p(g.ctypes.data)))
+        return float(loss[0]), g
+
+    def train_step(self, x, t, lr, scale=(1.0, 1.0, 1.0)):
+        x, t = x.contiguous(), t.contiguous()
+        n, H4, W4 = x.shape[:3]
+        sc = np.ascontiguousarray(scale, np.float32)
+        loss = np.zeros(1, np.float32)
+        self.check(lem_cnn_train_step(self.net, _ptr(x), _ptr(t), n, H4, W4, C.c_void_p(sc.ctypes.data), lr,
+                                      C.c_void_p(loss.ctypes.data)))
+        return float(loss[0])
+
+    @staticmethod
+    def unflatten(flat):
+        """Flat parameters -> list of (w (3, 3, Cin, Cout), b (Cout,))."""
+        out, o = [], 0
+        for ci, co in LAYERS:
+            w = np.asarray(flat[o:o + 9 * ci * co]).reshape(3, 3, ci, co)
+            o += 9 * ci * co
+            b = np.asarray(flat[o:o + co])
+            o += co
+            out.append((w, b))
+        return out
+
+
+LAYERS = [(7, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 3)]

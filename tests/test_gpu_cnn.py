@@ -1,0 +1,272 @@
+"""GPU parity of the learned proposer through the C ABI against the FP64 reference in
+oracle/cnn.py, and the map candidates of the expansion kernel in lockstep with the oracle.
+
+Tolerances.  The convolution kernels keep the weights, the layer inputs and the gradients
+of the pre-activations in bfloat16 and accumulate in FP32.  Two references are used:
+  * the FP64 network with the same bfloat16 storage (oracle ``store="bf16"``: operands
+    rounded where the kernel stores them, FP64 arithmetic).  The kernel then differs
+    only by FP32 accumulation (relative 2^-24 per add over <= 288-term dot products and
+    <= 2 x 9216-pixel sums: ~1e-5), by the rare element whose FP32 and FP64 values round
+    to different bfloat16 neighbours (one ulp, 2^-8, on ~1e-4 of the elements) and the
+    ReLU decisions those flip: 1e-3 on the normalised L2 error ||gpu - ref|| / ||ref||;
+  * the unrounded FP64 network, which shows what bfloat16 storage costs: each stored
+    operand carries a relative error of at most 2^-9, a 3x3x32 dot product of such terms
+    stays within a few 2^-9 of its scale, six layers give ~6 * 4 * 2^-9 ~ 5e-2 on the
+    output (bound 2.5e-2 measured 7e-3); the gradients also pass through the ReLU masks,
+    and a mask that flips where a pre-activation is within rounding of 0 moves a whole
+    gradient element, so their bound is 0.15 (measured 0.09 at the first layer).
+The quarter-resolution features are 16-term FP32 means: 1e-5 absolute on values of order 1.
+Map candidates are copied labels, so the lockstep test has the same near-tie allowance as
+the propagation/perturbation lockstep.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+from synth import random_labels
+from tests.conftest import TINY_PARAMS
+
+pytestmark = pytest.mark.gpu
+
+EMU_TOL = 1e-3     # against the FP64 network with bfloat16 storage
+FWD_TOL = 2.5e-2   # forward, against the unrounded FP64 network
+GRAD_TOL = 0.15    # gradients, against the unrounded FP64 network
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def _params(seed, scale=1.0):
+    """Seeded He-normal weights and small biases, (w (3,3,ci,co), b) per layer, FP32 values."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in cnn.LAYERS:
+        w = rng.normal(scale=scale * np.sqrt(2.0 / (9 * ci)), size=(3, 3, ci, co)).astype(np.float32)
+        b = rng.normal(scale=0.05, size=co).astype(np.float32)
+        out.append((w, b))
+    return out
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([w.ravel(), b]) for w, b in params]).astype(np.float32)
+
+
+def _f64(params):
+    return [(w.astype(np.float64), b.astype(np.float64)) for w, b in params]
+
+
+def _nerr(a, ref):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - ref) / max(np.linalg.norm(ref), 1e-30))
+
+
+def test_param_layout_round_trip(torch_cuda):
+    from paper_1603_08328_gb300.lem import ProposalNet, lem_cnn_num_params
+    assert lem_cnn_num_params() == sum(9 * ci * co + co for ci, co in cnn.LAYERS)
+    net = ProposalNet(seed=3)
+    p = _flat(_params(0))
+    net.set_params(p)
+    assert (net.get_params() == p).all()
+
+
+@pytest.mark.parametrize("H4,W4", [(37, 29), (1, 1), (8, 16), (96, 113)])
+def test_forward_matches_oracle(torch_cuda, H4, W4):
+    """Forward pass over several 128-pixel tiles with a ragged tail, a single pixel, an exact
+    tile, and the quarter-resolution grid of a 450 x 375 image."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet
+    params = _params(1)
+    net = ProposalNet(seed=0)
+    net.set_params(_flat(params))
+    rng = np.random.default_rng(H4 * 1000 + W4)
+    x = rng.uniform(0.0, 1.0, size=(H4, W4, 7)).astype(np.float32)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    emu, _, _ = cnn.forward(_f64(params), x.astype(np.float64), store="bf16")
+    ref, _, _ = cnn.forward(_f64(params), x.astype(np.float64))
+    e_emu, err = _nerr(y, emu), _nerr(y, ref)
+    print(f"forward {H4}x{W4}: normalised error {e_emu:.2e} (bf16 storage), {err:.2e} (FP64)")
+    assert e_emu <= EMU_TOL
+    assert err <= FWD_TOL
+    assert np.abs(y - ref).max() <= 4 * FWD_TOL * np.abs(ref).max()
+
+
+def test_gradients_match_oracle(torch_cuda):
+    """Loss and every layer's weight and bias gradient over two images against the FP64
+    backward pass.  Targets are kept at least 0.3 away from the outputs so that the L1 sign
+    is the same on both sides."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet
+    params = _params(2)
+    net = ProposalNet(seed=0)
+    net.set_params(_flat(params))
+    rng = np.random.default_rng(7)
+    n, H4, W4 = 2, 19, 23
+    xs = rng.uniform(0.0, 1.0, size=(n, H4, W4, 7)).astype(np.float32)
+    scale = np.array([1.0, 2.0, 0.5])
+    p64 = _f64(params)
+    tg = []
+    for i in range(n):
+        out, _, _ = cnn.forward(p64, xs[i].astype(np.float64))
+        t = out + np.where(rng.uniform(size=out.shape) < 0.5, -1.0, 1.0) * rng.uniform(0.3, 0.8, size=out.shape)
+        tg.append(t.astype(np.float32))
+
+    def reference(store):
+        grads, loss_sum = None, 0.0
+        for i in range(n):
+            out, acts, pre = cnn.forward(p64, xs[i].astype(np.float64), store=store)
+            loss, dout = cnn.l1_loss(out, tg[i].astype(np.float64), scale)
+            g = cnn.backward(p64, acts, pre, dout / n, store=store)
+            loss_sum += loss / n
+            grads = g if grads is None else [(a[0] + b[0], a[1] + b[1]) for a, b in zip(grads, g)]
+        return loss_sum, grads
+
+    loss_emu, g_emu = reference("bf16")
+    loss_ref, g_ref = reference(None)
+    loss, flat = net.gradients(torch.from_numpy(xs).cuda(), torch.from_numpy(np.stack(tg)).cuda(), scale)
+    assert loss == pytest.approx(loss_emu, rel=EMU_TOL)
+    assert loss == pytest.approx(loss_ref, rel=FWD_TOL)
+    got = net.unflatten(flat)
+    for li in range(len(got)):
+        (gw, gb), (ew_, eb_), (rw, rb) = got[li], g_emu[li], g_ref[li]
+        e1, e2 = _nerr(gw, ew_), _nerr(gb, eb_)
+        f1, f2 = _nerr(gw, rw), _nerr(gb, rb)
+        print(f"layer {li}: weight/bias-gradient error {e1:.2e}/{e2:.2e} (bf16 storage), "
+              f"{f1:.2e}/{f2:.2e} (FP64)")
+        assert e1 <= EMU_TOL and e2 <= EMU_TOL
+        assert f1 <= GRAD_TOL and f2 <= GRAD_TOL
+
+
+def test_training_reduces_the_loss(torch_cuda):
+    """Adam steps on a fixed batch: the L1 loss falls well below its starting value."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet
+    net = ProposalNet(seed=4)
+    rng = np.random.default_rng(3)
+    n, H4, W4 = 4, 24, 32
+    x = rng.uniform(0.0, 1.0, size=(n, H4, W4, 7)).astype(np.float32)
+    # a smooth function of the inputs for the network to fit
+    t = np.stack([x[..., 6] * 0.8 + 0.1, (x[..., 0] - x[..., 3]) * 0.2, (x[..., 1] - 0.5) * 0.1], axis=-1)
+    xc, tc = torch.from_numpy(x).cuda(), torch.from_numpy(t.astype(np.float32)).cuda()
+    losses = [net.train_step(xc, tc, 2e-3) for _ in range(60)]
+    print(f"loss {losses[0]:.4f} -> {losses[-1]:.4f}")
+    assert losses[-1] < 0.5 * losses[0]
+
+
+def test_features_and_targets_match_oracle(torch_cuda, tiny_pair):
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(TINY_PARAMS, k_cnn=(1,))
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+    H, W = g.H, g.W
+    lab = random_labels(9, H * W, H, W, params["disp_max"], 0.3).reshape(H, W, 3)
+    g.set_labels(lab.reshape(-1, 3))
+    x = g.cnn_features().cpu().numpy()
+    t = g.cnn_targets().cpu().numpy()
+    xr = cnn.quarter_features(tiny_pair["left"], tiny_pair["right"], lab, params["disp_max"])
+    tr = cnn.quarter_targets(lab, params["disp_max"])
+    assert x.shape == xr.shape and t.shape == tr.shape
+    assert np.abs(x - xr).max() <= 1e-5
+    assert np.abs(t - tr).max() <= 1e-5
+
+
+def test_cnn_propose_matches_oracle(torch_cuda, tiny_pair):
+    """Features, forward pass and upsampling into the handle's proposal map, against the FP64
+    chain: the disparity a u + b v + c and the slopes of every pixel's proposal."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet, Stereo
+    params = dict(TINY_PARAMS, k_cnn=(1,))
+    dmax = params["disp_max"]
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+    H, W = g.H, g.W
+    lab = random_labels(10, H * W, H, W, dmax, 0.2).reshape(H, W, 3)
+    g.set_labels(lab.reshape(-1, 3))
+    p = _params(5, scale=0.7)
+    net = ProposalNet(seed=0)
+    net.set_params(_flat(p))
+    g.cnn_propose(net)
+    prop = g.proposals().cpu().numpy().astype(np.float64)
+    x = cnn.quarter_features(tiny_pair["left"], tiny_pair["right"], lab, dmax)
+    y, _, _ = cnn.forward(_f64(p), x, store="bf16")
+    ref = cnn.upsample_planes(y, H, W, dmax)
+    v, u = np.mgrid[0:H, 0:W]
+    d = prop[..., 0] * u + prop[..., 1] * v + prop[..., 2]
+    d_ref = ref[..., 0] * u + ref[..., 1] * v + ref[..., 2]
+    scale_d = np.abs(y[..., 0]).max() * dmax
+    # features within 1e-5 feed the network; c = d - a u - b v is recovered in FP32
+    assert np.abs(d - d_ref).max() <= 8 * EMU_TOL * scale_d + 1e-3
+    for c in (0, 1):
+        assert np.abs(prop[..., c] - ref[..., c]).max() <= 8 * EMU_TOL * np.abs(y[..., c + 1]).max() + 1e-6
+
+
+def test_map_candidates_in_lockstep_with_oracle(torch_cuda, tiny_pair):
+    """k_cnn = 2 map candidates from the same proposal map (fronto-parallel planes at the
+    rendered disparity) on both sides, group by group as in the propagation lockstep."""
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(TINY_PARAMS, seed=29)
+    gt = tiny_pair["disp"].astype(np.float32)
+    gt_map = np.stack([np.zeros_like(gt), np.zeros_like(gt), gt], axis=-1)
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], k_cnn=(2,), **params)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], k_cnn=(2,), **params)
+    o.init_state()
+    g.set_proposals(gt_map)
+    o.set_proposals(gt_map)
+    assert (g.proposals().cpu().numpy() == gt_map).all()
+    q_prev = g.energy()[1]
+    flips = switched = 0
+    for it in range(2):
+        for grp in range(16):
+            st = g.expand_group(it, 0, grp)
+            acc, _ = o.expand_group(it, 0, grp)
+            assert st.maxflow_limit == 0
+            abc = g.labels()[0].cpu().numpy()
+            lab, _ = o.state()
+            flips += int((abc != lab).any(axis=-1).sum())
+            switched += acc
+            o.set_labels(abc)
+            q = g.energy()[1]
+            assert q <= q_prev
+            q_prev = q
+    print(f"map lockstep: {flips} differing pixels over {switched} switches")
+    assert flips <= max(10, 0.002 * switched)
+    st = g.iterate(1)
+    assert st.evals == g.evals_per_iteration()
+
+
+def test_map_candidates_need_a_map(torch_cuda, tiny_pair):
+    from paper_1603_08328_gb300.lem import LemError, LEM_ERR_ARG, Stereo
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], k_cnn=(1,), **TINY_PARAMS)
+    with pytest.raises(LemError) as e:
+        g.expand_group(0, 0, 0)
+    assert e.value.code == LEM_ERR_ARG
+    g0 = Stereo(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    with pytest.raises(LemError):
+        g0.set_proposals(np.zeros((g0.H, g0.W, 3), np.float32))
+
+
+def test_trained_proposer_lowers_the_energy(torch_cuda):
+    """Self-distillation gain: a network trained on 16 synthetic 384x288 scenes (inputs: the
+    labels after 1-3 iterations; targets: the labels after 8) and used as k_cnn = 1 map
+    candidate at the finest level reaches a lower energy after two iterations on a held-out
+    scene than the method alone."""
+    from paper_1603_08328_gb300 import proposer
+    from paper_1603_08328_gb300.lem import ProposalNet, Stereo
+    from synth import workload_pair
+    pairs = [workload_pair("train_384x288", 100 + i) for i in range(16)]
+    x, t = proposer.make_dataset(pairs, n_in=(1, 2, 3), n_out=8, disp_max=48.0, seed=3)
+    net = ProposalNet(seed=1)
+    losses = proposer.train(net, x, t, steps=1000, batch=8, lr=2e-3)
+    assert np.mean(losses[-50:]) < 0.7 * np.mean(losses[:50])
+    test = workload_pair("train_384x288", 901)
+    base = Stereo(test["left"], test["right"], disp_max=48.0, seed=7)
+    with_net = Stereo(test["left"], test["right"], disp_max=48.0, seed=7, k_cnn=(1, 0, 0))
+    e_base = [e for e, _, _ in proposer.solve(base, 2)]
+    e_net = [e for e, _, _ in proposer.solve(with_net, 2, net)]
+    print(f"energy after 1, 2 iterations: {e_base} alone, {e_net} with the proposer")
+    assert e_net[1] < e_base[1]

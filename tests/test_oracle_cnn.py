@@ -64,3 +64,78 @@ def test_input_gradient_by_finite_differences():
         xm = x.copy(); xm[idx] -= eps
         fd = ((cnn.conv3x3(xp, w) * dy).sum() - (cnn.conv3x3(xm, w) * dy).sum()) / (2 * eps)
         assert dx[idx] == pytest.approx(fd, rel=1e-6)
+
+
+def test_quarter_features_and_targets_of_a_global_plane():
+    """A single plane d = a u + b v + c: the 4x4 block mean of d is d at the block centre
+    (d is linear), the block means of a, b are a, b, and constant colours stay constant."""
+    H, W, dmax = 16, 20, 40.0
+    a, b, c = 0.3, -0.2, 9.0
+    lab = np.broadcast_to(np.array([a, b, c]), (H, W, 3)).copy()
+    left = np.full((H, W, 3), 51.0)
+    right = np.full((H, W, 3), 102.0)
+    x = cnn.quarter_features(left, right, lab, dmax)
+    t = cnn.quarter_targets(lab, dmax)
+    for V in range(H // 4):
+        for U in range(W // 4):
+            d_centre = a * (4 * U + 1.5) + b * (4 * V + 1.5) + c
+            assert np.allclose(x[V, U, :3], 0.2) and np.allclose(x[V, U, 3:6], 0.4)
+            assert x[V, U, 6] == pytest.approx(d_centre / dmax, rel=1e-12)
+            assert t[V, U] == pytest.approx([d_centre / dmax, a, b], rel=1e-12)
+
+
+def test_upsampling_reproduces_a_global_plane():
+    """Bilinear interpolation of a linear function is exact: (d/dmax, a, b) sampled from one
+    plane at the quarter-cell centres gives that plane back at every pixel between the first
+    and last centres (and a, b everywhere)."""
+    H, W, dmax = 23, 30, 50.0
+    a, b, c = -0.15, 0.4, 12.5
+    H4, W4 = (H + 3) // 4, (W + 3) // 4
+    y = np.zeros((H4, W4, 3))
+    for V in range(H4):
+        for U in range(W4):
+            y[V, U] = ((a * (4 * U + 1.5) + b * (4 * V + 1.5) + c) / dmax, a, b)
+    out = cnn.upsample_planes(y, H, W, dmax)
+    assert np.allclose(out[..., 0], a) and np.allclose(out[..., 1], b)
+    inner = out[2:4 * (H4 - 1) + 2, 2:4 * (W4 - 1) + 2]
+    assert np.allclose(inner[..., 2], c, atol=1e-9)
+
+
+def test_round_bf16_ties_to_even_and_matches_torch():
+    """bfloat16 keeps 8 significant bits: 1 + 2^-8 is a tie that goes to the even 1.0,
+    1 + 3 * 2^-8 a tie that goes up to 1 + 2^-6, and torch's CPU conversion agrees on
+    random values over many binades."""
+    assert cnn.round_bf16([1.0 + 2.0 ** -8])[0] == 1.0
+    assert cnn.round_bf16([1.0 + 3 * 2.0 ** -8])[0] == 1.0 + 2.0 ** -6
+    assert cnn.round_bf16([1.0 + 2.0 ** -8 + 2.0 ** -20])[0] == 1.0 + 2.0 ** -7
+    assert cnn.round_bf16([-3.0])[0] == -3.0
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x = (rng.normal(size=4000) * np.exp2(rng.integers(-30, 30, size=4000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert (cnn.round_bf16(x) == ref).all()
+
+
+def test_bf16_storage_model_is_the_rounded_network():
+    """store='bf16' is the plain network applied to rounded weights and inputs when every
+    activation is already a bfloat16 value (then the stored roundings change nothing)."""
+    rng = np.random.default_rng(6)
+    layers = [(7, 4), (4, 3)]
+    params = [(rng.normal(size=(3, 3, ci, co)), rng.normal(size=co)) for ci, co in layers]
+    x = rng.normal(size=(5, 6, 7))
+    out_s, acts_s, _ = cnn.forward(params, x, store="bf16")
+    rp = [(cnn.round_bf16(w), b) for w, b in params]
+    h1 = np.maximum(cnn.conv3x3(cnn.round_bf16(x), rp[0][0], rp[0][1]), 0.0)
+    assert (acts_s[1] == cnn.round_bf16(h1)).all()
+    assert np.allclose(out_s, cnn.conv3x3(cnn.round_bf16(h1), rp[1][0], rp[1][1]), rtol=0, atol=1e-12)
+
+
+def test_targets_clamp_steep_slopes():
+    """Mean slopes beyond +-1 are clamped; the disparity channel is not."""
+    lab = np.zeros((4, 4, 3))
+    lab[..., 0] = 3.0
+    lab[..., 1] = -0.5
+    t = cnn.quarter_targets(lab, 10.0)
+    assert t[0, 0, 1] == 1.0 and t[0, 0, 2] == -0.5
+    # d = 3 u - 0.5 v averaged over the block: 3 * 1.5 - 0.5 * 1.5 = 3.75, over dmax = 10
+    assert t[0, 0, 0] == pytest.approx(0.375)

@@ -506,3 +506,51 @@ def test_batched_visits_are_exact_moves(tiny_pair):
     for _ in range(30):
         y, x = int(rng.integers(0, o4.H)), int(rng.integers(0, o4.W))
         assert cost[y, x] == pytest.approx(o4.phi_def(lab[y, x], x, y), abs=1e-11)
+
+
+def test_map_proposals_draw_the_propagation_pixel(tiny_pair):
+    """A map candidate is the proposal map's label at a pixel r of the centre cell, drawn
+    exactly as the propagation proposal draws r; a constant map gives its constant."""
+    rng = np.random.default_rng(5)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    M = _random_state(o, rng)
+    const = np.broadcast_to(np.float32([0.25, -0.5, 7.0]), M.shape)
+    cell = (20, 10, 5, 5)
+    for k in range(30):
+        st = oracle.proposal_stream(11, 1, 0, 4, 2, k)
+        assert (oracle.propose_map(M, st, cell) == oracle.propose(M, st, cell, 0, 0, 0, 0.0, 15.0)).all()
+        assert (oracle.propose_map(const, st, cell) == np.float32([0.25, -0.5, 7.0])).all()
+
+
+def test_map_proposals_are_exact_moves_and_help(tiny_pair):
+    """Map candidates sit between propagation and perturbation: every move stays an exact
+    expansion (energy never increases), a cleared map reproduces k_cnn = 0 bit for bit, and a
+    map of the true disparities (fronto-parallel planes) beats one iteration without it."""
+    kw = dict(TINY_PARAMS)
+    gt = tiny_pair["disp"].astype(np.float32)
+    gt_map = np.stack([np.zeros_like(gt), np.zeros_like(gt), gt], axis=-1)
+    om = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], k_cnn=(2,), **kw)
+    oc = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], k_cnn=(2,), **kw)
+    o0 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **kw)
+    for o in (om, oc, o0):
+        o.init_state()
+    om.set_proposals(gt_map)
+    oc.set_proposals(gt_map)
+    oc.set_proposals(None)
+    q_prev = om.energy()[1]
+    for g in range(16):
+        om.expand_group(0, 0, g)
+        q = om.energy()[1]
+        assert q <= q_prev
+        q_prev = q
+    oc.iterate(0)
+    o0.iterate(0)
+    lc, cc = oc.state(); l0, c0 = o0.state()
+    assert (lc == l0).all() and (cc == c0).all()
+    v, u = np.mgrid[0:om.H, 0:om.W]
+
+    def bad(o):
+        lab, _ = o.state()
+        return (np.abs(lab[..., 0] * u + lab[..., 1] * v + lab[..., 2] - gt) > 1.0).mean()
+    assert bad(om) < bad(o0) - 0.02
+    assert om.energy()[1] < o0.energy()[1]
