@@ -8,6 +8,13 @@ random initialisation; warm-up steps run on a separate handle.  L2 is flushed
 between timed steps; each step is timed with CUDA events on the library's
 stream.
 
+The launch configuration of every level is chosen by the library's autotuner
+on the warm-up handle (it changes only the time, never a label).  A second
+block measures the time to reach the plain method's energy: 10 iterations of
+the plain method give E_plain; the time to E <= 1.001 E_plain is taken for the
+plain method and for the method with learned proposals (when trained weights
+are present), CNN inference included.
+
 Prints one JSON line.  --impl reference times the CPU oracle instead.
 """
 from __future__ import annotations
@@ -41,6 +48,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
+    ap.add_argument("--no-time-to-energy", action="store_true")
     return ap.parse_args()
 
 
@@ -248,6 +257,58 @@ def run_reference(args):
 
 # --- GPU -------------------------------------------------------------------------
 
+def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
+    """Time (CUDA events around each outer iteration, learned proposals' inference
+    included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
+    the plain method, for the plain method and for the learned proposer (k_cnn = 1 at the
+    finest level) when its trained weights are present."""
+    import torch
+    from paper_1603_08328_gb300 import proposer
+
+    def run(g, net, n):
+        curve, t = [], 0.0
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if net is not None:
+                g.cnn_propose(net)
+            g.check(lem.lem_expand_iteration(g.h, 1, None))
+            b.record(stream)
+            b.synchronize()
+            t += a.elapsed_time(b)
+            curve.append((g.energy()[0], t))
+        return curve
+
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, **params)
+    plain = run(g, None, n_plain)
+    g.close()
+    target = 1.001 * plain[-1][0]
+
+    def first(curve):
+        for k, (e, t) in enumerate(curve):
+            if e <= target:
+                return k + 1, t
+        return None, None
+
+    pi, pt = first(plain)
+    out = {"target_energy": target, "plain_energy": plain[-1][0], "plain_iters": pi, "plain_ms": pt,
+           "plain_curve": [[round(e, 1), round(t, 2)] for e, t in plain]}
+    if not os.path.exists(proposer.WEIGHTS):
+        out["learned"] = "no trained weights"
+        return out
+    net = proposer.load()
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, k_cnn=(1, 0, 0), **params)
+    curve = run(g, net, max_iters)
+    g.close()
+    li, lt = first(curve)
+    out.update({"learned_iters": li, "learned_ms": lt, "learned_energy": curve[-1][0],
+                "learned_curve": [[round(e, 1), round(t, 2)] for e, t in curve],
+                "speedup": (pt / lt) if (pt and lt) else None,
+                "learned_config": "k_cnn = (1, 0, 0), proposal map refreshed before every iteration"})
+    net.close()
+    return out
+
 def run_lem(args):
     import numpy as np
     import torch
@@ -267,13 +328,22 @@ def run_lem(args):
     stream = torch.cuda.current_stream()
     H, W = pair["left"].shape[:2]
 
-    # warm-up: a separate handle, W outer iterations
+    # warm-up: a separate handle, W outer iterations, then the autotuner on its state
     warm = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1000 + rank, **PARAMS)
     warm.iterate(max(1, args.warmup), stats=False)
+    tuned = {}
+    tuning = None
+    if not args.no_tune:
+        t = warm.autotune(repeats=2)
+        tuned = dict(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval),
+                     level_strip_rows=list(t.strip_rows))
+        tuning = dict(tuned, ms=[round(x, 4) for x in t.ms], ms_default=[round(x, 4) for x in t.ms_default],
+                      configs_tried=t.configs_tried)
     torch.cuda.synchronize()
     warm.close()
+    params = dict(PARAMS, **tuned)
 
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **PARAMS)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **params)
     p = dict(gf_radius=g.params.gf_radius, n_levels=g.params.n_levels, cell=list(g.params.cell),
              k_prop=list(g.params.k_prop), k_rand=list(g.params.k_rand))
     work = launches_and_work(H, W, p)
@@ -304,7 +374,7 @@ def run_lem(args):
 
     # per-launch durations of the expansion kernel (one launch per lem_expand_group call),
     # on a fresh handle over one outer iteration, L2 flushed before every launch
-    g2 = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **PARAMS)
+    g2 = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **params)
     per, cut = [], []
     for wk in work:
         flush.zero_()
@@ -347,7 +417,7 @@ def run_lem(args):
     for j in range(args.e2e_jobs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        prm = lem.lem_default_params(seed=7 + j, **PARAMS)
+        prm = lem.lem_default_params(seed=7 + j, **params)
         prm.stream = stream.cuda_stream
         li = lem.lem_image(hl.data_ptr(), H, W, 3 * W, 0)
         ri = lem.lem_image(hr.data_ptr(), H, W, 3 * W, 0)
@@ -359,6 +429,8 @@ def run_lem(args):
     e2e_job = max_over_ranks(sum(e2e_t) / len(e2e_t), dist)
     e2e_v = world * n_iters_job * evals_per_step / e2e_job
 
+    tte = None if args.no_time_to_energy else time_to_energy(lem, pair, params, stream, seed=21 + rank)
+
     if rank != 0:
         return
     value = world * evals_per_step * args.steps / t_max
@@ -369,17 +441,21 @@ def run_lem(args):
         "config": {"workload": WORKLOAD, "height": H, "width": W, "disp_max": 60, "cells": p["cell"],
                    "window": 4 * p["gf_radius"] + 1, "step": "one outer iteration (48 level-group launches)",
                    "schedule": "sequential proposals (Algorithm 2)", "l2": "flushed between timed steps",
+                   "launch_config": tuning or "default",
                    "parallelism": f"replicas x{world}", "evals_per_step": evals_per_step},
         "e2e": {"value": e2e_v, "unit": METRIC, "h2d_bytes_per_step": 2 * H * W * 3, "d2h_bytes_per_step": H * W * 4,
                 "step": f"one job: host images -> lem_create -> {n_iters_job} iterations -> host disparity",
                 "jobs": args.e2e_jobs, "ms_per_job": 1e3 * e2e_job},
-        "gpu_launches": len(work) * args.steps,
+        # the first step launches the 48 (level, group) kernels directly; later steps replay
+        # them as one CUDA graph that also increments the device iteration index
+        "gpu_launches": len(work) * args.steps + max(0, args.steps - 1),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic_from_profile("k_expand_group"), "kernel": "k_expand_group",
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
                      "launch_avg_ms": 1e3 * launch_avg},
         "clocks": clk.summary(),
         "energy": {"before": e0, "after": e1},
+        "time_to_energy": tte,
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,

@@ -99,6 +99,13 @@ typedef struct {
                              uniformly from the centre cell (as propagation draws f_r); the
                              perturbations follow.  Needs a map (lem_set_proposals or
                              lem_cnn_propose) before the first expansion. */
+    /* Launch configuration of the expansion kernel per grid level (0 = the default).
+     * None of them changes a result: each cost is summed in a fixed order by one
+     * thread and the cut is the unique minimal one.  lem_autotune picks them. */
+    int level_threads[3];     /* threads per CTA: 256, 512 or 1024; default by region size
+                                 (<= 400 nodes: 256, <= 2500: 512, else 1024)               */
+    int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval */
+    int level_strip_rows[3];  /* rows per strip of the cost pipeline; default strip_rows         */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -292,6 +299,30 @@ int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int
                              uint8_t *take_alpha, int64_t *flow, int32_t *status, int max_rounds, int gr_interval,
                              void *stream);
 
+/* Autotuner result: the per-level launch configuration chosen, its time per
+ * (level, group) launch and that of the default configuration. */
+typedef struct {
+    int threads[3];
+    int gr_interval[3];
+    int strip_rows[3];
+    float ms[3];           /* mean time of one (level, group) launch, chosen configuration */
+    float ms_default[3];   /* same, default configuration                                   */
+    int configs_tried;     /* candidate configurations timed (all levels)                   */
+} lem_tuning;
+
+/* Times the expansion kernel of every level on this handle's own images and
+ * labels for each candidate configuration (threads {256, 512, 1024} x
+ * gr_interval {8, 16, 32, 64} x strip_rows {8, 16, 32}; candidates whose shared
+ * memory does not fit are skipped), `repeats` launches of groups 0 and 10 of
+ * the level at the handle's current iteration each, and keeps the fastest per
+ * level in the handle's parameters (level_threads, level_gr_interval,
+ * level_strip_rows).  Labels, cost cache and statistics counters are restored
+ * after every trial, so the handle's state is unchanged; a captured iteration
+ * graph is rebuilt on the next lem_expand_iteration.  Synchronises the stream.
+ * out may be NULL.  Errors: LEM_ERR_ARG (repeats outside 1..100),
+ * LEM_ERR_MAXFLOW_LIMIT (a trial cut hit the round limit), LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_autotune(lem_handle *h, int repeats, lem_tuning *out);
+
 /* Number of pixel-label cost evaluations in one outer iteration (sum over all
  * region visits of |R| x proposals).  Host only. */
 int64_t lem_evals_per_iteration(const lem_handle *h);
@@ -352,8 +383,9 @@ int lem_cnn_features(lem_handle *h, int pair, float *x);
 int lem_cnn_targets(lem_handle *h, int pair, float *t);
 /* Features, forward pass and bilinear upsampling of (d, a, b) to a plane per
  * pixel (c = d - a u - b v), stored as the proposal map of every pair of `h`.
- * Uses the handle's stream.  Errors: LEM_ERR_ARG (also when every k_cnn is 0),
- * LEM_ERR_OOM, LEM_ERR_CUDA. */
+ * Stream-ordered on the handle's stream (no synchronisation; the first call
+ * allocates the handle's quarter-resolution buffers).  Errors: LEM_ERR_ARG
+ * (also when every k_cnn is 0), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_propose(lem_cnn *net, lem_handle *h);
 
 #ifdef __cplusplus

@@ -28,6 +28,7 @@ struct lem_handle {
     float *phiA = nullptr;
     float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
     bool prop_set = false;
+    float *cnn_buf = nullptr;           // network input / output of one pair (lem_cnn_propose)
     long long *e_part = nullptr, *e_out = nullptr;
     lem::Counters *ctr = nullptr;
     int *n_fp64 = nullptr;
@@ -139,11 +140,20 @@ int check_params(const lem_params *p) {
     if (p->store_dtype != LEM_STORE_F32 && p->store_dtype != LEM_STORE_F16 && p->store_dtype != LEM_STORE_BF16)
         return fail(nullptr, LEM_ERR_ARG, "store_dtype must be LEM_STORE_F32, LEM_STORE_F16 or LEM_STORE_BF16");
     if (p->max_rounds < 1 || p->gr_interval < 1) return fail(nullptr, LEM_ERR_ARG, "max_rounds/gr_interval must be >= 1");
-    if (p->strip_rows < 1 || p->strip_rows > 64) return fail(nullptr, LEM_ERR_ARG, "strip_rows must be 1..64");
+    if (p->strip_rows < 4 || p->strip_rows > 64 || p->strip_rows % 4)
+        return fail(nullptr, LEM_ERR_ARG, "strip_rows must be a multiple of 4 in [4, 64]");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
         return fail(nullptr, LEM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+    for (int l = 0; l < 3; ++l) {
+        const int t = p->level_threads[l];
+        if (t != 0 && t != 256 && t != 512 && t != 1024)
+            return fail(nullptr, LEM_ERR_ARG, "level_threads must be 0, 256, 512 or 1024");
+        if (p->level_gr_interval[l] < 0) return fail(nullptr, LEM_ERR_ARG, "level_gr_interval must be >= 0");
+        if (p->level_strip_rows[l] < 0 || p->level_strip_rows[l] > 64 || p->level_strip_rows[l] % 4)
+            return fail(nullptr, LEM_ERR_ARG, "level_strip_rows must be 0 or a multiple of 4 up to 64");
+    }
     return LEM_OK;
 }
 
@@ -164,6 +174,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->lab);
     cudaFree(h->phiA);
     cudaFree(h->prop);
+    cudaFree(h->cnn_buf);
     cudaFree(h->e_part);
     cudaFree(h->e_out);
     cudaFree(h->ctr);
@@ -504,9 +515,13 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     lv.k_prop = h->p.k_prop[level];
     lv.k_rand = h->p.k_rand[level];
     lv.k_cnn = h->p.k_cnn[level];
+    lv.threads = h->p.level_threads[level];
     if (h->prop && !h->prop_set)
         return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
-    LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kparams(h), lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
+    lem::KParams kp = kparams(h);
+    if (h->p.level_gr_interval[level] > 0) kp.gr_interval = h->p.level_gr_interval[level];
+    if (h->p.level_strip_rows[level] > 0) kp.T = h->p.level_strip_rows[level];
+    LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                          h->lab, h->phiA, h->prop, h->ctr, st));
     return LEM_OK;
@@ -765,11 +780,10 @@ int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
     if (!net) return fail(h, LEM_ERR_ARG, "network is NULL");
     if (!h->prop) return fail(h, LEM_ERR_ARG, "every k_cnn is 0: the handle keeps no proposal map");
     if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
-    // quarter-resolution buffers sized for the largest pair
+    // quarter-resolution buffers sized for the largest pair, kept by the handle
     const size_t n4 = (size_t)((h->maxH + 3) / 4) * ((h->maxW + 3) / 4);
-    float *buf = nullptr;
-    LEM_CUDA(h, cudaMalloc(&buf, sizeof(float) * n4 * 10));
-    float *x = buf, *y = buf + 7 * n4;
+    if (!h->cnn_buf) LEM_CUDA(h, cudaMalloc(&h->cnn_buf, sizeof(float) * n4 * 10));
+    float *x = h->cnn_buf, *y = h->cnn_buf + 7 * n4;
     int rc = LEM_OK;
     for (int b = 0; b < h->B && rc == LEM_OK; ++b) {
         const lem::PairDesc &pd = h->pairs[b];
@@ -787,12 +801,111 @@ int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
         e = lem::launch_cnn_upsample(y, pd.H, pd.W, dmax, h->prop + pd.off, h->st);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "lem_cnn_propose upsample");
     }
-    // the buffer is read by kernels on h->st: free it once they are done
-    cudaError_t e = cudaStreamSynchronize(h->st);
-    cudaFree(buf);
     if (rc != LEM_OK) return rc;
-    if (e != cudaSuccess) return cuda_fail(h, e, "lem_cnn_propose");
     h->prop_set = true;
+    return LEM_OK;
+}
+
+int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (repeats < 1 || repeats > 100) return fail(h, LEM_ERR_ARG, "repeats must be 1..100");
+    if (h->prop && !h->prop_set) return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set");
+    const size_t n = (size_t)h->total;
+    float4 *save = nullptr;
+    LEM_CUDA(h, cudaMalloc(&save, sizeof(float4) * n));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    lem::Counters ctr0{};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save, h->lab, sizeof(float4) * n, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctr0, h->ctr, sizeof(ctr0), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    lem_tuning res{};
+    int rc = e == cudaSuccess ? LEM_OK : cuda_fail(h, e, "lem_autotune setup");
+    const lem_params keep = h->p;
+    static const int kThreads[3] = {256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[3] = {8, 16, 32};
+    // time of `repeats` launches of groups 0 and 10 at `level`, state restored after each;
+    // < 0 when the configuration cannot launch
+    auto trial = [&](int level, float &ms) -> int {
+        float tot = 0.f;
+        for (int r = 0; r < repeats; ++r)
+            for (int g : {0, 10}) {
+                cudaError_t ce = cudaEventRecord(ev[0], h->st);
+                if (ce != cudaSuccess) return cuda_fail(h, ce, "lem_autotune event");
+                int rr = expand_group_impl(h, h->iter, level, g, h->st);
+                if (rr != LEM_OK) {
+                    cudaGetLastError();
+                    ms = -1.f;
+                    return LEM_OK;  // configuration does not launch: skipped
+                }
+                ce = cudaEventRecord(ev[1], h->st);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(ev[1]);
+                float t = 0.f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, ev[0], ev[1]);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(h->lab, save, sizeof(float4) * n, cudaMemcpyDeviceToDevice, h->st);
+                if (ce != cudaSuccess) return cuda_fail(h, ce, "lem_autotune trial");
+                tot += t;
+            }
+        ms = tot / (2.f * repeats);
+        return LEM_OK;
+    };
+    for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) {
+        // the default configuration first
+        h->p.level_threads[l] = 0;
+        h->p.level_gr_interval[l] = 0;
+        h->p.level_strip_rows[l] = 0;
+        float best = -1.f;
+        rc = trial(l, best);
+        res.ms_default[l] = best;
+        const int s3 = 3 * h->p.cell[l];
+        int bt = lem::threads_for_nodes(std::min(h->maxW, s3) * std::min(h->maxH, s3));
+        int bg = keep.gr_interval, bs = keep.strip_rows;
+        for (int ti = 0; ti < 3 && rc == LEM_OK; ++ti)
+            for (int gi = 0; gi < 4 && rc == LEM_OK; ++gi)
+                for (int si = 0; si < 3 && rc == LEM_OK; ++si) {
+                    h->p.level_threads[l] = kThreads[ti];
+                    h->p.level_gr_interval[l] = kGr[gi];
+                    h->p.level_strip_rows[l] = kRows[si];
+                    float ms = -1.f;
+                    rc = trial(l, ms);
+                    ++res.configs_tried;
+                    if (rc == LEM_OK && ms >= 0.f && (best < 0.f || ms < best)) {
+                        best = ms;
+                        bt = kThreads[ti];
+                        bg = kGr[gi];
+                        bs = kRows[si];
+                    }
+                }
+        h->p.level_threads[l] = bt;
+        h->p.level_gr_interval[l] = bg;
+        h->p.level_strip_rows[l] = bs;
+        res.threads[l] = bt;
+        res.gr_interval[l] = bg;
+        res.strip_rows[l] = bs;
+        res.ms[l] = best;
+    }
+    // statistics counters back to their values before tuning
+    lem::Counters ctr1{};
+    if (rc == LEM_OK) {
+        e = cudaMemcpyAsync(&ctr1, h->ctr, sizeof(ctr1), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctr, &ctr0, sizeof(ctr0), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lem_autotune restore");
+        else if (ctr1.limit_hits != ctr0.limit_hits)
+            rc = fail(h, LEM_ERR_MAXFLOW_LIMIT, "a trial cut hit the push-relabel round limit");
+    }
+    if (rc != LEM_OK) h->p = keep;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaFree(save);
+    if (rc != LEM_OK) return rc;
+    // the captured graph holds the old launch configuration
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    if (out) *out = res;
     return LEM_OK;
 }
 

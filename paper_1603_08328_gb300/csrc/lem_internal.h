@@ -46,6 +46,7 @@ struct Level {
     int s;              // cell size
     int k_prop, k_rand;
     int k_cnn;          // map candidates (proposal indices k_prop .. k_prop + k_cnn - 1)
+    int threads;        // CTA size of the expansion kernel (0: by region size)
 };
 
 // Per-launch counters written by the expansion kernels.
@@ -63,6 +64,9 @@ struct Counters {
 size_t unary_smem_bytes(const KParams &kp, int H, int W, int rw, int rh);
 // Shared-memory bytes of the CTA min-cut for a w x h region.
 size_t cut_smem_bytes(int w, int h);
+
+// CTA size of the expansion and cut kernels for regions of n nodes
+inline int threads_for_nodes(int n) { return n <= 400 ? 256 : (n <= 2500 ? 512 : 1024); }
 
 // bytes per packed image pixel in format fmt
 inline size_t px_bytes(int fmt) { return fmt == LEM_STORE_F32 ? 16 : 8; }

@@ -367,12 +367,29 @@ __device__ __forceinline__ float strided_sum(const float *base, int stride, int 
     for (; i < count; ++i) a0 += base[i * stride];
     return (a0 + a1) + (a2 + a3);
 }
-// the same over `count` consecutive rows of a ring of RS rows (row pitch rs) from slot s0
-__device__ __forceinline__ float ring_sum(const float *base, int rs, int RS, int s0, int count) {
-    const int c1 = min(count, RS - s0);
-    return strided_sum(base + s0 * rs, rs, c1) + strided_sum(base, rs, count - c1);
-}
 __device__ __forceinline__ int ring_next(int s, int RS) { return s + 1 == RS ? 0 : s + 1; }
+// the same over `count` consecutive rows of a ring of RS rows (row pitch rs) from
+// slot s0, with the same association as strided_sum over those rows in order
+// (wherever the ring wraps)
+__device__ __forceinline__ float ring_sum(const float *base, int rs, int RS, int s0, int count) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int i = 0, s = s0;
+    for (; i + 4 <= count; i += 4) {
+        a0 += base[s * rs];
+        s = ring_next(s, RS);
+        a1 += base[s * rs];
+        s = ring_next(s, RS);
+        a2 += base[s * rs];
+        s = ring_next(s, RS);
+        a3 += base[s * rs];
+        s = ring_next(s, RS);
+    }
+    for (; i < count; ++i) {
+        a0 += base[s * rs];
+        s = ring_next(s, RS);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
 
 // Thread layout of one pipeline stage over an R x C item grid: threads form
 // rows of min(C, nt) columns; the (single) division happens once per stage.
@@ -396,8 +413,11 @@ struct Grid2 {
 //
 // Strip pipeline: M rows enter a ring of T + 2r' rows of the four channels
 // (rho, (I - c) rho); every T rows of K (R grown by r') get vertical then
-// horizontal window sums and their a_k, b_k, which enter a second ring; every
-// T rows of R get the window means of a_k, b_k and phi.
+// horizontal window sums and their a_k, b_k, which enter a second ring of
+// T + 2r' + 4 rows; every T rows of R get the window means of a_k, b_k and phi.
+// Every sliding window sum restarts at rows (and columns) Ky0 + 4m, Ry0 + 4m,
+// Kx0 + 4m, Rx0 + 4m and is accumulated by one thread in a fixed order, so with
+// T a multiple of 4 the result does not depend on T or on the CTA size.
 __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                              float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, r = kp.r, T = kp.T;
@@ -407,12 +427,12 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
     const int Kx0 = max(0, Rx0 - r), Kx1 = min(W, Rx0 + Rw + r);
     const int Ky0 = max(0, Ry0 - r), Ky1 = min(H, Ry0 + Rh + r);
     const int Mw = Mx1 - Mx0, Kw = Kx1 - Kx0;
-    const int RS = T + 2 * r;
+    const int RS = T + 2 * r, RSA = RS + 4;
     float *Xr = sm;                          // [RS][4][Mw]  raw-cost channels of M rows (ring)
     float *Vb = Xr + (size_t)RS * 4 * Mw;    // [T][4][Mw]   vertical sums (also [T][4][Kw])
     float *Bb = Vb + (size_t)T * 4 * Mw;     // [T][4][Kw]   box sums      (also [T][4][Rw])
-    float *ABr = Bb + (size_t)T * 4 * Kw;    // [RS][4][Kw]  a_k, b_k of K rows (ring)
-    int *rowI = (int *)(ABr + (size_t)RS * 4 * Kw);  // [RS] integer part of the row warp offset
+    float *ABr = Bb + (size_t)T * 4 * Kw;    // [RSA][4][Kw] a_k, b_k of K rows (ring)
+    int *rowI = (int *)(ABr + (size_t)RSA * 4 * Kw);  // [RS] integer part of the row warp offset
     float *rowF = (float *)(rowI + RS);              // [RS] fractional part
 
     const int fmt = P.fmt;
@@ -435,7 +455,9 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
     int kSlot = 0;  // ring slot of row kNext in ABr
     for (int p0 = Ry0; p0 < Ry0 + Rh; p0 += T) {
         const int p1 = min(Ry0 + Rh, p0 + T);
-        const int kNeed = min(Ky1, p1 + r);
+        // K rows are computed in chunks that start at Ky0 + 4m: the rows needed
+        // up to p1 + r, rounded up to that grid (at most 3 rows ahead)
+        const int kNeed = min(Ky1, Ky0 + ((p1 + r - Ky0 + 3) & ~3));
         while (kNext < kNeed) {
             const int k0 = kNext, k1 = min(kNeed, k0 + T);
             const int mNeed = min(My1, k1 + r);
@@ -574,7 +596,7 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                     const int ky = k0 + row;
                     const int ny = min(H - 1, ky + r) - max(0, ky - r) + 1;
                     int slot = kSlot + row;
-                    if (slot >= RS) slot -= RS;
+                    if (slot >= RSA) slot -= RSA;
                     float *A = ABr + slot * 4 * Kw;
                     const float *B = Bb + row * 4 * Kw;
                     const float4 *G = P.gst + 3 * ((size_t)ky * W + Kx0);
@@ -600,7 +622,7 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                 }
             }
             kSlot += k1 - k0;
-            if (kSlot >= RS) kSlot -= RS;
+            if (kSlot >= RSA) kSlot -= RSA;
             kNext = k1;
             __syncthreads();
         }
@@ -616,20 +638,20 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
                         const int py0 = p0 + 4 * grp, py1 = min(p1, py0 + 4);
                         const int ylo = max(0, py0 - r), yhi = min(H - 1, py0 + r);
                         int sIn = kSlot - (kNext - ylo);
-                        if (sIn < 0) sIn += RS;
-                        float sm = ring_sum(A, rs, RS, sIn, yhi - ylo + 1);
+                        if (sIn < 0) sIn += RSA;
+                        float sm = ring_sum(A, rs, RSA, sIn, yhi - ylo + 1);
                         V[(py0 - p0) * rs] = sm;
                         int sA = sIn + (yhi - ylo + 1);
-                        if (sA >= RS) sA -= RS;
+                        if (sA >= RSA) sA -= RSA;
                         int sO = sIn;
                         for (int py = py0 + 1; py < py1; ++py) {
                             if (py + r <= H - 1) {
                                 sm += A[sA * rs];
-                                sA = ring_next(sA, RS);
+                                sA = ring_next(sA, RSA);
                             }
                             if (py - r - 1 >= 0) {
                                 sm -= A[sO * rs];
-                                sO = ring_next(sO, RS);
+                                sO = ring_next(sO, RSA);
                             }
                             V[(py - p0) * rs] = sm;
                         }
@@ -1351,13 +1373,12 @@ size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
     const int r = kp.r, T = kp.T;
     const int Mw = std::min(W, rw + 4 * r), Kw = std::min(W, rw + 2 * r);
     (void)rh;
-    const int RS = T + 2 * r;
-    return sizeof(float) * ((size_t)RS * 4 * Mw + (size_t)T * 4 * Mw + (size_t)T * 4 * Kw + (size_t)RS * 4 * Kw +
+    const int RS = T + 2 * r, RSA = RS + 4;
+    return sizeof(float) * ((size_t)RS * 4 * Mw + (size_t)T * 4 * Mw + (size_t)T * 4 * Kw + (size_t)RSA * 4 * Kw +
                             2 * (size_t)RS);
 }
 
 // threads per CTA for a region of n nodes: about 4-8 nodes per thread
-int threads_for_nodes(int n) { return n <= 400 ? 256 : (n <= 2500 ? 512 : 1024); }
 
 cudaError_t set_smem(const void *fn, size_t bytes) {
     if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1462,7 +1483,9 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     const int s = lv.s;
     const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
     const size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
-    const int nt = threads_for_nodes(rw * rh);
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
+    if (nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
     if (nt == 256)
         return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
     if (nt == 512)

@@ -41,7 +41,13 @@ class lem_params(C.Structure):
         ("store_dtype", C.c_int), ("cond_fp64", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p),
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
+        ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
     ]
+
+
+class lem_tuning(C.Structure):
+    _fields_ = [("threads", C.c_int * 3), ("gr_interval", C.c_int * 3), ("strip_rows", C.c_int * 3),
+                ("ms", C.c_float * 3), ("ms_default", C.c_float * 3), ("configs_tried", C.c_int)]
 
 
 class lem_region(C.Structure):
@@ -105,6 +111,8 @@ def lib():
         L.lem_cnn_features.argtypes = [H, C.c_int, vp]
         L.lem_cnn_targets.argtypes = [H, C.c_int, vp]
         L.lem_cnn_propose.argtypes = [N, H]
+        L.lem_autotune.argtypes = [H, C.c_int, P(lem_tuning)]
+        L.lem_autotune.restype = C.c_int
         for name in ("lem_set_proposals", "lem_get_proposals", "lem_cnn_create", "lem_cnn_destroy",
                      "lem_cnn_get_params", "lem_cnn_set_params", "lem_cnn_forward", "lem_cnn_gradients",
                      "lem_cnn_train_step", "lem_cnn_features", "lem_cnn_targets", "lem_cnn_propose"):
@@ -132,7 +140,7 @@ def lem_default_params(**overrides) -> lem_params:
     for k, v in overrides.items():
         if k == "lambda":
             k = "lam"
-        if k in ("cell", "k_prop", "k_rand", "k_cnn"):
+        if k in ("cell", "k_prop", "k_rand", "k_cnn", "level_threads", "level_gr_interval", "level_strip_rows"):
             v = list(v) + [0] * (3 - len(v))
             v = (C.c_int * 3)(*v)
         setattr(p, k, v)
@@ -244,6 +252,10 @@ def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, 
 
 def lem_evals_per_iteration(h) -> int:
     return lib().lem_evals_per_iteration(h)
+
+
+def lem_autotune(h, repeats, out=None):
+    return lib().lem_autotune(h, repeats, C.byref(out) if out is not None else None)
 
 
 def lem_set_proposals(h, pair, abc_ptr):
@@ -453,6 +465,16 @@ class Stereo:
 
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
+
+    def autotune(self, repeats=2):
+        """Picks the per-level launch configuration (lem_autotune); returns the lem_tuning."""
+        t = lem_tuning()
+        self.check(lem_autotune(self.h, repeats, t))
+        for k in ("level_threads", "level_gr_interval", "level_strip_rows"):
+            src = {"level_threads": t.threads, "level_gr_interval": t.gr_interval,
+                   "level_strip_rows": t.strip_rows}[k]
+            setattr(self.params, k, (C.c_int * 3)(*src))
+        return t
 
     # learned proposer -------------------------------------------------------------
     def set_proposals(self, abc, pair=0):

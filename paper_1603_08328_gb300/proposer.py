@@ -14,11 +14,15 @@ CUDA library.
 """
 from __future__ import annotations
 
+import argparse
+import os
 import time
 
 import numpy as np
 
 from .lem import ProposalNet, Stereo
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "proposer_384x288.npy")
 
 # Disparity is predicted as d / disp_max (order 1); the slopes are small (|a|, |b| < 1),
 # so they are weighted up in the L1 loss.
@@ -75,3 +79,69 @@ def solve(stereo: Stereo, n_iters, net: ProposalNet | None = None, first=1):
         torch.cuda.synchronize()
         out.append((st.energy, time.perf_counter() - t0, st.evals))
     return out
+
+
+def load(path=WEIGHTS, seed=0) -> ProposalNet:
+    """A network with the weights stored at `path` (flat float32, lem_cnn_get_params order)."""
+    net = ProposalNet(seed=seed)
+    net.set_params(np.load(path))
+    return net
+
+
+def _render(args):
+    from synth import workload_pair
+    name, seed = args
+    p = workload_pair(name, seed)
+    return p["left"], p["right"]
+
+
+def render_scenes(name, seeds, processes=0):
+    """Synthetic pairs rendered in worker processes (spawned, so safe after CUDA use)."""
+    import multiprocessing as mp
+    processes = processes or min(16, os.cpu_count() or 1)
+    if processes <= 1:
+        return [_render((name, s)) for s in seeds]
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_render, [(name, s) for s in seeds], chunksize=8)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="train the plane-proposal network on synthetic scenes")
+    ap.add_argument("--scenes", type=int, default=2000)
+    ap.add_argument("--first-seed", type=int, default=10000)
+    ap.add_argument("--chunk", type=int, default=50, help="pairs per batch handle")
+    ap.add_argument("--iters", type=int, default=10, help="iterations of the plain method for the targets")
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--out", default=WEIGHTS)
+    args = ap.parse_args(argv)
+    import torch
+    from synth.scenes import WORKLOADS
+    name = "train_384x288"
+    dmax = WORKLOADS[name]["disp_max"]
+    t0 = time.time()
+    scenes = render_scenes(name, range(args.first_seed, args.first_seed + args.scenes))
+    print(f"rendered {len(scenes)} scenes in {time.time() - t0:.1f} s", flush=True)
+    t0 = time.time()
+    xs, ts = [], []
+    for c in range(0, len(scenes), args.chunk):
+        pairs = [dict(left=l, right=r) for l, r in scenes[c:c + args.chunk]]
+        x, t = make_dataset(pairs, n_in=(1, 2, 3), n_out=args.iters, disp_max=dmax, seed=c + 1)
+        xs.append(x)
+        ts.append(t)
+    x, t = torch.cat(xs), torch.cat(ts)
+    print(f"dataset {tuple(x.shape)} in {time.time() - t0:.1f} s", flush=True)
+    net = ProposalNet(seed=1)
+    t0 = time.time()
+    losses = train(net, x, t, steps=args.steps, batch=args.batch, lr=args.lr, log_every=max(1, args.steps // 10))
+    torch.cuda.synchronize()
+    print(f"trained {args.steps} steps in {time.time() - t0:.1f} s: loss {np.mean(losses[:100]):.4f} -> "
+          f"{np.mean(losses[-100:]):.4f}", flush=True)
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.save(args.out, net.get_params())
+    print(f"wrote {args.out}")
+
+
+if __name__ == "__main__":
+    main()

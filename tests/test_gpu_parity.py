@@ -318,3 +318,47 @@ def test_16bit_image_storage_data_term(torch_cuda, store):
     q0 = g.energy()[1]
     st = g.iterate(1)
     assert st.maxflow_limit == 0 and st.energy_q < q0
+
+
+def test_launch_configuration_does_not_change_results(torch_cuda):
+    """Threads per CTA, global-relabel interval and strip rows change only the time: the
+    labels after an iteration are bit-identical (fixed summation order per cost, unique
+    minimal cut)."""
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 3)
+    base = dict(disp_max=60.0, seed=9)
+    a = Stereo(pair["left"], pair["right"], **base)
+    b = Stereo(pair["left"], pair["right"], level_threads=(1024, 256, 512), level_gr_interval=(8, 64, 16),
+               level_strip_rows=(8, 32, 8), **base)
+    a.iterate(1)
+    b.iterate(1)
+    la, lb = a.labels()[0].cpu().numpy(), b.labels()[0].cpu().numpy()
+    assert (la == lb).all()
+    assert a.energy()[1] == b.energy()[1]
+
+
+def test_autotune_keeps_the_state_and_the_results(torch_cuda):
+    """lem_autotune restores labels and counters, picks valid configurations that are no
+    slower than the default, and the tuned handle then follows the untuned one bit for bit."""
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 4)
+    base = dict(disp_max=60.0, seed=13)
+    a = Stereo(pair["left"], pair["right"], **base)
+    b = Stereo(pair["left"], pair["right"], **base)
+    a.iterate(1)
+    b.iterate(1)
+    q0 = b.energy()[1]
+    lab0 = b.labels()[0].cpu().numpy()
+    t = b.autotune(repeats=1)
+    assert t.configs_tried >= 3 * 20
+    for l in range(3):
+        assert t.threads[l] in (256, 512, 1024) and t.gr_interval[l] in (8, 16, 32, 64)
+        assert t.strip_rows[l] in (8, 16, 32)
+        assert 0 < t.ms[l] <= t.ms_default[l]
+    print("tuned:", list(t.threads), list(t.gr_interval), list(t.strip_rows),
+          [round(x, 3) for x in t.ms], [round(x, 3) for x in t.ms_default])
+    assert (b.labels()[0].cpu().numpy() == lab0).all() and b.energy()[1] == q0
+    sa = a.iterate(2)
+    sb = b.iterate(2)
+    assert sa.evals == sb.evals and sa.accepted == sb.accepted
+    assert (a.labels()[0].cpu().numpy() == b.labels()[0].cpu().numpy()).all()
