@@ -49,7 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
+    ap.add_argument("--launch-config", default=None,
+                    help="fixed per-level configuration 'threads/gr_interval/strip_rows', each three "
+                         "comma-separated values (e.g. 256,512,512/16,16,16/8,32,16); skips the autotuner")
     ap.add_argument("--no-time-to-energy", action="store_true")
+    ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
+    ap.add_argument("--mode", default="step", choices=["step", "proposer"],
+                    help="proposer: time only the proposal network (one JSON line of its own)")
     return ap.parse_args()
 
 
@@ -257,6 +263,71 @@ def run_reference(args):
 
 # --- GPU -------------------------------------------------------------------------
 
+def conv_flops_per_pixel():
+    """Algorithmic flops of one forward pass per quarter-resolution pixel: 2 * 9 * Cin * Cout
+    summed over the layers, real channel counts (7 -> 32 -> ... -> 32 -> 3)."""
+    layers = [(7, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 3)]
+    return 2 * 9 * sum(ci * co for ci, co in layers)
+
+
+def proposer_timing(lem, stream, reps=20):
+    """Proposal network: forward pass on the quarter-resolution grid of a 1500 x 1000 image
+    (375 x 250 x 7) and one training step (forward, both gradients and Adam) on 16 images of
+    96 x 72, each timed with CUDA events (median of `reps`), as algorithmic TFLOP/s (the
+    backward pass counted as twice the forward) against the measured dense BF16 peak."""
+    import torch
+    net = lem.ProposalNet(seed=0, stream=stream)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(250, 375, 7, device="cuda", generator=g)
+    xt = torch.rand(16, 72, 96, 7, device="cuda", generator=g)
+    tt = torch.rand(16, 72, 96, 3, device="cuda", generator=g)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sorted(ts)[len(ts) // 2]
+
+    t_fwd = timed(lambda: net.forward(x))
+    t_train = timed(lambda: net.train_step(xt, tt, 1e-4))
+    fpp = conv_flops_per_pixel()
+    f_fwd = fpp * 250 * 375
+    f_train = 3 * fpp * 16 * 72 * 96
+    peak = None
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        peak_note = "of measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, ValueError, KeyError):
+        peak, peak_note = 1900.0, "of fallback (1.9 PFLOP/s bf16)"
+    net.close()
+    fwd_tf = f_fwd / t_fwd / 1e12
+    return {"forward_1500x1000_ms": 1e3 * t_fwd, "forward_tflops": fwd_tf,
+            "train_step_16x96x72_ms": 1e3 * t_train, "train_tflops": f_train / t_train / 1e12,
+            "flops_per_quarter_pixel": fpp, "peak_tflops": peak, "forward_frac": fwd_tf / peak,
+            "peak_note": peak_note,
+            "note": "mma.sync m16n8k16 BF16 implicit-GEMM convolutions, FP32 accumulation"}
+
+
+def run_proposer_mode(args):
+    """--mode proposer: only the proposal-network timing, one JSON line."""
+    import torch
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    __graft_entry__.build()
+    from paper_1603_08328_gb300 import lem
+    out = proposer_timing(lem, torch.cuda.current_stream())
+    print(json.dumps({"mode": "proposer", **out}), flush=True)
+
+
 def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
     """Time (CUDA events around each outer iteration, learned proposals' inference
     included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
@@ -333,7 +404,11 @@ def run_lem(args):
     warm.iterate(max(1, args.warmup), stats=False)
     tuned = {}
     tuning = None
-    if not args.no_tune:
+    if args.launch_config:
+        t3 = [[int(x) for x in part.split(",")] for part in args.launch_config.split("/")]
+        tuned = dict(level_threads=t3[0], level_gr_interval=t3[1], level_strip_rows=t3[2])
+        tuning = dict(tuned, source="--launch-config")
+    elif not args.no_tune:
         t = warm.autotune(repeats=2)
         tuned = dict(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval),
                      level_strip_rows=list(t.strip_rows))
@@ -430,6 +505,7 @@ def run_lem(args):
     e2e_v = world * n_iters_job * evals_per_step / e2e_job
 
     tte = None if args.no_time_to_energy else time_to_energy(lem, pair, params, stream, seed=21 + rank)
+    prop = None if args.no_proposer else proposer_timing(lem, stream)
 
     if rank != 0:
         return
@@ -456,6 +532,7 @@ def run_lem(args):
         "clocks": clk.summary(),
         "energy": {"before": e0, "after": e1},
         "time_to_energy": tte,
+        "proposer": prop,
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
@@ -475,6 +552,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "proposer":
+        run_proposer_mode(args)
     else:
         run_lem(args)
 

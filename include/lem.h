@@ -159,6 +159,15 @@ int lem_create(const lem_image *left, const lem_image *right, const lem_params *
 int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pairs, const lem_params *p,
                      lem_handle **out);
 
+/* lem_create_batch with a disparity range per pair: disp_ranges holds
+ * (disp_min, disp_max) of pair b at [2b], [2b+1] (HOST, copied; NULL: the
+ * range of `p` for every pair).  The range bounds the pair's random initial
+ * labels and perturbations (Sec. 3.4) and scales its network input.
+ * Errors as lem_create_batch, and LEM_ERR_ARG for a range that is not finite
+ * with max >= min. */
+int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int n_pairs,
+                            const double *disp_ranges, const lem_params *p, lem_handle **out);
+
 /* Number of pairs of a handle (-1 for NULL). */
 int lem_pair_count(const lem_handle *h);
 

@@ -309,12 +309,22 @@ const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_
 
 int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pairs, const lem_params *p,
                      lem_handle **out) {
+    return lem_create_batch_ranges(lefts, rights, n_pairs, nullptr, p, out);
+}
+
+int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int n_pairs,
+                            const double *disp_ranges, const lem_params *p, lem_handle **out) {
     if (!out) return fail(nullptr, LEM_ERR_ARG, "out is NULL");
     *out = nullptr;
     int rc;
     if ((rc = check_params(p)) != LEM_OK) return rc;
     if (!lefts || !rights || n_pairs < 1 || n_pairs > 4096)
         return fail(nullptr, LEM_ERR_ARG, "lefts/rights NULL or n_pairs outside [1, 4096]");
+    if (disp_ranges)
+        for (int b = 0; b < n_pairs; ++b)
+            if (!(disp_ranges[2 * b + 1] >= disp_ranges[2 * b]) || !std::isfinite(disp_ranges[2 * b]) ||
+                !std::isfinite(disp_ranges[2 * b + 1]))
+                return fail(nullptr, LEM_ERR_ARG, "disparity range of pair " + std::to_string(b) + " is not finite with max >= min");
     for (int b = 0; b < n_pairs; ++b) {
         if ((rc = check_image(&lefts[b], "left")) != LEM_OK) return rc;
         if ((rc = check_image(&rights[b], "right")) != LEM_OK) return rc;
@@ -335,6 +345,8 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
         pd.off = off;
         // pair 0 keeps the seed, so a batch of one reproduces lem_create
         pd.seed = p->seed + 0x9E3779B97F4A7C15ull * (unsigned long long)b;
+        pd.disp_min = disp_ranges ? disp_ranges[2 * b] : p->disp_min;
+        pd.disp_max = disp_ranges ? disp_ranges[2 * b + 1] : p->disp_max;
         off += (long long)pd.H * pd.W;
         h->pairs.push_back(pd);
         h->maxH = std::max(h->maxH, pd.H);
@@ -425,7 +437,7 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
             e = lem::launch_guide_stats(dl, ls, H, W, p->gf_radius, p->gf_eps, p->cond_fp64, (float4 *)P.gst,
                                         h->n_fp64, h->st);
         if (e == cudaSuccess)
-            e = lem::launch_init_labels(H, W, pd.seed, p->disp_min, p->disp_max, h->lab + pd.off, h->st);
+            e = lem::launch_init_labels(H, W, pd.seed, pd.disp_min, pd.disp_max, h->lab + pd.off, h->st);
         if (e == cudaSuccess) e = lem::launch_pixel_costs(P, kp, h->lab + pd.off, std::min(p->threads, 128), h->st);
         // the temporary upload buffer must outlive the kernels that read it
         if (tmp) {
@@ -761,17 +773,18 @@ int lem_get_proposals(lem_handle *h, int pair, float *abc_dev) {
 int lem_cnn_features(lem_handle *h, int pair, float *x) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (!x || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "x is NULL or pair out of range");
-    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
-    LEM_CUDA(h, lem::launch_cnn_features(planes(h, pair), h->lab + h->pairs[pair].off, (float)h->p.disp_max, x, h->st));
+    const lem::PairDesc &pd = h->pairs[pair];
+    if (!(pd.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
+    LEM_CUDA(h, lem::launch_cnn_features(planes(h, pair), h->lab + pd.off, (float)pd.disp_max, x, h->st));
     return LEM_OK;
 }
 
 int lem_cnn_targets(lem_handle *h, int pair, float *t) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (!t || pair < 0 || pair >= h->B) return fail(h, LEM_ERR_ARG, "t is NULL or pair out of range");
-    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network target needs disp_max > 0");
     const lem::PairDesc &pd = h->pairs[pair];
-    LEM_CUDA(h, lem::launch_cnn_targets(h->lab + pd.off, pd.H, pd.W, (float)h->p.disp_max, t, h->st));
+    if (!(pd.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network target needs disp_max > 0");
+    LEM_CUDA(h, lem::launch_cnn_targets(h->lab + pd.off, pd.H, pd.W, (float)pd.disp_max, t, h->st));
     return LEM_OK;
 }
 
@@ -779,7 +792,8 @@ int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (!net) return fail(h, LEM_ERR_ARG, "network is NULL");
     if (!h->prop) return fail(h, LEM_ERR_ARG, "every k_cnn is 0: the handle keeps no proposal map");
-    if (!(h->p.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
+    for (const lem::PairDesc &pd : h->pairs)
+        if (!(pd.disp_max > 0)) return fail(h, LEM_ERR_ARG, "the network input needs disp_max > 0");
     // quarter-resolution buffers sized for the largest pair, kept by the handle
     const size_t n4 = (size_t)((h->maxH + 3) / 4) * ((h->maxW + 3) / 4);
     if (!h->cnn_buf) LEM_CUDA(h, cudaMalloc(&h->cnn_buf, sizeof(float) * n4 * 10));
@@ -787,7 +801,7 @@ int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
     int rc = LEM_OK;
     for (int b = 0; b < h->B && rc == LEM_OK; ++b) {
         const lem::PairDesc &pd = h->pairs[b];
-        const float dmax = (float)h->p.disp_max;
+        const float dmax = (float)pd.disp_max;
         cudaError_t e = lem::launch_cnn_features(planes(h, b), h->lab + pd.off, dmax, x, h->st);
         if (e != cudaSuccess) {
             rc = cuda_fail(h, e, "lem_cnn_propose features");

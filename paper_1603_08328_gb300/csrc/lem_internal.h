@@ -39,6 +39,7 @@ struct PairDesc {
     int H, W;
     long long off;
     unsigned long long seed;
+    double disp_min, disp_max;  // disparity range of the pair's random draws
 };
 
 // One grid level of Algorithm 1.

@@ -1126,6 +1126,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     P.gst += 3 * pd.off;
     P.wfw += pd.off;
     kp.seed = pd.seed;
+    kp.disp_min = pd.disp_min;
+    kp.disp_max = pd.disp_max;
     float4 *lab = lab_all + pd.off;
     float *phiA = phiA_all + pd.off;
     const float4 *prop = prop_all ? prop_all + pd.off : nullptr;

@@ -75,6 +75,9 @@ def lib():
         L.lem_default_params.restype = None
         L.lem_create.argtypes = [P(lem_image), P(lem_image), P(lem_params), P(H)]
         L.lem_create_batch.argtypes = [P(lem_image), P(lem_image), C.c_int, P(lem_params), P(H)]
+        L.lem_create_batch_ranges.argtypes = [P(lem_image), P(lem_image), C.c_int, P(C.c_double), P(lem_params),
+                                              P(H)]
+        L.lem_create_batch_ranges.restype = C.c_int
         L.lem_pair_count.argtypes = [H]
         L.lem_pair_info.argtypes = [H, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int64)]
         L.lem_energy_pair.argtypes = [H, C.c_int, P(C.c_double), P(C.c_int64)]
@@ -171,6 +174,21 @@ def lem_create_batch(lefts, rights, params: lem_params):
     ra = (lem_image * n)(*rights)
     h = C.c_void_p()
     rc = lib().lem_create_batch(la, ra, n, C.byref(params), C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def lem_create_batch_ranges(lefts, rights, disp_ranges, params: lem_params):
+    n = len(lefts)
+    la = (lem_image * n)(*lefts)
+    ra = (lem_image * n)(*rights)
+    rg = None
+    if disp_ranges is not None:
+        flat = [float(x) for r in disp_ranges for x in r]
+        assert len(flat) == 2 * n
+        rg = (C.c_double * (2 * n))(*flat)
+    h = C.c_void_p()
+    rc = lib().lem_create_batch_ranges(la, ra, n, rg, C.byref(params), C.byref(h))
     _check(rc, None)
     return h
 
@@ -329,8 +347,9 @@ class Stereo:
     """One handle on one pair.  Images are numpy uint8 (H, W, 3) host arrays or
     CUDA uint8 tensors; batch outputs are CUDA tensors."""
 
-    def __init__(self, left, right, stream=None, **params):
-        """left/right: one image each, or lists of images (a batch of pairs)."""
+    def __init__(self, left, right, stream=None, disp_ranges=None, **params):
+        """left/right: one image each, or lists of images (a batch of pairs); disp_ranges:
+        optional (disp_min, disp_max) per pair of a batch."""
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -344,7 +363,10 @@ class Stereo:
         if isinstance(left, (list, tuple)):
             lis = [self._image(x) for x in left]
             ris = [self._image(x) for x in right]
-            self.h = lem_create_batch(lis, ris, self.params)
+            if disp_ranges is not None:
+                self.h = lem_create_batch_ranges(lis, ris, disp_ranges, self.params)
+            else:
+                self.h = lem_create_batch(lis, ris, self.params)
             li = lis[0]
         else:
             li, ri = self._image(left), self._image(right)

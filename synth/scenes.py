@@ -12,7 +12,7 @@ left view shows, at every pixel, the segment of largest disparity whose support
 contains it (so occlusion boundaries are real).  Texture is multi-octave value
 noise attached to each surface in left-view coordinates, so the right view is
 an exact warp: right pixel (u_r, v) shows the surface point (u_l, v) with
-``u_l - d(u_l, v) = u_r`` (closed form for planes, Newton for quadrics), again
+``u_l - d(u_l, v) = u_r`` (closed form for planes, Newton for quadrics, keeping converged roots), again
 taking the nearest (largest-disparity) surface.  Gaussian noise (sigma in gray
 levels) is added independently to both views before rounding to uint8.
 
@@ -142,17 +142,39 @@ def _make_scene(rng: np.random.Generator, H: int, W: int, dmin: float, dmax: flo
     return segs
 
 
+def _window(s, H, W, right):
+    """Row and column slices that contain every pixel the segment can cover in the
+    left view, or (right=True) in the right view (its support shifted by its
+    disparity range over the support's bounding box)."""
+    if not np.isfinite(s.rx):
+        return slice(0, H), slice(0, W)
+    R = max(s.rx, s.ry) + 1.0
+    v0, v1 = int(np.floor(s.v0 - R)), int(np.ceil(s.v0 + R)) + 1
+    u0, u1 = s.u0 - R, s.u0 + R
+    if right:
+        corners = [s.a * uu + s.b * vv + s.c for uu in (u0, u1) for vv in (s.v0 - R, s.v0 + R)]
+        dhi = max(corners) + max(0.0, s.kappa) * 2.0 * R * R
+        dlo = min(corners) + min(0.0, s.kappa) * 2.0 * R * R
+        u0, u1 = u0 - dhi - 2.0, u1 - dlo + 2.0
+    cu0, cu1 = int(np.floor(u0)), int(np.ceil(u1)) + 1
+    return slice(max(0, v0), max(0, min(H, v1))), slice(max(0, cu0), max(0, min(W, cu1)))
+
+
 def _render(segs, H, W):
-    """Left view, right view (noise-free, float) and left ground-truth disparity."""
+    """Left view, right view (noise-free, float) and left ground-truth disparity.
+    Each segment is evaluated only inside the window it can cover, and textures only
+    at the pixels it wins."""
     v, u = np.mgrid[0:H, 0:W].astype(np.float64)
     # left view: nearest segment containing the pixel
     best_d = np.full((H, W), -np.inf)
     best_s = np.zeros((H, W), dtype=np.int64)
     for k, s in enumerate(segs):
-        d = s.disparity(u, v)
-        m = s.inside(u, v) & (d > best_d)
-        best_d[m] = d[m]
-        best_s[m] = k
+        ys, xs = _window(s, H, W, False)
+        uu, vv = u[ys, xs], v[ys, xs]
+        d = s.disparity(uu, vv)
+        m = s.inside(uu, vv) & (d > best_d[ys, xs])
+        best_d[ys, xs][m] = d[m]
+        best_s[ys, xs][m] = k
     left = np.zeros((H, W, 3))
     for k, s in enumerate(segs):
         m = best_s == k
@@ -160,18 +182,29 @@ def _render(segs, H, W):
             left[m] = s.tex(u[m], v[m])
     # right view: for each segment solve u_l - d(u_l, v) = u_r
     rbest = np.full((H, W), -np.inf)
-    right = np.zeros((H, W, 3))
-    for s in segs:
-        ul = (u + s.b * v + s.c) / (1.0 - s.a)
+    rseg = np.full((H, W), -1, dtype=np.int64)
+    rul = np.zeros((H, W))
+    for k, s in enumerate(segs):
+        ys, xs = _window(s, H, W, True)
+        uu, vv = u[ys, xs], v[ys, xs]
+        ul = (uu + s.b * vv + s.c) / (1.0 - s.a)
         if s.kappa != 0.0:
             for _ in range(30):
-                g = ul - s.disparity(ul, v) - u
-                ul = ul - g / (1.0 - s.ddu(ul, v))
-        d = s.disparity(ul, v)
-        m = s.inside(ul, v) & (d > rbest)
+                g = ul - s.disparity(ul, vv) - uu
+                ul = ul - g / (1.0 - s.ddu(ul, vv))
+        d = s.disparity(ul, vv)
+        # a quadric's equation has a second root; Newton can also stall between
+        # them: keep only solutions that satisfy the warp equation
+        ok = np.abs(ul - d - uu) < 1e-6
+        m = s.inside(ul, vv) & ok & (d > rbest[ys, xs])
+        rbest[ys, xs][m] = d[m]
+        rseg[ys, xs][m] = k
+        rul[ys, xs][m] = ul[m]
+    right = np.zeros((H, W, 3))
+    for k, s in enumerate(segs):
+        m = rseg == k
         if m.any():
-            rbest[m] = d[m]
-            right[m] = s.tex(ul[m], v[m])
+            right[m] = s.tex(rul[m], v[m])
     return left, right, best_d
 
 
@@ -207,9 +240,39 @@ WORKLOADS = {
     "train_384x288": dict(height=288, width=384, disp_max=48.0, n_planes=7, n_quadrics=3),
 }
 
+# The uneven batch: 8 pairs from 640x480 to 2900x2000, disparity ranges 64-800 px.
+BATCH8 = [
+    dict(height=480, width=640, disp_max=64.0, n_planes=8, n_quadrics=3),
+    dict(height=600, width=800, disp_max=96.0, n_planes=10, n_quadrics=4),
+    dict(height=768, width=1024, disp_max=128.0, n_planes=14, n_quadrics=5),
+    dict(height=960, width=1280, disp_max=192.0, n_planes=18, n_quadrics=6),
+    dict(height=1000, width=1500, disp_max=256.0, n_planes=22, n_quadrics=8),
+    dict(height=1080, width=1920, disp_max=400.0, n_planes=26, n_quadrics=10),
+    dict(height=1600, width=2400, disp_max=600.0, n_planes=30, n_quadrics=12),
+    dict(height=2000, width=2900, disp_max=800.0, n_planes=34, n_quadrics=14),
+]
+
 
 def workload_pair(name: str, seed: int = 0):
     return make_pair(seed, **WORKLOADS[name])
+
+
+def batch8_pair(index: int, seed: int = 0):
+    """Pair `index` (0..7) of the uneven batch."""
+    return make_pair(seed * 8 + index, **BATCH8[index])
+
+
+def _batch8_images(args):
+    p = batch8_pair(*args)
+    return {"left": p["left"], "right": p["right"], "disp": p["disp"]}
+
+
+def render_batch8(seed: int = 0, processes: int = 8):
+    """All 8 pairs of the uneven batch (left, right, disp), rendered in spawned
+    worker processes (safe after CUDA has been initialised in the caller)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_batch8_images, [(i, seed) for i in range(len(BATCH8))], chunksize=1)
 
 
 def random_labels(seed: int, n: int, height: int, width: int, disp_max: float,

@@ -1,0 +1,137 @@
+"""Parity at the full sizes: the 1500 x 1000 pair (disparity 0-400) with FP16 image storage
+and the batched 4-candidate schedule, and the uneven batch of 8 pairs from 640 x 480 to
+2900 x 2000 (disparity 64-800) with BF16 storage and learned proposals, in the launch
+configuration the benchmark uses (one launch per (level, group) over all pairs, CUDA graph
+replay, autotuned).  The oracle is too slow for whole iterations at these sizes, so it
+checks sampled outputs one by one: region data terms and the cached phi_p(f_p) of sampled
+pixels against the definition, with the 16-bit storage tolerance 2e-3 (16-bit floats keep
+the 0..255 colours exactly; the x-gradient carries a relative error of 2^-11 (FP16) or
+2^-8 (BF16) of values below 128, which moves a truncated cost term by at most 0.9 * 0.5 *
+2^-8 * 2 ~ 3.5e-3 absolute in the worst pixel and far less in a window mean).  The rest is
+checked through properties that hold at any size: no cut hits its round limit, the
+evaluation count is exact, the quantised energy never increases, and pair 0 of the batch
+equals its own handle bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import BATCH8, random_labels, render_batch8, workload_pair
+
+pytestmark = pytest.mark.gpu
+
+TOL16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def large(torch_cuda):
+    pair = workload_pair("large_1500x1000", 0)
+    return pair, oracle.Oracle(pair["left"], pair["right"], disp_max=400.0)
+
+
+def _rel(gpu, ref):
+    return np.abs(np.asarray(gpu, np.float64) - ref) / np.maximum(1.0, np.abs(ref))
+
+
+def _sample_cache(g, o, pair_index, rng, n, W):
+    """max relative error of the cached phi_p(f_p) against the definition at n pixels."""
+    abc, _, cost = g.labels(pair_index)
+    abc, cost = abc.cpu().numpy(), cost.cpu().numpy()
+    H = abc.shape[0]
+    worst = 0.0
+    for _ in range(n):
+        y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+        ref = o.phi_def(abc[y, x], x, y)
+        worst = max(worst, float(_rel(cost[y, x], ref)))
+    return worst
+
+
+def test_large_fp16_data_term_sampled(large):
+    from paper_1603_08328_gb300.lem import LEM_STORE_F16, Stereo
+    pair, o = large
+    g = Stereo(pair["left"], pair["right"], disp_max=400.0, store_dtype=LEM_STORE_F16)
+    H, W = 1000, 1500
+    # level-0/1/2 interior regions, corner, right and bottom borders (ragged)
+    regions = [(700, 500, 15, 15), (300, 620, 45, 45), (600, 400, 75, 75), (0, 0, 50, 50),
+               (1460, 300, 40, 75), (20, 955, 75, 45)]
+    labels = random_labels(17, 2 * len(regions), H, W, 400.0, 0.3).reshape(len(regions), 2, 3)
+    costs = g.unary(regions, labels)
+    worst = 0.0
+    for r, lab, c in zip(regions, labels, costs):
+        for k in range(2):
+            ref = o.region_cost(*r, lab[k])
+            worst = max(worst, float(_rel(c[k].cpu().numpy(), ref).max()))
+    print(f"1500x1000 FP16 data term: max rel err {worst:.2e}")
+    assert worst <= TOL16
+
+
+def test_large_fp16_batched_iterations(large):
+    from paper_1603_08328_gb300.lem import LEM_STORE_F16, Stereo
+    pair, o = large
+    g = Stereo(pair["left"], pair["right"], disp_max=400.0, store_dtype=LEM_STORE_F16, candidates_per_visit=4)
+    q0 = g.energy()[1]
+    st = g.iterate(1)
+    assert st.maxflow_limit == 0 and st.evals == g.evals_per_iteration()
+    assert st.energy_q < q0
+    t = g.autotune(repeats=1)
+    print("tuned:", list(t.threads), list(t.gr_interval), list(t.strip_rows), [round(x, 3) for x in t.ms])
+    q = st.energy_q
+    for _ in range(2):          # the first runs directly and captures the graph, the second replays it
+        st = g.iterate(1)
+        assert st.maxflow_limit == 0 and st.evals == g.evals_per_iteration()
+        assert st.energy_q <= q
+        q = st.energy_q
+    worst = _sample_cache(g, o, 0, np.random.default_rng(2), 40, 1500)
+    disp = g.labels()[1].cpu().numpy()
+    bad = float((np.abs(disp - pair["disp"]) > 1.0).mean())
+    print(f"1500x1000: cache rel err {worst:.2e}, bad > 1 px after 3 iterations {bad:.3f}")
+    assert worst <= TOL16
+    assert bad < 0.5
+
+
+def test_uneven_batch_of_8_bf16_with_learned_proposals(torch_cuda):
+    torch = torch_cuda
+    from paper_1603_08328_gb300 import proposer
+    from paper_1603_08328_gb300.lem import LEM_STORE_BF16, Stereo
+    import os
+    pairs = render_batch8(0)
+    ranges = [(0.0, c["disp_max"]) for c in BATCH8]
+    kw = dict(store_dtype=LEM_STORE_BF16, candidates_per_visit=4, k_cnn=(1, 0, 0), seed=5)
+    g = Stereo([p["left"] for p in pairs], [p["right"] for p in pairs], disp_ranges=ranges, **kw)
+    assert len(g.pairs) == 8
+    if os.path.exists(proposer.WEIGHTS):
+        net = proposer.load()
+    else:
+        from paper_1603_08328_gb300.lem import ProposalNet
+        net = ProposalNet(seed=0)
+    q0 = [g.energy(b)[1] for b in range(8)]
+    for it in range(2):
+        g.cnn_propose(net)
+        st = g.iterate(1)
+        assert st.maxflow_limit == 0 and st.evals == g.evals_per_iteration()
+    q1 = [g.energy(b)[1] for b in range(8)]
+    assert all(b < a for a, b in zip(q0, q1))
+    # pair 0 equals a handle of its own (same seed, same range, same proposal network)
+    s0 = Stereo(pairs[0]["left"], pairs[0]["right"], disp_max=ranges[0][1], **kw)
+    for it in range(2):
+        s0.cnn_propose(net)
+        s0.iterate(1)
+    assert (s0.labels()[0].cpu().numpy() == g.labels(0)[0].cpu().numpy()).all()
+    # sampled costs of the smallest and the largest pair against the definition
+    for b in (0, 7):
+        o = oracle.Oracle(pairs[b]["left"], pairs[b]["right"], disp_max=ranges[b][1])
+        worst = _sample_cache(g, o, b, np.random.default_rng(b), 25, BATCH8[b]["width"])
+        print(f"pair {b} ({BATCH8[b]['width']}x{BATCH8[b]['height']}): cache rel err {worst:.2e}")
+        assert worst <= TOL16
+        del o
+    torch.cuda.synchronize()
