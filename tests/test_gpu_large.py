@@ -4,10 +4,10 @@ and the batched 4-candidate schedule, and the uneven batch of 8 pairs from 640 x
 configuration the benchmark uses (one launch per (level, group) over all pairs, CUDA graph
 replay, autotuned).  The oracle is too slow for whole iterations at these sizes, so it
 checks sampled outputs one by one: region data terms and the cached phi_p(f_p) of sampled
-pixels against the definition, with the 16-bit storage tolerance 2e-3 (16-bit floats keep
-the 0..255 colours exactly; the x-gradient carries a relative error of 2^-11 (FP16) or
-2^-8 (BF16) of values below 128, which moves a truncated cost term by at most 0.9 * 0.5 *
-2^-8 * 2 ~ 3.5e-3 absolute in the worst pixel and far less in a window mean).  The rest is
+pixels against the definition, with the tolerance stated for 16-bit image storage, 2e-3
+(16-bit floats keep the 0..255 colours exactly; only the x-gradient is rounded, by at most
+2^-12 (FP16) or 2^-9 (BF16) of its value, and those unbiased roundings are averaged by the
+guided filter over at least 441 pixels).  The rest is
 checked through properties that hold at any size: no cut hits its round limit, the
 evaluation count is exact, the quantised energy never increases, and pair 0 of the batch
 equals its own handle bit for bit.
