@@ -313,7 +313,7 @@ def proposer_timing(lem, stream, reps=20):
             "train_step_16x96x72_ms": 1e3 * t_train, "train_tflops": f_train / t_train / 1e12,
             "flops_per_quarter_pixel": fpp, "peak_tflops": peak, "forward_frac": fwd_tf / peak,
             "peak_note": peak_note,
-            "note": "mma.sync m16n8k16 BF16 implicit-GEMM convolutions, FP32 accumulation"}
+            "note": "BF16 implicit-GEMM convolutions: forward and input gradient on tcgen05.mma (kind::f16, TMEM accumulator), weight gradient on mma.sync m16n8k16; FP32 accumulation"}
 
 
 def run_proposer_mode(args):

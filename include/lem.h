@@ -354,8 +354,9 @@ int lem_get_proposals(lem_handle *h, int pair, float *abc_dev);
  * channels, ReLU after all but the last; input (H4, W4, 7) = left RGB, right
  * RGB (/255) and label disparity (/disp_max) at quarter resolution (4x4 block
  * means, H4 = ceil(H/4), W4 = ceil(W/4)); output (H4, W4, 3) = (d/disp_max, a,
- * b).  BF16 tensor-core convolutions with FP32 accumulation; FP32 master
- * weights trained by Adam on an L1 loss.  Runs on the stream given at creation
+ * b).  BF16 tensor-core convolutions with FP32 accumulation (forward and input
+ * gradient on tcgen05 with a TMEM accumulator, weight gradient on mma.sync);
+ * FP32 master weights trained by Adam on an L1 loss.  Runs on the stream given at creation
  * (NULL: legacy default stream). */
 typedef struct lem_cnn lem_cnn;
 
@@ -364,6 +365,11 @@ typedef struct lem_cnn lem_cnn;
 int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out);
 int lem_cnn_destroy(lem_cnn *net);
 const char *lem_cnn_last_error(const lem_cnn *net);
+/* Synchronises the network's stream and reports LEM_ERR_CUDA if a convolution
+ * tile gave up waiting for its tensor-core MMAs since the last check (the
+ * kernels bound that wait and leave such a tile's output unwritten);
+ * lem_cnn_gradients runs this check itself.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_cnn_check(lem_cnn *net);
 /* Number of parameters: per layer, weights (3, 3, Cin, Cout) row-major, then the
  * Cout biases; layers in order (Cin, Cout) = (7,32), (32,32) x4, (32,3). */
 int64_t lem_cnn_num_params(void);

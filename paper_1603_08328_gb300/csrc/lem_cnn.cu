@@ -4,11 +4,13 @@
 // the prediction into a full-resolution map of plane labels that the
 // expansion kernel can draw candidates from.
 //
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
-// BF16 operands, FP32 accumulation):
-//   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = pixels, N = Cout, K = 9 Cin)
+// Convolutions are implicit GEMMs on the tensor cores (BF16 operands, FP32
+// accumulation):
+//   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = 128 pixels, N = Cout, K = 9 Cin)
+//                on tcgen05.mma with the accumulator in tensor memory
 //   input grad   dX        = the same kernel with flipped, transposed weights
 //   weight grad  dW[o][k]  = sum_p dZ[p][o] Xpatch[p][k]      (M = Cout, N = 9 Cin, K = pixels)
+//                on mma.sync m16n8k16 (M = Cout is below tcgen05's smallest M of 64)
 // Activations are BF16, NHWC, channels padded to a multiple of 16; the weights
 // have an FP32 master copy updated by Adam.
 #include <cuda_bf16.h>
@@ -62,71 +64,187 @@ __device__ __forceinline__ void gather_patch(const bf16 *X, int H, int W, int u,
     }
 }
 
-// Y = conv3x3(X) (+ bias), 128 pixels per CTA, 8 warps of 16 pixels.
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) helpers.  Operands sit in shared memory
+// in the no-swizzle K-major canonical layout: 8-row x 16-byte core matrices,
+// each 128 contiguous bytes; core matrix (row group g, k chunk c) of a tile
+// with K columns is at byte (g * K/8 + c) * 128.  The accumulator lives in
+// tensor memory (TMEM): row i of the 128-row tile is TMEM lane i.
+// ---------------------------------------------------------------------------
+__device__ unsigned int g_mma_timeouts = 0;  // waits on an MMA completion that gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// shared-memory matrix descriptor: start address, leading-dimension byte offset
+// (between core matrices along K), stride byte offset (between 8-row groups),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tc(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// bounded wait for phase 0 of an mbarrier; false if it gave up
+__device__ __forceinline__ bool mbar_wait0(uint32_t mbar, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+template <int N>
+__device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&out)[N]);
+template <>
+__device__ __forceinline__ void tmem_load_row<32>(uint32_t taddr, float (&o)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(r[j]);
+}
+template <>
+__device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&o)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = __uint_as_float(r[j]);
+}
+
+constexpr int kConvThreads = 128;       // 4 warps: warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int kMmaWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
+static_assert(kConvThreads == kTileP, "one thread per pixel row of the tile");
+
+// Y = conv3x3(X) (+ bias) for 128 pixels per CTA as one 128 x COUT x 9CIN GEMM
+// on the tensor cores: the pixels' 3x3 patches (A, 128 x K) and the weights
+// (B, COUT x K, both K-major) are staged in shared memory, one thread issues
+// K/16 tcgen05.mma into a TMEM accumulator, and each warp reads its 32 rows
+// back for the epilogue.
 //   X  : H*W*CIN bf16;  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]);
 //   Z  : optional fp32 pre-activation H*W*COUT;  Y : optional bf16 output (ReLU if relu)
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias,
-                                              float *Z, bf16 *Y, int relu) {
-    constexpr int K = 9 * CIN, LDA = K + 8;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    bf16 *As = reinterpret_cast<bf16 *>(sm_raw);    // [kTileP][LDA]
-    bf16 *Bs = As + kTileP * LDA;                     // [COUT][LDA]
+__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int W, const bf16 *Bt,
+                                                       const float *bias, float *Z, bf16 *Y, int relu) {
+    constexpr int K = 9 * CIN, KC = K / 8, CH = CIN / 8;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *As = sm_raw;                          // 128 x K, core-matrix layout
+    unsigned char *Bs = sm_raw + (size_t)kTileP * K * 2; // COUT x K, core-matrix layout
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = H * W, p0 = blockIdx.x * kTileP;
-    // stage the weights and the pixels' patches
-    for (int q = tid; q < COUT * (K / 8); q += blockDim.x) {
-        const int o = q / (K / 8), c8 = q - o * (K / 8);
-        *reinterpret_cast<uint4 *>(Bs + o * LDA + c8 * 8) = *reinterpret_cast<const uint4 *>(Bt + (size_t)o * K + c8 * 8);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    // two threads per pixel
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // weights: row o, k chunk c -> core matrix (o/8, c), row o%8
+    for (int q = tid; q < COUT * KC; q += kConvThreads) {
+        const int o = q / KC, c = q - o * KC;
+        *reinterpret_cast<uint4 *>(Bs + ((o >> 3) * KC + c) * 128 + (o & 7) * 16) =
+            *reinterpret_cast<const uint4 *>(Bt + (size_t)o * K + c * 8);
+    }
+    // patches: one thread per pixel row r, k chunk c = tap * CH + c8
     {
-        const int pl = tid >> 1, part = tid & 1;
-        const int p = p0 + pl;
-        if (p < n) {
-            gather_patch<CIN>(X, H, W, p % W, p / W, As + pl * LDA, part, 2);
-        } else {
-            for (int k = part * 8; k < K; k += 16) *reinterpret_cast<uint4 *>(As + pl * LDA + k) = make_uint4(0, 0, 0, 0);
+        const int r = tid, p = p0 + r;
+        unsigned char *row = As + (size_t)(r >> 3) * KC * 128 + (r & 7) * 16;
+        const int u = p % W, v = p / W;
+        for (int c = 0; c < KC; ++c) {
+            const int tap = c / CH, c8 = c - tap * CH;
+            const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (p < n && uu >= 0 && uu < W && vv >= 0 && vv < H)
+                val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
+            *reinterpret_cast<uint4 *>(row + c * 128) = val;
         }
     }
+    // generic-proxy stores -> visible to the tensor core's async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    const int g = lane >> 2, t = lane & 3;
-    constexpr int NT = COUT / 8;
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const bf16 *Aw = As + (warp * 16) * LDA;
-#pragma unroll 2
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[4];
-        a[0] = ld_u32(Aw + g * LDA + k0 + t * 2);
-        a[1] = ld_u32(Aw + (g + 8) * LDA + k0 + t * 2);
-        a[2] = ld_u32(Aw + g * LDA + k0 + t * 2 + 8);
-        a[3] = ld_u32(Aw + (g + 8) * LDA + k0 + t * 2 + 8);
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            uint32_t b[2];
-            b[0] = ld_u32(Bs + (j * 8 + g) * LDA + k0 + t * 2);
-            b[1] = ld_u32(Bs + (j * 8 + g) * LDA + k0 + t * 2 + 8);
-            mma_bf16(acc[j], a, b);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tbase = tmem_base;
+    if (tid == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+        constexpr uint32_t idesc = idesc_bf16(kTileP, COUT);
+#pragma unroll 1
+        for (int kk = 0; kk < K / 16; ++kk) {
+            // K step kk covers core-matrix columns 2kk, 2kk+1
+            const uint64_t ad = smem_desc(a0 + kk * 256, 128, KC * 128);
+            const uint64_t bd = smem_desc(b0 + kk * 256, 128, KC * 128);
+            mma_tc(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&mbar))
+                     : "memory");
     }
-    // epilogue: c0 (row g, col 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+    const bool ok = mbar_wait0(smem_u32(&mbar), kMmaWaitLimit);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        float acc[COUT];
+        tmem_load_row<COUT>(tbase + ((uint32_t)(warp * 32) << 16), acc);
+        const int p = p0 + warp * 32 + lane;
+        if (p < n) {
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
+            for (int o = 0; o < COUT; ++o) acc[o] += bias ? bias[o] : 0.f;
+            if (Z) {
+                float4 *z4 = reinterpret_cast<float4 *>(Z + (size_t)p * COUT);
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int p = p0 + warp * 16 + g + 8 * r;
-            if (p >= n) continue;
+                for (int o = 0; o < COUT; o += 4) z4[o / 4] = make_float4(acc[o], acc[o + 1], acc[o + 2], acc[o + 3]);
+            }
+            if (Y) {
+                uint4 *y4 = reinterpret_cast<uint4 *>(Y + (size_t)p * COUT);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int o = j * 8 + 2 * t + c;
-                float z = acc[j][2 * r + c] + (bias ? bias[o] : 0.f);
-                if (Z) Z[(size_t)p * COUT + o] = z;
-                if (Y) Y[(size_t)p * COUT + o] = __float2bfloat16_rn(relu ? fmaxf(z, 0.f) : z);
+                for (int o = 0; o < COUT; o += 8) {
+                    __nv_bfloat162 h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float x0 = relu ? fmaxf(acc[o + 2 * j], 0.f) : acc[o + 2 * j];
+                        const float x1 = relu ? fmaxf(acc[o + 2 * j + 1], 0.f) : acc[o + 2 * j + 1];
+                        h[j] = __floats2bfloat162_rn(x0, x1);
+                    }
+                    y4[o / 8] = *reinterpret_cast<uint4 *>(h);
+                }
             }
         }
+    } else if (tid == 0) {
+        atomicAdd(&g_mma_timeouts, 1u);
+        // give the MMAs in flight one more bounded chance before TMEM is freed
+        mbar_wait0(smem_u32(&mbar), kMmaWaitLimit);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tbase));
 }
 
 // dW[o][k] += sum_p dZ[p][o] Xpatch[p][k] over the CTA's 128 pixels; dB[o] += sum_p dZ[p][o].
@@ -135,7 +253,7 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) k_conv_wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW,
                                                     float *dB) {
     constexpr int K = 9 * CIN, LDP = kTileP + 8;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
+    extern __shared__ __align__(128) unsigned char sm_raw[];
     bf16 *At = reinterpret_cast<bf16 *>(sm_raw);  // [COUT][LDP]  dZ transposed (A: M = COUT, K = pixels)
     bf16 *Bt = At + COUT * LDP;                   // [K][LDP]     Xpatch transposed (B col layout: N = K)
     bf16 *Pt = Bt + K * LDP;                      // [kTileP][K]  patch staging (pixel-major)
@@ -282,7 +400,7 @@ __global__ void k_take3(const float *z, int n, float *y) {
 
 template <int CIN, int COUT>
 size_t conv_smem() {
-    return sizeof(bf16) * ((size_t)kTileP * (9 * CIN + 8) + (size_t)COUT * (9 * CIN + 8));
+    return (size_t)2 * 9 * CIN * (kTileP + COUT);
 }
 template <int CIN, int COUT>
 size_t wgrad_smem() {
@@ -296,7 +414,7 @@ cudaError_t conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias,
     cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nb = (H * W + kTileP - 1) / kTileP;
-    k_conv<CIN, COUT><<<nb, 256, sm, st>>>(X, H, W, Bt, bias, Z, Y, relu);
+    k_conv<CIN, COUT><<<nb, kConvThreads, sm, st>>>(X, H, W, Bt, bias, Z, Y, relu);
     return cudaGetLastError();
 }
 
@@ -405,9 +523,33 @@ cudaError_t backward(lem_cnn *net, int H4, int W4) {
 }
 }  // namespace
 
+namespace {
+// reports (and clears) tensor-core completion waits that gave up
+int check_mma_timeouts(lem_cnn *net) {
+    unsigned int t = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&t, g_mma_timeouts, sizeof(t));
+    if (e != cudaSuccess) return cnn_fail(net, e, "reading the MMA timeout counter");
+    if (t) {
+        const unsigned int zero = 0;
+        cudaMemcpyToSymbol(g_mma_timeouts, &zero, sizeof(zero));
+        const std::string m = std::to_string(t) + " convolution tile(s) gave up waiting for the tensor core";
+        if (net) net->err = m;
+        g_cnn_err = m;
+        return LEM_ERR_CUDA;
+    }
+    return LEM_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *lem_cnn_last_error(const lem_cnn *net) { return net ? net->err.c_str() : g_cnn_err.c_str(); }
+
+int lem_cnn_check(lem_cnn *net) {
+    if (!net) return LEM_ERR_ARG;
+    CNN_CUDA(net, cudaStreamSynchronize(net->st));
+    return check_mma_timeouts(net);
+}
 
 int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out) {
     if (!out) return LEM_ERR_ARG;
@@ -577,7 +719,7 @@ int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_i
         std::copy(g.begin(), g.end(), grads);
     }
     CNN_CUDA(net, cudaStreamSynchronize(net->st));
-    return LEM_OK;
+    return check_mma_timeouts(net);
 }
 
 int lem_cnn_train_step(lem_cnn *net, const float *x, const float *target, int n_images, int H4, int W4,

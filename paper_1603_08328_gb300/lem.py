@@ -104,6 +104,8 @@ def lib():
         L.lem_cnn_destroy.argtypes = [N]
         L.lem_cnn_last_error.argtypes = [N]
         L.lem_cnn_last_error.restype = C.c_char_p
+        L.lem_cnn_check.argtypes = [N]
+        L.lem_cnn_check.restype = C.c_int
         L.lem_cnn_num_params.argtypes = []
         L.lem_cnn_num_params.restype = C.c_int64
         L.lem_cnn_get_params.argtypes = [N, vp]
@@ -299,6 +301,10 @@ def lem_cnn_destroy(net):
 def lem_cnn_last_error(net) -> str:
     s = lib().lem_cnn_last_error(net)
     return s.decode() if s else ""
+
+
+def lem_cnn_check(net):
+    return lib().lem_cnn_check(net)
 
 
 def lem_cnn_num_params() -> int:
@@ -560,6 +566,10 @@ class ProposalNet:
         if rc != LEM_OK:
             raise LemError(rc, lem_cnn_last_error(self.net))
         return rc
+
+    def sync_check(self):
+        """Synchronise and raise if a convolution tile gave up waiting for the tensor core."""
+        self.check(lem_cnn_check(self.net))
 
     def get_params(self) -> np.ndarray:
         out = np.empty(lem_cnn_num_params(), np.float32)

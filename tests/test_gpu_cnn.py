@@ -88,6 +88,7 @@ def test_forward_matches_oracle(torch_cuda, H4, W4):
     rng = np.random.default_rng(H4 * 1000 + W4)
     x = rng.uniform(0.0, 1.0, size=(H4, W4, 7)).astype(np.float32)
     y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    net.sync_check()
     emu, _, _ = cnn.forward(_f64(params), x.astype(np.float64), store="bf16")
     ref, _, _ = cnn.forward(_f64(params), x.astype(np.float64))
     e_emu, err = _nerr(y, emu), _nerr(y, ref)
