@@ -134,6 +134,8 @@ def lib():
         L.lo_put_state.argtypes = [C.c_void_p, fp, dp]
         L.lo_expand_group.restype = C.c_longlong
         L.lo_expand_group.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, P(C.c_longlong)]
+        L.lo_expand_cells.restype = C.c_longlong
+        L.lo_expand_cells.argtypes = [C.c_void_p, C.c_int, C.c_int, ip, C.c_int, P(C.c_longlong)]
         L.lo_iterate.restype = C.c_longlong
         L.lo_iterate.argtypes = [C.c_void_p, C.c_int, P(C.c_longlong)]
         L.lo_region_of.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip]
@@ -265,6 +267,13 @@ class Oracle:
             return
         self._prop = _f32(abc).reshape(self.H, self.W, 3)
         lib().lo_set_proposals(self.h, _ptr(self._prop, C.c_float))
+
+    def expand_cells(self, it, level, cells):
+        """Algorithm 2 on the listed cells (i, j) of one group; returns (switched, evals)."""
+        arr = np.ascontiguousarray(np.asarray(cells, np.int32).reshape(-1, 2))
+        ev = C.c_longlong()
+        acc = lib().lo_expand_cells(self.h, it, level, _ptr(arr, C.c_int), arr.shape[0], C.byref(ev))
+        return acc, ev.value
 
     def expand_group(self, it, level, group):
         ev = C.c_longlong()

@@ -1294,6 +1294,26 @@ long long lo_expand_group(lo_ctx *c, int iter, int level, int group, long long *
     return acc;
 }
 
+/* The alpha_ij-expansions of an explicit list of cells (i, j) = (cells[2k],
+ * cells[2k+1]) of one group, as lo_expand_group runs them: used by the
+ * stripe-decomposed driver, where each domain runs the cells whose centre
+ * cell lies in its stripe.  Returns the number of switched pixels. */
+long long lo_expand_cells(lo_ctx *c, int iter, int level, const int *cells, int ncell, long long *evals) {
+    double rd, rn;
+    outer_delta(c, iter, &rd, &rn);
+    long long acc = 0, ev = 0;
+    int nt = c->p.n_threads;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : acc, ev) num_threads(nt > 0 ? nt : omp_get_max_threads())
+    for (int k = 0; k < ncell; k++) {
+        long long a = 0, e = 0;
+        iterative_expansion(c, iter, level, cells[2 * k], cells[2 * k + 1], rd, rn, &a, &e);
+        acc += a;
+        ev += e;
+    }
+    if (evals) *evals = ev;
+    return acc;
+}
+
 /* One outer iteration of Algorithm 1: every grid level, every group. */
 long long lo_iterate(lo_ctx *c, int iter, long long *evals) {
     long long acc = 0, ev = 0;
