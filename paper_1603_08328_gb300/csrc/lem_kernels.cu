@@ -807,6 +807,25 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
     const int WPR = (w + 31) >> 5, NW = h * WPR;
     uint32_t *M = bits, *Fa = bits + 8 * NW, *Fb = Fa + NW, *VIS = Fb + NW;
     const FastDiv fwpr(WPR);
+    if (WPR == 1) {
+        // rows of at most 32 nodes: one warp per row builds all 9 words of it
+        for (int y = warp; y < h; y += nwarp) {
+            const bool in = lane < w;
+            const int i = y * w + lane;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t m = __ballot_sync(0xffffffffu, in && res[k * n + i] > 0);
+                if (lane == 0) M[k * NW + y] = m;
+            }
+            const bool seed = in && v[i] < 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, seed);
+            if (lane == 0) {
+                Fa[y] = m;
+                VIS[y] = m;
+            }
+            if (in) hh[i] = seed ? 1 : kInf;
+        }
+    } else
     // planes and seeds: one warp per (plane, row word), lane = bit
     for (int t = warp; t < 9 * NW; t += nwarp) {
         const int k = t / NW;  // uniform per warp
