@@ -784,12 +784,25 @@ __device__ long long block_sum_ll(long long v, long long *red) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int dir_off(int k, int w) { return dir_dx(k) + dir_dy(k) * w; }
 
-// j / d for 0 <= j, d < 2^16 by one 64-bit multiply: floor(j * ceil(2^32 / d) / 2^32)
-struct FastDiv {
-    unsigned long long m;
-    int d;
-    __device__ explicit FastDiv(int d_) : m(((1ull << 32) + (unsigned)d_ - 1) / (unsigned)d_), d(d_) {}
-    __device__ __forceinline__ int div(int j) const { return (int)(((unsigned long long)j * m) >> 32); }
+// Row and column of the indices j0, j0 + step, j0 + 2 step, ... of a row-major
+// grid with rows of w entries, advanced by exact integer steps (one division
+// at construction, none per index).
+struct RowCol {
+    int y, x, dy, dx, w;
+    __device__ RowCol(int j0, int step, int w_) : w(w_) {
+        y = j0 / w;
+        x = j0 - y * w;
+        dy = step / w;
+        dx = step - dy * w;
+    }
+    __device__ __forceinline__ void next() {
+        y += dy;
+        x += dx;
+        if (x >= w) {
+            x -= w;
+            ++y;
+        }
+    }
 };
 
 // Exact distances to the sink in the residual graph, by a bit-parallel BFS
@@ -806,44 +819,28 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     const int WPR = (w + 31) >> 5, NW = h * WPR;
     uint32_t *M = bits, *Fa = bits + 8 * NW, *Fb = Fa + NW, *VIS = Fb + NW;
-    const FastDiv fwpr(WPR);
-    if (WPR == 1) {
-        // rows of at most 32 nodes: one warp per row builds all 9 words of it
-        for (int y = warp; y < h; y += nwarp) {
-            const bool in = lane < w;
-            const int i = y * w + lane;
+    // planes and seeds: one warp per row, one pass per row word, lane = bit
+    for (int y = warp; y < h; y += nwarp) {
+        for (int wi = 0; wi < WPR; ++wi) {
+            const int word = y * WPR + wi;
+            const int x = wi * 32 + lane;
+            const bool in = x < w;
+            const int i = y * w + x;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const uint32_t m = __ballot_sync(0xffffffffu, in && res[k * n + i] > 0);
-                if (lane == 0) M[k * NW + y] = m;
+                bool pred = false;
+                if (in) pred = res[k * n + i] > 0;
+                const uint32_t m = __ballot_sync(0xffffffffu, pred);
+                if (lane == 0) M[k * NW + word] = m;
             }
-            const bool seed = in && v[i] < 0;
+            bool seed = false;
+            if (in) seed = v[i] < 0;
             const uint32_t m = __ballot_sync(0xffffffffu, seed);
-            if (lane == 0) {
-                Fa[y] = m;
-                VIS[y] = m;
-            }
-            if (in) hh[i] = seed ? 1 : kInf;
-        }
-    } else
-    // planes and seeds: one warp per (plane, row word), lane = bit
-    for (int t = warp; t < 9 * NW; t += nwarp) {
-        const int k = t / NW;  // uniform per warp
-        const int word = t - k * NW;
-        const int y = fwpr.div(word), wi = word - y * WPR;
-        const int x = wi * 32 + lane;
-        const int i = y * w + x;
-        bool pred = false;
-        if (x < w) pred = (k < 8) ? (res[k * n + i] > 0) : (v[i] < 0);
-        const uint32_t m = __ballot_sync(0xffffffffu, pred);
-        if (k < 8) {
-            if (lane == 0) M[k * NW + word] = m;
-        } else {
             if (lane == 0) {
                 Fa[word] = m;
                 VIS[word] = m;
             }
-            if (x < w) hh[i] = pred ? 1 : kInf;
+            if (in) hh[i] = seed ? 1 : kInf;
         }
     }
     __syncthreads();
@@ -851,8 +848,9 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
     int level = 1;
     for (;;) {
         int any = 0;
-        for (int word = tid; word < NW; word += nt) {
-            const int y = fwpr.div(word), wi = word - y * WPR;
+        RowCol rw(tid, nt, WPR);
+        for (int word = tid; word < NW; word += nt, rw.next()) {
+            const int y = rw.y, wi = rw.x;
             const uint32_t vis = VIS[word];
             uint32_t cand = 0;
             if (~vis) {
@@ -872,7 +870,9 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
                         sh = f;
                     cand |= M[k * NW + word] & sh;
                 }
-                cand &= ~vis;
+                // only bits of nodes inside the row can be reached
+                const int tail = w - wi * 32;
+                cand &= ~vis & (tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u));
             }
             Fn[word] = cand;
             if (cand) {
@@ -907,8 +907,8 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
 // of every minimum cut and one with cap_t > in on the sink side, and the slack
 // of one unit keeps these strict.  Needs res (initial capacities) and v.
 __device__ void clamp_terminals(int n, int w, int h, const int *res, int *v) {
-    const FastDiv fw(w);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    RowCol rc(threadIdx.x, blockDim.x, w);
+    for (int i = threadIdx.x; i < n; i += blockDim.x, rc.next()) {
         const int e = v[i];
         if (e > 0) {
             int out = 1;
@@ -916,7 +916,7 @@ __device__ void clamp_terminals(int n, int w, int h, const int *res, int *v) {
             for (int k = 0; k < 8; ++k) out += res[k * n + i];
             v[i] = min(e, out);
         } else if (e < 0) {
-            const int iy = fw.div(i), ix = i - iy * w;
+            const int iy = rc.y, ix = rc.x;
             int in = 1;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -1088,9 +1088,9 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
     const int n = R.z * R.w, w = R.z, h = R.w;
     const int64_t off = offsets[i];
     CutSmem cs = cut_layout(smi, n);
-    const FastDiv fw(w);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int iy = fw.div(j), ix = j - iy * w;
+    RowCol rc(threadIdx.x, blockDim.x, w);
+    for (int j = threadIdx.x; j < n; j += blockDim.x, rc.next()) {
+        const int iy = rc.y, ix = rc.x;
         cs.v[j] = tcaps[2 * (off + j)] - tcaps[2 * (off + j) + 1];
         for (int k = 0; k < 8; ++k) {
             int c = 0;
@@ -1158,7 +1158,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     CutSmem cs = cut_layout(smf, n);
-    const FastDiv fw(w);
     // outer perturbation sizes of this iteration, copied into Algorithm 2
     double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
     double rn = ldexp(1.0, -iter);
@@ -1194,8 +1193,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
             const float4 al = s_alpha[t - t0];
             region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
             // (region_unary ends with a barrier; its shared memory is reused below)
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                const int iy = fw.div(j), ix = j - iy * w;
+            RowCol rb(threadIdx.x, blockDim.x, w);
+            for (int j = threadIdx.x; j < n; j += blockDim.x, rb.next()) {
+                const int iy = rb.y, ix = rb.x;
                 NodeCaps o;
                 build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
                 cs.v[j] = o.cap_s - o.cap_t;
@@ -1208,10 +1208,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
             const int st =
                 cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
             if (st == LEM_OK) {
-                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                RowCol rm(threadIdx.x, blockDim.x, w);
+                for (int j = threadIdx.x; j < n; j += blockDim.x, rm.next()) {
                     if (cs.hh[j] == kInf) continue;
-                    const int iy = fw.div(j);
-                    const size_t p = (size_t)(y0 + iy) * W + x0 + (j - iy * w);
+                    const size_t p = (size_t)(y0 + rm.y) * W + x0 + rm.x;
                     lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
                     ++acc;
                 }
