@@ -954,16 +954,53 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
         }
         if (tid == 0) s_cnt = 0;
         __syncthreads();
-        for (int base = 0; base < n; base += nt) {
-            const int i = base + tid;
-            const bool a = i < n && v[i] > 0 && hh[i] != kInf;
-            const uint32_t m = __ballot_sync(0xffffffffu, a);
-            if (m) {
-                int pos = 0;
-                if (lane == 0) pos = atomicAdd(&s_cnt, __popc(m));
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (a) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+        if (n < 2 * nt) {
+            // small regions: one node per thread
+            for (int base = 0; base < n; base += nt) {
+                const int i = base + tid;
+                const bool a = i < n && v[i] > 0 && hh[i] != kInf;
+                const uint32_t m = __ballot_sync(0xffffffffu, a);
+                if (m) {
+                    int pos = 0;
+                    if (lane == 0) pos = atomicAdd(&s_cnt, __popc(m));
+                    pos = __shfl_sync(0xffffffffu, pos, 0);
+                    if (a) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+                }
             }
+        } else
+        // four consecutive nodes per thread (one 16-byte load of v, one 8-byte
+        // load of hh), warp-aggregated appends
+        for (int base = 0; base < n; base += 4 * nt) {
+            const int i0 = base + 4 * tid;
+            bool a0 = false, a1 = false, a2 = false, a3 = false;
+            if (i0 + 3 < n) {
+                const int4 vv = *reinterpret_cast<const int4 *>(v + i0);
+                const ushort4 h4 = *reinterpret_cast<const ushort4 *>(hh + i0);
+                a0 = vv.x > 0 && h4.x != kInf;
+                a1 = vv.y > 0 && h4.y != kInf;
+                a2 = vv.z > 0 && h4.z != kInf;
+                a3 = vv.w > 0 && h4.w != kInf;
+            } else if (i0 < n) {
+                a0 = v[i0] > 0 && hh[i0] != kInf;
+                a1 = i0 + 1 < n && v[i0 + 1] > 0 && hh[i0 + 1] != kInf;
+                a2 = i0 + 2 < n && v[i0 + 2] > 0 && hh[i0 + 2] != kInf;
+            }
+            const int c = (int)a0 + (int)a1 + (int)a2 + (int)a3;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (tot == 0) continue;
+            int pos = 0;
+            if (lane == 31) pos = atomicAdd(&s_cnt, tot);
+            pos = __shfl_sync(0xffffffffu, pos, 31) + incl - c;
+            if (a0) list[pos++] = (uint16_t)i0;
+            if (a1) list[pos++] = (uint16_t)(i0 + 1);
+            if (a2) list[pos++] = (uint16_t)(i0 + 2);
+            if (a3) list[pos] = (uint16_t)(i0 + 3);
         }
         __syncthreads();
         const int cnt = s_cnt;
@@ -1027,7 +1064,8 @@ __device__ __forceinline__ CutSmem cut_layout(void *base, int n) {
     CutSmem c;
     c.res = (int *)base;
     c.v = c.res + 8 * n;
-    c.hh = (uint16_t *)(c.v + n);
+    // heights start on a 16-byte boundary so four of them load as one 8-byte word
+    c.hh = (uint16_t *)((char *)base + ((36 * (size_t)n + 15) & ~(size_t)15));
     c.bits = (uint32_t *)(c.hh + ((n + 1) & ~1));
     return c;
 }
@@ -1413,7 +1451,8 @@ size_t cut_smem_bytes(int w, int h) {
     const size_t n = (size_t)w * h;
     const size_t planes = (size_t)11 * h * ((w + 31) / 32) * sizeof(uint32_t);
     const size_t list = ((n + 1) & ~(size_t)1) * sizeof(uint16_t);
-    return 9 * n * sizeof(int) + ((n + 1) & ~(size_t)1) * sizeof(uint16_t) + std::max(planes, list);
+    return ((9 * n * sizeof(int) + 15) & ~(size_t)15) + ((n + 1) & ~(size_t)1) * sizeof(uint16_t) +
+           std::max(planes, list);
 }
 
 cudaError_t launch_preprocess(const uint8_t *left, int64_t lstride, const uint8_t *right, int64_t rstride, int H,
