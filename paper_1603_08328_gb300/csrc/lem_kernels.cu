@@ -854,22 +854,26 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
             const uint32_t vis = VIS[word];
             uint32_t cand = 0;
             if (~vis) {
+                // frontier words of rows y-1, y, y+1 around column word wi, shifted by
+                // dx = -1, 0, +1: sh[dy+1][dx+1] holds, at bit b, the frontier bit of
+                // node (x + dx, y + dy) for the node x at bit b
+                uint32_t sh[3][3];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int yy = y + dir_dy(k);
-                    if (yy < 0 || yy >= h) continue;
-                    const uint32_t *F = Fc + yy * WPR;
-                    const uint32_t f = F[wi];
-                    uint32_t sh;
-                    const int dx = dir_dx(k);
-                    if (dx > 0)
-                        sh = (f >> 1) | (wi + 1 < WPR ? F[wi + 1] << 31 : 0u);
-                    else if (dx < 0)
-                        sh = (f << 1) | (wi > 0 ? F[wi - 1] >> 31 : 0u);
-                    else
-                        sh = f;
-                    cand |= M[k * NW + word] & sh;
+                for (int r = 0; r < 3; ++r) {
+                    const int yy = y + r - 1;
+                    uint32_t c = 0, lw = 0, rw2 = 0;
+                    if (yy >= 0 && yy < h) {
+                        const uint32_t *F = Fc + yy * WPR;
+                        c = F[wi];
+                        lw = wi > 0 ? F[wi - 1] : 0u;
+                        rw2 = wi + 1 < WPR ? F[wi + 1] : 0u;
+                    }
+                    sh[r][0] = (c << 1) | (lw >> 31);  // dx = -1
+                    sh[r][1] = c;                       // dx = 0
+                    sh[r][2] = (c >> 1) | (rw2 << 31);  // dx = +1
                 }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) cand |= M[k * NW + word] & sh[dir_dy(k) + 1][dir_dx(k) + 1];
                 // only bits of nodes inside the row can be reached
                 const int tail = w - wi * 32;
                 cand &= ~vis & (tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u));
