@@ -934,6 +934,71 @@ __device__ void clamp_terminals(int n, int w, int h, const int *res, int *v) {
     }
 }
 
+// Global relabel of a region of at most 32 x 32 nodes by one warp (all 32
+// lanes of warp 0 call it): lane y keeps row y's residual bitplanes and BFS
+// words in registers and a BFS level moves frontier rows between lanes with
+// shuffles, so no level needs a CTA barrier.  Same result as global_relabel:
+// exact distances to the sink in hh (kInf where the sink cannot be reached);
+// returns whether a node with excess can reach it.
+__device__ __noinline__ bool warp_relabel(int n, int w, int h, const int *res, const int *v, uint16_t *hh,
+                                          int *levels) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t full = 0xffffffffu;
+    const uint32_t rowmask = w >= 32 ? full : ((1u << w) - 1u);
+    uint32_t M[8], F = 0u, VIS = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) M[k] = 0u;
+    for (int y = 0; y < h; ++y) {
+        const bool in = lane < w;
+        const int i = y * w + lane;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            bool p = false;
+            if (in) p = res[k * n + i] > 0;
+            const uint32_t m = __ballot_sync(full, p);
+            if (lane == y) M[k] = m;
+        }
+        bool seed = false;
+        if (in) seed = v[i] < 0;
+        const uint32_t m = __ballot_sync(full, seed);
+        if (lane == y) {
+            F = m;
+            VIS = m;
+        }
+        if (in) hh[i] = seed ? 1 : kInf;
+    }
+    __syncwarp();
+    int level = 1;
+    for (;;) {
+        const uint32_t up = __shfl_up_sync(full, F, 1), dn = __shfl_down_sync(full, F, 1);
+        const uint32_t rows[3] = {lane > 0 ? up : 0u, F, lane + 1 < h ? dn : 0u};  // dy = -1, 0, +1
+        uint32_t cand = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t r = rows[dir_dy(k) + 1];
+            const int dx = dir_dx(k);
+            cand |= M[k] & (dx > 0 ? (r >> 1) : (dx < 0 ? (r << 1) : r));
+        }
+        cand &= ~VIS & rowmask;
+        if (lane >= h) cand = 0u;
+        VIS |= cand;
+        F = cand;
+        uint32_t c = cand;
+        while (c) {
+            const int b = __ffs(c) - 1;
+            c &= c - 1;
+            hh[lane * w + b] = (uint16_t)(level + 1);
+        }
+        if (!__any_sync(full, cand != 0u)) break;
+        ++level;
+    }
+    __syncwarp();
+    *levels += level;
+    int act = 0;
+    for (int i = lane; i < n; i += 32) act |= (v[i] > 0 && hh[i] != kInf);
+    return __any_sync(full, act) != 0;
+}
+
 struct CutCount {
     int rounds, relabels, levels;
 };
@@ -946,9 +1011,21 @@ struct CutCount {
 __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
                            int gr_interval, CutCount &cc) {
     __shared__ int s_cnt;
+    __shared__ int s_act;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     uint16_t *list = (uint16_t *)bits;
-    bool act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
+    // regions of at most 32 x 32 nodes: the relabel runs on warp 0 alone
+    const bool small = w <= 32 && h <= 32;
+    auto relabel = [&]() -> bool {
+        if (!small) return global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
+        if (tid < 32) {
+            const bool a = warp_relabel(n, w, h, res, v, hh, &cc.levels);
+            if (tid == 0) s_act = a ? 1 : 0;
+        }
+        __syncthreads();
+        return s_act != 0;
+    };
+    bool act = relabel();
     ++cc.relabels;
     int rounds = 0;
     while (act) {
@@ -1049,7 +1126,7 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
         // a round with no active node, or the periodic point, hands over to an
         // exact global relabel (which also decides termination)
         if (cnt == 0 || rounds % gr_interval == 0) {
-            act = global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
+            act = relabel();
             ++cc.relabels;
         }
     }
