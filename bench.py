@@ -54,8 +54,10 @@ def parse():
                          "comma-separated values (e.g. 256,512,512/16,16,16/8,32,16); skips the autotuner")
     ap.add_argument("--no-time-to-energy", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
-    ap.add_argument("--mode", default="step", choices=["step", "proposer"],
-                    help="proposer: time only the proposal network (one JSON line of its own)")
+    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8"],
+                    help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs "
+                         "(one JSON line of its own)")
+    ap.add_argument("--batch-iters", type=int, default=10, help="outer iterations per pair in --mode batch8")
     return ap.parse_args()
 
 
@@ -328,6 +330,92 @@ def run_proposer_mode(args):
     print(json.dumps({"mode": "proposer", **out}), flush=True)
 
 
+def run_batch8_mode(args):
+    """--mode batch8: 8 pairs from 640x480 to 2900x2000 (disparity 64-800), BF16 images,
+    batched 4-candidate visits, learned proposals (k_cnn = 1 at the finest level) when
+    trained weights exist, autotuned, all on one stream of one GPU.  Two runs:
+      * one batch handle for all 8 pairs (one launch per (level, group) over every
+        pair): aggregate evals/s;
+      * one handle per pair, the pairs served one after another: per-pair latency
+        (host images in, n iterations, host disparity out) p50 / p99 and aggregate.
+    Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    __graft_entry__.build()
+    from paper_1603_08328_gb300 import lem, proposer
+    from synth import BATCH8, render_batch8
+    stream = torch.cuda.current_stream()
+    pairs = render_batch8(args.seed)
+    ranges = [(0.0, c["disp_max"]) for c in BATCH8]
+    net = proposer.load() if os.path.exists(proposer.WEIGHTS) else None
+    kw = dict(store_dtype=lem.LEM_STORE_BF16, candidates_per_visit=4, seed=5)
+    if net is not None:
+        kw["k_cnn"] = (1, 0, 0)
+    n_it = args.batch_iters
+
+    def iterate(g):
+        if net is not None:
+            g.cnn_propose(net)
+        g.check(lem.lem_expand_iteration(g.h, 1, None))
+
+    # tune on the largest pair's own handle (one warm-up iteration first)
+    t0h = lem.Stereo(pairs[-1]["left"], pairs[-1]["right"], stream=stream, disp_max=ranges[-1][1], **kw)
+    iterate(t0h)
+    t = t0h.autotune(repeats=1)
+    t0h.close()
+    kw.update(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval), level_strip_rows=list(t.strip_rows))
+
+    # batched: one handle over all pairs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = lem.Stereo([p["left"] for p in pairs], [p["right"] for p in pairs], stream=stream, disp_ranges=ranges, **kw)
+    evals_it = g.evals_per_iteration()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_it):
+        iterate(g)
+    b.record(stream)
+    b.synchronize()
+    gpu_s = a.elapsed_time(b) / 1e3
+    disp = g.labels("all")[1].cpu().numpy()
+    batch_job_s = time.perf_counter() - t0
+    st = g.iterate(0)
+    assert st.maxflow_limit == 0
+    g.close()
+
+    # served one by one: per-pair latency, host images in and host disparity out
+    lat, evals_total = [], 0
+    for p, rg in zip(pairs, ranges):
+        H, W = p["left"].shape[:2]
+        hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h1 = lem.Stereo(p["left"], p["right"], stream=stream, disp_max=rg[1], **kw)
+        for _ in range(n_it):
+            iterate(h1)
+        lem._check(lem.lem_get_labels(h1.h, None, lem.C.c_void_p(hd.data_ptr()), None, 0), h1.h)
+        lat.append(time.perf_counter() - t1)
+        evals_total += h1.evals_per_iteration() * n_it
+        h1.close()
+    lat_ms = np.array(lat) * 1e3
+    sizes = [f"{c['width']}x{c['height']}/{int(c['disp_max'])}" for c in BATCH8]
+    out = {"mode": "batch8", "metric": METRIC, "unit": METRIC, "iterations": n_it,
+           "pairs": sizes, "pixels": int(sum(c["width"] * c["height"] for c in BATCH8)),
+           "config": {"store": "bf16", "candidates_per_visit": 4, "learned_proposals": net is not None,
+                      "launch_config": {k: kw[k] for k in ("level_threads", "level_gr_interval", "level_strip_rows")}},
+           "batched": {"value": evals_it * n_it / gpu_s, "gpu_ms": 1e3 * gpu_s, "job_ms": 1e3 * batch_job_s,
+                       "evals": evals_it * n_it},
+           "per_pair": {"value": evals_total / sum(lat), "latency_ms": [round(x, 2) for x in lat_ms],
+                        "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))},
+           "disparity_finite": bool(np.isfinite(disp).all())}
+    print(json.dumps(out), flush=True)
+
+
 def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
     """Time (CUDA events around each outer iteration, learned proposals' inference
     included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
@@ -554,6 +642,8 @@ def main():
         run_reference(args)
     elif args.mode == "proposer":
         run_proposer_mode(args)
+    elif args.mode == "batch8":
+        run_batch8_mode(args)
     else:
         run_lem(args)
 

@@ -321,7 +321,7 @@ typedef struct {
 
 /* Times the expansion kernel of every level on this handle's own images and
  * labels for each candidate configuration (threads {256, 512, 1024} x
- * gr_interval {8, 16, 32, 64} x strip_rows {8, 16, 32}; candidates whose shared
+ * gr_interval {8, 16, 32, 64} x strip_rows {8, 12, 16, 24, 32}; candidates whose shared
  * memory does not fit are skipped), `repeats` launches of groups 0 and 10 of
  * the level at the handle's current iteration each, and keeps the fastest per
  * level in the handle's parameters (level_threads, level_gr_interval,

@@ -837,7 +837,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     lem_tuning res{};
     int rc = e == cudaSuccess ? LEM_OK : cuda_fail(h, e, "lem_autotune setup");
     const lem_params keep = h->p;
-    static const int kThreads[3] = {256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[3] = {8, 16, 32};
+    static const int kThreads[3] = {256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[5] = {8, 12, 16, 24, 32};
     // time of `repeats` launches of groups 0 and 10 at `level`, state restored after each;
     // < 0 when the configuration cannot launch
     auto trial = [&](int level, float &ms) -> int {
@@ -877,7 +877,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         int bg = keep.gr_interval, bs = keep.strip_rows;
         for (int ti = 0; ti < 3 && rc == LEM_OK; ++ti)
             for (int gi = 0; gi < 4 && rc == LEM_OK; ++gi)
-                for (int si = 0; si < 3 && rc == LEM_OK; ++si) {
+                for (int si = 0; si < 5 && rc == LEM_OK; ++si) {
                     h->p.level_threads[l] = kThreads[ti];
                     h->p.level_gr_interval[l] = kGr[gi];
                     h->p.level_strip_rows[l] = kRows[si];
