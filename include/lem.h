@@ -308,6 +308,47 @@ int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int
                              uint8_t *take_alpha, int64_t *flow, int32_t *status, int max_rounds, int gr_interval,
                              void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* Right view and post-processing (Sec. 3.2 after Eq. photofunc, Sec. 3.4 end) */
+/* ------------------------------------------------------------------------- */
+
+/* A handle that estimates the RIGHT image's labels.  The data term of the right
+ * view swaps the images and adds the disparity in the warp; that is the left-view
+ * problem of the horizontally mirrored pair, so the handle is created on
+ * (mirror(right), mirror(left)) and its labels, cost cache and energy live in
+ * mirrored coordinates: right pixel (u, v) is label (W - 1 - u, v), and a
+ * mirrored plane (a', b', c') is the right-image plane (-a', b', c' + a' (W - 1)).
+ * Everything else (iterations, energy, batch calls) works as on any handle.
+ * The images are read once, as by lem_create.  Errors as lem_create. */
+int lem_create_right_view(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out);
+
+/* Post-processing parameters.  The paper applies the left-right consistency
+ * check and weighted median filtering of Bleyer et al. (2011) without giving
+ * their settings; the defaults are that paper's: a 1-pixel consistency
+ * threshold, a 41 x 41 median window and gamma = 10 on 0..255 colours. */
+typedef struct {
+    float lr_threshold;   /* |d_L(p) - d_R(q)| <= lr_threshold marks p consistent            */
+    int median_radius;    /* window (2 r + 1)^2, clipped to the image; 0..64                  */
+    float median_gamma;   /* weight exp(-|I_p - I_q|_1 / gamma) on the left colours          */
+} lem_post_params;
+void lem_default_post_params(lem_post_params *pp);
+
+/* Final disparity map of pair 0 of hL (left view) with hR from
+ * lem_create_right_view on the same images:
+ *   1. p is consistent when q = (rint(u - d_L(p)), v) lies in the image and
+ *      |d_L(p) - d_R(q)| <= lr_threshold (disparities (a u + b v) + c in FP32);
+ *   2. an inconsistent p takes, of the nearest consistent pixels to its left and
+ *      right on its row, the plane giving the lower disparity at p (occlusions are
+ *      filled from the background);
+ *   3. an inconsistent p's disparity becomes the weighted median of the filled
+ *      disparities in its window: the smallest window value whose cumulative
+ *      weight, in ascending order of value, reaches half the total.
+ * disp: DEVICE, H*W floats (final disparities); valid: DEVICE, H*W bytes (1 =
+ * consistent) or NULL.  Synchronises hL's stream (and hR's when it differs).
+ * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE (views of different sizes), LEM_ERR_OOM,
+ * LEM_ERR_CUDA. */
+int lem_postprocess(lem_handle *hL, lem_handle *hR, const lem_post_params *pp, float *disp, uint8_t *valid);
+
 /* Autotuner result: the per-level launch configuration chosen, its time per
  * (level, group) launch and that of the default configuration. */
 typedef struct {

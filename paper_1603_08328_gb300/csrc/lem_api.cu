@@ -463,6 +463,45 @@ int lem_create(const lem_image *left, const lem_image *right, const lem_params *
     return lem_create_batch(left, right, 1, p, out);
 }
 
+int lem_create_right_view(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out) {
+    if (!out) return fail(nullptr, LEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc;
+    if ((rc = check_params(p)) != LEM_OK) return rc;
+    if ((rc = check_image(left, "left")) != LEM_OK) return rc;
+    if ((rc = check_image(right, "right")) != LEM_OK) return rc;
+    if (left->height != right->height || left->width != right->width)
+        return fail(nullptr, LEM_ERR_SHAPE, "left and right images differ in size");
+    const int H = left->height, W = left->width;
+    const size_t img = (size_t)H * W * 3;
+    cudaStream_t st = (cudaStream_t)p->stream;
+    uint8_t *buf = nullptr;  // [staged left][staged right][mirrored right][mirrored left]
+    cudaError_t e = cudaMalloc(&buf, 4 * img);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lem_create_right_view");
+    const lem_image *src[2] = {right, left};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        const uint8_t *d = src[k]->data;
+        int64_t ds = src[k]->stride_row;
+        if (!src[k]->on_device) {
+            e = cudaMemcpy2DAsync(buf + k * img, 3 * W, src[k]->data, src[k]->stride_row, 3 * W, H,
+                                  cudaMemcpyHostToDevice, st);
+            d = buf + k * img;
+            ds = 3 * W;
+        }
+        if (e == cudaSuccess) e = lem::launch_mirror_rgb(d, ds, H, W, buf + (2 + k) * img, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(nullptr, e, "lem_create_right_view mirror");
+    }
+    // the mirrored right image is the reference view, the mirrored left the matched one
+    lem_image l2{buf + 2 * img, H, W, 3LL * W, 1}, r2{buf + 3 * img, H, W, 3LL * W, 1};
+    rc = lem_create_batch(&l2, &r2, 1, p, out);
+    cudaFree(buf);
+    return rc;
+}
+
 int lem_pair_count(const lem_handle *h) { return h ? h->B : -1; }
 
 int lem_pair_info(const lem_handle *h, int pair, int *height, int *width, int64_t *pixel_offset) {
@@ -920,6 +959,35 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     h->gexec = nullptr;
     h->graph = nullptr;
     if (out) *out = res;
+    return LEM_OK;
+}
+
+void lem_default_post_params(lem_post_params *pp) {
+    if (!pp) return;
+    pp->lr_threshold = 1.0f;
+    pp->median_radius = 20;
+    pp->median_gamma = 10.0f;
+}
+
+int lem_postprocess(lem_handle *hL, lem_handle *hR, const lem_post_params *pp, float *disp, uint8_t *valid) {
+    if (!hL || !hR) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!pp || !disp) return fail(hL, LEM_ERR_ARG, "params or disp is NULL");
+    if (!(pp->lr_threshold >= 0.f) || pp->median_radius < 0 || pp->median_radius > 64 || !(pp->median_gamma > 0.f))
+        return fail(hL, LEM_ERR_ARG, "lr_threshold >= 0, median_radius in [0, 64] and median_gamma > 0 are required");
+    if (hL->pairs[0].H != hR->pairs[0].H || hL->pairs[0].W != hR->pairs[0].W)
+        return fail(hL, LEM_ERR_SHAPE, "the two views differ in size");
+    const size_t n = (size_t)hL->pairs[0].H * hL->pairs[0].W;
+    // the right view's labels must be final before the left stream reads them
+    if (hR->st != hL->st) LEM_CUDA(hL, cudaStreamSynchronize(hR->st));
+    char *tmp = nullptr;
+    LEM_CUDA(hL, cudaMalloc(&tmp, n * sizeof(float) + n));
+    float *filled = (float *)tmp;
+    uint8_t *vbuf = valid ? valid : (uint8_t *)(tmp + n * sizeof(float));
+    cudaError_t e = lem::launch_postprocess(planes(hL, 0), hL->lab, hR->lab, pp->lr_threshold, pp->median_radius,
+                                            pp->median_gamma, vbuf, filled, disp, hL->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hL->st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(hL, e, "lem_postprocess");
     return LEM_OK;
 }
 

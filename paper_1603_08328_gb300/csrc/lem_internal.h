@@ -116,6 +116,13 @@ cudaError_t launch_cnn_upsample(const float *y, int H, int W, float dmax, float4
 // prop (float4 a, b, c, 0) from / to a caller's H*W*3 array
 cudaError_t launch_props_in(int n, const float *abc, float4 *prop, cudaStream_t st);
 cudaError_t launch_props_out(int n, const float4 *prop, float *abc, cudaStream_t st);
+// Post-processing of one left view (planes PL, labels labL) with the labels labRm of
+// the right view estimated on the mirrored pair: consistency mask into valid, the
+// filled disparities into filled, the final disparities into disp (all H*W).
+cudaError_t launch_postprocess(const DevPlanes &PL, const float4 *labL, const float4 *labRm, float thr, int radius,
+                               float gamma, uint8_t *valid, float *filled, float *disp, cudaStream_t st);
+// dst (H*W*3 uint8, row stride 3W) = src mirrored horizontally (src row stride in bytes)
+cudaError_t launch_mirror_rgb(const uint8_t *src, int64_t stride, int H, int W, uint8_t *dst, cudaStream_t st);
 // Batch min-cut whose region/offset/counter scratch is a static device array
 // (no allocation); at most LEM_NOALLOC_MAX_REGIONS regions.
 cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, int n_regions, int max_nodes,

@@ -1432,6 +1432,128 @@ __global__ void k_props_in(int n, const float *abc, float4 *prop) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) prop[p] = make_float4(abc[3 * (size_t)p], abc[3 * (size_t)p + 1], abc[3 * (size_t)p + 2], 0.f);
 }
+
+// ---------------------------------------------------------------------------
+// post-processing: left-right consistency, occlusion filling, weighted median
+// (Sec. 3.4, after Bleyer et al. 2011).  Disparities are (a u + b v) + c in FP32
+// with one rounding per operation.  The right view's labels come from a handle
+// on the mirrored pair: right pixel u is mirrored column W - 1 - u.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float plane_disp(const float4 &f, int u, int v) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(f.x, (float)u), __fmul_rn(f.y, (float)v)), f.z);
+}
+
+__global__ void k_lr_check(const float4 *labL, const float4 *labRm, int H, int W, float thr, uint8_t *valid) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    const int u = p % W, v = p / W;
+    const float dL = plane_disp(labL[p], u, v);
+    const float qf = rintf(__fsub_rn((float)u, dL));
+    bool ok = false;
+    if (qf >= 0.f && qf <= (float)(W - 1)) {
+        const int q = (int)qf, um = W - 1 - q;
+        const float dR = plane_disp(labRm[(size_t)v * W + um], um, v);
+        ok = fabsf(__fsub_rn(dL, dR)) <= thr;
+    }
+    valid[p] = ok ? 1 : 0;
+}
+
+// filled disparity of every pixel: its own where consistent, else the lower of the
+// planes of the nearest consistent pixels to its left and right on the row
+__global__ void k_fill(const float4 *labL, const uint8_t *valid, int H, int W, float *disp) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H * W) return;
+    const int u = p % W, v = p / W;
+    const size_t row = (size_t)v * W;
+    if (valid[p]) {
+        disp[p] = plane_disp(labL[p], u, v);
+        return;
+    }
+    float best = 0.f;
+    bool have = false;
+    int k = u - 1;
+    while (k >= 0 && !valid[row + k]) --k;
+    if (k >= 0) {
+        best = plane_disp(labL[row + k], u, v);
+        have = true;
+    }
+    k = u + 1;
+    while (k < W && !valid[row + k]) ++k;
+    if (k < W) {
+        const float d = plane_disp(labL[row + k], u, v);
+        best = have ? fminf(best, d) : d;
+        have = true;
+    }
+    disp[p] = have ? best : plane_disp(labL[p], u, v);
+}
+
+// order-preserving map of a float to an unsigned key
+__device__ __forceinline__ uint32_t fkey(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// one warp per inconsistent pixel: the smallest window value whose cumulative
+// colour weight reaches half the total, found by bisection on the value keys
+__global__ void k_wmedian(DevPlanes P, const uint8_t *valid, const float *disp, int radius, float inv_gamma,
+                          float *out) {
+    const int H = P.H, W = P.W;
+    const int lane = threadIdx.x & 31;
+    const int p = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (p >= H * W) return;
+    if (valid[p]) {
+        if (lane == 0) out[p] = disp[p];
+        return;
+    }
+    const int u = p % W, v = p / W;
+    const int x0 = max(0, u - radius), x1 = min(W - 1, u + radius);
+    const int y0 = max(0, v - radius), y1 = min(H - 1, v + radius);
+    const int ww = x1 - x0 + 1, cnt = ww * (y1 - y0 + 1);
+    const float4 c = load_px(P.L, p, P.fmt);
+    // total weight and the value range
+    float tot = 0.f;
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    for (int j = lane; j < cnt; j += 32) {
+        const int yy = y0 + j / ww, xx = x0 + j % ww;
+        const size_t q = (size_t)yy * W + xx;
+        const float4 cq = load_px(P.L, q, P.fmt);
+        const float l1 = fabsf(cq.x - c.x) + fabsf(cq.y - c.y) + fabsf(cq.z - c.z);
+        tot += expf(-l1 * inv_gamma);
+        const uint32_t k = fkey(disp[q]);
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    const float half = 0.5f * tot;
+    // smallest key k in [kmin, kmax] with weight(<= k) >= half
+    uint32_t lo = kmin, hi = kmax;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        float s = 0.f;
+        for (int j = lane; j < cnt; j += 32) {
+            const int yy = y0 + j / ww, xx = x0 + j % ww;
+            const size_t q = (size_t)yy * W + xx;
+            if (fkey(disp[q]) <= mid) {
+                const float4 cq = load_px(P.L, q, P.fmt);
+                s += expf(-(fabsf(cq.x - c.x) + fabsf(cq.y - c.y) + fabsf(cq.z - c.z)) * inv_gamma);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (s >= half)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    if (lane == 0) out[p] = fkey_inv(lo);
+}
+
 __global__ void k_props_out(int n, const float4 *prop, float *abc) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -1664,6 +1786,32 @@ cudaError_t launch_props_in(int n, const float *abc, float4 *prop, cudaStream_t 
 }
 cudaError_t launch_props_out(int n, const float4 *prop, float *abc, cudaStream_t st) {
     k_props_out<<<(n + 255) / 256, 256, 0, st>>>(n, prop, abc);
+    return cudaGetLastError();
+}
+
+__global__ void k_mirror_rgb(const uint8_t *src, int64_t stride, int H, int W, uint8_t *dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const uint8_t *s = src + (size_t)y * stride + 3 * (size_t)(W - 1 - x);
+    uint8_t *d = dst + ((size_t)y * W + x) * 3;
+    d[0] = s[0];
+    d[1] = s[1];
+    d[2] = s[2];
+}
+
+cudaError_t launch_mirror_rgb(const uint8_t *src, int64_t stride, int H, int W, uint8_t *dst, cudaStream_t st) {
+    dim3 grid((W + 255) / 256, H);
+    k_mirror_rgb<<<grid, 256, 0, st>>>(src, stride, H, W, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_postprocess(const DevPlanes &PL, const float4 *labL, const float4 *labRm, float thr, int radius,
+                               float gamma, uint8_t *valid, float *filled, float *disp, cudaStream_t st) {
+    const int n = PL.H * PL.W;
+    k_lr_check<<<(n + 255) / 256, 256, 0, st>>>(labL, labRm, PL.H, PL.W, thr, valid);
+    k_fill<<<(n + 255) / 256, 256, 0, st>>>(labL, valid, PL.H, PL.W, filled);
+    const long long threads = 32LL * n;
+    k_wmedian<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(PL, valid, filled, radius, 1.0f / gamma, disp);
     return cudaGetLastError();
 }
 

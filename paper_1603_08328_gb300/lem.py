@@ -45,6 +45,10 @@ class lem_params(C.Structure):
     ]
 
 
+class lem_post_params(C.Structure):
+    _fields_ = [("lr_threshold", C.c_float), ("median_radius", C.c_int), ("median_gamma", C.c_float)]
+
+
 class lem_tuning(C.Structure):
     _fields_ = [("threads", C.c_int * 3), ("gr_interval", C.c_int * 3), ("strip_rows", C.c_int * 3),
                 ("ms", C.c_float * 3), ("ms_default", C.c_float * 3), ("configs_tried", C.c_int)]
@@ -116,6 +120,12 @@ def lib():
         L.lem_cnn_features.argtypes = [H, C.c_int, vp]
         L.lem_cnn_targets.argtypes = [H, C.c_int, vp]
         L.lem_cnn_propose.argtypes = [N, H]
+        L.lem_create_right_view.argtypes = [P(lem_image), P(lem_image), P(lem_params), P(H)]
+        L.lem_create_right_view.restype = C.c_int
+        L.lem_default_post_params.argtypes = [P(lem_post_params)]
+        L.lem_default_post_params.restype = None
+        L.lem_postprocess.argtypes = [H, H, P(lem_post_params), vp, vp]
+        L.lem_postprocess.restype = C.c_int
         L.lem_autotune.argtypes = [H, C.c_int, P(lem_tuning)]
         L.lem_autotune.restype = C.c_int
         for name in ("lem_set_proposals", "lem_get_proposals", "lem_cnn_create", "lem_cnn_destroy",
@@ -274,6 +284,25 @@ def lem_evals_per_iteration(h) -> int:
     return lib().lem_evals_per_iteration(h)
 
 
+def lem_create_right_view(left: lem_image, right: lem_image, params: lem_params):
+    h = C.c_void_p()
+    rc = lib().lem_create_right_view(C.byref(left), C.byref(right), C.byref(params), C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def lem_default_post_params(**overrides) -> lem_post_params:
+    pp = lem_post_params()
+    lib().lem_default_post_params(C.byref(pp))
+    for k, v in overrides.items():
+        setattr(pp, k, v)
+    return pp
+
+
+def lem_postprocess(hL, hR, pp: lem_post_params, disp_ptr, valid_ptr):
+    return lib().lem_postprocess(hL, hR, C.byref(pp), disp_ptr, valid_ptr)
+
+
 def lem_autotune(h, repeats, out=None):
     return lib().lem_autotune(h, repeats, C.byref(out) if out is not None else None)
 
@@ -353,9 +382,10 @@ class Stereo:
     """One handle on one pair.  Images are numpy uint8 (H, W, 3) host arrays or
     CUDA uint8 tensors; batch outputs are CUDA tensors."""
 
-    def __init__(self, left, right, stream=None, disp_ranges=None, **params):
+    def __init__(self, left, right, stream=None, disp_ranges=None, view="left", **params):
         """left/right: one image each, or lists of images (a batch of pairs); disp_ranges:
-        optional (disp_min, disp_max) per pair of a batch."""
+        optional (disp_min, disp_max) per pair of a batch.  view="right" estimates the right
+        image's labels (lem_create_right_view: labels in mirrored coordinates)."""
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -376,7 +406,11 @@ class Stereo:
             li = lis[0]
         else:
             li, ri = self._image(left), self._image(right)
-            self.h = lem_create(li, ri, self.params)
+            if view == "right":
+                self.h = lem_create_right_view(li, ri, self.params)
+            else:
+                self.h = lem_create(li, ri, self.params)
+        self.view = view
         self.H, self.W = li.height, li.width
         self.pairs = [lem_pair_info(self.h, b)[1:] for b in range(lem_pair_count(self.h))]
         self.total = sum(hh * ww for hh, ww, _ in self.pairs)
@@ -493,6 +527,15 @@ class Stereo:
 
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
+
+    def postprocess(self, right_view: "Stereo", **pp):
+        """Consistency check with the right view, occlusion filling and weighted median
+        (lem_postprocess); returns (disparity (H, W), consistent (H, W) bool) CUDA tensors."""
+        torch = self.torch
+        disp = torch.empty(self.H, self.W, dtype=torch.float32, device="cuda")
+        valid = torch.empty(self.H, self.W, dtype=torch.uint8, device="cuda")
+        self.check(lem_postprocess(self.h, right_view.h, lem_default_post_params(**pp), _ptr(disp), _ptr(valid)))
+        return disp, valid.bool()
 
     def autotune(self, repeats=2):
         """Picks the per-level launch configuration (lem_autotune); returns the lem_tuning."""
