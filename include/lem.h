@@ -106,6 +106,12 @@ typedef struct {
                                  (<= 400 nodes: 256, <= 2500: 512, else 1024)               */
     int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval */
     int level_strip_rows[3];  /* rows per strip of the cost pipeline; default strip_rows         */
+    int k_rans[3];        /* RANSAC proposals per region visit, per level (Algorithm 2, lines 5-8;
+                             default 0, the paper's setting outside its V3 experiments, where it
+                             uses 1).  Proposal indices K_prop .. K_prop + k_rans - 1 take the plane
+                             LO-RANSAC fits to the current disparities of the centre cell: 32
+                             three-pixel hypotheses drawn from the proposal's stream, 1 px inliers,
+                             the best refined twice by least squares. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -307,6 +313,16 @@ int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float
 int lem_mincut_batch_noalloc(const lem_region *regions, int n_regions, const int32_t *tcaps, const int32_t *ncaps,
                              uint8_t *take_alpha, int64_t *flow, int32_t *status, int max_rounds, int gr_interval,
                              void *stream);
+
+/* The candidate labels of one visit (Algorithm 2; the RANSAC and map candidates
+ * included) of each listed cell of pair 0 at grid level `level` and outer
+ * iteration `iter`, drawn from the current labels as lem_expand_group draws
+ * them when no move happens in between: proposal t of cell k is alpha[(k *
+ * nprop + t) * 3 .. + 2], nprop = k_prop + k_rans + (k_cnn if a map is set) +
+ * k_rand of that level.  cells: HOST, n_cells pairs (i, j); alpha: DEVICE.
+ * Synchronises the stream.  Errors: LEM_ERR_ARG, LEM_ERR_SHAPE (cell outside
+ * the grid), LEM_ERR_CUDA. */
+int lem_propose_batch(lem_handle *h, int iter, int level, const int *cells, int n_cells, float *alpha);
 
 /* ------------------------------------------------------------------------- */
 /* Right view and post-processing (Sec. 3.2 after Eq. photofunc, Sec. 3.4 end) */

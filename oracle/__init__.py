@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("reverse_order", C.c_int),
         ("visit", C.c_int),
         ("k_cnn", C.c_int * 3),
+        ("k_rans", C.c_int * 3),
     ]
 
 
@@ -64,7 +65,7 @@ PAPER_DEFAULTS = dict(gf_radius=10, gf_eps=1e-4, tau_col=10.0, tau_grad=2.0, alp
                       lam=1.0, tau_dis=1.0, eps_w=0.01, gamma=10.0, disp_min=0.0, disp_max=60.0,
                       n_levels=3, cell=(5, 15, 25), k_prop=(1, 2, 2), k_rand=(7, 0, 0),
                       quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0, visit=1,
-                      k_cnn=(0, 0, 0))
+                      k_cnn=(0, 0, 0), k_rans=(0, 0, 0))
 
 
 def make_params(**kw) -> Params:
@@ -72,7 +73,7 @@ def make_params(**kw) -> Params:
     d.update(kw)
     p = Params()
     for k, v in d.items():
-        if k in ("cell", "k_prop", "k_rand", "k_cnn"):
+        if k in ("cell", "k_prop", "k_rand", "k_cnn", "k_rans"):
             v = list(v) + [0] * (3 - len(v))
             setattr(p, k, (C.c_int * 3)(*v))
         else:
@@ -128,6 +129,7 @@ def lib():
                                  C.c_double, C.c_double, C.c_double, C.c_double, fp]
         L.lo_propose_map.argtypes = [fp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, fp]
         L.lo_set_proposals.argtypes = [C.c_void_p, fp]
+        L.lo_propose_ransac.argtypes = [fp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, fp]
         L.lo_init_state.argtypes = [C.c_void_p]
         L.lo_set_labels.argtypes = [C.c_void_p, fp]
         L.lo_get_state.argtypes = [C.c_void_p, fp, dp]
@@ -330,6 +332,16 @@ def propose_map(prop, stream, cell):
     out = np.empty(3, np.float32)
     cx0, cy0, cw, ch = cell
     lib().lo_propose_map(_ptr(prop, C.c_float), W, stream, cx0, cy0, cw, ch, _ptr(out, C.c_float))
+    return out
+
+
+def propose_ransac(lab, stream, cell):
+    """RANSAC candidate: a plane fitted to the disparities of the centre cell's labels."""
+    lab = _f32(lab)
+    W = lab.shape[1]
+    out = np.empty(3, np.float32)
+    cx0, cy0, cw, ch = cell
+    lib().lo_propose_ransac(_ptr(lab, C.c_float), W, stream, cx0, cy0, cw, ch, _ptr(out, C.c_float))
     return out
 
 

@@ -67,6 +67,7 @@ typedef struct {
     int reverse_order;    /* visit the regions of a group in reverse order        */
     int visit;            /* candidates drawn per region visit (1: Algorithm 2)   */
     int k_cnn[3];         /* candidates per visit cell taken from the proposal map */
+    int k_rans[3];        /* RANSAC plane candidates per visit (Algorithm 2, lines 5-8) */
 } lo_params;
 
 typedef struct {
@@ -1073,6 +1074,129 @@ void lo_propose_map(const float *map, int W, uint64_t stream, int cx0, int cy0, 
     alpha[2] = m[2];
 }
 
+/* RANSAC proposer (Algorithm 2, lines 5-8): a plane fitted to the current
+ * disparities of the centre cell C_ij by LO-RANSAC (Chum et al. 2003).  The paper
+ * gives no settings; the readings: the points are the pixels r of C_ij with their
+ * disparities d_r = (a u + b v) + c in FP64, taken on the 2^-20 grid (round half to
+ * even) so that every sum below is an exact integer; 32 hypotheses, each the plane
+ * through three pixels drawn uniformly from the proposal's stream (a repeated pixel
+ * or three collinear pixels make a hypothesis void); inliers are the points within
+ * 1 px of the plane; the hypothesis with the most inliers (the first on ties) is
+ * refined twice by a least-squares fit to its inliers (skipped with fewer than 3
+ * inliers or a singular system).  Coordinates are taken relative to the cell's
+ * corner.  With no valid hypothesis the candidate is the label of the first drawn
+ * pixel.  Every floating-point step below is one correctly rounded operation in the
+ * order written. */
+#define RANSAC_HYP 32
+#define RANSAC_LO 2
+#define RANSAC_Q 1048576.0 /* 2^20 */
+
+static int64_t ransac_dq(const float *f, int u, int v) {
+    const double d = ((double)f[0] * (double)u + (double)f[1] * (double)v) + (double)f[2];
+    return (int64_t)nearbyint(d * RANSAC_Q);
+}
+
+static int ransac_inliers(const int64_t *dq, int n, int cw, double a, double b, double c, unsigned char *in) {
+    int cnt = 0;
+    for (int k = 0; k < n; k++) {
+        const int x = k % cw, y = k / cw;
+        const double r = (double)dq[k] / RANSAC_Q - ((a * (double)x + b * (double)y) + c);
+        const int ok = fabs(r) <= 1.0;
+        if (in) in[k] = (unsigned char)ok;
+        cnt += ok;
+    }
+    return cnt;
+}
+
+void lo_propose_ransac(const float *lab, int W, uint64_t stream, int cx0, int cy0, int cw, int ch, float *alpha) {
+    uint64_t st = stream;
+    const int n = cw * ch;
+    int64_t *dq = (int64_t *)malloc(sizeof(int64_t) * n);
+    unsigned char *in = (unsigned char *)malloc(n);
+    for (int k = 0; k < n; k++) {
+        const int u = cx0 + k % cw, v = cy0 + k / cw;
+        dq[k] = ransac_dq(lab + ((size_t)v * W + u) * 3, u, v);
+    }
+    int best = -1, best_cnt = -1, first = -1;
+    double ba = 0, bb = 0, bc = 0;
+    for (int hyp = 0; hyp < RANSAC_HYP; hyp++) {
+        int id[3];
+        for (int j = 0; j < 3; j++) {
+            int k = (int)(sm_u01(&st) * n);
+            if (k >= n) k = n - 1;
+            id[j] = k;
+        }
+        if (first < 0) first = id[0];
+        if (id[0] == id[1] || id[0] == id[2] || id[1] == id[2]) continue;
+        const int64_t x0 = id[0] % cw, y0 = id[0] / cw, x1 = id[1] % cw, y1 = id[1] / cw;
+        const int64_t x2 = id[2] % cw, y2 = id[2] / cw;
+        const int64_t du1 = x1 - x0, dv1 = y1 - y0, du2 = x2 - x0, dv2 = y2 - y0;
+        const int64_t det = du1 * dv2 - du2 * dv1;
+        if (det == 0) continue;
+        const int64_t dd1 = dq[id[1]] - dq[id[0]], dd2 = dq[id[2]] - dq[id[0]];
+        const int64_t na = dd1 * dv2 - dd2 * dv1, nb = du1 * dd2 - du2 * dd1;
+        const double den = (double)det * RANSAC_Q;
+        const double a = (double)na / den, b = (double)nb / den;
+        const double c = ((double)dq[id[0]] / RANSAC_Q - a * (double)x0) - b * (double)y0;
+        const int cnt = ransac_inliers(dq, n, cw, a, b, c, NULL);
+        if (cnt > best_cnt) {
+            best_cnt = cnt;
+            best = hyp;
+            ba = a;
+            bb = b;
+            bc = c;
+        }
+    }
+    if (best < 0) {
+        const int k = first < 0 ? 0 : first;
+        const float *f = lab + ((size_t)(cy0 + k / cw) * W + cx0 + k % cw) * 3;
+        alpha[0] = f[0];
+        alpha[1] = f[1];
+        alpha[2] = f[2];
+        free(dq);
+        free(in);
+        return;
+    }
+    for (int it = 0; it < RANSAC_LO; it++) {
+        const int cnt = ransac_inliers(dq, n, cw, ba, bb, bc, in);
+        if (cnt < 3) break;
+        int64_t Suu = 0, Suv = 0, Su = 0, Svv = 0, Sv = 0, Sn = 0, Sud = 0, Svd = 0, Sd = 0;
+        for (int k = 0; k < n; k++) {
+            if (!in[k]) continue;
+            const int64_t x = k % cw, y = k / cw;
+            Suu += x * x;
+            Suv += x * y;
+            Su += x;
+            Svv += y * y;
+            Sv += y;
+            Sn += 1;
+            Sud += x * dq[k];
+            Svd += y * dq[k];
+            Sd += dq[k];
+        }
+        const double m00 = (double)Suu, m01 = (double)Suv, m02 = (double)Su, m11 = (double)Svv, m12 = (double)Sv;
+        const double m22 = (double)Sn, r0 = (double)Sud, r1 = (double)Svd, r2 = (double)Sd;
+        /* Cramer's rule on the symmetric system [m00 m01 m02; m01 m11 m12; m02 m12 m22] */
+        const double c00 = m11 * m22 - m12 * m12, c01 = m01 * m22 - m12 * m02, c02 = m01 * m12 - m11 * m02;
+        const double det = (m00 * c00 - m01 * c01) + m02 * c02;
+        if (det == 0.0) break;
+        const double da = (r0 * c00 - m01 * (r1 * m22 - m12 * r2)) + m02 * (r1 * m12 - m11 * r2);
+        const double db = (m00 * (r1 * m22 - m12 * r2) - r0 * c01) + m02 * (m01 * r2 - r1 * m02);
+        const double dc = (m00 * (m11 * r2 - r1 * m12) - m01 * (m01 * r2 - r1 * m02)) + r0 * c02;
+        const double den = det * RANSAC_Q;
+        ba = da / den;
+        bb = db / den;
+        bc = dc / den;
+    }
+    /* back to image coordinates */
+    const double c_img = (bc - ba * (double)cx0) - bb * (double)cy0;
+    alpha[0] = (float)ba;
+    alpha[1] = (float)bb;
+    alpha[2] = (float)c_img;
+    free(dq);
+    free(in);
+}
+
 /* Candidate alpha of one proposal (Algorithm 2).  perturb = 0: propagation,
  * alpha = f_r.  perturb = 1: the label f_r is turned into a disparity d and unit
  * normal n at r, d' = d + U[-rd, rd] (clamped to [dmin, dmax]), n' = n + rn * v
@@ -1215,12 +1339,12 @@ void lo_region_of(int H, int W, int s, int ci, int cj, int *R, int *C) {
     C[3] = cy1 - cy0;
 }
 
-/* Algorithm 2 at cell (i, j): K_prop propagation proposals, then K_rand
- * perturbation proposals with the perturbation size halved after each.  The
- * perturbation sizes are this call's own copies of the outer ones.
- * With a proposal map, k_cnn map proposals sit between the two kinds
- * (proposal indices K_prop .. K_prop + k_cnn - 1); k_cnn = 0 is the method as
- * published.
+/* Algorithm 2 at cell (i, j): K_prop propagation proposals, K_RANS RANSAC
+ * proposals, then K_rand perturbation proposals with the perturbation size
+ * halved after each.  The perturbation sizes are this call's own copies of the
+ * outer ones.  With a proposal map, k_cnn map proposals follow the RANSAC ones
+ * (proposal indices K_prop + K_RANS .. K_prop + K_RANS + k_cnn - 1); k_cnn = 0 is
+ * the method as published.
  * With visit = K > 1 (the batched schedule variant) the candidates of each run
  * of K consecutive proposals are all drawn from the labels at the start of
  * that run; their moves are then made one after the other, each against the
@@ -1230,19 +1354,23 @@ static void iterative_expansion(lo_ctx *c, int iter, int level, int ci, int cj, 
     const int H = c->H, W = c->W, s = c->p.cell[level];
     int R[4], C[4];
     lo_region_of(H, W, s, ci, cj, R, C);
-    const int kp = c->p.k_prop[level], kc = c->prop ? c->p.k_cnn[level] : 0;
-    const int nprop = kp + kc + c->p.k_rand[level];
+    const int kp = c->p.k_prop[level], kr = c->p.k_rans[level], kc = c->prop ? c->p.k_cnn[level] : 0;
+    const int nprop = kp + kr + kc + c->p.k_rand[level];
     const int K = c->p.visit < 1 ? 1 : (c->p.visit > 64 ? 64 : c->p.visit);
     float alpha[64][3];
     for (int t0 = 0; t0 < nprop; t0 += K) {
         const int t1 = t0 + K < nprop ? t0 + K : nprop;
         for (int t = t0; t < t1; t++) {
             const uint64_t stream = lo_proposal_stream(c->p.seed, iter, level, ci, cj, t);
-            if (t >= kp && t < kp + kc) {
+            if (t >= kp && t < kp + kr) {
+                lo_propose_ransac(c->lab, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
+                continue;
+            }
+            if (t >= kp + kr && t < kp + kr + kc) {
                 lo_propose_map(c->prop, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
                 continue;
             }
-            const int perturb = t >= kp + kc;
+            const int perturb = t >= kp + kr + kc;
             lo_propose(c->lab, W, stream, C[0], C[1], C[2], C[3], perturb, perturb ? rd : 0.0, perturb ? rn : 0.0,
                        c->p.disp_min, c->p.disp_max, alpha[t - t0]);
             if (perturb) {

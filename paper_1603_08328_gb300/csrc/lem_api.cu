@@ -129,8 +129,8 @@ int check_params(const lem_params *p) {
         if (p->cell[l] < 1) return fail(nullptr, LEM_ERR_ARG, "cell size must be >= 1");
         if (9 * p->cell[l] * p->cell[l] > LEM_MAX_REGION_NODES)
             return fail(nullptr, LEM_ERR_ARG, "cell size too large: a 3x3-cell region exceeds LEM_MAX_REGION_NODES");
-        if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_cnn[l] < 0 || p->k_cnn[l] > 64 ||
-            p->k_prop[l] + p->k_rand[l] < 1)
+        if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_cnn[l] < 0 || p->k_cnn[l] > 64 || p->k_rans[l] < 0 ||
+            p->k_rans[l] > 64 || p->k_prop[l] + p->k_rand[l] < 1)
             return fail(nullptr, LEM_ERR_ARG,
                         "each level needs a propagation or perturbation proposal; k_cnn must be 0..64");
     }
@@ -303,6 +303,7 @@ void lem_default_params(lem_params *p) {
     p->use_graph = 1;
     p->candidates_per_visit = 1;
     p->k_cnn[0] = p->k_cnn[1] = p->k_cnn[2] = 0;
+    p->k_rans[0] = p->k_rans[1] = p->k_rans[2] = 0;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
@@ -566,6 +567,7 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     lv.k_prop = h->p.k_prop[level];
     lv.k_rand = h->p.k_rand[level];
     lv.k_cnn = h->p.k_cnn[level];
+    lv.k_rans = h->p.k_rans[level];
     lv.threads = h->p.level_threads[level];
     if (h->prop && !h->prop_set)
         return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
@@ -962,6 +964,40 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     return LEM_OK;
 }
 
+int lem_propose_batch(lem_handle *h, int iter, int level, const int *cells, int n_cells, float *alpha) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (!cells || !alpha || n_cells < 1 || iter < 0 || level < 0 || level >= h->p.n_levels)
+        return fail(h, LEM_ERR_ARG, "cells/alpha NULL, n_cells < 1, or iter/level out of range");
+    if (h->prop && !h->prop_set) return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set");
+    const lem::PairDesc &pd = h->pairs[0];
+    const int s = h->p.cell[level];
+    const int nx = (pd.W + s - 1) / s, ny = (pd.H + s - 1) / s;
+    for (int k = 0; k < n_cells; ++k)
+        if (cells[2 * k] < 0 || cells[2 * k] >= nx || cells[2 * k + 1] < 0 || cells[2 * k + 1] >= ny)
+            return fail(h, LEM_ERR_SHAPE, "cell " + std::to_string(k) + " is outside the grid");
+    lem::Level lv;
+    lv.s = s;
+    lv.k_prop = h->p.k_prop[level];
+    lv.k_rand = h->p.k_rand[level];
+    lv.k_cnn = h->p.k_cnn[level];
+    lv.k_rans = h->p.k_rans[level];
+    lv.threads = 0;
+    lem::KParams kp = kparams(h);
+    kp.seed = pd.seed;
+    kp.disp_min = pd.disp_min;
+    kp.disp_max = pd.disp_max;
+    int2 *dc = nullptr;
+    LEM_CUDA(h, cudaMalloc(&dc, sizeof(int2) * n_cells));
+    cudaError_t e = cudaMemcpyAsync(dc, cells, sizeof(int2) * n_cells, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+        e = lem::launch_propose_batch(planes(h, 0), kp, lv, level, iter, dc, n_cells, h->lab + pd.off,
+                                      h->prop ? h->prop + pd.off : nullptr, alpha, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(dc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lem_propose_batch");
+    return LEM_OK;
+}
+
 void lem_default_post_params(lem_post_params *pp) {
     if (!pp) return;
     pp->lr_threshold = 1.0f;
@@ -998,7 +1034,7 @@ int64_t lem_evals_per_iteration(const lem_handle *h) {
         for (int l = 0; l < h->p.n_levels; ++l) {
             const int s = h->p.cell[l];
             const int nx = (pd.W + s - 1) / s, ny = (pd.H + s - 1) / s;
-            const int np = h->p.k_prop[l] + h->p.k_rand[l] + (h->prop ? h->p.k_cnn[l] : 0);
+            const int np = h->p.k_prop[l] + h->p.k_rand[l] + h->p.k_rans[l] + (h->prop ? h->p.k_cnn[l] : 0);
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
                     const int x0 = std::max(0, (i - 1) * s), x1 = std::min(pd.W, (i + 2) * s);

@@ -46,7 +46,8 @@ struct PairDesc {
 struct Level {
     int s;              // cell size
     int k_prop, k_rand;
-    int k_cnn;          // map candidates (proposal indices k_prop .. k_prop + k_cnn - 1)
+    int k_cnn;          // map candidates (after the RANSAC candidates)
+    int k_rans;         // RANSAC plane candidates (proposal indices k_prop .. k_prop + k_rans - 1)
     int threads;        // CTA size of the expansion kernel (0: by region size)
 };
 
@@ -98,6 +99,10 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
                                 cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
+// candidates of one visit of each listed cell (see lem_propose_batch)
+cudaError_t launch_propose_batch(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                                 const int2 *cells, int n_cells, const float4 *lab, const float4 *prop, float *alpha,
+                                 cudaStream_t st);
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st);
 cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,

@@ -226,6 +226,180 @@ __device__ float4 propose(const float4 *lab, int W, unsigned long long stream, i
     return plane_from(m0, m1, m2, ru, rv, dp);
 }
 
+
+// ---------------------------------------------------------------------------
+// RANSAC proposer (Algorithm 2, lines 5-8): LO-RANSAC plane fit to the current
+// disparities of the centre cell, computed by the whole CTA.  The steps and their
+// rounding are the oracle's: disparities on the 2^-20 grid, 32 hypotheses through
+// three pixels drawn from the proposal's stream, 1 px inliers, the best (first on
+// ties) refined twice by least squares with exact integer sums and Cramer's rule
+// in FP64 with one rounding per operation, cell-relative coordinates.
+// ---------------------------------------------------------------------------
+constexpr int kRansacHyp = 32;
+constexpr int kRansacLo = 2;
+constexpr int kRansacMaxCell = 25 * 25;
+constexpr double kRansacQ = 1048576.0;
+
+struct RansacSmem {
+    long long dq[kRansacMaxCell];
+    int id[kRansacHyp * 3];
+    double pl[kRansacHyp * 3];
+    int cnt[kRansacHyp];
+    int ok[kRansacHyp];
+    unsigned long long sums[10];
+    double best[3];
+    int state;  // 0: no valid hypothesis, 1: plane in best
+};
+
+__device__ __forceinline__ bool ransac_inlier(long long dq, int x, int y, double a, double b, double c) {
+    const double r = __dsub_rn(__ddiv_rn(__ll2double_rn(dq), kRansacQ),
+                               __dadd_rn(__dadd_rn(__dmul_rn(a, (double)x), __dmul_rn(b, (double)y)), c));
+    return fabs(r) <= 1.0;
+}
+
+// all threads of the CTA; *out written by thread 0; ends with a barrier
+__device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, int cx0, int cy0, int cw, int chh,
+                           RansacSmem *R, float4 *out) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    const int n = cw * chh;
+    for (int k = tid; k < n; k += nt) {
+        const int x = k % cw, y = k / cw, u = cx0 + x, v = cy0 + y;
+        const float4 f = lab[(size_t)v * W + u];
+        const double d = __dadd_rn(__dadd_rn(__dmul_rn((double)f.x, (double)u), __dmul_rn((double)f.y, (double)v)),
+                                   (double)f.z);
+        R->dq[k] = __double2ll_rn(__dmul_rn(d, kRansacQ));
+    }
+    if (tid == 0) {
+        Rng g{stream};
+        for (int j = 0; j < 3 * kRansacHyp; ++j) {
+            int k = (int)__dmul_rn(g.u01(), (double)n);
+            if (k >= n) k = n - 1;
+            R->id[j] = k;
+        }
+    }
+    __syncthreads();
+    if (tid < kRansacHyp) {
+        const int i0 = R->id[3 * tid], i1 = R->id[3 * tid + 1], i2 = R->id[3 * tid + 2];
+        int ok = 0;
+        if (i0 != i1 && i0 != i2 && i1 != i2) {
+            const long long x0 = i0 % cw, y0 = i0 / cw, x1 = i1 % cw, y1 = i1 / cw, x2 = i2 % cw, y2 = i2 / cw;
+            const long long du1 = x1 - x0, dv1 = y1 - y0, du2 = x2 - x0, dv2 = y2 - y0;
+            const long long det = du1 * dv2 - du2 * dv1;
+            if (det != 0) {
+                const long long dd1 = R->dq[i1] - R->dq[i0], dd2 = R->dq[i2] - R->dq[i0];
+                const long long na = dd1 * dv2 - dd2 * dv1, nb = du1 * dd2 - du2 * dd1;
+                const double den = __dmul_rn(__ll2double_rn(det), kRansacQ);
+                const double a = __ddiv_rn(__ll2double_rn(na), den), b = __ddiv_rn(__ll2double_rn(nb), den);
+                const double c = __dsub_rn(__dsub_rn(__ddiv_rn(__ll2double_rn(R->dq[i0]), kRansacQ),
+                                                     __dmul_rn(a, (double)x0)),
+                                           __dmul_rn(b, (double)y0));
+                R->pl[3 * tid] = a;
+                R->pl[3 * tid + 1] = b;
+                R->pl[3 * tid + 2] = c;
+                ok = 1;
+            }
+        }
+        R->ok[tid] = ok;
+    }
+    __syncthreads();
+    for (int hy = warp; hy < kRansacHyp; hy += nwarp) {
+        int c = 0;
+        if (R->ok[hy]) {
+            const double a = R->pl[3 * hy], b = R->pl[3 * hy + 1], cc = R->pl[3 * hy + 2];
+            for (int k = lane; k < n; k += 32) c += ransac_inlier(R->dq[k], k % cw, k / cw, a, b, cc) ? 1 : 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) R->cnt[hy] = R->ok[hy] ? c : -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int best = -1, bc = -1;
+        for (int hy = 0; hy < kRansacHyp; ++hy)
+            if (R->cnt[hy] > bc) {
+                bc = R->cnt[hy];
+                best = hy;
+            }
+        if (bc < 0) {
+            R->state = 0;
+            const int k = R->id[0];
+            const float4 f = lab[(size_t)(cy0 + k / cw) * W + cx0 + k % cw];
+            *out = make_float4(f.x, f.y, f.z, 0.f);
+        } else {
+            R->state = 1;
+            R->best[0] = R->pl[3 * best];
+            R->best[1] = R->pl[3 * best + 1];
+            R->best[2] = R->pl[3 * best + 2];
+        }
+    }
+    __syncthreads();
+    if (R->state == 0) return;  // (uniform) the barrier above published *out
+    for (int it = 0; it < kRansacLo; ++it) {
+        if (tid < 10) R->sums[tid] = 0ull;
+        __syncthreads();
+        const double a = R->best[0], b = R->best[1], c = R->best[2];
+        long long s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = tid; k < n; k += nt) {
+            const long long x = k % cw, y = k / cw, dq = R->dq[k];
+            if (!ransac_inlier(dq, (int)x, (int)y, a, b, c)) continue;
+            s[0] += x * x;
+            s[1] += x * y;
+            s[2] += x;
+            s[3] += y * y;
+            s[4] += y;
+            s[5] += 1;
+            s[6] += x * dq;
+            s[7] += y * dq;
+            s[8] += dq;
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            long long vq = s[q];
+            for (int o = 16; o > 0; o >>= 1) vq += __shfl_xor_sync(0xffffffffu, vq, o);
+            if (lane == 0 && vq != 0) atomicAdd(&R->sums[q], (unsigned long long)vq);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R->sums[9] = 0ull;  // 1: stop refining
+            if ((long long)R->sums[5] < 3) {
+                R->sums[9] = 1ull;
+            } else {
+                const double m00 = __ll2double_rn((long long)R->sums[0]), m01 = __ll2double_rn((long long)R->sums[1]);
+                const double m02 = __ll2double_rn((long long)R->sums[2]), m11 = __ll2double_rn((long long)R->sums[3]);
+                const double m12 = __ll2double_rn((long long)R->sums[4]), m22 = __ll2double_rn((long long)R->sums[5]);
+                const double r0 = __ll2double_rn((long long)R->sums[6]), r1 = __ll2double_rn((long long)R->sums[7]);
+                const double r2 = __ll2double_rn((long long)R->sums[8]);
+                const double c00 = __dsub_rn(__dmul_rn(m11, m22), __dmul_rn(m12, m12));
+                const double c01 = __dsub_rn(__dmul_rn(m01, m22), __dmul_rn(m12, m02));
+                const double c02 = __dsub_rn(__dmul_rn(m01, m12), __dmul_rn(m11, m02));
+                const double det = __dadd_rn(__dsub_rn(__dmul_rn(m00, c00), __dmul_rn(m01, c01)), __dmul_rn(m02, c02));
+                if (det == 0.0) {
+                    R->sums[9] = 1ull;
+                } else {
+                    const double t1 = __dsub_rn(__dmul_rn(r1, m22), __dmul_rn(m12, r2));
+                    const double t2 = __dsub_rn(__dmul_rn(r1, m12), __dmul_rn(m11, r2));
+                    const double t3 = __dsub_rn(__dmul_rn(m01, r2), __dmul_rn(r1, m02));
+                    const double t4 = __dsub_rn(__dmul_rn(m11, r2), __dmul_rn(r1, m12));
+                    const double da = __dadd_rn(__dsub_rn(__dmul_rn(r0, c00), __dmul_rn(m01, t1)), __dmul_rn(m02, t2));
+                    const double db = __dadd_rn(__dsub_rn(__dmul_rn(m00, t1), __dmul_rn(r0, c01)), __dmul_rn(m02, t3));
+                    const double dc = __dadd_rn(__dsub_rn(__dmul_rn(m00, t4), __dmul_rn(m01, t3)), __dmul_rn(r0, c02));
+                    const double den = __dmul_rn(det, kRansacQ);
+                    R->best[0] = __ddiv_rn(da, den);
+                    R->best[1] = __ddiv_rn(db, den);
+                    R->best[2] = __ddiv_rn(dc, den);
+                }
+            }
+        }
+        __syncthreads();
+        if (R->sums[9]) break;  // (uniform)
+    }
+    if (tid == 0) {
+        const double a = R->best[0], b = R->best[1];
+        const double c = __dsub_rn(__dsub_rn(R->best[2], __dmul_rn(a, (double)cx0)), __dmul_rn(b, (double)cy0));
+        *out = make_float4(__double2float_rn(a), __double2float_rn(b), __double2float_rn(c), 0.f);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // K0: packing, contrast weights, guide statistics, random init
 // ---------------------------------------------------------------------------
@@ -1282,29 +1456,33 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     double rn = ldexp(1.0, -iter);
     long long acc = 0, hits = 0;
     CutCount cc{0, 0, 0};
-    // proposal indices: [0, k_prop) propagation, [k_prop, k_prop + kc) map
-    // candidates of the learned proposer, then k_rand perturbations
-    const int kc = prop ? lv.k_cnn : 0;
-    const int nprop = lv.k_prop + kc + lv.k_rand;
+    // proposal indices: [0, k_prop) propagation, then k_rans RANSAC planes, then
+    // kc map candidates of the learned proposer, then k_rand perturbations
+    const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
+    const int nprop = lv.k_prop + kr + kc + lv.k_rand;
     const int K = kp.visit;
     for (int t0 = 0; t0 < nprop; t0 += K) {
         const int t1 = min(nprop, t0 + K);
         // the candidates of one visit, all drawn from the labels at its start
-        // (K = 1: Algorithm 2 as printed)
-        if (threadIdx.x == 0) {
-            for (int t = t0; t < t1; ++t) {
-                const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
-                if (t >= lv.k_prop && t < lv.k_prop + kc) {
-                    s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
-                    continue;
-                }
-                const bool perturb = t >= lv.k_prop + kc;
-                s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
-                                          perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
-                if (perturb) {
-                    rd *= 0.5;
-                    rn *= 0.5;
-                }
+        // (K = 1: Algorithm 2 as printed): propagation, RANSAC (whole CTA), map
+        // candidates, perturbation
+        for (int t = t0; t < t1; ++t) {
+            const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+            if (t >= lv.k_prop && t < lv.k_prop + kr) {
+                ransac_cta(lab, W, stream, cx0, cy0, cw, chh, reinterpret_cast<RansacSmem *>(smf), &s_alpha[t - t0]);
+                continue;
+            }
+            if (threadIdx.x != 0) continue;
+            if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
+                s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+                continue;
+            }
+            const bool perturb = t >= lv.k_prop + kr + kc;
+            s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
+                                      perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
+            if (perturb) {
+                rd *= 0.5;
+                rn *= 0.5;
             }
         }
         __syncthreads();
@@ -1563,6 +1741,48 @@ __global__ void k_props_out(int n, const float4 *prop, float *abc) {
     abc[3 * (size_t)p + 2] = f.z;
 }
 
+// The candidates of one visit of each listed cell, drawn from the current labels
+// as k_expand_group draws them (no moves in between): one CTA per cell.
+//   cells: (ci, cj) per CTA; alpha: per cell, nprop labels (a, b, c)
+__global__ void k_propose_batch(DevPlanes P, KParams kp, Level lv, int level, int iter, const int2 *cells,
+                                const float4 *lab, const float4 *prop, float *alpha) {
+    extern __shared__ __align__(16) float smf[];
+    __shared__ float4 s_one;
+    const int W = P.W, H = P.H, s = lv.s;
+    const int ci = cells[blockIdx.x].x, cj = cells[blockIdx.x].y;
+    const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
+    double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
+    double rn = ldexp(1.0, -iter);
+    const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
+    const int nprop = lv.k_prop + kr + kc + lv.k_rand;
+    for (int t = 0; t < nprop; ++t) {
+        const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+        if (t >= lv.k_prop && t < lv.k_prop + kr) {
+            ransac_cta(lab, W, stream, cx0, cy0, cw, chh, reinterpret_cast<RansacSmem *>(smf), &s_one);
+        } else if (threadIdx.x == 0) {
+            if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
+                s_one = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+            } else {
+                const bool perturb = t >= lv.k_prop + kr + kc;
+                s_one = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0, perturb ? rn : 0.0,
+                                kp.disp_min, kp.disp_max);
+                if (perturb) {
+                    rd *= 0.5;
+                    rn *= 0.5;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float *o = alpha + ((size_t)blockIdx.x * nprop + t) * 3;
+            o[0] = s_one.x;
+            o[1] = s_one.y;
+            o[2] = s_one.z;
+        }
+        __syncthreads();
+    }
+}
+
 // A9: quantised energy, per-block partial sums
 __global__ void k_energy(DevPlanes P, KParams kp, const float4 *lab, long long *partials) {
     __shared__ long long red[33];
@@ -1745,7 +1965,8 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     if (n_items == 0) return cudaSuccess;
     const int s = lv.s;
     const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
-    const size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
+    size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
+    if (lv.k_rans > 0) sm = std::max(sm, sizeof(RansacSmem));
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
     if (nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
@@ -1757,6 +1978,17 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
 }
 
 __global__ void k_increment(int *x) { *x += 1; }
+
+cudaError_t launch_propose_batch(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                                 const int2 *cells, int n_cells, const float4 *lab, const float4 *prop, float *alpha,
+                                 cudaStream_t st) {
+    if (n_cells == 0) return cudaSuccess;
+    const size_t sm = sizeof(RansacSmem);
+    cudaError_t e = set_smem((const void *)k_propose_batch, sm);
+    if (e != cudaSuccess) return e;
+    k_propose_batch<<<n_cells, 128, sm, st>>>(P, kp, lv, level, iter, cells, lab, prop, alpha);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_increment(int *x, cudaStream_t st) {
     k_increment<<<1, 1, 0, st>>>(x);

@@ -42,6 +42,7 @@ class lem_params(C.Structure):
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
+        ("k_rans", C.c_int * 3),
     ]
 
 
@@ -120,6 +121,8 @@ def lib():
         L.lem_cnn_features.argtypes = [H, C.c_int, vp]
         L.lem_cnn_targets.argtypes = [H, C.c_int, vp]
         L.lem_cnn_propose.argtypes = [N, H]
+        L.lem_propose_batch.argtypes = [H, C.c_int, C.c_int, vp, C.c_int, vp]
+        L.lem_propose_batch.restype = C.c_int
         L.lem_create_right_view.argtypes = [P(lem_image), P(lem_image), P(lem_params), P(H)]
         L.lem_create_right_view.restype = C.c_int
         L.lem_default_post_params.argtypes = [P(lem_post_params)]
@@ -155,7 +158,8 @@ def lem_default_params(**overrides) -> lem_params:
     for k, v in overrides.items():
         if k == "lambda":
             k = "lam"
-        if k in ("cell", "k_prop", "k_rand", "k_cnn", "level_threads", "level_gr_interval", "level_strip_rows"):
+        if k in ("cell", "k_prop", "k_rand", "k_cnn", "k_rans", "level_threads", "level_gr_interval",
+                 "level_strip_rows"):
             v = list(v) + [0] * (3 - len(v))
             v = (C.c_int * 3)(*v)
         setattr(p, k, v)
@@ -282,6 +286,11 @@ def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, 
 
 def lem_evals_per_iteration(h) -> int:
     return lib().lem_evals_per_iteration(h)
+
+
+def lem_propose_batch(h, it, level, cells, alpha_ptr):
+    arr = np.ascontiguousarray(np.asarray(cells, np.int32).reshape(-1, 2))
+    return lib().lem_propose_batch(h, it, level, C.c_void_p(arr.ctypes.data), arr.shape[0], alpha_ptr)
 
 
 def lem_create_right_view(left: lem_image, right: lem_image, params: lem_params):
@@ -527,6 +536,12 @@ class Stereo:
 
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
+
+    def proposals_of(self, it, level, cells, nprop):
+        """Candidates of one visit of each cell (lem_propose_batch): (n_cells, nprop, 3) numpy."""
+        out = self.torch.empty(len(cells) * nprop * 3, dtype=self.torch.float32, device="cuda")
+        self.check(lem_propose_batch(self.h, it, level, cells, _ptr(out)))
+        return out.cpu().numpy().reshape(len(cells), nprop, 3)
 
     def postprocess(self, right_view: "Stereo", **pp):
         """Consistency check with the right view, occlusion filling and weighted median

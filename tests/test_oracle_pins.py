@@ -554,3 +554,54 @@ def test_map_proposals_are_exact_moves_and_help(tiny_pair):
         return (np.abs(lab[..., 0] * u + lab[..., 1] * v + lab[..., 2] - gt) > 1.0).mean()
     assert bad(om) < bad(o0) - 0.02
     assert om.energy()[1] < o0.energy()[1]
+
+
+def _plane_labels(H, W, a, b, c):
+    lab = np.empty((H, W, 3), np.float32)
+    lab[..., 0], lab[..., 1], lab[..., 2] = a, b, c
+    return lab
+
+
+def test_ransac_recovers_a_plane_among_outliers():
+    """Algorithm 2, lines 5-8 (LO-RANSAC on the centre cell): labels of one plane, 30 % of
+    them replaced by labels 5-20 px off it, give back that plane."""
+    rng = np.random.default_rng(3)
+    H, W = 40, 60
+    a, b, c = 0.125, -0.0625, 17.5           # multiples of 2^-10: exact disparities
+    lab = _plane_labels(H, W, a, b, c)
+    mask = rng.random((H, W)) < 0.3
+    off = rng.uniform(5, 20, size=(H, W)).astype(np.float32)
+    lab[..., 2] = np.where(mask, lab[..., 2] + off, lab[..., 2])
+    for k in range(20):
+        st = oracle.proposal_stream(4, 0, 2, 1, 1, k)
+        al = oracle.propose_ransac(lab, st, (25, 10, 25, 25))
+        assert np.allclose(al, [a, b, c], rtol=0, atol=2e-6), al
+
+
+def test_ransac_degenerate_cell_falls_back_to_a_drawn_label():
+    """A one-pixel-wide cell has only collinear points: every hypothesis is void and the
+    candidate is the label of the first drawn pixel (one of the cell's labels)."""
+    rng = np.random.default_rng(4)
+    lab = rng.normal(size=(10, 8, 3)).astype(np.float32)
+    for k in range(10):
+        al = oracle.propose_ransac(lab, oracle.proposal_stream(1, 0, 0, 0, 0, k), (3, 2, 1, 5))
+        assert any((al == lab[y, 3]).all() for y in range(2, 7))
+
+
+def test_ransac_candidates_are_exact_moves(tiny_pair):
+    """K_RANS = 1 (between propagation and perturbation): every move is still an exact
+    expansion, so the energy never increases, and the cost cache stays exact."""
+    kw = dict(TINY_PARAMS, k_rans=(1,))
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **kw)
+    o.init_state()
+    q_prev = o.energy()[1]
+    for g in range(16):
+        o.expand_group(0, 0, g)
+        q = o.energy()[1]
+        assert q <= q_prev
+        q_prev = q
+    lab, cost = o.state()
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        y, x = int(rng.integers(0, o.H)), int(rng.integers(0, o.W))
+        assert cost[y, x] == pytest.approx(o.phi_def(lab[y, x], x, y), abs=1e-11)
