@@ -54,6 +54,7 @@ def parse():
                          "comma-separated values (e.g. 256,512,512/16,16,16/8,32,16); skips the autotuner")
     ap.add_argument("--no-time-to-energy", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
+    ap.add_argument("--no-bf", action="store_true", help="skip the LE-BF variant timing")
     ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8"],
                     help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs "
                          "(one JSON line of its own)")
@@ -416,6 +417,61 @@ def run_batch8_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def bf_flops(H, W, r, x0, y0, w, h):
+    """FP32 operations of the LE-BF data term of one candidate on region R: about 30 per
+    raw cost over M (R grown by the window radius 2 r') and one multiply-add (2 flops) per
+    window pixel of every output pixel, windows clipped to the image.  The colour weights
+    come from a 766-entry table of the integer L1 distance and are not counted."""
+    import numpy as np
+    R = 2 * r
+    mw = min(W, x0 + w + R) - max(0, x0 - R)
+    mh = min(H, y0 + h + R) - max(0, y0 - R)
+    xs = np.arange(x0, x0 + w)
+    ys = np.arange(y0, y0 + h)
+    cx = np.minimum(W - 1, xs + R) - np.maximum(0, xs - R) + 1
+    cy = np.minimum(H - 1, ys + R) - np.maximum(0, ys - R) + 1
+    return 30 * mw * mh + 2 * int(cx.sum()) * int(cy.sum())
+
+
+def bf_timing(lem, pair, stream, seed, flush, steps=3):
+    """The LE-BF variant (Sec. 4: bilateral weights over the 41 x 41 window, lambda = 20)
+    on the same pair: outer iterations 1 .. steps timed with CUDA events (L2 flushed
+    before each), evals/s, and the data term's algorithmic FP32 rate against the FP32
+    peak."""
+    import torch
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, data_term=lem.LEM_DATA_BF,
+                   lam=20.0, **PARAMS)
+    H, W = pair["left"].shape[:2]
+    g.iterate(1, stats=False)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.check(lem.lem_expand_iteration(g.h, 1, None))
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    st = g.iterate(0)
+    evals = g.evals_per_iteration()
+    r = g.params.gf_radius
+    flops = 0
+    for l in range(g.params.n_levels):
+        s = g.params.cell[l]
+        nprop = g.params.k_prop[l] + g.params.k_rand[l]
+        for regs in region_geometry(H, W, s).values():
+            flops += nprop * sum(bf_flops(H, W, r, *R) for R in regs)
+    g.close()
+    t = sum(ts) / len(ts)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"ms_per_iteration": 1e3 * t, "evals_per_s": evals / t, "data_term_tflops": flops / t / 1e12,
+            "frac": flops / t / 1e12 / peak, "peak_tflops": peak, "maxflow_limit": st.maxflow_limit,
+            "config": "data_term = LE-BF, lambda = 20, gamma_bf = 10, default launch configuration, "
+                      f"iterations 2-{steps + 1}, L2 flushed between iterations",
+            "note": "whole-iteration time (cuts included); flops count only the data term"}
+
+
 def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
     """Time (CUDA events around each outer iteration, learned proposals' inference
     included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
@@ -594,6 +650,7 @@ def run_lem(args):
 
     tte = None if args.no_time_to_energy else time_to_energy(lem, pair, params, stream, seed=21 + rank)
     prop = None if args.no_proposer else proposer_timing(lem, stream)
+    lebf = None if args.no_bf else bf_timing(lem, pair, stream, seed=31 + rank, flush=flush)
 
     if rank != 0:
         return
@@ -621,6 +678,7 @@ def run_lem(args):
         "energy": {"before": e0, "after": e1},
         "time_to_energy": tte,
         "proposer": prop,
+        "le_bf": lebf,
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,

@@ -42,6 +42,8 @@ extern "C" {
 #define LEM_ERR_OOM (-5)           /* device allocation failed                           */
 
 /* internal storage of the packed images */
+#define LEM_DATA_GF 0
+#define LEM_DATA_BF 1
 #define LEM_STORE_F32 0
 #define LEM_STORE_F16 1
 #define LEM_STORE_BF16 2
@@ -112,6 +114,11 @@ typedef struct {
                              LO-RANSAC fits to the current disparities of the centre cell: 32
                              three-pixel hypotheses drawn from the proposal's stream, 1 px inliers,
                              the best refined twice by least squares. */
+    int data_term;        /* LEM_DATA_GF (default): guided-filter weights (Eq. gf, LE-GF);
+                             LEM_DATA_BF: bilateral weights exp(-|I_p - I_s|_1 / bf_gamma) over the
+                             (4r'+1)^2 window, not normalised, O(|W|) per pixel (Sec. 4, LE-BF; the
+                             paper uses lambda = 20 with it) */
+    double bf_gamma;      /* LE-BF weight scale on 0..255 colours (default 10)                     */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */

@@ -57,6 +57,8 @@ class Params(C.Structure):
         ("visit", C.c_int),
         ("k_cnn", C.c_int * 3),
         ("k_rans", C.c_int * 3),
+        ("data_term", C.c_int),
+        ("bf_gamma", C.c_double),
     ]
 
 
@@ -65,7 +67,7 @@ PAPER_DEFAULTS = dict(gf_radius=10, gf_eps=1e-4, tau_col=10.0, tau_grad=2.0, alp
                       lam=1.0, tau_dis=1.0, eps_w=0.01, gamma=10.0, disp_min=0.0, disp_max=60.0,
                       n_levels=3, cell=(5, 15, 25), k_prop=(1, 2, 2), k_rand=(7, 0, 0),
                       quant_scale=65536.0, seed=1, n_threads=0, reverse_order=0, visit=1,
-                      k_cnn=(0, 0, 0), k_rans=(0, 0, 0))
+                      k_cnn=(0, 0, 0), k_rans=(0, 0, 0), data_term=0, bf_gamma=10.0)
 
 
 def make_params(**kw) -> Params:
@@ -104,6 +106,8 @@ def lib():
         L.lo_phi_def.restype = C.c_double
         L.lo_phi_def.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
         L.lo_phi_weights.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+        L.lo_phi_bf.restype = C.c_double
+        L.lo_phi_bf.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
         L.lo_region_cost.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, fp, dp]
         L.lo_psibar.restype = C.c_double
         L.lo_psibar.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, fp, fp]
@@ -202,6 +206,10 @@ class Oracle:
     def phi_def(self, abc, u, v):
         a, b, c = (float(x) for x in _f32(abc))
         return lib().lo_phi_def(self.h, a, b, c, int(u), int(v))
+
+    def phi_bf(self, abc, u, v):
+        a, b, c = (float(x) for x in _f32(abc))
+        return lib().lo_phi_bf(self.h, a, b, c, int(u), int(v))
 
     def phi_weights(self, u, v):
         r = self.p["gf_radius"]

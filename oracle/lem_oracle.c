@@ -68,6 +68,8 @@ typedef struct {
     int visit;            /* candidates drawn per region visit (1: Algorithm 2)   */
     int k_cnn[3];         /* candidates per visit cell taken from the proposal map */
     int k_rans[3];        /* RANSAC plane candidates per visit (Algorithm 2, lines 5-8) */
+    int data_term;        /* 0: guided filter (LE-GF), 1: bilateral weights (LE-BF)  */
+    double bf_gamma;      /* LE-BF weight scale on 0..255 colours                    */
 } lo_params;
 
 typedef struct {
@@ -427,8 +429,32 @@ void lo_phi_weights(const lo_ctx *c, int pu, int pv, double *out) {
  * window centre k in R grown by r', then their window means at p in R.  Box
  * sums are plain separable sums over the clipped windows.  out is w*h,
  * row-major. */
+/* LE-BF data term (Sec. 4, "LE-BF"): the weights of Eq. unary are bilateral,
+ * w_ps = exp(-|I_p - I_s|_1 / gamma) on the 0..255 left colours, "defined
+ * similarly to Eq. smweight" (readings: gamma = bf_gamma, default 10 like the
+ * smoothness weight; the window is the LE-GF matching window, (4r'+1)^2 clipped
+ * to the image; the weights are not normalised, as in Eq. smweight), so
+ * phi_p(f) = sum_{s in W_p} w_ps rho(s|f), O(|W|) per pixel. */
+double lo_phi_bf(const lo_ctx *c, double a, double b, double cc, int pu, int pv) {
+    const int H = c->H, W = c->W, R = 2 * c->p.gf_radius;
+    const double *lp = c->Lc + ((size_t)pv * W + pu) * 4;
+    double sum = 0.0;
+    for (int sv = imax(0, pv - R); sv <= imin(H - 1, pv + R); sv++)
+        for (int su = imax(0, pu - R); su <= imin(W - 1, pu + R); su++) {
+            const double *ls = c->Lc + ((size_t)sv * W + su) * 4;
+            const double l1 = fabs(lp[0] - ls[0]) + fabs(lp[1] - ls[1]) + fabs(lp[2] - ls[2]);
+            sum += exp(-l1 / c->p.bf_gamma) * lo_rho(c, a, b, cc, su, sv);
+        }
+    return sum;
+}
+
 void lo_region_cost(const lo_ctx *c, int x0, int y0, int w, int h, const float *abc, double *out) {
     const int H = c->H, W = c->W, r = c->p.gf_radius;
+    if (c->p.data_term == 1) {
+        for (int y = 0; y < h; y++)
+            for (int x = 0; x < w; x++) out[y * w + x] = lo_phi_bf(c, abc[0], abc[1], abc[2], x0 + x, y0 + y);
+        return;
+    }
     const double a = abc[0], b = abc[1], cc = abc[2];
     int Mx0 = imax(x0 - 2 * r, 0), Mx1 = imin(x0 + w + 2 * r, W);
     int My0 = imax(y0 - 2 * r, 0), My1 = imin(y0 + h + 2 * r, H);

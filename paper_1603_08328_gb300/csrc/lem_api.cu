@@ -117,6 +117,8 @@ lem::KParams kparams(const lem_handle *h) {
     k.gr_interval = p.gr_interval;
     k.T = p.strip_rows;
     k.visit = p.candidates_per_visit;
+    k.bf = p.data_term == LEM_DATA_BF ? 1 : 0;
+    k.bf_inv_gamma = (float)(1.0 / p.bf_gamma);
     return k;
 }
 
@@ -142,6 +144,9 @@ int check_params(const lem_params *p) {
     if (p->max_rounds < 1 || p->gr_interval < 1) return fail(nullptr, LEM_ERR_ARG, "max_rounds/gr_interval must be >= 1");
     if (p->strip_rows < 4 || p->strip_rows > 64 || p->strip_rows % 4)
         return fail(nullptr, LEM_ERR_ARG, "strip_rows must be a multiple of 4 in [4, 64]");
+    if (p->data_term != LEM_DATA_GF && p->data_term != LEM_DATA_BF)
+        return fail(nullptr, LEM_ERR_ARG, "data_term must be LEM_DATA_GF or LEM_DATA_BF");
+    if (!(p->bf_gamma > 0)) return fail(nullptr, LEM_ERR_ARG, "bf_gamma must be > 0");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
@@ -304,6 +309,8 @@ void lem_default_params(lem_params *p) {
     p->candidates_per_visit = 1;
     p->k_cnn[0] = p->k_cnn[1] = p->k_cnn[2] = 0;
     p->k_rans[0] = p->k_rans[1] = p->k_rans[2] = 0;
+    p->data_term = LEM_DATA_GF;
+    p->bf_gamma = 10.0;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }

@@ -592,7 +592,7 @@ struct Grid2 {
 // Every sliding window sum restarts at rows (and columns) Ky0 + 4m, Ry0 + 4m,
 // Kx0 + 4m, Rx0 + 4m and is accumulated by one thread in a fixed order, so with
 // T a multiple of 4 the result does not depend on T or on the CTA size.
-__device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
+__device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                              float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, r = kp.r, T = kp.T;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -872,6 +872,102 @@ __device__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int
         }
         __syncthreads();
     }
+}
+
+// LE-BF data term (Sec. 4): phi_p(f) = sum over the (4r'+1)^2 window of p,
+// clipped to the image, of exp(-|I_p - I_s|_1 / gamma) rho(s|f), the weights on
+// the 0..255 left colours and not normalised.  rho is computed once per pixel of
+// M (the region grown by the window radius) into shared memory beside the packed
+// colours; each output pixel then sums its window row by row (row partial sums
+// keep the FP32 error of the 1681-term sum near that of 82 terms), taking the
+// weight from a table indexed by the integer colour distance.
+__device__ void region_unary_bf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
+                                float lb, float lc, float *sm, float *out, int pitch) {
+    const int H = P.H, W = P.W, R = 2 * kp.r;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int Mx0 = max(0, Rx0 - R), Mx1 = min(W, Rx0 + Rw + R);
+    const int My0 = max(0, Ry0 - R), My1 = min(H, Ry0 + Rh + R);
+    const int Mw = Mx1 - Mx0, Mh = My1 - My0;
+    float *rho = sm;                                         // [Mh][Mw]
+    uint32_t *col = reinterpret_cast<uint32_t *>(rho + (size_t)Mw * Mh);  // [Mh][Mw] packed R, G, B
+    float *tab = reinterpret_cast<float *>(col + (size_t)Mw * Mh);       // [766] exp(-i / gamma)
+    for (int i = tid; i < 766; i += nt) tab[i] = expf(-(float)i * kp.bf_inv_gamma);
+    const int fmt = P.fmt;
+    const float oma = 1.0f - kp.alpha_grad;
+    float sl;
+    const float sh = two_sum(1.0f, -la, sl);
+    for (int j = tid; j < Mw * Mh; j += nt) {
+        const int my = j / Mw, mx = j - my * Mw;
+        const int y = My0 + my, x = Mx0 + mx;
+        // warp offset of row y relative to column Mx0, float-float (as region_unary_gf)
+        float e1, e2, e3, e4;
+        const float p = two_prod(sh, (float)Mx0, e1);
+        const float q = two_prod(lb, (float)y, e2);
+        const float t1 = two_sum(p, -q, e3);
+        const float t2 = two_sum(t1, -lc, e4);
+        const float lo = __fadd_rn(__fadd_rn(__fsub_rn(e1, e2), __fadd_rn(e3, e4)), __fmul_rn(sl, (float)Mx0));
+        const float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
+        const float fl = floorf(th);
+        float F = __fadd_rn(__fsub_rn(th, fl), lo);
+        int I = (int)fl;
+        if (F < 0.f) {
+            F += 1.f;
+            I -= 1;
+        } else if (F >= 1.f) {
+            F -= 1.f;
+            I += 1;
+        }
+        const size_t rowb = (size_t)y * W;
+        const float4 l = load_px(P.L, rowb + x, fmt);
+        const float dx = (float)mx;
+        const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, F));
+        const float gf = floorf(g);
+        float t = g - gf;
+        int i0 = I + (int)gf;
+        if (i0 < 0) {
+            i0 = 0;
+            t = 0.f;
+        } else if (i0 >= W - 1) {
+            i0 = W - 1;
+            t = 0.f;
+        }
+        const int i1 = min(i0 + 1, W - 1);
+        const float4 r0 = load_px(P.R, rowb + i0, fmt), r1 = load_px(P.R, rowb + i1, fmt);
+        const float rr = fmaf(t, r1.x - r0.x, r0.x);
+        const float rg = fmaf(t, r1.y - r0.y, r0.y);
+        const float rb = fmaf(t, r1.z - r0.z, r0.z);
+        const float rd = fmaf(t, r1.w - r0.w, r0.w);
+        const float cdist = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
+        const float gdist = fabsf(l.w - rd);
+        rho[j] = oma * fminf(cdist, kp.tau_col) + kp.alpha_grad * fminf(gdist, kp.tau_grad);
+        col[j] = (uint32_t)l.x | ((uint32_t)l.y << 8) | ((uint32_t)l.z << 16);
+    }
+    __syncthreads();
+    for (int j = tid; j < Rw * Rh; j += nt) {
+        const int ry = j / Rw, rx = j - ry * Rw;
+        const int py = Ry0 + ry, px = Rx0 + rx;
+        const uint32_t cp = col[(py - My0) * Mw + (px - Mx0)];
+        const int sx0 = max(0, px - R) - Mx0, sx1 = min(W - 1, px + R) - Mx0;
+        float sum = 0.f;
+        for (int sy = max(0, py - R); sy <= min(H - 1, py + R); ++sy) {
+            const uint32_t *crow = col + (size_t)(sy - My0) * Mw;
+            const float *rrow = rho + (size_t)(sy - My0) * Mw;
+            float rs = 0.f;
+            for (int sx = sx0; sx <= sx1; ++sx) rs = fmaf(tab[__vsadu4(cp, crow[sx])], rrow[sx], rs);
+            sum += rs;
+        }
+        out[(size_t)ry * pitch + rx] = sum;
+    }
+    __syncthreads();
+}
+
+// data term of one label over one region: guided filter (LE-GF) or bilateral weights (LE-BF)
+__device__ __forceinline__ void region_unary(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh,
+                                             float la, float lb, float lc, float *sm, float *out, int pitch) {
+    if (kp.bf)
+        region_unary_bf(P, kp, Rx0, Ry0, Rw, Rh, la, lb, lc, sm, out, pitch);
+    else
+        region_unary_gf(P, kp, Rx0, Ry0, Rw, Rh, la, lb, lc, sm, out, pitch);
 }
 
 // ---------------------------------------------------------------------------
@@ -1853,6 +1949,10 @@ __global__ void k_planes_out(int H, int W, DevPlanes P, float *left, float *righ
 
 size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
     const int r = kp.r, T = kp.T;
+    if (kp.bf) {
+        const size_t mw = std::min(W, rw + 4 * r), mh = std::min(H, rh + 4 * r);
+        return mw * mh * 8 + 766 * sizeof(float);
+    }
     const int Mw = std::min(W, rw + 4 * r), Kw = std::min(W, rw + 2 * r);
     (void)rh;
     const int RS = T + 2 * r, RSA = RS + 4;

@@ -23,6 +23,7 @@ LEM_ERR_CUDA = -3
 LEM_ERR_MAXFLOW_LIMIT = -4
 LEM_ERR_OOM = -5
 LEM_STORE_F32, LEM_STORE_F16, LEM_STORE_BF16 = 0, 1, 2
+LEM_DATA_GF, LEM_DATA_BF = 0, 1
 LEM_MAX_REGION_NODES = 5625
 LEM_NOALLOC_MAX_REGIONS = 4096
 
@@ -42,7 +43,7 @@ class lem_params(C.Structure):
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
-        ("k_rans", C.c_int * 3),
+        ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double),
     ]
 
 

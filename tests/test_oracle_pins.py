@@ -605,3 +605,65 @@ def test_ransac_candidates_are_exact_moves(tiny_pair):
     for _ in range(20):
         y, x = int(rng.integers(0, o.H)), int(rng.integers(0, o.W))
         assert cost[y, x] == pytest.approx(o.phi_def(lab[y, x], x, y), abs=1e-11)
+
+
+def test_le_bf_uniform_colours_give_the_plain_window_sum(tiny_pair):
+    """LE-BF (Sec. 4): with one colour everywhere in the left view every bilateral weight is
+    exp(0) = 1, so phi_p is the unnormalised sum of rho over the (4r'+1)^2 window clipped
+    to the image; with a large gamma the weights of a textured view tend to 1 as well."""
+    H, W = 20, 30
+    L = np.full((H, W, 3), 120.0)
+    rng = np.random.default_rng(9)
+    R = rng.uniform(0, 255, size=(H, W, 3))
+    o = oracle.Oracle(L, R, gf_radius=2, data_term=1)
+    for (u, v) in [(0, 0), (15, 10), (29, 19), (4, 17)]:
+        ref = sum(o.rho((0.1, 0.0, 3.2), su, sv) for sv in range(max(0, v - 4), min(H, v + 5))
+                  for su in range(max(0, u - 4), min(W, u + 5)))
+        assert o.phi_bf((0.1, 0.0, 3.2), u, v) == pytest.approx(ref, rel=1e-13)
+    o2 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2, data_term=1, bf_gamma=1e12)
+    u, v = 40, 30
+    ref = sum(o2.rho((0, 0, 5.0), su, sv) for sv in range(v - 4, v + 5) for su in range(u - 4, u + 5))
+    assert o2.phi_bf((0, 0, 5.0), u, v) == pytest.approx(ref, rel=1e-9)
+
+
+def test_le_bf_zero_at_an_integer_shift_and_region_dispatch(tiny_pair):
+    """rho = 0 at the true fronto-parallel label of a noise-free shifted pair, so the
+    LE-BF cost is 0 there; the region computation of LE-BF is the per-pixel definition."""
+    L = tiny_pair["left"].astype(np.float64)
+    d = 6
+    R = np.empty_like(L)
+    R[:, :-d] = L[:, d:]
+    R[:, -d:] = L[:, -1:]
+    o = oracle.Oracle(L, R, gf_radius=2, data_term=1)
+    assert o.phi_bf((0, 0, d), 40, 30) == 0.0
+    o3 = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2, data_term=1)
+    reg = o3.region_cost(10, 20, 6, 4, (0.05, -0.02, 7.5))
+    for y in range(4):
+        for x in range(6):
+            assert reg[y, x] == o3.phi_bf((0.05, -0.02, 7.5), 10 + x, 20 + y)
+
+
+def test_le_bf_colour_step_weight():
+    """A left view of two colours differing by (10, 20, 10), an L1 distance of 40: each
+    window pixel on the other side of the step weighs exp(-40 / gamma) and each pixel on
+    the same side 1 (an L2 distance, a 0..1 colour scale or a normalised sum would all
+    give other values)."""
+    H, W = 16, 24
+    L = np.full((H, W, 3), 100.0)
+    L[:, 12:] += (10.0, 20.0, 10.0)
+    rng = np.random.default_rng(4)
+    R = rng.uniform(0, 255, size=(H, W, 3))
+    for gamma in (10.0, 25.0):
+        o = oracle.Oracle(L, R, gf_radius=2, data_term=1, bf_gamma=gamma)
+        f = (0.05, 0.02, 2.7)
+        for (u, v) in [(10, 8), (13, 3), (11, 15)]:
+            same = other = 0.0
+            for sv in range(max(0, v - 4), min(H, v + 5)):
+                for su in range(max(0, u - 4), min(W, u + 5)):
+                    if (su >= 12) == (u >= 12):
+                        same += o.rho(f, su, sv)
+                    else:
+                        other += o.rho(f, su, sv)
+            assert other > 0
+            ref = same + np.exp(-40.0 / gamma) * other
+            assert o.phi_bf(f, u, v) == pytest.approx(ref, rel=1e-12)
