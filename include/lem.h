@@ -49,8 +49,13 @@ extern "C" {
 #define LEM_STORE_BF16 2
 
 /* largest expansion region (nodes) a single CTA min-cut holds in shared memory:
- * 75 x 75, i.e. 3x3 cells of 25 px */
+ * 75 x 75, i.e. 3x3 cells of 25 px.  Levels with larger regions (or whose data
+ * term and cut need more shared memory than a CTA has) run each region on
+ * several co-resident CTAs of a cooperative launch, with the graph in global
+ * memory; the result is the same canonical cut. */
 #define LEM_MAX_REGION_NODES 5625
+/* largest cell size (pixels) of a grid level */
+#define LEM_MAX_CELL 1024
 
 typedef struct {
     const uint8_t *data; /* H x W x 3 RGB                                  */
@@ -77,7 +82,10 @@ typedef struct {
     double disp_min;      /* disparity range of the random init / perturbation          */
     double disp_max;
     int n_levels;         /* number of grid levels (<= 3)                               */
-    int cell[3];          /* cell size in pixels per level                              */
+    int cell[3];          /* cell size in pixels per level, 1..LEM_MAX_CELL; a level whose
+                             3x3-cell regions exceed LEM_MAX_REGION_NODES uses the multi-CTA
+                             path: lem_expand_iteration then launches directly (no CUDA graph)
+                             and lem_autotune leaves that level as it is                  */
     int k_prop[3];        /* propagation proposals per region visit, per level          */
     int k_rand[3];        /* perturbation proposals per region visit, per level         */
     double quant_scale;   /* S: every energy term is quantised as rne(S x)              */
@@ -146,6 +154,14 @@ typedef struct lem_handle lem_handle;
 /* Fills `p` with the paper's parameter values (see lem_params).  disp_max is
  * set to 60; callers set it to their range. */
 void lem_default_params(lem_params *p);
+
+/* The paper's settings for the Middlebury V3 benchmark (Sec. 4): the three cell
+ * sizes become 1, 3 and 9 % of the image width (rounded to the nearest pixel,
+ * at least 1 px), lambda = 0.5 and one RANSAC proposal per visit at every level
+ * (K_RANS = 1); every other field of `p` is kept.  The paper's MC-CNN matching
+ * cost is not part of this library: the data term stays the one `p` selects.
+ * Errors: LEM_ERR_ARG (p NULL, width < 1). */
+int lem_v3_params(lem_params *p, int width);
 
 /* Creates a handle for one rectified pair.  Copies both images to the device,
  * packs (R, G, B, x-gradient of gray) per pixel (Sec. 3.2, data term: gradient
@@ -233,11 +249,16 @@ int lem_pairwise_batch(lem_handle *h, const lem_region *regions, int n_regions, 
 
 /* Minimum s-t cut of each region graph (layout of lem_pairwise_batch) by
  * push-relabel with global relabelling, one CTA per region, in shared memory.
+ * When some region exceeds LEM_MAX_REGION_NODES (any size up to the image is
+ * accepted here) every region of the call runs on the multi-CTA path instead:
+ * several co-resident CTAs per region, the graph in global memory (scratch
+ * allocated by the call), same result.
  * take_alpha[p] = 1 iff p can reach the sink in the residual graph of the
  * maximum preflow: the unique minimal sink side among all minimum cuts.
  *   take_alpha : device uint8, 1 per node, packed like costs_alpha
  *   flow       : device int64, n_regions: max-flow value (= min-cut value)
- *   status     : device int32, n_regions: LEM_OK or LEM_ERR_MAXFLOW_LIMIT
+ *   status     : device int32, n_regions: LEM_OK or LEM_ERR_MAXFLOW_LIMIT (LEM_ERR_CUDA on the
+ *                multi-CTA path if a region barrier gave up after 1 s)
  * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE, LEM_ERR_CUDA.  A region that hits the
  * round limit only sets its status; the call still returns LEM_OK. */
 int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, const int32_t *tcaps,

@@ -37,6 +37,12 @@ struct lem_handle {
     size_t cap_regions = 0;
     // work items (pair, cell i, cell j) of every (level, group), concatenated
     int4 *d_items = nullptr;
+    // levels whose regions take the cooperative multi-CTA path, and its buffers
+    bool grid_level[3] = {false, false, false};
+    int *grid_slots = nullptr;
+    long long grid_slot_cap = 0;  // ints
+    void *grid_sync = nullptr;
+    int grid_sync_cap = 0;        // regions
     int item_off[3][16] = {};
     int item_cnt[3][16] = {};
     // one outer iteration as a CUDA graph; the iteration index lives on the device
@@ -122,6 +128,29 @@ lem::KParams kparams(const lem_handle *h) {
     return k;
 }
 
+// the Level record of `level` with its launch overrides
+lem::Level level_of(const lem_handle *h, int level) {
+    lem::Level lv;
+    lv.s = h->p.cell[level];
+    lv.k_prop = h->p.k_prop[level];
+    lv.k_rand = h->p.k_rand[level];
+    lv.k_cnn = h->p.k_cnn[level];
+    lv.k_rans = h->p.k_rans[level];
+    lv.threads = h->p.level_threads[level];
+    return lv;
+}
+
+lem::KParams kparams_level(const lem_handle *h, int level) {
+    lem::KParams kp = kparams(h);
+    if (h->p.level_gr_interval[level] > 0) kp.gr_interval = h->p.level_gr_interval[level];
+    if (h->p.level_strip_rows[level] > 0) kp.T = h->p.level_strip_rows[level];
+    return kp;
+}
+
+bool level_uses_grid(const lem_handle *h, int level) {
+    return lem::expand_uses_grid(kparams_level(h, level), level_of(h, level), h->maxW, h->maxH);
+}
+
 int check_params(const lem_params *p) {
     if (!p) return fail(nullptr, LEM_ERR_ARG, "params is NULL");
     if (p->gf_radius < 0 || p->gf_radius > 32) return fail(nullptr, LEM_ERR_ARG, "gf_radius out of range [0, 32]");
@@ -129,8 +158,8 @@ int check_params(const lem_params *p) {
     if (p->n_levels < 1 || p->n_levels > 3) return fail(nullptr, LEM_ERR_ARG, "n_levels must be 1..3");
     for (int l = 0; l < p->n_levels; ++l) {
         if (p->cell[l] < 1) return fail(nullptr, LEM_ERR_ARG, "cell size must be >= 1");
-        if (9 * p->cell[l] * p->cell[l] > LEM_MAX_REGION_NODES)
-            return fail(nullptr, LEM_ERR_ARG, "cell size too large: a 3x3-cell region exceeds LEM_MAX_REGION_NODES");
+        if (p->cell[l] > LEM_MAX_CELL)
+            return fail(nullptr, LEM_ERR_ARG, "cell size above LEM_MAX_CELL");
         if (p->k_prop[l] < 0 || p->k_rand[l] < 0 || p->k_cnn[l] < 0 || p->k_cnn[l] > 64 || p->k_rans[l] < 0 ||
             p->k_rans[l] > 64 || p->k_prop[l] + p->k_rand[l] < 1)
             return fail(nullptr, LEM_ERR_ARG,
@@ -188,6 +217,8 @@ void free_handle(lem_handle *h) {
     cudaFree(h->d_offsets);
     cudaFree(h->d_pairs);
     cudaFree(h->d_items);
+    cudaFree(h->grid_slots);
+    cudaFree(h->grid_sync);
     cudaFree(h->d_iter);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
@@ -411,6 +442,30 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
         CREATE_CUDA(cudaMalloc(&h->d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
         CREATE_CUDA(cudaMemcpy(h->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     }
+    // levels above the shared-memory cut: global slots for as many regions as
+    // one launch can hold co-resident (one CTA per SM at least)
+    {
+        int dev = 0, nsm = 0;
+        CREATE_CUDA(cudaGetDevice(&dev));
+        CREATE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        long long need = 0;
+        int regions = 0;
+        for (int l = 0; l < p->n_levels; ++l) {
+            if (!h->grid_level[l] && !level_uses_grid(h, l)) continue;
+            h->grid_level[l] = true;
+            int most = 0;
+            for (int g = 0; g < 16; ++g) most = std::max(most, h->item_cnt[l][g]);
+            const int m = std::max(1, std::min(most, nsm));
+            need = std::max(need, (long long)m * lem::grid_slot_ints_host(h->maxW, h->maxH, p->cell[l]));
+            regions = std::max(regions, m);
+        }
+        if (need > 0) {
+            CREATE_CUDA(cudaMalloc(&h->grid_slots, sizeof(int) * (size_t)need));
+            CREATE_CUDA(cudaMalloc(&h->grid_sync, lem::grid_sync_bytes() * regions));
+            h->grid_slot_cap = need;
+            h->grid_sync_cap = regions;
+        }
+    }
     // per pair: images on the device, packing, guide statistics, random labels, costs
     for (int b = 0; b < n_pairs; ++b) {
         const lem_image *left = &lefts[b], *right = &rights[b];
@@ -560,8 +615,27 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
     int mw, mh, mn, rc;
     size_t smem = 0;
     if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn, &smem)) != LEM_OK) return rc;
-    if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
-    if (smem > 227 * 1024) return fail(h, LEM_ERR_SHAPE, "region shape needs more shared memory than a CTA has");
+    if (mn > LEM_MAX_REGION_NODES || smem > 227 * 1024) {
+        // regions above the shared-memory cut: the multi-CTA path, with scratch
+        // slots for as many regions as one launch holds
+        int dev = 0, nsm = 0;
+        LEM_CUDA(h, cudaGetDevice(&dev));
+        LEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int m = std::min(n_regions, nsm);
+        const long long slot = lem::grid_slot_ints_wh(mw, mh);
+        int *slots = nullptr;
+        void *sync = nullptr;
+        cudaError_t e = cudaMalloc(&slots, sizeof(int) * (size_t)slot * m);
+        if (e == cudaSuccess) e = cudaMalloc(&sync, lem::grid_sync_bytes() * m);
+        if (e == cudaSuccess)
+            e = lem::launch_mincut_grid(kparams(h), h->d_regions, h->d_offsets, n_regions, mw, mh, tcaps, ncaps,
+                                        take_alpha, flow, status, h->ctr, slots, slot * m, sync, m, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        cudaFree(slots);
+        cudaFree(sync);
+        if (e != cudaSuccess) return cuda_fail(h, e, "lem_mincut_batch (multi-CTA path)");
+        return LEM_OK;
+    }
     LEM_CUDA(h, lem::launch_mincut_batch(kparams(h), h->d_regions, h->d_offsets, n_regions, mn, smem, tcaps, ncaps,
                                          take_alpha, flow, status, h->ctr, h->st));
     return LEM_OK;
@@ -569,18 +643,18 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
 
 // one (level, group) launch over every pair; iter < 0: read from h->d_iter
 static int expand_group_impl(lem_handle *h, int iter, int level, int group, cudaStream_t st) {
-    lem::Level lv;
-    lv.s = h->p.cell[level];
-    lv.k_prop = h->p.k_prop[level];
-    lv.k_rand = h->p.k_rand[level];
-    lv.k_cnn = h->p.k_cnn[level];
-    lv.k_rans = h->p.k_rans[level];
-    lv.threads = h->p.level_threads[level];
+    const lem::Level lv = level_of(h, level);
     if (h->prop && !h->prop_set)
         return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
-    lem::KParams kp = kparams(h);
-    if (h->p.level_gr_interval[level] > 0) kp.gr_interval = h->p.level_gr_interval[level];
-    if (h->p.level_strip_rows[level] > 0) kp.T = h->p.level_strip_rows[level];
+    const lem::KParams kp = kparams_level(h, level);
+    if (h->grid_level[level]) {
+        if (iter < 0) return fail(h, LEM_ERR_ARG, "levels above the shared-memory cut are not graph-captured");
+        LEM_CUDA(h, lem::launch_expand_grid(planes_base(h), kp, lv, level, iter, h->d_pairs, h->maxW, h->maxH,
+                                            h->d_items + h->item_off[level][group], h->item_cnt[level][group],
+                                            h->lab, h->phiA, h->prop, h->ctr, h->grid_slots, h->grid_slot_cap,
+                                            h->grid_sync, h->grid_sync_cap, st));
+        return LEM_OK;
+    }
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                          h->lab, h->phiA, h->prop, h->ctr, st));
@@ -626,7 +700,9 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (n_iters < 0) return fail(h, LEM_ERR_ARG, "n_iters < 0");
     int done = 0;
-    if (n_iters > 0 && h->p.use_graph && !h->gexec) {
+    // cooperative launches of the multi-CTA levels run directly, never as a graph
+    const bool graph_ok = !(h->grid_level[0] || h->grid_level[1] || h->grid_level[2]);
+    if (n_iters > 0 && h->p.use_graph && graph_ok && !h->gexec) {
         // the first iteration runs directly (it also sets the kernels' shared
         // memory limits), the graph is captured for the following ones
         for (int l = 0; l < h->p.n_levels; ++l)
@@ -868,6 +944,18 @@ int lem_cnn_propose(lem_cnn *net, lem_handle *h) {
     return LEM_OK;
 }
 
+int lem_v3_params(lem_params *p, int width) {
+    if (!p || width < 1) return fail(nullptr, LEM_ERR_ARG, "params NULL or width < 1");
+    static const double kFrac[3] = {0.01, 0.03, 0.09};
+    for (int l = 0; l < 3; ++l) {
+        p->cell[l] = std::max(1, (int)std::lround(kFrac[l] * width));
+        p->k_rans[l] = 1;
+    }
+    p->n_levels = 3;
+    p->lambda = 0.5;
+    return LEM_OK;
+}
+
 int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (repeats < 1 || repeats > 100) return fail(h, LEM_ERR_ARG, "repeats must be 1..100");
@@ -913,6 +1001,11 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         return LEM_OK;
     };
     for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) {
+        if (h->grid_level[l]) {
+            // the multi-CTA path has no tuned parameters
+            res.ms[l] = res.ms_default[l] = -1.f;
+            continue;
+        }
         // the default configuration first
         h->p.level_threads[l] = 0;
         h->p.level_gr_interval[l] = 0;
@@ -994,13 +1087,18 @@ int lem_propose_batch(lem_handle *h, int iter, int level, const int *cells, int 
     kp.disp_min = pd.disp_min;
     kp.disp_max = pd.disp_max;
     int2 *dc = nullptr;
+    long long *dq = nullptr;
     LEM_CUDA(h, cudaMalloc(&dc, sizeof(int2) * n_cells));
-    cudaError_t e = cudaMemcpyAsync(dc, cells, sizeof(int2) * n_cells, cudaMemcpyHostToDevice, h->st);
+    cudaError_t e = cudaSuccess;
+    if (lv.k_rans > 0 && s * s > lem::kRansacSmemCell)
+        e = cudaMalloc(&dq, sizeof(long long) * (size_t)s * s * n_cells);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cells, sizeof(int2) * n_cells, cudaMemcpyHostToDevice, h->st);
     if (e == cudaSuccess)
         e = lem::launch_propose_batch(planes(h, 0), kp, lv, level, iter, dc, n_cells, h->lab + pd.off,
-                                      h->prop ? h->prop + pd.off : nullptr, alpha, h->st);
+                                      h->prop ? h->prop + pd.off : nullptr, alpha, dq, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     cudaFree(dc);
+    if (dq) cudaFree(dq);
     if (e != cudaSuccess) return cuda_fail(h, e, "lem_propose_batch");
     return LEM_OK;
 }

@@ -101,10 +101,33 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
                                 cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
+// Regions above the shared-memory cut (more than LEM_MAX_REGION_NODES nodes, or
+// a data term + cut that needs more than a CTA's shared memory) take the
+// cooperative multi-CTA path.
+bool expand_uses_grid(const KParams &kp, const Level &lv, int max_w, int max_h);
+// ints of one region slot of that path at cell size s; bytes of one region's sync record
+long long grid_slot_ints_host(int max_w, int max_h, int s);
+size_t grid_sync_bytes();
+// One (level, group) launch of the multi-CTA path; items in chunks of at most
+// min(co-resident CTAs, sync_cap, slots that fit in slot_cap_ints) regions.
+cudaError_t launch_expand_grid(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                               const PairDesc *pairs, int max_w, int max_h, const int4 *items, int n_items,
+                               float4 *lab, float *phiA, const float4 *prop, Counters *ctr, int *slots,
+                               long long slot_cap_ints, void *sync, int sync_cap, cudaStream_t st);
+// lem_mincut_batch on the multi-CTA path (any region size); slots of
+// grid_slot_ints(max_w, max_h) ints per region
+long long grid_slot_ints_wh(int w, int h);
+cudaError_t launch_mincut_grid(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
+                               int max_w, int max_h, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                               int64_t *flow, int32_t *status, Counters *ctr, int *slots, long long slot_cap_ints,
+                               void *sync, int sync_cap, cudaStream_t st);
 // candidates of one visit of each listed cell (see lem_propose_batch)
 cudaError_t launch_propose_batch(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                  const int2 *cells, int n_cells, const float4 *lab, const float4 *prop, float *alpha,
-                                 cudaStream_t st);
+                                 long long *dq_scratch, cudaStream_t st);
+// RANSAC cells of more pixels than this keep their quantised disparities in a
+// global scratch of s * s entries per cell
+constexpr int kRansacSmemCell = 25 * 25;
 cudaError_t launch_energy(const DevPlanes &P, const KParams &kp, const float4 *lab, long long *partials,
                           long long *out, cudaStream_t st);
 cudaError_t launch_labels_out(int H, int W, const float4 *lab, float *abc, float *disp, float *cost,

@@ -237,7 +237,7 @@ __device__ float4 propose(const float4 *lab, int W, unsigned long long stream, i
 // ---------------------------------------------------------------------------
 constexpr int kRansacHyp = 32;
 constexpr int kRansacLo = 2;
-constexpr int kRansacMaxCell = 25 * 25;
+constexpr int kRansacMaxCell = kRansacSmemCell;
 constexpr double kRansacQ = 1048576.0;
 
 struct RansacSmem {
@@ -257,9 +257,11 @@ __device__ __forceinline__ bool ransac_inlier(long long dq, int x, int y, double
     return fabs(r) <= 1.0;
 }
 
-// all threads of the CTA; *out written by thread 0; ends with a barrier
+// all threads of the CTA; *out written by thread 0; ends with a barrier.
+//   dq: cw * chh quantised disparities of the cell (R->dq for cells of at most
+//       kRansacMaxCell pixels, else a global scratch of the CTA)
 __device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, int cx0, int cy0, int cw, int chh,
-                           RansacSmem *R, float4 *out) {
+                           RansacSmem *R, long long *dq, float4 *out) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     const int n = cw * chh;
     for (int k = tid; k < n; k += nt) {
@@ -267,7 +269,7 @@ __device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, 
         const float4 f = lab[(size_t)v * W + u];
         const double d = __dadd_rn(__dadd_rn(__dmul_rn((double)f.x, (double)u), __dmul_rn((double)f.y, (double)v)),
                                    (double)f.z);
-        R->dq[k] = __double2ll_rn(__dmul_rn(d, kRansacQ));
+        dq[k] = __double2ll_rn(__dmul_rn(d, kRansacQ));
     }
     if (tid == 0) {
         Rng g{stream};
@@ -286,11 +288,11 @@ __device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, 
             const long long du1 = x1 - x0, dv1 = y1 - y0, du2 = x2 - x0, dv2 = y2 - y0;
             const long long det = du1 * dv2 - du2 * dv1;
             if (det != 0) {
-                const long long dd1 = R->dq[i1] - R->dq[i0], dd2 = R->dq[i2] - R->dq[i0];
+                const long long dd1 = dq[i1] - dq[i0], dd2 = dq[i2] - dq[i0];
                 const long long na = dd1 * dv2 - dd2 * dv1, nb = du1 * dd2 - du2 * dd1;
                 const double den = __dmul_rn(__ll2double_rn(det), kRansacQ);
                 const double a = __ddiv_rn(__ll2double_rn(na), den), b = __ddiv_rn(__ll2double_rn(nb), den);
-                const double c = __dsub_rn(__dsub_rn(__ddiv_rn(__ll2double_rn(R->dq[i0]), kRansacQ),
+                const double c = __dsub_rn(__dsub_rn(__ddiv_rn(__ll2double_rn(dq[i0]), kRansacQ),
                                                      __dmul_rn(a, (double)x0)),
                                            __dmul_rn(b, (double)y0));
                 R->pl[3 * tid] = a;
@@ -306,7 +308,7 @@ __device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, 
         int c = 0;
         if (R->ok[hy]) {
             const double a = R->pl[3 * hy], b = R->pl[3 * hy + 1], cc = R->pl[3 * hy + 2];
-            for (int k = lane; k < n; k += 32) c += ransac_inlier(R->dq[k], k % cw, k / cw, a, b, cc) ? 1 : 0;
+            for (int k = lane; k < n; k += 32) c += ransac_inlier(dq[k], k % cw, k / cw, a, b, cc) ? 1 : 0;
         }
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) R->cnt[hy] = R->ok[hy] ? c : -1;
@@ -339,17 +341,17 @@ __device__ void ransac_cta(const float4 *lab, int W, unsigned long long stream, 
         const double a = R->best[0], b = R->best[1], c = R->best[2];
         long long s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int k = tid; k < n; k += nt) {
-            const long long x = k % cw, y = k / cw, dq = R->dq[k];
-            if (!ransac_inlier(dq, (int)x, (int)y, a, b, c)) continue;
+            const long long x = k % cw, y = k / cw, dqk = dq[k];
+            if (!ransac_inlier(dqk, (int)x, (int)y, a, b, c)) continue;
             s[0] += x * x;
             s[1] += x * y;
             s[2] += x;
             s[3] += y * y;
             s[4] += y;
             s[5] += 1;
-            s[6] += x * dq;
-            s[7] += y * dq;
-            s[8] += dq;
+            s[6] += x * dqk;
+            s[7] += y * dqk;
+            s[8] += dqk;
         }
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -1565,7 +1567,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
         for (int t = t0; t < t1; ++t) {
             const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
             if (t >= lv.k_prop && t < lv.k_prop + kr) {
-                ransac_cta(lab, W, stream, cx0, cy0, cw, chh, reinterpret_cast<RansacSmem *>(smf), &s_alpha[t - t0]);
+                RansacSmem *rs = reinterpret_cast<RansacSmem *>(smf);
+                ransac_cta(lab, W, stream, cx0, cy0, cw, chh, rs, rs->dq, &s_alpha[t - t0]);
                 continue;
             }
             if (threadIdx.x != 0) continue;
@@ -1841,7 +1844,7 @@ __global__ void k_props_out(int n, const float4 *prop, float *abc) {
 // as k_expand_group draws them (no moves in between): one CTA per cell.
 //   cells: (ci, cj) per CTA; alpha: per cell, nprop labels (a, b, c)
 __global__ void k_propose_batch(DevPlanes P, KParams kp, Level lv, int level, int iter, const int2 *cells,
-                                const float4 *lab, const float4 *prop, float *alpha) {
+                                const float4 *lab, const float4 *prop, float *alpha, long long *dq_g) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_one;
     const int W = P.W, H = P.H, s = lv.s;
@@ -1854,7 +1857,9 @@ __global__ void k_propose_batch(DevPlanes P, KParams kp, Level lv, int level, in
     for (int t = 0; t < nprop; ++t) {
         const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
         if (t >= lv.k_prop && t < lv.k_prop + kr) {
-            ransac_cta(lab, W, stream, cx0, cy0, cw, chh, reinterpret_cast<RansacSmem *>(smf), &s_one);
+            RansacSmem *rs = reinterpret_cast<RansacSmem *>(smf);
+            ransac_cta(lab, W, stream, cx0, cy0, cw, chh, rs, dq_g ? dq_g + (size_t)blockIdx.x * s * s : rs->dq,
+                       &s_one);
         } else if (threadIdx.x == 0) {
             if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
                 s_one = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
@@ -1944,6 +1949,479 @@ __global__ void k_planes_out(int H, int W, DevPlanes P, float *left, float *righ
         g[6] = b.z;
         g[7] = b.w;
         g[8] = c.x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Regions above the shared-memory cut.  With cells proportional to the image
+// width (Sec. 4, Middlebury V3: 1, 3 and 9 % of the width) a 3x3-cell region
+// reaches 135x135 or 405x405 nodes at 1500 px.  Such a region is spread over
+// G CTAs of one cooperative launch (all co-resident): its graph, heights and
+// relabel bitplanes live in a global slot (L2-resident), the data term runs
+// on 64x128 tiles spread over the CTAs, and the CTAs meet at region barriers.
+// The cut is the same canonical minimal sink side as the CTA cut's.
+// ---------------------------------------------------------------------------
+constexpr int kGridTileW = 64, kGridTileH = 128;
+constexpr int kGridInf = 0x3fffffff;
+constexpr long long kRegionWaitNs = 1000000000ll;  // a region barrier gives up after 1 s
+constexpr int kGridThreads = 512;
+
+struct RegionSync {
+    unsigned int bar;  // arrivals at region barriers
+    int acc[3];        // reduction slots, keyed by barrier generation mod 3
+    int err;           // set when a barrier gave up
+    int pad[3];
+    float4 alpha[kMaxVisit];  // candidates of the current visit
+};
+
+// ints of one region slot for regions up to w x h nodes: residuals (8n),
+// excess (n), heights (n), active list (n), relabel bitplanes (11 h WPR words),
+// rounded to 256 bytes
+__host__ __device__ inline long long grid_slot_ints(int w, int h) {
+    const long long n = (long long)w * h, wpr = (w + 31) / 32;
+    return (12 * n + 11 * h * wpr + 63) & ~63ll;
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// the CTA's place in its region and the barrier state
+struct RegionCtx {
+    RegionSync *rs;
+    int G, c;
+    unsigned gen;  // barriers passed (the same in every thread of every CTA of the region)
+    int *s_flag, *s_val;
+};
+
+// Barrier of the G CTAs of one region (every thread calls it).  Writes before
+// it are visible after it in every CTA of the region (release by thread 0
+// after the CTA barrier, acquire before the next one).  Returns false in every
+// thread once a barrier of the region gave up (1 s without all arrivals).
+__device__ bool region_sync(RegionCtx &x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bad = *(volatile int *)&x.rs->err;
+        if (!bad) {
+            __threadfence();
+            atomicAdd(&x.rs->bar, 1u);
+            const unsigned target = (x.gen + 1) * (unsigned)x.G;
+            const long long t0 = global_ns();
+            while (ld_acquire(&x.rs->bar) < target) {
+                if (global_ns() - t0 > kRegionWaitNs) {
+                    atomicExch(&x.rs->err, 1);
+                    bad = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            __threadfence();
+            // the slot of the reduction two barriers ahead: its last readers passed this barrier
+            if (x.c == 0) atomicExch(&x.rs->acc[(x.gen + 2) % 3], 0);
+        }
+        *x.s_flag = bad;
+    }
+    ++x.gen;
+    __syncthreads();
+    return *x.s_flag == 0;
+}
+
+// Sum over the CTAs of the region of `val` (taken from thread 0 of each CTA);
+// includes a barrier.  -1 when a barrier gave up.
+__device__ int region_sum(RegionCtx &x, int val) {
+    if (threadIdx.x == 0 && val) atomicAdd(&x.rs->acc[x.gen % 3], val);
+    const bool ok = region_sync(x);
+    if (threadIdx.x == 0) *x.s_val = ok ? atomicAdd(&x.rs->acc[(x.gen - 1) % 3], 0) : -1;
+    __syncthreads();
+    return *x.s_val;
+}
+
+// Exact distances to the sink, by the bit-parallel BFS of global_relabel with
+// the bitplanes in global memory: CTA c builds and scans the row words
+// [NW c / G, NW (c+1) / G) and every BFS level ends with a region barrier.
+// Returns 1 when a node with excess reaches the sink, 0 when none does, -1
+// when a barrier gave up.
+__device__ int grid_relabel(int n, int w, int h, const int *res, const int *v, int *hh, uint32_t *bits, int i0,
+                            int i1, RegionCtx &x, int *levels) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    const int WPR = (w + 31) >> 5, NW = h * WPR;
+    const int wb0 = (int)((long long)NW * x.c / x.G), wb1 = (int)((long long)NW * (x.c + 1) / x.G);
+    uint32_t *M = bits, *Fa = bits + 8 * (size_t)NW, *Fb = Fa + NW, *VIS = Fb + NW;
+    for (int word = wb0 + warp; word < wb1; word += nwarp) {
+        const int y = word / WPR, wi = word - y * WPR;
+        const int xx = wi * 32 + lane;
+        const bool in = xx < w;
+        const int i = y * w + xx;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            bool pred = false;
+            if (in) pred = res[(size_t)k * n + i] > 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, pred);
+            if (lane == 0) M[(size_t)k * NW + word] = m;
+        }
+        bool seed = false;
+        if (in) seed = v[i] < 0;
+        const uint32_t m = __ballot_sync(0xffffffffu, seed);
+        if (lane == 0) {
+            Fa[word] = m;
+            VIS[word] = m;
+        }
+        if (in) hh[i] = seed ? 1 : kGridInf;
+    }
+    if (!region_sync(x)) return -1;
+    uint32_t *Fc = Fa, *Fn = Fb;
+    int level = 1;
+    for (;;) {
+        int any = 0;
+        for (int word = wb0 + tid; word < wb1; word += nt) {
+            const int y = word / WPR, wi = word - y * WPR;
+            const uint32_t vis = VIS[word];
+            uint32_t cand = 0;
+            if (~vis) {
+                uint32_t sh[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const int yy = y + r - 1;
+                    uint32_t cw = 0, lw = 0, rw = 0;
+                    if (yy >= 0 && yy < h) {
+                        const uint32_t *F = Fc + (size_t)yy * WPR;
+                        cw = F[wi];
+                        lw = wi > 0 ? F[wi - 1] : 0u;
+                        rw = wi + 1 < WPR ? F[wi + 1] : 0u;
+                    }
+                    sh[r][0] = (cw << 1) | (lw >> 31);
+                    sh[r][1] = cw;
+                    sh[r][2] = (cw >> 1) | (rw << 31);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) cand |= M[(size_t)k * NW + word] & sh[dir_dy(k) + 1][dir_dx(k) + 1];
+                const int tail = w - wi * 32;
+                cand &= ~vis & (tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u));
+            }
+            Fn[word] = cand;
+            if (cand) {
+                VIS[word] = vis | cand;
+                any = 1;
+                uint32_t cc = cand;
+                const int base = y * w + wi * 32;
+                while (cc) {
+                    const int b = __ffs(cc) - 1;
+                    cc &= cc - 1;
+                    hh[base + b] = level + 1;
+                }
+            }
+        }
+        any = __syncthreads_or(any);
+        const int tot = region_sum(x, any);
+        if (tot < 0) return -1;
+        if (tot == 0) break;
+        uint32_t *t = Fc;
+        Fc = Fn;
+        Fn = t;
+        ++level;
+    }
+    *levels += level;
+    int act = 0;
+    for (int i = i0 + tid; i < i1; i += nt) act |= (v[i] > 0 && hh[i] != kGridInf);
+    act = __syncthreads_or(act);
+    const int tot = region_sum(x, act);
+    return tot < 0 ? -1 : (tot > 0 ? 1 : 0);
+}
+
+// Terminal reduction of clamp_terminals for the nodes [i0, i1) of the CTA.
+__device__ void grid_clamp_terminals(int n, int w, int h, const int *res, int *v, int i0, int i1) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int e = v[i];
+        if (e > 0) {
+            int out = 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out += res[(size_t)k * n + i];
+            v[i] = min(e, out);
+        } else if (e < 0) {
+            const int iy = i / w, ix = i - iy * w;
+            int in = 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
+                if (jx < 0 || jx >= w || jy < 0 || jy >= h) continue;
+                in += res[(size_t)(k ^ 4) * n + i + dir_off(k, w)];
+            }
+            v[i] = max(e, -in);
+        }
+    }
+}
+
+// Maximum preflow of the region, rounds as in cta_maxflow: each CTA compacts
+// and pushes its own nodes [i0, i1) (pushes into other CTAs' nodes are device
+// atomics), and a round ends with a region barrier that also sums the active
+// counts.  LEM_OK: hh[i] != kGridInf exactly on the minimal sink side;
+// LEM_ERR_MAXFLOW_LIMIT, or LEM_ERR_CUDA when a barrier gave up.
+__device__ int grid_maxflow(int n, int w, int h, int *res, int *v, int *hh, int *list, uint32_t *bits, int i0,
+                            int i1, int max_rounds, int gr_interval, RegionCtx &x, CutCount &cc, int *s_cnt) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    int act = grid_relabel(n, w, h, res, v, hh, bits, i0, i1, x, &cc.levels);
+    ++cc.relabels;
+    if (act < 0) return LEM_ERR_CUDA;
+    int rounds = 0;
+    while (act) {
+        if (rounds >= max_rounds) {
+            cc.rounds += rounds;
+            return LEM_ERR_MAXFLOW_LIMIT;
+        }
+        if (tid == 0) *s_cnt = 0;
+        __syncthreads();
+        for (int base = i0; base < i1; base += nt) {
+            const int i = base + tid;
+            const bool a = i < i1 && v[i] > 0 && hh[i] != kGridInf;
+            const uint32_t m = __ballot_sync(0xffffffffu, a);
+            if (m) {
+                int pos = 0;
+                if (lane == 0) pos = atomicAdd(s_cnt, __popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                if (a) list[i0 + pos + __popc(m & ((1u << lane) - 1u))] = i;
+            }
+        }
+        __syncthreads();
+        const int cnt = *s_cnt;
+        for (int q = tid; q < cnt; q += nt) {
+            const int i = list[i0 + q];
+            const int e = v[i];
+            const int hu = hh[i];
+            int r[8], hn[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = res[(size_t)k * n + i];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? hh[i + dir_off(k, w)] : kGridInf;
+            int left = e, mh = kGridInf;
+            int d[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                d[k] = 0;
+                if (r[k] > 0 && hn[k] + 1 == hu && left > 0) {
+                    d[k] = min(left, r[k]);
+                    left -= d[k];
+                }
+                if (r[k] - d[k] > 0) mh = min(mh, hn[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (d[k] == 0) continue;
+                const int j = i + dir_off(k, w);
+                atomicSub(&res[(size_t)k * n + i], d[k]);
+                atomicAdd(&res[(size_t)(k ^ 4) * n + j], d[k]);
+                atomicAdd(&v[j], d[k]);
+            }
+            if (left != e) atomicSub(&v[i], e - left);
+            if (left > 0) hh[i] = (mh >= n + 1) ? kGridInf : mh + 1;
+        }
+        ++rounds;
+        const int tot = region_sum(x, cnt);
+        if (tot < 0) return LEM_ERR_CUDA;
+        if (tot == 0 || rounds % gr_interval == 0) {
+            act = grid_relabel(n, w, h, res, v, hh, bits, i0, i1, x, &cc.levels);
+            ++cc.relabels;
+            if (act < 0) return LEM_ERR_CUDA;
+        }
+    }
+    cc.rounds += rounds;
+    return LEM_OK;
+}
+
+// All expansions of one group at one level for regions above the shared-memory
+// cut: G CTAs per region (blockIdx.x = region * G + c), Algorithm 2 as in
+// k_expand_group.  CTA 0 of a region draws the candidates of a visit; the data
+// term runs on tiles; each CTA builds, clamps and commits its own node range.
+//   slots: one global slot of slot_ints ints per region of the launch
+//   sync : one zeroed RegionSync per region of the launch
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_expand_grid(DevPlanes P, KParams kp, Level lv, int level, int iter, int G, const PairDesc *pairs,
+                  const int4 *items, float4 *lab_all, float *phiA_all, const float4 *prop_all, int *slots,
+                  long long slot_ints, RegionSync *sync, Counters *ctr) {
+    extern __shared__ __align__(16) float smf[];
+    __shared__ float4 s_alpha[kMaxVisit];
+    __shared__ long long red[33];
+    __shared__ int s_flag, s_val, s_cnt;
+    const int ridx = blockIdx.x / G, c = blockIdx.x - ridx * G;
+    const int4 item = items[ridx];
+    const PairDesc pd = pairs[item.x];
+    P.H = pd.H;
+    P.W = pd.W;
+    P.L = px_offset(P.L, pd.off, P.fmt);
+    P.R = px_offset(P.R, pd.off, P.fmt);
+    P.gst += 3 * pd.off;
+    P.wfw += pd.off;
+    kp.seed = pd.seed;
+    kp.disp_min = pd.disp_min;
+    kp.disp_max = pd.disp_max;
+    float4 *lab = lab_all + pd.off;
+    float *phiA = phiA_all + pd.off;
+    const float4 *prop = prop_all ? prop_all + pd.off : nullptr;
+    const int H = P.H, W = P.W, s = lv.s;
+    const int ci = item.y, cj = item.z;
+    const int x0 = max(0, (ci - 1) * s), x1 = min(W, (ci + 2) * s);
+    const int y0 = max(0, (cj - 1) * s), y1 = min(H, (cj + 2) * s);
+    const int w = x1 - x0, h = y1 - y0, n = w * h;
+    const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
+    int *res = slots + (size_t)ridx * slot_ints;
+    int *v = res + 8 * (size_t)n, *hh = v + n, *list = hh + n;
+    uint32_t *bits = reinterpret_cast<uint32_t *>(list + n);
+    RegionCtx x{sync + ridx, G, c, 0u, &s_flag, &s_val};
+    const int i0 = (int)((long long)n * c / G), i1 = (int)((long long)n * (c + 1) / G);
+    double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
+    double rn = ldexp(1.0, -iter);
+    long long acc = 0, hits = 0;
+    CutCount cc{0, 0, 0};
+    const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
+    const int nprop = lv.k_prop + kr + kc + lv.k_rand;
+    const int K = kp.visit;
+    const int ntx = (w + kGridTileW - 1) / kGridTileW, nty = (h + kGridTileH - 1) / kGridTileH;
+    bool ok = true;
+    for (int t0 = 0; t0 < nprop && ok; t0 += K) {
+        const int t1 = min(nprop, t0 + K);
+        if (c == 0) {
+            for (int t = t0; t < t1; ++t) {
+                const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+                if (t >= lv.k_prop && t < lv.k_prop + kr) {
+                    // the quantised disparities of a large cell go to the slot (not in use yet)
+                    RansacSmem *rsm = reinterpret_cast<RansacSmem *>(smf);
+                    long long *dq = cw * chh <= kRansacMaxCell ? rsm->dq : reinterpret_cast<long long *>(res);
+                    ransac_cta(lab, W, stream, cx0, cy0, cw, chh, rsm, dq, &s_alpha[t - t0]);
+                    continue;
+                }
+                if (threadIdx.x != 0) continue;
+                if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
+                    s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+                    continue;
+                }
+                const bool perturb = t >= lv.k_prop + kr + kc;
+                s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
+                                          perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
+                if (perturb) {
+                    rd *= 0.5;
+                    rn *= 0.5;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < t1 - t0) x.rs->alpha[threadIdx.x] = s_alpha[threadIdx.x];
+        }
+        if (!(ok = region_sync(x))) break;
+        for (int t = t0; t < t1; ++t) {
+            const float4 al = x.rs->alpha[t - t0];
+            // data term phi_p(alpha) on the tiles of the region, into phiA
+            for (int q = c; q < ntx * nty; q += G) {
+                const int ty = q / ntx, tx = q - ty * ntx;
+                const int tx0 = x0 + tx * kGridTileW, ty0 = y0 + ty * kGridTileH;
+                const int tw = min(kGridTileW, x1 - tx0), th = min(kGridTileH, y1 - ty0);
+                region_unary(P, kp, tx0, ty0, tw, th, al.x, al.y, al.z, smf, phiA + (size_t)ty0 * W + tx0, W);
+            }
+            if (!(ok = region_sync(x))) break;
+            for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+                const int iy = j / w, ix = j - iy * w;
+                NodeCaps o;
+                build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
+                v[j] = o.cap_s - o.cap_t;
+                for (int d = 0; d < 4; ++d) res[(size_t)d * n + j] = o.k[d];
+                for (int d = 4; d < 8; ++d) res[(size_t)d * n + j] = 0;
+            }
+            if (!(ok = region_sync(x))) break;
+            grid_clamp_terminals(n, w, h, res, v, i0, i1);
+            if (!(ok = region_sync(x))) break;
+            const int st = grid_maxflow(n, w, h, res, v, hh, list, bits, i0, i1, kp.max_rounds, kp.gr_interval, x,
+                                        cc, &s_cnt);
+            if (st == LEM_OK) {
+                for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+                    if (hh[j] == kGridInf) continue;
+                    const int iy = j / w, ix = j - iy * w;
+                    const size_t p = (size_t)(y0 + iy) * W + x0 + ix;
+                    lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
+                    ++acc;
+                }
+            } else {
+                ++hits;
+                if (st != LEM_ERR_MAXFLOW_LIMIT) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!(ok = region_sync(x))) break;
+        }
+    }
+    acc = block_sum_ll(acc, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctr->accepted, (unsigned long long)acc);
+        if (c == 0) {
+            // a region whose barriers gave up counts as a cut that did not finish
+            atomicAdd(&ctr->limit_hits, (unsigned long long)(hits + (ok ? 0 : 1)));
+            atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop);
+            atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
+            atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
+            atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
+        }
+    }
+}
+
+// The min-cut of lem_mincut_batch for regions above the shared-memory cut:
+// G co-resident CTAs per region, the graph in the region's global slot.
+//   flow: zeroed by the caller (each CTA adds its share)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_mincut_grid(KParams kp, const int4 *regions, const int64_t *offsets, int G, const int32_t *tcaps,
+                  const int32_t *ncaps, uint8_t *take, int64_t *flow, int32_t *status, int *slots,
+                  long long slot_ints, RegionSync *sync, Counters *ctr) {
+    __shared__ long long red[33];
+    __shared__ int s_flag, s_val, s_cnt;
+    const int ridx = blockIdx.x / G, c = blockIdx.x - ridx * G;
+    const int4 R = regions[ridx];
+    const int w = R.z, h = R.w, n = w * h;
+    const int64_t off = offsets[ridx];
+    int *res = slots + (size_t)ridx * slot_ints;
+    int *v = res + 8 * (size_t)n, *hh = v + n, *list = hh + n;
+    uint32_t *bits = reinterpret_cast<uint32_t *>(list + n);
+    RegionCtx x{sync + ridx, G, c, 0u, &s_flag, &s_val};
+    const int i0 = (int)((long long)n * c / G), i1 = (int)((long long)n * (c + 1) / G);
+    for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+        const int iy = j / w, ix = j - iy * w;
+        v[j] = tcaps[2 * (off + j)] - tcaps[2 * (off + j) + 1];
+        for (int k = 0; k < 8; ++k) {
+            int cap = 0;
+            const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
+            if (k < 4 && jx >= 0 && jx < w && jy >= 0 && jy < h) cap = max(0, (int)ncaps[4 * (off + j) + k]);
+            res[(size_t)k * n + j] = cap;
+        }
+    }
+    int st = LEM_ERR_CUDA;
+    CutCount cc{0, 0, 0};
+    long long capt = 0;
+    if (region_sync(x)) {
+        grid_clamp_terminals(n, w, h, res, v, i0, i1);
+        if (region_sync(x)) {
+            for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) capt += max(0, -v[j]);
+            st = grid_maxflow(n, w, h, res, v, hh, list, bits, i0, i1, kp.max_rounds, kp.gr_interval, x, cc, &s_cnt);
+        }
+    }
+    long long rt = 0;
+    for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+        take[off + j] = (st == LEM_OK && hh[j] != kGridInf) ? 1 : 0;
+        rt += max(0, -v[j]);
+    }
+    const long long part = block_sum_ll(capt - rt, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&flow[ridx]), (unsigned long long)part);
+        if (c == 0) {
+            status[ridx] = st;
+            atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
+            atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
+            atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
+        }
     }
 }
 
@@ -2077,16 +2555,127 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
 }
 
+bool expand_uses_grid(const KParams &kp, const Level &lv, int max_w, int max_h) {
+    const int s = lv.s;
+    const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
+    if ((long long)rw * rh > LEM_MAX_REGION_NODES) return true;
+    size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
+    if (lv.k_rans > 0) sm = std::max(sm, sizeof(RansacSmem));
+    return sm > 227 * 1024;
+}
+
+long long grid_slot_ints_host(int max_w, int max_h, int s) {
+    return grid_slot_ints(std::min(max_w, 3 * s), std::min(max_h, 3 * s));
+}
+
+size_t grid_sync_bytes() { return sizeof(RegionSync); }
+
+long long grid_slot_ints_wh(int w, int h) { return grid_slot_ints(w, h); }
+
+cudaError_t launch_expand_grid(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                               const PairDesc *pairs, int max_w, int max_h, const int4 *items, int n_items,
+                               float4 *lab, float *phiA, const float4 *prop, Counters *ctr, int *slots,
+                               long long slot_cap_ints, void *sync, int sync_cap, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    const int s = lv.s;
+    const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
+    size_t sm = unary_bytes_host(kp, max_h, max_w, std::min(rw, kGridTileW), std::min(rh, kGridTileH));
+    if (lv.k_rans > 0) sm = std::max(sm, sizeof(RansacSmem));
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e = set_smem((const void *)k_expand_grid<kGridThreads>, sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_grid<kGridThreads>, kGridThreads,
+                                                           sm)) != cudaSuccess)
+        return e;
+    const int cap = per_sm * nsm;
+    const long long slot_ints = grid_slot_ints(rw, rh);
+    const long long by_slots = slot_cap_ints / slot_ints;
+    const int chunk = (int)std::min<long long>({(long long)n_items, (long long)cap, (long long)sync_cap, by_slots});
+    if (chunk < 1) return cudaErrorInvalidConfiguration;
+    const int nodes = rw * rh;
+    for (int b = 0; b < n_items; b += chunk) {
+        const int m = std::min(chunk, n_items - b);
+        // CTAs per region: all co-resident, and at least 2048 nodes each
+        int G = std::max(1, std::min(cap / m, (nodes + 2047) / 2048));
+        if ((e = cudaMemsetAsync(sync, 0, sizeof(RegionSync) * m, st)) != cudaSuccess) return e;
+        DevPlanes Pc = P;
+        KParams kc = kp;
+        Level lc = lv;
+        int lvl = level, it = iter, g = G;
+        const PairDesc *pp = pairs;
+        const int4 *ip = items + b;
+        float4 *lp = lab;
+        float *fp = phiA;
+        const float4 *prp = prop;
+        int *sp = slots;
+        long long si = slot_ints;
+        RegionSync *syp = reinterpret_cast<RegionSync *>(sync);
+        Counters *cp = ctr;
+        void *args[] = {&Pc, &kc, &lc, &lvl, &it, &g, &pp, &ip, &lp, &fp, &prp, &sp, &si, &syp, &cp};
+        e = cudaLaunchCooperativeKernel((const void *)k_expand_grid<kGridThreads>, dim3(m * G), dim3(kGridThreads),
+                                        args, sm, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_mincut_grid(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
+                               int max_w, int max_h, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
+                               int64_t *flow, int32_t *status, Counters *ctr, int *slots, long long slot_cap_ints,
+                               void *sync, int sync_cap, cudaStream_t st) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mincut_grid<kGridThreads>, kGridThreads, 0)) !=
+        cudaSuccess)
+        return e;
+    const int cap = per_sm * nsm;
+    const long long slot_ints = grid_slot_ints(max_w, max_h);
+    const int chunk = (int)std::min<long long>(
+        {(long long)n_regions, (long long)cap, (long long)sync_cap, slot_cap_ints / slot_ints});
+    if (chunk < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaMemsetAsync(flow, 0, sizeof(int64_t) * n_regions, st)) != cudaSuccess) return e;
+    const int nodes = max_w * max_h;
+    for (int b = 0; b < n_regions; b += chunk) {
+        const int m = std::min(chunk, n_regions - b);
+        int G = std::max(1, std::min(cap / m, (nodes + 2047) / 2048));
+        if ((e = cudaMemsetAsync(sync, 0, sizeof(RegionSync) * m, st)) != cudaSuccess) return e;
+        KParams kc = kp;
+        const int4 *rp = regions + b;
+        const int64_t *op = offsets + b;
+        int g = G;
+        const int32_t *tp = tcaps, *np = ncaps;
+        uint8_t *tk = take;
+        int64_t *fp = flow + b;
+        int32_t *sp = status + b;
+        int *sl = slots;
+        long long si = slot_ints;
+        RegionSync *syp = reinterpret_cast<RegionSync *>(sync);
+        Counters *cp = ctr;
+        void *args[] = {&kc, &rp, &op, &g, &tp, &np, &tk, &fp, &sp, &sl, &si, &syp, &cp};
+        e = cudaLaunchCooperativeKernel((const void *)k_mincut_grid<kGridThreads>, dim3(m * G), dim3(kGridThreads),
+                                        args, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 __global__ void k_increment(int *x) { *x += 1; }
 
 cudaError_t launch_propose_batch(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                  const int2 *cells, int n_cells, const float4 *lab, const float4 *prop, float *alpha,
-                                 cudaStream_t st) {
+                                 long long *dq_scratch, cudaStream_t st) {
     if (n_cells == 0) return cudaSuccess;
+    if (lv.k_rans > 0 && lv.s * lv.s > kRansacMaxCell && !dq_scratch) return cudaErrorInvalidValue;
     const size_t sm = sizeof(RansacSmem);
     cudaError_t e = set_smem((const void *)k_propose_batch, sm);
     if (e != cudaSuccess) return e;
-    k_propose_batch<<<n_cells, 128, sm, st>>>(P, kp, lv, level, iter, cells, lab, prop, alpha);
+    k_propose_batch<<<n_cells, 128, sm, st>>>(P, kp, lv, level, iter, cells, lab, prop, alpha,
+                                              lv.s * lv.s > kRansacMaxCell ? dq_scratch : nullptr);
     return cudaGetLastError();
 }
 

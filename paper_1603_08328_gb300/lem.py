@@ -132,6 +132,8 @@ def lib():
         L.lem_postprocess.restype = C.c_int
         L.lem_autotune.argtypes = [H, C.c_int, P(lem_tuning)]
         L.lem_autotune.restype = C.c_int
+        L.lem_v3_params.argtypes = [P(lem_params), C.c_int]
+        L.lem_v3_params.restype = C.c_int
         for name in ("lem_set_proposals", "lem_get_proposals", "lem_cnn_create", "lem_cnn_destroy",
                      "lem_cnn_get_params", "lem_cnn_set_params", "lem_cnn_forward", "lem_cnn_gradients",
                      "lem_cnn_train_step", "lem_cnn_features", "lem_cnn_targets", "lem_cnn_propose"):
@@ -153,9 +155,18 @@ class LemError(RuntimeError):
 
 # --- same-name wrappers of the C functions ------------------------------------
 
+def lem_v3_params(p: lem_params, width: int) -> lem_params:
+    _check(lib().lem_v3_params(C.byref(p), int(width)))
+    return p
+
+
 def lem_default_params(**overrides) -> lem_params:
+    """The paper's defaults with `overrides` applied; v3_width=W first applies the
+    Middlebury V3 settings for images W pixels wide (lem_v3_params)."""
     p = lem_params()
     lib().lem_default_params(C.byref(p))
+    if "v3_width" in overrides:
+        lem_v3_params(p, overrides.pop("v3_width"))
     for k, v in overrides.items():
         if k == "lambda":
             k = "lam"

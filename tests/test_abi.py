@@ -67,7 +67,11 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(L):
     assert lib.lem_create(None, C.byref(im_a), C.byref(p), C.byref(h)) == L.LEM_ERR_ARG
     assert lib.lem_create(C.byref(im_a), C.byref(im_b), C.byref(p), C.byref(h)) == L.LEM_ERR_SHAPE
     assert "differ" in L.lem_last_error(None)
-    bad = L.lem_default_params(gf_radius=2, cell=(30, 15, 25))
+    bad = L.lem_default_params(gf_radius=2, cell=(1025, 15, 25))     # above LEM_MAX_CELL
+    assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
+    bad = L.lem_default_params(gf_radius=2, data_term=2)
+    assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
+    bad = L.lem_default_params(gf_radius=2, data_term=1, bf_gamma=0.0)
     assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
     bad = L.lem_default_params(gf_radius=2, threads=100)
     assert lib.lem_create(C.byref(im_a), C.byref(im_a), C.byref(bad), C.byref(h)) == L.LEM_ERR_ARG
@@ -83,3 +87,17 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(L):
     assert lib.lem_expand_iteration(None, 1, None) == L.LEM_ERR_ARG
     assert lib.lem_destroy(None) == L.LEM_OK
     assert lib.lem_evals_per_iteration(None) == -1
+
+
+def test_v3_settings(L):
+    """Sec. 4, Middlebury V3: cells of 1, 3 and 9 % of the image width, lambda = 0.5,
+    K_RANS = 1; the other fields stay as they were."""
+    p = L.lem_default_params(v3_width=1500)
+    assert list(p.cell) == [15, 45, 135] and p.lam == 0.5 and list(p.k_rans) == [1, 1, 1]
+    assert p.gf_radius == 10 and list(p.k_prop) == [1, 2, 2] and list(p.k_rand) == [7, 0, 0]
+    p = L.lem_default_params(v3_width=2872, disp_max=300.0)
+    assert list(p.cell) == [29, 86, 258] and p.disp_max == 300.0
+    assert list(L.lem_default_params(v3_width=10).cell) == [1, 1, 1]      # rounded, at least 1 px
+    assert L.lib().lem_v3_params(None, 100) == L.LEM_ERR_ARG
+    with pytest.raises(L.LemError):
+        L.lem_default_params(v3_width=0)
