@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-time-to-energy", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
     ap.add_argument("--no-bf", action="store_true", help="skip the LE-BF variant timing")
+    ap.add_argument("--no-v3", action="store_true", help="skip the V3-settings timing (1500 x 1000)")
     ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8"],
                     help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs "
                          "(one JSON line of its own)")
@@ -472,6 +473,57 @@ def bf_timing(lem, pair, stream, seed, flush, steps=3):
             "note": "whole-iteration time (cuts included); flops count only the data term"}
 
 
+def v3_timing(lem, stream, seed, flush):
+    """The paper's Middlebury V3 settings (Sec. 4: cells of 1, 3 and 9 % of the width,
+    lambda = 0.5, one RANSAC proposal per visit) on the 1500 x 1000 pair (disparity
+    0-400, FP32): cells 15 / 45 / 135 px, so levels 1 and 2 (135x135 and 405x405-node
+    regions) run on the multi-CTA path.  Outer iteration 1 is timed launch by launch with
+    CUDA events (L2 flushed before each launch); per level: time, evals/s, cut rounds."""
+    import torch
+    from synth import workload_pair
+    pair = workload_pair("large_1500x1000", 0)
+    H, W = pair["left"].shape[:2]
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, disp_max=400.0, v3_width=W)
+    g.iterate(1, stats=False)
+    p = g.params
+    levels = {}
+    total = 0.0
+    e_before = g.energy()[0]
+    for l in range(p.n_levels):
+        s = p.cell[l]
+        nprop = p.k_prop[l] + p.k_rand[l] + p.k_rans[l]
+        groups = region_geometry(H, W, s)
+        d = {"cell": s, "region_nodes": min(W, 3 * s) * min(H, 3 * s), "ms": 0.0, "evals": 0, "cuts": 0,
+             "path": "multi-CTA" if min(W, 3 * s) * min(H, 3 * s) > 5625 else "CTA"}
+        st0 = g.iterate(0)
+        for grp in range(16):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.check(lem.lem_expand_group(g.h, 1, l, grp, None))
+            b.record(stream)
+            b.synchronize()
+            d["ms"] += a.elapsed_time(b)
+            d["evals"] += sum(w * h for (_, _, w, h) in groups[grp]) * nprop
+            d["cuts"] += len(groups[grp]) * nprop
+        st = g.iterate(0)
+        d["rounds_per_cut"] = st.pr_rounds / max(1, d["cuts"])
+        d["relabels_per_cut"] = st.pr_global_relabels / max(1, d["cuts"])
+        d["bfs_levels_per_relabel"] = st.pr_bfs_levels / max(1, st.pr_global_relabels)
+        d["maxflow_limit"] = st.maxflow_limit
+        d["evals_per_s"] = d["evals"] / (d["ms"] / 1e3)
+        total += d["ms"]
+        levels[str(l)] = d
+    e_after = g.energy()[0]
+    evals = g.evals_per_iteration()
+    g.close()
+    return {"workload": "large_1500x1000 (disparity 0-400, FP32 images), V3 settings: cells 1/3/9 % of the width, "
+                        "lambda 0.5, K_RANS 1", "ms_per_iteration": total, "evals_per_s": evals / (total / 1e3),
+            "evals_per_iteration": evals, "energy": {"before": e_before, "after": e_after}, "levels": levels,
+            "note": "iteration 1, one lem_expand_group call per (level, group), L2 flushed before each"}
+
+
 def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
     """Time (CUDA events around each outer iteration, learned proposals' inference
     included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
@@ -651,6 +703,7 @@ def run_lem(args):
     tte = None if args.no_time_to_energy else time_to_energy(lem, pair, params, stream, seed=21 + rank)
     prop = None if args.no_proposer else proposer_timing(lem, stream)
     lebf = None if args.no_bf else bf_timing(lem, pair, stream, seed=31 + rank, flush=flush)
+    v3 = None if args.no_v3 else v3_timing(lem, stream, seed=41 + rank, flush=flush)
 
     if rank != 0:
         return
@@ -679,6 +732,7 @@ def run_lem(args):
         "time_to_energy": tte,
         "proposer": prop,
         "le_bf": lebf,
+        "v3": v3,
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,

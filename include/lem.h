@@ -114,7 +114,8 @@ typedef struct {
      * thread and the cut is the unique minimal one.  lem_autotune picks them. */
     int level_threads[3];     /* threads per CTA: 256, 512 or 1024; default by region size
                                  (<= 400 nodes: 256, <= 2500: 512, else 1024)               */
-    int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval */
+    int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval
+                                 (CTA path) or max(gr_interval, 64) (multi-CTA path)          */
     int level_strip_rows[3];  /* rows per strip of the cost pipeline; default strip_rows         */
     int k_rans[3];        /* RANSAC proposals per region visit, per level (Algorithm 2, lines 5-8;
                              default 0, the paper's setting outside its V3 experiments, where it

@@ -142,6 +142,10 @@ lem::Level level_of(const lem_handle *h, int level) {
 
 lem::KParams kparams_level(const lem_handle *h, int level) {
     lem::KParams kp = kparams(h);
+    // the multi-CTA path pays a region barrier per BFS level, so it relabels
+    // less often by default (64 rounds: the fastest of 16..128 on the
+    // 1500 x 1000 V3 levels; the interval never changes a result)
+    if (h->grid_level[level]) kp.gr_interval = std::max(kp.gr_interval, 64);
     if (h->p.level_gr_interval[level] > 0) kp.gr_interval = h->p.level_gr_interval[level];
     if (h->p.level_strip_rows[level] > 0) kp.T = h->p.level_strip_rows[level];
     return kp;

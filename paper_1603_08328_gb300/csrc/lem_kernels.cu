@@ -1965,21 +1965,45 @@ constexpr int kGridTileW = 64, kGridTileH = 128;
 constexpr int kGridInf = 0x3fffffff;
 constexpr long long kRegionWaitNs = 1000000000ll;  // a region barrier gives up after 1 s
 constexpr int kGridThreads = 512;
+constexpr int kGridUnroll = 4;  // compaction: 4 x 4 nodes per thread per pass
 
 struct RegionSync {
-    unsigned int bar;  // arrivals at region barriers
-    int acc[3];        // reduction slots, keyed by barrier generation mod 3
-    int err;           // set when a barrier gave up
-    int pad[3];
+    // one word per barrier generation mod 3: arrivals in the high 32 bits, the
+    // sum of the values the CTAs bring in the low 32
+    unsigned long long slot[3];
+    int err;  // set by a CTA whose barrier gave up (diagnostics)
+    int pad;
     float4 alpha[kMaxVisit];  // candidates of the current visit
 };
 
 // ints of one region slot for regions up to w x h nodes: residuals (8n),
-// excess (n), heights (n), active list (n), relabel bitplanes (11 h WPR words),
-// rounded to 256 bytes
+// then excess, heights and the active list (n4 = n rounded up to 4 each, so
+// every array starts on 16 bytes), then the relabel bitplanes (11 h WPR
+// words); rounded to 256 bytes
 __host__ __device__ inline long long grid_slot_ints(int w, int h) {
-    const long long n = (long long)w * h, wpr = (w + 31) / 32;
-    return (12 * n + 11 * h * wpr + 63) & ~63ll;
+    const long long n = (long long)w * h, n4 = (n + 3) & ~3ll, wpr = (w + 31) / 32;
+    return (8 * n + 3 * n4 + 11 * h * wpr + 63) & ~63ll;
+}
+
+// the arrays of a region of n nodes in its slot
+struct GridSlot {
+    int *res, *v, *hh, *list;
+    uint32_t *bits;
+};
+__device__ __forceinline__ GridSlot grid_slot(int *base, int n) {
+    const size_t n4 = ((size_t)n + 3) & ~(size_t)3;
+    GridSlot g;
+    g.res = base;
+    g.v = base + 8 * (size_t)n;
+    g.hh = g.v + n4;
+    g.list = g.hh + n4;
+    g.bits = reinterpret_cast<uint32_t *>(g.list + n4);
+    return g;
+}
+
+// node range [i0, i1) of CTA c of G: boundaries on multiples of 4 (the last range ends at n)
+__device__ __forceinline__ int grid_range_start(int n, int c, int G) {
+    return c >= G ? n : (int)(((long long)n * c / G) & ~3ll);
 }
 
 __device__ __forceinline__ long long global_ns() {
@@ -1988,10 +2012,14 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // the CTA's place in its region and the barrier state
@@ -1999,50 +2027,55 @@ struct RegionCtx {
     RegionSync *rs;
     int G, c;
     unsigned gen;  // barriers passed (the same in every thread of every CTA of the region)
-    int *s_flag, *s_val;
+    int *s_flag;   // shared: this CTA gave up at a barrier
+    int *s_val;    // shared: result of the last barrier
 };
 
-// Barrier of the G CTAs of one region (every thread calls it).  Writes before
-// it are visible after it in every CTA of the region (release by thread 0
-// after the CTA barrier, acquire before the next one).  Returns false in every
-// thread once a barrier of the region gave up (1 s without all arrivals).
-__device__ bool region_sync(RegionCtx &x) {
+// Barrier of the G CTAs of one region that also sums `val` (thread 0's value
+// of each CTA); every thread calls it and gets the sum, or -1 once this CTA's
+// wait gave up (1 s without all arrivals; every later barrier of the CTA then
+// returns -1 at once, and the other CTAs give up at their next barrier).
+// Thread 0 arrives with a release reduction on the generation's word and
+// polls it with acquire loads: writes before the barrier in any CTA of the
+// region are visible after it in every CTA.
+__device__ int region_step(RegionCtx &x, int val) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int bad = *(volatile int *)&x.rs->err;
-        if (!bad) {
-            __threadfence();
-            atomicAdd(&x.rs->bar, 1u);
-            const unsigned target = (x.gen + 1) * (unsigned)x.G;
-            const long long t0 = global_ns();
-            while (ld_acquire(&x.rs->bar) < target) {
-                if (global_ns() - t0 > kRegionWaitNs) {
-                    atomicExch(&x.rs->err, 1);
-                    bad = 1;
-                    break;
+        int out = -1;
+        if (!*x.s_flag) {
+            unsigned long long *w = &x.rs->slot[x.gen % 3];
+            red_release_add_u64(w, (1ull << 32) + (unsigned)val);
+            const unsigned long long need = (unsigned long long)x.G << 32;
+            unsigned long long cur = ld_acquire_u64(w);
+            long long t0 = 0;
+            for (int k = 0; cur < need; ++k) {
+                if ((k & 63) == 63) {
+                    const long long t = global_ns();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if (t - t0 > kRegionWaitNs) {
+                        atomicExch(&x.rs->err, 1);
+                        *x.s_flag = 1;
+                        break;
+                    }
                 }
-                __nanosleep(100);
+                cur = ld_acquire_u64(w);
             }
-            __threadfence();
-            // the slot of the reduction two barriers ahead: its last readers passed this barrier
-            if (x.c == 0) atomicExch(&x.rs->acc[(x.gen + 2) % 3], 0);
+            if (cur >= need) {
+                out = (int)(cur & 0xffffffffull);
+                // the word of the barrier two ahead: its last readers have all arrived here
+                if (x.c == 0) x.rs->slot[(x.gen + 2) % 3] = 0ull;
+            }
         }
-        *x.s_flag = bad;
+        *x.s_val = out;
     }
     ++x.gen;
     __syncthreads();
-    return *x.s_flag == 0;
-}
-
-// Sum over the CTAs of the region of `val` (taken from thread 0 of each CTA);
-// includes a barrier.  -1 when a barrier gave up.
-__device__ int region_sum(RegionCtx &x, int val) {
-    if (threadIdx.x == 0 && val) atomicAdd(&x.rs->acc[x.gen % 3], val);
-    const bool ok = region_sync(x);
-    if (threadIdx.x == 0) *x.s_val = ok ? atomicAdd(&x.rs->acc[(x.gen - 1) % 3], 0) : -1;
-    __syncthreads();
     return *x.s_val;
 }
+
+__device__ __forceinline__ bool region_sync(RegionCtx &x) { return region_step(x, 0) >= 0; }
+__device__ __forceinline__ int region_sum(RegionCtx &x, int val) { return region_step(x, val); }
 
 // Exact distances to the sink, by the bit-parallel BFS of global_relabel with
 // the bitplanes in global memory: CTA c builds and scans the row words
@@ -2178,15 +2211,54 @@ __device__ int grid_maxflow(int n, int w, int h, int *res, int *v, int *hh, int 
         }
         if (tid == 0) *s_cnt = 0;
         __syncthreads();
-        for (int base = i0; base < i1; base += nt) {
-            const int i = base + tid;
-            const bool a = i < i1 && v[i] > 0 && hh[i] != kGridInf;
-            const uint32_t m = __ballot_sync(0xffffffffu, a);
-            if (m) {
+        // 4 consecutive nodes per thread and kGridUnroll such groups per pass,
+        // every load of a pass issued before the first append (the node range
+        // starts on a multiple of 4, the arrays on 16 bytes)
+        for (int base = i0; base < i1; base += 4 * kGridUnroll * nt) {
+            int4 vv[kGridUnroll], h4[kGridUnroll];
+#pragma unroll
+            for (int u = 0; u < kGridUnroll; ++u) {
+                const int j = base + 4 * (u * nt + tid);
+                vv[u] = make_int4(0, 0, 0, 0);
+                h4[u] = make_int4(kGridInf, kGridInf, kGridInf, kGridInf);
+                if (j + 3 < i1) {
+                    vv[u] = *reinterpret_cast<const int4 *>(v + j);
+                    h4[u] = *reinterpret_cast<const int4 *>(hh + j);
+                } else if (j < i1) {
+                    vv[u].x = v[j];
+                    h4[u].x = hh[j];
+                    if (j + 1 < i1) {
+                        vv[u].y = v[j + 1];
+                        h4[u].y = hh[j + 1];
+                    }
+                    if (j + 2 < i1) {
+                        vv[u].z = v[j + 2];
+                        h4[u].z = hh[j + 2];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGridUnroll; ++u) {
+                const int j = base + 4 * (u * nt + tid);
+                const bool a0 = vv[u].x > 0 && h4[u].x != kGridInf, a1 = vv[u].y > 0 && h4[u].y != kGridInf;
+                const bool a2 = vv[u].z > 0 && h4[u].z != kGridInf, a3 = vv[u].w > 0 && h4[u].w != kGridInf;
+                const int cnt4 = (int)a0 + (int)a1 + (int)a2 + (int)a3;
+                int incl = cnt4;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                if (tot == 0) continue;
                 int pos = 0;
-                if (lane == 0) pos = atomicAdd(s_cnt, __popc(m));
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (a) list[i0 + pos + __popc(m & ((1u << lane) - 1u))] = i;
+                if (lane == 31) pos = atomicAdd(s_cnt, tot);
+                pos = __shfl_sync(0xffffffffu, pos, 31) + incl - cnt4;
+                int *L = list + i0;
+                if (a0) L[pos++] = j;
+                if (a1) L[pos++] = j + 1;
+                if (a2) L[pos++] = j + 2;
+                if (a3) L[pos] = j + 3;
             }
         }
         __syncthreads();
@@ -2196,10 +2268,17 @@ __device__ int grid_maxflow(int n, int w, int h, int *res, int *v, int *hh, int 
             const int e = v[i];
             const int hu = hh[i];
             int r[8], hn[8];
+            // residuals and neighbour heights loaded together (neighbours by position)
+            const int iy = i / w, ix = i - iy * w;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) r[k] = res[(size_t)k * n + i];
+            for (int k = 0; k < 8; ++k) {
+                r[k] = res[(size_t)k * n + i];
+                const int jx = ix + dir_dx(k), jy = iy + dir_dy(k);
+                hn[k] = (jx >= 0 && jx < w && jy >= 0 && jy < h) ? hh[i + dir_off(k, w)] : kGridInf;
+            }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? hh[i + dir_off(k, w)] : kGridInf;
+            for (int k = 0; k < 8; ++k)
+                if (r[k] <= 0) hn[k] = kGridInf;
             int left = e, mh = kGridInf;
             int d[8];
 #pragma unroll
@@ -2272,10 +2351,12 @@ __global__ void __launch_bounds__(NT, 1)
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     int *res = slots + (size_t)ridx * slot_ints;
-    int *v = res + 8 * (size_t)n, *hh = v + n, *list = hh + n;
-    uint32_t *bits = reinterpret_cast<uint32_t *>(list + n);
+    const GridSlot gs = grid_slot(res, n);
+    int *v = gs.v, *hh = gs.hh, *list = gs.list;
+    uint32_t *bits = gs.bits;
     RegionCtx x{sync + ridx, G, c, 0u, &s_flag, &s_val};
-    const int i0 = (int)((long long)n * c / G), i1 = (int)((long long)n * (c + 1) / G);
+    if (threadIdx.x == 0) s_flag = 0;  // read only by thread 0
+    const int i0 = grid_range_start(n, c, G), i1 = grid_range_start(n, c + 1, G);
     double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
     double rn = ldexp(1.0, -iter);
     long long acc = 0, hits = 0;
@@ -2384,10 +2465,12 @@ __global__ void __launch_bounds__(NT, 1)
     const int w = R.z, h = R.w, n = w * h;
     const int64_t off = offsets[ridx];
     int *res = slots + (size_t)ridx * slot_ints;
-    int *v = res + 8 * (size_t)n, *hh = v + n, *list = hh + n;
-    uint32_t *bits = reinterpret_cast<uint32_t *>(list + n);
+    const GridSlot gs = grid_slot(res, n);
+    int *v = gs.v, *hh = gs.hh, *list = gs.list;
+    uint32_t *bits = gs.bits;
     RegionCtx x{sync + ridx, G, c, 0u, &s_flag, &s_val};
-    const int i0 = (int)((long long)n * c / G), i1 = (int)((long long)n * (c + 1) / G);
+    if (threadIdx.x == 0) s_flag = 0;  // read only by thread 0
+    const int i0 = grid_range_start(n, c, G), i1 = grid_range_start(n, c + 1, G);
     for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
         const int iy = j / w, ix = j - iy * w;
         v[j] = tcaps[2 * (off + j)] - tcaps[2 * (off + j) + 1];
