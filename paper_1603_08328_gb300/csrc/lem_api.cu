@@ -124,7 +124,7 @@ lem::KParams kparams(const lem_handle *h) {
     k.T = p.strip_rows;
     k.visit = p.candidates_per_visit;
     k.bf = p.data_term == LEM_DATA_BF ? 1 : 0;
-    k.bf_inv_gamma = (float)(1.0 / p.bf_gamma);
+    k.bf_log2e_inv_gamma = (float)(1.4426950408889634 / p.bf_gamma);
     return k;
 }
 

@@ -32,7 +32,7 @@ struct KParams {
     int T;              // strip rows of the aggregation pipeline
     int visit;          // candidates drawn per region visit (1: Algorithm 2)
     int bf;             // data term: 0 guided filter (LE-GF), 1 bilateral weights (LE-BF)
-    float bf_inv_gamma; // LE-BF: 1 / gamma of the colour weights
+    float bf_log2e_inv_gamma; // LE-BF: log2(e) / gamma of the colour weights
 };
 
 // One stereo pair inside a batch handle: its size, the pixel offset of its

@@ -879,10 +879,19 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
 // LE-BF data term (Sec. 4): phi_p(f) = sum over the (4r'+1)^2 window of p,
 // clipped to the image, of exp(-|I_p - I_s|_1 / gamma) rho(s|f), the weights on
 // the 0..255 left colours and not normalised.  rho is computed once per pixel of
-// M (the region grown by the window radius) into shared memory beside the packed
-// colours; each output pixel then sums its window row by row (row partial sums
-// keep the FP32 error of the 1681-term sum near that of 82 terms), taking the
-// weight from a table indexed by the integer colour distance.
+// M (the region grown by the window radius) into shared memory, packed with the
+// pixel's colours in one 8-byte word; each output pixel then sums its window row
+// by row (row partial sums keep the FP32 error of the 1681-term sum near that of
+// 82 terms).  A weight is 2^(-d log2(e) / gamma) for the integer L1 distance d
+// (byte-wise SAD of the packed colours), on the special-function unit: one
+// 8-byte shared load, the SAD, one FMA for the exponent, ex2.approx and the FMA
+// of the sum per window pixel.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ void region_unary_bf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                                 float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, R = 2 * kp.r;
@@ -890,10 +899,7 @@ __device__ void region_unary_bf(const DevPlanes &P, const KParams &kp, int Rx0, 
     const int Mx0 = max(0, Rx0 - R), Mx1 = min(W, Rx0 + Rw + R);
     const int My0 = max(0, Ry0 - R), My1 = min(H, Ry0 + Rh + R);
     const int Mw = Mx1 - Mx0, Mh = My1 - My0;
-    float *rho = sm;                                         // [Mh][Mw]
-    uint32_t *col = reinterpret_cast<uint32_t *>(rho + (size_t)Mw * Mh);  // [Mh][Mw] packed R, G, B
-    float *tab = reinterpret_cast<float *>(col + (size_t)Mw * Mh);       // [766] exp(-i / gamma)
-    for (int i = tid; i < 766; i += nt) tab[i] = expf(-(float)i * kp.bf_inv_gamma);
+    float2 *cr = reinterpret_cast<float2 *>(sm);  // [Mh][Mw]: (packed R, G, B bits, rho)
     const int fmt = P.fmt;
     const float oma = 1.0f - kp.alpha_grad;
     float sl;
@@ -941,21 +947,28 @@ __device__ void region_unary_bf(const DevPlanes &P, const KParams &kp, int Rx0, 
         const float rd = fmaf(t, r1.w - r0.w, r0.w);
         const float cdist = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
         const float gdist = fabsf(l.w - rd);
-        rho[j] = oma * fminf(cdist, kp.tau_col) + kp.alpha_grad * fminf(gdist, kp.tau_grad);
-        col[j] = (uint32_t)l.x | ((uint32_t)l.y << 8) | ((uint32_t)l.z << 16);
+        const uint32_t pc = (uint32_t)l.x | ((uint32_t)l.y << 8) | ((uint32_t)l.z << 16);
+        cr[j] = make_float2(__uint_as_float(pc),
+                            oma * fminf(cdist, kp.tau_col) + kp.alpha_grad * fminf(gdist, kp.tau_grad));
     }
     __syncthreads();
+    // exponent of a weight: -k d with k = log2(e) / gamma; d enters as the float
+    // 2^23 + d (its bits are 0x4B000000 | d), so one FMA gives -k d exactly rounded
+    const float nk = -kp.bf_log2e_inv_gamma, c0 = 8388608.0f * kp.bf_log2e_inv_gamma;
     for (int j = tid; j < Rw * Rh; j += nt) {
         const int ry = j / Rw, rx = j - ry * Rw;
         const int py = Ry0 + ry, px = Rx0 + rx;
-        const uint32_t cp = col[(py - My0) * Mw + (px - Mx0)];
+        const uint32_t cp = __float_as_uint(cr[(py - My0) * Mw + (px - Mx0)].x);
         const int sx0 = max(0, px - R) - Mx0, sx1 = min(W - 1, px + R) - Mx0;
         float sum = 0.f;
         for (int sy = max(0, py - R); sy <= min(H - 1, py + R); ++sy) {
-            const uint32_t *crow = col + (size_t)(sy - My0) * Mw;
-            const float *rrow = rho + (size_t)(sy - My0) * Mw;
+            const float2 *row = cr + (size_t)(sy - My0) * Mw;
             float rs = 0.f;
-            for (int sx = sx0; sx <= sx1; ++sx) rs = fmaf(tab[__vsadu4(cp, crow[sx])], rrow[sx], rs);
+            for (int sx = sx0; sx <= sx1; ++sx) {
+                const float2 e = row[sx];
+                const float d = __uint_as_float(0x4B000000u | __vsadu4(cp, __float_as_uint(e.x)));
+                rs = fmaf(ex2_approx(fmaf(d, nk, c0)), e.y, rs);
+            }
             sum += rs;
         }
         out[(size_t)ry * pitch + rx] = sum;
@@ -2512,7 +2525,7 @@ size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
     const int r = kp.r, T = kp.T;
     if (kp.bf) {
         const size_t mw = std::min(W, rw + 4 * r), mh = std::min(H, rh + 4 * r);
-        return mw * mh * 8 + 766 * sizeof(float);
+        return mw * mh * 8;
     }
     const int Mw = std::min(W, rw + 4 * r), Kw = std::min(W, rw + 2 * r);
     (void)rh;
