@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
     ap.add_argument("--no-bf", action="store_true", help="skip the LE-BF variant timing")
     ap.add_argument("--no-v3", action="store_true", help="skip the V3-settings timing (1500 x 1000)")
-    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8"],
-                    help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs "
-                         "(one JSON line of its own)")
+    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8", "v3", "lebf"],
+                    help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs; "
+                         "v3: only the V3-settings block; lebf: only the LE-BF block (one JSON line each)")
     ap.add_argument("--batch-iters", type=int, default=10, help="outer iterations per pair in --mode batch8")
     return ap.parse_args()
 
@@ -748,10 +748,30 @@ def run_lem(args):
         dist.destroy_process_group()
 
 
+def run_block_mode(args):
+    """--mode v3 / lebf: one of the variant blocks of the default run on its own."""
+    import torch
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    __graft_entry__.build()
+    from paper_1603_08328_gb300 import lem
+    from synth import workload_pair
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.mode == "v3":
+        out = v3_timing(lem, stream, seed=41, flush=flush)
+    else:
+        out = bf_timing(lem, workload_pair(WORKLOAD, args.seed), stream, seed=31, flush=flush)
+    print(json.dumps({"mode": args.mode, **out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode in ("v3", "lebf"):
+        run_block_mode(args)
     elif args.mode == "proposer":
         run_proposer_mode(args)
     elif args.mode == "batch8":

@@ -2405,11 +2405,13 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             __syncthreads();
-            if (threadIdx.x < t1 - t0) x.rs->alpha[threadIdx.x] = s_alpha[threadIdx.x];
+            // published by the thread that releases at the barrier
+            if (threadIdx.x == 0)
+                for (int t = 0; t < t1 - t0; ++t) x.rs->alpha[t] = s_alpha[t];
         }
         if (!(ok = region_sync(x))) break;
         for (int t = t0; t < t1; ++t) {
-            const float4 al = x.rs->alpha[t - t0];
+            const float4 al = __ldcg(&x.rs->alpha[t - t0]);
             // data term phi_p(alpha) on the tiles of the region, into phiA
             for (int q = c; q < ntx * nty; q += G) {
                 const int ty = q / ntx, tx = q - ty * ntx;

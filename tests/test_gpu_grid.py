@@ -10,7 +10,9 @@ of the paper's Middlebury V3 settings, Sec. 4: 1, 3 and 9 % of the image width).
   and bound as the CTA path's lockstep test), with and without RANSAC;
 * the V3 settings on the 1500 x 1000 pair (regions of 45x45, 135x135 and 405x405
   nodes): exact evaluation count, no cut at its round limit, monotone energy, and the
-  cached phi_p(f_p) of sampled pixels against the definition (FP32 storage: 1e-4).
+  cached phi_p(f_p) of sampled pixels against the definition (FP32 storage: 1e-4);
+* the multi-CTA path with the LE-BF data term and with 4-candidate visits, in lockstep
+  on the tiny scene, and a batch of two pairs equal to separate handles bit for bit.
 """
 import numpy as np
 import pytest
@@ -157,3 +159,78 @@ def test_v3_settings_1500x1000(torch_cuda):
     print(f"V3 1500x1000: energy {q0 / 65536:.0f} -> {s1.energy:.0f} -> {s2.energy:.0f}; "
           f"cached phi max rel err {worst:.2e}")
     assert worst <= PHI_TOL
+
+
+def _lockstep(g, o, iters, pair, params):
+    """Group-by-group lockstep; a group whose GPU and oracle labels differ but whose two
+    label maps have the same FP64 quantised energy (evaluated by the oracle from the
+    definition) is an exact tie between candidates and is counted apart (ties keep the
+    current label, and which of two tied candidates comes first to a pixel decides it)."""
+    q_prev = g.energy()[1]
+    flips = switched = tied = 0
+    judge = oracle.Oracle(pair["left"], pair["right"], **params)
+    for it in range(iters):
+        for grp in range(16):
+            st = g.expand_group(it, 0, grp)
+            acc, _ = o.expand_group(it, 0, grp)
+            assert st.maxflow_limit == 0
+            abc = g.labels()[0].cpu().numpy()
+            lab, _ = o.state()
+            n = int((abc != lab).any(axis=-1).sum())
+            if n:
+                judge.set_labels(abc)
+                qg = judge.energy()[1]
+                judge.set_labels(lab)
+                if judge.energy()[1] == qg:
+                    tied += n
+                    n = 0
+            flips += n
+            switched += acc
+            o.set_labels(abc)
+            q = g.energy()[1]
+            assert q <= q_prev
+            q_prev = q
+    return flips, switched, tied
+
+
+@pytest.mark.parametrize("variant", ["le_bf", "visit4", "visit1"])
+def test_grid_variants_in_lockstep_on_tiny(torch_cuda, tiny_pair, variant):
+    """The multi-CTA path with the other data term (LE-BF, lambda = 20) and with the
+    batched 4-candidate schedule: 30 px cells on the 96x72 scene give regions of up to
+    90x72 nodes."""
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(gf_radius=2, disp_max=15.0, n_levels=1, cell=(30,), k_prop=(2,), k_rand=(6,), seed=53)
+    if variant == "le_bf":
+        params.update(data_term=1, lam=20.0)
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], candidates_per_visit=4 if variant == "visit4" else 1,
+               **params)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], visit=4 if variant == "visit4" else 1, **params)
+    o.init_state()
+    flips, switched, tied = _lockstep(g, o, 3, tiny_pair, dict(params, visit=4 if variant == "visit4" else 1))
+    print(f"multi-CTA {variant} lockstep: {flips} differing pixels over {switched} switches "
+          f"(+ {tied} in exact ties)")
+    assert switched > 0
+    assert flips <= max(10, 0.002 * switched)
+
+
+def test_grid_batch_equals_separate_handles(torch_cuda, tiny_pair):
+    """A batch handle whose level runs on the multi-CTA path solves each pair as its own
+    handle does, bit for bit (regions of both pairs in one cooperative launch)."""
+    from paper_1603_08328_gb300.lem import Stereo
+    from synth import make_pair
+    # 80 x 110: as a handle of its own its 30 px level is on the multi-CTA path too
+    # (90x80-node regions), so both sides compute every data term on the same tiles
+    p1 = make_pair(5, 80, 110, 15.0, n_planes=2, n_quadrics=1)
+    params = dict(gf_radius=2, disp_max=15.0, n_levels=2, cell=(5, 30), k_prop=(1, 2), k_rand=(7, 1), seed=61)
+    batch = Stereo([tiny_pair["left"], p1["left"]], [tiny_pair["right"], p1["right"]], **params)
+    st = batch.iterate(2)
+    assert st.maxflow_limit == 0
+    s0 = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+    s1 = Stereo(p1["left"], p1["right"], **dict(params, seed=(61 + 0x9E3779B97F4A7C15) % (1 << 64)))
+    s0.iterate(2)
+    s1.iterate(2)
+    for b, single in ((0, s0), (1, s1)):
+        ab, _, cb = batch.labels(b)
+        a1, _, c1 = single.labels()
+        assert (ab.cpu().numpy() == a1.cpu().numpy()).all()
+        assert (cb.cpu().numpy() == c1.cpu().numpy()).all()
