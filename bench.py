@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
     ap.add_argument("--no-bf", action="store_true", help="skip the LE-BF variant timing")
     ap.add_argument("--no-v3", action="store_true", help="skip the V3-settings timing (1500 x 1000)")
-    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8", "v3", "lebf"],
+    ap.add_argument("--no-large", action="store_true", help="skip the 1500 x 1000 FP16 batched timing")
+    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8", "v3", "lebf", "large"],
                     help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs; "
                          "v3: only the V3-settings block; lebf: only the LE-BF block (one JSON line each)")
     ap.add_argument("--batch-iters", type=int, default=10, help="outer iterations per pair in --mode batch8")
@@ -473,6 +474,41 @@ def bf_timing(lem, pair, stream, seed, flush, steps=3):
             "note": "whole-iteration time (cuts included); flops count only the data term"}
 
 
+def large_timing(lem, stream, seed, flush, steps=3):
+    """The 1500 x 1000 pair (disparity 0-400) in the production configuration: FP16 image
+    storage, batched 4-candidate visits, autotuned launch configuration, outer iterations
+    replayed as a CUDA graph.  Iterations 2 .. steps + 1 timed with CUDA events (L2 flushed
+    before each)."""
+    import torch
+    from synth import workload_pair
+    pair = workload_pair("large_1500x1000", 0)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, disp_max=400.0,
+                   store_dtype=lem.LEM_STORE_F16, candidates_per_visit=4)
+    g.iterate(1, stats=False)
+    t = g.autotune(repeats=1)
+    g.iterate(1, stats=False)           # first iteration after tuning: graph capture
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.check(lem.lem_expand_iteration(g.h, 1, None))
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    st = g.iterate(0)
+    evals = g.evals_per_iteration()
+    g.close()
+    ms = 1e3 * sum(ts) / len(ts)
+    return {"workload": "large_1500x1000 (disparity 0-400), FP16 images, 4-candidate visits, autotuned, CUDA graph",
+            "ms_per_iteration": ms, "evals_per_iteration": evals, "evals_per_s": evals / (ms / 1e3),
+            "maxflow_limit": st.maxflow_limit,
+            "launch_config": {"threads": list(t.threads), "gr_interval": list(t.gr_interval),
+                              "strip_rows": list(t.strip_rows)},
+            "note": f"iterations 3-{steps + 2} after one plain and one tuned iteration, L2 flushed between"}
+
+
 def v3_timing(lem, stream, seed, flush):
     """The paper's Middlebury V3 settings (Sec. 4: cells of 1, 3 and 9 % of the width,
     lambda = 0.5, one RANSAC proposal per visit) on the 1500 x 1000 pair (disparity
@@ -704,6 +740,7 @@ def run_lem(args):
     prop = None if args.no_proposer else proposer_timing(lem, stream)
     lebf = None if args.no_bf else bf_timing(lem, pair, stream, seed=31 + rank, flush=flush)
     v3 = None if args.no_v3 else v3_timing(lem, stream, seed=41 + rank, flush=flush)
+    large = None if args.no_large else large_timing(lem, stream, seed=51 + rank, flush=flush)
 
     if rank != 0:
         return
@@ -733,6 +770,7 @@ def run_lem(args):
         "proposer": prop,
         "le_bf": lebf,
         "v3": v3,
+        "large": large,
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
@@ -749,7 +787,7 @@ def run_lem(args):
 
 
 def run_block_mode(args):
-    """--mode v3 / lebf: one of the variant blocks of the default run on its own."""
+    """--mode v3 / lebf / large: one of the extra blocks of the default run on its own."""
     import torch
     import __graft_entry__
     if not torch.cuda.is_available():
@@ -761,6 +799,8 @@ def run_block_mode(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if args.mode == "v3":
         out = v3_timing(lem, stream, seed=41, flush=flush)
+    elif args.mode == "large":
+        out = large_timing(lem, stream, seed=51, flush=flush)
     else:
         out = bf_timing(lem, workload_pair(WORKLOAD, args.seed), stream, seed=31, flush=flush)
     print(json.dumps({"mode": args.mode, **out}), flush=True)
@@ -770,7 +810,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.mode in ("v3", "lebf"):
+    elif args.mode in ("v3", "lebf", "large"):
         run_block_mode(args)
     elif args.mode == "proposer":
         run_proposer_mode(args)

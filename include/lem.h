@@ -112,7 +112,7 @@ typedef struct {
     /* Launch configuration of the expansion kernel per grid level (0 = the default).
      * None of them changes a result: each cost is summed in a fixed order by one
      * thread and the cut is the unique minimal one.  lem_autotune picks them. */
-    int level_threads[3];     /* threads per CTA: 256, 512 or 1024; default by region size
+    int level_threads[3];     /* threads per CTA: 128, 256, 512 or 1024; default by region size
                                  (<= 400 nodes: 256, <= 2500: 512, else 1024)               */
     int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval
                                  (CTA path) or max(gr_interval, 64) (multi-CTA path)          */
@@ -406,7 +406,7 @@ typedef struct {
 } lem_tuning;
 
 /* Times the expansion kernel of every level on this handle's own images and
- * labels for each candidate configuration (threads {256, 512, 1024} x
+ * labels for each candidate configuration (threads {128, 256, 512, 1024} x
  * gr_interval {8, 16, 32, 64} x strip_rows {8, 12, 16, 24, 32}; candidates whose shared
  * memory does not fit are skipped), `repeats` launches of groups 0 and 10 of
  * the level at the handle's current iteration each, and keeps the fastest per

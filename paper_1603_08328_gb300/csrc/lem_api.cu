@@ -186,8 +186,8 @@ int check_params(const lem_params *p) {
         return fail(nullptr, LEM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
     for (int l = 0; l < 3; ++l) {
         const int t = p->level_threads[l];
-        if (t != 0 && t != 256 && t != 512 && t != 1024)
-            return fail(nullptr, LEM_ERR_ARG, "level_threads must be 0, 256, 512 or 1024");
+        if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024)
+            return fail(nullptr, LEM_ERR_ARG, "level_threads must be 0, 128, 256, 512 or 1024");
         if (p->level_gr_interval[l] < 0) return fail(nullptr, LEM_ERR_ARG, "level_gr_interval must be >= 0");
         if (p->level_strip_rows[l] < 0 || p->level_strip_rows[l] > 64 || p->level_strip_rows[l] % 4)
             return fail(nullptr, LEM_ERR_ARG, "level_strip_rows must be 0 or a multiple of 4 up to 64");
@@ -977,7 +977,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     lem_tuning res{};
     int rc = e == cudaSuccess ? LEM_OK : cuda_fail(h, e, "lem_autotune setup");
     const lem_params keep = h->p;
-    static const int kThreads[3] = {256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[5] = {8, 12, 16, 24, 32};
+    static const int kThreads[4] = {128, 256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[5] = {8, 12, 16, 24, 32};
     // time of `repeats` launches of groups 0 and 10 at `level`, state restored after each;
     // < 0 when the configuration cannot launch
     auto trial = [&](int level, float &ms) -> int {
@@ -1020,7 +1020,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         const int s3 = 3 * h->p.cell[l];
         int bt = lem::threads_for_nodes(std::min(h->maxW, s3) * std::min(h->maxH, s3));
         int bg = keep.gr_interval, bs = keep.strip_rows;
-        for (int ti = 0; ti < 3 && rc == LEM_OK; ++ti)
+        for (int ti = 0; ti < 4 && rc == LEM_OK; ++ti)
             for (int gi = 0; gi < 4 && rc == LEM_OK; ++gi)
                 for (int si = 0; si < 5 && rc == LEM_OK; ++si) {
                     h->p.level_threads[l] = kThreads[ti];

@@ -1533,7 +1533,7 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
 //   items  : one (pair, cell i, cell j) per CTA
 //   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
 template <int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
                    const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all,
                    const float4 *prop_all, Counters *ctr) {
@@ -2645,7 +2645,9 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     if (lv.k_rans > 0) sm = std::max(sm, sizeof(RansacSmem));
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
-    if (nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
+    if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
+    if (nt == 128)
+        return expand_nt<128>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
     if (nt == 256)
         return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
     if (nt == 512)
