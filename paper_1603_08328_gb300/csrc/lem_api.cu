@@ -26,6 +26,7 @@ struct lem_handle {
     void *L = nullptr, *R = nullptr;  // packed images, lem::px_bytes(p.store_dtype) per pixel
     float4 *gst = nullptr, *wfw = nullptr, *lab = nullptr;
     float *phiA = nullptr;
+    float *phiB = nullptr;              // second data-term plane of the two-CTA visits
     float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
     bool prop_set = false;
     float *cnn_buf = nullptr;           // network input / output of one pair (lem_cnn_propose)
@@ -180,6 +181,7 @@ int check_params(const lem_params *p) {
     if (p->data_term != LEM_DATA_GF && p->data_term != LEM_DATA_BF)
         return fail(nullptr, LEM_ERR_ARG, "data_term must be LEM_DATA_GF or LEM_DATA_BF");
     if (!(p->bf_gamma > 0)) return fail(nullptr, LEM_ERR_ARG, "bf_gamma must be > 0");
+    if (p->cluster_visits != 0 && p->cluster_visits != 1) return fail(nullptr, LEM_ERR_ARG, "cluster_visits must be 0 or 1");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
@@ -211,6 +213,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->wfw);
     cudaFree(h->lab);
     cudaFree(h->phiA);
+    cudaFree(h->phiB);
     cudaFree(h->prop);
     cudaFree(h->cnn_buf);
     cudaFree(h->e_part);
@@ -346,6 +349,7 @@ void lem_default_params(lem_params *p) {
     p->k_rans[0] = p->k_rans[1] = p->k_rans[2] = 0;
     p->data_term = LEM_DATA_GF;
     p->bf_gamma = 10.0;
+    p->cluster_visits = 1;
 }
 
 const char *lem_last_error(const lem_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
@@ -415,6 +419,7 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
     CREATE_CUDA(cudaMalloc(&h->wfw, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->lab, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->phiA, sizeof(float) * n));
+    CREATE_CUDA(cudaMalloc(&h->phiB, sizeof(float) * n));
     for (int l = 0; l < p->n_levels; ++l)
         if (p->k_cnn[l] > 0 && !h->prop) CREATE_CUDA(cudaMalloc(&h->prop, sizeof(float4) * n));
     CREATE_CUDA(cudaMalloc(&h->e_part, sizeof(long long) * lem::energy_partials(h->maxH, h->maxW)));
@@ -661,7 +666,8 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     }
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
-                                         h->lab, h->phiA, h->prop, h->ctr, st));
+                                         h->lab, h->phiA, h->prop, h->ctr, h->p.cluster_visits ? h->phiB : nullptr,
+                                         st));
     return LEM_OK;
 }
 

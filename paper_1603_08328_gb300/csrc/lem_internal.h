@@ -96,9 +96,12 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 // All expansions of one (level, group) over every pair of the batch: items
 // lists (pair, cell i, cell j); iter < 0 reads the iteration from *iter_dev.
 // prop: proposal maps of all pairs (same offsets as lab), or NULL when lv.k_cnn == 0.
+// phiB: a second data-term plane (same offsets as phiA), or NULL; with it, levels
+// whose visit is two propagation candidates run two CTAs per region (a cluster)
+// that compute both candidates' data terms at once, with the sequential result.
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
-                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
+                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
                                 cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
 // Regions above the shared-memory cut (more than LEM_MAX_REGION_NODES nodes, or

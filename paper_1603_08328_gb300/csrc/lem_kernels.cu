@@ -1527,20 +1527,74 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
     }
 }
 
+// One expansion move of region [x0, x0+w) x [y0, y0+h) with candidate al whose
+// data term phi_p(al) is in `phi` (image plane, row pitch W): graph, terminal
+// reduction, CTA min-cut, commit of the minimal sink side.  All threads call
+// it; it ends with a barrier.
+__device__ void expand_move(const DevPlanes &P, const KParams &kp, float4 *lab, const float *phi, float4 al, int x0,
+                            int y0, int w, int h, const CutSmem &cs, CutCount &cc, long long &acc, long long &hits) {
+    const int n = w * h, W = P.W;
+    RowCol rb(threadIdx.x, blockDim.x, w);
+    for (int j = threadIdx.x; j < n; j += blockDim.x, rb.next()) {
+        const int iy = rb.y, ix = rb.x;
+        NodeCaps o;
+        build_node(P, kp, lab, al, phi[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
+        cs.v[j] = o.cap_s - o.cap_t;
+        for (int d = 0; d < 4; ++d) cs.res[d * n + j] = o.k[d];
+        for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
+    }
+    __syncthreads();
+    clamp_terminals(n, w, h, cs.res, cs.v);
+    __syncthreads();
+    const int st = cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
+    if (st == LEM_OK) {
+        RowCol rm(threadIdx.x, blockDim.x, w);
+        for (int j = threadIdx.x; j < n; j += blockDim.x, rm.next()) {
+            if (cs.hh[j] == kInf) continue;
+            const size_t p = (size_t)(y0 + rm.y) * W + x0 + rm.x;
+            lab[p] = make_float4(al.x, al.y, al.z, phi[p]);
+            ++acc;
+        }
+    } else if (threadIdx.x == 0) {
+        ++hits;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool same_label(float4 a, float4 b) {
+    return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y) &&
+           __float_as_uint(a.z) == __float_as_uint(b.z);
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // All expansions of one group at one level: one CTA per region, Algorithm 2.
 //   P      : base planes of all pairs (H/W unused); pair b's planes start at
 //            pixel pairs[b].off
-//   items  : one (pair, cell i, cell j) per CTA
+//   items  : one (pair, cell i, cell j) per CTA (per CTA pair with phiB_all)
 //   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
-template <int NT>
+//   SPEC   : a launch in clusters of two CTAs per region (phiB_all), for
+//            levels whose visit is two propagation candidates (K_prop = 2, no
+//            other proposals, K = 1).  The second candidate is alpha_2 = f_r2
+//            after the first move, and the first move can only change f_r2 to
+//            alpha_1; so CTA 1 computes phi(f_r2 before the move) into phiB
+//            while CTA 0 computes phi(alpha_1), and after the first move CTA 0
+//            redraws alpha_2 and takes its data term from phiB (unchanged f_r2)
+//            or phiA (f_r2 = alpha_1).  The moves and their results are those
+//            of the sequential visit, bit for bit.
+template <int NT, bool SPEC>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
                    const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all,
-                   const float4 *prop_all, Counters *ctr) {
+                   const float4 *prop_all, Counters *ctr, float *phiB_all) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha[kMaxVisit];
     __shared__ long long red[33];
-    const int4 item = items[blockIdx.x];
+    __shared__ int s_src;
+    const int rank = SPEC ? (int)(blockIdx.x & 1u) : 0;
+    const int4 item = items[SPEC ? (blockIdx.x >> 1) : blockIdx.x];
     const PairDesc pd = pairs[item.x];
     P.H = pd.H;
     P.W = pd.W;
@@ -1562,79 +1616,86 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     CutSmem cs = cut_layout(smf, n);
-    // outer perturbation sizes of this iteration, copied into Algorithm 2
-    double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
-    double rn = ldexp(1.0, -iter);
     long long acc = 0, hits = 0;
     CutCount cc{0, 0, 0};
-    // proposal indices: [0, k_prop) propagation, then k_rans RANSAC planes, then
-    // kc map candidates of the learned proposer, then k_rand perturbations
-    const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
-    const int nprop = lv.k_prop + kr + kc + lv.k_rand;
-    const int K = kp.visit;
-    for (int t0 = 0; t0 < nprop; t0 += K) {
-        const int t1 = min(nprop, t0 + K);
-        // the candidates of one visit, all drawn from the labels at its start
-        // (K = 1: Algorithm 2 as printed): propagation, RANSAC (whole CTA), map
-        // candidates, perturbation
-        for (int t = t0; t < t1; ++t) {
-            const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
-            if (t >= lv.k_prop && t < lv.k_prop + kr) {
-                RansacSmem *rs = reinterpret_cast<RansacSmem *>(smf);
-                ransac_cta(lab, W, stream, cx0, cy0, cw, chh, rs, rs->dq, &s_alpha[t - t0]);
-                continue;
-            }
-            if (threadIdx.x != 0) continue;
-            if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
-                s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
-                continue;
-            }
-            const bool perturb = t >= lv.k_prop + kr + kc;
-            s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
-                                      perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
-            if (perturb) {
-                rd *= 0.5;
-                rn *= 0.5;
-            }
+    if constexpr (SPEC) {
+        float *phiB = phiB_all + pd.off;
+        const unsigned long long st1 = proposal_stream(kp.seed, iter, level, ci, cj, 0);
+        const unsigned long long st2 = proposal_stream(kp.seed, iter, level, ci, cj, 1);
+        if (threadIdx.x == 0) {
+            s_alpha[0] = propose(lab, W, st1, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+            s_alpha[1] = propose(lab, W, st2, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
         }
         __syncthreads();
-        for (int t = t0; t < t1; ++t) {
-            const float4 al = s_alpha[t - t0];
-            region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
-            // (region_unary ends with a barrier; its shared memory is reused below)
-            RowCol rb(threadIdx.x, blockDim.x, w);
-            for (int j = threadIdx.x; j < n; j += blockDim.x, rb.next()) {
-                const int iy = rb.y, ix = rb.x;
-                NodeCaps o;
-                build_node(P, kp, lab, al, phiA[(size_t)(y0 + iy) * W + x0 + ix], x0, y0, w, h, ix, iy, o);
-                cs.v[j] = o.cap_s - o.cap_t;
-                for (int d = 0; d < 4; ++d) cs.res[d * n + j] = o.k[d];
-                for (int d = 4; d < 8; ++d) cs.res[d * n + j] = 0;
-            }
-            __syncthreads();
-            clamp_terminals(n, w, h, cs.res, cs.v);
-            __syncthreads();
-            const int st =
-                cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
-            if (st == LEM_OK) {
-                RowCol rm(threadIdx.x, blockDim.x, w);
-                for (int j = threadIdx.x; j < n; j += blockDim.x, rm.next()) {
-                    if (cs.hh[j] == kInf) continue;
-                    const size_t p = (size_t)(y0 + rm.y) * W + x0 + rm.x;
-                    lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
-                    ++acc;
+        const float4 a1 = s_alpha[0], a2s = s_alpha[1];
+        if (rank == 1) {
+            region_unary(P, kp, x0, y0, w, h, a2s.x, a2s.y, a2s.z, smf, phiB + (size_t)y0 * W + x0, W);
+            cluster_sync_all();
+            return;
+        }
+        region_unary(P, kp, x0, y0, w, h, a1.x, a1.y, a1.z, smf, phiA + (size_t)y0 * W + x0, W);
+        cluster_sync_all();
+        expand_move(P, kp, lab, phiA, a1, x0, y0, w, h, cs, cc, acc, hits);
+        if (threadIdx.x == 0) {
+            const float4 a2 = propose(lab, W, st2, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+            s_alpha[1] = a2;
+            s_src = same_label(a2, a2s) ? 1 : (same_label(a2, a1) ? 0 : 2);
+        }
+        __syncthreads();
+        const float4 a2 = s_alpha[1];
+        const int src = s_src;
+        if (src == 2)  // (not reachable: the first move sets f_r2 to alpha_1 or keeps it)
+            region_unary(P, kp, x0, y0, w, h, a2.x, a2.y, a2.z, smf, phiA + (size_t)y0 * W + x0, W);
+        expand_move(P, kp, lab, src == 1 ? phiB : phiA, a2, x0, y0, w, h, cs, cc, acc, hits);
+    } else {
+        // outer perturbation sizes of this iteration, copied into Algorithm 2
+        double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
+        double rn = ldexp(1.0, -iter);
+        // proposal indices: [0, k_prop) propagation, then k_rans RANSAC planes, then
+        // kc map candidates of the learned proposer, then k_rand perturbations
+        const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
+        const int nprop = lv.k_prop + kr + kc + lv.k_rand;
+        const int K = kp.visit;
+        for (int t0 = 0; t0 < nprop; t0 += K) {
+            const int t1 = min(nprop, t0 + K);
+            // the candidates of one visit, all drawn from the labels at its start
+            // (K = 1: Algorithm 2 as printed): propagation, RANSAC (whole CTA), map
+            // candidates, perturbation
+            for (int t = t0; t < t1; ++t) {
+                const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+                if (t >= lv.k_prop && t < lv.k_prop + kr) {
+                    RansacSmem *rs = reinterpret_cast<RansacSmem *>(smf);
+                    ransac_cta(lab, W, stream, cx0, cy0, cw, chh, rs, rs->dq, &s_alpha[t - t0]);
+                    continue;
                 }
-            } else if (threadIdx.x == 0) {
-                ++hits;
+                if (threadIdx.x != 0) continue;
+                if (t >= lv.k_prop + kr && t < lv.k_prop + kr + kc) {
+                    s_alpha[t - t0] = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+                    continue;
+                }
+                const bool perturb = t >= lv.k_prop + kr + kc;
+                s_alpha[t - t0] = propose(lab, W, stream, cx0, cy0, cw, chh, perturb, perturb ? rd : 0.0,
+                                          perturb ? rn : 0.0, kp.disp_min, kp.disp_max);
+                if (perturb) {
+                    rd *= 0.5;
+                    rn *= 0.5;
+                }
             }
             __syncthreads();
+            for (int t = t0; t < t1; ++t) {
+                const float4 al = s_alpha[t - t0];
+                region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
+                // (region_unary ends with a barrier; its shared memory is reused below)
+                expand_move(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acc, hits);
+            }
         }
     }
+    const int nprop_all = lv.k_prop + lv.k_rans + (prop ? lv.k_cnn : 0) + lv.k_rand;
     acc = block_sum_ll(acc, red);
     if (threadIdx.x == 0) {
         atomicAdd(&ctr->accepted, (unsigned long long)acc);
         atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
-        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop);
+        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop_all);
         atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
         atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
         atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
@@ -2626,17 +2687,35 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 template <int NT>
 cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, const int *iter_dev,
                       const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA,
-                      const float4 *prop, Counters *ctr, size_t sm, cudaStream_t st) {
-    cudaError_t e = set_smem((const void *)k_expand_group<NT>, sm);
-    if (e != cudaSuccess) return e;
-    k_expand_group<NT>
-        <<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA, prop, ctr);
-    return cudaGetLastError();
+                      const float4 *prop, Counters *ctr, float *phiB, size_t sm, cudaStream_t st) {
+    cudaError_t e;
+    if (!phiB) {
+        if ((e = set_smem((const void *)k_expand_group<NT, false>, sm)) != cudaSuccess) return e;
+        k_expand_group<NT, false><<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA,
+                                                           prop, ctr, nullptr);
+        return cudaGetLastError();
+    }
+    if ((e = set_smem((const void *)k_expand_group<NT, true>, sm)) != cudaSuccess) return e;
+    // two CTAs per region, co-scheduled as a cluster
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * n_items);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_expand_group<NT, true>, P, kp, lv, level, iter, iter_dev, pairs, items, lab,
+                              phiA, prop, ctr, phiB);
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
-                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr,
+                                int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
                                 cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const int s = lv.s;
@@ -2646,13 +2725,20 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
     if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
+    // the two-CTA visit only for two propagation candidates per visit
+    const bool two = phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop) &&
+                     kp.visit == 1;
+    float *pb = two ? phiB : nullptr;
     if (nt == 128)
-        return expand_nt<128>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
+        return expand_nt<128>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
+                              st);
     if (nt == 256)
-        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
+        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
+                              st);
     if (nt == 512)
-        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
-    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, sm, st);
+        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
+                              st);
+    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm, st);
 }
 
 bool expand_uses_grid(const KParams &kp, const Level &lv, int max_w, int max_h) {

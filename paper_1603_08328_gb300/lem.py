@@ -43,7 +43,7 @@ class lem_params(C.Structure):
         ("max_rounds", C.c_int), ("gr_interval", C.c_int), ("strip_rows", C.c_int), ("threads", C.c_int),
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
-        ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double),
+        ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double), ("cluster_visits", C.c_int),
     ]
 
 

@@ -340,6 +340,52 @@ def test_launch_configuration_does_not_change_results(torch_cuda):
     assert a.energy()[1] == b.energy()[1] == c.energy()[1]
 
 
+def test_two_propagation_visits_in_lockstep_with_oracle(tiny_pair, torch_cuda):
+    """A level whose visit is two propagation candidates (the cluster visit of two CTAs),
+    15 px cells on the tiny scene, group by group against the oracle."""
+    from paper_1603_08328_gb300.lem import Stereo
+    params = dict(TINY_PARAMS, seed=37, cell=(15,), k_prop=(2,), k_rand=(0,))
+    g = Stereo(tiny_pair["left"], tiny_pair["right"], **params)
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **params)
+    o.init_state()
+    q_prev = g.energy()[1]
+    flips = switched = 0
+    for it in range(3):
+        for grp in range(16):
+            st = g.expand_group(it, 0, grp)
+            acc, _ = o.expand_group(it, 0, grp)
+            assert st.maxflow_limit == 0
+            abc = g.labels()[0].cpu().numpy()
+            lab, _ = o.state()
+            flips += int((abc != lab).any(axis=-1).sum())
+            switched += acc
+            o.set_labels(abc)
+            q = g.energy()[1]
+            assert q <= q_prev
+            q_prev = q
+    print(f"two-candidate cluster visits lockstep: {flips} differing pixels over {switched} switches")
+    assert switched > 0
+    assert flips <= max(10, 0.002 * switched)
+
+
+def test_cluster_visits_equal_one_cta_visits(torch_cuda):
+    """Levels 1 and 2 (two propagation candidates per visit) run two CTAs per region by
+    default; with cluster_visits = 0 they run one.  The labels, cost cache and energy after
+    two iterations are bit-identical."""
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 5)
+    base = dict(disp_max=60.0, seed=13)
+    a = Stereo(pair["left"], pair["right"], **base)
+    b = Stereo(pair["left"], pair["right"], cluster_visits=0, **base)
+    sa, sb = a.iterate(2), b.iterate(2)
+    assert sa.maxflow_limit == 0 and sb.maxflow_limit == 0
+    assert sa.evals == sb.evals and sa.accepted == sb.accepted
+    (la, _, ca), (lb, _, cb) = a.labels(), b.labels()
+    assert (la.cpu().numpy() == lb.cpu().numpy()).all()
+    assert (ca.cpu().numpy() == cb.cpu().numpy()).all()
+    assert a.energy()[1] == b.energy()[1]
+
+
 def test_autotune_keeps_the_state_and_the_results(torch_cuda):
     """lem_autotune restores labels and counters, picks valid configurations that are no
     slower than the default, and the tuned handle then follows the untuned one bit for bit."""
