@@ -2709,6 +2709,13 @@ cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, in
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    // a device that cannot co-schedule two such CTAs runs one CTA per region (same result)
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_expand_group<NT, true>, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return expand_nt<NT>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, nullptr,
+                             sm, st);
+    }
     return cudaLaunchKernelEx(&cfg, k_expand_group<NT, true>, P, kp, lv, level, iter, iter_dev, pairs, items, lab,
                               phiA, prop, ctr, phiB);
 }
