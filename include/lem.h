@@ -129,12 +129,12 @@ typedef struct {
                              paper uses lambda = 20 with it) */
     double bf_gamma;      /* LE-BF weight scale on 0..255 colours (default 10)                     */
     int cluster_visits;   /* 1 (default): a level whose visit is two propagation candidates (K_prop = 2,
-                             no other proposal, candidates_per_visit = 1) runs two CTAs per region as a
-                             cluster: the second CTA computes the data term of the second candidate as
-                             drawn before the first move while the first CTA makes that move; the
-                             first move can only turn f_r into alpha_1, so the second move then takes
-                             its data term from one of the two planes.  Same labels as 0 (one CTA),
-                             bit for bit. */
+                             no other proposal) runs two CTAs per region as a cluster when its regions
+                             leave SMs idle (two CTAs per region fit in one wave): the second CTA
+                             computes the data term of the second candidate as drawn before the first
+                             move while the first CTA makes that move; the first move can only turn
+                             f_r into alpha_1, so the second move then takes its data term from one of
+                             the two planes.  Same labels as 0 (one CTA), bit for bit. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */

@@ -1577,13 +1577,15 @@ __device__ __forceinline__ void cluster_sync_all() {
 //   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
 //   SPEC   : a launch in clusters of two CTAs per region (phiB_all), for
 //            levels whose visit is two propagation candidates (K_prop = 2, no
-//            other proposals, K = 1).  The second candidate is alpha_2 = f_r2
-//            after the first move, and the first move can only change f_r2 to
+//            other proposals).  The second candidate is alpha_2 = f_r2 after
+//            the first move, and the first move can only change f_r2 to
 //            alpha_1; so CTA 1 computes phi(f_r2 before the move) into phiB
 //            while CTA 0 computes phi(alpha_1), and after the first move CTA 0
 //            redraws alpha_2 and takes its data term from phiB (unchanged f_r2)
-//            or phiA (f_r2 = alpha_1).  The moves and their results are those
-//            of the sequential visit, bit for bit.
+//            or phiA (f_r2 = alpha_1).  With batched visits (K >= 2) both
+//            candidates come from the visit-start labels and alpha_2 is the
+//            first draw.  The moves and their results are those of the
+//            one-CTA visit, bit for bit.
 template <int NT, bool SPEC>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
@@ -1640,6 +1642,11 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
             const float4 a2 = propose(lab, W, st2, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
             s_alpha[1] = a2;
             s_src = same_label(a2, a2s) ? 1 : (same_label(a2, a1) ? 0 : 2);
+            if (kp.visit > 1) {
+                // batched visits draw both candidates from the labels at the visit start
+                s_alpha[1] = a2s;
+                s_src = 1;
+            }
         }
         __syncthreads();
         const float4 a2 = s_alpha[1];
@@ -2709,9 +2716,16 @@ cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, in
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    // a device that cannot co-schedule two such CTAs runs one CTA per region (same result)
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_expand_group<NT, true>, &cfg) != cudaSuccess || clusters < 1) {
+    // The second CTA only pays off on SMs the launch would leave idle: with more
+    // regions than one wave of single CTAs holds, or on a device that cannot
+    // co-schedule the pair, one CTA per region (same result).
+    int clusters = 0, per_sm = 0, dev = 0, nsm = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&clusters, k_expand_group<NT, true>, &cfg) == cudaSuccess &&
+                    cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_group<NT, true>, NT, sm) ==
+                        cudaSuccess;
+    if (!ok || clusters < n_items || 2 * n_items > per_sm * nsm) {
         cudaGetLastError();
         return expand_nt<NT>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, nullptr,
                              sm, st);
@@ -2733,8 +2747,7 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
     if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
     // the two-CTA visit only for two propagation candidates per visit
-    const bool two = phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop) &&
-                     kp.visit == 1;
+    const bool two = phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop);
     float *pb = two ? phiB : nullptr;
     if (nt == 128)
         return expand_nt<128>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,

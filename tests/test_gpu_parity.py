@@ -371,19 +371,20 @@ def test_two_propagation_visits_in_lockstep_with_oracle(tiny_pair, torch_cuda):
 def test_cluster_visits_equal_one_cta_visits(torch_cuda):
     """Levels 1 and 2 (two propagation candidates per visit) run two CTAs per region by
     default; with cluster_visits = 0 they run one.  The labels, cost cache and energy after
-    two iterations are bit-identical."""
+    two iterations are bit-identical, with one-candidate and with 4-candidate visits."""
     from paper_1603_08328_gb300.lem import Stereo
     pair = workload_pair("middlebury_450x375", 5)
     base = dict(disp_max=60.0, seed=13)
-    a = Stereo(pair["left"], pair["right"], **base)
-    b = Stereo(pair["left"], pair["right"], cluster_visits=0, **base)
-    sa, sb = a.iterate(2), b.iterate(2)
-    assert sa.maxflow_limit == 0 and sb.maxflow_limit == 0
-    assert sa.evals == sb.evals and sa.accepted == sb.accepted
-    (la, _, ca), (lb, _, cb) = a.labels(), b.labels()
-    assert (la.cpu().numpy() == lb.cpu().numpy()).all()
-    assert (ca.cpu().numpy() == cb.cpu().numpy()).all()
-    assert a.energy()[1] == b.energy()[1]
+    for visit in (1, 4):
+        a = Stereo(pair["left"], pair["right"], candidates_per_visit=visit, **base)
+        b = Stereo(pair["left"], pair["right"], candidates_per_visit=visit, cluster_visits=0, **base)
+        sa, sb = a.iterate(2), b.iterate(2)
+        assert sa.maxflow_limit == 0 and sb.maxflow_limit == 0
+        assert sa.evals == sb.evals and sa.accepted == sb.accepted
+        (la, _, ca), (lb, _, cb) = a.labels(), b.labels()
+        assert (la.cpu().numpy() == lb.cpu().numpy()).all()
+        assert (ca.cpu().numpy() == cb.cpu().numpy()).all()
+        assert a.energy()[1] == b.energy()[1]
 
 
 def test_autotune_keeps_the_state_and_the_results(torch_cuda):
