@@ -1,6 +1,6 @@
 """GPU parity: every step of the hot path, called through the C ABI, against the FP64 oracle.
 
-Tolerances (derived in the design doc from the FP32 arithmetic of the kernels):
+Tolerances (derived from the FP32 arithmetic of the kernels):
   data term phi          |gpu - oracle| <= 1e-4 * max(1, |oracle|)
   quantised capacities   each quantised term within 1 unit; sums of up to 9 terms within 12
   min-cut                bit-exact flow and cut on the same int32 graph
