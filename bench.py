@@ -224,9 +224,18 @@ def cpu_oracle_baseline(pair, p, seed):
     t = time.perf_counter()
     _, evals = o.iterate(0)
     dt = time.perf_counter() - t
+    # the same oracle on one host core, on a smaller sample: the first two groups of the
+    # finest level of iteration 1
+    o1 = oracle.Oracle(pair["left"], pair["right"], seed=seed, n_threads=1, **PARAMS)
+    o1.put_state(*o.state())
+    t1 = time.perf_counter()
+    ev1 = sum(o1.expand_group(1, 0, grp)[1] for grp in (0, 1))
+    dt1 = time.perf_counter() - t1
     return {"value": evals / dt, "unit": METRIC, "cores": oracle.openmp_threads(), "kind": "oracle",
             "sample": f"outer iteration 0 of {WORKLOAD} (all 48 level-group launches, {evals} evals), "
-                      f"{dt:.2f} s"}
+                      f"{dt:.2f} s",
+            "one_core": {"value": ev1 / dt1, "unit": METRIC, "cores": 1,
+                         "sample": f"groups 0 and 1 of level 0, iteration 1 ({ev1} evals), {dt1:.2f} s"}}
 
 
 def run_reference(args):
