@@ -569,6 +569,13 @@ __device__ __forceinline__ float ring_sum(const float *base, int rs, int RS, int
 
 // Thread layout of one pipeline stage over an R x C item grid: threads form
 // rows of min(C, nt) columns; the (single) division happens once per stage.
+// raw cost (Eq. photofunc) from the colour and gradient differences, each
+// operation rounded once in a fixed order, so every kernel that inlines it gets
+// the same bits whatever the compiler fuses around it
+__device__ __forceinline__ float rho_mix(float col, float gd, const KParams &kp, float oma) {
+    return __fmaf_rn(oma, fminf(col, kp.tau_col), __fmul_rn(kp.alpha_grad, fminf(gd, kp.tau_grad)));
+}
+
 struct Grid2 {
     int tc, tr, cpr, rpp;
     __device__ Grid2(int C) {
@@ -697,11 +704,11 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                             const float rd = fmaf(t, r1.w - r0.w, r0.w);
                             const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
                             const float gd = fabsf(l.w - rd);
-                            const float rho = oma * fminf(col, kp.tau_col) + kp.alpha_grad * fminf(gd, kp.tau_grad);
+                            const float rho = rho_mix(col, gd, kp, oma);
                             o[xc] = rho;
-                            o[Mw + xc] = (l.x * inv255 - cr) * rho;
-                            o[2 * Mw + xc] = (l.y * inv255 - cg) * rho;
-                            o[3 * Mw + xc] = (l.z * inv255 - cb) * rho;
+                            o[Mw + xc] = __fmul_rn(__fmaf_rn(l.x, inv255, -cr), rho);
+                            o[2 * Mw + xc] = __fmul_rn(__fmaf_rn(l.y, inv255, -cg), rho);
+                            o[3 * Mw + xc] = __fmul_rn(__fmaf_rn(l.z, inv255, -cb), rho);
                         }
                     }
                 }
@@ -865,9 +872,11 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                     const int px = Rx0 + col;
                     const float n = (float)((min(W - 1, px + r) - max(0, px - r) + 1) * ny);
                     const float4 l = load_px(P.L, rowb + px, fmt);
-                    const float phi = (B[col] * (l.x * inv255 - cr) + B[Rw + col] * (l.y * inv255 - cg) +
-                                       B[2 * Rw + col] * (l.z * inv255 - cb) + B[3 * Rw + col]) /
-                                      n;
+                    const float gu = __fmaf_rn(l.x, inv255, -cr), gv = __fmaf_rn(l.y, inv255, -cg);
+                    const float gw = __fmaf_rn(l.z, inv255, -cb);
+                    const float phi =
+                        __fmaf_rn(B[col], gu, __fmaf_rn(B[Rw + col], gv, __fmaf_rn(B[2 * Rw + col], gw, B[3 * Rw + col]))) /
+                        n;
                     out[(size_t)row * pitch + (p0 - Ry0) * (size_t)pitch + col] = phi;
                 }
             }
@@ -948,8 +957,7 @@ __device__ void region_unary_bf(const DevPlanes &P, const KParams &kp, int Rx0, 
         const float cdist = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
         const float gdist = fabsf(l.w - rd);
         const uint32_t pc = (uint32_t)l.x | ((uint32_t)l.y << 8) | ((uint32_t)l.z << 16);
-        cr[j] = make_float2(__uint_as_float(pc),
-                            oma * fminf(cdist, kp.tau_col) + kp.alpha_grad * fminf(gdist, kp.tau_grad));
+        cr[j] = make_float2(__uint_as_float(pc), rho_mix(cdist, gdist, kp, oma));
     }
     __syncthreads();
     // exponent of a weight: -k d with k = log2(e) / gamma; d enters as the float
