@@ -383,6 +383,8 @@ typedef struct {
     int median_radius;    /* window (2 r + 1)^2, clipped to the image; 0..64                  */
     float median_gamma;   /* weight exp(-|I_p - I_q|_1 / gamma) on the left colours          */
 } lem_post_params;
+/* Fills `pp` with the defaults above (threshold 1, radius 20, gamma 10); a NULL
+ * pointer is ignored. */
 void lem_default_post_params(lem_post_params *pp);
 
 /* Final disparity map of pair 0 of hL (left view) with hR from
@@ -456,7 +458,10 @@ typedef struct lem_cnn lem_cnn;
 /* He-initialised network (normal weights from a SplitMix64 stream of `seed`,
  * zero biases).  Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out);
+/* Frees the network and its device buffers (NULL: nothing).  Returns LEM_OK. */
 int lem_cnn_destroy(lem_cnn *net);
+/* Text of the last error on `net` (NULL: of the last failed lem_cnn_create);
+ * owned by the library, valid until the next call on the same network. */
 const char *lem_cnn_last_error(const lem_cnn *net);
 /* Synchronises the network's stream and reports LEM_ERR_CUDA if a convolution
  * tile gave up waiting for its tensor-core MMAs since the last check (the
@@ -466,7 +471,9 @@ int lem_cnn_check(lem_cnn *net);
 /* Number of parameters: per layer, weights (3, 3, Cin, Cout) row-major, then the
  * Cout biases; layers in order (Cin, Cout) = (7,32), (32,32) x4, (32,3). */
 int64_t lem_cnn_num_params(void);
-/* All parameters to / from a HOST array of lem_cnn_num_params() floats. */
+/* All parameters to / from a HOST array of lem_cnn_num_params() floats, in that
+ * order; set_params also refreshes the BF16 copies the kernels read.  Errors:
+ * LEM_ERR_ARG (NULL), LEM_ERR_CUDA. */
 int lem_cnn_get_params(lem_cnn *net, float *host);
 int lem_cnn_set_params(lem_cnn *net, const float *host);
 /* Forward pass: x DEVICE (H4*W4*7 floats), y DEVICE (H4*W4*3 floats).
