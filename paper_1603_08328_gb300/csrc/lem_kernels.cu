@@ -586,6 +586,28 @@ struct Grid2 {
     }
 };
 
+// Warp offset of row y relative to column x0: Q(y) = (1 - a) x0 - b y - c, with
+// 1 - a = sh + sl in float-float, kept as integer I + fraction F in [0, 1).
+__device__ __forceinline__ void row_offset(float sh, float sl, float lb, float lc, int x0, int y, int &I, float &F) {
+    float e1, e2, e3, e4;
+    const float p = two_prod(sh, (float)x0, e1);
+    const float q = two_prod(lb, (float)y, e2);
+    const float t1 = two_sum(p, -q, e3);
+    const float t2 = two_sum(t1, -lc, e4);
+    const float lo = __fadd_rn(__fadd_rn(__fsub_rn(e1, e2), __fadd_rn(e3, e4)), __fmul_rn(sl, (float)x0));
+    const float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
+    const float fl = floorf(th);
+    F = __fadd_rn(__fsub_rn(th, fl), lo);
+    I = (int)fl;
+    if (F < 0.f) {
+        F += 1.f;
+        I -= 1;
+    } else if (F >= 1.f) {
+        F -= 1.f;
+        I += 1;
+    }
+}
+
 // phi_p(f) for p in [Rx0, Rx0+Rw) x [Ry0, Ry0+Rh); out[(py-Ry0)*pitch + px-Rx0].
 // Guided-filter aggregation (Eq. gf): mean over the windows W'_k containing p
 // of a_k . I_p + b_k, a_k = (Sigma_k+eU)^-1 (mean(I rho) - mu_k mean(rho)),
@@ -615,8 +637,6 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
     float *Vb = Xr + (size_t)RS * 4 * Mw;    // [T][4][Mw]   vertical sums (also [T][4][Kw])
     float *Bb = Vb + (size_t)T * 4 * Mw;     // [T][4][Kw]   box sums      (also [T][4][Rw])
     float *ABr = Bb + (size_t)T * 4 * Kw;    // [RSA][4][Kw] a_k, b_k of K rows (ring)
-    int *rowI = (int *)(ABr + (size_t)RSA * 4 * Kw);  // [RS] integer part of the row warp offset
-    float *rowF = (float *)(rowI + RS);              // [RS] fractional part
 
     const int fmt = P.fmt;
     const float4 cen4 = load_px(P.L, (size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2), fmt);
@@ -646,39 +666,15 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
             const int mNeed = min(My1, k1 + r);
             if (mNext < mNeed) {
                 const int nrow = mNeed - mNext;
-                for (int i = tid; i < nrow; i += nt) {
-                    const int y = mNext + i;
-                    float e1, e2, e3, e4;
-                    const float p = two_prod(sh, (float)Rx0, e1);
-                    const float q = two_prod(lb, (float)y, e2);
-                    const float t1 = two_sum(p, -q, e3);
-                    const float t2 = two_sum(t1, -lc, e4);
-                    const float lo = __fadd_rn(__fadd_rn(__fsub_rn(e1, e2), __fadd_rn(e3, e4)),
-                                               __fmul_rn(sl, (float)Rx0));
-                    const float th = fminf(fmaxf(t2, -1.0e9f), 1.0e9f);
-                    const float fl = floorf(th);
-                    float F = __fadd_rn(__fsub_rn(th, fl), lo);
-                    int I = (int)fl;
-                    if (F < 0.f) {
-                        F += 1.f;
-                        I -= 1;
-                    } else if (F >= 1.f) {
-                        F -= 1.f;
-                        I += 1;
-                    }
-                    int slot = mSlot + i;
-                    if (slot >= RS) slot -= RS;
-                    rowI[slot] = I;
-                    rowF[slot] = F;
-                }
-                __syncthreads();
                 if (gM.tr < gM.rpp) {
                     for (int i = gM.tr; i < nrow; i += gM.rpp) {
                         const int y = mNext + i;
                         int slot = mSlot + i;
                         if (slot >= RS) slot -= RS;
-                        const int Ib = rowI[slot];
-                        const float Fb = rowF[slot];
+                        // the row's warp offset, by every thread of the row (no barrier)
+                        int Ib;
+                        float Fb;
+                        row_offset(sh, sl, lb, lc, Rx0, y, Ib, Fb);
                         const size_t rowb = (size_t)y * W;
                         float *o = Xr + (size_t)slot * 4 * Mw;
                         for (int xc = gM.tc; xc < Mw; xc += gM.cpr) {
@@ -2608,8 +2604,7 @@ size_t unary_bytes_host(const KParams &kp, int H, int W, int rw, int rh) {
     const int Mw = std::min(W, rw + 4 * r), Kw = std::min(W, rw + 2 * r);
     (void)rh;
     const int RS = T + 2 * r, RSA = RS + 4;
-    return sizeof(float) * ((size_t)RS * 4 * Mw + (size_t)T * 4 * Mw + (size_t)T * 4 * Kw + (size_t)RSA * 4 * Kw +
-                            2 * (size_t)RS);
+    return sizeof(float) * ((size_t)RS * 4 * Mw + (size_t)T * 4 * Mw + (size_t)T * 4 * Kw + (size_t)RSA * 4 * Kw);
 }
 
 // threads per CTA for a region of n nodes: about 4-8 nodes per thread
