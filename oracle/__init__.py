@@ -89,7 +89,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # LEM_ORACLE_LIB: a separately compiled copy (the mutation tests load copies
+        # with planted mistakes to show that the pins catch them)
+        _lib = C.CDLL(os.environ.get("LEM_ORACLE_LIB") or build())
         L = _lib
         P = C.POINTER
         dp, fp, ip, i32p, u8p, i64p = (P(C.c_double), P(C.c_float), P(C.c_int), P(C.c_int32),

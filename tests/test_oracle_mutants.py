@@ -1,0 +1,60 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in a copy of
+`oracle/lem_oracle.c` (a wrong sign, a dropped term, transposed operands, a wrong
+normalisation, a wrong seed set of the cut), compiles it apart, and runs the pins of
+`tests/test_oracle_pins.py` against that copy in a child process: some pin must fail.
+The oracle itself is not changed; mistakes are only ever planted in these copies."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lem_oracle.c")
+
+# (name, text in lem_oracle.c, replacement): every occurrence is replaced
+MUTANTS = [
+    ("warp adds the disparity", "double up = su - d;", "double up = su + d;"),
+    ("gradient term dropped from the raw cost",
+     "return (1.0 - pa) * fmin(col, c->p.tau_col) + pa * fmin(gd, c->p.tau_grad);",
+     "return (1.0 - pa) * fmin(col, c->p.tau_col);"),
+    ("plane slopes transposed", "double d = a * su + b * sv + cc;", "double d = a * sv + b * su + cc;"),
+    ("interpolation weights swapped", "double rv = (1.0 - t) * r0[ch] + t * r1[ch];",
+     "double rv = t * r0[ch] + (1.0 - t) * r1[ch];"),
+    ("guided-filter offset b_k with the wrong sign", "bk -= ai * mu[i];", "bk += ai * mu[i];"),
+    ("window mean normalised by one pixel too many", "mr /= n;", "mr /= n + 1;"),
+    ("smoothness term one-sided",
+     "return fabs(disp_at(fp, pu, pv) - disp_at(fq, pu, pv)) + fabs(disp_at(fq, qu, qv) - disp_at(fp, qu, qv));",
+     "return fabs(disp_at(fp, pu, pv) - disp_at(fq, pu, pv));"),
+    ("smoothness term not truncated", "fmin(lo_psibar(pu, pv, qu, qv, fp, fq), c->p.tau_dis)",
+     "lo_psibar(pu, pv, qu, qv, fp, fq)"),
+    ("cut side seeded from every node", "if (res_t[i] > 0) {", "if (res_t[i] >= 0) {"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {old}"
+    mutant = tmp_path / "lem_oracle_mutant.c"
+    mutant.write_text(src.replace(old, new))
+    so = tmp_path / "liblem_oracle_mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", str(mutant),
+                    "-o", str(so), "-lm"], check=True)
+    env = dict(os.environ, LEM_ORACLE_LIB=str(so))
+    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
+                          "-q", "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode != 0, f"no pin caught the mistake '{name}':\n{out.stdout[-1500:]}"
+
+
+def test_unmodified_copy_passes(tmp_path):
+    """Control: the same procedure on an unmodified copy passes every pin."""
+    so = tmp_path / "liblem_oracle_copy.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", SRC, "-o",
+                    str(so), "-lm"], check=True)
+    env = dict(os.environ, LEM_ORACLE_LIB=str(so))
+    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
+                          "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-1500:]
