@@ -58,3 +58,62 @@ def test_unmodified_copy_passes(tmp_path):
                           "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
                          text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-1500:]
+
+
+# the Python parts of the oracle: (name, module file, text, replacement, pin file)
+PY_MUTANTS = [
+    ("convolution instead of correlation", "cnn.py", "y += xp[i:i + H, j:j + W] @ w[i, j]",
+     "y += xp[i:i + H, j:j + W] @ w[2 - i, 2 - j]", "test_oracle_cnn.py"),
+    ("input gradient without the flip", "cnn.py", "dx += dyp[2 - i:2 - i + H, 2 - j:2 - j + W] @ w[i, j].T",
+     "dx += dyp[i:i + H, j:j + W] @ w[i, j].T", "test_oracle_cnn.py"),
+    ("weight gradient with a flipped window", "cnn.py", "dw[i, j] = xp[i:i + H, j:j + W]",
+     "dw[i, j] = xp[2 - i:2 - i + H, 2 - j:2 - j + W]", "test_oracle_cnn.py"),
+    ("bfloat16 ties rounded away from zero", "cnn.py",
+     "up = (rest > 0x8000) | ((rest == 0x8000) & ((keep & 1) == 1))", "up = rest >= 0x8000", "test_oracle_cnn.py"),
+    ("quarter-grid centre off by half a pixel", "cnn.py", "fv = min(max((vv - 1.5) / 4.0, 0.0), H4 - 1.0)",
+     "fv = min(max((vv - 2.0) / 4.0, 0.0), H4 - 1.0)", "test_oracle_cnn.py"),
+    ("target slopes not clamped", "cnn.py", "t[..., 1:] = np.clip(t[..., 1:], -1.0, 1.0)", "pass",
+     "test_oracle_cnn.py"),
+    ("mirrored plane offset with the wrong sign", "postproc.py", "out = np.stack([-a, b, c + a * (W - 1)], axis=-1)",
+     "out = np.stack([-a, b, c - a * (W - 1)], axis=-1)", "test_oracle_post.py"),
+    ("consistency match on the wrong side", "postproc.py", "q = np.rint(u - dL)", "q = np.rint(u + dL)",
+     "test_oracle_post.py"),
+    ("filling from the foreground", "postproc.py", "out[y, x] = min(cands)", "out[y, x] = max(cands)",
+     "test_oracle_post.py"),
+    ("weighted median one element too far", "postproc.py", "k = int(np.searchsorted(cw, 0.5 * cw[-1]))",
+     "k = int(np.searchsorted(cw, 0.5 * cw[-1], side='right'))", "test_oracle_post.py"),
+]
+
+
+@pytest.mark.parametrize("name,module,old,new,pins", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_python_pins_catch_planted_mistake(tmp_path, name, module, old, new, pins):
+    import shutil
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    path = pkg / module
+    text = path.read_text()
+    assert text.count(old) == 1, f"mutation site not found: {old}"
+    path.write_text(text.replace(old, new))
+    # the child starts in tmp_path, so `import oracle` finds the planted copy first
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    env.pop("LEM_ORACLE_LIB", None)
+    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins), "-x", "-q",
+                          "-p", "no:cacheprovider", "-m", "not gpu"], cwd=str(tmp_path), env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode != 0, f"no pin caught the mistake '{name}':\n{out.stdout[-1500:]}"
+
+
+def test_python_unmodified_copy_passes(tmp_path):
+    """Control for the Python parts: an unmodified copy of the package passes their pins."""
+    import shutil
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    env.pop("LEM_ORACLE_LIB", None)
+    for pins in ("test_oracle_cnn.py", "test_oracle_post.py"):
+        out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins), "-q",
+                              "-p", "no:cacheprovider", "-m", "not gpu",
+                              "-W", "ignore::pytest.PytestAssertRewriteWarning"], cwd=str(tmp_path), env=env,
+                             capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stdout[-1500:]
