@@ -289,8 +289,9 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
  * first call runs one iteration directly and captures one iteration (48
  * launches and the increment of a device-side iteration index) as a CUDA
  * graph on a private stream; later iterations replay that graph on the
- * handle's stream.  stats may be NULL (no synchronisation); when given, the
- * call synchronises and fills all fields (energy after the last iteration).
+ * handle's stream (a handle with a level on the multi-CTA path always launches
+ * directly).  stats may be NULL (no synchronisation); when given, the call
+ * synchronises and fills all fields (energy after the last iteration).
  * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats);
 
