@@ -621,6 +621,16 @@ def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
     net.close()
     return out
 
+def _block(fn, *a, **kw):
+    """One extra measurement; an exception becomes {"error": ...} in the JSON line."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_lem(args):
     import numpy as np
     import torch
@@ -745,11 +755,12 @@ def run_lem(args):
     e2e_job = max_over_ranks(sum(e2e_t) / len(e2e_t), dist)
     e2e_v = world * n_iters_job * evals_per_step / e2e_job
 
-    tte = None if args.no_time_to_energy else time_to_energy(lem, pair, params, stream, seed=21 + rank)
-    prop = None if args.no_proposer else proposer_timing(lem, stream)
-    lebf = None if args.no_bf else bf_timing(lem, pair, stream, seed=31 + rank, flush=flush)
-    v3 = None if args.no_v3 else v3_timing(lem, stream, seed=41 + rank, flush=flush)
-    large = None if args.no_large else large_timing(lem, stream, seed=51 + rank, flush=flush)
+    # the extra blocks report their own failure instead of taking the headline line with them
+    tte = None if args.no_time_to_energy else _block(time_to_energy, lem, pair, params, stream, seed=21 + rank)
+    prop = None if args.no_proposer else _block(proposer_timing, lem, stream)
+    lebf = None if args.no_bf else _block(bf_timing, lem, pair, stream, seed=31 + rank, flush=flush)
+    v3 = None if args.no_v3 else _block(v3_timing, lem, stream, seed=41 + rank, flush=flush)
+    large = None if args.no_large else _block(large_timing, lem, stream, seed=51 + rank, flush=flush)
 
     if rank != 0:
         return
@@ -789,7 +800,7 @@ def run_lem(args):
                    for k, v in by_level.items()},
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_baseline(pair, p, seed=1)
+        out["cpu_baseline"] = _block(cpu_oracle_baseline, pair, p, seed=1)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
