@@ -755,12 +755,14 @@ def run_lem(args):
     e2e_job = max_over_ranks(sum(e2e_t) / len(e2e_t), dist)
     e2e_v = world * n_iters_job * evals_per_step / e2e_job
 
-    # the extra blocks report their own failure instead of taking the headline line with them
-    tte = None if args.no_time_to_energy else _block(time_to_energy, lem, pair, params, stream, seed=21 + rank)
-    prop = None if args.no_proposer else _block(proposer_timing, lem, stream)
-    lebf = None if args.no_bf else _block(bf_timing, lem, pair, stream, seed=31 + rank, flush=flush)
-    v3 = None if args.no_v3 else _block(v3_timing, lem, stream, seed=41 + rank, flush=flush)
-    large = None if args.no_large else _block(large_timing, lem, stream, seed=51 + rank, flush=flush)
+    # the extra blocks report their own failure instead of taking the headline line with
+    # them; only rank 0 prints them, so only rank 0 runs them
+    extra = rank == 0
+    tte = None if args.no_time_to_energy or not extra else _block(time_to_energy, lem, pair, params, stream, seed=21)
+    prop = None if args.no_proposer or not extra else _block(proposer_timing, lem, stream)
+    lebf = None if args.no_bf or not extra else _block(bf_timing, lem, pair, stream, seed=31, flush=flush)
+    v3 = None if args.no_v3 or not extra else _block(v3_timing, lem, stream, seed=41, flush=flush)
+    large = None if args.no_large or not extra else _block(large_timing, lem, stream, seed=51, flush=flush)
 
     if rank != 0:
         return
