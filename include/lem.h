@@ -117,7 +117,7 @@ typedef struct {
     int level_gr_interval[3]; /* push-relabel rounds between global relabels; default gr_interval
                                  (CTA path) or max(gr_interval, 64) (multi-CTA path)          */
     int level_strip_rows[3];  /* rows per strip of the cost pipeline; default strip_rows         */
-    int k_rans[3];        /* RANSAC proposals per region visit, per level (Algorithm 2, lines 5-8;
+    int k_rans[3];        /* RANSAC proposals per region visit, per level (Algorithm 2, RANSAC proposal;
                              default 0, the paper's setting outside its V3 experiments, where it
                              uses 1).  Proposal indices K_prop .. K_prop + k_rans - 1 take the plane
                              LO-RANSAC fits to the current disparities of the centre cell: 32

@@ -67,7 +67,7 @@ typedef struct {
     int reverse_order;    /* visit the regions of a group in reverse order        */
     int visit;            /* candidates drawn per region visit (1: Algorithm 2)   */
     int k_cnn[3];         /* candidates per visit cell taken from the proposal map */
-    int k_rans[3];        /* RANSAC plane candidates per visit (Algorithm 2, lines 5-8) */
+    int k_rans[3];        /* RANSAC plane candidates per visit (Algorithm 2, RANSAC proposal) */
     int data_term;        /* 0: guided filter (LE-GF), 1: bilateral weights (LE-BF)  */
     double bf_gamma;      /* LE-BF weight scale on 0..255 colours                    */
 } lo_params;
@@ -1100,7 +1100,7 @@ void lo_propose_map(const float *map, int W, uint64_t stream, int cx0, int cy0, 
     alpha[2] = m[2];
 }
 
-/* RANSAC proposer (Algorithm 2, lines 5-8): a plane fitted to the current
+/* RANSAC proposer (Algorithm 2, RANSAC proposal): a plane fitted to the current
  * disparities of the centre cell C_ij by LO-RANSAC (Chum et al. 2003).  The paper
  * gives no settings; the readings: the points are the pixels r of C_ij with their
  * disparities d_r = (a u + b v) + c in FP64, taken on the 2^-20 grid (round half to

@@ -228,7 +228,7 @@ __device__ float4 propose(const float4 *lab, int W, unsigned long long stream, i
 
 
 // ---------------------------------------------------------------------------
-// RANSAC proposer (Algorithm 2, lines 5-8): LO-RANSAC plane fit to the current
+// RANSAC proposer (Algorithm 2, RANSAC proposal): LO-RANSAC plane fit to the current
 // disparities of the centre cell, computed by the whole CTA.  The steps and their
 // rounding are the oracle's: disparities on the 2^-20 grid, 32 hypotheses through
 // three pixels drawn from the proposal's stream, 1 px inliers, the best (first on
@@ -626,7 +626,6 @@ __device__ __forceinline__ void row_offset(float sh, float sl, float lb, float l
 __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                              float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, r = kp.r, T = kp.T;
-    const int tid = threadIdx.x, nt = blockDim.x;
     const int Mx0 = max(0, Rx0 - 2 * r), Mx1 = min(W, Rx0 + Rw + 2 * r);
     const int My0 = max(0, Ry0 - 2 * r), My1 = min(H, Ry0 + Rh + 2 * r);
     const int Kx0 = max(0, Rx0 - r), Kx1 = min(W, Rx0 + Rw + r);

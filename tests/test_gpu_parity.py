@@ -415,7 +415,7 @@ def test_autotune_keeps_the_state_and_the_results(torch_cuda):
 
 
 def test_ransac_candidates_in_lockstep_with_oracle(tiny_pair, torch_cuda):
-    """K_RANS = 1 (Algorithm 2, lines 5-8), group by group from the same labels.  The
+    """K_RANS = 1 (Algorithm 2, RANSAC proposal), group by group from the same labels.  The
     candidates themselves are bit-identical (test_visit_candidates_bit_identical); a RANSAC
     plane is fitted to the current labels, so far more pixels than with propagation or
     perturbation have phi(alpha) within FP32 rounding of phi(f_p) and near-ties decided

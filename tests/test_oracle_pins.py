@@ -563,7 +563,7 @@ def _plane_labels(H, W, a, b, c):
 
 
 def test_ransac_recovers_a_plane_among_outliers():
-    """Algorithm 2, lines 5-8 (LO-RANSAC on the centre cell): labels of one plane, 30 % of
+    """Algorithm 2, RANSAC proposal (LO-RANSAC on the centre cell): labels of one plane, 30 % of
     them replaced by labels 5-20 px off it, give back that plane."""
     rng = np.random.default_rng(3)
     H, W = 40, 60
