@@ -101,3 +101,20 @@ def test_v3_settings(L):
     assert L.lib().lem_v3_params(None, 100) == L.LEM_ERR_ARG
     with pytest.raises(L.LemError):
         L.lem_default_params(v3_width=0)
+
+
+def test_parameter_checks_of_the_later_options(L):
+    """Argument checks that run before any GPU work: launch shape, cluster visits,
+    candidates per visit, proposer counts and strip rows."""
+    lib = L.lib()
+    a = np.zeros((32, 40, 3), np.uint8)
+    im = L.lem_image(a.ctypes.data, 32, 40, 120, 0)
+    h = C.c_void_p()
+    bad = [dict(level_threads=(96, 0, 0)), dict(cluster_visits=2), dict(candidates_per_visit=9),
+           dict(candidates_per_visit=0), dict(k_cnn=(65, 0, 0)), dict(k_rans=(0, 65, 0)), dict(strip_rows=6),
+           dict(level_strip_rows=(0, 68, 0)), dict(level_gr_interval=(-1, 0, 0)), dict(cell=(0, 15, 25)),
+           dict(quant_scale=0.0), dict(store_dtype=3), dict(max_rounds=0), dict(threads=1056)]
+    for kw in bad:
+        p = L.lem_default_params(gf_radius=2, **kw)
+        assert lib.lem_create(C.byref(im), C.byref(im), C.byref(p), C.byref(h)) == L.LEM_ERR_ARG, kw
+        assert not h.value
