@@ -82,6 +82,13 @@ PY_MUTANTS = [
      "test_oracle_post.py"),
     ("weighted median one element too far", "postproc.py", "k = int(np.searchsorted(cw, 0.5 * cw[-1]))",
      "k = int(np.searchsorted(cw, 0.5 * cw[-1], side='right'))", "test_oracle_post.py"),
+    # (a mistake in the band sizes would leave the gloo ranks waiting for each other, so
+    # the exchange's content is mutated, not its size)
+    ("exchange sends only the centre cells' changes", "stripes.py",
+     "changed[R[1]:R[1] + R[3], R[0]:R[0] + R[2]] = True",
+     "changed[cj * s:min(H, cj * s + s), ci * s:min(W, ci * s + s)] = True", "test_stripes.py"),
+    ("boundary cells owned by two stripes", "stripes.py", "if top <= j * s < bot", "if top <= j * s <= bot",
+     "test_stripes.py"),
 ]
 
 
