@@ -486,17 +486,23 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
         uint8_t *tmp = nullptr;
         if (!left->on_device || !right->on_device) {
             CREATE_CUDA(cudaMalloc(&tmp, 2 * np * 3));
+            cudaError_t ce = cudaSuccess;
             if (!left->on_device) {
-                CREATE_CUDA(cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H,
-                                              cudaMemcpyHostToDevice, h->st));
+                ce = cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H, cudaMemcpyHostToDevice,
+                                       h->st);
                 dl = tmp;
                 ls = 3 * W;
             }
-            if (!right->on_device) {
-                CREATE_CUDA(cudaMemcpy2DAsync(tmp + 3 * np, 3 * W, right->data, right->stride_row, 3 * W, H,
-                                              cudaMemcpyHostToDevice, h->st));
+            if (ce == cudaSuccess && !right->on_device) {
+                ce = cudaMemcpy2DAsync(tmp + 3 * np, 3 * W, right->data, right->stride_row, 3 * W, H,
+                                       cudaMemcpyHostToDevice, h->st);
                 dr = tmp + 3 * np;
                 rs = 3 * W;
+            }
+            if (ce != cudaSuccess) {
+                cudaStreamSynchronize(h->st);
+                cudaFree(tmp);
+                return bail(cuda_fail(h, ce, "lem_create image upload"));
             }
         }
         lem::DevPlanes P = planes(h, b);
@@ -530,7 +536,7 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
 int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out) {
     if (!left || !right) {
         if (out) *out = nullptr;
-        return fail(nullptr, LEM_ERR_ARG, "left image is NULL");
+        return fail(nullptr, LEM_ERR_ARG, "left or right image is NULL");
     }
     return lem_create_batch(left, right, 1, p, out);
 }
@@ -686,8 +692,10 @@ static int build_graph(lem_handle *h) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
-    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return e != cudaSuccess ? cuda_fail(h, e, "graph capture") : cuda_fail(h, e2, "cudaStreamEndCapture");
+    }
     h->graph = graph;
     LEM_CUDA(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
     return LEM_OK;
