@@ -1068,7 +1068,12 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         else if (ctr1.limit_hits != ctr0.limit_hits)
             rc = fail(h, LEM_ERR_MAXFLOW_LIMIT, "a trial cut hit the push-relabel round limit");
     }
-    if (rc != LEM_OK) h->p = keep;
+    if (rc != LEM_OK) {
+        // a failed trial may have left its moves in the labels
+        h->p = keep;
+        if (cudaMemcpyAsync(h->lab, save, sizeof(float4) * n, cudaMemcpyDeviceToDevice, h->st) == cudaSuccess)
+            cudaStreamSynchronize(h->st);
+    }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     cudaFree(save);

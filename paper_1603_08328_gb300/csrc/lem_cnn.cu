@@ -470,12 +470,19 @@ size_t nweights(int l) { return (size_t)9 * kRealCin[l] * kRealCout[l]; }
 
 int ensure_capacity(lem_cnn *net, size_t npix) {
     if (npix <= net->cap) return LEM_OK;
-    for (int l = 0; l <= kLayers; ++l) cudaFree(net->act[l]);
-    for (int l = 0; l < kLayers; ++l) cudaFree(net->pre[l]);
-    cudaFree(net->dz);
-    cudaFree(net->dx);
-    cudaFree(net->xin);
-    cudaFree(net->tgt);
+    // pointers are cleared as they are freed, so a failed allocation below
+    // leaves nothing dangling for a later call or lem_cnn_destroy
+    auto drop = [](auto *&p) {
+        cudaFree(p);
+        p = nullptr;
+    };
+    net->cap = 0;
+    for (int l = 0; l <= kLayers; ++l) drop(net->act[l]);
+    for (int l = 0; l < kLayers; ++l) drop(net->pre[l]);
+    drop(net->dz);
+    drop(net->dx);
+    drop(net->xin);
+    drop(net->tgt);
     for (int l = 0; l <= kLayers; ++l) {
         const int c = l == 0 ? kCin[0] : kCout[l - 1];
         CNN_CUDA(net, cudaMalloc(&net->act[l], sizeof(bf16) * npix * c));
