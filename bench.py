@@ -796,6 +796,9 @@ def run_lem(args):
         "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
                             "evals_per_s": v["evals"] / (v["ms"] / 1e3),
                             "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
+                            # one cut per candidate and region, one node per pixel of the region
+                            "cuts_per_s": v["cuts"] / (v["ms"] / 1e3),
+                            "nodes_per_cut": v["evals"] / max(1, v["cuts"]),
                             "rounds_per_cut": v["rounds"] / max(1, v["cuts"]),
                             "relabels_per_cut": v["relabels"] / max(1, v["cuts"]),
                             "bfs_levels_per_relabel": v["bfs_levels"] / max(1, v["relabels"])}
