@@ -431,8 +431,8 @@ def run_batch8_mode(args):
 def bf_flops(H, W, r, x0, y0, w, h):
     """FP32 operations of the LE-BF data term of one candidate on region R: about 30 per
     raw cost over M (R grown by the window radius 2 r') and one multiply-add (2 flops) per
-    window pixel of every output pixel, windows clipped to the image.  The colour weights
-    come from a 766-entry table of the integer L1 distance and are not counted."""
+    window pixel of every output pixel, windows clipped to the image.  The colour weight of
+    each window pixel (one exp2 on the special-function unit) is not counted."""
     import numpy as np
     R = 2 * r
     mw = min(W, x0 + w + R) - max(0, x0 - R)
