@@ -159,8 +159,10 @@ typedef struct {
 
 typedef struct lem_handle lem_handle;
 
-/* Fills `p` with the paper's parameter values (see lem_params).  disp_max is
- * set to 60; callers set it to their range. */
+/* Fills `p` with the paper's parameter values (Sec. 4, settings of the
+ * experiments: cells 5 / 15 / 25, {K_prop, K_rand} = {1, 7}, {2, 0}, {2, 0}, the
+ * data-term and smoothness constants; see lem_params).  disp_max is set to 60;
+ * callers set it to their range. */
 void lem_default_params(lem_params *p);
 
 /* The paper's settings for the Middlebury V3 benchmark (Sec. 4): the three cell
@@ -183,7 +185,8 @@ int lem_v3_params(lem_params *p, int width);
  * LEM_ERR_OOM, LEM_ERR_CUDA.  On error *out is NULL. */
 int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out);
 
-/* A handle for n_pairs independent pairs (sizes may differ), solved together:
+/* A handle for n_pairs independent pairs (sizes may differ), each prepared as by
+ * lem_create (Sec. 3.2) and solved together:
  * each (level, group) launch of lem_expand_group / lem_expand_iteration runs
  * the regions of every pair (pairs are independent, so their regions never
  * interact).  Pair b draws its random numbers from seed + b * 0x9E3779B97F4A7C15,
@@ -205,18 +208,20 @@ int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pair
 int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int n_pairs,
                             const double *disp_ranges, const lem_params *p, lem_handle **out);
 
-/* Number of pairs of a handle (-1 for NULL). */
+/* Number of pairs of a handle (-1 for NULL).  Handle bookkeeping; the paper
+ * has no counterpart. */
 int lem_pair_count(const lem_handle *h);
 
 /* Height, width and first pixel index (in the concatenated per-pixel arrays)
  * of pair `pair`.  Any output may be NULL.  Errors: LEM_ERR_ARG. */
 int lem_pair_info(const lem_handle *h, int pair, int *height, int *width, int64_t *pixel_offset);
 
-/* Quantised energy of one pair (see lem_energy).  Synchronises the stream.
+/* Quantised energy of one pair (Eq. mrf; see lem_energy).  Synchronises the stream.
  * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_energy_pair(lem_handle *h, int pair, double *energy, int64_t *energy_q);
 
-/* Frees the handle and everything it owns.  NULL is accepted. */
+/* Frees the handle and everything it owns.  NULL is accepted.  Handle
+ * bookkeeping; the paper has no counterpart. */
 int lem_destroy(lem_handle *h);
 
 /* Text of the last error on `h` (or of the last failed lem_create when h is
@@ -255,7 +260,9 @@ int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, con
 int lem_pairwise_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *alpha,
                        const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *const_term);
 
-/* Minimum s-t cut of each region graph (layout of lem_pairwise_batch) by
+/* Minimum s-t cut of each region graph (layout of lem_pairwise_batch): the exact
+ * solution of one alpha_ij-expansion's binary problem (Eq. expansion, Sec. 3.3),
+ * which is submodular by Lemma 2 and is solved by graph cuts.  Computed by
  * push-relabel with global relabelling, one CTA per region, in shared memory.
  * When some region exceeds LEM_MAX_REGION_NODES (any size up to the image is
  * accepted here) every region of the call runs on the multi-CTA path instead:
@@ -296,13 +303,14 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats);
 
 /* Current labels and cost cache.  abc: float32 H*W*3, disp: float32 H*W
- * (d_p = a u + b v + c), cost: float32 H*W; any may be NULL; `on_device`
- * says whether the pointers are device (1) or host (0) memory.  Host copies
- * synchronise the stream.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+ * (d_p = a u + b v + c, Eq. disparity_plane), cost: phi_p(f_p) (Eq. unary_term),
+ * float32 H*W; any may be NULL; `on_device` says whether the pointers are
+ * device (1) or host (0) memory.  Host copies synchronise the stream.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_get_labels(lem_handle *h, float *abc, float *disp, float *cost, int on_device);
 
-/* Replaces the labels (float32 H*W*3) and, when `cost` is not NULL, the cost
- * cache (float32 H*W, taken as phi_p(f_p) for the new labels); with cost NULL
+/* Replaces the labels (float32 H*W*3; planes of Eq. disparity_plane) and, when
+ * `cost` is not NULL, the cost cache (float32 H*W, taken as phi_p(f_p) of
+ * Eq. unary_term for the new labels); with cost NULL
  * the cache is recomputed by the data term.  on_device as in lem_get_labels.
  * Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_device);
@@ -314,7 +322,7 @@ int lem_set_labels(lem_handle *h, const float *abc, const float *cost, int on_de
 int lem_energy(lem_handle *h, double *energy, int64_t *energy_q);
 
 /* Device views of the handle's packed planes (for tests): left/right packed
- * pixels (4 floats: R, G, B, gradient) as float32 H*W*4, guide statistics as
+ * pixels (4 floats: R, G, B, gradient; Sec. 3.2, data term) as float32 H*W*4, guide statistics as
  * float32 H*W*9 {mu_r, mu_g, mu_b, A00, A01, A02, A11, A12, A22}, and
  * lambda*max(w, eps) for the 4 forward neighbours as float32 H*W*4.  Copies
  * into caller device buffers; any may be NULL.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
@@ -323,11 +331,12 @@ int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float
 /* Largest n_regions of lem_mincut_batch_noalloc. */
 #define LEM_NOALLOC_MAX_REGIONS 4096
 
-/* lem_mincut_batch for callers that cannot allocate device memory when they
- * cut: code that runs inside a preallocated memory arena, a host thread that
- * must not call cudaMalloc/cudaFree because those synchronise the device, or an
- * embedding that forbids growing the device heap.  The paper has no
- * counterpart; this is a deployment variant of the same min-cut.
+/* lem_mincut_batch (Eq. expansion, Sec. 3.3) for callers that cannot allocate
+ * device memory when they cut: code that runs inside a preallocated memory
+ * arena, a host thread that must not call cudaMalloc/cudaFree because those
+ * synchronise the device, or an embedding that forbids growing the device
+ * heap.  The paper has no counterpart for the allocation-free form; the cut is
+ * the same.
  *
  * It needs no handle and allocates nothing: the scratch the batch min-cut
  * keeps per call (region descriptors, packed offsets, work counters) is a
@@ -415,7 +424,8 @@ typedef struct {
     int configs_tried;     /* candidate configurations timed (all levels)                   */
 } lem_tuning;
 
-/* Times the expansion kernel of every level on this handle's own images and
+/* Launch-shape tuning; the paper has no counterpart, and labels never depend
+ * on it.  Times the expansion kernel of every level on this handle's own images and
  * labels for each candidate configuration (threads {128, 256, 512, 1024} x
  * gr_interval {8, 16, 32, 64} x strip_rows {8, 12, 16, 24, 32}; candidates whose shared
  * memory does not fit are skipped), `repeats` launches of groups 0 and 10 of
@@ -428,8 +438,8 @@ typedef struct {
  * LEM_ERR_MAXFLOW_LIMIT (a trial cut hit the round limit), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_autotune(lem_handle *h, int repeats, lem_tuning *out);
 
-/* Number of pixel-label cost evaluations in one outer iteration (sum over all
- * region visits of |R| x proposals).  Host only. */
+/* Number of pixel-label cost evaluations in one outer iteration of Algorithm 1
+ * (sum over all region visits of |R| x proposals).  Host only. */
 int64_t lem_evals_per_iteration(const lem_handle *h);
 
 /* ------------------------------------------------------------------------- */
