@@ -399,9 +399,24 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _on_own_stream(fn):
+    """Runs a method with the object's stream current, so that the tensors it
+    allocates and copies are ordered with the library calls it makes."""
+    import functools
+
+    @functools.wraps(fn)
+    def wrapped(self, *args, **kwargs):
+        with self.torch.cuda.stream(self.stream):
+            return fn(self, *args, **kwargs)
+    return wrapped
+
+
 class Stereo:
     """One handle on one pair.  Images are numpy uint8 (H, W, 3) host arrays or
-    CUDA uint8 tensors; batch outputs are CUDA tensors."""
+    CUDA uint8 tensors; batch outputs are CUDA tensors.  Every call runs on
+    `stream` (default: the current stream at construction), the tensor copies and
+    allocations this wrapper makes included; results are ready in that stream's
+    order."""
 
     def __init__(self, left, right, stream=None, disp_ranges=None, view="left", **params):
         """left/right: one image each, or lists of images (a batch of pairs); disp_ranges:
@@ -461,6 +476,7 @@ class Stereo:
         return _check(rc, self.h)
 
     # batch calls ------------------------------------------------------------
+    @_on_own_stream
     def unary(self, regions, labels):
         """labels: (n_regions, K, 3) float32 -> list of (K, h, w) cost tensors."""
         torch = self.torch
@@ -475,6 +491,7 @@ class Stereo:
             off += K * s
         return res
 
+    @_on_own_stream
     def pairwise(self, regions, alpha, costs_alpha):
         torch = self.torch
         al = torch.as_tensor(np.ascontiguousarray(alpha, np.float32)).cuda()
@@ -486,6 +503,7 @@ class Stereo:
         self.check(lem_pairwise_batch(self.h, regions, _ptr(al), _ptr(ca), _ptr(tc), _ptr(nc), _ptr(ct)))
         return tc, nc, ct
 
+    @_on_own_stream
     def mincut(self, regions, tcaps, ncaps):
         torch = self.torch
         n = sum(r[2] * r[3] for r in regions)
@@ -508,6 +526,7 @@ class Stereo:
         self.check(lem_expand_iteration(self.h, n, s))
         return s
 
+    @_on_own_stream
     def labels(self, pair=None):
         """(abc, disp, cost) of pair 0 (single pair) or of `pair`; pair='all' gives flat arrays."""
         torch = self.torch
@@ -522,6 +541,7 @@ class Stereo:
         n = hh * ww
         return abc[off:off + n].view(hh, ww, 3), disp[off:off + n].view(hh, ww), cost[off:off + n].view(hh, ww)
 
+    @_on_own_stream
     def set_labels(self, abc, cost=None):
         torch = self.torch
         a = torch.as_tensor(np.ascontiguousarray(abc, np.float32)).cuda()
@@ -533,6 +553,7 @@ class Stereo:
         self.check(rc)
         return e, q
 
+    @_on_own_stream
     def planes(self):
         torch = self.torch
         n = self.total
@@ -549,12 +570,14 @@ class Stereo:
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
 
+    @_on_own_stream
     def proposals_of(self, it, level, cells, nprop):
         """Candidates of one visit of each cell (lem_propose_batch): (n_cells, nprop, 3) numpy."""
         out = self.torch.empty(len(cells) * nprop * 3, dtype=self.torch.float32, device="cuda")
         self.check(lem_propose_batch(self.h, it, level, cells, _ptr(out)))
         return out.cpu().numpy().reshape(len(cells), nprop, 3)
 
+    @_on_own_stream
     def postprocess(self, right_view: "Stereo", **pp):
         """Consistency check with the right view, occlusion filling and weighted median
         (lem_postprocess); returns (disparity (H, W), consistent (H, W) bool) CUDA tensors."""
@@ -575,6 +598,7 @@ class Stereo:
         return t
 
     # learned proposer -------------------------------------------------------------
+    @_on_own_stream
     def set_proposals(self, abc, pair=0):
         """Proposal map (H, W, 3) of plane labels for the k_cnn map candidates."""
         torch = self.torch
@@ -582,6 +606,7 @@ class Stereo:
         self._prop_keep = a
         self.check(lem_set_proposals(self.h, pair, _ptr(a)))
 
+    @_on_own_stream
     def proposals(self, pair=0):
         hh, ww, _ = self.pairs[pair]
         out = self.torch.empty(hh, ww, 3, dtype=self.torch.float32, device="cuda")
@@ -592,12 +617,14 @@ class Stereo:
         hh, ww, _ = self.pairs[pair]
         return (hh + 3) // 4, (ww + 3) // 4
 
+    @_on_own_stream
     def cnn_features(self, pair=0):
         H4, W4 = self.quarter_shape(pair)
         x = self.torch.empty(H4, W4, 7, dtype=self.torch.float32, device="cuda")
         self.check(lem_cnn_features(self.h, pair, _ptr(x)))
         return x
 
+    @_on_own_stream
     def cnn_targets(self, pair=0):
         H4, W4 = self.quarter_shape(pair)
         t = self.torch.empty(H4, W4, 3, dtype=self.torch.float32, device="cuda")
@@ -651,6 +678,7 @@ class ProposalNet:
         assert a.size == lem_cnn_num_params()
         self.check(lem_cnn_set_params(self.net, C.c_void_p(a.ctypes.data)))
 
+    @_on_own_stream
     def forward(self, x):
         """x: (H4, W4, 7) CUDA float32 -> (H4, W4, 3)."""
         x = x.contiguous()
@@ -659,6 +687,7 @@ class ProposalNet:
         self.check(lem_cnn_forward(self.net, _ptr(x), H4, W4, _ptr(y)))
         return y
 
+    @_on_own_stream
     def gradients(self, x, t, scale=(1.0, 1.0, 1.0)):
         """x: (n, H4, W4, 7), t: (n, H4, W4, 3) CUDA -> (loss, flat gradients in get_params order)."""
         x, t = x.contiguous(), t.contiguous()
@@ -670,6 +699,7 @@ class ProposalNet:
                                      C.c_void_p(loss.ctypes.data), C.c_void_p(g.ctypes.data)))
         return float(loss[0]), g
 
+    @_on_own_stream
     def train_step(self, x, t, lr, scale=(1.0, 1.0, 1.0)):
         x, t = x.contiguous(), t.contiguous()
         n, H4, W4 = x.shape[:3]
