@@ -1,6 +1,6 @@
 """Builds the CUDA library ``liblem.so`` in-tree for sm_103a (nvcc, no cmake).
 
-The two translation units compile in parallel; the result is linked with the
+The translation units compile in parallel; the result is linked with the
 static CUDA runtime so it loads without extra library paths.
 """
 from __future__ import annotations
