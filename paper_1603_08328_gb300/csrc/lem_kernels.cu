@@ -1,18 +1,26 @@
 // CUDA kernels of local-expansion-move stereo (arXiv 1603.08328) for sm_103a.
 //
-// Layout in device memory (one pair):
-//   L, R  : float4 per pixel (R, G, B, x-gradient of gray), 0..255 scale
+// Layout in device memory (one pair; a batch concatenates its pairs):
+//   L, R  : per pixel (R, G, B, x-gradient of gray), 0..255 scale, as float4
+//           or as four FP16 / BF16 values
 //   gst   : 3 float4 per pixel, guide mean mu_k and (Sigma_k + eU)^-1 (sym.)
 //   wfw   : float4 per pixel, lambda * max(w_pq, eps), forward neighbours
 //   lab   : float4 per pixel (a, b, c, phi_p(f_p)): label and cost cache
 //   phiA  : float per pixel, phi_p(alpha) of the candidate being evaluated
 //           (expansion regions of one group are disjoint, so one plane serves)
+//   phiB  : float per pixel, the second candidate's phi in a two-CTA visit
 //
-// One CTA evaluates, cuts and commits one expansion region.  The data term is
-// computed through the filtering region M as a strip pipeline in shared
-// memory (raw cost rows -> vertical window sums -> horizontal window sums ->
-// guided-filter coefficients -> their window means), then the move graph is
-// built in shared memory and cut by push-relabel with global relabelling.
+// Regions of up to 5625 nodes (k_expand_group): one CTA evaluates, cuts and
+// commits one expansion region; where a visit is two propagation candidates,
+// a cluster of two CTAs computes the second data term alongside the first
+// move.  The guided-filter data term is computed through the filtering
+// region M as a strip pipeline in shared memory (raw cost rows -> vertical
+// window sums -> horizontal window sums -> guided-filter coefficients -> their
+// window means); the LE-BF data term sums bilateral weights times raw costs
+// over each pixel's window.  The move graph is built in shared memory and cut
+// by push-relabel with global relabelling.  Larger regions (k_expand_grid)
+// run on several co-resident CTAs of a cooperative launch, with the graph in
+// global memory and region barriers between rounds.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
