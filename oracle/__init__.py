@@ -144,6 +144,8 @@ def lib():
         L.lo_expand_group.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, P(C.c_longlong)]
         L.lo_expand_cells.restype = C.c_longlong
         L.lo_expand_cells.argtypes = [C.c_void_p, C.c_int, C.c_int, ip, C.c_int, P(C.c_longlong)]
+        L.lo_visit_candidates.restype = C.c_int
+        L.lo_visit_candidates.argtypes = [C.c_void_p, fp, C.c_int, C.c_int, C.c_int, C.c_int, fp]
         L.lo_iterate.restype = C.c_longlong
         L.lo_iterate.argtypes = [C.c_void_p, C.c_int, P(C.c_longlong)]
         L.lo_region_of.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip]
@@ -291,6 +293,15 @@ class Oracle:
         ev = C.c_longlong()
         acc = lib().lo_expand_group(self.h, it, level, group, C.byref(ev))
         return acc, ev.value
+
+    def visit_candidates(self, lab, it, level, ci, cj):
+        """Every candidate of the visit of cell (ci, cj), drawn from `lab` with no move in
+        between (Algorithm 2 with the outer perturbation sizes of iteration `it`)."""
+        lab = _f32(lab)
+        n = lib().lo_visit_candidates(self.h, _ptr(lab, C.c_float), it, level, ci, cj, None)
+        out = np.empty((n, 3), np.float32)
+        lib().lo_visit_candidates(self.h, _ptr(lab, C.c_float), it, level, ci, cj, _ptr(out, C.c_float))
+        return out
 
     def iterate(self, it):
         ev = C.c_longlong()

@@ -1375,35 +1375,52 @@ void lo_region_of(int H, int W, int s, int ci, int cj, int *R, int *C) {
  * of K consecutive proposals are all drawn from the labels at the start of
  * that run; their moves are then made one after the other, each against the
  * labels left by the previous one.  visit = 1 is Algorithm 2 as printed. */
+static int visit_proposals(const lo_ctx *c, int level) {
+    const int kc = c->prop ? c->p.k_cnn[level] : 0;
+    return c->p.k_prop[level] + c->p.k_rans[level] + kc + c->p.k_rand[level];
+}
+
+/* Candidates t0 .. t1-1 of the visit of cell (i, j) at `level`, drawn from the
+ * labels `lab` (Algorithm 2, in proposal order: propagation, RANSAC, map,
+ * perturbation) at pixels of the centre cell C_ij.  *rd and *rn are the visit's
+ * own perturbation sizes, halved after each perturbation proposal. */
+static void draw_candidates(const lo_ctx *c, const float *lab, int iter, int level, int ci, int cj, int t0, int t1,
+                            double *rd, double *rn, float (*alpha)[3]) {
+    const int W = c->W;
+    int R[4], C[4];
+    lo_region_of(c->H, W, c->p.cell[level], ci, cj, R, C);
+    const int kp = c->p.k_prop[level], kr = c->p.k_rans[level], kc = c->prop ? c->p.k_cnn[level] : 0;
+    for (int t = t0; t < t1; t++) {
+        const uint64_t stream = lo_proposal_stream(c->p.seed, iter, level, ci, cj, t);
+        if (t >= kp && t < kp + kr) {
+            lo_propose_ransac(lab, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
+            continue;
+        }
+        if (t >= kp + kr && t < kp + kr + kc) {
+            lo_propose_map(c->prop, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
+            continue;
+        }
+        const int perturb = t >= kp + kr + kc;
+        lo_propose(lab, W, stream, C[0], C[1], C[2], C[3], perturb, perturb ? *rd : 0.0, perturb ? *rn : 0.0,
+                   c->p.disp_min, c->p.disp_max, alpha[t - t0]);
+        if (perturb) {
+            *rd *= 0.5;
+            *rn *= 0.5;
+        }
+    }
+}
+
 static void iterative_expansion(lo_ctx *c, int iter, int level, int ci, int cj, double rd, double rn,
                                 long long *accepted, long long *evals) {
     const int H = c->H, W = c->W, s = c->p.cell[level];
     int R[4], C[4];
     lo_region_of(H, W, s, ci, cj, R, C);
-    const int kp = c->p.k_prop[level], kr = c->p.k_rans[level], kc = c->prop ? c->p.k_cnn[level] : 0;
-    const int nprop = kp + kr + kc + c->p.k_rand[level];
+    const int nprop = visit_proposals(c, level);
     const int K = c->p.visit < 1 ? 1 : (c->p.visit > 64 ? 64 : c->p.visit);
     float alpha[64][3];
     for (int t0 = 0; t0 < nprop; t0 += K) {
         const int t1 = t0 + K < nprop ? t0 + K : nprop;
-        for (int t = t0; t < t1; t++) {
-            const uint64_t stream = lo_proposal_stream(c->p.seed, iter, level, ci, cj, t);
-            if (t >= kp && t < kp + kr) {
-                lo_propose_ransac(c->lab, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
-                continue;
-            }
-            if (t >= kp + kr && t < kp + kr + kc) {
-                lo_propose_map(c->prop, W, stream, C[0], C[1], C[2], C[3], alpha[t - t0]);
-                continue;
-            }
-            const int perturb = t >= kp + kr + kc;
-            lo_propose(c->lab, W, stream, C[0], C[1], C[2], C[3], perturb, perturb ? rd : 0.0, perturb ? rn : 0.0,
-                       c->p.disp_min, c->p.disp_max, alpha[t - t0]);
-            if (perturb) {
-                rd *= 0.5;
-                rn *= 0.5;
-            }
-        }
+        draw_candidates(c, c->lab, iter, level, ci, cj, t0, t1, &rd, &rn, alpha);
         for (int t = t0; t < t1; t++) {
             *accepted += expand_move(c, R[0], R[1], R[2], R[3], alpha[t - t0], NULL);
             *evals += (long long)R[2] * R[3];
@@ -1466,6 +1483,20 @@ long long lo_expand_cells(lo_ctx *c, int iter, int level, const int *cells, int 
     }
     if (evals) *evals = ev;
     return acc;
+}
+
+/* Every candidate of the visit of cell (i, j) at `level` in outer iteration
+ * `iter`, drawn from the labels `lab` (H x W x 3) as the visit draws them when
+ * no move happens in between (Algorithm 2 with the outer perturbation sizes of
+ * Algorithm 1).  out: room for the visit's proposal count x 3 floats, or NULL.
+ * Returns that count. */
+int lo_visit_candidates(const lo_ctx *c, const float *lab, int iter, int level, int ci, int cj, float *out) {
+    const int nprop = visit_proposals(c, level);
+    if (!out) return nprop;
+    double rd, rn;
+    outer_delta(c, iter, &rd, &rn);
+    draw_candidates(c, lab, iter, level, ci, cj, 0, nprop, &rd, &rn, (float(*)[3])out);
+    return nprop;
 }
 
 /* One outer iteration of Algorithm 1: every grid level, every group. */

@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake in a copy of
 `oracle/lem_oracle.c` (a wrong sign, a dropped term, transposed operands, a wrong
-normalisation, a wrong seed set of the cut), compiles it apart, and runs the pins of
-`tests/test_oracle_pins.py` against that copy in a child process: some pin must fail.
+normalisation, a wrong seed set of the cut, a missing halving, a loose threshold),
+compiles it apart, and runs the pins of `tests/test_oracle_pins.py` against that copy in
+a child process: some pin must fail.
 The oracle itself is not changed; mistakes are only ever planted in these copies."""
 import os
 import subprocess
@@ -29,35 +30,92 @@ MUTANTS = [
     ("smoothness term not truncated", "fmin(lo_psibar(pu, pv, qu, qv, fp, fq), c->p.tau_dis)",
      "lo_psibar(pu, pv, qu, qv, fp, fq)"),
     ("cut side seeded from every node", "if (res_t[i] > 0) {", "if (res_t[i] >= 0) {"),
+    ("sample covariance of the guide", "for (int i = 0; i < 9; i++) S[i] /= n;",
+     "for (int i = 0; i < 9; i++) S[i] /= n - 1;"),
+    ("regulariser added to a row instead of the diagonal", "S[4 * i] += c->p.gf_eps;", "S[i] += c->p.gf_eps;"),
+    ("contrast weight without its floor", "if (w < c->p.eps_w) w = c->p.eps_w;", ""),
+    ("LE-BF window of radius r'", "const int H = c->H, W = c->W, R = 2 * c->p.gf_radius;",
+     "const int H = c->H, W = c->W, R = c->p.gf_radius;"),
+    ("LE-BF weight of the squared colour distance", "exp(-l1 / c->p.bf_gamma)", "exp(-l1 * l1 / c->p.bf_gamma)"),
+    ("energy without the diagonal pairs", "if (qx < 0 || qx >= W || qy >= H) continue;",
+     "if (qx < 0 || qx >= W || qy >= H || d == 1 || d == 3) continue;"),
+    ("energy without lambda", "double ps = lam * lo_psi(", "double ps = lo_psi("),
+    ("quantisation truncates", "return (int64_t)nearbyint(S * x);", "return (int64_t)(S * x);"),
+    ("pair above B + C not lowered", "if (A > B + C) {", "if (0) {"),
+    ("initial plane with the printed sign", "double cc = ((n[0] * u + n[1] * v) + n[2] * z0) / n[2];",
+     "double cc = -((n[0] * u + n[1] * v) + n[2] * z0) / n[2];"),
+    ("visit draws from the expansion region", "lo_propose(lab, W, stream, C[0], C[1], C[2], C[3], perturb,",
+     "lo_propose(lab, W, stream, R[0], R[1], R[2], R[3], perturb,"),
+    ("perturbation size not halved within a visit", "            *rd *= 0.5;\n            *rn *= 0.5;\n", ""),
+    ("perturbation size not halved per iteration", "double f = ldexp(1.0, -iter);", "double f = 1.0;"),
+    ("perturbation with a flipped normal", "double n[3] = {-a / len, -b / len, 1.0 / len};",
+     "double n[3] = {a / len, b / len, 1.0 / len};"),
+    ("perturbed disparity not clamped to the range", "    if (dp < dmin) dp = dmin;\n    if (dp > dmax) dp = dmax;\n",
+     ""),
+    ("RANSAC hypothesis slopes swapped", "const double a = (double)na / den, b = (double)nb / den;",
+     "const double a = (double)nb / den, b = (double)na / den;"),
+    ("RANSAC inlier band of 2 px", "const int ok = fabs(r) <= 1.0;", "const int ok = fabs(r) <= 2.0;"),
+    ("RANSAC without the least-squares refinement", "#define RANSAC_LO 2", "#define RANSAC_LO 0"),
+    ("groups by (i div 4, j mod 4)", "const int gi = group % 4, gj = group / 4;",
+     "const int gi = group / 4, gj = group % 4;"),
+    ("region one cell short on the left", "int x0 = imax(0, (ci - 1) * s), x1 = imin(W, (ci + 2) * s);",
+     "int x0 = imax(0, ci * s), x1 = imin(W, (ci + 2) * s);"),
+    ("switched pixels keep their old cost", "            c->cost[p] = phiA[i];\n", ""),
 ]
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+def _pins_against(so, first_failure):
+    """Runs the pins of tests/test_oracle_pins.py in a child process that loads the
+    oracle library `so`; returns (exit code, end of its output)."""
+    env = dict(os.environ, LEM_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
+           "-p", "no:cacheprovider", "-m", "not gpu"] + (["-x"] if first_failure else [])
+    out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return out.returncode, out.stdout[-1500:]
+
+
+def _compile(src_text, d):
+    c = os.path.join(d, "lem_oracle_copy.c")
+    so = os.path.join(d, "liblem_oracle_copy.so")
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", c, "-o", so,
+                    "-lm"], check=True)
+    return so
+
+
+@pytest.fixture(scope="module")
+def c_mutant_runs(tmp_path_factory):
+    """Every planted copy (and one unmodified copy, name None) compiled and checked
+    against the pins, several at a time."""
+    from concurrent.futures import ThreadPoolExecutor
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site not found: {old}"
-    mutant = tmp_path / "lem_oracle_mutant.c"
-    mutant.write_text(src.replace(old, new))
-    so = tmp_path / "liblem_oracle_mutant.so"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", str(mutant),
-                    "-o", str(so), "-lm"], check=True)
-    env = dict(os.environ, LEM_ORACLE_LIB=str(so))
-    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
-                          "-q", "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env,
-                         capture_output=True, text=True, timeout=600)
-    assert out.returncode != 0, f"no pin caught the mistake '{name}':\n{out.stdout[-1500:]}"
+
+    def run(case):
+        name, old, new = case
+        d = str(tmp_path_factory.mktemp("mutant"))
+        if name is None:
+            return name, _pins_against(_compile(src, d), first_failure=False)
+        if src.count(old) < 1:
+            return name, (None, f"mutation site not found: {old}")
+        return name, _pins_against(_compile(src.replace(old, new), d), first_failure=True)
+
+    cases = [(None, None, None)] + MUTANTS
+    with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as pool:
+        return dict(pool.map(run, cases))
 
 
-def test_unmodified_copy_passes(tmp_path):
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(c_mutant_runs, name):
+    rc, tail = c_mutant_runs[name]
+    assert rc is not None, tail
+    assert rc != 0, f"no pin caught the mistake '{name}':\n{tail}"
+
+
+def test_unmodified_copy_passes(c_mutant_runs):
     """Control: the same procedure on an unmodified copy passes every pin."""
-    so = tmp_path / "liblem_oracle_copy.so"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", SRC, "-o",
-                    str(so), "-lm"], check=True)
-    env = dict(os.environ, LEM_ORACLE_LIB=str(so))
-    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
-                          "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
-                         text=True, timeout=600)
-    assert out.returncode == 0, out.stdout[-1500:]
+    rc, tail = c_mutant_runs[None]
+    assert rc == 0, tail
 
 
 # the Python parts of the oracle: (name, module file, text, replacement, pin file)

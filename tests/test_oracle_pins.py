@@ -667,3 +667,136 @@ def test_le_bf_colour_step_weight():
             assert other > 0
             ref = same + np.exp(-40.0 / gamma) * other
             assert o.phi_bf(f, u, v) == pytest.approx(ref, rel=1e-12)
+
+
+# --- pins found missing by planting mistakes (tests/test_oracle_mutants.py) ---------
+
+# forward neighbour offsets (each unordered 8-neighbour pair once) and their direction index
+_FWD = {(1, 0): 0, (-1, 1): 1, (0, 1): 2, (1, 1): 3}
+
+
+def test_energy_is_the_sum_of_its_terms(tiny_pair):
+    """Eq. mrf with lambda = 2.5: E = sum_p phi_p(f_p) + lambda sum over unordered 8-neighbour
+    pairs of psi_pq.  Here every pixel's 8 neighbours are visited and the sum halved (each pair
+    seen from both ends, psi being symmetric in (p, f_p) <-> (q, f_q)); the quantised energy is
+    sum Q(phi_p) + sum Q(lambda psi_pq), Q(x) = rne(S x)."""
+    lam, S = 2.5, 65536.0
+    left = np.ascontiguousarray(tiny_pair["left"][:30, :40])
+    right = np.ascontiguousarray(tiny_pair["right"][:30, :40])
+    o = oracle.Oracle(left, right, gf_radius=2, lam=lam, disp_max=15.0)
+    rng = np.random.default_rng(8)
+    lab = _random_state(o, rng)
+    cost = rng.uniform(0.0, 3.0, size=(o.H, o.W))
+    E, Eq = o.energy_of(lab, cost)
+    H, W = o.H, o.W
+    both = 0.0
+    q = int(np.rint(S * cost).astype(np.int64).sum())
+    for y in range(H):
+        for x in range(W):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    qx, qy = x + dx, y + dy
+                    if (dx, dy) == (0, 0) or not (0 <= qx < W and 0 <= qy < H):
+                        continue
+                    if (dx, dy) in _FWD:
+                        v = o.psi(x, y, _FWD[(dx, dy)], lab[y, x], lab[qy, qx])
+                        q += int(np.rint(S * (lam * v)))
+                    else:
+                        v = o.psi(qx, qy, _FWD[(-dx, -dy)], lab[qy, qx], lab[y, x])
+                    both += v
+    assert E == pytest.approx(cost.sum() + lam * both / 2.0, rel=1e-12)
+    assert Eq == q
+
+
+def test_visit_candidates_follow_algorithms_1_and_2(tiny_pair):
+    """The candidates of one visit at the 5 px level (K_prop = 1, K_rand = 7): the propagation
+    proposal is the label f_r of a pixel r of the centre cell C_ij; the k-th perturbation
+    (k = 0 .. 6) moves the disparity at its pixel r by at most r_d 2^-k (then clamps it to the
+    range) and tilts the normal by at most asin(r_n 2^-k), where r_d = (d_max - d_min)/2 and
+    r_n = 1 are halved after every outer iteration (Algorithm 1) and after every perturbation
+    of the visit (Algorithm 2)."""
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **TINY_PARAMS)
+    H, W, s = o.H, o.W, 5
+    rng = np.random.default_rng(12)
+    lab = np.empty((H, W, 3), np.float32)
+    lab[..., 0] = rng.uniform(-0.2, 0.2, (H, W))
+    lab[..., 1] = rng.uniform(-0.2, 0.2, (H, W))
+    v, u = np.mgrid[0:H, 0:W]
+    lab[..., 2] = rng.uniform(2.0, 13.0, (H, W)) - lab[..., 0] * u - lab[..., 1] * v
+    where = {tuple(lab[y, x]): (x, y) for y in range(H) for x in range(W)}
+    assert len(where) == H * W
+    for it in (0, 2):
+        rd0, rn0 = 7.5 * 2.0 ** -it, 2.0 ** -it
+        for (ci, cj) in [(3, 4), (0, 0), (19, 14), (10, 7), (6, 13)]:
+            _, cell = oracle.region_of(H, W, s, ci, cj)
+            cx0, cy0, cw, ch = cell
+            cands = o.visit_candidates(lab, it, 0, ci, cj).astype(np.float64)
+            assert cands.shape == (8, 3)
+            x, y = where[tuple(np.float32(cands[0]))]
+            assert cx0 <= x < cx0 + cw and cy0 <= y < cy0 + ch
+            for k in range(7):
+                st = oracle.proposal_stream(TINY_PARAMS["seed"], it, 0, ci, cj, 1 + k)
+                f = oracle.propose(lab, st, cell, 0, 0.0, 0.0, 0.0, 15.0)   # the same stream's pixel r
+                x, y = where[tuple(f)]
+                f, b = f.astype(np.float64), cands[1 + k]
+                rd, rn = rd0 * 2.0 ** -k, rn0 * 2.0 ** -k
+                d0 = f[0] * x + f[1] * y + f[2]
+                d1 = b[0] * x + b[1] * y + b[2]
+                lo, hi = min(max(d0 - rd, 0.0), 15.0), min(max(d0 + rd, 0.0), 15.0)
+                assert lo - 1e-3 <= d1 <= hi + 1e-3, (it, ci, cj, k)
+                n0 = np.array([-f[0], -f[1], 1.0]); n0 /= np.linalg.norm(n0)
+                n1 = np.array([-b[0], -b[1], 1.0]); n1 /= np.linalg.norm(n1)
+                assert np.arccos(np.clip(abs(n0 @ n1), -1, 1)) <= np.arcsin(min(rn, 1.0)) + 1e-4
+
+
+def test_ransac_refines_by_least_squares_on_inliers():
+    """LO-RANSAC (Algorithm 2, RANSAC proposal; the least-squares refinement on the inliers
+    within 1 px): 60 % of the cell's disparities lie on a plane with Gaussian noise of 0.2 px,
+    20 % sit 2.5 px above it (no plane's 1 px band holds both groups) and 20 % 5-20 px off.  The
+    refined plane is the least-squares fit of the noisy inliers: slopes within 6e-3 and the
+    disparity at the cell centre within 0.06 px of the true plane in every trial, far closer
+    than a plane through three noisy points, and unbiased by the points at 2.5 px."""
+    rng = np.random.default_rng(6)
+    H, W = 40, 60
+    a, b, c = 0.125, -0.0625, 17.5
+    lab = _plane_labels(H, W, a, b, c)
+    kind = rng.random((H, W))
+    off = np.where(kind < 0.6, rng.normal(0.0, 0.2, (H, W)),
+                   np.where(kind < 0.8, 2.5 + rng.normal(0.0, 0.05, (H, W)), rng.uniform(5, 20, (H, W))))
+    lab[..., 2] = lab[..., 2] + off.astype(np.float32)
+    cell = (25, 10, 25, 25)
+    uc, vc = 25 + 12, 10 + 12
+    for k in range(20):
+        al = oracle.propose_ransac(lab, oracle.proposal_stream(9, 0, 2, 1, 1, k), cell).astype(np.float64)
+        assert abs(al[0] - a) <= 6e-3 and abs(al[1] - b) <= 6e-3, al
+        assert abs((al[0] * uc + al[1] * vc + al[2]) - (a * uc + b * vc + c)) <= 0.06, al
+
+
+def test_rounding_above_b_plus_c_is_lowered():
+    """Lemma 1 makes psi(f_p, f_q) <= psi(f_p, alpha) + psi(alpha, f_q), but after rounding
+    Q(A) can exceed Q(B) + Q(C) by one unit.  For fronto-parallel labels d1 < d_alpha < d2 the
+    real terms are exactly additive; picking the gaps so the rounding goes up for A and down
+    for B and C, the pair's A is lowered to B + C: the pair is counted as lowered and its edge
+    capacity is 0, never negative."""
+    img = np.full((8, 8, 3), 100, np.uint8)
+    o = oracle.Oracle(img, img, gf_radius=1)
+    S = 65536.0
+    rng = np.random.default_rng(10)
+    lab = np.zeros((8, 8, 3), np.float32)
+    for _ in range(1000):
+        d1 = np.float32(5.0)
+        da = np.float32(d1 + rng.uniform(0.01, 0.2))
+        d2 = np.float32(da + rng.uniform(0.01, 0.2))
+        fp, fa, fq = (np.float32([0, 0, d]) for d in (d1, da, d2))
+        A = np.rint(S * o.psi(3, 3, 0, fp, fq))
+        B = np.rint(S * o.psi(3, 3, 0, fp, fa))
+        C = np.rint(S * o.psi(3, 3, 0, fa, fq))
+        if A > B + C:
+            break
+    else:
+        pytest.fail("no rounding case found")
+    lab[3, 3], lab[3, 4] = fp, fq
+    g = o.build_graph(3, 3, 2, 1, fa, lab, np.zeros((8, 8)), np.zeros((1, 2)))
+    assert g["nclamp"] == 1 and g["clamp_mask"][0, 0] == 1
+    assert g["ncap"][0, 0, 0] == 0
+    assert (g["ncap"] >= 0).all() and (g["tcap"] >= 0).all()
