@@ -61,6 +61,9 @@ MUTANTS = [
     ("region one cell short on the left", "int x0 = imax(0, (ci - 1) * s), x1 = imin(W, (ci + 2) * s);",
      "int x0 = imax(0, ci * s), x1 = imin(W, (ci + 2) * s);"),
     ("switched pixels keep their old cost", "            c->cost[p] = phiA[i];\n", ""),
+    ("map candidates drawn before the RANSAC ones",
+     "if (t >= kp && t < kp + kr) {\n            lo_propose_ransac",
+     "if (t >= kp + kc && t < kp + kc + kr) {\n            lo_propose_ransac"),
 ]
 
 

@@ -800,3 +800,35 @@ def test_rounding_above_b_plus_c_is_lowered():
     assert g["nclamp"] == 1 and g["clamp_mask"][0, 0] == 1
     assert g["ncap"][0, 0, 0] == 0
     assert (g["ncap"] >= 0).all() and (g["tcap"] >= 0).all()
+
+
+def test_visit_order_propagation_ransac_map_perturbation(tiny_pair):
+    """Order of the proposals in a visit: K_prop propagation, K_RANS RANSAC, k_cnn map
+    candidates, then K_rand perturbations with the size halved after each (Algorithm 2 with
+    the RANSAC and map proposals in the candidate slots).  The visit's draw equals the
+    single-proposal functions composed in that order, each with proposal index t's stream."""
+    kw = dict(TINY_PARAMS, k_prop=(2,), k_rans=(1,), k_cnn=(2,), k_rand=(3,))
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **kw)
+    rng = np.random.default_rng(14)
+    lab = _random_state(o, rng)
+    prop = _random_state(o, rng)
+    o.set_proposals(prop)
+    H, W, s = o.H, o.W, 5
+    for it in (0, 1):
+        for (ci, cj) in [(2, 3), (19, 14), (7, 0)]:
+            _, cell = oracle.region_of(H, W, s, ci, cj)
+            got = o.visit_candidates(lab, it, 0, ci, cj)
+            rd, rn = 7.5 * 2.0 ** -it, 2.0 ** -it
+            want = []
+            for t in range(8):
+                st = oracle.proposal_stream(TINY_PARAMS["seed"], it, 0, ci, cj, t)
+                if t < 2:
+                    want.append(oracle.propose(lab, st, cell, 0, 0.0, 0.0, 0.0, 15.0))
+                elif t < 3:
+                    want.append(oracle.propose_ransac(lab, st, cell))
+                elif t < 5:
+                    want.append(oracle.propose_map(prop, st, cell))
+                else:
+                    want.append(oracle.propose(lab, st, cell, 1, rd, rn, 0.0, 15.0))
+                    rd, rn = rd * 0.5, rn * 0.5
+            assert (got == np.array(want)).all(), (it, ci, cj)
