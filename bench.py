@@ -195,8 +195,13 @@ def launches_and_work(H, W, p):
 
 
 def kernel_source_sha():
-    with open(os.path.join(ROOT, "paper_1603_08328_gb300", "csrc", "lem_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """SHA-256 of the expansion kernel's sources: lem_kernels.cu followed by the internal
+    header it includes."""
+    h = hashlib.sha256()
+    for name in ("lem_kernels.cu", "lem_internal.h"):
+        with open(os.path.join(ROOT, "paper_1603_08328_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def traffic_from_profile(kernel):
