@@ -10,7 +10,8 @@ Layouts: activations are (H, W, C); weights of a layer are (3, 3, Cin, Cout)
 (kernel row, kernel column, input channel, output channel); y = x * w + bias
 with y[v, u, o] = sum_{i,j,c} x[v + i - 1, u + j - 1, c] w[i, j, c, o].
 
-Parity pins: tests/test_oracle_cnn.py (finite differences, scipy correlation).
+Parity pins: tests/test_oracle_cnn.py (finite differences, scipy correlation, closed
+forms of the Adam update).
 """
 from __future__ import annotations
 
@@ -116,6 +117,20 @@ def l1_loss(out, target, scale):
     n = out.shape[0] * out.shape[1]
     loss = float((np.abs(diff) * scale).sum() / n)
     return loss, np.sign(diff) * scale / n
+
+
+def adam_step(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, "Adam: a method for stochastic optimization",
+    ICLR 2015) of the flat parameters w with gradient g, first and second moments m, v
+    and 1-based step count `step`: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+    w <- w - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+    Returns (w, m, v); the inputs are not changed."""
+    w, g = np.asarray(w, np.float64), np.asarray(g, np.float64)
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** step)
+    vh = v / (1.0 - b2 ** step)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
 def quarter_features(left, right, lab, dmax):

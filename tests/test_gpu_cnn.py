@@ -160,6 +160,38 @@ def test_training_reduces_the_loss(torch_cuda):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_adam_steps_follow_the_update_rule(torch_cuda):
+    """Two Adam steps of lem_cnn_train_step against oracle/cnn.adam_step (Kingma and Ba 2015)
+    fed with the library's own gradients of the same batch, taken by lem_cnn_gradients just
+    before each step.  The weight gradients are summed with FP32 atomics, so the two gradient
+    passes agree to ~1e-6 relative, not bit for bit; where |g| > 1e-5 the update
+    lr m^ / (sqrt(v^) + eps) moves by far less than 1e-3 lr under such noise, and the FP32
+    update and storage of the parameters add ~1e-7 of their size."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet
+    net = ProposalNet(seed=5)
+    rng = np.random.default_rng(9)
+    n, H4, W4 = 2, 12, 16
+    x = torch.from_numpy(rng.uniform(0.0, 1.0, size=(n, H4, W4, 7)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.uniform(-0.5, 1.0, size=(n, H4, W4, 3)).astype(np.float32)).cuda()
+    lr = 1e-3
+    p = net.get_params().astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    ok = np.ones(p.shape, bool)
+    for step in (1, 2):
+        _, g = net.gradients(x, t)
+        ok &= np.abs(g) > 1e-5
+        want, m, v = cnn.adam_step(p, g, m, v, step, lr)
+        net.train_step(x, t, lr)
+        got = net.get_params().astype(np.float64)
+        err = np.abs(got - want)[ok]
+        print(f"Adam step {step}: {ok.sum()} of {ok.size} parameters compared, max error {err.max():.2e}")
+        assert ok.sum() > 0.5 * ok.size
+        assert err.max() <= 1e-3 * lr + 1e-6 * np.abs(want).max()
+        p = got
+
+
 def test_features_and_targets_match_oracle(torch_cuda, tiny_pair):
     torch = torch_cuda
     from paper_1603_08328_gb300.lem import Stereo

@@ -139,3 +139,28 @@ def test_targets_clamp_steep_slopes():
     assert t[0, 0, 1] == 1.0 and t[0, 0, 2] == -0.5
     # d = 3 u - 0.5 v averaged over the block: 3 * 1.5 - 0.5 * 1.5 = 3.75, over dmax = 10
     assert t[0, 0, 0] == pytest.approx(0.375)
+
+
+def test_adam_closed_forms():
+    """Adam (Kingma and Ba 2015): on the first step the bias-corrected moments are g and g^2,
+    so every parameter moves by lr g / (|g| + eps), i.e. by lr against the sign of its
+    gradient; a second step with the same gradient moves it by lr again; a zero gradient
+    leaves it in place; and the moments follow their recurrences."""
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=50)
+    g = rng.normal(size=50)
+    g[:5] = 0.0
+    z = np.zeros(50)
+    w1, m1, v1 = cnn.adam_step(w, g, z, z, 1, 1e-3)
+    assert np.allclose(w1 - w, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert (w1[:5] == w[:5]).all()
+    assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+    w2, m2, v2 = cnn.adam_step(w1, g, m1, v1, 2, 1e-3)
+    nz = g != 0
+    assert np.allclose((w2 - w1)[nz], -1e-3 * np.sign(g[nz]), rtol=1e-6, atol=0)
+    assert np.allclose(m2, 0.19 * g) and np.allclose(v2, (0.001 * 0.999 + 0.001) * g * g)
+    # a gradient that changes sign: the first moment carries the old direction
+    w3, _, _ = cnn.adam_step(w1, -g, m1, v1, 2, 1e-3)
+    mh = (0.9 * 0.1 * g - 0.1 * g) / (1 - 0.81)
+    vh = (0.999 * 0.001 + 0.001) * g * g / (1 - 0.999 ** 2)
+    assert np.allclose(w3 - w1, -1e-3 * mh / (np.sqrt(vh) + 1e-8), rtol=1e-9, atol=1e-15)
