@@ -135,6 +135,10 @@ PY_MUTANTS = [
      "fv = min(max((vv - 2.0) / 4.0, 0.0), H4 - 1.0)", "test_oracle_cnn.py"),
     ("target slopes not clamped", "cnn.py", "t[..., 1:] = np.clip(t[..., 1:], -1.0, 1.0)", "pass",
      "test_oracle_cnn.py"),
+    ("Adam without the bias correction of the first moment", "cnn.py", "mh = m / (1.0 - b1 ** step)", "mh = m",
+     "test_oracle_cnn.py"),
+    ("Adam with eps inside the square root", "cnn.py", "(np.sqrt(vh) + eps)", "np.sqrt(vh + eps)",
+     "test_oracle_cnn.py"),
     ("mirrored plane offset with the wrong sign", "postproc.py", "out = np.stack([-a, b, c + a * (W - 1)], axis=-1)",
      "out = np.stack([-a, b, c - a * (W - 1)], axis=-1)", "test_oracle_post.py"),
     ("consistency match on the wrong side", "postproc.py", "q = np.rint(u - dL)", "q = np.rint(u + dL)",
