@@ -61,6 +61,13 @@ MUTANTS = [
     ("region one cell short on the left", "int x0 = imax(0, (ci - 1) * s), x1 = imin(W, (ci + 2) * s);",
      "int x0 = imax(0, ci * s), x1 = imin(W, (ci + 2) * s);"),
     ("switched pixels keep their old cost", "            c->cost[p] = phiA[i];\n", ""),
+    ("region scheme without the product of means in the covariance", "cov[ch] = s[1 + ch] / n - mu[ch] * mr;",
+     "cov[ch] = s[1 + ch] / n;"),
+    ("output window means normalised by the unclipped window", "double n = (double)(kx1 - kx0 + 1) * (ky1 - ky0 + 1);",
+     "double n = (double)(2 * r + 1) * (2 * r + 1);"),
+    ("Dinic without the reverse residual", "                g.cap[stack_e[k] ^ 1] += b;\n", ""),
+    ("graph edge p->q built as q->p", "if (ncap[i * 4 + d] > 0) fg_add(g, i, jy * w + jx, ncap[i * 4 + d]);",
+     "if (ncap[i * 4 + d] > 0) fg_add(g, jy * w + jx, i, ncap[i * 4 + d]);"),
     ("map candidates drawn before the RANSAC ones",
      "if (t >= kp && t < kp + kr) {\n            lo_propose_ransac",
      "if (t >= kp + kc && t < kp + kc + kr) {\n            lo_propose_ransac"),
