@@ -68,6 +68,15 @@ MUTANTS = [
     ("Dinic without the reverse residual", "                g.cap[stack_e[k] ^ 1] += b;\n", ""),
     ("graph edge p->q built as q->p", "if (ncap[i * 4 + d] > 0) fg_add(g, i, jy * w + jx, ncap[i * 4 + d]);",
      "if (ncap[i * 4 + d] > 0) fg_add(g, jy * w + jx, i, ncap[i * 4 + d]);"),
+    ("initial disparities ignore d_min", "double z0 = dmin + (dmax - dmin) * sm_u01(&st);",
+     "double z0 = dmax * sm_u01(&st);"),
+    ("perturbed disparity clamped at 0 instead of d_min", "    if (dp < dmin) dp = dmin;\n",
+     "    if (dp < 0.0) dp = 0.0;\n"),
+    ("outer perturbation size d_max / 2", "*rd = 0.5 * (c->p.disp_max - c->p.disp_min) * f;",
+     "*rd = 0.5 * c->p.disp_max * f;"),
+    ("x-gradient without the 1/2", "o[3] = 0.5 * (g[xp] - g[xm]);", "o[3] = g[xp] - g[xm];"),
+    ("gray weights of R and B swapped", "g[x] = 0.299 * c[0] + 0.587 * c[1] + 0.114 * c[2];",
+     "g[x] = 0.114 * c[0] + 0.587 * c[1] + 0.299 * c[2];"),
     ("map candidates drawn before the RANSAC ones",
      "if (t >= kp && t < kp + kr) {\n            lo_propose_ransac",
      "if (t >= kp + kc && t < kp + kc + kr) {\n            lo_propose_ransac"),
@@ -98,12 +107,16 @@ def _compile(src_text, d):
 def c_mutant_runs(tmp_path_factory):
     """Every planted copy (and one unmodified copy, name None) compiled and checked
     against the pins, several at a time."""
+    import tempfile
     from concurrent.futures import ThreadPoolExecutor
     src = open(SRC).read()
+    # one base directory made here; the workers make theirs with tempfile, which is
+    # safe across threads (pytest's factory is not)
+    base = str(tmp_path_factory.mktemp("mutants"))
 
     def run(case):
         name, old, new = case
-        d = str(tmp_path_factory.mktemp("mutant"))
+        d = tempfile.mkdtemp(dir=base)
         if name is None:
             return name, _pins_against(_compile(src, d), first_failure=False)
         if src.count(old) < 1:

@@ -832,3 +832,43 @@ def test_visit_order_propagation_ransac_map_perturbation(tiny_pair):
                     want.append(oracle.propose(lab, st, cell, 1, rd, rn, 0.0, 15.0))
                     rd, rn = rd * 0.5, rn * 0.5
             assert (got == np.array(want)).all(), (it, ci, cj)
+
+
+def test_disparity_range_with_a_nonzero_minimum(tiny_pair):
+    """Disparity range [20, 60] (reading R20: the range is [d_min, d_max], r_d starts at
+    (d_max - d_min)/2 = 20): the initial planes pass through disparities drawn over the whole
+    range (Sec. 3.4), and every perturbed disparity stays within r_d 2^-k of its pixel's
+    disparity and inside the range (R10), reaching d_min when labels sit just above it."""
+    dmin, dmax = 20.0, 60.0
+    d = []
+    for k in range(3000):
+        u, v = k % 96, k // 96
+        f = oracle.init_label(5, 96, u, v, dmin, dmax).astype(np.float64)
+        d.append(f[0] * u + f[1] * v + f[2])
+    d = np.array(d)
+    assert d.min() >= dmin - 1e-3 and d.max() <= dmax + 1e-3
+    assert d.min() < dmin + 1.0 and d.max() > dmax - 1.0
+    o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], **dict(TINY_PARAMS, disp_min=dmin, disp_max=dmax))
+    H, W, s = o.H, o.W, 5
+    rng = np.random.default_rng(13)
+    lab = np.empty((H, W, 3), np.float32)
+    lab[..., 0] = rng.uniform(-0.05, 0.05, (H, W))
+    lab[..., 1] = rng.uniform(-0.05, 0.05, (H, W))
+    v, u = np.mgrid[0:H, 0:W]
+    lab[..., 2] = rng.uniform(20.5, 22.0, (H, W)) - lab[..., 0] * u - lab[..., 1] * v
+    where = {tuple(lab[y, x]): (x, y) for y in range(H) for x in range(W)}
+    at_min = 0
+    for (ci, cj) in [(3, 4), (0, 0), (19, 14), (10, 7), (6, 13), (12, 2)]:
+        _, cell = oracle.region_of(H, W, s, ci, cj)
+        cands = o.visit_candidates(lab, 0, 0, ci, cj).astype(np.float64)
+        for k in range(7):
+            st = oracle.proposal_stream(TINY_PARAMS["seed"], 0, 0, ci, cj, 1 + k)
+            f = oracle.propose(lab, st, cell, 0, 0.0, 0.0, dmin, dmax)
+            x, y = where[tuple(f)]
+            f, b = f.astype(np.float64), cands[1 + k]
+            rd = 0.5 * (dmax - dmin) * 2.0 ** -k
+            d0 = f[0] * x + f[1] * y + f[2]
+            d1 = b[0] * x + b[1] * y + b[2]
+            assert max(d0 - rd, dmin) - 1e-3 <= d1 <= min(d0 + rd, dmax) + 1e-3, (ci, cj, k, d0, d1)
+            at_min += abs(d1 - dmin) < 1e-3
+    assert at_min > 0
