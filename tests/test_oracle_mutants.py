@@ -77,6 +77,11 @@ MUTANTS = [
     ("x-gradient without the 1/2", "o[3] = 0.5 * (g[xp] - g[xm]);", "o[3] = g[xp] - g[xm];"),
     ("gray weights of R and B swapped", "g[x] = 0.299 * c[0] + 0.587 * c[1] + 0.114 * c[2];",
      "g[x] = 0.114 * c[0] + 0.587 * c[1] + 0.299 * c[2];"),
+    ("pair term C - A credited as B - A", "U1[i] += C - A;", "U1[i] += B - A;"),
+    ("pair weight read at the wrong node", "int bu = fwd ? pu : qu, bv = fwd ? pv : qv;", "int bu = pu, bv = pv;"),
+    ("fixed neighbour folded with alpha on both sides",
+     "double pa = lam * wv * fmin(lo_psibar(pu, pv, qu, qv, alpha, fq), c->p.tau_dis);",
+     "double pa = lam * wv * fmin(lo_psibar(pu, pv, qu, qv, alpha, alpha), c->p.tau_dis);"),
     ("map candidates drawn before the RANSAC ones",
      "if (t >= kp && t < kp + kr) {\n            lo_propose_ransac",
      "if (t >= kp + kc && t < kp + kc + kr) {\n            lo_propose_ransac"),

@@ -260,24 +260,40 @@ def _random_state(o, rng, spread=0.6):
     return lab
 
 
-def test_move_graph_encodes_the_energy_exactly(tiny_pair):
+def _smooth_state(o, rng):
+    """Labels close to one plane: neighbouring pairs stay below the truncation tau_dis, so
+    A, B and C of a pair differ (the random state truncates nearly every pair)."""
+    H, W = o.H, o.W
+    lab = np.empty((H, W, 3), np.float32)
+    lab[..., 0] = 0.05 + rng.normal(0, 0.002, (H, W))
+    lab[..., 1] = -0.03 + rng.normal(0, 0.002, (H, W))
+    lab[..., 2] = 6.0 + rng.normal(0, 0.03, (H, W))
+    return lab
+
+
+@pytest.mark.parametrize("labels", ["rough", "smooth"])
+def test_move_graph_encodes_the_energy_exactly(tiny_pair, labels):
     """|R| = 16: for all 2^16 moves x, const + cut(x) equals the quantised energy of f (+) x summed
     term by term from the definitions (phi by definition, psi of Eq. smooth_phi), except one unit
-    less for each pair that was lowered to B + C (submodularity after rounding) and stays at (0,0)."""
+    less for each pair that was lowered to B + C (submodularity after rounding) and stays at (0,0).
+    Rough labels truncate nearly every pair at tau_dis; smooth ones keep them below it, where the
+    pair's A, B and C differ and the edge p->q carries B + C - A > 0."""
     o = oracle.Oracle(tiny_pair["left"], tiny_pair["right"], gf_radius=2)
     S, lam = 65536.0, o.p["lam"]
     rng = np.random.default_rng(9)
-    lab = _random_state(o, rng)
+    lab = _random_state(o, rng) if labels == "rough" else _smooth_state(o, rng)
     x0, y0, w, h = 34, 24, 4, 4
     cost = np.zeros((o.H, o.W))
     for y in range(y0, y0 + h):
         for x in range(x0, x0 + w):
             cost[y, x] = o.phi_def(lab[y, x], x, y)
     alpha = lab[y0 + 1, x0 + 1].copy()
-    alpha[2] += 0.3
-    alpha[0] += 0.01
+    alpha[2] += 0.3 if labels == "rough" else 0.1
+    alpha[0] += 0.01 if labels == "rough" else 0.002
     phiA = np.array([[o.phi_def(alpha, x0 + x, y0 + y) for x in range(w)] for y in range(h)])
     g = o.build_graph(x0, y0, w, h, alpha, lab, cost, phiA)
+    if labels == "smooth":
+        assert (g["ncap"] > 0).sum() >= 30      # untruncated pairs with an edge of their own
     tcap, ncap = g["tcap"].reshape(-1, 2).astype(np.int64), g["ncap"].reshape(-1, 4).astype(np.int64)
     Q = lambda z: int(np.rint(S * z))
     fdx, fdy = [1, -1, 0, 1], [0, 1, 1, 1]
