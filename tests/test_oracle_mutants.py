@@ -170,6 +170,15 @@ PY_MUTANTS = [
      "test_oracle_post.py"),
     ("filling from the foreground", "postproc.py", "out[y, x] = min(cands)", "out[y, x] = max(cands)",
      "test_oracle_post.py"),
+    ("weighted-median window one row short", "postproc.py",
+     "y0, y1 = max(0, y - radius), min(H, y + radius + 1)", "y0, y1 = max(0, y - radius), min(H, y + radius)",
+     "test_oracle_post.py"),
+    ("consistency match rounded down", "postproc.py", "q = np.rint(u - dL)", "q = np.floor(u - dL)",
+     "test_oracle_post.py"),
+    ("filling searches to the left only", "postproc.py", "for step in (-1, 1):", "for step in (-1,):",
+     "test_oracle_post.py"),
+    ("L1 loss not averaged over pixels", "cnn.py", "loss = float((np.abs(diff) * scale).sum() / n)",
+     "loss = float((np.abs(diff) * scale).sum())", "test_oracle_cnn.py"),
     ("weighted median one element too far", "postproc.py", "k = int(np.searchsorted(cw, 0.5 * cw[-1]))",
      "k = int(np.searchsorted(cw, 0.5 * cw[-1], side='right'))", "test_oracle_post.py"),
     # (a mistake in the band sizes would leave the gloo ranks waiting for each other, so

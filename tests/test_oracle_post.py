@@ -85,3 +85,26 @@ def test_weighted_median_follows_the_colour_weights():
     assert pp.is_weighted_median(out[2, 2], disp.ravel(), w.ravel())
     # the two bright pixels (values 0 and 12) hold almost all the weight: the lower wins
     assert out[2, 2] == 0.0
+
+
+@pytest.mark.parametrize("edge", ["last row", "last column", "first row", "first column"])
+def test_weighted_median_window_reaches_the_radius(edge):
+    """Rule 3's window holds r rows and columns on every side of the pixel ((2r + 1)^2,
+    r = 2 here).  With equal weights (one colour) and 25 values (12 zeros, 8 twos and five
+    ones on one edge of the window) the lower median is 1; without that edge it would be 0."""
+    H = W = 12
+    r, y, x = 2, 5, 5
+    left = np.full((H, W, 3), 80, np.uint8)
+    valid = np.ones((H, W), bool)
+    valid[y, x] = False
+    win = np.full((5, 5), 2.0)
+    sl = {"last row": np.s_[4, :], "last column": np.s_[:, 4], "first row": np.s_[0, :],
+          "first column": np.s_[:, 0]}[edge]
+    win[sl] = 1.0
+    rest = np.argwhere(win == 2.0)[:12]
+    win[rest[:, 0], rest[:, 1]] = 0.0
+    disp = np.full((H, W), 9.0)
+    disp[y - r:y + r + 1, x - r:x + r + 1] = win
+    out = pp.weighted_median(disp, valid, left, radius=r, gamma=10.0)
+    assert out[y, x] == 1.0
+    assert (out[valid] == disp[valid]).all()
