@@ -191,23 +191,54 @@ PY_MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("name,module,old,new,pins", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
-def test_python_pins_catch_planted_mistake(tmp_path, name, module, old, new, pins):
+def _python_mutant(d, module, old, new, pins):
+    """Copies the oracle package into directory d with one mistake planted in `module` and
+    runs the pin file `pins` against the copy in a child process; (exit code, output end),
+    or (None, reason) when the mutation site is missing."""
     import shutil
-    pkg = tmp_path / "oracle"
-    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
-                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
-    path = pkg / module
-    text = path.read_text()
-    assert text.count(old) == 1, f"mutation site not found: {old}"
-    path.write_text(text.replace(old, new))
-    # the child starts in tmp_path, so `import oracle` finds the planted copy first
-    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    pkg = os.path.join(d, "oracle")
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg, ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    path = os.path.join(pkg, module)
+    with open(path) as f:
+        text = f.read()
+    if text.count(old) != 1:
+        return None, f"mutation site not found once: {old}"
+    with open(path, "w") as f:
+        f.write(text.replace(old, new))
+    # the child starts in d, so `import oracle` finds the planted copy first
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([d, ROOT]), OMP_NUM_THREADS="2")
     env.pop("LEM_ORACLE_LIB", None)
     out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins), "-x", "-q",
-                          "-p", "no:cacheprovider", "-m", "not gpu"], cwd=str(tmp_path), env=env,
+                          "-p", "no:cacheprovider", "-m", "not gpu"], cwd=d, env=env,
                          capture_output=True, text=True, timeout=600)
-    assert out.returncode != 0, f"no pin caught the mistake '{name}':\n{out.stdout[-1500:]}"
+    return out.returncode, out.stdout[-1500:]
+
+
+@pytest.fixture(scope="module")
+def py_mutant_runs(tmp_path_factory):
+    """The planted copies of the network and post-processing references, several at a time
+    (the stripe-decomposed driver's start gloo ranks and run one at a time in their test)."""
+    import tempfile
+    from concurrent.futures import ThreadPoolExecutor
+    base = str(tmp_path_factory.mktemp("py_mutants"))
+    cases = [m for m in PY_MUTANTS if m[1] != "stripes.py"]
+
+    def run(case):
+        name, module, old, new, pins = case
+        return name, _python_mutant(tempfile.mkdtemp(dir=base), module, old, new, pins)
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as pool:
+        return dict(pool.map(run, cases))
+
+
+@pytest.mark.parametrize("name,module,old,new,pins", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_python_pins_catch_planted_mistake(py_mutant_runs, tmp_path, name, module, old, new, pins):
+    if module == "stripes.py":
+        rc, tail = _python_mutant(str(tmp_path), module, old, new, pins)
+    else:
+        rc, tail = py_mutant_runs[name]
+    assert rc is not None, tail
+    assert rc != 0, f"no pin caught the mistake '{name}':\n{tail}"
 
 
 def test_python_unmodified_copy_passes(tmp_path):
