@@ -30,6 +30,12 @@ MUTANTS = [
     ("smoothness term not truncated", "fmin(lo_psibar(pu, pv, qu, qv, fp, fq), c->p.tau_dis)",
      "lo_psibar(pu, pv, qu, qv, fp, fq)"),
     ("cut side seeded from every node", "if (res_t[i] > 0) {", "if (res_t[i] >= 0) {"),
+    ("colour and gradient truncations swapped",
+     "return (1.0 - pa) * fmin(col, c->p.tau_col) + pa * fmin(gd, c->p.tau_grad);",
+     "return (1.0 - pa) * fmin(col, c->p.tau_grad) + pa * fmin(gd, c->p.tau_col);"),
+    ("colour distance L2 instead of L1", "        col += fabs(l[ch] - rv);", "        col += (l[ch] - rv) * (l[ch] - rv);"),
+    ("match clamped half a pixel inside the right border", "    if (up > W - 1) up = W - 1;\n",
+     "    if (up > W - 1) up = W - 1.5;\n"),
     ("sample covariance of the guide", "for (int i = 0; i < 9; i++) S[i] /= n;",
      "for (int i = 0; i < 9; i++) S[i] /= n - 1;"),
     ("regulariser added to a row instead of the diagonal", "S[4 * i] += c->p.gf_eps;", "S[i] += c->p.gf_eps;"),

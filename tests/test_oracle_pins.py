@@ -888,3 +888,48 @@ def test_disparity_range_with_a_nonzero_minimum(tiny_pair):
             assert max(d0 - rd, dmin) - 1e-3 <= d1 <= min(d0 + rd, dmax) + 1e-3, (ci, cj, k, d0, d1)
             at_min += abs(d1 - dmin) < 1e-3
     assert at_min > 0
+
+
+def test_rho_closed_forms_of_eq_photofunc():
+    """Eq. photofunc on constructed pairs, right(u) = left(u + D) + offset + k u (all three
+    channels): at the true disparity D the colour term is the L1 norm of the colour difference
+    and the gradient term the ramp's slope k (the gray ramp's central difference), each
+    truncated by its own threshold (tau_col = 10 on colour, tau_grad = 2 on gradient) and mixed
+    (1 - alpha) : alpha = 0.1 : 0.9.  A match outside the right image is clamped to its first
+    or last column (reading R6)."""
+    rng = np.random.default_rng(21)
+    H, W, D = 6, 40, 5
+    base = rng.integers(20, 120, size=(H, W + D, 3))
+    u_r = np.arange(W)[None, :, None]
+    left = np.ascontiguousarray(base[:, :W].astype(np.uint8))
+
+    def rho_at(offset, k):
+        right = np.ascontiguousarray((base[:, D:W + D] + np.array(offset) + k * u_r).astype(np.uint8))
+        o = oracle.Oracle(left, right, gf_radius=1, disp_max=20.0)
+        lab = np.float32([0.0, 0.0, D])
+        return [(u, o.rho(lab, u, 3)) for u in range(D + 1, W - 1)], o
+
+    for (u, r) in rho_at((2, -1, 1), 0)[0]:
+        assert r == pytest.approx(0.1 * 4.0, abs=1e-12)
+    for (u, r) in rho_at((10, 10, 10), 0)[0]:
+        assert r == pytest.approx(0.1 * 10.0, abs=1e-12)
+    for (u, r) in rho_at((0, 0, 0), 1)[0]:
+        assert r == pytest.approx(0.1 * min(3.0 * (u - D), 10.0) + 0.9 * 1.0, abs=1e-12)
+    for (u, r) in rho_at((0, 0, 0), 3)[0]:
+        assert r == pytest.approx(0.1 * min(9.0 * (u - D), 10.0) + 0.9 * 2.0, abs=1e-12)
+    # clamping: a uniform left image; the right image equals it except in the columns next
+    # to its first and last ones, so a match clamped anywhere but onto the edge column has
+    # another cost
+    left = np.full((H, W, 3), 100, np.uint8)
+    right = left.copy()
+    right[:, 1] = 120
+    right[:, W - 2] = 120
+    o = oracle.Oracle(left, right, gf_radius=1, disp_max=20.0)
+    for u in (2, 17, 39):
+        at_first = o.rho(np.float32([0, 0, u]), u, 2)              # u' = 0
+        at_last = o.rho(np.float32([0, 0, u - (W - 1)]), u, 2)      # u' = W - 1
+        assert at_first != o.rho(np.float32([0, 0, u - 0.5]), u, 2)
+        assert at_last != o.rho(np.float32([0, 0, u - (W - 1.5)]), u, 2)
+        for extra in (0.5, 7.0):
+            assert o.rho(np.float32([0, 0, u + extra]), u, 2) == at_first
+            assert o.rho(np.float32([0, 0, u - (W - 1) - extra]), u, 2) == at_last
