@@ -36,6 +36,16 @@ MUTANTS = [
     ("colour distance L2 instead of L1", "        col += fabs(l[ch] - rv);", "        col += (l[ch] - rv) * (l[ch] - rv);"),
     ("match clamped half a pixel inside the right border", "    if (up > W - 1) up = W - 1;\n",
      "    if (up > W - 1) up = W - 1.5;\n"),
+    ("smoothness term evaluated at p on both sides",
+     "return fabs(disp_at(fp, pu, pv) - disp_at(fq, pu, pv)) + fabs(disp_at(fq, qu, qv) - disp_at(fp, qu, qv));",
+     "return fabs(disp_at(fp, pu, pv) - disp_at(fq, pu, pv)) + fabs(disp_at(fq, pu, pv) - disp_at(fp, pu, pv));"),
+    ("contrast weight inside the truncation", "    return wv * fmin(lo_psibar(pu, pv, qu, qv, fp, fq), c->p.tau_dis);",
+     "    return fmin(wv * lo_psibar(pu, pv, qu, qv, fp, fq), c->p.tau_dis);"),
+    ("contrast weight of the L2 colour distance",
+     "double l1 = fabs(lp[0] - lq[0]) + fabs(lp[1] - lq[1]) + fabs(lp[2] - lq[2]);",
+     "double l1 = sqrt((lp[0] - lq[0]) * (lp[0] - lq[0]) + (lp[1] - lq[1]) * (lp[1] - lq[1]) + "
+     "(lp[2] - lq[2]) * (lp[2] - lq[2]));"),
+    ("regulariser on the 0..255 scale", "S[4 * i] += c->p.gf_eps;", "S[4 * i] += c->p.gf_eps * 255.0;"),
     ("sample covariance of the guide", "for (int i = 0; i < 9; i++) S[i] /= n;",
      "for (int i = 0; i < 9; i++) S[i] /= n - 1;"),
     ("regulariser added to a row instead of the diagonal", "S[4 * i] += c->p.gf_eps;", "S[i] += c->p.gf_eps;"),
