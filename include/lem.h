@@ -331,22 +331,29 @@ int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float
 /* Largest n_regions of lem_mincut_batch_noalloc. */
 #define LEM_NOALLOC_MAX_REGIONS 4096
 
-/* lem_mincut_batch (Eq. expansion, Sec. 3.3) for callers that cannot allocate
- * device memory when they cut: code that runs inside a preallocated memory
- * arena, a host thread that must not call cudaMalloc/cudaFree because those
- * synchronise the device, or an embedding that forbids growing the device
- * heap.  The paper has no counterpart for the allocation-free form; the cut is
- * the same.
+/* The cut of lem_mincut_batch for callers that cannot allocate device memory
+ * when they cut: code that runs inside a preallocated memory arena, a host
+ * thread that must not call cudaMalloc/cudaFree because those synchronise the
+ * device, or an embedding that forbids growing the device heap.  The paper has
+ * no counterpart for the allocation-free form; the cut is the same.
  *
  * It needs no handle and allocates nothing: the scratch the batch min-cut
  * keeps per call (region descriptors, packed offsets, work counters) is a
  * fixed array of about 96 KiB in the library's device memory, which every GPU
  * that loads the library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with that
- * device current); make that first call before any stream capture.  Every call
- * shares the array and overwrites it (the counters are cleared first), so
- * calls whose work overlaps on the GPU race: order them on one stream, or
- * synchronise between them.
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  A cudaDeviceReset unloads the array, so
+ * this entry point must not be called after a device reset in the same
+ * process.  Every call shares the array and overwrites it (the counters are
+ * cleared first), so calls whose work overlaps on the GPU race: order them on
+ * one stream, or synchronise between them.
+ *
+ * `regions` is copied to the device with cudaMemcpyAsync on `stream`.  From
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister) that copy is
+ * asynchronous; from pageable memory the call may return only once the copy
+ * has been staged, which can wait for earlier work on the stream.  Callers
+ * that must not block pass page-locked `regions`.
  *   regions     : host, n_regions <= LEM_NOALLOC_MAX_REGIONS entries, each
  *                 region at most LEM_MAX_REGION_NODES nodes; x0/y0 are ignored
  *   tcaps/ncaps : device int32, layout of lem_pairwise_batch

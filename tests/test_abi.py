@@ -120,22 +120,15 @@ def test_parameter_checks_of_the_later_options(L):
         assert not h.value
 
 
-def test_readme_c_example_compiles_and_links(L):
-    """The C example of README.md is valid C99 against include/lem.h and links with
-    the in-tree liblem.so (compiled and linked only: running it needs a GPU)."""
+def test_c_example_compiles_and_links(L):
+    """tests/c_example.c (the usage example the README shows) is valid C99 against
+    include/lem.h and links with the in-tree liblem.so (compiled and linked only:
+    running it needs a GPU)."""
     import subprocess
     import tempfile
-    readme = open(os.path.join(ROOT, "README.md")).read()
-    block = re.search(r"```c\n(.*?)```", readme, flags=re.S).group(1)
-    body = "\n".join(line for line in block.splitlines() if not line.startswith("#include"))
-    code = ('#include <stdint.h>\n#include <stdio.h>\n#include "lem.h"\n'
-            "int example(const uint8_t *left_rgb, const uint8_t *right_rgb, int H, int W, float *disparity_host);\n"
-            "int example(const uint8_t *left_rgb, const uint8_t *right_rgb, int H, int W, float *disparity_host) {\n"
-            + body + "\n    return 0;\n}\nint main(void) { return 0; }\n")
+    src = os.path.join(ROOT, "tests", "c_example.c")
     libdir = os.path.dirname(L.LIB_PATH)
     with tempfile.TemporaryDirectory() as d:
-        src = os.path.join(d, "example.c")
-        open(src, "w").write(code)
         out = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I" + os.path.join(ROOT, "include"),
                               src, "-o", os.path.join(d, "example"), "-L" + libdir, "-llem",
                               "-Wl,-rpath," + libdir], capture_output=True, text=True)

@@ -2,8 +2,11 @@
 
 Such callers (code inside a preallocated memory arena, a host thread that must not
 call cudaMalloc because it synchronises the device) get the same cut from a fixed
-scratch array in the library's device memory.  This file is collected last so a run
-that stops at the first failure has already run every other test.
+scratch array in the library's device memory.  The test checks the cut against
+lem_mincut_batch and, for one graph per call, against the oracle's Dinic max-flow,
+and that the second call leaves the device's free memory unchanged.  This file is
+collected last so a run that stops at the first failure has already run every
+other test.
 """
 import ctypes as C
 
@@ -31,6 +34,8 @@ def test_noalloc_mincut_equals_mincut_batch_on_two_calls_in_a_row():
     from paper_1603_08328_gb300 import lem
     from synth import workload_pair
 
+    import oracle
+
     pair = workload_pair("tiny_96x72", 0)
     ref = lem.Stereo(pair["left"], pair["right"], gf_radius=2, disp_max=15.0, n_levels=1, cell=(5,),
                      k_prop=(1,), k_rand=(7,))
@@ -48,16 +53,31 @@ def test_noalloc_mincut_equals_mincut_batch_on_two_calls_in_a_row():
         flow = torch.full((len(regions),), -1, dtype=torch.int64, device="cuda")
         st = torch.full((len(regions),), 99, dtype=torch.int32, device="cuda")
         p = ref.params
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = lem.lem_mincut_batch_noalloc(regions, C.c_void_p(tc.data_ptr()), C.c_void_p(nc.data_ptr()),
                                           C.c_void_p(take.data_ptr()), C.c_void_p(flow.data_ptr()),
                                           C.c_void_p(st.data_ptr()), p.max_rounds, p.gr_interval,
                                           C.c_void_p(stream.cuda_stream))
         assert rc == lem.LEM_OK, lem.lem_last_error(None)
         torch.cuda.synchronize()
+        if call == 1:
+            # (the first call may load the library's module lazily, which places the
+            # static scratch array; the second finds everything in place) no device
+            # memory was taken by the call
+            assert torch.cuda.mem_get_info()[0] == free_before
         # min-cut results are integers: bit-exact, as for lem_mincut_batch against the oracle
         assert (st.cpu().numpy() == 0).all() and (st_ref.cpu().numpy() == 0).all()
         assert (flow.cpu().numpy() == flow_ref.cpu().numpy()).all()
         assert (take.cpu().numpy() == take_ref.cpu().numpy()).all()
+        # and the oracle's Dinic max-flow on the 45 x 45 graph of this call: flow and
+        # minimal sink side bit-exact
+        k = 1
+        off = sum(w * h for (_, _, w, h) in regions[:k])
+        w, h = regions[k][2], regions[k][3]
+        f, cut = oracle.maxflow(w, h, graphs[k][0], graphs[k][1], "dinic")
+        assert int(flow.cpu().numpy()[k]) == f
+        assert (take.cpu().numpy()[off:off + w * h].reshape(h, w) == cut).all()
     ref.close()
 
 
