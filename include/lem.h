@@ -135,6 +135,14 @@ typedef struct {
                              move while the first CTA makes that move; the first move can only turn
                              f_r into alpha_1, so the second move then takes its data term from one of
                              the two planes.  Same labels as 0 (one CTA), bit for bit. */
+    int split_visits;     /* batched visits (candidates_per_visit >= 2) on the guided-filter data term,
+                             without RANSAC proposals, at levels whose regions are at most
+                             LEM_MAX_REGION_NODES nodes and whose filtering regions are at most 128 px
+                             wide: 1 runs each visit as two launches, the data terms of all its
+                             candidates (one warp per region and candidate, exact fixed-point window
+                             sums) and then its moves (one CTA per region; level_threads is that CTA's
+                             size, 32 .. 1024); 0 (default) runs the visit in one kernel.  The moves
+                             are the same; the data terms differ only in FP32 rounding. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -155,6 +163,8 @@ typedef struct {
     int64_t pr_rounds;     /* push-relabel rounds (all cuts)                           */
     int64_t pr_global_relabels; /* global relabels (all cuts)                          */
     int64_t pr_bfs_levels; /* BFS frontiers processed by the global relabels           */
+    int64_t accepted_by_kind[4]; /* switched pixels by proposal kind: propagation, RANSAC,
+                                    map (learned proposer), perturbation                   */
 } lem_stats;
 
 typedef struct lem_handle lem_handle;
@@ -327,6 +337,39 @@ int lem_energy(lem_handle *h, double *energy, int64_t *energy_q);
  * lambda*max(w, eps) for the 4 forward neighbours as float32 H*W*4.  Copies
  * into caller device buffers; any may be NULL.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
 int lem_get_planes(lem_handle *h, float *left, float *right, float *guide, float *weights);
+
+/* Measures the current device's FP32 fused multiply-add throughput and its
+ * shared-memory load bandwidth (16-byte conflict-free loads), each the best of
+ * five timed launches of a microbenchmark kernel over every SM, on `stream`
+ * (cudaStream_t, NULL: the legacy default stream).  These are the roofs the data
+ * term is reported against; the paper has no counterpart.  Synchronises the
+ * stream.  Errors: LEM_ERR_ARG (NULL output), LEM_ERR_OOM, LEM_ERR_CUDA. */
+int lem_measure_peaks(void *stream, double *fp32_tflops, double *smem_gbs);
+
+/* Kinds of the expansion launches that lem_get_kernel_times reports. */
+#define LEM_KERNEL_EXPAND 0       /* one-kernel visits (k_expand_group)                      */
+#define LEM_KERNEL_VISIT_UNARY 1  /* data terms of a batched visit (k_visit_unary)           */
+#define LEM_KERNEL_VISIT_CUT 2    /* moves of a batched visit (k_visit_cut)                   */
+#define LEM_KERNEL_GRID 3         /* multi-CTA regions (k_expand_grid)                        */
+#define LEM_KERNEL_KINDS 4
+typedef struct {
+    double ms[3][LEM_KERNEL_KINDS];       /* GPU time per level and kind, from CUDA events between launches */
+    int64_t launches[3][LEM_KERNEL_KINDS];
+} lem_kernel_times;
+
+/* Kernel timing of lem_expand_iteration (a measurement aid; the paper has no
+ * counterpart).  With on = 1 every outer iteration records a CUDA event on the
+ * handle's stream before its first launch and after each expansion launch (as
+ * event nodes of the CUDA graph when iterations are replayed as one); results
+ * are unchanged.  Turning it on or off drops the captured graph, which the
+ * next lem_expand_iteration captures again.  Errors: LEM_ERR_ARG. */
+int lem_set_kernel_timing(lem_handle *h, int on);
+/* Time of each launch kind at each level in the last outer iteration issued
+ * on the handle
+ * (events are overwritten by every iteration, so call it after each one; the
+ * time between two events is the launch between them).  Synchronises the
+ * stream.  All zero when timing is off.  Errors: LEM_ERR_ARG, LEM_ERR_CUDA. */
+int lem_get_kernel_times(lem_handle *h, lem_kernel_times *out);
 
 /* Largest n_regions of lem_mincut_batch_noalloc. */
 #define LEM_NOALLOC_MAX_REGIONS 4096

@@ -1,6 +1,7 @@
 """Builds the CUDA library ``liblem.so`` in-tree for sm_103a (nvcc, no cmake).
 
-The translation units compile in parallel; the result is linked with the
+The translation units (kernels, host API, proposal network, peak
+microbenchmarks) compile in parallel; the result is linked with the
 static CUDA runtime so it loads without extra library paths.
 """
 from __future__ import annotations
@@ -15,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblem.so")
-SOURCES = ["lem_kernels.cu", "lem_api.cu", "lem_cnn.cu"]
+SOURCES = ["lem_kernels.cu", "lem_api.cu", "lem_cnn.cu", "lem_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

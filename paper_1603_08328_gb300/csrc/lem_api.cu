@@ -27,6 +27,11 @@ struct lem_handle {
     float4 *gst = nullptr, *wfw = nullptr, *lab = nullptr;
     float *phiA = nullptr;
     float *phiB = nullptr;              // second data-term plane of the two-CTA visits
+    // batched visits split into data-term and cut launches (lem::visit_split):
+    // candidates_per_visit data-term planes and the candidate labels of a launch
+    float *phiK = nullptr;
+    float4 *alphaK = nullptr;
+    bool split_level[3] = {false, false, false};
     float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
     bool prop_set = false;
     float *cnn_buf = nullptr;           // network input / output of one pair (lem_cnn_propose)
@@ -53,6 +58,15 @@ struct lem_handle {
     cudaGraphExec_t gexec = nullptr;
     int iter = 0;
     int fp64_inverses = 0;
+    // kernel timing (lem_set_kernel_timing): an event before the first launch of an
+    // outer iteration and after each launch, with the kind of that launch
+    bool ktime = false;
+    std::vector<cudaEvent_t> kev;
+    std::vector<int> kkind;
+    int kn = 0;        // events recorded so far in the iteration being issued
+    int kn_last = 0;   // events of the last iteration issued (direct or captured)
+    int kn_graph = 0;  // events of the captured iteration
+    bool capturing = false;
     lem::Counters last{};  // device counters at the previous stats read
     std::string err;
 };
@@ -126,6 +140,26 @@ lem::KParams kparams(const lem_handle *h) {
     k.visit = p.candidates_per_visit;
     k.bf = p.data_term == LEM_DATA_BF ? 1 : 0;
     k.bf_log2e_inv_gamma = (float)(1.4426950408889634 / p.bf_gamma);
+    // fixed-point scales of the warp data term: the largest powers of two for which
+    // no window sum of (2r'+1)^2 raw-cost channel terms (|term| <= rho_max, the
+    // largest raw cost, since |I/255 - c| <= 1) exceeds 2^31, and no window sum of
+    // guided-filter coefficients exceeds 2^62; |a_k| <= sqrt(3) rho_max / e and
+    // |b_k| <= rho_max (1 + 3 / e) bound the coefficients ((Sigma_k + eU)^-1 has
+    // norm <= 1/e, guide values and their covariance with rho lie in [-1, 1] and
+    // [-rho_max, rho_max]); margins of 1 % and 2x cover rounding
+    {
+        const double n = (2.0 * p.gf_radius + 1) * (2.0 * p.gf_radius + 1);
+        const double rho_max = std::max(1e-30, std::fabs(1.0 - p.alpha_grad) * std::fabs(p.tau_col) +
+                                                   std::fabs(p.alpha_grad) * std::fabs(p.tau_grad));
+        const double coef_max = 2.0 * rho_max * (1.0 + 3.0 / p.gf_eps);
+        auto pow2_floor = [](double x) {
+            int e = 0;
+            std::frexp(x, &e);
+            return std::ldexp(1.0, e - 1);
+        };
+        k.q1 = (float)std::min(std::ldexp(1.0, 30), pow2_floor(2147483647.0 / (1.01 * n * rho_max)));
+        k.q2 = (float)std::min(std::ldexp(1.0, 32), pow2_floor(std::ldexp(1.0, 62) / (n * coef_max)));
+    }
     return k;
 }
 
@@ -182,14 +216,15 @@ int check_params(const lem_params *p) {
         return fail(nullptr, LEM_ERR_ARG, "data_term must be LEM_DATA_GF or LEM_DATA_BF");
     if (!(p->bf_gamma > 0)) return fail(nullptr, LEM_ERR_ARG, "bf_gamma must be > 0");
     if (p->cluster_visits != 0 && p->cluster_visits != 1) return fail(nullptr, LEM_ERR_ARG, "cluster_visits must be 0 or 1");
+    if (p->split_visits != 0 && p->split_visits != 1) return fail(nullptr, LEM_ERR_ARG, "split_visits must be 0 or 1");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
         return fail(nullptr, LEM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
     for (int l = 0; l < 3; ++l) {
         const int t = p->level_threads[l];
-        if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024)
-            return fail(nullptr, LEM_ERR_ARG, "level_threads must be 0, 128, 256, 512 or 1024");
+        if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256 && t != 512 && t != 1024)
+            return fail(nullptr, LEM_ERR_ARG, "level_threads must be 0, 32, 64, 128, 256, 512 or 1024");
         if (p->level_gr_interval[l] < 0) return fail(nullptr, LEM_ERR_ARG, "level_gr_interval must be >= 0");
         if (p->level_strip_rows[l] < 0 || p->level_strip_rows[l] > 64 || p->level_strip_rows[l] % 4)
             return fail(nullptr, LEM_ERR_ARG, "level_strip_rows must be 0 or a multiple of 4 up to 64");
@@ -214,6 +249,8 @@ void free_handle(lem_handle *h) {
     cudaFree(h->lab);
     cudaFree(h->phiA);
     cudaFree(h->phiB);
+    cudaFree(h->phiK);
+    cudaFree(h->alphaK);
     cudaFree(h->prop);
     cudaFree(h->cnn_buf);
     cudaFree(h->e_part);
@@ -230,6 +267,7 @@ void free_handle(lem_handle *h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    for (cudaEvent_t e : h->kev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -300,6 +338,7 @@ int read_counters(lem_handle *h, lem_stats *stats) {
     stats->pr_rounds = (int64_t)(c.rounds - h->last.rounds);
     stats->pr_global_relabels = (int64_t)(c.relabels - h->last.relabels);
     stats->pr_bfs_levels = (int64_t)(c.bfs_levels - h->last.bfs_levels);
+    for (int k = 0; k < 4; ++k) stats->accepted_by_kind[k] = (int64_t)(c.accepted_kind[k] - h->last.accepted_kind[k]);
     stats->fp64_inverses = h->fp64_inverses;
     stats->iterations = h->iter;
     h->last = c;
@@ -475,6 +514,22 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
             h->grid_sync_cap = regions;
         }
     }
+    // levels whose batched visits run as data-term + cut launches: their planes
+    // and candidate labels
+    {
+        int most = 0;
+        for (int l = 0; l < p->n_levels; ++l) {
+            h->split_level[l] = p->split_visits && !h->grid_level[l] &&
+                                lem::visit_split(kparams_level(h, l), level_of(h, l), h->maxW, h->maxH);
+            if (!h->split_level[l]) continue;
+            for (int g = 0; g < 16; ++g) most = std::max(most, h->item_cnt[l][g]);
+        }
+        if (most > 0) {
+            const int K = p->candidates_per_visit;
+            CREATE_CUDA(cudaMalloc(&h->phiK, sizeof(float) * n * K));
+            CREATE_CUDA(cudaMalloc(&h->alphaK, sizeof(float4) * (size_t)most * K));
+        }
+    }
     // per pair: images on the device, packing, guide statistics, random labels, costs
     for (int b = 0; b < n_pairs; ++b) {
         const lem_image *left = &lefts[b], *right = &rights[b];
@@ -604,6 +659,14 @@ int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, con
     int mw, mh, mn, rc;
     if ((rc = stage_regions(h, regions, n_regions, K, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
     if ((int64_t)n_regions * K > (1LL << 31) - 1) return fail(h, LEM_ERR_ARG, "too many region-label pairs");
+    // a handle whose expansions use the warp data term (batched visits) gets the same
+    // computation here
+    const lem::KParams kp = kparams(h);
+    if (h->p.split_visits && h->p.candidates_per_visit >= 2 && lem::unary_warp_fits(kp, h->W, mw)) {
+        LEM_CUDA(h, lem::launch_unary_batch_warp(planes(h), kp, h->d_regions, h->d_offsets, n_regions, K, mw, labels,
+                                                 costs, h->st));
+        return LEM_OK;
+    }
     LEM_CUDA(h, lem::launch_unary_batch(planes(h), kparams(h), h->d_regions, h->d_offsets, n_regions, K, mw, mh,
                                         labels, costs, h->p.threads, h->st));
     return LEM_OK;
@@ -656,38 +719,87 @@ int lem_mincut_batch(lem_handle *h, const lem_region *regions, int n_regions, co
     return LEM_OK;
 }
 
+// kernel timing: records the next event of the iteration after a launch of `kind`
+// (kind < 0: the event before the first launch).  In a stream capture the event
+// becomes an event node of the graph.
+static int ktime_mark(lem_handle *h, int kind, int level, cudaStream_t st) {
+    if (!h->ktime) return LEM_OK;
+    if (kind < 0) h->kn = 0;
+    if (h->kn >= (int)h->kev.size()) {
+        cudaEvent_t e = nullptr;
+        LEM_CUDA(h, cudaEventCreate(&e));
+        h->kev.push_back(e);
+        h->kkind.push_back(-1);
+    }
+    h->kkind[h->kn] = kind < 0 ? -1 : kind + LEM_KERNEL_KINDS * level;
+    LEM_CUDA(h, cudaEventRecordWithFlags(h->kev[h->kn], st, h->capturing ? cudaEventRecordExternal : 0));
+    ++h->kn;
+    return LEM_OK;
+}
+
 // one (level, group) launch over every pair; iter < 0: read from h->d_iter
 static int expand_group_impl(lem_handle *h, int iter, int level, int group, cudaStream_t st) {
     const lem::Level lv = level_of(h, level);
     if (h->prop && !h->prop_set)
         return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
     const lem::KParams kp = kparams_level(h, level);
+    int rc;
+    if (h->split_level[level]) {
+        // batched visits: per visit, the data terms of its candidates, then its moves
+        const int nprop = lv.k_prop + (h->prop ? lv.k_cnn : 0) + lv.k_rand;
+        const int K = kp.visit;
+        const int4 *items = h->d_items + h->item_off[level][group];
+        const int n_items = h->item_cnt[level][group];
+        for (int t0 = 0; t0 < nprop; t0 += K) {
+            const int nK = std::min(K, nprop - t0);
+            LEM_CUDA(h, lem::launch_visit_unary(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
+                                                h->maxH, items, n_items, t0, nK, h->lab, h->phiK, h->total, h->prop,
+                                                h->alphaK, st));
+            if ((rc = ktime_mark(h, LEM_KERNEL_VISIT_UNARY, level, st)) != LEM_OK) return rc;
+            LEM_CUDA(h, lem::launch_visit_cut(planes_base(h), kp, lv, h->d_pairs, h->maxW, h->maxH, items, n_items,
+                                              t0, nK, h->prop ? lv.k_cnn : 0, h->lab, h->phiK, h->total, h->alphaK,
+                                              h->ctr, st));
+            if ((rc = ktime_mark(h, LEM_KERNEL_VISIT_CUT, level, st)) != LEM_OK) return rc;
+        }
+        return LEM_OK;
+    }
     if (h->grid_level[level]) {
         if (iter < 0) return fail(h, LEM_ERR_ARG, "levels above the shared-memory cut are not graph-captured");
         LEM_CUDA(h, lem::launch_expand_grid(planes_base(h), kp, lv, level, iter, h->d_pairs, h->maxW, h->maxH,
                                             h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                             h->lab, h->phiA, h->prop, h->ctr, h->grid_slots, h->grid_slot_cap,
                                             h->grid_sync, h->grid_sync_cap, st));
-        return LEM_OK;
+        return ktime_mark(h, LEM_KERNEL_GRID, level, st);
     }
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                          h->lab, h->phiA, h->prop, h->ctr, h->p.cluster_visits ? h->phiB : nullptr,
                                          st));
-    return LEM_OK;
+    return ktime_mark(h, LEM_KERNEL_EXPAND, level, st);
 }
 
 // Captures one outer iteration (every level and group, then the increment of
 // the device iteration index) as a CUDA graph on a private stream.
 static int build_graph(lem_handle *h) {
     if (!h->cap_st) LEM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    // kernel-timing events are created before the capture begins
+    if (h->ktime)
+        while ((int)h->kev.size() < h->kn_last + 1) {
+            cudaEvent_t ev = nullptr;
+            LEM_CUDA(h, cudaEventCreate(&ev));
+            h->kev.push_back(ev);
+            h->kkind.push_back(-1);
+        }
     LEM_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
-    int rc = LEM_OK;
+    h->capturing = true;
+    int rc = ktime_mark(h, -1, 0, h->cap_st);
     for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
         for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, -1, l, g, h->cap_st);
     cudaError_t e = rc == LEM_OK ? lem::launch_increment(h->d_iter, h->cap_st) : cudaSuccess;
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
+    h->capturing = false;
+    h->kn_graph = h->kn;
     if (rc != LEM_OK) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
@@ -705,7 +817,11 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (iter < 0 || level < 0 || level >= h->p.n_levels || group < 0 || group > 15)
         return fail(h, LEM_ERR_ARG, "iter/level/group out of range");
+    // kernel timing covers lem_expand_iteration only
+    const bool kt = h->ktime;
+    h->ktime = false;
     int rc = expand_group_impl(h, iter, level, group, h->st);
+    h->ktime = kt;
     if (rc != LEM_OK) return rc;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -723,30 +839,30 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     if (n_iters > 0 && h->p.use_graph && graph_ok && !h->gexec) {
         // the first iteration runs directly (it also sets the kernels' shared
         // memory limits), the graph is captured for the following ones
-        for (int l = 0; l < h->p.n_levels; ++l)
-            for (int g = 0; g < 16; ++g) {
-                int rc = expand_group_impl(h, h->iter, l, g, h->st);
-                if (rc != LEM_OK) return rc;
-            }
+        int rc = ktime_mark(h, -1, 0, h->st);
+        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
+            for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, h->iter, l, g, h->st);
+        if (rc != LEM_OK) return rc;
+        h->kn_last = h->kn;
         ++h->iter;
         ++done;
-        int rc = build_graph(h);
-        if (rc != LEM_OK) return rc;
+        if ((rc = build_graph(h)) != LEM_OK) return rc;
     }
     if (done < n_iters && h->gexec) {
         // the device iteration index follows the host one
         LEM_CUDA(h, cudaMemcpyAsync(h->d_iter, &h->iter, sizeof(int), cudaMemcpyHostToDevice, h->st));
         for (; done < n_iters; ++done) {
             LEM_CUDA(h, cudaGraphLaunch(h->gexec, h->st));
+            h->kn_last = h->kn_graph;
             ++h->iter;
         }
     }
     for (; done < n_iters; ++done) {
-        for (int l = 0; l < h->p.n_levels; ++l)
-            for (int g = 0; g < 16; ++g) {
-                int rc = expand_group_impl(h, h->iter, l, g, h->st);
-                if (rc != LEM_OK) return rc;
-            }
+        int rc = ktime_mark(h, -1, 0, h->st);
+        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
+            for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, h->iter, l, g, h->st);
+        if (rc != LEM_OK) return rc;
+        h->kn_last = h->kn;
         ++h->iter;
     }
     if (stats) {
@@ -756,6 +872,37 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
         if ((rc = read_counters(h, stats)) != LEM_OK) return rc;
         stats->energy_q = eq;
         stats->energy = (double)eq / h->p.quant_scale;
+    }
+    return LEM_OK;
+}
+
+int lem_set_kernel_timing(lem_handle *h, int on) {
+    if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
+    if (on != 0 && on != 1) return fail(h, LEM_ERR_ARG, "on must be 0 or 1");
+    if ((on != 0) != h->ktime) {
+        // the captured graph is recaptured with (or without) the event nodes
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->gexec = nullptr;
+        h->graph = nullptr;
+    }
+    h->ktime = on != 0;
+    h->kn = h->kn_last = h->kn_graph = 0;
+    return LEM_OK;
+}
+
+int lem_get_kernel_times(lem_handle *h, lem_kernel_times *out) {
+    if (!h || !out) return fail(h, LEM_ERR_ARG, "handle or output is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (!h->ktime || h->kn_last < 2) return LEM_OK;
+    LEM_CUDA(h, cudaStreamSynchronize(h->st));
+    for (int i = 1; i < h->kn_last; ++i) {
+        float ms = 0.f;
+        LEM_CUDA(h, cudaEventElapsedTime(&ms, h->kev[i - 1], h->kev[i]));
+        const int k = h->kkind[i];
+        if (k < 0 || k >= 3 * LEM_KERNEL_KINDS) continue;
+        out->ms[k / LEM_KERNEL_KINDS][k % LEM_KERNEL_KINDS] += ms;
+        out->launches[k / LEM_KERNEL_KINDS][k % LEM_KERNEL_KINDS] += 1;
     }
     return LEM_OK;
 }
@@ -992,6 +1139,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     int rc = e == cudaSuccess ? LEM_OK : cuda_fail(h, e, "lem_autotune setup");
     const lem_params keep = h->p;
     static const int kThreads[4] = {128, 256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[5] = {8, 12, 16, 24, 32};
+    static const int kThreadsSplit[6] = {32, 64, 128, 256, 512, 1024};
     // time of `repeats` launches of groups 0 and 10 at `level`, state restored after each;
     // < 0 when the configuration cannot launch
     auto trial = [&](int level, float &ms) -> int {
@@ -1032,22 +1180,27 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         rc = trial(l, best);
         res.ms_default[l] = best;
         const int s3 = 3 * h->p.cell[l];
-        int bt = lem::threads_for_nodes(std::min(h->maxW, s3) * std::min(h->maxH, s3));
+        const int nodes = std::min(h->maxW, s3) * std::min(h->maxH, s3);
+        int bt = h->split_level[l] ? lem::visit_cut_threads(nodes) : lem::threads_for_nodes(nodes);
         int bg = keep.gr_interval, bs = keep.strip_rows;
-        for (int ti = 0; ti < 4 && rc == LEM_OK; ++ti)
+        // split levels: the cut CTA's size (32 .. 1024) and the relabel interval (the
+        // warp data term has no strip rows); one-kernel levels: all three
+        const int *threads = h->split_level[l] ? kThreadsSplit : kThreads;
+        const int nthreads = h->split_level[l] ? 6 : 4, nrows = h->split_level[l] ? 1 : 5;
+        for (int ti = 0; ti < nthreads && rc == LEM_OK; ++ti)
             for (int gi = 0; gi < 4 && rc == LEM_OK; ++gi)
-                for (int si = 0; si < 5 && rc == LEM_OK; ++si) {
-                    h->p.level_threads[l] = kThreads[ti];
+                for (int si = 0; si < nrows && rc == LEM_OK; ++si) {
+                    h->p.level_threads[l] = threads[ti];
                     h->p.level_gr_interval[l] = kGr[gi];
-                    h->p.level_strip_rows[l] = kRows[si];
+                    h->p.level_strip_rows[l] = h->split_level[l] ? 0 : kRows[si];
                     float ms = -1.f;
                     rc = trial(l, ms);
                     ++res.configs_tried;
                     if (rc == LEM_OK && ms >= 0.f && (best < 0.f || ms < best)) {
                         best = ms;
-                        bt = kThreads[ti];
+                        bt = threads[ti];
                         bg = kGr[gi];
-                        bs = kRows[si];
+                        bs = h->p.level_strip_rows[l];
                     }
                 }
         h->p.level_threads[l] = bt;

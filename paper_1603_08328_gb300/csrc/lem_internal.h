@@ -33,6 +33,10 @@ struct KParams {
     int visit;          // candidates drawn per region visit (1: Algorithm 2)
     int bf;             // data term: 0 guided filter (LE-GF), 1 bilateral weights (LE-BF)
     float bf_log2e_inv_gamma; // LE-BF: log2(e) / gamma of the colour weights
+    // fixed-point scales (powers of two) of the exact window sums of the warp
+    // data term: q1 for the raw-cost channels (32-bit), q2 for the guided-filter
+    // coefficients (64-bit); chosen on the host so no window sum can overflow
+    float q1, q2;
 };
 
 // One stereo pair inside a batch handle: its size, the pixel offset of its
@@ -61,6 +65,8 @@ struct Counters {
     unsigned long long rounds;      // push-relabel rounds
     unsigned long long relabels;    // global relabels
     unsigned long long bfs_levels;  // BFS frontiers summed over global relabels
+    unsigned long long accepted_kind[4];  // switched pixels by proposal kind: propagation, RANSAC,
+                                          // map (learned proposer), perturbation
 };
 
 // Shared-memory bytes the region cost pipeline needs for regions up to
@@ -104,6 +110,31 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
                                 cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
+// Batched visits on the guided-filter data term without RANSAC proposals, regions
+// of at most LEM_MAX_REGION_NODES nodes and filtering regions at most 128 px
+// wide: a visit is a data-term launch (one warp per region and candidate, exact
+// fixed-point window sums) and a cut launch (one CTA per region, the visit's
+// moves in order).  phiK holds nK data-term planes of plane_stride floats,
+// alphaK n_items * nK candidate labels.  lv.threads is the cut CTA's size
+// (32 .. 1024; 0: by region size).
+bool visit_split(const KParams &kp, const Level &lv, int max_w, int max_h);
+// lem_unary_batch with the warp data term of that path (one warp per region and
+// label), for regions at most max_w wide whose filtering region fits it
+bool unary_warp_fits(const KParams &kp, int W, int max_w);
+cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const int4 *regions,
+                                    const int64_t *offsets, int n_regions, int K, int max_w, const float *labels,
+                                    float *costs, cudaStream_t st);
+int visit_cut_threads(int nodes);
+cudaError_t launch_visit_unary(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                               const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
+                               int n_items, int t0, int nK, const float4 *lab, float *phiK, long long plane_stride,
+                               const float4 *prop, float4 *alphaK, cudaStream_t st);
+// (t0: first proposal index of the visit, kc: map candidates per visit, for the
+// per-kind switch counts)
+cudaError_t launch_visit_cut(const DevPlanes &P, const KParams &kp, const Level &lv, const PairDesc *pairs,
+                             int max_w, int max_h, const int4 *items, int n_items, int t0, int nK, int kc,
+                             float4 *lab, const float *phiK, long long plane_stride, const float4 *alphaK,
+                             Counters *ctr, cudaStream_t st);
 // Regions above the shared-memory cut (more than LEM_MAX_REGION_NODES nodes, or
 // a data term + cut that needs more than a CTA's shared memory) take the
 // cooperative multi-CTA path.

@@ -108,20 +108,39 @@ __device__ __forceinline__ float two_prod(float a, float b, float &err) {
 }
 
 // d_(u,v)(f1) - d_(u,v)(f2) with d_p(f) = a u + b v + c, in float-float so the
-// result is accurate even for steep planes with large |c|.  Antisymmetric
-// bit for bit: dd(f2, f1) == -dd(f1, f2).
-__device__ __forceinline__ float disp_diff(const float4 &f1, const float4 &f2, float u, float v) {
-    float al, bl, cl, e1, e2, e3, e4;
-    const float ah = two_sum(f1.x, -f2.x, al);
-    const float bh = two_sum(f1.y, -f2.y, bl);
-    const float ch = two_sum(f1.z, -f2.z, cl);
-    const float x1 = two_prod(ah, u, e1);
-    const float x2 = two_prod(bh, v, e2);
+// result is accurate even for steep planes with large |c|.  The coefficient
+// differences (dd_coef) are taken once per label pair and evaluated at any
+// position (dd_eval).  Antisymmetric bit for bit: swapping f1 and f2 negates
+// every intermediate exactly, so dd(f2, f1) == -dd(f1, f2).
+struct DDCoef {
+    float ah, al, bh, bl, ch, cl;
+};
+__device__ __forceinline__ DDCoef dd_coef(const float4 &f1, const float4 &f2) {
+    DDCoef d;
+    d.ah = two_sum(f1.x, -f2.x, d.al);
+    d.bh = two_sum(f1.y, -f2.y, d.bl);
+    d.ch = two_sum(f1.z, -f2.z, d.cl);
+    return d;
+}
+__device__ __forceinline__ float dd_eval(const DDCoef &d, float u, float v) {
+    float e1, e2, e3, e4;
+    const float x1 = two_prod(d.ah, u, e1);
+    const float x2 = two_prod(d.bh, v, e2);
     const float s1 = two_sum(x1, x2, e3);
-    const float s2 = two_sum(s1, ch, e4);
+    const float s2 = two_sum(s1, d.ch, e4);
     float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4));
-    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fmul_rn(al, u), __fmul_rn(bl, v)), cl));
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fmul_rn(d.al, u), __fmul_rn(d.bl, v)), d.cl));
     return __fadd_rn(s2, lo);
+}
+__device__ __forceinline__ float disp_diff(const float4 &f1, const float4 &f2, float u, float v) {
+    return dd_eval(dd_coef(f1, f2), u, v);
+}
+
+// Q(wl min(pb, tau)) for psi-bar pb = |D1| + |D2| (Eq. smooth, Eq. smooth_phi),
+// Q(x) = rne(S x)
+__device__ __forceinline__ int q_of(float wl, float tau, float S, float D1, float D2) {
+    const float pb = __fadd_rn(fabsf(D1), fabsf(D2));
+    return __float2int_rn(__fmul_rn(__fmul_rn(wl, fminf(pb, tau)), S));
 }
 
 // Q(lambda psi_pq(f1, f2)) for the pair (p = (u1,v1), q = (u2,v2)) with weight
@@ -130,11 +149,8 @@ __device__ __forceinline__ float disp_diff(const float4 &f1, const float4 &f2, f
 // Symmetric bit for bit under swapping (f1 at p) <-> (f2 at q).
 __device__ __forceinline__ int q_psi(float wl, float tau, float S, const float4 &f1, const float4 &f2, int u1,
                                      int v1, int u2, int v2) {
-    const float D1 = disp_diff(f1, f2, (float)u1, (float)v1);
-    const float D2 = disp_diff(f1, f2, (float)u2, (float)v2);
-    const float pb = __fadd_rn(fabsf(D1), fabsf(D2));
-    const float psi = __fmul_rn(wl, fminf(pb, tau));
-    return __float2int_rn(__fmul_rn(psi, S));
+    const DDCoef d = dd_coef(f1, f2);
+    return q_of(wl, tau, S, dd_eval(d, (float)u1, (float)v1), dd_eval(d, (float)u2, (float)v2));
 }
 
 __device__ __forceinline__ int q_cost(float phi, float S) { return __float2int_rn(__fmul_rn(phi, S)); }
@@ -997,6 +1013,325 @@ __device__ __forceinline__ void region_unary(const DevPlanes &P, const KParams &
 }
 
 // ---------------------------------------------------------------------------
+// A3 + A4 by one warp: the data term of one label over one region whose
+// filtering region M is at most 32 NC pixels wide.  Lane l owns the M columns
+// l, l + 32, ..., and the warp walks down the rows of M once:
+//   * raw cost rho (Eq. photofunc) of the new row and its guide products
+//     (I - c) rho enter per-lane vertical window sums; the row that leaves the
+//     window is subtracted (its rho from a per-lane ring in shared memory, its
+//     products recomputed from the left image);
+//   * each completed row of K (R grown by r') gets its horizontal window sums
+//     from an inclusive prefix sum across the lanes (warp shuffles), then the
+//     guided-filter coefficients a_k, b_k (Eq. gf);
+//   * a_k, b_k enter a second pair of vertical window sums (their ring is in
+//     shared memory too), and each completed row of R gets the horizontal
+//     window sums of the coefficients the same way and phi_p = mean(a) . I_p +
+//     mean(b).
+// Every window sum is exact: the raw-cost channels are summed as 32-bit
+// fixed-point integers (scale kp.q1, a power of two chosen so that no window sum
+// of (2r'+1)^2 terms can overflow; prefix sums wrap modulo 2^32, which leaves
+// each difference exact), the coefficients as 64-bit fixed-point integers
+// (scale kp.q2, sums mod 2^64).  So the result depends on no summation order, launch shape or
+// strip size, and the only rounding in the sums is that of each term to its
+// fixed-point grid (2^-21 for the default raw costs, 2^-33 for coefficients).
+// ring: shared memory owned by the warp (warp_ring_floats).  The next M row's
+// image values are loaded while a row is processed.
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T, int NC>
+__device__ __forceinline__ void warp_prefix(T (&p)[NC], int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const T t = __shfl_up_sync(kFull, p[j], o);
+            if (lane >= o) p[j] += t;
+        }
+    }
+    T carry = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        p[j] += carry;
+        carry = __shfl_sync(kFull, p[j], 31);
+    }
+}
+// element m (0 <= m < 32 NC) of a prefix array held as p[m >> 5] on lane m & 31;
+// m < 0 gives 0.  Every lane of the warp must call it.
+template <typename T, int NC>
+__device__ __forceinline__ T warp_at(const T (&p)[NC], int m) {
+    const int src = m & 31, blk = m >> 5;
+    T v = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const T t = __shfl_sync(kFull, p[j], src);
+        if (j == blk) v = t;
+    }
+    return m < 0 ? (T)0 : v;
+}
+
+// raw cost of left pixel (x, y) for the plane whose row warp offset is (Ib, Fb)
+// (row_offset), also returning the left pixel
+__device__ __forceinline__ float raw_cost(const DevPlanes &P, const KParams &kp, size_t rowb, int x, int Rx0,
+                                          float sh, float sl, int Ib, float Fb, float oma, float4 &l) {
+    const int W = P.W, fmt = P.fmt;
+    l = load_px(P.L, rowb + x, fmt);
+    const float dx = (float)(x - Rx0);
+    const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, Fb));
+    const float gf = floorf(g);
+    float t = g - gf;
+    int i0 = Ib + (int)gf;
+    if (i0 < 0) {
+        i0 = 0;
+        t = 0.f;
+    } else if (i0 >= W - 1) {
+        i0 = W - 1;
+        t = 0.f;
+    }
+    const int i1 = min(i0 + 1, W - 1);
+    const float4 r0 = load_px(P.R, rowb + i0, fmt), r1 = load_px(P.R, rowb + i1, fmt);
+    const float rr = fmaf(t, r1.x - r0.x, r0.x);
+    const float rg = fmaf(t, r1.y - r0.y, r0.y);
+    const float rb = fmaf(t, r1.z - r0.z, r0.z);
+    const float rd = fmaf(t, r1.w - r0.w, r0.w);
+    const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
+    const float gd = fabsf(l.w - rd);
+    return rho_mix(col, gd, kp, oma);
+}
+
+__device__ __forceinline__ int yEndOf(int Ry0, int Rh, int r) { return Ry0 + Rh + 2 * r; }
+
+// image values of one M pixel that its raw cost needs: the left pixel, the two
+// right pixels of the linear tap and its weight, and the left pixel of the row
+// leaving the vertical window
+struct RowPx {
+    float4 l, r0, r1, ll;
+    float t;
+};
+
+template <int NC>
+__device__ __forceinline__ void fetch_row(const DevPlanes &P, int y, int yl, bool add, bool leave, int Mx0, int Mx1,
+                                          int Rx0, float sh, float sl, float lb, float lc, int lane,
+                                          RowPx (&o)[NC]) {
+    const int W = P.W, fmt = P.fmt;
+    int Ib = 0;
+    float Fb = 0.f;
+    if (add) row_offset(sh, sl, lb, lc, Rx0, y, Ib, Fb);
+    const size_t rowb = (size_t)y * W, rowl = (size_t)yl * W;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int x = Mx0 + lane + 32 * j;
+        if (x >= Mx1) continue;
+        if (add) {
+            o[j].l = load_px(P.L, rowb + x, fmt);
+            const float dx = (float)(x - Rx0);
+            const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, Fb));
+            const float gf = floorf(g);
+            float t = g - gf;
+            int i0 = Ib + (int)gf;
+            if (i0 < 0) {
+                i0 = 0;
+                t = 0.f;
+            } else if (i0 >= W - 1) {
+                i0 = W - 1;
+                t = 0.f;
+            }
+            o[j].t = t;
+            o[j].r0 = load_px(P.R, rowb + i0, fmt);
+            o[j].r1 = load_px(P.R, rowb + min(i0 + 1, W - 1), fmt);
+        }
+        if (leave) o[j].ll = load_px(P.L, rowl + x, fmt);
+    }
+}
+
+// raw cost (Eq. photofunc) from the fetched image values (the steps of raw_cost)
+__device__ __forceinline__ float rho_of(const RowPx &q, const KParams &kp, float oma) {
+    const float rr = fmaf(q.t, q.r1.x - q.r0.x, q.r0.x);
+    const float rg = fmaf(q.t, q.r1.y - q.r0.y, q.r0.y);
+    const float rb = fmaf(q.t, q.r1.z - q.r0.z, q.r0.z);
+    const float rd = fmaf(q.t, q.r1.w - q.r0.w, q.r0.w);
+    const float col = fabsf(q.l.x - rr) + fabsf(q.l.y - rg) + fabsf(q.l.z - rb);
+    const float gd = fabsf(q.l.w - rd);
+    return rho_mix(col, gd, kp, oma);
+}
+
+// ring (shared memory of the calling warp): raw costs [2r'+1][mwp], then the
+// guided-filter coefficients [2r'+1][4][kwp]; mwp, kwp >= the widths of M and K
+template <int NC>
+__device__ void warp_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
+                              float lb, float lc, float *ring, int mwp, int kwp, float *out, int pitch) {
+    const int H = P.H, W = P.W, r = kp.r, fmt = P.fmt;
+    const int lane = threadIdx.x & 31;
+    const int Mx0 = max(0, Rx0 - 2 * r), Mx1 = min(W, Rx0 + Rw + 2 * r);
+    const int My0 = max(0, Ry0 - 2 * r), My1 = min(H, Ry0 + Rh + 2 * r);
+    const int Kx0 = max(0, Rx0 - r), Kx1 = min(W, Rx0 + Rw + r);
+    const int Ky0 = max(0, Ry0 - r), Ky1 = min(H, Ry0 + Rh + r);
+    const int Kw = Kx1 - Kx0;
+    const int WIN = 2 * r + 1;
+    float *rho_ring = ring;                 // [WIN][mwp]
+    float *ab_ring = ring + WIN * mwp;      // [WIN][4][kwp]
+    const float4 cen4 = load_px(P.L, (size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2), fmt);
+    const float inv255 = 1.0f / 255.0f;
+    const float cr = cen4.x * inv255, cg = cen4.y * inv255, cb = cen4.z * inv255;
+    float sl;
+    const float sh = two_sum(1.0f, -la, sl);
+    const float oma = 1.0f - kp.alpha_grad;
+    const float q1 = kp.q1, q2 = kp.q2;
+
+    unsigned vs[4][NC];            // vertical window sums of the raw-cost channels (fixed point, mod 2^32)
+    unsigned long long va[4][NC];  // vertical window sums of a_k (3) and b_k (fixed point, mod 2^64)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            vs[c][j] = 0u;
+            va[c][j] = 0ull;
+        }
+    const int yS1 = min(yEndOf(Ry0, Rh, r), Ky1 + r);  // rows that feed stage 1
+    const int yEnd = yEndOf(Ry0, Rh, r);               // one past the last row that completes an R row
+    RowPx cur[NC], nxt[NC];
+    fetch_row<NC>(P, My0, My0 - WIN, My0 < My1, false, Mx0, Mx1, Rx0, sh, sl, lb, lc, lane, cur);
+    int slot1 = 0, slot2 = 0;  // ring slots of the row entering stage 1 / K row entering stage 2
+    for (int y = My0; y < yEnd; ++y) {
+        // the next row's image values are loaded while this row is processed
+        if (y + 1 < yS1)
+            fetch_row<NC>(P, y + 1, y + 1 - WIN, y + 1 < My1, y + 1 - WIN >= My0, Mx0, Mx1, Rx0, sh, sl, lb, lc,
+                          lane, nxt);
+        // ---- stage 1: raw-cost channels of M row y; K row ky = y - r completes
+        if (y < yS1) {
+            const bool add = y < My1, leave = y - WIN >= My0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int c = lane + 32 * j;
+                if (Mx0 + c >= Mx1) continue;
+                float *slotp = rho_ring + slot1 * mwp + c;  // the leaving row's slot is the entering row's
+                if (leave) {
+                    const float rho = *slotp;
+                    const float4 l = cur[j].ll;
+                    vs[0][j] -= (unsigned)__float2int_rn(__fmul_rn(rho, q1));
+                    vs[1][j] -= (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.x, inv255, -cr), rho), q1));
+                    vs[2][j] -= (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.y, inv255, -cg), rho), q1));
+                    vs[3][j] -= (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.z, inv255, -cb), rho), q1));
+                }
+                if (add) {
+                    const float4 l = cur[j].l;
+                    const float rho = rho_of(cur[j], kp, oma);
+                    *slotp = rho;
+                    vs[0][j] += (unsigned)__float2int_rn(__fmul_rn(rho, q1));
+                    vs[1][j] += (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.x, inv255, -cr), rho), q1));
+                    vs[2][j] += (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.y, inv255, -cg), rho), q1));
+                    vs[3][j] += (unsigned)__float2int_rn(__fmul_rn(__fmul_rn(__fmaf_rn(l.z, inv255, -cb), rho), q1));
+                }
+            }
+            if (++slot1 == WIN) slot1 = 0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) cur[j] = nxt[j];
+        }
+        const int ky = y - r;
+        if (ky < Ky0) continue;
+        // ---- stage 2: coefficients of K row ky (when it is a row of K) enter the
+        // vertical sums; the K row ky - WIN leaves
+        {
+            const int kyl = ky - WIN;
+            const bool real = ky < Ky1;
+            float a[4][NC];
+            if (real) {
+                const int ny = min(H - 1, ky + r) - max(0, ky - r) + 1;
+                unsigned p[4][NC];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) p[c][j] = vs[c][j];
+                    warp_prefix<unsigned, NC>(p[c], lane);
+                }
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    a[0][j] = a[1][j] = a[2][j] = a[3][j] = 0.f;
+                    if (32 * j >= Kw) continue;  // (warp-uniform) no K column in this block
+                    const int kx = Kx0 + lane + 32 * j;
+                    const int hi = min(W - 1, kx + r) - Mx0, lo = max(0, kx - r) - Mx0 - 1;
+                    float S[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        S[c] = (float)(int)(warp_at<unsigned, NC>(p[c], hi) - warp_at<unsigned, NC>(p[c], lo));
+                    if (kx < Kx1) {
+                        const int nx = min(W - 1, kx + r) - max(0, kx - r) + 1;
+                        const float inv = 1.0f / __fmul_rn((float)(nx * ny), q1);
+                        const float mr = __fmul_rn(S[0], inv);
+                        const float4 *G = P.gst + 3 * ((size_t)ky * W + kx);
+                        const float4 g0 = G[0], g1 = G[1], g2 = G[2];
+                        const float u0 = g0.x - cr, u1 = g0.y - cg, u2 = g0.z - cb;
+                        const float v0 = __fmaf_rn(-u0, mr, __fmul_rn(S[1], inv));
+                        const float v1 = __fmaf_rn(-u1, mr, __fmul_rn(S[2], inv));
+                        const float v2 = __fmaf_rn(-u2, mr, __fmul_rn(S[3], inv));
+                        const float a0 = __fmaf_rn(g0.w, v0, __fmaf_rn(g1.x, v1, __fmul_rn(g1.y, v2)));
+                        const float a1 = __fmaf_rn(g1.x, v0, __fmaf_rn(g1.z, v1, __fmul_rn(g1.w, v2)));
+                        const float a2 = __fmaf_rn(g1.y, v0, __fmaf_rn(g1.w, v1, __fmul_rn(g2.x, v2)));
+                        a[0][j] = a0;
+                        a[1][j] = a1;
+                        a[2][j] = a2;
+                        a[3][j] = __fsub_rn(mr, __fmaf_rn(a0, u0, __fmaf_rn(a1, u1, __fmul_rn(a2, u2))));
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int c = lane + 32 * j;
+                if (Kx0 + c >= Kx1) continue;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    float *slotp = ab_ring + (slot2 * 4 + ch) * kwp + c;
+                    if (kyl >= Ky0) va[ch][j] -= (unsigned long long)__float2ll_rn(__fmul_rn(*slotp, q2));
+                    if (real) {
+                        *slotp = a[ch][j];
+                        va[ch][j] += (unsigned long long)__float2ll_rn(__fmul_rn(a[ch][j], q2));
+                    }
+                }
+            }
+            if (++slot2 == WIN) slot2 = 0;
+        }
+        // ---- R row py = ky - r completes: horizontal sums of the coefficients, phi
+        const int py = ky - r;
+        if (py < Ry0) continue;
+        {
+            const int ny = min(H - 1, py + r) - max(0, py - r) + 1;
+            unsigned long long p[4][NC];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) p[c][j] = va[c][j];
+                warp_prefix<unsigned long long, NC>(p[c], lane);
+            }
+            const size_t rowb = (size_t)py * W;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                if (32 * j >= Rw) continue;  // (warp-uniform) no R column in this block
+                const int px = Rx0 + lane + 32 * j;
+                const int hi = min(W - 1, px + r) - Kx0, lo = max(0, px - r) - Kx0 - 1;
+                float S[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    S[c] = __ll2float_rn((long long)(warp_at<unsigned long long, NC>(p[c], hi) -
+                                                     warp_at<unsigned long long, NC>(p[c], lo)));
+                if (px < Rx0 + Rw) {
+                    const int nx = min(W - 1, px + r) - max(0, px - r) + 1;
+                    const float4 l = load_px(P.L, rowb + px, fmt);
+                    const float gu = __fmaf_rn(l.x, inv255, -cr), gv = __fmaf_rn(l.y, inv255, -cg);
+                    const float gw = __fmaf_rn(l.z, inv255, -cb);
+                    const float num = __fmaf_rn(S[0], gu, __fmaf_rn(S[1], gv, __fmaf_rn(S[2], gw, S[3])));
+                    out[(size_t)(py - Ry0) * pitch + (px - Rx0)] = __fdiv_rn(num, __fmul_rn((float)(nx * ny), q2));
+                }
+            }
+        }
+    }
+}
+
+// shared-memory floats of one warp's rings for M and K at most mwp and kwp wide
+__host__ __device__ inline int warp_ring_floats(int r, int mwp, int kwp) { return (2 * r + 1) * (mwp + 4 * kwp); }
+
+
+
+// ---------------------------------------------------------------------------
 // A5: expansion-move graph of one node
 // ---------------------------------------------------------------------------
 struct NodeCaps {
@@ -1012,11 +1347,18 @@ __device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *
                            float phi_al, int x0, int y0, int w, int h, int ix, int iy, NodeCaps &o) {
     const int H = P.H, W = P.W;
     const int pu = x0 + ix, pv = y0 + iy;
+    const float fu = (float)pu, fv = (float)pv;
     const float4 fp = lab[(size_t)pv * W + pu];
     int U0 = q_cost(fp.w, kp.S), U1 = q_cost(phi_al, kp.S);
     long long cst = 0;
     int ncl = 0;
     const float4 wp = P.wfw[(size_t)pv * W + pu];
+    // psi(f_p, alpha) on every pair of p: its coefficient differences and its value
+    // at p are shared by the 8 neighbours (the term of a backward pair (q, p) with
+    // alpha at q is psi(f_p, alpha) on the same pair: each label is evaluated at
+    // both ends, and the differences are antisymmetric bit for bit)
+    const DDCoef dpa = dd_coef(fp, al);
+    const float dpa_p = dd_eval(dpa, fu, fv);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int d = k & 3;
@@ -1024,16 +1366,20 @@ __device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *
         if (fwd) o.k[d] = 0;
         const int qu = pu + dir_dx(k), qv = pv + dir_dy(k);
         if (qu < 0 || qu >= W || qv < 0 || qv >= H) continue;
+        const float gu = (float)qu, gv = (float)qv;
         const float wl = fwd ? comp(wp, d) : comp(P.wfw[(size_t)qv * W + qu], d);
-        const float4 fq = lab[(size_t)qv * W + qu];
         const bool qin = qu >= x0 && qu < x0 + w && qv >= y0 && qv < y0 + h;
         if (!qin) {
-            U0 += q_psi(wl, kp.tau_dis, kp.S, fp, fq, pu, pv, qu, qv);
-            U1 += q_psi(wl, kp.tau_dis, kp.S, al, fq, pu, pv, qu, qv);
+            const float4 fq = lab[(size_t)qv * W + qu];
+            const DDCoef dpq = dd_coef(fp, fq), daq = dd_coef(al, fq);
+            U0 += q_of(wl, kp.tau_dis, kp.S, dd_eval(dpq, fu, fv), dd_eval(dpq, gu, gv));
+            U1 += q_of(wl, kp.tau_dis, kp.S, dd_eval(daq, fu, fv), dd_eval(daq, gu, gv));
         } else if (fwd) {
-            int A = q_psi(wl, kp.tau_dis, kp.S, fp, fq, pu, pv, qu, qv);
-            const int B = q_psi(wl, kp.tau_dis, kp.S, fp, al, pu, pv, qu, qv);
-            const int C = q_psi(wl, kp.tau_dis, kp.S, al, fq, pu, pv, qu, qv);
+            const float4 fq = lab[(size_t)qv * W + qu];
+            const DDCoef dpq = dd_coef(fp, fq), daq = dd_coef(al, fq);
+            int A = q_of(wl, kp.tau_dis, kp.S, dd_eval(dpq, fu, fv), dd_eval(dpq, gu, gv));
+            const int B = q_of(wl, kp.tau_dis, kp.S, dpa_p, dd_eval(dpa, gu, gv));
+            const int C = q_of(wl, kp.tau_dis, kp.S, dd_eval(daq, fu, fv), dd_eval(daq, gu, gv));
             if (A > B + C) {
                 A = B + C;
                 ++ncl;
@@ -1044,7 +1390,7 @@ __device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *
         } else {
             // backward neighbour q: the pair (q, p) is forward from q, whose C
             // term psi(alpha at q, f_p at p) lands on p's unary with a minus sign
-            U1 -= q_psi(wl, kp.tau_dis, kp.S, al, fp, qu, qv, pu, pv);
+            U1 -= q_of(wl, kp.tau_dis, kp.S, dd_eval(dpa, gu, gv), dpa_p);
         }
     }
     const int m = min(U0, U1);
@@ -1299,10 +1645,50 @@ struct CutCount {
     int rounds, relabels, levels;
 };
 
+// One push of node i with e > 0 excess at height hu: along admissible edges (to
+// a neighbour one level lower) as far as the residual capacities allow, then,
+// with excess left and no admissible edge, a relabel from the heights read here.
+// All loads come first (independent), the pushes are decided in registers, and
+// the updates are fire-and-forget shared atomics (a neighbour may push into i's
+// reverse edges or excess at the same time; it only ever adds).  A stale
+// height read only costs extra rounds: the global relabel restores exact
+// heights and decides termination.
+__device__ __forceinline__ void push_node(int n, int w, int *res, int *v, uint16_t *hh, int i, int e, int hu) {
+    int r[8], hn[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = res[k * n + i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? (int)hh[i + dir_off(k, w)] : (int)kInf;
+    int left = e, mh = kInf;
+    int d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        d[k] = 0;
+        if (r[k] > 0 && hn[k] + 1 == hu && left > 0) {
+            d[k] = min(left, r[k]);
+            left -= d[k];
+        }
+        if (r[k] - d[k] > 0) mh = min(mh, hn[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (d[k] == 0) continue;
+        const int j = i + dir_off(k, w);
+        atomicSub(&res[k * n + i], d[k]);
+        atomicAdd(&res[(k ^ 4) * n + j], d[k]);
+        atomicAdd(&v[j], d[k]);
+    }
+    if (left != e) atomicSub(&v[i], e - left);
+    if (left > 0) hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
+}
+
 // Maximum preflow.  On return (LEM_OK) hh[i] != kInf exactly for the nodes that
 // reach the sink in the residual graph: the minimal sink side of the cut.
-// Each round first compacts the active nodes (excess, finite height) into a
-// list, so warps only run the push path for nodes that have work.
+// Regions of at most two nodes per thread: each thread pushes its own active
+// nodes every round, and one barrier (which also reduces "any node was active")
+// ends the round.  Larger regions first compact the active nodes (excess,
+// finite height) into a list each round, so warps only run the push path for
+// nodes that have work.
 //   list: n 16-bit entries; shares storage with the relabel's bitplanes
 __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
                            int gr_interval, CutCount &cc) {
@@ -1324,6 +1710,32 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
     bool act = relabel();
     ++cc.relabels;
     int rounds = 0;
+    if (n <= 2 * nt) {
+        while (act) {
+            if (rounds >= max_rounds) {
+                cc.rounds += rounds;
+                return LEM_ERR_MAXFLOW_LIMIT;
+            }
+            int any = 0;
+            for (int i = tid; i < n; i += nt) {
+                const int e = v[i];
+                const int hu = hh[i];
+                if (e > 0 && hu != kInf) {
+                    any = 1;
+                    push_node(n, w, res, v, hh, i, e, hu);
+                }
+            }
+            ++rounds;
+            // a round with no active node, or the periodic point, hands over to an
+            // exact global relabel (which also decides termination)
+            if (!__syncthreads_or(any) || rounds % gr_interval == 0) {
+                act = relabel();
+                ++cc.relabels;
+            }
+        }
+        cc.rounds += rounds;
+        return LEM_OK;
+    }
     while (act) {
         if (rounds >= max_rounds) {
             cc.rounds += rounds;
@@ -1331,20 +1743,6 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
         }
         if (tid == 0) s_cnt = 0;
         __syncthreads();
-        if (n < 2 * nt) {
-            // small regions: one node per thread
-            for (int base = 0; base < n; base += nt) {
-                const int i = base + tid;
-                const bool a = i < n && v[i] > 0 && hh[i] != kInf;
-                const uint32_t m = __ballot_sync(0xffffffffu, a);
-                if (m) {
-                    int pos = 0;
-                    if (lane == 0) pos = atomicAdd(&s_cnt, __popc(m));
-                    pos = __shfl_sync(0xffffffffu, pos, 0);
-                    if (a) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
-                }
-            }
-        } else
         // four consecutive nodes per thread (one 16-byte load of v, one 8-byte
         // load of hh), warp-aggregated appends
         for (int base = 0; base < n; base += 4 * nt) {
@@ -1383,39 +1781,7 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
         const int cnt = s_cnt;
         for (int q = tid; q < cnt; q += nt) {
             const int i = list[q];
-            const int e = v[i];
-            const int hu = hh[i];
-            // all loads first (independent), then the pushes decided in
-            // registers, then fire-and-forget atomics
-            int r[8], hn[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) r[k] = res[k * n + i];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? (int)hh[i + dir_off(k, w)] : (int)kInf;
-            int left = e, mh = kInf;
-            int d[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                d[k] = 0;
-                if (r[k] > 0 && hn[k] + 1 == hu && left > 0) {
-                    d[k] = min(left, r[k]);
-                    left -= d[k];
-                }
-                if (r[k] - d[k] > 0) mh = min(mh, hn[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (d[k] == 0) continue;
-                const int j = i + dir_off(k, w);
-                atomicSub(&res[k * n + i], d[k]);
-                atomicAdd(&res[(k ^ 4) * n + j], d[k]);
-                atomicAdd(&v[j], d[k]);
-            }
-            if (left != e) atomicSub(&v[i], e - left);
-            // excess left and no admissible edge: relabel from the heights read
-            // above (a stale read only costs extra rounds; the global relabel
-            // restores exact heights)
-            if (left > 0) hh[i] = (mh >= n + 1) ? kInf : (uint16_t)(mh + 1);
+            push_node(n, w, res, v, hh, i, v[i], hh[i]);
         }
         ++rounds;
         __syncthreads();
@@ -1572,6 +1938,23 @@ __device__ void expand_move(const DevPlanes &P, const KParams &kp, float4 *lab, 
     __syncthreads();
 }
 
+// kind of proposal t of a visit (the order of Algorithm 2 with the learned
+// proposer's map candidates): 0 propagation, 1 RANSAC, 2 map, 3 perturbation
+__device__ __forceinline__ int proposal_kind(const Level &lv, int kc, int t) {
+    return t < lv.k_prop ? 0 : (t < lv.k_prop + lv.k_rans ? 1 : (t < lv.k_prop + lv.k_rans + kc ? 2 : 3));
+}
+
+// block sums of the per-kind switched-pixel counts into the counters (all threads)
+__device__ void add_accepted(const long long (&acck)[4], long long *red, Counters *ctr) {
+    long long tot = 0;
+    for (int k = 0; k < 4; ++k) {
+        const long long s = block_sum_ll(acck[k], red);
+        tot += s;
+        if (threadIdx.x == 0 && s) atomicAdd(&ctr->accepted_kind[k], (unsigned long long)s);
+    }
+    if (threadIdx.x == 0) atomicAdd(&ctr->accepted, (unsigned long long)tot);
+}
+
 __device__ __forceinline__ bool same_label(float4 a, float4 b) {
     return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y) &&
            __float_as_uint(a.z) == __float_as_uint(b.z);
@@ -1629,7 +2012,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     CutSmem cs = cut_layout(smf, n);
-    long long acc = 0, hits = 0;
+    long long acck[4] = {0, 0, 0, 0}, hits = 0;
     CutCount cc{0, 0, 0};
     if constexpr (SPEC) {
         float *phiB = phiB_all + pd.off;
@@ -1648,7 +2031,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
         }
         region_unary(P, kp, x0, y0, w, h, a1.x, a1.y, a1.z, smf, phiA + (size_t)y0 * W + x0, W);
         cluster_sync_all();
-        expand_move(P, kp, lab, phiA, a1, x0, y0, w, h, cs, cc, acc, hits);
+        expand_move(P, kp, lab, phiA, a1, x0, y0, w, h, cs, cc, acck[0], hits);
         if (threadIdx.x == 0) {
             const float4 a2 = propose(lab, W, st2, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
             s_alpha[1] = a2;
@@ -1664,7 +2047,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
         const int src = s_src;
         if (src == 2)  // (not reachable: the first move sets f_r2 to alpha_1 or keeps it)
             region_unary(P, kp, x0, y0, w, h, a2.x, a2.y, a2.z, smf, phiA + (size_t)y0 * W + x0, W);
-        expand_move(P, kp, lab, src == 1 ? phiB : phiA, a2, x0, y0, w, h, cs, cc, acc, hits);
+        expand_move(P, kp, lab, src == 1 ? phiB : phiA, a2, x0, y0, w, h, cs, cc, acck[0], hits);
     } else {
         // outer perturbation sizes of this iteration, copied into Algorithm 2
         double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
@@ -1704,16 +2087,163 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
                 const float4 al = s_alpha[t - t0];
                 region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
                 // (region_unary ends with a barrier; its shared memory is reused below)
-                expand_move(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acc, hits);
+                expand_move(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acck[proposal_kind(lv, kc, t)], hits);
             }
         }
     }
     const int nprop_all = lv.k_prop + lv.k_rans + (prop ? lv.k_cnn : 0) + lv.k_rand;
-    acc = block_sum_ll(acc, red);
+    add_accepted(acck, red, ctr);
     if (threadIdx.x == 0) {
-        atomicAdd(&ctr->accepted, (unsigned long long)acc);
         atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
         atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop_all);
+        atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
+        atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
+        atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched visits (K >= 2 candidates per visit, guided-filter data term, no
+// RANSAC proposal): the candidates of a visit are all drawn from the labels at
+// its start, so their data terms are independent of the visit's moves.  One
+// visit of a (level, group) is then two launches:
+//   k_visit_unary : one warp per (region, candidate): draws the candidate and
+//                   computes its data term (warp_unary_gf) into plane t of phiK;
+//   k_visit_cut   : one CTA per region: the K moves in candidate order, each
+//                   against the labels the previous one left (graph, terminal
+//                   reduction, push-relabel, commit).
+// The moves, and so the labels, are those of the one-kernel visit; only the
+// data term's summation differs (exact fixed-point sums here).
+// ---------------------------------------------------------------------------
+// the candidate of proposal t of a visit (lane 0 of the calling warp draws it;
+// every lane gets it): propagation, map candidates, then perturbations whose
+// size halves per perturbation of the region's Algorithm 2 call
+__device__ __forceinline__ float4 visit_candidate(const KParams &kp, const Level &lv, int level, int iter, int ci,
+                                                  int cj, int t, const float4 *lab, const float4 *prop, int W, int cx0,
+                                                  int cy0, int cw, int chh) {
+    float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned long long stream = proposal_stream(kp.seed, iter, level, ci, cj, t);
+        const int kc = prop ? lv.k_cnn : 0;
+        if (t < lv.k_prop) {
+            al = propose(lab, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+        } else if (t < lv.k_prop + kc) {
+            al = propose(prop, W, stream, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
+        } else {
+            const int np = t - lv.k_prop - kc;  // perturbations before this one
+            const double rd = __dmul_rn(__dmul_rn(0.5 * (kp.disp_max - kp.disp_min), ldexp(1.0, -iter)),
+                                        ldexp(1.0, -np));
+            const double rn = __dmul_rn(ldexp(1.0, -iter), ldexp(1.0, -np));
+            al = propose(lab, W, stream, cx0, cy0, cw, chh, true, rd, rn, kp.disp_min, kp.disp_max);
+        }
+    }
+    al.x = __shfl_sync(kFull, al.x, 0);
+    al.y = __shfl_sync(kFull, al.y, 0);
+    al.z = __shfl_sync(kFull, al.z, 0);
+    al.w = 0.f;
+    return al;
+}
+
+// region of an item and its centre cell
+struct ItemGeom {
+    int x0, y0, w, h, cx0, cy0, cw, chh;
+};
+__device__ __forceinline__ ItemGeom item_geom(int ci, int cj, int s, int H, int W) {
+    ItemGeom g;
+    g.x0 = max(0, (ci - 1) * s);
+    g.y0 = max(0, (cj - 1) * s);
+    g.w = min(W, (ci + 2) * s) - g.x0;
+    g.h = min(H, (cj + 2) * s) - g.y0;
+    g.cx0 = ci * s;
+    g.cy0 = cj * s;
+    g.cw = min(W, g.cx0 + s) - g.cx0;
+    g.chh = min(H, g.cy0 + s) - g.cy0;
+    return g;
+}
+
+// the planes of pair pd (the batch's arrays offset to its pixels)
+__device__ __forceinline__ void pair_planes(DevPlanes &P, KParams &kp, const PairDesc &pd) {
+    P.H = pd.H;
+    P.W = pd.W;
+    P.L = px_offset(P.L, pd.off, P.fmt);
+    P.R = px_offset(P.R, pd.off, P.fmt);
+    P.gst += 3 * pd.off;
+    P.wfw += pd.off;
+    kp.seed = pd.seed;
+    kp.disp_min = pd.disp_min;
+    kp.disp_max = pd.disp_max;
+}
+
+//   units: n_items * nK, unit u = (item u / nK, proposal t0 + u % nK)
+//   phiK : nK planes of plane_stride floats (every pair's pixels); alphaK[u]
+template <int NC>
+__global__ void __launch_bounds__(128) k_visit_unary(DevPlanes P, KParams kp, Level lv, int level, int iter,
+                                                     const int *iter_dev, const PairDesc *pairs, const int4 *items,
+                                                     int n_items, int t0, int nK, const float4 *lab_all,
+                                                     float *phiK, long long plane_stride, const float4 *prop_all,
+                                                     float4 *alphaK, int mwp, int kwp) {
+    extern __shared__ __align__(16) float smw[];
+    const int warp = threadIdx.x >> 5;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= n_items * nK) return;  // the whole warp leaves together
+    const int it = unit / nK, t = unit - it * nK;
+    const int4 item = items[it];
+    const PairDesc pd = pairs[item.x];
+    pair_planes(P, kp, pd);
+    if (iter < 0) iter = *iter_dev;
+    const ItemGeom g = item_geom(item.y, item.z, lv.s, P.H, P.W);
+    const float4 *lab = lab_all + pd.off;
+    const float4 *prop = prop_all ? prop_all + pd.off : nullptr;
+    const float4 al = visit_candidate(kp, lv, level, iter, item.y, item.z, t0 + t, lab, prop, P.W, g.cx0, g.cy0, g.cw,
+                                      g.chh);
+    if ((threadIdx.x & 31) == 0) alphaK[unit] = al;
+    float *ring = smw + (size_t)warp * warp_ring_floats(kp.r, mwp, kwp);
+    float *out = phiK + (size_t)t * plane_stride + pd.off + (size_t)g.y0 * P.W + g.x0;
+    warp_unary_gf<NC>(P, kp, g.x0, g.y0, g.w, g.h, al.x, al.y, al.z, ring, mwp, kwp, out, P.W);
+}
+
+// lem_unary_batch on handles with batched visits: the warp data term of the
+// expansion path, one warp per (region, label)
+template <int NC>
+__global__ void __launch_bounds__(128) k_unary_batch_warp(DevPlanes P, KParams kp, const int4 *regions,
+                                                          const int64_t *offsets, int n_regions, int K,
+                                                          const float *labels, float *costs, int mwp, int kwp) {
+    extern __shared__ __align__(16) float smw[];
+    const int warp = threadIdx.x >> 5;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= n_regions * K) return;
+    const int i = unit / K, k = unit - i * K;
+    const int4 R = regions[i];
+    const float *l = labels + (size_t)unit * 3;
+    float *out = costs + offsets[i] + (int64_t)k * R.z * R.w;
+    warp_unary_gf<NC>(P, kp, R.x, R.y, R.z, R.w, l[0], l[1], l[2],
+                      smw + (size_t)warp * warp_ring_floats(kp.r, mwp, kwp), mwp, kwp, out, R.z);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT)
+    k_visit_cut(DevPlanes P, KParams kp, Level lv, const PairDesc *pairs, const int4 *items, int t0, int nK, int kc,
+                float4 *lab_all, const float *phiK, long long plane_stride, const float4 *alphaK, Counters *ctr) {
+    extern __shared__ __align__(16) float smf[];
+    __shared__ long long red[33];
+    const int4 item = items[blockIdx.x];
+    const PairDesc pd = pairs[item.x];
+    pair_planes(P, kp, pd);
+    const ItemGeom g = item_geom(item.y, item.z, lv.s, P.H, P.W);
+    const int n = g.w * g.h;
+    float4 *lab = lab_all + pd.off;
+    CutSmem cs = cut_layout(smf, n);
+    long long acck[4] = {0, 0, 0, 0}, hits = 0;
+    CutCount cc{0, 0, 0};
+    for (int t = 0; t < nK; ++t) {
+        const float4 al = alphaK[(size_t)blockIdx.x * nK + t];
+        expand_move(P, kp, lab, phiK + (size_t)t * plane_stride + pd.off, al, g.x0, g.y0, g.w, g.h, cs, cc,
+                    acck[proposal_kind(lv, kc, t0 + t)], hits);
+    }
+    add_accepted(acck, red, ctr);
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
+        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nK);
         atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
         atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
         atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
@@ -2451,7 +2981,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int i0 = grid_range_start(n, c, G), i1 = grid_range_start(n, c + 1, G);
     double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
     double rn = ldexp(1.0, -iter);
-    long long acc = 0, hits = 0;
+    long long acck[4] = {0, 0, 0, 0}, hits = 0;
     CutCount cc{0, 0, 0};
     const int kc = prop ? lv.k_cnn : 0, kr = lv.k_rans;
     const int nprop = lv.k_prop + kr + kc + lv.k_rand;
@@ -2518,7 +3048,7 @@ __global__ void __launch_bounds__(NT, 1)
                     const int iy = j / w, ix = j - iy * w;
                     const size_t p = (size_t)(y0 + iy) * W + x0 + ix;
                     lab[p] = make_float4(al.x, al.y, al.z, phiA[p]);
-                    ++acc;
+                    ++acck[proposal_kind(lv, kc, t)];
                 }
             } else {
                 ++hits;
@@ -2530,9 +3060,8 @@ __global__ void __launch_bounds__(NT, 1)
             if (!(ok = region_sync(x))) break;
         }
     }
-    acc = block_sum_ll(acc, red);
+    add_accepted(acck, red, ctr);
     if (threadIdx.x == 0) {
-        atomicAdd(&ctr->accepted, (unsigned long long)acc);
         if (c == 0) {
             // a region whose barriers gave up counts as a cut that did not finish
             atomicAdd(&ctr->limit_hits, (unsigned long long)(hits + (ok ? 0 : 1)));
@@ -2769,6 +3298,152 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
         return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
                               st);
     return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm, st);
+}
+
+namespace {
+// filtering-region width and per-warp ring bytes of the warp data term at a level
+struct VisitShape {
+    int rw, rh, nc, mwp, kwp;
+    size_t ring_bytes;
+    int warps;  // most warps (units) per CTA of k_visit_unary
+};
+VisitShape visit_shape(const KParams &kp, const Level &lv, int max_w, int max_h) {
+    VisitShape v;
+    v.rw = std::min(max_w, 3 * lv.s);
+    v.rh = std::min(max_h, 3 * lv.s);
+    v.mwp = std::min(max_w, v.rw + 4 * kp.r);
+    v.kwp = std::min(max_w, v.rw + 2 * kp.r);
+    v.nc = (v.mwp + 31) / 32;
+    v.ring_bytes = sizeof(float) * (size_t)warp_ring_floats(kp.r, v.mwp, v.kwp);
+    v.warps = (int)std::min<size_t>(4, (227 * 1024) / v.ring_bytes);
+    return v;
+}
+
+// warps per CTA of a warp data-term launch of `units` units: up to `most` (the
+// shared-memory limit), fewer when the launch would not give every SM two CTAs
+int warps_per_cta(int units, int most) {
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    int w = std::max(1, std::min(4, most));
+    while (w > 1 && (units + w - 1) / w < 2 * nsm) w >>= 1;
+    return w;
+}
+
+template <int NC>
+cudaError_t unary_batch_warp_nc(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
+                                int n_regions, int K, const float *labels, float *costs, int mwp, int kwp, int most,
+                                cudaStream_t st) {
+    const size_t ring = sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp);
+    const int units = n_regions * K, w = warps_per_cta(units, most);
+    cudaError_t e = set_smem((const void *)k_unary_batch_warp<NC>, ring * w);
+    if (e != cudaSuccess) return e;
+    k_unary_batch_warp<NC><<<(units + w - 1) / w, 32 * w, ring * w, st>>>(P, kp, regions, offsets, n_regions, K,
+                                                                          labels, costs, mwp, kwp);
+    return cudaGetLastError();
+}
+
+template <int NC>
+cudaError_t visit_unary_nc(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                           const int *iter_dev, const PairDesc *pairs, const int4 *items, int n_items, int t0, int nK,
+                           const float4 *lab, float *phiK, long long plane_stride, const float4 *prop, float4 *alphaK,
+                           int mwp, int kwp, int most, cudaStream_t st) {
+    const size_t ring = sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp);
+    const int units = n_items * nK, w = warps_per_cta(units, most);
+    cudaError_t e = set_smem((const void *)k_visit_unary<NC>, ring * w);
+    if (e != cudaSuccess) return e;
+    k_visit_unary<NC><<<(units + w - 1) / w, 32 * w, ring * w, st>>>(
+        P, kp, lv, level, iter, iter_dev, pairs, items, n_items, t0, nK, lab, phiK, plane_stride, prop, alphaK, mwp,
+        kwp);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t visit_cut_nt(const DevPlanes &P, const KParams &kp, const Level &lv, const PairDesc *pairs,
+                         const int4 *items, int n_items, int t0, int nK, int kc, float4 *lab, const float *phiK,
+                         long long plane_stride, const float4 *alphaK, Counters *ctr, size_t smem, cudaStream_t st) {
+    cudaError_t e = set_smem((const void *)k_visit_cut<NT>, smem);
+    if (e != cudaSuccess) return e;
+    k_visit_cut<NT><<<n_items, NT, smem, st>>>(P, kp, lv, pairs, items, t0, nK, kc, lab, phiK, plane_stride, alphaK,
+                                               ctr);
+    return cudaGetLastError();
+}
+}  // namespace
+
+bool visit_split(const KParams &kp, const Level &lv, int max_w, int max_h) {
+    if (kp.visit < 2 || kp.bf || lv.k_rans > 0) return false;
+    const VisitShape v = visit_shape(kp, lv, max_w, max_h);
+    if ((long long)v.rw * v.rh > LEM_MAX_REGION_NODES || cut_smem_bytes(v.rw, v.rh) > 227 * 1024) return false;
+    return v.nc <= 4 && v.warps >= 1;
+}
+
+bool unary_warp_fits(const KParams &kp, int W, int max_w) {
+    const int mwp = std::min(W, max_w + 4 * kp.r), kwp = std::min(W, max_w + 2 * kp.r);
+    return !kp.bf && (mwp + 31) / 32 <= 4 && sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp) <= 227 * 1024;
+}
+
+cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const int4 *regions,
+                                    const int64_t *offsets, int n_regions, int K, int max_w, const float *labels,
+                                    float *costs, cudaStream_t st) {
+    const int mwp = std::min(P.W, max_w + 4 * kp.r), kwp = std::min(P.W, max_w + 2 * kp.r);
+    const int nc = (mwp + 31) / 32;
+    const int most =
+        (int)std::min<size_t>(4, (227 * 1024) / (sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp)));
+#define LEM_UBW(NC_) unary_batch_warp_nc<NC_>(P, kp, regions, offsets, n_regions, K, labels, costs, mwp, kwp, most, st)
+    switch (nc) {
+        case 1: return LEM_UBW(1);
+        case 2: return LEM_UBW(2);
+        case 3: return LEM_UBW(3);
+        case 4: return LEM_UBW(4);
+        default: return cudaErrorInvalidConfiguration;
+    }
+#undef LEM_UBW
+}
+
+int visit_cut_threads(int nodes) { return nodes <= 400 ? 64 : (nodes <= 2500 ? 256 : 512); }
+
+cudaError_t launch_visit_unary(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
+                               const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
+                               int n_items, int t0, int nK, const float4 *lab, float *phiK, long long plane_stride,
+                               const float4 *prop, float4 *alphaK, cudaStream_t st) {
+    if (n_items == 0 || nK < 1) return cudaSuccess;
+    const VisitShape v = visit_shape(kp, lv, max_w, max_h);
+#define LEM_VISIT_UNARY(NC_)                                                                                      \
+    visit_unary_nc<NC_>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, t0, nK, lab, phiK, plane_stride, \
+                        prop, alphaK, v.mwp, v.kwp, v.warps, st)
+    switch (v.nc) {
+        case 1: return LEM_VISIT_UNARY(1);
+        case 2: return LEM_VISIT_UNARY(2);
+        case 3: return LEM_VISIT_UNARY(3);
+        case 4: return LEM_VISIT_UNARY(4);
+        default: return cudaErrorInvalidConfiguration;
+    }
+#undef LEM_VISIT_UNARY
+}
+
+cudaError_t launch_visit_cut(const DevPlanes &P, const KParams &kp, const Level &lv, const PairDesc *pairs,
+                             int max_w, int max_h, const int4 *items, int n_items, int t0, int nK, int kc,
+                             float4 *lab, const float *phiK, long long plane_stride, const float4 *alphaK,
+                             Counters *ctr, cudaStream_t st) {
+    if (n_items == 0 || nK < 1) return cudaSuccess;
+    const VisitShape v = visit_shape(kp, lv, max_w, max_h);
+    const size_t csm = cut_smem_bytes(v.rw, v.rh);
+    const int nt = lv.threads > 0 ? lv.threads : visit_cut_threads(v.rw * v.rh);
+#define LEM_VISIT_CUT(NT_) \
+    visit_cut_nt<NT_>(P, kp, lv, pairs, items, n_items, t0, nK, kc, lab, phiK, plane_stride, alphaK, ctr, csm, st)
+    switch (nt) {
+        case 32: return LEM_VISIT_CUT(32);
+        case 64: return LEM_VISIT_CUT(64);
+        case 128: return LEM_VISIT_CUT(128);
+        case 256: return LEM_VISIT_CUT(256);
+        case 512: return LEM_VISIT_CUT(512);
+        case 1024: return LEM_VISIT_CUT(1024);
+        default: return cudaErrorInvalidValue;
+    }
+#undef LEM_VISIT_CUT
 }
 
 bool expand_uses_grid(const KParams &kp, const Level &lv, int max_w, int max_h) {

@@ -44,6 +44,7 @@ class lem_params(C.Structure):
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
         ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double), ("cluster_visits", C.c_int),
+        ("split_visits", C.c_int),
     ]
 
 
@@ -60,10 +61,19 @@ class lem_region(C.Structure):
     _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("w", C.c_int), ("h", C.c_int)]
 
 
+LEM_KERNEL_EXPAND, LEM_KERNEL_VISIT_UNARY, LEM_KERNEL_VISIT_CUT, LEM_KERNEL_GRID = 0, 1, 2, 3
+KERNEL_KIND_NAMES = ("k_expand_group", "k_visit_unary", "k_visit_cut", "k_expand_grid")
+
+
+class lem_kernel_times(C.Structure):
+    _fields_ = [("ms", (C.c_double * 4) * 3), ("launches", (C.c_int64 * 4) * 3)]
+
+
 class lem_stats(C.Structure):
     _fields_ = [("energy_q", C.c_int64), ("energy", C.c_double), ("evals", C.c_int64), ("accepted", C.c_int64),
                 ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32),
-                ("pr_rounds", C.c_int64), ("pr_global_relabels", C.c_int64), ("pr_bfs_levels", C.c_int64)]
+                ("pr_rounds", C.c_int64), ("pr_global_relabels", C.c_int64), ("pr_bfs_levels", C.c_int64),
+                ("accepted_by_kind", C.c_int64 * 4)]
 
 
 _lib = None
@@ -134,6 +144,12 @@ def lib():
         L.lem_autotune.restype = C.c_int
         L.lem_v3_params.argtypes = [P(lem_params), C.c_int]
         L.lem_v3_params.restype = C.c_int
+        L.lem_measure_peaks.argtypes = [vp, P(C.c_double), P(C.c_double)]
+        L.lem_measure_peaks.restype = C.c_int
+        L.lem_set_kernel_timing.argtypes = [H, C.c_int]
+        L.lem_set_kernel_timing.restype = C.c_int
+        L.lem_get_kernel_times.argtypes = [H, P(lem_kernel_times)]
+        L.lem_get_kernel_times.restype = C.c_int
         for name in ("lem_set_proposals", "lem_get_proposals", "lem_cnn_create", "lem_cnn_destroy",
                      "lem_cnn_get_params", "lem_cnn_set_params", "lem_cnn_forward", "lem_cnn_gradients",
                      "lem_cnn_train_step", "lem_cnn_features", "lem_cnn_targets", "lem_cnn_propose"):
@@ -294,6 +310,16 @@ def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, 
                              stream):
     return lib().lem_mincut_batch_noalloc(_regions(regions), len(regions), tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr,
                                           status_ptr, max_rounds, gr_interval, stream)
+
+
+def lem_measure_peaks(stream=None):
+    """(FP32 FMA TFLOP/s, shared-memory GB/s) of the current device, measured by the
+    library's microbenchmarks on `stream` (a torch stream, a raw handle or None)."""
+    st = getattr(stream, "cuda_stream", stream)
+    f = C.c_double()
+    b = C.c_double()
+    _check(lib().lem_measure_peaks(C.c_void_p(st), C.byref(f), C.byref(b)))
+    return f.value, b.value
 
 
 def lem_evals_per_iteration(h) -> int:
@@ -569,6 +595,17 @@ class Stereo:
 
     def evals_per_iteration(self):
         return lem_evals_per_iteration(self.h)
+
+    def set_kernel_timing(self, on=True):
+        """Events between the expansion launches of every outer iteration (lem_set_kernel_timing)."""
+        self.check(lib().lem_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        """{(level, kernel name): (ms, launches)} of the last outer iteration (lem_get_kernel_times)."""
+        t = lem_kernel_times()
+        self.check(lib().lem_get_kernel_times(self.h, C.byref(t)))
+        return {(l, n): (t.ms[l][k], t.launches[l][k]) for l in range(3) for k, n in enumerate(KERNEL_KIND_NAMES)
+                if t.launches[l][k]}
 
     @_on_own_stream
     def proposals_of(self, it, level, cells, nprop):

@@ -15,13 +15,10 @@ from tests.conftest import TINY_PARAMS
 
 pytestmark = pytest.mark.gpu
 
-PHI_TOL = 1e-4
 BF_TINY = dict(TINY_PARAMS, data_term=1, bf_gamma=10.0, lam=20.0)
 
 
-def _rel_err(gpu, ref):
-    gpu = np.asarray(gpu, np.float64)
-    return np.abs(gpu - ref) / np.maximum(1.0, np.abs(ref))
+from tests.tolerance import PHI_TOL, rel_err as _rel_err, report  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -54,11 +51,13 @@ def test_bf_unary_tiny_all_regions(tiny_bf):
     labs[1, 1] = [0.0, 0.0, 2.5]
     labs[2, 0] = [1.7, -0.8, -40.0]
     costs = g.unary(REGIONS, labs)
-    worst = 0.0
+    gl, rl = [], []
     for r, lab, c in zip(REGIONS, labs, costs):
         c = c.cpu().numpy()
         for k in range(K):
-            worst = max(worst, _rel_err(c[k], o.region_cost(*r, lab[k])).max())
+            gl.append(c[k])
+            rl.append(o.region_cost(*r, lab[k]))
+    worst = report("LE-BF phi, ragged tiny regions", gl, rl)
     assert worst <= PHI_TOL, worst
 
 
@@ -70,7 +69,7 @@ def test_bf_unary_is_the_window_sum(tiny_bf):
     c = g.unary([r], lab[None])[0][0].cpu().numpy()
     for (yy, xx) in [(0, 0), (5, 8), (3, 4)]:
         ref = o.phi_bf(lab[0], r[0] + xx, r[1] + yy)
-        assert abs(c[yy, xx] - ref) <= PHI_TOL * max(1.0, abs(ref))
+        assert _rel_err(c[yy, xx], ref) <= PHI_TOL
 
 
 def test_bf_initial_costs(tiny_bf):
@@ -79,8 +78,8 @@ def test_bf_initial_costs(tiny_bf):
     abc, _, cost = g.labels()
     lab, ocost = o.state()
     assert (abc.cpu().numpy() == lab).all()
-    err = _rel_err(cost.cpu().numpy(), ocost)
-    assert err.max() <= PHI_TOL, err.max()
+    worst = report("LE-BF initial cost cache", [cost.cpu().numpy()], [ocost])
+    assert worst <= PHI_TOL, worst
 
 
 def test_bf_unary_middlebury_shapes(torch_cuda):
@@ -94,10 +93,8 @@ def test_bf_unary_middlebury_shapes(torch_cuda):
     regions = [(150, 120, 75, 75), (0, 0, 45, 45), (405, 300, 45, 75), (435, 360, 15, 15), (100, 200, 15, 15)]
     labs = random_labels(19, len(regions), 375, 450, 60.0).reshape(len(regions), 1, 3)
     costs = g.unary(regions, labs)
-    worst = 0.0
-    for r, lab, c in zip(regions, labs, costs):
-        worst = max(worst, _rel_err(c[0].cpu().numpy(), o.region_cost(*r, lab[0])).max())
-    print(f"LE-BF phi rel err: max {worst:.3e}")
+    worst = report("LE-BF phi, 450x375 regions at r' = 10", [c[0].cpu().numpy() for c in costs],
+                   [o.region_cost(*r, lab[0]) for r, lab in zip(regions, labs)])
     assert worst <= PHI_TOL, worst
     st = g.iterate(1)
     assert st.maxflow_limit == 0 and st.evals == g.evals_per_iteration()
