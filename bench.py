@@ -1,20 +1,32 @@
 """Benchmark: pixel-label cost evaluations per second of local-expansion-move stereo.
 
+Headline workload: the 1500 x 1000 pair (disparities 0-400, ~40 slanted and
+curved segments), images stored in FP16, costs in FP32, every region of a cell
+group evaluated with 4 candidate labels per visit in one launch pair (the
+data terms of all candidates, then the moves), outer iterations replayed as
+CUDA graphs, launch configuration chosen by the library's autotuner.
+
 One step = one outer iteration of Algorithm 1 (3 grid levels x 16 disjoint
-groups, every alpha_ij-expansion evaluated, cut and committed) on the
-Middlebury-V2-shaped synthetic pair (450 x 375, disparities 0-60, cells
-5/15/25 px, 41 x 41 matching windows, FP32).  Steps continue one run from the
-random initialisation; warm-up steps run on a separate handle.  L2 is flushed
-between timed steps; each step is timed with CUDA events on the library's
-stream.
+groups).  A handle runs the method's 10 outer iterations (Sec. 4 settings) and
+no more: step i is iteration i mod 10 of handle i div 10, so every timed step is
+an iteration the method actually runs.  Warm-up iterations and the autotuner
+run on a separate handle.  L2 is flushed between timed steps; each step is timed
+with CUDA events on the library's stream, and the library records events
+between its launches (lem_set_kernel_timing) so the time of each kernel kind
+comes from the timed steps themselves.
 
-The launch configuration of every level is chosen by the library's autotuner
-on the warm-up handle (it changes only the time, never a label).  A second
-block measures the time to reach the plain method's energy: 10 iterations of
-the plain method give E_plain; the time to E <= 1.001 E_plain is taken for the
-plain method and for the method with learned proposals (when trained weights
-are present), CNN inference included.
-
+Beside the headline the JSON line carries:
+  * e2e        : whole jobs through the C ABI (pinned host images -> lem_create ->
+                 10 iterations -> host disparity);
+  * roofline   : the dominant kernel's algorithmic work over its time in the timed
+                 steps, against the FP32 FMA peak measured by the library's own
+                 microbenchmark (lem_measure_peaks) on this GPU;
+  * time_to_energy_ms / plain_ms / speedup : time to E <= 1.001 E_plain, E_plain
+                 the energy of the plain method (sequential proposals, FP32 images)
+                 after its 10 iterations, with learned proposals plus batched visits,
+                 against the plain method itself, on the same pair and GPU;
+  * cpu_baseline: the FP64 oracle on the host cores, one outer iteration of the
+                 same workload (per-iteration only).
 Prints one JSON line.  --impl reference times the CPU oracle instead.
 """
 from __future__ import annotations
@@ -31,12 +43,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "middlebury_450x375"
-PARAMS = dict(disp_max=60.0)          # everything else: the paper's values (lem_default_params)
+WORKLOAD = "large_1500x1000"
+DISP_MAX = 400.0
+ITERS_PER_HANDLE = 10                 # the method's outer iterations (Sec. 4)
 METRIC = "pixel-label cost evals/s"
-FP32_LANES_PER_SM = 128               # FP32 FMA lanes per SM (Blackwell)
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+
+
+def headline_params(lem):
+    """The headline configuration: the paper's settings, FP16 image storage, 4-candidate visits."""
+    return dict(disp_max=DISP_MAX, store_dtype=lem.LEM_STORE_F16, candidates_per_visit=4)
 
 
 def parse():
@@ -49,18 +64,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
-    ap.add_argument("--launch-config", default=None,
-                    help="fixed per-level configuration 'threads/gr_interval/strip_rows', each three "
-                         "comma-separated values (e.g. 256,512,512/16,16,16/8,32,16); skips the autotuner")
     ap.add_argument("--no-time-to-energy", action="store_true")
-    ap.add_argument("--no-proposer", action="store_true", help="skip the proposal-network timing")
-    ap.add_argument("--no-bf", action="store_true", help="skip the LE-BF variant timing")
-    ap.add_argument("--no-v3", action="store_true", help="skip the V3-settings timing (1500 x 1000)")
-    ap.add_argument("--no-large", action="store_true", help="skip the 1500 x 1000 FP16 batched timing")
-    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8", "v3", "lebf", "large"],
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra blocks (proposer, LE-BF, V3, 450x375)")
+    ap.add_argument("--mode", default="step", choices=["step", "proposer", "batch8", "v3", "lebf", "cnn_gain"],
                     help="proposer: time only the proposal network; batch8: the uneven batch of 8 pairs; "
-                         "v3: only the V3-settings block; lebf: only the LE-BF block (one JSON line each)")
+                         "v3 / lebf: one extra block; cnn_gain: learned proposals on held-out seeds "
+                         "(one JSON line each)")
     ap.add_argument("--batch-iters", type=int, default=10, help="outer iterations per pair in --mode batch8")
+    ap.add_argument("--seeds", type=int, default=20, help="held-out seeds of --mode cnn_gain")
     return ap.parse_args()
 
 
@@ -177,25 +189,24 @@ def algorithmic_flops(H, W, r, x0, y0, w, h):
     return 30 * mw * mh + 44 * kw * kh + 24 * w * h
 
 
-def launches_and_work(H, W, p):
+def iteration_work(H, W, p):
+    """Per level: pixel-label evals and data-term flops of one outer iteration (every
+    candidate of every region)."""
     r = p["gf_radius"]
-    out = []
+    out = {}
     for l in range(p["n_levels"]):
         s = p["cell"][l]
         nprop = p["k_prop"][l] + p["k_rand"][l]
-        groups = region_geometry(H, W, s)
-        for g in range(16):
-            regs = groups[g]
-            if not regs:
-                continue
-            evals = sum(w * h for (_, _, w, h) in regs) * nprop
-            flops = sum(algorithmic_flops(H, W, r, *R) for R in regs) * nprop
-            out.append(dict(level=l, group=g, evals=evals, flops=flops, regions=len(regs)))
+        evals = flops = 0
+        for regs in region_geometry(H, W, s).values():
+            evals += sum(w * h for (_, _, w, h) in regs) * nprop
+            flops += sum(algorithmic_flops(H, W, r, *R) for R in regs) * nprop
+        out[l] = dict(evals=evals, flops=flops)
     return out
 
 
 def kernel_source_sha():
-    """SHA-256 of the expansion kernel's sources: lem_kernels.cu followed by the internal
+    """SHA-256 of the expansion kernels' sources: lem_kernels.cu followed by the internal
     header it includes."""
     h = hashlib.sha256()
     for name in ("lem_kernels.cu", "lem_internal.h"):
@@ -218,41 +229,62 @@ def traffic_from_profile(kernel):
     return e.get("dram_bytes_per_launch")
 
 
+def measured_peaks(lem, stream):
+    """FP32 FMA TFLOP/s and shared-memory GB/s of this GPU from the library's
+    microbenchmarks, with the SM clocks sampled while they ran."""
+    import torch
+    dev = torch.cuda.current_device()
+    with ClockSampler(dev) as clk:
+        time.sleep(0.3)
+        fp32, smem = lem.lem_measure_peaks(stream)
+        fp32b, smemb = lem.lem_measure_peaks(stream)
+        time.sleep(0.3)
+    return {"fp32_tflops": max(fp32, fp32b), "smem_gbs": max(smem, smemb), "clocks": clk.summary(),
+            "how": "lem_measure_peaks: FMA chains on every SM (8 CTAs x 256 threads per SM) and 16-byte "
+                   "conflict-free shared loads (2 CTAs x 1024 threads per SM), best of 5 launches each"}
+
+
 # --- CPU oracle ------------------------------------------------------------------
 
-def cpu_oracle_baseline(pair, p, seed):
+ORACLE_PARAMS = dict(disp_max=DISP_MAX, visit=4)   # the headline schedule (images are FP64 in the oracle)
+
+
+def cpu_oracle_baseline(pair, seed):
     """The oracle, as it stands, on the host cores: one full outer iteration (iteration
-    0 from the random initialisation) of the same workload."""
+    0 from the random initialisation) of the headline workload, per-iteration only; and
+    on one host core, the first 2400 cells of group 0 of the finest level."""
     import oracle
-    o = oracle.Oracle(pair["left"], pair["right"], seed=seed, **PARAMS)
+    o = oracle.Oracle(pair["left"], pair["right"], seed=seed, **ORACLE_PARAMS)
     o.init_state()
     t = time.perf_counter()
     _, evals = o.iterate(0)
     dt = time.perf_counter() - t
-    # the same oracle on one host core, on a smaller sample: the first two groups of the
-    # finest level of iteration 1
-    o1 = oracle.Oracle(pair["left"], pair["right"], seed=seed, n_threads=1, **PARAMS)
+    o1 = oracle.Oracle(pair["left"], pair["right"], seed=seed, n_threads=1, **ORACLE_PARAMS)
     o1.put_state(*o.state())
+    H, W = pair["left"].shape[:2]
+    cells = oracle.group_cells(H, W, 5, 0)[:2400]
     t1 = time.perf_counter()
-    ev1 = sum(o1.expand_group(1, 0, grp)[1] for grp in (0, 1))
+    _, ev1 = o1.expand_cells(1, 0, cells)
     dt1 = time.perf_counter() - t1
     return {"value": evals / dt, "unit": METRIC, "cores": oracle.openmp_threads(), "kind": "oracle",
-            "sample": f"outer iteration 0 of {WORKLOAD} (all 48 level-group launches, {evals} evals), "
-                      f"{dt:.2f} s",
+            "sample": f"outer iteration 0 of {WORKLOAD} (4-candidate visits, all 48 level-group steps, "
+                      f"{evals} evals), {dt:.2f} s; per-iteration only",
             "one_core": {"value": ev1 / dt1, "unit": METRIC, "cores": 1,
-                         "sample": f"groups 0 and 1 of level 0, iteration 1 ({ev1} evals), {dt1:.2f} s"}}
+                         "sample": f"2400 cells of group 0 of level 0, iteration 1 ({ev1} evals), {dt1:.2f} s"}}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle timed on the host cores, one (level, group)
-    expansion per step, cycling through the 48 of an outer iteration."""
+    """--impl reference: the CPU oracle timed on the host cores on the headline
+    workload, one (level, group) step of the batched schedule per step, cycling
+    through the 48 of an outer iteration."""
     rank, world, dist = dist_init(args.gpus)
     if rank != 0:
         return
     import oracle
     from synth import workload_pair
     pair = workload_pair(WORKLOAD, args.seed)
-    o = oracle.Oracle(pair["left"], pair["right"], seed=args.seed + 1, **PARAMS)
+    H, W = pair["left"].shape[:2]
+    o = oracle.Oracle(pair["left"], pair["right"], seed=args.seed + 1, **ORACLE_PARAMS)
     o.init_state()
     nl = len(oracle.PAPER_DEFAULTS["cell"])
     seq = [(it, l, g) for it in range(1000) for l in range(nl) for g in range(16)]
@@ -272,15 +304,14 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "height": 375, "width": 450, "disp_max": 60, "cells": [5, 15, 25],
-                       "window": 41, "step": "one (level, group) expansion of the CPU oracle"},
+            "config": {"workload": WORKLOAD, "height": H, "width": W, "disp_max": DISP_MAX, "cells": [5, 15, 25],
+                       "window": 41, "candidates_per_visit": 4,
+                       "step": "one (level, group) step of the FP64 CPU oracle"},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} (level, group) expansions of outer iteration 0.."},
+                             "sample": f"{args.steps} (level, group) steps of outer iteration 0.. of {WORKLOAD}"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
-
-# --- GPU -------------------------------------------------------------------------
 
 def conv_flops_per_pixel():
     """Algorithmic flops of one forward pass per quarter-resolution pixel: 2 * 9 * Cin * Cout
@@ -335,18 +366,6 @@ def proposer_timing(lem, stream, reps=20):
             "note": "BF16 implicit-GEMM convolutions: forward and input gradient on tcgen05.mma (kind::f16, TMEM accumulator), weight gradient on mma.sync m16n8k16; FP32 accumulation"}
 
 
-def run_proposer_mode(args):
-    """--mode proposer: only the proposal-network timing, one JSON line."""
-    import torch
-    import __graft_entry__
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device")
-    __graft_entry__.build()
-    from paper_1603_08328_gb300 import lem
-    out = proposer_timing(lem, torch.cuda.current_stream())
-    print(json.dumps({"mode": "proposer", **out}), flush=True)
-
-
 def run_batch8_mode(args):
     """--mode batch8: 8 pairs from 640x480 to 2900x2000 (disparity 64-800), BF16 images,
     batched 4-candidate visits, learned proposals (k_cnn = 1 at the finest level) when
@@ -355,7 +374,8 @@ def run_batch8_mode(args):
         pair): aggregate evals/s;
       * one handle per pair, the pairs served one after another: per-pair latency
         (host images in, n iterations, host disparity out) p50 / p99 and aggregate.
-    Prints one JSON line."""
+    Both with one CTA per region and with work-queue launches (work_queue = 1, largest
+    regions first); the better batched throughput is `value`.  Prints one JSON line."""
     import numpy as np
     import torch
 
@@ -386,50 +406,57 @@ def run_batch8_mode(args):
     t0h.close()
     kw.update(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval), level_strip_rows=list(t.strip_rows))
 
-    # batched: one handle over all pairs
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g = lem.Stereo([p["left"] for p in pairs], [p["right"] for p in pairs], stream=stream, disp_ranges=ranges, **kw)
-    evals_it = g.evals_per_iteration()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(n_it):
-        iterate(g)
-    b.record(stream)
-    b.synchronize()
-    gpu_s = a.elapsed_time(b) / 1e3
-    disp = g.labels("all")[1].cpu().numpy()
-    batch_job_s = time.perf_counter() - t0
-    st = g.iterate(0)
-    assert st.maxflow_limit == 0
-    g.close()
-
-    # served one by one: per-pair latency, host images in and host disparity out
-    lat, evals_total = [], 0
-    for p, rg in zip(pairs, ranges):
-        H, W = p["left"].shape[:2]
-        hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    def one_setting(kw):
+        # batched: one handle over all pairs
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        h1 = lem.Stereo(p["left"], p["right"], stream=stream, disp_max=rg[1], **kw)
+        t0 = time.perf_counter()
+        g = lem.Stereo([p["left"] for p in pairs], [p["right"] for p in pairs], stream=stream, disp_ranges=ranges,
+                       **kw)
+        evals_it = g.evals_per_iteration()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         for _ in range(n_it):
-            iterate(h1)
-        lem._check(lem.lem_get_labels(h1.h, None, lem.C.c_void_p(hd.data_ptr()), None, 0), h1.h)
-        lat.append(time.perf_counter() - t1)
-        evals_total += h1.evals_per_iteration() * n_it
-        h1.close()
-    lat_ms = np.array(lat) * 1e3
+            iterate(g)
+        b.record(stream)
+        b.synchronize()
+        gpu_s = a.elapsed_time(b) / 1e3
+        disp = g.labels("all")[1].cpu().numpy()
+        batch_job_s = time.perf_counter() - t0
+        st = g.iterate(0)
+        assert st.maxflow_limit == 0
+        g.close()
+        # served one by one: per-pair latency, host images in and host disparity out
+        lat, evals_total = [], 0
+        for p, rg in zip(pairs, ranges):
+            H, W = p["left"].shape[:2]
+            hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            h1 = lem.Stereo(p["left"], p["right"], stream=stream, disp_max=rg[1], **kw)
+            for _ in range(n_it):
+                iterate(h1)
+            lem._check(lem.lem_get_labels(h1.h, None, lem.C.c_void_p(hd.data_ptr()), None, 0), h1.h)
+            lat.append(time.perf_counter() - t1)
+            evals_total += h1.evals_per_iteration() * n_it
+            h1.close()
+        lat_ms = np.array(lat) * 1e3
+        return {"batched": {"value": evals_it * n_it / gpu_s, "gpu_ms": 1e3 * gpu_s, "job_ms": 1e3 * batch_job_s,
+                            "evals": evals_it * n_it},
+                "per_pair": {"value": evals_total / sum(lat), "latency_ms": [round(x, 2) for x in lat_ms],
+                             "p50_ms": float(np.percentile(lat_ms, 50)),
+                             "p99_ms": float(np.percentile(lat_ms, 99))},
+                "disparity_finite": bool(np.isfinite(disp).all())}
+
+    runs = {"one_cta_per_region": one_setting(dict(kw, work_queue=0)),
+            "work_queue": one_setting(dict(kw, work_queue=1))}
+    best = max(runs, key=lambda k: runs[k]["batched"]["value"])
     sizes = [f"{c['width']}x{c['height']}/{int(c['disp_max'])}" for c in BATCH8]
     out = {"mode": "batch8", "metric": METRIC, "unit": METRIC, "iterations": n_it,
            "pairs": sizes, "pixels": int(sum(c["width"] * c["height"] for c in BATCH8)),
            "config": {"store": "bf16", "candidates_per_visit": 4, "learned_proposals": net is not None,
                       "launch_config": {k: kw[k] for k in ("level_threads", "level_gr_interval", "level_strip_rows")}},
-           "batched": {"value": evals_it * n_it / gpu_s, "gpu_ms": 1e3 * gpu_s, "job_ms": 1e3 * batch_job_s,
-                       "evals": evals_it * n_it},
-           "per_pair": {"value": evals_total / sum(lat), "latency_ms": [round(x, 2) for x in lat_ms],
-                        "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))},
-           "disparity_finite": bool(np.isfinite(disp).all())}
+           "best": best, "value": runs[best]["batched"]["value"], **runs}
     print(json.dumps(out), flush=True)
 
 
@@ -449,14 +476,14 @@ def bf_flops(H, W, r, x0, y0, w, h):
     return 30 * mw * mh + 2 * int(cx.sum()) * int(cy.sum())
 
 
-def bf_timing(lem, pair, stream, seed, flush, steps=3):
+def bf_timing(lem, pair, stream, seed, flush, steps=3, fp32_peak=None):
     """The LE-BF variant (Sec. 4: bilateral weights over the 41 x 41 window, lambda = 20)
-    on the same pair: outer iterations 1 .. steps timed with CUDA events (L2 flushed
-    before each), evals/s, and the data term's algorithmic FP32 rate against the FP32
-    peak."""
+    on the 450 x 375 pair (disparities 0-60, sequential proposals, FP32 images): outer
+    iterations 2 .. steps + 1 timed with CUDA events (L2 flushed before each), evals/s,
+    and the data term's algorithmic FP32 rate against the measured FP32 peak."""
     import torch
     g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, data_term=lem.LEM_DATA_BF,
-                   lam=20.0, **PARAMS)
+                   lam=20.0, disp_max=60.0)
     H, W = pair["left"].shape[:2]
     g.iterate(1, stats=False)
     ts = []
@@ -480,50 +507,16 @@ def bf_timing(lem, pair, stream, seed, flush, steps=3):
             flops += nprop * sum(bf_flops(H, W, r, *R) for R in regs)
     g.close()
     t = sum(ts) / len(ts)
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak if fp32_peak else lem.lem_measure_peaks(stream)[0]
     return {"ms_per_iteration": 1e3 * t, "evals_per_s": evals / t, "data_term_tflops": flops / t / 1e12,
-            "frac": flops / t / 1e12 / peak, "peak_tflops": peak, "maxflow_limit": st.maxflow_limit,
+            "frac": flops / t / 1e12 / peak, "peak_tflops": peak, "peak_note": "of measured (lem_measure_peaks)",
+            "maxflow_limit": st.maxflow_limit,
             "config": "data_term = LE-BF, lambda = 20, gamma_bf = 10, default launch configuration, "
                       f"iterations 2-{steps + 1}, L2 flushed between iterations",
             "note": "whole-iteration time (cuts included); flops count only the data term"}
 
 
-def large_timing(lem, stream, seed, flush, steps=3):
-    """The 1500 x 1000 pair (disparity 0-400) in the production configuration: FP16 image
-    storage, batched 4-candidate visits, autotuned launch configuration, outer iterations
-    replayed as a CUDA graph.  Iterations 2 .. steps + 1 timed with CUDA events (L2 flushed
-    before each)."""
-    import torch
-    from synth import workload_pair
-    pair = workload_pair("large_1500x1000", 0)
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, disp_max=400.0,
-                   store_dtype=lem.LEM_STORE_F16, candidates_per_visit=4)
-    g.iterate(1, stats=False)
-    t = g.autotune(repeats=1)
-    g.iterate(1, stats=False)           # first iteration after tuning: graph capture
-    ts = []
-    for _ in range(steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        g.check(lem.lem_expand_iteration(g.h, 1, None))
-        b.record(stream)
-        b.synchronize()
-        ts.append(a.elapsed_time(b) / 1e3)
-    st = g.iterate(0)
-    evals = g.evals_per_iteration()
-    g.close()
-    ms = 1e3 * sum(ts) / len(ts)
-    return {"workload": "large_1500x1000 (disparity 0-400), FP16 images, 4-candidate visits, autotuned, CUDA graph",
-            "ms_per_iteration": ms, "evals_per_iteration": evals, "evals_per_s": evals / (ms / 1e3),
-            "maxflow_limit": st.maxflow_limit,
-            "launch_config": {"threads": list(t.threads), "gr_interval": list(t.gr_interval),
-                              "strip_rows": list(t.strip_rows)},
-            "note": f"iterations 3-{steps + 2} after one plain and one tuned iteration, L2 flushed between"}
-
-
-def v3_timing(lem, stream, seed, flush):
+def v3_timing(lem, stream, seed, flush, pair=None):
     """The paper's Middlebury V3 settings (Sec. 4: cells of 1, 3 and 9 % of the width,
     lambda = 0.5, one RANSAC proposal per visit) on the 1500 x 1000 pair (disparity
     0-400, FP32): cells 15 / 45 / 135 px, so levels 1 and 2 (135x135 and 405x405-node
@@ -531,7 +524,8 @@ def v3_timing(lem, stream, seed, flush):
     CUDA events (L2 flushed before each launch); per level: time, evals/s, cut rounds."""
     import torch
     from synth import workload_pair
-    pair = workload_pair("large_1500x1000", 0)
+    if pair is None:
+        pair = workload_pair("large_1500x1000", 0)
     H, W = pair["left"].shape[:2]
     g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, disp_max=400.0, v3_width=W)
     g.iterate(1, stats=False)
@@ -574,17 +568,47 @@ def v3_timing(lem, stream, seed, flush):
             "note": "iteration 1, one lem_expand_group call per (level, group), L2 flushed before each"}
 
 
-def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
-    """Time (CUDA events around each outer iteration, learned proposals' inference
-    included) to reach E <= 1.001 E_plain, E_plain the energy after n_plain iterations of
-    the plain method, for the plain method and for the learned proposer (k_cnn = 1 at the
-    finest level) when its trained weights are present."""
+def _block(fn, *a, **kw):
+    """One extra measurement; an exception becomes {"error": ...} in the JSON line."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+# --- GPU -------------------------------------------------------------------------
+
+def timed_iteration(lem, g, stream, flush=None):
+    """One outer iteration of handle g between CUDA events on the library's stream
+    (L2 flushed first when a buffer is given): seconds."""
     import torch
+    if flush is not None:
+        flush.zero_()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.check(lem.lem_expand_iteration(g.h, 1, None))
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def time_to_energy(lem, pair, stream, tuned, seed=21, n_plain=ITERS_PER_HANDLE, max_iters=ITERS_PER_HANDLE):
+    """Time to E <= 1.001 E_plain on one pair, E_plain the energy of the plain method (the
+    paper's schedule: sequential proposals, FP32 images) after its 10 iterations, for
+      * the plain method itself (autotuned after its first iteration, which is timed);
+      * batched visits (4 candidates, FP16 images), the headline configuration;
+      * batched visits plus learned proposals (k_cnn = 1 at the finest level, the proposal
+        map refreshed by the network before every iteration, inference timed).
+    Times are CUDA events around each iteration (autotuning excluded)."""
     from paper_1603_08328_gb300 import proposer
 
-    def run(g, net, n):
+    def run(g, net, n, tune=False):
         curve, t = [], 0.0
-        for _ in range(n):
+        for k in range(n):
+            import torch
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -595,10 +619,13 @@ def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
             b.synchronize()
             t += a.elapsed_time(b)
             curve.append((g.energy()[0], t))
+            if tune and k == 0:
+                g.autotune(repeats=1)
         return curve
 
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, **params)
-    plain = run(g, None, n_plain)
+    base = dict(disp_max=DISP_MAX, seed=seed)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, **base)
+    plain = run(g, None, n_plain, tune=True)
     g.close()
     target = 1.001 * plain[-1][0]
 
@@ -610,30 +637,53 @@ def time_to_energy(lem, pair, params, stream, seed, n_plain=10, max_iters=10):
 
     pi, pt = first(plain)
     out = {"target_energy": target, "plain_energy": plain[-1][0], "plain_iters": pi, "plain_ms": pt,
-           "plain_curve": [[round(e, 1), round(t, 2)] for e, t in plain]}
+           "plain_curve": [[round(e, 1), round(t, 2)] for e, t in plain],
+           "plain_config": "sequential proposals (Algorithm 2), FP32 images, autotuned after iteration 1"}
+    fast = dict(base, **headline_params(lem), **tuned)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, **fast)
+    bat = run(g, None, max_iters)
+    g.close()
+    bi, bt = first(bat)
+    out.update({"batched_iters": bi, "batched_ms": bt, "batched_curve": [[round(e, 1), round(t, 2)] for e, t in bat]})
     if not os.path.exists(proposer.WEIGHTS):
         out["learned"] = "no trained weights"
         return out
     net = proposer.load()
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=seed, k_cnn=(1, 0, 0), **params)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, k_cnn=(1, 0, 0), **fast)
     curve = run(g, net, max_iters)
     g.close()
+    net.close()
     li, lt = first(curve)
     out.update({"learned_iters": li, "learned_ms": lt, "learned_energy": curve[-1][0],
                 "learned_curve": [[round(e, 1), round(t, 2)] for e, t in curve],
                 "speedup": (pt / lt) if (pt and lt) else None,
-                "learned_config": "k_cnn = (1, 0, 0), proposal map refreshed before every iteration"})
-    net.close()
+                "learned_config": "batched visits (4 candidates, FP16 images) + k_cnn = (1, 0, 0), proposal map "
+                                  "refreshed before every iteration"})
     return out
 
-def _block(fn, *a, **kw):
-    """One extra measurement; an exception becomes {"error": ...} in the JSON line."""
-    try:
-        return fn(*a, **kw)
-    except Exception as e:  # noqa: BLE001 - reported, not hidden
-        import traceback
-        traceback.print_exc(file=sys.stderr)
-        return {"error": f"{type(e).__name__}: {e}"}
+
+def middlebury_timing(lem, stream, flush, steps=3):
+    """The 450 x 375 Middlebury-V2-shaped pair (disparities 0-60) with the paper's
+    schedule (sequential proposals, FP32 images): iterations 2 .. steps + 1, L2 flushed
+    before each, kernel times from the library's events."""
+    from synth import workload_pair
+    pair = workload_pair("middlebury_450x375", 0)
+    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=61, disp_max=60.0)
+    g.set_kernel_timing(True)
+    g.iterate(1, stats=False)
+    ts, kt = [], {}
+    for _ in range(steps):
+        ts.append(timed_iteration(lem, g, stream, flush))
+        for (l, k), (ms, n) in g.kernel_times().items():
+            kt[f"{k} level {l}"] = kt.get(f"{k} level {l}", 0.0) + ms
+    st = g.iterate(0)
+    evals = g.evals_per_iteration()
+    g.close()
+    t = sum(ts) / len(ts)
+    return {"workload": "middlebury_450x375 (disparity 0-60), FP32 images, sequential proposals",
+            "ms_per_iteration": 1e3 * t, "evals_per_s": evals / t, "maxflow_limit": st.maxflow_limit,
+            "kernel_ms_per_iteration": {k: v / steps for k, v in kt.items()},
+            "note": f"iterations 2-{steps + 1}, default launch configuration, L2 flushed between"}
 
 
 def run_lem(args):
@@ -654,93 +704,83 @@ def run_lem(args):
     pair = workload_pair(WORKLOAD, args.seed + rank)
     stream = torch.cuda.current_stream()
     H, W = pair["left"].shape[:2]
+    params = headline_params(lem)
 
-    # warm-up: a separate handle, W outer iterations, then the autotuner on its state
-    warm = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1000 + rank, **PARAMS)
-    warm.iterate(max(1, args.warmup), stats=False)
-    tuned = {}
-    tuning = None
-    if args.launch_config:
-        t3 = [[int(x) for x in part.split(",")] for part in args.launch_config.split("/")]
-        tuned = dict(level_threads=t3[0], level_gr_interval=t3[1], level_strip_rows=t3[2])
-        tuning = dict(tuned, source="--launch-config")
-    elif not args.no_tune:
-        t = warm.autotune(repeats=2)
+    # warm-up: a separate handle, W outer iterations (at most the method's 10), then the
+    # autotuner on its state
+    warm = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1000 + rank, **params)
+    warm.iterate(min(ITERS_PER_HANDLE, max(1, args.warmup)), stats=False)
+    tuned, tuning = {}, "default"
+    if not args.no_tune:
+        t = warm.autotune(repeats=1)
         tuned = dict(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval),
                      level_strip_rows=list(t.strip_rows))
         tuning = dict(tuned, ms=[round(x, 4) for x in t.ms], ms_default=[round(x, 4) for x in t.ms_default],
                       configs_tried=t.configs_tried)
     torch.cuda.synchronize()
     warm.close()
-    params = dict(PARAMS, **tuned)
+    params = dict(params, **tuned)
 
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **params)
-    p = dict(gf_radius=g.params.gf_radius, n_levels=g.params.n_levels, cell=list(g.params.cell),
-             k_prop=list(g.params.k_prop), k_rand=list(g.params.k_rand))
-    work = launches_and_work(H, W, p)
-    evals_per_step = g.evals_per_iteration()
-    assert evals_per_step == sum(x["evals"] for x in work)
+    pinfo = None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
-    e0, q0 = g.energy()
-    g.iterate(0)                       # stats baseline: counters restart here
-    times = []
+    times, kt, launches, evals_total, graph_steps = [], {}, 0, 0, 0
+    e_first = e_last = None
+    g = None
     torch.cuda.synchronize()
     barrier(dist)
     with ClockSampler(dev) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            g.check(lem.lem_expand_iteration(g.h, 1, None))
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b) / 1e3)
+        for i in range(args.steps):
+            if i % ITERS_PER_HANDLE == 0:
+                # a new handle (new random initialisation) every 10 iterations: created and
+                # initialised outside the timed iterations
+                if g is not None:
+                    e_last = g.energy()[0]
+                    st = g.iterate(0)
+                    assert st.maxflow_limit == 0, "a cut hit its round limit"
+                    g.close()
+                g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank + 7919 * (i // 10), **params)
+                g.set_kernel_timing(True)
+                g.iterate(0)
+                if e_first is None:
+                    e_first = g.energy()[0]
+                if pinfo is None:
+                    pinfo = dict(gf_radius=g.params.gf_radius, n_levels=g.params.n_levels,
+                                 cell=list(g.params.cell), k_prop=list(g.params.k_prop),
+                                 k_rand=list(g.params.k_rand))
+                torch.cuda.synchronize()
+            times.append(timed_iteration(lem, g, stream, flush))
+            for key, (ms, n) in g.kernel_times().items():
+                d = kt.setdefault(key, [0.0, 0])
+                d[0] += ms
+                d[1] += n
+                launches += n
+            graph_steps += 1 if i % ITERS_PER_HANDLE else 0
+            evals_total += g.evals_per_iteration()
     torch.cuda.synchronize()
-    t_total = sum(times)
-    t_max = max_over_ranks(t_total, dist)
-    e1, q1 = g.energy()
+    e_last = g.energy()[0]
     st = g.iterate(0)
     assert st.maxflow_limit == 0, "a cut hit its round limit"
+    evals_per_step = g.evals_per_iteration()
+    g.close()
+    t_total = sum(times)
+    t_max = max_over_ranks(t_total, dist)
 
-    # per-launch durations of the expansion kernel (one launch per lem_expand_group call),
-    # on a fresh handle over one outer iteration, L2 flushed before every launch
-    g2 = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1 + rank, **params)
-    per, cut = [], []
-    for wk in work:
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        sts = lem.lem_stats()
-        a.record(stream)
-        g2.check(lem.lem_expand_group(g2.h, 0, wk["level"], wk["group"], None))
-        b.record(stream)
-        b.synchronize()
-        per.append(a.elapsed_time(b) / 1e3)
-        lem.lib().lem_expand_iteration(g2.h, 0, lem.C.byref(sts))
-        cut.append((sts.pr_rounds, sts.pr_global_relabels, sts.pr_bfs_levels))
-    g2.close()
-    flops = sum(wk["flops"] for wk in work)
-    launch_avg = sum(per) / len(per)
-    achieved = flops / len(work) / launch_avg / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    by_level = {}
-    for wk, t, c in zip(work, per, cut):
-        d = by_level.setdefault(wk["level"], {"ms": 0.0, "evals": 0, "flops": 0, "launches": 0, "cuts": 0,
-                                              "rounds": 0, "relabels": 0, "bfs_levels": 0})
-        d["ms"] += 1e3 * t
-        d["evals"] += wk["evals"]
-        d["flops"] += wk["flops"]
-        d["launches"] += 1
-        lv = wk["level"]
-        d["cuts"] += wk["regions"] * (p["k_prop"][lv] + p["k_rand"][lv])
-        d["rounds"] += c[0]
-        d["relabels"] += c[1]
-        d["bfs_levels"] += c[2]
+    # per kernel kind: time and launches in the timed steps, and the levels it ran
+    work = iteration_work(H, W, pinfo)
+    peaks = measured_peaks(lem, stream) if rank == 0 else None
+    kinds = {}
+    for (l, k), (ms, n) in kt.items():
+        d = kinds.setdefault(k, {"ms": 0.0, "launches": 0, "levels": []})
+        d["ms"] += ms
+        d["launches"] += n
+        d["levels"].append(l)
+    dom = max(kinds.items(), key=lambda kv: kv[1]["ms"])[0]
+    roof = {"kernel": dom,
+            "kernel_ms_per_step": {f"{k} level {l}": round(v[0] / args.steps, 4) for (l, k), v in sorted(kt.items())},
+            "launches_per_step": {f"{k} level {l}": v[1] / args.steps for (l, k), v in sorted(kt.items())}}
 
     # end to end through the C ABI: pinned host images in, disparity map out,
     # one job = create + 10 outer iterations
-    n_iters_job = 10
     hl = torch.from_numpy(pair["left"]).pin_memory()
     hr = torch.from_numpy(pair["right"]).pin_memory()
     hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
@@ -753,71 +793,201 @@ def run_lem(args):
         li = lem.lem_image(hl.data_ptr(), H, W, 3 * W, 0)
         ri = lem.lem_image(hr.data_ptr(), H, W, 3 * W, 0)
         h = lem.lem_create(li, ri, prm)
-        lem._check(lem.lem_expand_iteration(h, n_iters_job, None), h)
+        lem._check(lem.lem_expand_iteration(h, ITERS_PER_HANDLE, None), h)
         lem._check(lem.lem_get_labels(h, None, lem.C.c_void_p(hd.data_ptr()), None, 0), h)
         e2e_t.append(time.perf_counter() - t0)
         lem.lem_destroy(h)
     e2e_job = max_over_ranks(sum(e2e_t) / len(e2e_t), dist)
-    e2e_v = world * n_iters_job * evals_per_step / e2e_job
+    e2e_v = world * ITERS_PER_HANDLE * evals_per_step / e2e_job
 
     # the extra blocks report their own failure instead of taking the headline line with
     # them; only rank 0 prints them, so only rank 0 runs them
     extra = rank == 0
-    tte = None if args.no_time_to_energy or not extra else _block(time_to_energy, lem, pair, params, stream, seed=21)
-    prop = None if args.no_proposer or not extra else _block(proposer_timing, lem, stream)
-    lebf = None if args.no_bf or not extra else _block(bf_timing, lem, pair, stream, seed=31, flush=flush)
-    v3 = None if args.no_v3 or not extra else _block(v3_timing, lem, stream, seed=41, flush=flush)
-    large = None if args.no_large or not extra else _block(large_timing, lem, stream, seed=51, flush=flush)
+    tte = None if args.no_time_to_energy or not extra else _block(time_to_energy, lem, pair, stream, tuned)
+    more = {}
+    if extra and not args.no_extra:
+        more["middlebury_450x375"] = _block(middlebury_timing, lem, stream, flush)
+        more["proposer"] = _block(proposer_timing, lem, stream)
+        more["le_bf"] = _block(bf_timing, lem, workload_pair("middlebury_450x375", args.seed), stream, seed=31,
+                               flush=flush, fp32_peak=peaks["fp32_tflops"])
+        more["v3"] = _block(v3_timing, lem, stream, seed=41, flush=flush, pair=pair)
 
     if rank != 0:
         return
-    value = world * evals_per_step * args.steps / t_max
+    value = world * evals_total / t_max
+    # the dominant kernel's roofline: the data term's algorithmic FP32 work on the
+    # batched-visit levels, else the data-term work of the whole iteration over the
+    # one-kernel expansion time
+    fp32_peak = peaks["fp32_tflops"]
+    dk = kinds[dom]
+    flops_launch = sum(work[l]["flops"] for l in dk["levels"]) / (dk["launches"] / args.steps)
+    launch_ms = dk["ms"] / dk["launches"]
+    achieved = flops_launch / (launch_ms / 1e3) / 1e12
+    roof.update({"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": achieved / fp32_peak, "traffic": traffic_from_profile(dom),
+                 "launch_avg_ms": launch_ms, "flops_per_launch": flops_launch, "levels": dk["levels"],
+                 "peak_note": "of measured: FP32 FMA throughput from lem_measure_peaks on this GPU",
+                 "work_note": "algorithmic FP32 operations of the data term (30 per raw cost over M, 44 per "
+                              "regression window, 24 per output pixel, per candidate and region) of the levels "
+                              "this kernel runs"})
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "height": H, "width": W, "disp_max": 60, "cells": p["cell"],
-                   "window": 4 * p["gf_radius"] + 1, "step": "one outer iteration (48 level-group launches)",
-                   "schedule": "sequential proposals (Algorithm 2)", "l2": "flushed between timed steps",
-                   "launch_config": tuning or "default",
+        "config": {"workload": WORKLOAD, "height": H, "width": W, "disp_max": DISP_MAX, "cells": pinfo["cell"],
+                   "window": 4 * pinfo["gf_radius"] + 1, "store": "fp16 images, fp32 costs",
+                   "candidates_per_visit": 4, "step": "one outer iteration (48 level-group steps)",
+                   "iterations_per_handle": ITERS_PER_HANDLE, "l2": "flushed between timed steps",
+                   "graph": "outer iterations replayed as CUDA graphs", "launch_config": tuning,
                    "parallelism": f"replicas x{world}", "evals_per_step": evals_per_step},
         "e2e": {"value": e2e_v, "unit": METRIC, "h2d_bytes_per_step": 2 * H * W * 3, "d2h_bytes_per_step": H * W * 4,
-                "step": f"one job: host images -> lem_create -> {n_iters_job} iterations -> host disparity",
+                "step": f"one job: host images -> lem_create -> {ITERS_PER_HANDLE} iterations -> host disparity",
                 "jobs": args.e2e_jobs, "ms_per_job": 1e3 * e2e_job},
-        # the first step launches the 48 (level, group) kernels directly; later steps replay
-        # them as one CUDA graph that also increments the device iteration index
-        "gpu_launches": len(work) * args.steps + max(0, args.steps - 1),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic_from_profile("k_expand_group"), "kernel": "k_expand_group",
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-                     "launch_avg_ms": 1e3 * launch_avg},
+        # every expansion launch of the timed steps (counted from the library's events) and
+        # the iteration-index kernel of each graph replay
+        "gpu_launches": launches + graph_steps,
+        "roofline": roof,
         "clocks": clk.summary(),
-        "energy": {"before": e0, "after": e1},
-        "time_to_energy": tte,
-        "proposer": prop,
-        "le_bf": lebf,
-        "v3": v3,
-        "large": large,
-        "levels": {str(k): {"ms": round(v["ms"], 3), "launches": v["launches"],
-                            "evals_per_s": v["evals"] / (v["ms"] / 1e3),
-                            "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
-                            # one cut per candidate and region, one node per pixel of the region
-                            "cuts_per_s": v["cuts"] / (v["ms"] / 1e3),
-                            "nodes_per_cut": v["evals"] / max(1, v["cuts"]),
-                            "rounds_per_cut": v["rounds"] / max(1, v["cuts"]),
-                            "relabels_per_cut": v["relabels"] / max(1, v["cuts"]),
-                            "bfs_levels_per_relabel": v["bfs_levels"] / max(1, v["relabels"])}
-                   for k, v in by_level.items()},
+        "energy": {"first_handle_initial": e_first, "last_handle_final": e_last},
+        "peaks": peaks,
     }
+    if tte is not None:
+        out["time_to_energy"] = tte
+        if isinstance(tte, dict) and tte.get("learned_ms"):
+            out["time_to_energy_ms"] = tte["learned_ms"]
+            out["plain_ms"] = tte["plain_ms"]
+            out["speedup"] = tte["speedup"]
+    out.update(more)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = _block(cpu_oracle_baseline, pair, p, seed=1)
+        out["cpu_baseline"] = _block(cpu_oracle_baseline, pair, seed=1)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
+def run_proposer_mode(args):
+    """--mode proposer: only the proposal-network timing, one JSON line."""
+    import torch
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    __graft_entry__.build()
+    from paper_1603_08328_gb300 import lem
+    out = proposer_timing(lem, torch.cuda.current_stream())
+    print(json.dumps({"mode": "proposer", **out}), flush=True)
+
+
+def _render(args):
+    from synth import workload_pair
+    seed, name = args
+    p = workload_pair(name, seed)
+    return {"left": p["left"], "right": p["right"]}
+
+
+def run_cnn_gain_mode(args):
+    """--mode cnn_gain: the learned proposer on held-out 1500 x 1000 scenes (seeds 100 ..
+    100 + n - 1 of the headline workload; the network was trained on 384 x 288 scenes only).
+    Per seed: E_plain after the plain method's 10 iterations (sequential proposals, FP32
+    images); then, both with 4-candidate visits and FP16 images at one launch configuration,
+    batched visits without and with learned proposals (k_cnn = 1 at the finest level) for up
+    to 10 iterations each: time to E <= 1.001 E_plain, energy at equal wall-clock (the energy
+    the run without the network has when the run with it reaches the target) and the share
+    of switched pixels and of map candidates' moves that came from the network.  One JSON
+    line with the per-seed records and their medians."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    seeds = [100 + k for k in range(args.seeds)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        pairs = pool.map(_render, [(s, WORKLOAD) for s in seeds], chunksize=1)
+    __graft_entry__.build()
+    from paper_1603_08328_gb300 import lem, proposer
+    stream = torch.cuda.current_stream()
+    net = proposer.load()
+    # one launch configuration for every run: tuned once on the first scene
+    t = lem.Stereo(pairs[0]["left"], pairs[0]["right"], stream=stream, seed=5, **headline_params(lem))
+    t.iterate(1, stats=False)
+    tu = t.autotune(repeats=1)
+    t.close()
+    tuned = dict(level_threads=list(tu.threads), level_gr_interval=list(tu.gr_interval),
+                 level_strip_rows=list(tu.strip_rows))
+
+    def run(g, use_net, n):
+        curve, t_ms, acc_map, acc_all = [], 0.0, 0, 0
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if use_net:
+                g.cnn_propose(net)
+            g.check(lem.lem_expand_iteration(g.h, 1, None))
+            b.record(stream)
+            b.synchronize()
+            t_ms += a.elapsed_time(b)
+            st = g.iterate(0)
+            acc_all += st.accepted
+            acc_map += st.accepted_by_kind[2]
+            curve.append((st.energy, t_ms))
+        return curve, acc_map, acc_all
+
+    recs = []
+    for s, pr in zip(seeds, pairs):
+        g = lem.Stereo(pr["left"], pr["right"], stream=stream, seed=s, disp_max=DISP_MAX)
+        g.iterate(1, stats=False)
+        g.iterate(ITERS_PER_HANDLE - 1, stats=False)
+        e_plain = g.energy()[0]
+        g.close()
+        target = 1.001 * e_plain
+        fast = dict(headline_params(lem), seed=s, **tuned)
+        g = lem.Stereo(pr["left"], pr["right"], stream=stream, **fast)
+        base, _, acc_b = run(g, False, ITERS_PER_HANDLE)
+        g.close()
+        g = lem.Stereo(pr["left"], pr["right"], stream=stream, k_cnn=(1, 0, 0), **fast)
+        cnn, acc_map, acc_c = run(g, True, ITERS_PER_HANDLE)
+        g.close()
+
+        def first(curve):
+            for k, (e, tt) in enumerate(curve):
+                if e <= target:
+                    return k + 1, tt
+            return None, None
+
+        bi, bt = first(base)
+        ci, ct = first(cnn)
+        # energy at equal wall-clock: the run without the network at the time the run with
+        # it reached the target (its last iteration finished by then)
+        e_base_at = None
+        if ct is not None:
+            done = [e for e, tt in base if tt <= ct]
+            e_base_at = done[-1] if done else None
+        recs.append({"seed": s, "e_plain": e_plain, "batched_ms": bt, "batched_iters": bi, "cnn_ms": ct,
+                     "cnn_iters": ci, "speedup": (bt / ct) if (bt and ct) else None,
+                     "e_cnn_at_target": cnn[ci - 1][0] if ci else None, "e_batched_at_same_time": e_base_at,
+                     "cnn_share_of_switches": acc_map / max(1, acc_c),
+                     "e_after_2": {"batched": base[1][0], "cnn": cnn[1][0]}})
+    net.close()
+    sp = [r["speedup"] for r in recs if r["speedup"]]
+    gain2 = [r["e_after_2"]["batched"] - r["e_after_2"]["cnn"] for r in recs]
+    out = {"mode": "cnn_gain", "workload": WORKLOAD, "seeds": seeds,
+           "config": {"plain": "sequential proposals, FP32 images, 10 iterations -> E_plain",
+                      "batched": "4-candidate visits, FP16 images", "learned": "batched + k_cnn = (1, 0, 0)",
+                      "launch_config": tuned},
+           "median_speedup": float(np.median(sp)) if sp else None,
+           "seeds_reaching_target": {"batched": sum(1 for r in recs if r["batched_ms"]),
+                                     "cnn": sum(1 for r in recs if r["cnn_ms"])},
+           "median_energy_gain_after_2_iterations": float(np.median(gain2)),
+           "median_cnn_share_of_switches": float(np.median([r["cnn_share_of_switches"] for r in recs])),
+           "per_seed": recs}
+    print(json.dumps(out), flush=True)
+
+
 def run_block_mode(args):
-    """--mode v3 / lebf / large: one of the extra blocks of the default run on its own."""
+    """--mode v3 / lebf: one of the extra blocks of the default run on its own."""
     import torch
     import __graft_entry__
     if not torch.cuda.is_available():
@@ -829,10 +999,8 @@ def run_block_mode(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if args.mode == "v3":
         out = v3_timing(lem, stream, seed=41, flush=flush)
-    elif args.mode == "large":
-        out = large_timing(lem, stream, seed=51, flush=flush)
     else:
-        out = bf_timing(lem, workload_pair(WORKLOAD, args.seed), stream, seed=31, flush=flush)
+        out = bf_timing(lem, workload_pair("middlebury_450x375", args.seed), stream, seed=31, flush=flush)
     print(json.dumps({"mode": args.mode, **out}), flush=True)
 
 
@@ -840,12 +1008,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.mode in ("v3", "lebf", "large"):
+    elif args.mode in ("v3", "lebf"):
         run_block_mode(args)
     elif args.mode == "proposer":
         run_proposer_mode(args)
     elif args.mode == "batch8":
         run_batch8_mode(args)
+    elif args.mode == "cnn_gain":
+        run_cnn_gain_mode(args)
     else:
         run_lem(args)
 

@@ -143,6 +143,10 @@ typedef struct {
                              sums) and then its moves (one CTA per region; level_threads is that CTA's
                              size, 32 .. 1024); 0 (default) runs the visit in one kernel.  The moves
                              are the same; the data terms differ only in FP32 rounding. */
+    int work_queue;       /* 1: one-kernel expansion launches run as many CTAs as fit on the GPU at
+                             once, each taking regions from a work queue (largest first) until none
+                             is left; 0 (default): one CTA per region.  The regions of a group are
+                             independent, so the results are the same. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */

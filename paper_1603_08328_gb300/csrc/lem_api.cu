@@ -31,6 +31,7 @@ struct lem_handle {
     // candidates_per_visit data-term planes and the candidate labels of a launch
     float *phiK = nullptr;
     float4 *alphaK = nullptr;
+    int *d_queue = nullptr;             // work-queue counters of the 48 (level, group) launches
     bool split_level[3] = {false, false, false};
     float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
     bool prop_set = false;
@@ -217,6 +218,7 @@ int check_params(const lem_params *p) {
     if (!(p->bf_gamma > 0)) return fail(nullptr, LEM_ERR_ARG, "bf_gamma must be > 0");
     if (p->cluster_visits != 0 && p->cluster_visits != 1) return fail(nullptr, LEM_ERR_ARG, "cluster_visits must be 0 or 1");
     if (p->split_visits != 0 && p->split_visits != 1) return fail(nullptr, LEM_ERR_ARG, "split_visits must be 0 or 1");
+    if (p->work_queue != 0 && p->work_queue != 1) return fail(nullptr, LEM_ERR_ARG, "work_queue must be 0 or 1");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
@@ -251,6 +253,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->phiB);
     cudaFree(h->phiK);
     cudaFree(h->alphaK);
+    cudaFree(h->d_queue);
     cudaFree(h->prop);
     cudaFree(h->cnn_buf);
     cudaFree(h->e_part);
@@ -467,6 +470,8 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
     CREATE_CUDA(cudaMalloc(&h->n_fp64, sizeof(int)));
     CREATE_CUDA(cudaMalloc(&h->d_pairs, sizeof(lem::PairDesc) * n_pairs));
     CREATE_CUDA(cudaMalloc(&h->d_iter, sizeof(int)));
+    CREATE_CUDA(cudaMalloc(&h->d_queue, sizeof(int) * 2 * 48));
+    CREATE_CUDA(cudaMemsetAsync(h->d_queue, 0, sizeof(int) * 2 * 48, h->st));
     CREATE_CUDA(cudaMemsetAsync(h->n_fp64, 0, sizeof(int), h->st));
     CREATE_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
     CREATE_CUDA(cudaMemcpyAsync(h->d_pairs, h->pairs.data(), sizeof(lem::PairDesc) * n_pairs, cudaMemcpyHostToDevice,
@@ -485,6 +490,17 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
                         for (int ci = gi; ci < nx; ci += 4) items.push_back(make_int4(b, ci, cj, 0));
                 }
                 h->item_cnt[l][g] = (int)items.size() - h->item_off[l][g];
+                // largest regions first (the clipped border regions of every pair last), so
+                // the block scheduler starts the longest work first; the regions of a group
+                // are independent, so the order changes no result
+                auto area = [&](const int4 &it) {
+                    const lem::PairDesc &pd = h->pairs[it.x];
+                    const int w = std::min(pd.W, (it.y + 2) * s) - std::max(0, (it.y - 1) * s);
+                    const int hh = std::min(pd.H, (it.z + 2) * s) - std::max(0, (it.z - 1) * s);
+                    return (long long)w * hh;
+                };
+                std::stable_sort(items.begin() + h->item_off[l][g], items.end(),
+                                 [&](const int4 &a, const int4 &b) { return area(a) > area(b); });
             }
         }
         CREATE_CUDA(cudaMalloc(&h->d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
@@ -774,7 +790,7 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                          h->lab, h->phiA, h->prop, h->ctr, h->p.cluster_visits ? h->phiB : nullptr,
-                                         st));
+                                         h->p.work_queue ? h->d_queue + 2 * (16 * level + group) : nullptr, st));
     return ktime_mark(h, LEM_KERNEL_EXPAND, level, st);
 }
 

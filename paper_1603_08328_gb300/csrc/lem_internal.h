@@ -105,10 +105,12 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 // phiB: a second data-term plane (same offsets as phiA), or NULL; with it, levels
 // whose visit is two propagation candidates run two CTAs per region (a cluster)
 // that compute both candidates' data terms at once, with the sequential result.
+// queue: NULL (one CTA per item), or two zeroed ints of a work queue that a
+// grid of co-resident CTAs drains (left zeroed after the launch); not with phiB.
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
-                                cudaStream_t st);
+                                int *queue, cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
 // Batched visits on the guided-filter data term without RANSAC proposals, regions
 // of at most LEM_MAX_REGION_NODES nodes and filtering regions at most 128 px

@@ -1967,7 +1967,10 @@ __device__ __forceinline__ void cluster_sync_all() {
 // All expansions of one group at one level: one CTA per region, Algorithm 2.
 //   P      : base planes of all pairs (H/W unused); pair b's planes start at
 //            pixel pairs[b].off
-//   items  : one (pair, cell i, cell j) per CTA (per CTA pair with phiB_all)
+//   items  : one (pair, cell i, cell j) per CTA (per CTA pair with phiB_all), or
+//            with queue (two ints: next item, finished CTAs; zero before the
+//            launch, zero again after it) taken from that work queue by a grid of
+//            at most the co-resident CTAs until all n_items are done
 //   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
 //   SPEC   : a launch in clusters of two CTAs per region (phiB_all), for
 //            levels whose visit is two propagation candidates (K_prop = 2, no
@@ -1982,16 +1985,36 @@ __device__ __forceinline__ void cluster_sync_all() {
 //            one-CTA visit, bit for bit.
 template <int NT, bool SPEC>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
-    k_expand_group(DevPlanes P, KParams kp, Level lv, int level, int iter, const int *iter_dev,
+    k_expand_group(DevPlanes P0, KParams kp0, Level lv, int level, int iter, const int *iter_dev,
                    const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all,
-                   const float4 *prop_all, Counters *ctr, float *phiB_all) {
+                   const float4 *prop_all, Counters *ctr, float *phiB_all, int n_items, int *queue) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha[kMaxVisit];
     __shared__ long long red[33];
     __shared__ int s_src;
+    __shared__ int s_item;
     const int rank = SPEC ? (int)(blockIdx.x & 1u) : 0;
-    const int4 item = items[SPEC ? (blockIdx.x >> 1) : blockIdx.x];
+    if (iter < 0) iter = *iter_dev;
+    long long acck[4] = {0, 0, 0, 0}, hits = 0;
+    unsigned long long evals = 0;
+    CutCount cc{0, 0, 0};
+    // one item per CTA, or (queue) items taken from a work queue until none is left
+    for (int pass = 0;; ++pass) {
+    int idx;
+    if (queue) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        idx = s_item;
+        __syncthreads();
+        if (idx >= n_items) break;
+    } else {
+        if (pass > 0) break;
+        idx = SPEC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    }
+    const int4 item = items[idx];
     const PairDesc pd = pairs[item.x];
+    DevPlanes P = P0;
+    KParams kp = kp0;
     P.H = pd.H;
     P.W = pd.W;
     P.L = px_offset(P.L, pd.off, P.fmt);
@@ -2004,7 +2027,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     float4 *lab = lab_all + pd.off;
     float *phiA = phiA_all + pd.off;
     const float4 *prop = prop_all ? prop_all + pd.off : nullptr;
-    if (iter < 0) iter = *iter_dev;
     const int H = P.H, W = P.W, s = lv.s;
     const int ci = item.y, cj = item.z;
     const int x0 = max(0, (ci - 1) * s), x1 = min(W, (ci + 2) * s);
@@ -2012,8 +2034,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
     CutSmem cs = cut_layout(smf, n);
-    long long acck[4] = {0, 0, 0, 0}, hits = 0;
-    CutCount cc{0, 0, 0};
+    evals += (unsigned long long)n * (unsigned long long)(lv.k_prop + lv.k_rans + (prop ? lv.k_cnn : 0) + lv.k_rand);
     if constexpr (SPEC) {
         float *phiB = phiB_all + pd.off;
         const unsigned long long st1 = proposal_stream(kp.seed, iter, level, ci, cj, 0);
@@ -2091,14 +2112,21 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
             }
         }
     }
-    const int nprop_all = lv.k_prop + lv.k_rans + (prop ? lv.k_cnn : 0) + lv.k_rand;
+    }
     add_accepted(acck, red, ctr);
     if (threadIdx.x == 0) {
         atomicAdd(&ctr->limit_hits, (unsigned long long)hits);
-        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)nprop_all);
+        atomicAdd(&ctr->evals, evals);
         atomicAdd(&ctr->rounds, (unsigned long long)cc.rounds);
         atomicAdd(&ctr->relabels, (unsigned long long)cc.relabels);
         atomicAdd(&ctr->bfs_levels, (unsigned long long)cc.levels);
+        // the last CTA to finish resets the queue for the next launch (every CTA has
+        // taken its last item before it counts itself done)
+        if (queue && atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+            queue[0] = 0;
+            queue[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -3233,12 +3261,26 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 template <int NT>
 cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, const int *iter_dev,
                       const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA,
-                      const float4 *prop, Counters *ctr, float *phiB, size_t sm, cudaStream_t st) {
+                      const float4 *prop, Counters *ctr, float *phiB, int *queue, size_t sm, cudaStream_t st) {
     cudaError_t e;
     if (!phiB) {
         if ((e = set_smem((const void *)k_expand_group<NT, false>, sm)) != cudaSuccess) return e;
-        k_expand_group<NT, false><<<n_items, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA,
-                                                           prop, ctr, nullptr);
+        int grid = n_items;
+        if (queue) {
+            // work queue: at most as many CTAs as are co-resident
+            int per_sm = 0, dev = 0, nsm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_group<NT, false>, NT, sm) !=
+                    cudaSuccess ||
+                cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 1;
+                nsm = 1;
+            }
+            grid = std::max(1, std::min(n_items, per_sm * nsm));
+        }
+        k_expand_group<NT, false><<<grid, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA,
+                                                        prop, ctr, nullptr, n_items, queue);
         return cudaGetLastError();
     }
     if ((e = set_smem((const void *)k_expand_group<NT, true>, sm)) != cudaSuccess) return e;
@@ -3267,16 +3309,16 @@ cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, in
     if (!ok || clusters < n_items || 2 * n_items > per_sm * nsm) {
         cudaGetLastError();
         return expand_nt<NT>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, nullptr,
-                             sm, st);
+                             queue, sm, st);
     }
     return cudaLaunchKernelEx(&cfg, k_expand_group<NT, true>, P, kp, lv, level, iter, iter_dev, pairs, items, lab,
-                              phiA, prop, ctr, phiB);
+                              phiA, prop, ctr, phiB, n_items, (int *)nullptr);
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
-                                cudaStream_t st) {
+                                int *queue, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const int s = lv.s;
     const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
@@ -3288,16 +3330,13 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     // the two-CTA visit only for two propagation candidates per visit
     const bool two = phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop);
     float *pb = two ? phiB : nullptr;
-    if (nt == 128)
-        return expand_nt<128>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
-                              st);
-    if (nt == 256)
-        return expand_nt<256>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
-                              st);
-    if (nt == 512)
-        return expand_nt<512>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm,
-                              st);
-    return expand_nt<1024>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, sm, st);
+#define LEM_EXPAND_NT(NT_) \
+    expand_nt<NT_>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, queue, sm, st)
+    if (nt == 128) return LEM_EXPAND_NT(128);
+    if (nt == 256) return LEM_EXPAND_NT(256);
+    if (nt == 512) return LEM_EXPAND_NT(512);
+    return LEM_EXPAND_NT(1024);
+#undef LEM_EXPAND_NT
 }
 
 namespace {

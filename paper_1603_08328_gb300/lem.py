@@ -44,7 +44,7 @@ class lem_params(C.Structure):
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
         ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double), ("cluster_visits", C.c_int),
-        ("split_visits", C.c_int),
+        ("split_visits", C.c_int), ("work_queue", C.c_int),
     ]
 
 
@@ -310,6 +310,14 @@ def lem_mincut_batch_noalloc(regions, tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr, 
                              stream):
     return lib().lem_mincut_batch_noalloc(_regions(regions), len(regions), tcaps_ptr, ncaps_ptr, take_ptr, flow_ptr,
                                           status_ptr, max_rounds, gr_interval, stream)
+
+
+def lem_set_kernel_timing(h, on):
+    return lib().lem_set_kernel_timing(h, on)
+
+
+def lem_get_kernel_times(h, out):
+    return lib().lem_get_kernel_times(h, C.byref(out))
 
 
 def lem_measure_peaks(stream=None):
@@ -598,12 +606,12 @@ class Stereo:
 
     def set_kernel_timing(self, on=True):
         """Events between the expansion launches of every outer iteration (lem_set_kernel_timing)."""
-        self.check(lib().lem_set_kernel_timing(self.h, 1 if on else 0))
+        self.check(lem_set_kernel_timing(self.h, 1 if on else 0))
 
     def kernel_times(self):
         """{(level, kernel name): (ms, launches)} of the last outer iteration (lem_get_kernel_times)."""
         t = lem_kernel_times()
-        self.check(lib().lem_get_kernel_times(self.h, C.byref(t)))
+        self.check(lem_get_kernel_times(self.h, t))
         return {(l, n): (t.ms[l][k], t.launches[l][k]) for l in range(3) for k, n in enumerate(KERNEL_KIND_NAMES)
                 if t.launches[l][k]}
 

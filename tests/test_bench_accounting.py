@@ -24,12 +24,12 @@ def _coverage(n, s):
 def test_evals_per_step_is_the_per_pixel_coverage(H, W):
     """Evals of one outer iteration = sum over pixels of (regions covering it) x
     (proposals per visit), level by level."""
-    work = bench.launches_and_work(H, W, PAPER)
+    work = bench.iteration_work(H, W, PAPER)
     want = 0
     for lv, s in enumerate(PAPER["cell"]):
         n_prop = PAPER["k_prop"][lv] + PAPER["k_rand"][lv]
         want += n_prop * int(np.outer(_coverage(H, s), _coverage(W, s)).sum())
-    assert sum(wk["evals"] for wk in work) == want
+    assert sum(wk["evals"] for wk in work.values()) == want
 
 
 def test_interior_pixel_gets_108_evals_per_iteration():
@@ -41,11 +41,11 @@ def test_interior_pixel_gets_108_evals_per_iteration():
     assert total == 108
 
 
-def test_headline_step_count():
-    """The 450x375 step: 48 launches (3 levels x 16 groups), 17 638 600 evals."""
-    work = bench.launches_and_work(375, 450, PAPER)
-    assert len(work) == 48
-    assert sum(wk["evals"] for wk in work) == 17638600
+def test_step_counts():
+    """Evals of one outer iteration: 17 638 600 on the 450x375 pair, 160 252 300 on the
+    1500x1000 headline pair (the library's lem_evals_per_iteration reports the same)."""
+    assert sum(wk["evals"] for wk in bench.iteration_work(375, 450, PAPER).values()) == 17638600
+    assert sum(wk["evals"] for wk in bench.iteration_work(1000, 1500, PAPER).values()) == 160252300
 
 
 @pytest.mark.parametrize("s,per_eval", [(5, 666), (15, 223), (25, 165)])

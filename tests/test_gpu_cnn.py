@@ -303,3 +303,48 @@ def test_trained_proposer_lowers_the_energy(torch_cuda):
     e_net = [e for e, _, _ in proposer.solve(with_net, 2, net)]
     print(f"energy after 1, 2 iterations: {e_base} alone, {e_net} with the proposer")
     assert e_net[1] < e_base[1]
+
+
+def _render_large(seed):
+    from synth import workload_pair
+    p = workload_pair("large_1500x1000", seed)
+    return {"left": p["left"], "right": p["right"]}
+
+
+def test_shipped_proposer_gains_on_held_out_1500x1000_scenes(torch_cuda):
+    """The shipped network (trained on 384x288 scenes only) on three held-out 1500x1000
+    scenes (seeds 100-102 of the large workload) under the batched schedule (4-candidate
+    visits, FP16 images): with one map candidate per visit at the finest level, the energy
+    after two outer iterations is lower than without it on the median scene, and the map
+    candidates account for part of the switched pixels (their acceptance rate, counted by
+    proposal kind in lem_stats)."""
+    import multiprocessing as mp
+    import os
+    from paper_1603_08328_gb300 import proposer
+    from paper_1603_08328_gb300.lem import LEM_STORE_F16, Stereo
+    if not os.path.exists(proposer.WEIGHTS):
+        pytest.skip("no trained weights")
+    seeds = [100, 101, 102]
+    with mp.get_context("spawn").Pool(3) as pool:
+        pairs = pool.map(_render_large, seeds)
+    net = proposer.load()
+    kw = dict(disp_max=400.0, store_dtype=LEM_STORE_F16, candidates_per_visit=4)
+    gains, shares = [], []
+    for s, pr in zip(seeds, pairs):
+        base = Stereo(pr["left"], pr["right"], seed=s, **kw)
+        with_net = Stereo(pr["left"], pr["right"], seed=s, k_cnn=(1, 0, 0), **kw)
+        e_base = base.iterate(2).energy
+        acc = acc_map = 0
+        for _ in range(2):
+            with_net.cnn_propose(net)
+            st = with_net.iterate(1)
+            acc += st.accepted
+            acc_map += st.accepted_by_kind[2]
+        gains.append(e_base - st.energy)
+        shares.append(acc_map / max(1, acc))
+        base.close()
+        with_net.close()
+    net.close()
+    print(f"energy gain after 2 iterations per scene: {gains}; share of switches from map candidates: {shares}")
+    assert float(np.median(gains)) > 0
+    assert min(shares) > 0

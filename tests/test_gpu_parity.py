@@ -334,6 +334,25 @@ def test_launch_configuration_does_not_change_results(torch_cuda):
     assert a.energy()[1] == b.energy()[1] == c.energy()[1]
 
 
+def test_work_queue_does_not_change_results(torch_cuda):
+    """Expansion launches that drain a work queue with the co-resident CTAs (work_queue = 1,
+    largest regions first) give the labels, cost cache and energy of one CTA per region,
+    bit for bit, with sequential and with 4-candidate visits, graph replay included."""
+    from paper_1603_08328_gb300.lem import Stereo
+    pair = workload_pair("middlebury_450x375", 6)
+    for visit in (1, 4):
+        base = dict(disp_max=60.0, seed=17, candidates_per_visit=visit)
+        a = Stereo(pair["left"], pair["right"], **base)
+        b = Stereo(pair["left"], pair["right"], work_queue=1, **base)
+        sa, sb = a.iterate(3), b.iterate(3)
+        assert sa.maxflow_limit == 0 and sb.maxflow_limit == 0
+        assert sa.evals == sb.evals == 3 * a.evals_per_iteration() and sa.accepted == sb.accepted
+        (la, _, ca), (lb, _, cb) = a.labels(), b.labels()
+        assert (la.cpu().numpy() == lb.cpu().numpy()).all()
+        assert (ca.cpu().numpy() == cb.cpu().numpy()).all()
+        assert a.energy()[1] == b.energy()[1]
+
+
 def test_two_propagation_visits_in_lockstep_with_oracle(tiny_pair, torch_cuda):
     """A level whose visit is two propagation candidates (the cluster visit of two CTAs),
     15 px cells on the tiny scene, group by group against the oracle."""
