@@ -9,8 +9,10 @@
 //   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = 128 pixels, N = Cout, K = 9 Cin)
 //                on tcgen05.mma with the accumulator in tensor memory
 //   input grad   dX        = the same kernel with flipped, transposed weights
-//   weight grad  dW[o][k]  = sum_p dZ[p][o] Xpatch[p][k]      (M = Cout, N = 9 Cin, K = pixels)
-//                on mma.sync m16n8k16 (M = Cout is below tcgen05's smallest M of 64)
+//   weight grad  dW^T[k][o] = sum_p Xpatch[p][k] dZ[p][o]     (M = 9 Cin, N = Cout, K = pixels)
+//                on tcgen05.mma: each CTA accumulates its pixel range in tensor
+//                memory and writes a partial sum; a second kernel adds the
+//                partials in a fixed order, so gradients are bit-reproducible
 // Activations are BF16, NHWC, channels padded to a multiple of 16; the weights
 // have an FP32 master copy updated by Adam.
 #include <cuda_bf16.h>
@@ -103,6 +105,20 @@ __device__ __forceinline__ bool mbar_wait0(uint32_t mbar, int limit) {
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
             : "r"(mbar)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// bounded wait for the phase of parity `parity` of an mbarrier; false if it gave up
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t mbar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
     }
@@ -247,69 +263,152 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tbase));
 }
 
-// dW[o][k] += sum_p dZ[p][o] Xpatch[p][k] over the CTA's 128 pixels; dB[o] += sum_p dZ[p][o].
-//   dZ : H*W*COUT bf16; X : H*W*CIN bf16; dW : COUT x 9CIN fp32 (atomic accumulation)
+// Weight gradient on the tensor cores: dW^T[k][o] = sum_p Xpatch[p][k] dZ[p][o]
+// as a GEMM with M = 9 CIN (padded to 128-row tiles), N = COUT and K = the
+// pixels.  Each CTA takes `tiles_per_cta` consecutive 128-pixel tiles; per tile
+// the patches (A, MP x 128 pixels) and dZ (B, COUT x 128 pixels) are written to
+// shared memory in the K-major core-matrix layout, and one thread issues the
+// MMAs of every M tile into the CTA's accumulator in tensor memory (accumulating
+// across the tiles).  The CTA then writes its partial dW (COUT x 9CIN, the
+// layout of gW) and bias partial (sum of dZ over its pixels, in pixel order) to
+// part / partb at its index; k_wgrad_reduce adds the partials in index order.
+//   X  : H*W*CIN bf16;  dZ : H*W*COUT bf16
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_conv_wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW,
-                                                    float *dB) {
-    constexpr int K = 9 * CIN, LDP = kTileP + 8;
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const bf16 *dZ, int H, int W,
+                                                           int tiles_per_cta, float *part, float *partb) {
+    constexpr int K = 9 * CIN, MT = (K + 127) / 128, MP = MT * 128, PC = kTileP / 8, CH = CIN / 8;
+    constexpr int TC = MT * COUT <= 32 ? 32 : (MT * COUT <= 64 ? 64 : (MT * COUT <= 128 ? 128 : 256));
     extern __shared__ __align__(128) unsigned char sm_raw[];
-    bf16 *At = reinterpret_cast<bf16 *>(sm_raw);  // [COUT][LDP]  dZ transposed (A: M = COUT, K = pixels)
-    bf16 *Bt = At + COUT * LDP;                   // [K][LDP]     Xpatch transposed (B col layout: N = K)
-    bf16 *Pt = Bt + K * LDP;                      // [kTileP][K]  patch staging (pixel-major)
+    unsigned char *As = sm_raw;                             // MP x 128 pixels
+    unsigned char *Bs = sm_raw + (size_t)MP * kTileP * 2;   // COUT x 128 pixels
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float s_db[COUT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = H * W, p0 = blockIdx.x * kTileP;
-    {
-        const int pl = tid >> 1, part = tid & 1;
-        const int p = p0 + pl;
-        if (p < n) {
-            gather_patch<CIN>(X, H, W, p % W, p / W, Pt + pl * K, part, 2);
-        } else {
-            for (int k = part * 8; k < K; k += 16) *reinterpret_cast<uint4 *>(Pt + pl * K + k) = make_uint4(0, 0, 0, 0);
-        }
+    const int n = H * W;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TC));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    for (int q = tid; q < kTileP * COUT; q += blockDim.x) {
-        const int pl = q / COUT, o = q - pl * COUT;
-        const int p = p0 + pl;
-        At[o * LDP + pl] = p < n ? dZ[(size_t)p * COUT + o] : __float2bfloat16_rn(0.f);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    __syncthreads();
-    for (int q = tid; q < kTileP * K; q += blockDim.x) {
-        const int pl = q / K, k = q - pl * K;
-        Bt[k * LDP + pl] = Pt[pl * K + k];
+    if (tid < COUT) s_db[tid] = 0.f;
+    // rows K .. MP of A are padding: zero once, never written again
+    for (int q = tid; q < (MP - K) * PC; q += kConvThreads) {
+        const int m = K + q / PC, c = q % PC;
+        *reinterpret_cast<uint4 *>(As + ((size_t)(m >> 3) * PC + c) * 128 + (m & 7) * 16) = make_uint4(0, 0, 0, 0);
     }
-    // bias gradient: one thread per output channel
-    if (tid < COUT) {
-        float s = 0.f;
-        for (int pl = 0; pl < kTileP; ++pl) s += __bfloat162float(At[tid * LDP + pl]);
-        atomicAdd(&dB[tid], s);
-    }
-    __syncthreads();
-    const int g = lane >> 2, t = lane & 3;
-    constexpr int MT = COUT / 16, NT = K / 8;
-    for (int tile = warp; tile < MT * NT; tile += 8) {
-        const int mt = tile / NT, nt = tile - mt * NT;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        const bf16 *Aw = At + (mt * 16) * LDP;
-        const bf16 *Bw = Bt + (nt * 8) * LDP;
+    bool ok = true;
+    int issued = 0;
+    for (int t = 0; t < tiles_per_cta; ++t) {
+        const int p0 = (blockIdx.x * tiles_per_cta + t) * kTileP;
+        if (p0 >= n) break;
+        // the MMAs of the previous tile read A and B: wait for them before refilling
+        if (issued > 0) ok = ok && mbar_wait_parity(smem_u32(&mbar), (uint32_t)((issued - 1) & 1), kMmaWaitLimit);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        {
+            // thread r: pixel r of the tile; its patch values are column r of A,
+            // its output gradient column r of B
+            const int r = tid, p = p0 + r;
+            const int u = p % W, v = p / W;
+            for (int c = 0; c < 9 * CH; ++c) {
+                const int tap = c / CH, c8 = c - tap * CH;
+                const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (p < n && uu >= 0 && uu < W && vv >= 0 && vv < H)
+                    val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
-        for (int k0 = 0; k0 < kTileP; k0 += 16) {
-            uint32_t a[4], b[2];
-            a[0] = ld_u32(Aw + g * LDP + k0 + t * 2);
-            a[1] = ld_u32(Aw + (g + 8) * LDP + k0 + t * 2);
-            a[2] = ld_u32(Aw + g * LDP + k0 + t * 2 + 8);
-            a[3] = ld_u32(Aw + (g + 8) * LDP + k0 + t * 2 + 8);
-            b[0] = ld_u32(Bw + g * LDP + k0 + t * 2);
-            b[1] = ld_u32(Bw + g * LDP + k0 + t * 2 + 8);
-            mma_bf16(acc, a, b);
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int o = mt * 16 + g + 8 * r, k = nt * 8 + 2 * t + c;
-                atomicAdd(&dW[(size_t)o * K + k], acc[2 * r + c]);
+                for (int j = 0; j < 8; ++j) {
+                    const int m = tap * CIN + c8 * 8 + j;
+                    *reinterpret_cast<bf16 *>(As + ((size_t)(m >> 3) * PC + (r >> 3)) * 128 + (m & 7) * 16 +
+                                              (r & 7) * 2) = e[j];
+                }
             }
+#pragma unroll
+            for (int c8 = 0; c8 < COUT / 8; ++c8) {
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (p < n) val = *reinterpret_cast<const uint4 *>(dZ + (size_t)p * COUT + c8 * 8);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&val);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int o = c8 * 8 + j;
+                    *reinterpret_cast<bf16 *>(Bs + ((size_t)(o >> 3) * PC + (r >> 3)) * 128 + (o & 7) * 16 +
+                                              (r & 7) * 2) = e[j];
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // bias partial: the tile's dZ summed in pixel order
+        if (tid < COUT) {
+            float sb = 0.f;
+            for (int r = 0; r < kTileP; ++r)
+                sb += __bfloat162float(*reinterpret_cast<const bf16 *>(
+                    Bs + ((size_t)(tid >> 3) * PC + (r >> 3)) * 128 + (tid & 7) * 16 + (r & 7) * 2));
+            s_db[tid] += sb;
+        }
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            constexpr uint32_t idesc = idesc_bf16(128, COUT);
+#pragma unroll 1
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll 1
+                for (int kk = 0; kk < kTileP / 16; ++kk) {
+                    const uint64_t ad = smem_desc(a0 + mt * 16 * PC * 128 + kk * 256, 128, PC * 128);
+                    const uint64_t bd = smem_desc(b0 + kk * 256, 128, PC * 128);
+                    mma_tc(tmem_base + (uint32_t)(mt * COUT), ad, bd, idesc, (issued > 0 || kk > 0) ? 1u : 0u);
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        ++issued;
+        // (the bias sums above read B before the next tile overwrites it)
+        __syncthreads();
+    }
+    if (issued > 0) ok = ok && mbar_wait_parity(smem_u32(&mbar), (uint32_t)((issued - 1) & 1), kMmaWaitLimit);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float *pw = part + (size_t)blockIdx.x * COUT * K;
+    if (issued > 0 && ok) {
+#pragma unroll 1
+        for (int mt = 0; mt < MT; ++mt) {
+            float acc[COUT];
+            tmem_load_row<COUT>(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * COUT), acc);
+            const int m = mt * 128 + warp * 32 + lane;
+            if (m < K)
+#pragma unroll
+                for (int o = 0; o < COUT; ++o) pw[(size_t)o * K + m] = acc[o];
+        }
+    } else {
+        // no tile, or a wait that gave up: this partial is zero
+        if (!ok && tid == 0) atomicAdd(&g_mma_timeouts, 1u);
+        if (!ok && tid == 0) mbar_wait_parity(smem_u32(&mbar), (uint32_t)((issued - 1) & 1), kMmaWaitLimit);
+        for (int q = tid; q < COUT * K; q += kConvThreads) pw[q] = 0.f;
+    }
+    if (tid < COUT) partb[(size_t)blockIdx.x * COUT + tid] = s_db[tid];
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base), "r"(TC));
+}
+
+// gW += sum over the G partials (in index order), gB likewise
+__global__ void k_wgrad_reduce(const float *part, const float *partb, int G, int KK, int COUT, float *gW, float *gB) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < KK) {
+        float s = 0.f;
+        for (int g = 0; g < G; ++g) s += part[(size_t)g * KK + i];
+        gW[i] += s;
+    } else if (i < KK + COUT) {
+        const int o = i - KK;
+        float s = 0.f;
+        for (int g = 0; g < G; ++g) s += partb[(size_t)g * COUT + o];
+        gB[o] += s;
     }
 }
 
@@ -402,9 +501,11 @@ template <int CIN, int COUT>
 size_t conv_smem() {
     return (size_t)2 * 9 * CIN * (kTileP + COUT);
 }
+constexpr int kWgParts = 148;  // most CTAs (partial sums) of one weight-gradient launch
+
 template <int CIN, int COUT>
 size_t wgrad_smem() {
-    return sizeof(bf16) * ((size_t)COUT * (kTileP + 8) + (size_t)9 * CIN * (kTileP + 8) + (size_t)kTileP * 9 * CIN);
+    return (size_t)2 * kTileP * ((9 * CIN + 127) / 128 * 128 + COUT);
 }
 
 template <int CIN, int COUT>
@@ -418,14 +519,20 @@ cudaError_t conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias,
     return cudaGetLastError();
 }
 
+// part: kWgParts * COUT * 9CIN floats, partb: kWgParts * COUT floats (scratch)
 template <int CIN, int COUT>
-cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW, float *dB, cudaStream_t st) {
+cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW, float *dB, float *part, float *partb,
+                  cudaStream_t st) {
     const size_t sm = wgrad_smem<CIN, COUT>();
-    cudaError_t e =
-        cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int nb = (H * W + kTileP - 1) / kTileP;
-    k_conv_wgrad<CIN, COUT><<<nb, 256, sm, st>>>(X, dZ, H, W, dW, dB);
+    const int tiles = (H * W + kTileP - 1) / kTileP;
+    const int per = (tiles + kWgParts - 1) / kWgParts;
+    const int G = (tiles + per - 1) / per;
+    k_wgrad_tc<CIN, COUT><<<G, kConvThreads, sm, st>>>(X, dZ, H, W, per, part, partb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int KK = COUT * 9 * CIN;
+    k_wgrad_reduce<<<(KK + COUT + 255) / 256, 256, 0, st>>>(part, partb, G, KK, COUT, dW, dB);
     return cudaGetLastError();
 }
 
@@ -439,6 +546,7 @@ struct lem_cnn {
     float *mw[kLayers] = {}, *vw[kLayers] = {}, *mb[kLayers] = {}, *vb[kLayers] = {};
     bf16 *Bt[kLayers] = {}, *Bf[kLayers] = {};    // forward / input-gradient GEMM layouts
     float *gW[kLayers] = {}, *gB[kLayers] = {};   // gradients (padded GEMM layout)
+    float *wpart = nullptr, *wpartb = nullptr;    // per-CTA partials of the weight gradient
     // activations for one image of up to cap pixels
     size_t cap = 0;
     bf16 *act[kLayers + 1] = {};                  // layer inputs (bf16), act[0] = packed input
@@ -513,9 +621,9 @@ cudaError_t backward(lem_cnn *net, int H4, int W4) {
     cudaError_t e = cudaSuccess;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         // weight gradient of layer l: input act[l], output gradient dz
-        if (l == 5) e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, net->gW[5], net->gB[5], st);
-        else if (l == 0) e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, net->gW[0], net->gB[0], st);
-        else e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, net->gW[l], net->gB[l], st);
+        if (l == 5) e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, net->gW[5], net->gB[5], net->wpart, net->wpartb, st);
+        else if (l == 0) e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, net->gW[0], net->gB[0], net->wpart, net->wpartb, st);
+        else e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, net->gW[l], net->gB[l], net->wpart, net->wpartb, st);
         if (e != cudaSuccess || l == 0) break;
         // input gradient: conv of dz with the flipped, transposed weights
         if (l == 5) e = conv<16, 32>(net->dz, H4, W4, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
@@ -615,6 +723,8 @@ int lem_cnn_create(uint64_t seed, void *stream, lem_cnn **out) {
         if (e != cudaSuccess) return bail(cnn_fail(net, e, "lem_cnn_create"));
     }
     cudaError_t e = cudaMalloc(&net->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->wpart, sizeof(float) * kWgParts * 32 * 9 * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&net->wpartb, sizeof(float) * kWgParts * 32);
     if (e != cudaSuccess) return bail(cnn_fail(net, e, "lem_cnn_create"));
     *out = net;
     return LEM_OK;
@@ -633,6 +743,8 @@ int lem_cnn_destroy(lem_cnn *net) {
     cudaFree(net->dz);
     cudaFree(net->dx);
     cudaFree(net->loss);
+    cudaFree(net->wpart);
+    cudaFree(net->wpartb);
     cudaFree(net->xin);
     cudaFree(net->tgt);
     delete net;
