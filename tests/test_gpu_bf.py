@@ -114,6 +114,7 @@ def test_bf_expand_groups_in_lockstep_with_oracle(tiny_pair, torch_cuda):
     o.init_state()
     q_prev = g.energy()[1]
     flips = switched = 0
+    per_group = []  # differing pixels of each (iteration, group), each re-synchronised
     for it in range(3):
         for grp in range(16):
             st = g.expand_group(it, 0, grp)
@@ -121,13 +122,16 @@ def test_bf_expand_groups_in_lockstep_with_oracle(tiny_pair, torch_cuda):
             assert st.maxflow_limit == 0
             abc = g.labels()[0].cpu().numpy()
             lab, _ = o.state()
-            flips += int((abc != lab).any(axis=-1).sum())
+            per_group.append(int((abc != lab).any(axis=-1).sum()))
+            flips += per_group[-1]
             switched += acc
             o.set_labels(abc)
             q = g.energy()[1]
             assert q <= q_prev
             q_prev = q
     print(f"LE-BF lockstep: {flips} differing pixels over {switched} switches")
+    print(f"  differing pixels per (iteration, group) where nonzero: "
+          f"{[(i, d) for i, d in enumerate(per_group) if d]}")
     assert switched > 0
     assert flips <= max(10, 0.002 * switched)
 
