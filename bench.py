@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
+    ap.add_argument("--launch-config", default=None,
+                    help="fixed launch configuration instead of the autotuner's, as threads/relabel interval/"
+                         "strip rows per level, e.g. 256,512,512/8,16,16/12,32,12 (for profiling captures)")
     ap.add_argument("--no-time-to-energy", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the extra blocks (proposer, LE-BF, V3, 450x375)")
@@ -715,7 +718,11 @@ def run_lem(args):
     warm = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=1000 + rank, **params)
     warm.iterate(min(ITERS_PER_HANDLE, max(1, args.warmup)), stats=False)
     tuned, tuning = {}, "default"
-    if not args.no_tune:
+    if args.launch_config:
+        th, gr, sr = ([int(x) for x in part.split(",")] for part in args.launch_config.split("/"))
+        tuned = dict(level_threads=th, level_gr_interval=gr, level_strip_rows=sr)
+        tuning = dict(tuned, fixed=True)
+    elif not args.no_tune:
         t = warm.autotune(repeats=1)
         tuned = dict(level_threads=list(t.threads), level_gr_interval=list(t.gr_interval),
                      level_strip_rows=list(t.strip_rows))

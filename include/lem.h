@@ -547,8 +547,11 @@ int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *y);
 /* Loss and gradients over n_images inputs x (DEVICE, n*H4*W4*7) with targets
  * t (DEVICE, n*H4*W4*3): loss = mean over images and pixels of
  * sum_c scale_c |y_c - t_c|.  scale: HOST, 3 floats.  loss: HOST float or NULL;
- * grads: HOST array in the lem_cnn_get_params order, or NULL.  Synchronises
- * the stream.  Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
+ * grads: HOST array in the lem_cnn_get_params order, or NULL.  All images go
+ * through each layer together (one launch per layer and pass), so the network
+ * holds activations for n*H4*W4 pixels (about 1.3 KB each; grown on demand,
+ * kept until lem_cnn_destroy).  Synchronises the stream.  Errors: LEM_ERR_ARG
+ * (also when n*H4*W4*32 exceeds 2^31 - 1), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_gradients(lem_cnn *net, const float *x, const float *t, int n_images, int H4, int W4,
                       const float *scale, float *loss, float *grads);
 /* lem_cnn_gradients, then one Adam step (beta 0.9 / 0.999, eps 1e-8, rate lr). */

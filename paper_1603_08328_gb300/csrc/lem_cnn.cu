@@ -49,23 +49,6 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Gathers the 3x3 x CIN patch of pixel (u, v) (zero outside the image) into
-// dst[0 .. 9*CIN), k = (i*3 + j)*CIN + c.
-template <int CIN>
-__device__ __forceinline__ void gather_patch(const bf16 *X, int H, int W, int u, int v, bf16 *dst, int part,
-                                             int nparts) {
-    // 16-byte chunks of 8 channels
-    constexpr int CH = CIN / 8;
-    for (int q = part; q < 9 * CH; q += nparts) {
-        const int tap = q / CH, c8 = q - tap * CH;
-        const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (uu >= 0 && uu < W && vv >= 0 && vv < H)
-            val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
-        *reinterpret_cast<uint4 *>(dst + tap * CIN + c8 * 8) = val;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor core) helpers.  Operands sit in shared memory
 // in the no-swizzle K-major canonical layout: 8-row x 16-byte core matrices,
@@ -163,10 +146,12 @@ static_assert(kConvThreads == kTileP, "one thread per pixel row of the tile");
 // (B, COUT x K, both K-major) are staged in shared memory, one thread issues
 // K/16 tcgen05.mma into a TMEM accumulator, and each warp reads its 32 rows
 // back for the epilogue.
-//   X  : H*W*CIN bf16;  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]);
-//   Z  : optional fp32 pre-activation H*W*COUT;  Y : optional bf16 output (ReLU if relu)
+// B images of H x W pixels are stacked row after row; a patch never reaches
+// across an image's border (zero padding as for a single image).
+//   X  : B*H*W*CIN bf16;  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]);
+//   Z  : optional fp32 pre-activation B*H*W*COUT;  Y : optional bf16 output (ReLU if relu)
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int W, const bf16 *Bt,
+__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int W, int B, const bf16 *Bt,
                                                        const float *bias, float *Z, bf16 *Y, int relu) {
     constexpr int K = 9 * CIN, KC = K / 8, CH = CIN / 8;
     extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -175,7 +160,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = H * W, p0 = blockIdx.x * kTileP;
+    const int n = H * W * B, p0 = blockIdx.x * kTileP;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -194,13 +179,13 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
     {
         const int r = tid, p = p0 + r;
         unsigned char *row = As + (size_t)(r >> 3) * KC * 128 + (r & 7) * 16;
-        const int u = p % W, v = p / W;
+        const int u = p % W, y = p / W, v = y % H;  // row of the stacked images, row within the image
         for (int c = 0; c < KC; ++c) {
             const int tap = c / CH, c8 = c - tap * CH;
-            const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
+            const int uu = u + tap % 3 - 1, dv = tap / 3 - 1;
             uint4 val = make_uint4(0, 0, 0, 0);
-            if (p < n && uu >= 0 && uu < W && vv >= 0 && vv < H)
-                val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
+            if (p < n && uu >= 0 && uu < W && v + dv >= 0 && v + dv < H)
+                val = *reinterpret_cast<const uint4 *>(X + ((size_t)(y + dv) * W + uu) * CIN + c8 * 8);
             *reinterpret_cast<uint4 *>(row + c * 128) = val;
         }
     }
@@ -272,9 +257,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
 // across the tiles).  The CTA then writes its partial dW (COUT x 9CIN, the
 // layout of gW) and bias partial (sum of dZ over its pixels, in pixel order) to
 // part / partb at its index; k_wgrad_reduce adds the partials in index order.
-//   X  : H*W*CIN bf16;  dZ : H*W*COUT bf16
+//   X  : B*H*W*CIN bf16 (B stacked images, as in k_conv);  dZ : B*H*W*COUT bf16
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const bf16 *dZ, int H, int W,
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const bf16 *dZ, int H, int W, int B,
                                                            int tiles_per_cta, float *part, float *partb) {
     constexpr int K = 9 * CIN, MT = (K + 127) / 128, MP = MT * 128, PC = kTileP / 8, CH = CIN / 8;
     constexpr int TC = MT * COUT <= 32 ? 32 : (MT * COUT <= 64 ? 64 : (MT * COUT <= 128 ? 128 : 256));
@@ -285,7 +270,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const 
     __shared__ uint32_t tmem_base;
     __shared__ float s_db[COUT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = H * W;
+    const int n = H * W * B;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                      "r"(TC));
@@ -313,13 +298,13 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const 
             // thread r: pixel r of the tile; its patch values are column r of A,
             // its output gradient column r of B
             const int r = tid, p = p0 + r;
-            const int u = p % W, v = p / W;
+            const int u = p % W, y = p / W, v = y % H;  // as in k_conv
             for (int c = 0; c < 9 * CH; ++c) {
                 const int tap = c / CH, c8 = c - tap * CH;
-                const int uu = u + tap % 3 - 1, vv = v + tap / 3 - 1;
+                const int uu = u + tap % 3 - 1, dv = tap / 3 - 1;
                 uint4 val = make_uint4(0, 0, 0, 0);
-                if (p < n && uu >= 0 && uu < W && vv >= 0 && vv < H)
-                    val = *reinterpret_cast<const uint4 *>(X + ((size_t)vv * W + uu) * CIN + c8 * 8);
+                if (p < n && uu >= 0 && uu < W && v + dv >= 0 && v + dv < H)
+                    val = *reinterpret_cast<const uint4 *>(X + ((size_t)(y + dv) * W + uu) * CIN + c8 * 8);
                 const bf16 *e = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -509,27 +494,27 @@ size_t wgrad_smem() {
 }
 
 template <int CIN, int COUT>
-cudaError_t conv(const bf16 *X, int H, int W, const bf16 *Bt, const float *bias, float *Z, bf16 *Y, int relu,
-                 cudaStream_t st) {
+cudaError_t conv(const bf16 *X, int H, int W, int B, const bf16 *Bt, const float *bias, float *Z, bf16 *Y,
+                 int relu, cudaStream_t st) {
     const size_t sm = conv_smem<CIN, COUT>();
     cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int nb = (H * W + kTileP - 1) / kTileP;
-    k_conv<CIN, COUT><<<nb, kConvThreads, sm, st>>>(X, H, W, Bt, bias, Z, Y, relu);
+    const int nb = (H * W * B + kTileP - 1) / kTileP;
+    k_conv<CIN, COUT><<<nb, kConvThreads, sm, st>>>(X, H, W, B, Bt, bias, Z, Y, relu);
     return cudaGetLastError();
 }
 
 // part: kWgParts * COUT * 9CIN floats, partb: kWgParts * COUT floats (scratch)
 template <int CIN, int COUT>
-cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, float *dW, float *dB, float *part, float *partb,
-                  cudaStream_t st) {
+cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, int B, float *dW, float *dB, float *part,
+                  float *partb, cudaStream_t st) {
     const size_t sm = wgrad_smem<CIN, COUT>();
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int tiles = (H * W + kTileP - 1) / kTileP;
+    const int tiles = (H * W * B + kTileP - 1) / kTileP;
     const int per = (tiles + kWgParts - 1) / kWgParts;
     const int G = (tiles + per - 1) / per;
-    k_wgrad_tc<CIN, COUT><<<G, kConvThreads, sm, st>>>(X, dZ, H, W, per, part, partb);
+    k_wgrad_tc<CIN, COUT><<<G, kConvThreads, sm, st>>>(X, dZ, H, W, B, per, part, partb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int KK = COUT * 9 * CIN;
     k_wgrad_reduce<<<(KK + COUT + 255) / 256, 256, 0, st>>>(part, partb, G, KK, COUT, dW, dB);
@@ -547,14 +532,14 @@ struct lem_cnn {
     bf16 *Bt[kLayers] = {}, *Bf[kLayers] = {};    // forward / input-gradient GEMM layouts
     float *gW[kLayers] = {}, *gB[kLayers] = {};   // gradients (padded GEMM layout)
     float *wpart = nullptr, *wpartb = nullptr;    // per-CTA partials of the weight gradient
-    // activations for one image of up to cap pixels
+    // activations of up to cap pixels (all images of a training step, stacked)
     size_t cap = 0;
     bf16 *act[kLayers + 1] = {};                  // layer inputs (bf16), act[0] = packed input
     float *pre[kLayers] = {};                     // pre-activations (fp32)
     bf16 *dz = nullptr;                           // d loss / d pre-activation (bf16, 32 ch)
     float *dx = nullptr;                          // d loss / d layer input (fp32, 32 ch)
     float *loss = nullptr;
-    float *xin = nullptr, *tgt = nullptr;         // staging of one image's input / target
+    float *xin = nullptr, *tgt = nullptr;         // staging of an input / target
     int step = 0;
     std::string err;
 };
@@ -604,30 +589,33 @@ int ensure_capacity(lem_cnn *net, size_t npix) {
     return LEM_OK;
 }
 
-cudaError_t forward(lem_cnn *net, int H4, int W4) {
+cudaError_t forward(lem_cnn *net, int H4, int W4, int B) {
     cudaStream_t st = net->st;
-    cudaError_t e = conv<16, 32>(net->act[0], H4, W4, net->Bt[0], net->b[0], net->pre[0], net->act[1], 1, st);
+    cudaError_t e = conv<16, 32>(net->act[0], H4, W4, B, net->Bt[0], net->b[0], net->pre[0], net->act[1], 1, st);
     for (int l = 1; l < 5 && e == cudaSuccess; ++l)
-        e = conv<32, 32>(net->act[l], H4, W4, net->Bt[l], net->b[l], net->pre[l], net->act[l + 1], 1, st);
-    if (e == cudaSuccess) e = conv<32, 16>(net->act[5], H4, W4, net->Bt[5], net->b[5], net->pre[5], nullptr, 0, st);
+        e = conv<32, 32>(net->act[l], H4, W4, B, net->Bt[l], net->b[l], net->pre[l], net->act[l + 1], 1, st);
+    if (e == cudaSuccess) e = conv<32, 16>(net->act[5], H4, W4, B, net->Bt[5], net->b[5], net->pre[5], nullptr, 0, st);
     return e;
 }
 
-// backward of one image from d loss / d output (in net->dz, 16 channels);
-// accumulates into gW / gB
-cudaError_t backward(lem_cnn *net, int H4, int W4) {
+// backward of B stacked images from d loss / d output (in net->dz, 16
+// channels); accumulates into gW / gB
+cudaError_t backward(lem_cnn *net, int H4, int W4, int B) {
     cudaStream_t st = net->st;
-    const int n = H4 * W4;
+    const int n = H4 * W4 * B;
     cudaError_t e = cudaSuccess;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         // weight gradient of layer l: input act[l], output gradient dz
-        if (l == 5) e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, net->gW[5], net->gB[5], net->wpart, net->wpartb, st);
-        else if (l == 0) e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, net->gW[0], net->gB[0], net->wpart, net->wpartb, st);
-        else e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, net->gW[l], net->gB[l], net->wpart, net->wpartb, st);
+        if (l == 5)
+            e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, B, net->gW[5], net->gB[5], net->wpart, net->wpartb, st);
+        else if (l == 0)
+            e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, B, net->gW[0], net->gB[0], net->wpart, net->wpartb, st);
+        else
+            e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, B, net->gW[l], net->gB[l], net->wpart, net->wpartb, st);
         if (e != cudaSuccess || l == 0) break;
         // input gradient: conv of dz with the flipped, transposed weights
-        if (l == 5) e = conv<16, 32>(net->dz, H4, W4, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
-        else e = conv<32, 32>(net->dz, H4, W4, net->Bf[l], nullptr, net->dx, nullptr, 0, st);
+        if (l == 5) e = conv<16, 32>(net->dz, H4, W4, B, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
+        else e = conv<32, 32>(net->dz, H4, W4, B, net->Bf[l], nullptr, net->dx, nullptr, 0, st);
         if (e != cudaSuccess) break;
         // ReLU of layer l-1
         const int cnt = n * kCout[l - 1];
@@ -792,7 +780,7 @@ int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
     if (rc != LEM_OK) return rc;
     k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, (int)n, net->act[0]);
     CNN_CUDA(net, cudaGetLastError());
-    CNN_CUDA(net, forward(net, H4, W4));
+    CNN_CUDA(net, forward(net, H4, W4, 1));
     k_take3<<<(int)((n * 3 + 255) / 256), 256, 0, net->st>>>(net->pre[5], (int)n, out);
     CNN_CUDA(net, cudaGetLastError());
     return LEM_OK;
@@ -801,7 +789,10 @@ int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
 int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_images, int H4, int W4,
                       const float *scale, float *loss, float *grads) {
     if (!net || !x || !target || n_images < 1 || H4 < 1 || W4 < 1 || !scale) return LEM_ERR_ARG;
-    const size_t n = (size_t)H4 * W4;
+    // all images go through each layer in one launch: the batch is stacked as
+    // one (n_images * H4) x W4 grid whose patches stop at each image's border
+    const size_t n = (size_t)H4 * W4 * n_images;
+    if (n * 32 > (size_t)INT32_MAX) return LEM_ERR_ARG;
     int rc = ensure_capacity(net, n);
     if (rc != LEM_OK) return rc;
     for (int l = 0; l < kLayers; ++l) {
@@ -809,16 +800,14 @@ int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_i
         CNN_CUDA(net, cudaMemsetAsync(net->gB[l], 0, sizeof(float) * kCout[l], net->st));
     }
     CNN_CUDA(net, cudaMemsetAsync(net->loss, 0, sizeof(float), net->st));
-    const float inv_n = 1.f / (float)(n * n_images);
-    for (int i = 0; i < n_images; ++i) {
-        k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x + i * n * 7, (int)n, net->act[0]);
-        CNN_CUDA(net, cudaGetLastError());
-        CNN_CUDA(net, forward(net, H4, W4));
-        k_l1_loss<<<(int)((n + 255) / 256), 256, 0, net->st>>>(net->pre[5], target + i * n * 3, (int)n, scale[0],
-                                                             scale[1], scale[2], inv_n, net->dz, net->loss);
-        CNN_CUDA(net, cudaGetLastError());
-        CNN_CUDA(net, backward(net, H4, W4));
-    }
+    const float inv_n = 1.f / (float)n;
+    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, (int)n, net->act[0]);
+    CNN_CUDA(net, cudaGetLastError());
+    CNN_CUDA(net, forward(net, H4, W4, n_images));
+    k_l1_loss<<<(int)((n + 255) / 256), 256, 0, net->st>>>(net->pre[5], target, (int)n, scale[0], scale[1], scale[2],
+                                                         inv_n, net->dz, net->loss);
+    CNN_CUDA(net, cudaGetLastError());
+    CNN_CUDA(net, backward(net, H4, W4, n_images));
     if (loss) CNN_CUDA(net, cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, net->st));
     if (grads) {
         // real-channel gradients in the (3,3,ci,co) + bias order of lem_cnn_get_params

@@ -145,6 +145,34 @@ def test_gradients_match_oracle(torch_cuda):
         assert f1 <= GRAD_TOL and f2 <= GRAD_TOL
 
 
+def test_stacked_batch_equals_the_mean_of_single_images(torch_cuda):
+    """A training batch goes through each layer as one stacked grid of n_images x H4 rows.
+    Its loss and gradients equal the mean of the single-image calls (n = 4, a power of two,
+    so every bfloat16 rounding of the 1/n-scaled loss gradient scales exactly and only the
+    FP32 summation order differs); a 3x3 patch that reached across an image border would
+    move the border rows' terms far beyond that.  H4 x W4 = 17 x 29 (493 pixels) puts the
+    image borders inside pixel tiles."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import ProposalNet
+    net = ProposalNet(seed=0)
+    net.set_params(_flat(_params(5)))
+    rng = np.random.default_rng(21)
+    n, H4, W4 = 4, 17, 29
+    x = rng.uniform(0.0, 1.0, size=(n, H4, W4, 7)).astype(np.float32)
+    t = rng.uniform(-0.5, 0.5, size=(n, H4, W4, 3)).astype(np.float32)
+    xc, tc = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss, g = net.gradients(xc, tc)
+    singles = [net.gradients(xc[i:i + 1].contiguous(), tc[i:i + 1].contiguous()) for i in range(n)]
+    loss_mean = sum(s[0] for s in singles) / n
+    g_mean = np.mean([np.asarray(s[1], np.float64) for s in singles], axis=0)
+    err = _nerr(g, g_mean)
+    print(f"stacked batch of {n}: loss {loss:.6f} vs mean {loss_mean:.6f}, gradient error {err:.2e}")
+    assert loss == pytest.approx(loss_mean, rel=1e-5)
+    assert err <= 1e-5
+    for (gw, gb), (mw, mb) in zip(net.unflatten(g), net.unflatten(g_mean)):
+        assert _nerr(gw, mw) <= 1e-4 and _nerr(gb, mb) <= 1e-4
+
+
 def test_gradients_are_bit_reproducible_and_match_on_a_large_grid(torch_cuda):
     """The weight gradients come from per-CTA partial sums in tensor memory added in a fixed
     order: two passes over the same batch give the same bits.  On a 200 x 120 grid (188
@@ -291,6 +319,7 @@ def test_map_candidates_in_lockstep_with_oracle(torch_cuda, tiny_pair):
     assert (g.proposals().cpu().numpy() == gt_map).all()
     q_prev = g.energy()[1]
     flips = switched = 0
+    per_group = []  # differing pixels of each (iteration, group), each re-synchronised
     for it in range(2):
         for grp in range(16):
             st = g.expand_group(it, 0, grp)
@@ -298,13 +327,16 @@ def test_map_candidates_in_lockstep_with_oracle(torch_cuda, tiny_pair):
             assert st.maxflow_limit == 0
             abc = g.labels()[0].cpu().numpy()
             lab, _ = o.state()
-            flips += int((abc != lab).any(axis=-1).sum())
+            per_group.append(int((abc != lab).any(axis=-1).sum()))
+            flips += per_group[-1]
             switched += acc
             o.set_labels(abc)
             q = g.energy()[1]
             assert q <= q_prev
             q_prev = q
     print(f"map lockstep: {flips} differing pixels over {switched} switches")
+    print(f"  differing pixels per (iteration, group) where nonzero: "
+          f"{[(i, d) for i, d in enumerate(per_group) if d]}")
     assert flips <= max(10, 0.002 * switched)
     st = g.iterate(1)
     assert st.evals == g.evals_per_iteration()
