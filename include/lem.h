@@ -147,6 +147,15 @@ typedef struct {
                              once, each taking regions from a work queue (largest first) until none
                              is left; 0 (default): one CTA per region.  The regions of a group are
                              independent, so the results are the same. */
+    int dataflow;         /* 1: lem_expand_iteration runs each level as one launch instead of 16: the
+                             regions of all 16 groups drain one work queue in group order, and a region
+                             starts once every region of an earlier group within three cells of it (the
+                             regions whose moves read or write its labels or the one-pixel ring around
+                             them) is done.  Regions that touch each other still move in group order
+                             and the others commute, so the labels are those of the 16 group launches,
+                             bit for bit; a slow region holds up only its neighbours.  Levels with
+                             split_visits or the multi-CTA cut keep their group launches; the two-CTA
+                             cluster visit is not used.  0 (default): one launch per group. */
 } lem_params;
 
 /* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
@@ -169,6 +178,10 @@ typedef struct {
     int64_t pr_bfs_levels; /* BFS frontiers processed by the global relabels           */
     int64_t accepted_by_kind[4]; /* switched pixels by proposal kind: propagation, RANSAC,
                                     map (learned proposer), perturbation                   */
+    int64_t dep_waits_given_up; /* dataflow launches: regions that stopped waiting for a
+                                   neighbour after the wait limit (about 2 s) and moved anyway;
+                                   nonzero means the labels are not valid (reported by
+                                   lem_expand_iteration as LEM_ERR_CUDA when stats are read) */
 } lem_stats;
 
 typedef struct lem_handle lem_handle;

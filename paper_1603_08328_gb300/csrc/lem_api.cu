@@ -32,6 +32,8 @@ struct lem_handle {
     float *phiK = nullptr;
     float4 *alphaK = nullptr;
     int *d_queue = nullptr;             // work-queue counters of the 48 (level, group) launches
+    unsigned *d_done = nullptr;         // dataflow launches: one done flag per cell of a level (all pairs)
+    int done_cnt[3] = {0, 0, 0};        // cells of each level over all pairs
     bool split_level[3] = {false, false, false};
     float4 *prop = nullptr;             // proposal maps (allocated when some k_cnn > 0)
     bool prop_set = false;
@@ -219,6 +221,7 @@ int check_params(const lem_params *p) {
     if (p->cluster_visits != 0 && p->cluster_visits != 1) return fail(nullptr, LEM_ERR_ARG, "cluster_visits must be 0 or 1");
     if (p->split_visits != 0 && p->split_visits != 1) return fail(nullptr, LEM_ERR_ARG, "split_visits must be 0 or 1");
     if (p->work_queue != 0 && p->work_queue != 1) return fail(nullptr, LEM_ERR_ARG, "work_queue must be 0 or 1");
+    if (p->dataflow != 0 && p->dataflow != 1) return fail(nullptr, LEM_ERR_ARG, "dataflow must be 0 or 1");
     if (p->candidates_per_visit < 1 || p->candidates_per_visit > 8)
         return fail(nullptr, LEM_ERR_ARG, "candidates_per_visit must be 1..8");
     if (p->threads < 32 || p->threads > 1024 || p->threads % 32)
@@ -254,6 +257,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->phiK);
     cudaFree(h->alphaK);
     cudaFree(h->d_queue);
+    cudaFree(h->d_done);
     cudaFree(h->prop);
     cudaFree(h->cnn_buf);
     cudaFree(h->e_part);
@@ -342,6 +346,7 @@ int read_counters(lem_handle *h, lem_stats *stats) {
     stats->pr_global_relabels = (int64_t)(c.relabels - h->last.relabels);
     stats->pr_bfs_levels = (int64_t)(c.bfs_levels - h->last.bfs_levels);
     for (int k = 0; k < 4; ++k) stats->accepted_by_kind[k] = (int64_t)(c.accepted_kind[k] - h->last.accepted_kind[k]);
+    stats->dep_waits_given_up = (int64_t)(c.dep_give_ups - h->last.dep_give_ups);
     stats->fp64_inverses = h->fp64_inverses;
     stats->iterations = h->iter;
     h->last = c;
@@ -476,18 +481,28 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
     CREATE_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(lem::Counters), h->st));
     CREATE_CUDA(cudaMemcpyAsync(h->d_pairs, h->pairs.data(), sizeof(lem::PairDesc) * n_pairs, cudaMemcpyHostToDevice,
                                 h->st));
-    // work items of every (level, group): (pair, cell i, cell j)
+    // work items of every (level, group): (pair, cell i, cell j, index of the
+    // pair's cell (0, 0) among the level's done flags)
     {
         std::vector<int4> items;
+        int max_cells = 1;
         for (int l = 0; l < p->n_levels; ++l) {
             const int s = p->cell[l];
+            std::vector<int> base(n_pairs);
+            int cells = 0;
+            for (int b = 0; b < n_pairs; ++b) {
+                base[b] = cells;
+                cells += ((h->pairs[b].W + s - 1) / s) * ((h->pairs[b].H + s - 1) / s);
+            }
+            h->done_cnt[l] = cells;
+            max_cells = std::max(max_cells, cells);
             for (int g = 0; g < 16; ++g) {
                 h->item_off[l][g] = (int)items.size();
                 const int gi = g & 3, gj = g >> 2;
                 for (int b = 0; b < n_pairs; ++b) {
                     const int nx = (h->pairs[b].W + s - 1) / s, ny = (h->pairs[b].H + s - 1) / s;
                     for (int cj = gj; cj < ny; cj += 4)
-                        for (int ci = gi; ci < nx; ci += 4) items.push_back(make_int4(b, ci, cj, 0));
+                        for (int ci = gi; ci < nx; ci += 4) items.push_back(make_int4(b, ci, cj, base[b]));
                 }
                 h->item_cnt[l][g] = (int)items.size() - h->item_off[l][g];
                 // largest regions first (the clipped border regions of every pair last), so
@@ -503,6 +518,7 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
                                  [&](const int4 &a, const int4 &b) { return area(a) > area(b); });
             }
         }
+        if (p->dataflow) CREATE_CUDA(cudaMalloc(&h->d_done, sizeof(unsigned) * max_cells));
         CREATE_CUDA(cudaMalloc(&h->d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
         CREATE_CUDA(cudaMemcpy(h->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     }
@@ -790,7 +806,29 @@ static int expand_group_impl(lem_handle *h, int iter, int level, int group, cuda
     LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
                                          h->maxH, h->d_items + h->item_off[level][group], h->item_cnt[level][group],
                                          h->lab, h->phiA, h->prop, h->ctr, h->p.cluster_visits ? h->phiB : nullptr,
-                                         h->p.work_queue ? h->d_queue + 2 * (16 * level + group) : nullptr, st));
+                                         h->p.work_queue ? h->d_queue + 2 * (16 * level + group) : nullptr, nullptr,
+                                         st));
+    return ktime_mark(h, LEM_KERNEL_EXPAND, level, st);
+}
+
+// all 16 groups of one level: one dataflow launch (dataflow = 1, on levels
+// with one-kernel visits on the CTA cut), else 16 group launches
+static int expand_level_impl(lem_handle *h, int iter, int level, cudaStream_t st) {
+    if (!h->p.dataflow || h->split_level[level] || h->grid_level[level]) {
+        int rc = LEM_OK;
+        for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, iter, level, g, st);
+        return rc;
+    }
+    if (h->prop && !h->prop_set)
+        return fail(h, LEM_ERR_ARG, "k_cnn > 0 but no proposal map was set (lem_set_proposals / lem_cnn_propose)");
+    const lem::Level lv = level_of(h, level);
+    const lem::KParams kp = kparams_level(h, level);
+    const int first = h->item_off[level][0];
+    const int n_items = h->item_off[level][15] + h->item_cnt[level][15] - first;
+    LEM_CUDA(h, cudaMemsetAsync(h->d_done, 0, sizeof(unsigned) * h->done_cnt[level], st));
+    LEM_CUDA(h, lem::launch_expand_group(planes_base(h), kp, lv, level, iter, h->d_iter, h->d_pairs, h->maxW,
+                                         h->maxH, h->d_items + first, n_items, h->lab, h->phiA, h->prop, h->ctr,
+                                         nullptr, h->d_queue + 2 * (16 * level), h->d_done, st));
     return ktime_mark(h, LEM_KERNEL_EXPAND, level, st);
 }
 
@@ -809,8 +847,7 @@ static int build_graph(lem_handle *h) {
     LEM_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
     h->capturing = true;
     int rc = ktime_mark(h, -1, 0, h->cap_st);
-    for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
-        for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, -1, l, g, h->cap_st);
+    for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) rc = expand_level_impl(h, -1, l, h->cap_st);
     cudaError_t e = rc == LEM_OK ? lem::launch_increment(h->d_iter, h->cap_st) : cudaSuccess;
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
@@ -856,8 +893,7 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
         // the first iteration runs directly (it also sets the kernels' shared
         // memory limits), the graph is captured for the following ones
         int rc = ktime_mark(h, -1, 0, h->st);
-        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
-            for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, h->iter, l, g, h->st);
+        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) rc = expand_level_impl(h, h->iter, l, h->st);
         if (rc != LEM_OK) return rc;
         h->kn_last = h->kn;
         ++h->iter;
@@ -875,8 +911,7 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     }
     for (; done < n_iters; ++done) {
         int rc = ktime_mark(h, -1, 0, h->st);
-        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l)
-            for (int g = 0; g < 16 && rc == LEM_OK; ++g) rc = expand_group_impl(h, h->iter, l, g, h->st);
+        for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) rc = expand_level_impl(h, h->iter, l, h->st);
         if (rc != LEM_OK) return rc;
         h->kn_last = h->kn;
         ++h->iter;
@@ -888,6 +923,8 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
         if ((rc = read_counters(h, stats)) != LEM_OK) return rc;
         stats->energy_q = eq;
         stats->energy = (double)eq / h->p.quant_scale;
+        if (stats->dep_waits_given_up > 0)
+            return fail(h, LEM_ERR_CUDA, "a dataflow region gave up waiting for a neighbour; the labels are not valid");
     }
     return LEM_OK;
 }
@@ -1154,17 +1191,24 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
     lem_tuning res{};
     int rc = e == cudaSuccess ? LEM_OK : cuda_fail(h, e, "lem_autotune setup");
     const lem_params keep = h->p;
+    // trial launches record no kernel-timing events
+    const bool keep_ktime = h->ktime;
+    h->ktime = false;
     static const int kThreads[4] = {128, 256, 512, 1024}, kGr[4] = {8, 16, 32, 64}, kRows[5] = {8, 12, 16, 24, 32};
     static const int kThreadsSplit[6] = {32, 64, 128, 256, 512, 1024};
-    // time of `repeats` launches of groups 0 and 10 at `level`, state restored after each;
-    // < 0 when the configuration cannot launch
+    // time of `repeats` launches of groups 0 and 10 at `level` (with dataflow launches:
+    // of the level's one launch), state restored after each; < 0 when the configuration
+    // cannot launch
     auto trial = [&](int level, float &ms) -> int {
         float tot = 0.f;
+        const bool whole = h->p.dataflow && !h->split_level[level] && !h->grid_level[level];
+        const int ng = whole ? 1 : 2;
         for (int r = 0; r < repeats; ++r)
-            for (int g : {0, 10}) {
+            for (int gi = 0; gi < ng; ++gi) {
                 cudaError_t ce = cudaEventRecord(ev[0], h->st);
                 if (ce != cudaSuccess) return cuda_fail(h, ce, "lem_autotune event");
-                int rr = expand_group_impl(h, h->iter, level, g, h->st);
+                int rr = whole ? expand_level_impl(h, h->iter, level, h->st)
+                               : expand_group_impl(h, h->iter, level, gi == 0 ? 0 : 10, h->st);
                 if (rr != LEM_OK) {
                     cudaGetLastError();
                     ms = -1.f;
@@ -1179,7 +1223,7 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
                 if (ce != cudaSuccess) return cuda_fail(h, ce, "lem_autotune trial");
                 tot += t;
             }
-        ms = tot / (2.f * repeats);
+        ms = tot / (float)(ng * repeats);
         return LEM_OK;
     };
     for (int l = 0; l < h->p.n_levels && rc == LEM_OK; ++l) {
@@ -1236,7 +1280,10 @@ int lem_autotune(lem_handle *h, int repeats, lem_tuning *out) {
         if (e != cudaSuccess) rc = cuda_fail(h, e, "lem_autotune restore");
         else if (ctr1.limit_hits != ctr0.limit_hits)
             rc = fail(h, LEM_ERR_MAXFLOW_LIMIT, "a trial cut hit the push-relabel round limit");
+        else if (ctr1.dep_give_ups != ctr0.dep_give_ups)
+            rc = fail(h, LEM_ERR_CUDA, "a trial region gave up waiting for a neighbour");
     }
+    h->ktime = keep_ktime;
     if (rc != LEM_OK) {
         // a failed trial may have left its moves in the labels
         h->p = keep;

@@ -67,6 +67,7 @@ struct Counters {
     unsigned long long bfs_levels;  // BFS frontiers summed over global relabels
     unsigned long long accepted_kind[4];  // switched pixels by proposal kind: propagation, RANSAC,
                                           // map (learned proposer), perturbation
+    unsigned long long dep_give_ups;      // dataflow waits that reached their limit
 };
 
 // Shared-memory bytes the region cost pipeline needs for regions up to
@@ -107,10 +108,15 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 // that compute both candidates' data terms at once, with the sequential result.
 // queue: NULL (one CTA per item), or two zeroed ints of a work queue that a
 // grid of co-resident CTAs drains (left zeroed after the launch); not with phiB.
+// done: NULL, or (with queue, without phiB) one zeroed flag per cell of the
+// level of every pair: the items are then those of all 16 groups of the level
+// in group order, item.w is the index of its pair's cell (0, 0) in done, and
+// an item waits for the items of earlier groups within three cells before it
+// starts and sets its own flag when it is done (a dataflow launch of a level).
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
-                                int *queue, cudaStream_t st);
+                                int *queue, unsigned *done, cudaStream_t st);
 cudaError_t launch_increment(int *x, cudaStream_t st);
 // Batched visits on the guided-filter data term without RANSAC proposals, regions
 // of at most LEM_MAX_REGION_NODES nodes and filtering regions at most 128 px

@@ -1964,6 +1964,59 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Dataflow launches of a level.  The region of cell (ci, cj) covers cells
+// ci - 1 .. ci + 1 (and rows likewise); its moves read the labels of the region
+// and of the one-pixel ring around it and write the region's labels.  Two
+// regions more than three cells apart in either direction therefore neither
+// read nor write each other's pixels and their moves commute; regions closer
+// than that must move in group order.  A region waits for the done flags of
+// the cells of earlier groups within three cells (group index
+// (cj & 3) * 4 + (ci & 3), the order of the 16 group launches) and sets its
+// own flag after its last move.
+// ---------------------------------------------------------------------------
+constexpr int kDepWaitLimit = 1 << 24;  // polls, about 100 ns apart, before a wait gives up
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// all threads of the CTA; returns after the flags of the earlier-group cells
+// within three cells of (ci, cj) are set (or their waits gave up, counted in
+// ctr->dep_give_ups)
+__device__ void wait_for_earlier_neighbours(const unsigned *done, int base, int ci, int cj, int nx, int ny,
+                                            Counters *ctr) {
+    const int t = threadIdx.x;
+    if (t < 49) {
+        const int x = ci + t % 7 - 3, y = cj + t / 7 - 3;
+        const int g = ((cj & 3) << 2) | (ci & 3);
+        if (x >= 0 && x < nx && y >= 0 && y < ny && ((((y & 3) << 2) | (x & 3)) < g)) {
+            const unsigned *f = done + base + y * nx + x;
+            int polls = 0;
+            while (ld_acquire_gpu(f) == 0u) {
+                if (++polls > kDepWaitLimit) {
+                    atomicAdd(&ctr->dep_give_ups, 1ull);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// all threads of the CTA, after the region's last move: publishes its label
+// and cost writes and sets its done flag
+__device__ void mark_region_done(unsigned *done, int idx) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(done + idx), "r"(1u) : "memory");
+    }
+}
+
 // All expansions of one group at one level: one CTA per region, Algorithm 2.
 //   P      : base planes of all pairs (H/W unused); pair b's planes start at
 //            pixel pairs[b].off
@@ -1972,6 +2025,9 @@ __device__ __forceinline__ void cluster_sync_all() {
 //            launch, zero again after it) taken from that work queue by a grid of
 //            at most the co-resident CTAs until all n_items are done
 //   iter   : outer iteration, or -1 to read it from *iter_dev (graph replay)
+//   done   : NULL, or (with queue) the cells' done flags of a dataflow launch:
+//            items are then all 16 groups of the level in group order and
+//            item.w is the flag index of the pair's cell (0, 0)
 //   SPEC   : a launch in clusters of two CTAs per region (phiB_all), for
 //            levels whose visit is two propagation candidates (K_prop = 2, no
 //            other proposals).  The second candidate is alpha_2 = f_r2 after
@@ -1987,7 +2043,8 @@ template <int NT, bool SPEC>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     k_expand_group(DevPlanes P0, KParams kp0, Level lv, int level, int iter, const int *iter_dev,
                    const PairDesc *pairs, const int4 *items, float4 *lab_all, float *phiA_all,
-                   const float4 *prop_all, Counters *ctr, float *phiB_all, int n_items, int *queue) {
+                   const float4 *prop_all, Counters *ctr, float *phiB_all, int n_items, int *queue,
+                   unsigned *done) {
     extern __shared__ __align__(16) float smf[];
     __shared__ float4 s_alpha[kMaxVisit];
     __shared__ long long red[33];
@@ -2033,6 +2090,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
     const int y0 = max(0, (cj - 1) * s), y1 = min(H, (cj + 2) * s);
     const int w = x1 - x0, h = y1 - y0, n = w * h;
     const int cx0 = ci * s, cy0 = cj * s, cw = min(W, cx0 + s) - cx0, chh = min(H, cy0 + s) - cy0;
+    const int nx = (W + s - 1) / s, ny = (H + s - 1) / s;
+    if (!SPEC && done) wait_for_earlier_neighbours(done, item.w, ci, cj, nx, ny, ctr);
     CutSmem cs = cut_layout(smf, n);
     evals += (unsigned long long)n * (unsigned long long)(lv.k_prop + lv.k_rans + (prop ? lv.k_cnn : 0) + lv.k_rand);
     if constexpr (SPEC) {
@@ -2111,6 +2170,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
                 expand_move(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acck[proposal_kind(lv, kc, t)], hits);
             }
         }
+        if (done) mark_region_done(done, item.w + cj * nx + ci);
     }
     }
     add_accepted(acck, red, ctr);
@@ -3261,7 +3321,8 @@ cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const in
 template <int NT>
 cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter, const int *iter_dev,
                       const PairDesc *pairs, const int4 *items, int n_items, float4 *lab, float *phiA,
-                      const float4 *prop, Counters *ctr, float *phiB, int *queue, size_t sm, cudaStream_t st) {
+                      const float4 *prop, Counters *ctr, float *phiB, int *queue, unsigned *done, size_t sm,
+                      cudaStream_t st) {
     cudaError_t e;
     if (!phiB) {
         if ((e = set_smem((const void *)k_expand_group<NT, false>, sm)) != cudaSuccess) return e;
@@ -3280,7 +3341,7 @@ cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, in
             grid = std::max(1, std::min(n_items, per_sm * nsm));
         }
         k_expand_group<NT, false><<<grid, NT, sm, st>>>(P, kp, lv, level, iter, iter_dev, pairs, items, lab, phiA,
-                                                        prop, ctr, nullptr, n_items, queue);
+                                                        prop, ctr, nullptr, n_items, queue, done);
         return cudaGetLastError();
     }
     if ((e = set_smem((const void *)k_expand_group<NT, true>, sm)) != cudaSuccess) return e;
@@ -3309,17 +3370,18 @@ cudaError_t expand_nt(const DevPlanes &P, const KParams &kp, const Level &lv, in
     if (!ok || clusters < n_items || 2 * n_items > per_sm * nsm) {
         cudaGetLastError();
         return expand_nt<NT>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, nullptr,
-                             queue, sm, st);
+                             queue, nullptr, sm, st);
     }
     return cudaLaunchKernelEx(&cfg, k_expand_group<NT, true>, P, kp, lv, level, iter, iter_dev, pairs, items, lab,
-                              phiA, prop, ctr, phiB, n_items, (int *)nullptr);
+                              phiA, prop, ctr, phiB, n_items, (int *)nullptr, (unsigned *)nullptr);
 }
 
 cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                 const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
                                 int n_items, float4 *lab, float *phiA, const float4 *prop, Counters *ctr, float *phiB,
-                                int *queue, cudaStream_t st) {
+                                int *queue, unsigned *done, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
+    if (done && !queue) return cudaErrorInvalidValue;
     const int s = lv.s;
     const int rw = std::min(max_w, 3 * s), rh = std::min(max_h, 3 * s);
     size_t sm = std::max(unary_bytes_host(kp, max_h, max_w, rw, rh), cut_smem_bytes(rw, rh));
@@ -3328,10 +3390,11 @@ cudaError_t launch_expand_group(const DevPlanes &P, const KParams &kp, const Lev
     const int nt = lv.threads > 0 ? lv.threads : threads_for_nodes(rw * rh);
     if (nt != 128 && nt != 256 && nt != 512 && nt != 1024) return cudaErrorInvalidValue;
     // the two-CTA visit only for two propagation candidates per visit
-    const bool two = phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop);
+    const bool two = !done && phiB && lv.k_prop == 2 && lv.k_rand == 0 && lv.k_rans == 0 && (lv.k_cnn == 0 || !prop);
     float *pb = two ? phiB : nullptr;
 #define LEM_EXPAND_NT(NT_) \
-    expand_nt<NT_>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, queue, sm, st)
+    expand_nt<NT_>(P, kp, lv, level, iter, iter_dev, pairs, items, n_items, lab, phiA, prop, ctr, pb, queue, done, sm, \
+                   st)
     if (nt == 128) return LEM_EXPAND_NT(128);
     if (nt == 256) return LEM_EXPAND_NT(256);
     if (nt == 512) return LEM_EXPAND_NT(512);

@@ -44,7 +44,7 @@ class lem_params(C.Structure):
         ("use_graph", C.c_int), ("candidates_per_visit", C.c_int), ("k_cnn", C.c_int * 3),
         ("level_threads", C.c_int * 3), ("level_gr_interval", C.c_int * 3), ("level_strip_rows", C.c_int * 3),
         ("k_rans", C.c_int * 3), ("data_term", C.c_int), ("bf_gamma", C.c_double), ("cluster_visits", C.c_int),
-        ("split_visits", C.c_int), ("work_queue", C.c_int),
+        ("split_visits", C.c_int), ("work_queue", C.c_int), ("dataflow", C.c_int),
     ]
 
 
@@ -73,7 +73,7 @@ class lem_stats(C.Structure):
     _fields_ = [("energy_q", C.c_int64), ("energy", C.c_double), ("evals", C.c_int64), ("accepted", C.c_int64),
                 ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32),
                 ("pr_rounds", C.c_int64), ("pr_global_relabels", C.c_int64), ("pr_bfs_levels", C.c_int64),
-                ("accepted_by_kind", C.c_int64 * 4)]
+                ("accepted_by_kind", C.c_int64 * 4), ("dep_waits_given_up", C.c_int64)]
 
 
 _lib = None
