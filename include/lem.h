@@ -57,11 +57,30 @@ extern "C" {
 /* largest cell size (pixels) of a grid level */
 #define LEM_MAX_CELL 1024
 
+/* element types of a lem_image */
+#define LEM_IMG_U8 0   /* uint8 colours 0..255                                      */
+#define LEM_IMG_F16 1  /* IEEE half, colours on the 0..255 scale                    */
+#define LEM_IMG_BF16 2 /* bfloat16, colours on the 0..255 scale                     */
+#define LEM_IMG_F32 3  /* float, colours on the 0..255 scale                        */
+
+/* An image of H x W pixels, each `channels` values of type `dtype` of which the
+ * first three are R, G, B (further channels, e.g. alpha, are ignored).  The
+ * method's colour terms are those of 8-bit images (Sec. 3.2: colour L1 distance
+ * truncated at tau_col on the 0..255 scale, BT.601 gray for the gradient, the
+ * guide scaled to [0, 1]), so a float colour is rounded to the nearest integer
+ * and clamped to [0, 255] when the handle is created; a uint8 image is taken as
+ * it is.  A zero in channels, stride_px or dtype selects the default, so an
+ * image initialised with the first five fields only is packed 8-bit RGB.
+ * Ownership: read during lem_create* only (host images are copied). */
 typedef struct {
-    const uint8_t *data; /* H x W x 3 RGB                                  */
+    const void *data;    /* pixel (0, 0)                                                    */
     int height, width;
-    int64_t stride_row;  /* bytes between rows (>= 3*width)                */
-    int on_device;       /* 1: `data` is device memory, 0: host memory     */
+    int64_t stride_row;  /* bytes between rows (>= (width-1)*stride_px + channels*size)     */
+    int on_device;       /* 1: `data` is device memory, 0: host memory                      */
+    int channels;        /* values per pixel, 3..16 (0: 3)                                  */
+    int64_t stride_px;   /* bytes between pixels, >= channels*size (0: channels*size)       */
+    int dtype;           /* LEM_IMG_U8 (0), LEM_IMG_F16, LEM_IMG_BF16 or LEM_IMG_F32; the
+                            data pointer and both strides are multiples of the element size */
 } lem_image;
 
 /* Parameters.  lem_default_params() fills the values of the paper's
@@ -158,9 +177,16 @@ typedef struct {
                              cluster visit is not used.  0 (default): one launch per group. */
 } lem_params;
 
-/* An expansion region R (clipped to the image): columns [x0, x0+w), rows [y0, y0+h). */
+/* An expansion region R (clipped to the image): columns [x0, x0+w), rows
+ * [y0, y0+h) of pair `img` of the handle (0 for a single-pair handle).  The
+ * centre cell C of a 3x3-cell region (Sec. 3.3: the region is C grown by one
+ * cell; its propagation candidate is the label of a pixel of C) may be given in
+ * cx0, cy0, cw, ch; it must then lie inside R.  The batch calls do not read it
+ * (their candidates are passed in); cw = ch = 0 leaves it unset. */
 typedef struct {
     int x0, y0, w, h;
+    int img;                /* pair index, 0 .. lem_pair_count(h) - 1 */
+    int cx0, cy0, cw, ch;   /* centre cell (optional)                  */
 } lem_region;
 
 /* Counters (evals, accepted, maxflow_limit) cover the work done since the
@@ -207,9 +233,13 @@ int lem_v3_params(lem_params *p, int width);
  * (Eq. gf), the contrast weights lambda*max(w_pq, eps) of the 4 forward
  * neighbours (Eq. smweight), draws the random initial labels (Sec. 3.4:
  * random disparity in [disp_min, disp_max] and random unit normal) and fills
- * the cost cache phi_p(f_p).  left/right: same height and width.
- * Errors: LEM_ERR_ARG (null pointers, bad parameters), LEM_ERR_SHAPE,
- * LEM_ERR_OOM, LEM_ERR_CUDA.  On error *out is NULL. */
+ * the cost cache phi_p(f_p).  left/right: same height and width, any layout
+ * and element type lem_image describes (converted to packed 8-bit RGB on the
+ * device first).
+ * Errors: LEM_ERR_ARG (null pointers, bad parameters, an unknown dtype, fewer
+ * than 3 or more than 16 channels, a pointer or stride that is not a multiple
+ * of the element size), LEM_ERR_SHAPE (sizes, strides), LEM_ERR_OOM,
+ * LEM_ERR_CUDA.  On error *out is NULL. */
 int lem_create(const lem_image *left, const lem_image *right, const lem_params *p, lem_handle **out);
 
 /* A handle for n_pairs independent pairs (sizes may differ), each prepared as by
@@ -221,7 +251,7 @@ int lem_create(const lem_image *left, const lem_image *right, const lem_params *
  * label, cost and plane arrays of lem_get_labels, lem_set_labels and
  * lem_get_planes hold the pairs in order, each row-major (see lem_pair_info);
  * lem_energy sums over the pairs.  The batch entry points (lem_unary_batch,
- * lem_pairwise_batch, lem_mincut_batch) work on pair 0.
+ * lem_pairwise_batch, lem_mincut_batch) take each region's pair from its img.
  * Errors as lem_create; n_pairs must be in [1, 4096]. */
 int lem_create_batch(const lem_image *lefts, const lem_image *rights, int n_pairs, const lem_params *p,
                      lem_handle **out);
@@ -261,12 +291,13 @@ const char *lem_last_error(const lem_handle *h);
  * region M (Sec. 3.5): raw costs rho(s|alpha) (Eqs. warp, photofunc; linear
  * interpolation along u, u' clamped to [0, W-1]) over R grown by 2r', guided-
  * filter coefficients over R grown by r', their window means over R.
- *   regions : host, n_regions entries, each inside the image, w*h >= 1
+ *   regions : host, n_regions entries, each inside the image of its pair img, w*h >= 1
  *   labels  : device float32, n_regions*K*3: candidate k of region i at (i*K+k)*3
  *   costs   : device float32, packed region-major: region i starts at
  *             K * sum_{j<i} w_j*h_j; within it candidate k occupies w_i*h_i
  *             values, row-major over R.
- * Errors: LEM_ERR_ARG, LEM_ERR_SHAPE (region outside the image), LEM_ERR_CUDA. */
+ * Errors: LEM_ERR_ARG (also img out of range), LEM_ERR_SHAPE (region outside
+ * its image, centre cell outside the region), LEM_ERR_CUDA. */
 int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, const float *labels, int K,
                     float *costs);
 
@@ -276,7 +307,8 @@ int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, con
  * (B+C-A-D)(1-x_p)x_q decomposition with D = 0, valid by Lemma 1).  Every term
  * is quantised as rne(S x); a quantised A above B + C is lowered to B + C.
  * x_p = 1 (take alpha) puts p on the sink side.
- *   regions     : host, n_regions entries (at most LEM_MAX_REGION_NODES nodes each)
+ *   regions     : host, n_regions entries (at most LEM_MAX_REGION_NODES nodes each), against
+ *                 the labels of pair img
  *   alpha       : device float32, n_regions*3
  *   costs_alpha : device float32, phi_p(alpha) packed as lem_unary_batch with K = 1
  *   tcaps       : device int32, 2 per node {s->p: U_p(1)-m, p->t: U_p(0)-m}, packed like costs_alpha
@@ -415,7 +447,8 @@ int lem_get_kernel_times(lem_handle *h, lem_kernel_times *out);
  * has been staged, which can wait for earlier work on the stream.  Callers
  * that must not block pass page-locked `regions`.
  *   regions     : host, n_regions <= LEM_NOALLOC_MAX_REGIONS entries, each
- *                 region at most LEM_MAX_REGION_NODES nodes; x0/y0 are ignored
+ *                 region at most LEM_MAX_REGION_NODES nodes; x0, y0, img and the
+ *                 centre cell are ignored
  *   tcaps/ncaps : device int32, layout of lem_pairwise_batch
  *   take_alpha, flow, status : device outputs as in lem_mincut_batch
  *   max_rounds, gr_interval  : as in lem_params (>= 1)

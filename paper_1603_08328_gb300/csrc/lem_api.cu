@@ -42,6 +42,7 @@ struct lem_handle {
     lem::Counters *ctr = nullptr;
     int *n_fp64 = nullptr;
     int4 *d_regions = nullptr;
+    int *d_img = nullptr;               // pair of each staged region
     int64_t *d_offsets = nullptr;
     size_t cap_regions = 0;
     // work items (pair, cell i, cell j) of every (level, group), concatenated
@@ -237,12 +238,76 @@ int check_params(const lem_params *p) {
     return LEM_OK;
 }
 
+// element size of a lem_image dtype (0: unknown)
+size_t img_elem(int dtype) {
+    return dtype == LEM_IMG_U8 ? 1 : (dtype == LEM_IMG_F16 || dtype == LEM_IMG_BF16) ? 2 : dtype == LEM_IMG_F32 ? 4 : 0;
+}
+int img_channels(const lem_image *im) { return im->channels ? im->channels : 3; }
+int64_t img_stride_px(const lem_image *im) {
+    return im->stride_px ? im->stride_px : (int64_t)img_channels(im) * (int64_t)img_elem(im->dtype);
+}
+
 int check_image(const lem_image *im, const char *name) {
-    if (!im || !im->data) return fail(nullptr, LEM_ERR_ARG, std::string(name) + " image is NULL");
-    if (im->height < 1 || im->width < 2) return fail(nullptr, LEM_ERR_SHAPE, std::string(name) + " image too small");
-    if (im->stride_row < 3LL * im->width) return fail(nullptr, LEM_ERR_SHAPE, std::string(name) + " stride_row < 3*width");
+    const std::string nm(name);
+    if (!im || !im->data) return fail(nullptr, LEM_ERR_ARG, nm + " image is NULL");
+    if (im->height < 1 || im->width < 2) return fail(nullptr, LEM_ERR_SHAPE, nm + " image too small");
+    const int64_t es = (int64_t)img_elem(im->dtype);
+    if (!es) return fail(nullptr, LEM_ERR_ARG, nm + " image dtype is not one of LEM_IMG_*");
+    const int ch = img_channels(im);
+    if (ch < 3 || ch > 16) return fail(nullptr, LEM_ERR_ARG, nm + " image channels must be 3..16");
+    const int64_t spx = img_stride_px(im);
+    if (spx < ch * es) return fail(nullptr, LEM_ERR_SHAPE, nm + " image stride_px < channels * element size");
+    if (spx % es || im->stride_row % es || (uintptr_t)im->data % (uintptr_t)es)
+        return fail(nullptr, LEM_ERR_ARG, nm + " image pointer or strides not a multiple of the element size");
+    if (im->stride_row < (int64_t)(im->width - 1) * spx + ch * es)
+        return fail(nullptr, LEM_ERR_SHAPE, nm + " image stride_row shorter than a row");
     if ((int64_t)im->height * im->width > (1LL << 30)) return fail(nullptr, LEM_ERR_SHAPE, "image too large");
     return LEM_OK;
+}
+
+// Device packed 8-bit RGB (rows of `*stride` bytes) of a checked image: the
+// caller's own data when it already is that on the device, else a copy in
+// *tmp (device memory the caller frees once the kernels reading it are done).
+cudaError_t stage_rgb8(const lem_image *im, cudaStream_t st, uint8_t **tmp, const uint8_t **out, int64_t *stride) {
+    const int H = im->height, W = im->width;
+    const int64_t es = (int64_t)img_elem(im->dtype), spx = img_stride_px(im);
+    *tmp = nullptr;
+    const bool packed = im->dtype == LEM_IMG_U8 && spx == 3;
+    if (packed && im->on_device) {
+        *out = (const uint8_t *)im->data;
+        *stride = im->stride_row;
+        return cudaSuccess;
+    }
+    const size_t rgb = (size_t)H * W * 3;
+    // host images that need converting are first copied as they are (rows cut
+    // to their used bytes), then converted on the device
+    const int64_t row_used = (int64_t)(W - 1) * spx + img_channels(im) * es;
+    const int64_t pitch = (row_used + 15) & ~(int64_t)15;
+    const size_t raw = (!packed && !im->on_device) ? (size_t)pitch * H : 0;
+    cudaError_t e = cudaMalloc(tmp, rgb + raw);
+    if (e != cudaSuccess) return e;
+    if (packed) {
+        e = cudaMemcpy2DAsync(*tmp, 3 * W, im->data, im->stride_row, 3 * W, H, cudaMemcpyHostToDevice, st);
+    } else {
+        const void *src = im->data;
+        int64_t srow = im->stride_row;
+        if (!im->on_device) {
+            e = cudaMemcpy2DAsync(*tmp + rgb, pitch, im->data, im->stride_row, row_used, H, cudaMemcpyHostToDevice,
+                                  st);
+            src = *tmp + rgb;
+            srow = pitch;
+        }
+        if (e == cudaSuccess) e = lem::launch_to_rgb8(src, srow, spx, im->dtype, H, W, *tmp, st);
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        cudaFree(*tmp);
+        *tmp = nullptr;
+        return e;
+    }
+    *out = *tmp;
+    *stride = 3 * W;
+    return cudaSuccess;
 }
 
 void free_handle(lem_handle *h) {
@@ -265,6 +330,7 @@ void free_handle(lem_handle *h) {
     cudaFree(h->ctr);
     cudaFree(h->n_fp64);
     cudaFree(h->d_regions);
+    cudaFree(h->d_img);
     cudaFree(h->d_offsets);
     cudaFree(h->d_pairs);
     cudaFree(h->d_items);
@@ -283,14 +349,22 @@ int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_
                   int *max_n, size_t *max_cut_smem = nullptr) {
     if (!regions || n < 1) return fail(h, LEM_ERR_ARG, "regions is NULL or n_regions < 1");
     std::vector<int4> rg(n);
+    std::vector<int> im(n);
     std::vector<int64_t> off(n);
     int64_t acc = 0;
     int mw = 0, mh = 0, mn = 0;
     for (int i = 0; i < n; ++i) {
         const lem_region &r = regions[i];
-        if (r.w < 1 || r.h < 1 || r.x0 < 0 || r.y0 < 0 || r.x0 + r.w > h->W || r.y0 + r.h > h->H)
-            return fail(h, LEM_ERR_SHAPE, "region " + std::to_string(i) + " is empty or outside the image");
+        if (r.img < 0 || r.img >= h->B)
+            return fail(h, LEM_ERR_ARG, "region " + std::to_string(i) + ": img out of range");
+        const lem::PairDesc &pd = h->pairs[r.img];
+        if (r.w < 1 || r.h < 1 || r.x0 < 0 || r.y0 < 0 || r.x0 + r.w > pd.W || r.y0 + r.h > pd.H)
+            return fail(h, LEM_ERR_SHAPE, "region " + std::to_string(i) + " is empty or outside its image");
+        if ((r.cw != 0 || r.ch != 0) && (r.cw < 1 || r.ch < 1 || r.cx0 < r.x0 || r.cy0 < r.y0 ||
+                                         r.cx0 + r.cw > r.x0 + r.w || r.cy0 + r.ch > r.y0 + r.h))
+            return fail(h, LEM_ERR_SHAPE, "region " + std::to_string(i) + ": centre cell outside the region");
         rg[i] = make_int4(r.x0, r.y0, r.w, r.h);
+        im[i] = r.img;
         off[i] = acc;
         acc += (int64_t)K * r.w * r.h;
         mw = std::max(mw, r.w);
@@ -300,14 +374,19 @@ int stage_regions(lem_handle *h, const lem_region *regions, int n, int K, int64_
     }
     if ((size_t)n > h->cap_regions) {
         cudaFree(h->d_regions);
+        cudaFree(h->d_img);
         cudaFree(h->d_offsets);
         h->d_regions = nullptr;
+        h->d_img = nullptr;
         h->d_offsets = nullptr;
+        h->cap_regions = 0;
         LEM_CUDA(h, cudaMalloc(&h->d_regions, sizeof(int4) * n));
+        LEM_CUDA(h, cudaMalloc(&h->d_img, sizeof(int) * n));
         LEM_CUDA(h, cudaMalloc(&h->d_offsets, sizeof(int64_t) * n));
         h->cap_regions = n;
     }
     LEM_CUDA(h, cudaMemcpyAsync(h->d_regions, rg.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, h->st));
+    LEM_CUDA(h, cudaMemcpyAsync(h->d_img, im.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->st));
     LEM_CUDA(h, cudaMemcpyAsync(h->d_offsets, off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->st));
     // the staging vectors die on return: make sure the copies have read them
     LEM_CUDA(h, cudaStreamSynchronize(h->st));
@@ -568,29 +647,17 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
         const lem::PairDesc &pd = h->pairs[b];
         const int H = pd.H, W = pd.W;
         const size_t np = (size_t)H * W;
-        const uint8_t *dl = left->data, *dr = right->data;
-        int64_t ls = left->stride_row, rs = right->stride_row;
-        uint8_t *tmp = nullptr;
-        if (!left->on_device || !right->on_device) {
-            CREATE_CUDA(cudaMalloc(&tmp, 2 * np * 3));
-            cudaError_t ce = cudaSuccess;
-            if (!left->on_device) {
-                ce = cudaMemcpy2DAsync(tmp, 3 * W, left->data, left->stride_row, 3 * W, H, cudaMemcpyHostToDevice,
-                                       h->st);
-                dl = tmp;
-                ls = 3 * W;
-            }
-            if (ce == cudaSuccess && !right->on_device) {
-                ce = cudaMemcpy2DAsync(tmp + 3 * np, 3 * W, right->data, right->stride_row, 3 * W, H,
-                                       cudaMemcpyHostToDevice, h->st);
-                dr = tmp + 3 * np;
-                rs = 3 * W;
-            }
-            if (ce != cudaSuccess) {
-                cudaStreamSynchronize(h->st);
-                cudaFree(tmp);
-                return bail(cuda_fail(h, ce, "lem_create image upload"));
-            }
+        (void)np;
+        // packed 8-bit RGB of both images on the device (uploaded / converted as needed)
+        const uint8_t *dl = nullptr, *dr = nullptr;
+        int64_t ls = 0, rs = 0;
+        uint8_t *tmpl = nullptr, *tmpr = nullptr;
+        cudaError_t ce = stage_rgb8(left, h->st, &tmpl, &dl, &ls);
+        if (ce == cudaSuccess) ce = stage_rgb8(right, h->st, &tmpr, &dr, &rs);
+        if (ce != cudaSuccess) {
+            cudaStreamSynchronize(h->st);
+            cudaFree(tmpl);
+            return bail(cuda_fail(h, ce, "lem_create image upload"));
         }
         lem::DevPlanes P = planes(h, b);
         lem::KParams kp = kparams(h);
@@ -604,10 +671,11 @@ int lem_create_batch_ranges(const lem_image *lefts, const lem_image *rights, int
         if (e == cudaSuccess)
             e = lem::launch_init_labels(H, W, pd.seed, pd.disp_min, pd.disp_max, h->lab + pd.off, h->st);
         if (e == cudaSuccess) e = lem::launch_pixel_costs(P, kp, h->lab + pd.off, std::min(p->threads, 128), h->st);
-        // the temporary upload buffer must outlive the kernels that read it
-        if (tmp) {
+        // the temporary upload buffers must outlive the kernels that read them
+        if (tmpl || tmpr) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-            cudaFree(tmp);
+            cudaFree(tmpl);
+            cudaFree(tmpr);
         }
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "lem_create kernels"));
     }
@@ -640,28 +708,26 @@ int lem_create_right_view(const lem_image *left, const lem_image *right, const l
     const int H = left->height, W = left->width;
     const size_t img = (size_t)H * W * 3;
     cudaStream_t st = (cudaStream_t)p->stream;
-    uint8_t *buf = nullptr;  // [staged left][staged right][mirrored right][mirrored left]
-    cudaError_t e = cudaMalloc(&buf, 4 * img);
+    uint8_t *buf = nullptr;  // [mirrored right][mirrored left]
+    cudaError_t e = cudaMalloc(&buf, 2 * img);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lem_create_right_view");
     const lem_image *src[2] = {right, left};
+    uint8_t *tmp[2] = {nullptr, nullptr};
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        const uint8_t *d = src[k]->data;
-        int64_t ds = src[k]->stride_row;
-        if (!src[k]->on_device) {
-            e = cudaMemcpy2DAsync(buf + k * img, 3 * W, src[k]->data, src[k]->stride_row, 3 * W, H,
-                                  cudaMemcpyHostToDevice, st);
-            d = buf + k * img;
-            ds = 3 * W;
-        }
-        if (e == cudaSuccess) e = lem::launch_mirror_rgb(d, ds, H, W, buf + (2 + k) * img, st);
+        const uint8_t *d = nullptr;
+        int64_t ds = 0;
+        e = stage_rgb8(src[k], st, &tmp[k], &d, &ds);
+        if (e == cudaSuccess) e = lem::launch_mirror_rgb(d, ds, H, W, buf + k * img, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp[0]);
+    cudaFree(tmp[1]);
     if (e != cudaSuccess) {
         cudaFree(buf);
         return cuda_fail(nullptr, e, "lem_create_right_view mirror");
     }
     // the mirrored right image is the reference view, the mirrored left the matched one
-    lem_image l2{buf + 2 * img, H, W, 3LL * W, 1}, r2{buf + 3 * img, H, W, 3LL * W, 1};
+    lem_image l2{buf, H, W, 3LL * W, 1, 3, 3, LEM_IMG_U8}, r2{buf + img, H, W, 3LL * W, 1, 3, 3, LEM_IMG_U8};
     rc = lem_create_batch(&l2, &r2, 1, p, out);
     cudaFree(buf);
     return rc;
@@ -694,13 +760,13 @@ int lem_unary_batch(lem_handle *h, const lem_region *regions, int n_regions, con
     // a handle whose expansions use the warp data term (batched visits) gets the same
     // computation here
     const lem::KParams kp = kparams(h);
-    if (h->p.split_visits && h->p.candidates_per_visit >= 2 && lem::unary_warp_fits(kp, h->W, mw)) {
-        LEM_CUDA(h, lem::launch_unary_batch_warp(planes(h), kp, h->d_regions, h->d_offsets, n_regions, K, mw, labels,
-                                                 costs, h->st));
+    if (h->p.split_visits && h->p.candidates_per_visit >= 2 && lem::unary_warp_fits(kp, h->maxW, mw)) {
+        LEM_CUDA(h, lem::launch_unary_batch_warp(planes_base(h), kp, h->d_pairs, h->d_img, h->d_regions, h->d_offsets,
+                                                 n_regions, K, mw, labels, costs, h->st));
         return LEM_OK;
     }
-    LEM_CUDA(h, lem::launch_unary_batch(planes(h), kparams(h), h->d_regions, h->d_offsets, n_regions, K, mw, mh,
-                                        labels, costs, h->p.threads, h->st));
+    LEM_CUDA(h, lem::launch_unary_batch(planes_base(h), kparams(h), h->d_pairs, h->d_img, h->d_regions, h->d_offsets,
+                                        n_regions, K, mw, mh, labels, costs, h->p.threads, h->st));
     return LEM_OK;
 }
 
@@ -712,8 +778,9 @@ int lem_pairwise_batch(lem_handle *h, const lem_region *regions, int n_regions, 
     int mw, mh, mn, rc;
     if ((rc = stage_regions(h, regions, n_regions, 1, &total, &mw, &mh, &mn)) != LEM_OK) return rc;
     if (mn > LEM_MAX_REGION_NODES) return fail(h, LEM_ERR_SHAPE, "region larger than LEM_MAX_REGION_NODES");
-    LEM_CUDA(h, lem::launch_pairwise_batch(planes(h), kparams(h), h->d_regions, h->d_offsets, n_regions, h->lab,
-                                           alpha, costs_alpha, tcaps, ncaps, const_term, h->p.threads, h->st));
+    LEM_CUDA(h, lem::launch_pairwise_batch(planes_base(h), kparams(h), h->d_pairs, h->d_img, h->d_regions,
+                                           h->d_offsets, n_regions, h->lab, alpha, costs_alpha, tcaps, ncaps,
+                                           const_term, h->p.threads, h->st));
     return LEM_OK;
 }
 

@@ -90,13 +90,16 @@ cudaError_t launch_init_labels(int H, int W, unsigned long long seed, double dmi
                                cudaStream_t st);
 // phi_p(f_p) for every pixel with its own label (1x1 regions).
 cudaError_t launch_pixel_costs(const DevPlanes &P, const KParams &kp, float4 *lab, int threads, cudaStream_t st);
-cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
-                               int n_regions, int K, int max_w, int max_h, const float *labels, float *costs,
-                               int threads, cudaStream_t st);
-cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const int4 *regions,
-                                  const int64_t *offsets, int n_regions, const float4 *lab, const float *alpha,
-                                  const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *cterm,
-                                  int threads, cudaStream_t st);
+// The batch test surface.  P (and lab) are the base planes (labels) of all
+// pairs, P.H / P.W the largest pair's size; region i belongs to pair img[i]
+// (device array) and is offset to it by pairs[img[i]].
+cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                               const int4 *regions, const int64_t *offsets, int n_regions, int K, int max_w,
+                               int max_h, const float *labels, float *costs, int threads, cudaStream_t st);
+cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                                  const int4 *regions, const int64_t *offsets, int n_regions, const float4 *lab,
+                                  const float *alpha, const float *costs_alpha, int32_t *tcaps, int32_t *ncaps,
+                                  int64_t *cterm, int threads, cudaStream_t st);
 cudaError_t launch_mincut_batch(const KParams &kp, const int4 *regions, const int64_t *offsets, int n_regions,
                                 int max_nodes, size_t smem, const int32_t *tcaps, const int32_t *ncaps, uint8_t *take,
                                 int64_t *flow, int32_t *status, Counters *ctr, cudaStream_t st);
@@ -129,9 +132,9 @@ bool visit_split(const KParams &kp, const Level &lv, int max_w, int max_h);
 // lem_unary_batch with the warp data term of that path (one warp per region and
 // label), for regions at most max_w wide whose filtering region fits it
 bool unary_warp_fits(const KParams &kp, int W, int max_w);
-cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const int4 *regions,
-                                    const int64_t *offsets, int n_regions, int K, int max_w, const float *labels,
-                                    float *costs, cudaStream_t st);
+cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                                    const int4 *regions, const int64_t *offsets, int n_regions, int K, int max_w,
+                                    const float *labels, float *costs, cudaStream_t st);
 int visit_cut_threads(int nodes);
 cudaError_t launch_visit_unary(const DevPlanes &P, const KParams &kp, const Level &lv, int level, int iter,
                                const int *iter_dev, const PairDesc *pairs, int max_w, int max_h, const int4 *items,
@@ -195,6 +198,10 @@ cudaError_t launch_postprocess(const DevPlanes &PL, const float4 *labL, const fl
                                float gamma, uint8_t *valid, float *filled, float *disp, cudaStream_t st);
 // dst (H*W*3 uint8, row stride 3W) = src mirrored horizontally (src row stride in bytes)
 cudaError_t launch_mirror_rgb(const uint8_t *src, int64_t stride, int H, int W, uint8_t *dst, cudaStream_t st);
+// packed 8-bit RGB (rows of 3 W bytes) from an image of element type dtype
+// (LEM_IMG_*), srow / spx bytes between rows / pixels
+cudaError_t launch_to_rgb8(const void *src, int64_t srow, int64_t spx, int dtype, int H, int W, uint8_t *dst,
+                           cudaStream_t st);
 // Batch min-cut whose region/offset/counter scratch is a static device array
 // (no allocation); at most LEM_NOALLOC_MAX_REGIONS regions.
 cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, int n_regions, int max_nodes,

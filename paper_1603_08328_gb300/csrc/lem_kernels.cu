@@ -644,9 +644,10 @@ __device__ __forceinline__ void row_offset(float sh, float sl, float lb, float l
 // (rho, (I - c) rho); every T rows of K (R grown by r') get vertical then
 // horizontal window sums and their a_k, b_k, which enter a second ring of
 // T + 2r' + 4 rows; every T rows of R get the window means of a_k, b_k and phi.
-// Every sliding window sum restarts at rows (and columns) Ky0 + 4m, Ry0 + 4m,
-// Kx0 + 4m, Rx0 + 4m and is accumulated by one thread in a fixed order, so with
-// T a multiple of 4 the result does not depend on T or on the CTA size.
+// Every sliding window sum restarts at rows Ky0 + 4m, Ry0 + 4m and columns
+// Kx0 + 8m, Rx0 + 4m (at most 27, or 35 for the 8-column runs, terms per sum)
+// and is accumulated by one thread in a fixed order, so with T a multiple of 4
+// the result does not depend on T or on the CTA size.
 __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, int Ry0, int Rw, int Rh, float la,
                              float lb, float lc, float *sm, float *out, int pitch) {
     const int H = P.H, W = P.W, r = kp.r, T = kp.T;
@@ -673,7 +674,7 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
 
     // stage layouts (fixed for the call)
     const Grid2 gM(Mw), gK(Kw), gR(Rw), gV(4 * Mw), gV2(4 * Kw);
-    const int nchK = (Kw + 3) >> 2, nchR = (Rw + 3) >> 2;
+    const int nchK = (Kw + 7) >> 3, nchR = (Rw + 3) >> 2;
     const Grid2 gH(4 * nchK), gH2(4 * nchR);
 
     int mNext = My0, kNext = Ky0;
@@ -772,11 +773,11 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                 }
             }
             __syncthreads();
-            // horizontal window sums at K columns, 4 outputs per item
+            // horizontal window sums at K columns, 8 outputs per item
             if (gH.tr < gH.rpp) {
                 for (int cc = gH.tc; cc < 4 * nchK; cc += gH.cpr) {
                     const int ch = cc / nchK, chunk = cc - ch * nchK;
-                    const int kx0 = Kx0 + chunk * 4, kx1 = min(Kx1, kx0 + 4);
+                    const int kx0 = Kx0 + chunk * 8, kx1 = min(Kx1, kx0 + 8);
                     const int xlo = max(0, kx0 - r), xhi = min(W - 1, kx0 + r);
                     for (int row = gH.tr; row < k1 - k0; row += gH.rpp) {
                         const float *V = Vb + row * 4 * Mw + ch * Mw - Mx0;
@@ -1826,21 +1827,41 @@ __global__ void k_pixel_costs(DevPlanes P, KParams kp, float4 *lab) {
     region_unary(P, kp, x, y, 1, 1, f.x, f.y, f.z, smf, &lab[p].w, 1);
 }
 
-__global__ void k_unary_batch(DevPlanes P, KParams kp, const int4 *regions, const int64_t *offsets, int K,
-                              const float *labels, float *costs) {
+// the planes of pair pd (the batch's arrays offset to its pixels)
+__device__ __forceinline__ void pair_planes(DevPlanes &P, KParams &kp, const PairDesc &pd) {
+    P.H = pd.H;
+    P.W = pd.W;
+    P.L = px_offset(P.L, pd.off, P.fmt);
+    P.R = px_offset(P.R, pd.off, P.fmt);
+    P.gst += 3 * pd.off;
+    P.wfw += pd.off;
+    kp.seed = pd.seed;
+    kp.disp_min = pd.disp_min;
+    kp.disp_max = pd.disp_max;
+}
+
+// P: base planes of all pairs; region i belongs to pair img[i]
+__global__ void k_unary_batch(DevPlanes P, KParams kp, const PairDesc *pairs, const int *img, const int4 *regions,
+                              const int64_t *offsets, int K, const float *labels, float *costs) {
     extern __shared__ __align__(16) float smf[];
     const int i = blockIdx.x / K, k = blockIdx.x % K;
+    pair_planes(P, kp, pairs[img[i]]);
     const int4 R = regions[i];
     const float *l = labels + ((size_t)i * K + k) * 3;
     float *out = costs + offsets[i] + (int64_t)k * R.z * R.w;
     region_unary(P, kp, R.x, R.y, R.z, R.w, l[0], l[1], l[2], smf, out, R.z);
 }
 
-__global__ void k_pairwise_batch(DevPlanes P, KParams kp, const int4 *regions, const int64_t *offsets,
-                                 const float4 *lab, const float *alpha, const float *costs_alpha, int32_t *tcaps,
-                                 int32_t *ncaps, int64_t *cterm) {
+// P, lab_all: base planes and labels of all pairs; region i belongs to pair img[i]
+__global__ void k_pairwise_batch(DevPlanes P, KParams kp, const PairDesc *pairs, const int *img,
+                                 const int4 *regions, const int64_t *offsets, const float4 *lab_all,
+                                 const float *alpha, const float *costs_alpha, int32_t *tcaps, int32_t *ncaps,
+                                 int64_t *cterm) {
     __shared__ long long red[33];
     const int i = blockIdx.x;
+    const PairDesc pd = pairs[img[i]];
+    pair_planes(P, kp, pd);
+    const float4 *lab = lab_all + pd.off;
     const int4 R = regions[i];
     const float4 al = make_float4(alpha[3 * i], alpha[3 * i + 1], alpha[3 * i + 2], 0.f);
     const int n = R.z * R.w;
@@ -2249,18 +2270,6 @@ __device__ __forceinline__ ItemGeom item_geom(int ci, int cj, int s, int H, int 
     return g;
 }
 
-// the planes of pair pd (the batch's arrays offset to its pixels)
-__device__ __forceinline__ void pair_planes(DevPlanes &P, KParams &kp, const PairDesc &pd) {
-    P.H = pd.H;
-    P.W = pd.W;
-    P.L = px_offset(P.L, pd.off, P.fmt);
-    P.R = px_offset(P.R, pd.off, P.fmt);
-    P.gst += 3 * pd.off;
-    P.wfw += pd.off;
-    kp.seed = pd.seed;
-    kp.disp_min = pd.disp_min;
-    kp.disp_max = pd.disp_max;
-}
 
 //   units: n_items * nK, unit u = (item u / nK, proposal t0 + u % nK)
 //   phiK : nK planes of plane_stride floats (every pair's pixels); alphaK[u]
@@ -2293,7 +2302,8 @@ __global__ void __launch_bounds__(128) k_visit_unary(DevPlanes P, KParams kp, Le
 // lem_unary_batch on handles with batched visits: the warp data term of the
 // expansion path, one warp per (region, label)
 template <int NC>
-__global__ void __launch_bounds__(128) k_unary_batch_warp(DevPlanes P, KParams kp, const int4 *regions,
+__global__ void __launch_bounds__(128) k_unary_batch_warp(DevPlanes P, KParams kp, const PairDesc *pairs,
+                                                          const int *img, const int4 *regions,
                                                           const int64_t *offsets, int n_regions, int K,
                                                           const float *labels, float *costs, int mwp, int kwp) {
     extern __shared__ __align__(16) float smw[];
@@ -2301,6 +2311,7 @@ __global__ void __launch_bounds__(128) k_unary_batch_warp(DevPlanes P, KParams k
     const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
     if (unit >= n_regions * K) return;
     const int i = unit / K, k = unit - i * K;
+    pair_planes(P, kp, pairs[img[i]]);
     const int4 R = regions[i];
     const float *l = labels + (size_t)unit * 3;
     float *out = costs + offsets[i] + (int64_t)k * R.z * R.w;
@@ -3279,22 +3290,22 @@ cudaError_t launch_pixel_costs(const DevPlanes &P, const KParams &kp, float4 *la
     return cudaGetLastError();
 }
 
-cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
-                               int n_regions, int K, int max_w, int max_h, const float *labels, float *costs,
-                               int threads, cudaStream_t st) {
+cudaError_t launch_unary_batch(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                               const int4 *regions, const int64_t *offsets, int n_regions, int K, int max_w,
+                               int max_h, const float *labels, float *costs, int threads, cudaStream_t st) {
     const size_t sm = unary_bytes_host(kp, P.H, P.W, max_w, max_h);
     cudaError_t e = set_smem((const void *)k_unary_batch, sm);
     if (e != cudaSuccess) return e;
-    k_unary_batch<<<n_regions * K, threads, sm, st>>>(P, kp, regions, offsets, K, labels, costs);
+    k_unary_batch<<<n_regions * K, threads, sm, st>>>(P, kp, pairs, img, regions, offsets, K, labels, costs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const int4 *regions,
-                                  const int64_t *offsets, int n_regions, const float4 *lab, const float *alpha,
-                                  const float *costs_alpha, int32_t *tcaps, int32_t *ncaps, int64_t *cterm,
-                                  int threads, cudaStream_t st) {
-    k_pairwise_batch<<<n_regions, threads, 0, st>>>(P, kp, regions, offsets, lab, alpha, costs_alpha, tcaps, ncaps,
-                                                    cterm);
+cudaError_t launch_pairwise_batch(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                                  const int4 *regions, const int64_t *offsets, int n_regions, const float4 *lab,
+                                  const float *alpha, const float *costs_alpha, int32_t *tcaps, int32_t *ncaps,
+                                  int64_t *cterm, int threads, cudaStream_t st) {
+    k_pairwise_batch<<<n_regions, threads, 0, st>>>(P, kp, pairs, img, regions, offsets, lab, alpha, costs_alpha,
+                                                    tcaps, ncaps, cterm);
     return cudaGetLastError();
 }
 
@@ -3436,15 +3447,15 @@ int warps_per_cta(int units, int most) {
 }
 
 template <int NC>
-cudaError_t unary_batch_warp_nc(const DevPlanes &P, const KParams &kp, const int4 *regions, const int64_t *offsets,
-                                int n_regions, int K, const float *labels, float *costs, int mwp, int kwp, int most,
-                                cudaStream_t st) {
+cudaError_t unary_batch_warp_nc(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                                const int4 *regions, const int64_t *offsets, int n_regions, int K,
+                                const float *labels, float *costs, int mwp, int kwp, int most, cudaStream_t st) {
     const size_t ring = sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp);
     const int units = n_regions * K, w = warps_per_cta(units, most);
     cudaError_t e = set_smem((const void *)k_unary_batch_warp<NC>, ring * w);
     if (e != cudaSuccess) return e;
-    k_unary_batch_warp<NC><<<(units + w - 1) / w, 32 * w, ring * w, st>>>(P, kp, regions, offsets, n_regions, K,
-                                                                          labels, costs, mwp, kwp);
+    k_unary_batch_warp<NC><<<(units + w - 1) / w, 32 * w, ring * w, st>>>(P, kp, pairs, img, regions, offsets,
+                                                                          n_regions, K, labels, costs, mwp, kwp);
     return cudaGetLastError();
 }
 
@@ -3487,14 +3498,15 @@ bool unary_warp_fits(const KParams &kp, int W, int max_w) {
     return !kp.bf && (mwp + 31) / 32 <= 4 && sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp) <= 227 * 1024;
 }
 
-cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const int4 *regions,
-                                    const int64_t *offsets, int n_regions, int K, int max_w, const float *labels,
-                                    float *costs, cudaStream_t st) {
+cudaError_t launch_unary_batch_warp(const DevPlanes &P, const KParams &kp, const PairDesc *pairs, const int *img,
+                                    const int4 *regions, const int64_t *offsets, int n_regions, int K, int max_w,
+                                    const float *labels, float *costs, cudaStream_t st) {
     const int mwp = std::min(P.W, max_w + 4 * kp.r), kwp = std::min(P.W, max_w + 2 * kp.r);
     const int nc = (mwp + 31) / 32;
     const int most =
         (int)std::min<size_t>(4, (227 * 1024) / (sizeof(float) * (size_t)warp_ring_floats(kp.r, mwp, kwp)));
-#define LEM_UBW(NC_) unary_batch_warp_nc<NC_>(P, kp, regions, offsets, n_regions, K, labels, costs, mwp, kwp, most, st)
+#define LEM_UBW(NC_) \
+    unary_batch_warp_nc<NC_>(P, kp, pairs, img, regions, offsets, n_regions, K, labels, costs, mwp, kwp, most, st)
     switch (nc) {
         case 1: return LEM_UBW(1);
         case 2: return LEM_UBW(2);
@@ -3703,6 +3715,35 @@ cudaError_t launch_props_out(int n, const float4 *prop, float *abc, cudaStream_t
     return cudaGetLastError();
 }
 
+// Packed 8-bit RGB from an image of any element type and layout: the first
+// three values of each pixel, a float rounded to the nearest integer and
+// clamped to [0, 255] (NaN to 0).
+__global__ void k_to_rgb8(const unsigned char *src, int64_t srow, int64_t spx, int dtype, int H, int W,
+                          uint8_t *dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const unsigned char *s = src + (size_t)y * srow + (size_t)x * spx;
+    uint8_t *d = dst + ((size_t)y * W + x) * 3;
+    for (int c = 0; c < 3; ++c) {
+        if (dtype == LEM_IMG_U8) {
+            d[c] = s[c];
+            continue;
+        }
+        float v;
+        if (dtype == LEM_IMG_F16) v = __half2float(reinterpret_cast<const __half *>(s)[c]);
+        else if (dtype == LEM_IMG_BF16) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(s)[c]);
+        else v = reinterpret_cast<const float *>(s)[c];
+        d[c] = (uint8_t)rintf(fminf(fmaxf(v, 0.f), 255.f));
+    }
+}
+
+cudaError_t launch_to_rgb8(const void *src, int64_t srow, int64_t spx, int dtype, int H, int W, uint8_t *dst,
+                           cudaStream_t st) {
+    dim3 grid((W + 255) / 256, H);
+    k_to_rgb8<<<grid, 256, 0, st>>>((const unsigned char *)src, srow, spx, dtype, H, W, dst);
+    return cudaGetLastError();
+}
+
 __global__ void k_mirror_rgb(const uint8_t *src, int64_t stride, int H, int W, uint8_t *dst) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= W || y >= H) return;
@@ -3831,8 +3872,11 @@ cudaError_t launch_mincut_noalloc(const KParams &kp, const lem_region *regions, 
     int4 *d_regions = (int4 *)(scr + kNoAllocRegionsOff);
     int64_t *d_offsets = (int64_t *)(scr + kNoAllocOffsetsOff);
     Counters *d_ctr = (Counters *)(scr + kNoAllocCountersOff);
-    // lem_region is four ints, the layout of int4
-    e = cudaMemcpyAsync(d_regions, regions, sizeof(int4) * n_regions, cudaMemcpyHostToDevice, st);
+    // the first four ints of each lem_region (x0, y0, w, h), packed as int4
+    static_assert(sizeof(lem_region) >= sizeof(int4) && offsetof(lem_region, h) == 3 * sizeof(int),
+                  "lem_region starts with x0, y0, w, h");
+    e = cudaMemcpy2DAsync(d_regions, sizeof(int4), regions, sizeof(lem_region), sizeof(int4), n_regions,
+                          cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st);
     if (e != cudaSuccess) return e;

@@ -28,9 +28,12 @@ LEM_MAX_REGION_NODES = 5625
 LEM_NOALLOC_MAX_REGIONS = 4096
 
 
+LEM_IMG_U8, LEM_IMG_F16, LEM_IMG_BF16, LEM_IMG_F32 = 0, 1, 2, 3
+
+
 class lem_image(C.Structure):
     _fields_ = [("data", C.c_void_p), ("height", C.c_int), ("width", C.c_int), ("stride_row", C.c_int64),
-                ("on_device", C.c_int)]
+                ("on_device", C.c_int), ("channels", C.c_int), ("stride_px", C.c_int64), ("dtype", C.c_int)]
 
 
 class lem_params(C.Structure):
@@ -58,7 +61,8 @@ class lem_tuning(C.Structure):
 
 
 class lem_region(C.Structure):
-    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("w", C.c_int), ("h", C.c_int)]
+    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("w", C.c_int), ("h", C.c_int), ("img", C.c_int),
+                ("cx0", C.c_int), ("cy0", C.c_int), ("cw", C.c_int), ("ch", C.c_int)]
 
 
 LEM_KERNEL_EXPAND, LEM_KERNEL_VISIT_UNARY, LEM_KERNEL_VISIT_CUT, LEM_KERNEL_GRID = 0, 1, 2, 3
@@ -259,6 +263,7 @@ def lem_destroy(h):
 
 
 def _regions(regions):
+    """(x0, y0, w, h[, img[, cx0, cy0, cw, ch]]) tuples -> lem_region array."""
     arr = (lem_region * len(regions))()
     for i, r in enumerate(regions):
         arr[i] = lem_region(*[int(x) for x in r])
@@ -486,14 +491,25 @@ class Stereo:
         self.total = sum(hh * ww for hh, ww, _ in self.pairs)
 
     def _image(self, img):
+        """An (H, W, C >= 3) image: a CUDA tensor (uint8, float16, bfloat16, float32; any strides
+        with a unit channel step) or a host array (uint8, float16, float32), passed as it is."""
         torch = self.torch
         if isinstance(img, torch.Tensor):
-            assert img.dtype == torch.uint8 and img.is_cuda and img.is_contiguous()
+            codes = {torch.uint8: LEM_IMG_U8, torch.float16: LEM_IMG_F16, torch.bfloat16: LEM_IMG_BF16,
+                     torch.float32: LEM_IMG_F32}
+            assert img.is_cuda and img.dim() == 3 and img.dtype in codes and img.stride(2) == 1
             self._keep.append(img)
-            return lem_image(img.data_ptr(), img.shape[0], img.shape[1], 3 * img.shape[1], 1)
-        a = np.ascontiguousarray(img, dtype=np.uint8)
+            es = img.element_size()
+            return lem_image(img.data_ptr(), img.shape[0], img.shape[1], img.stride(0) * es, 1, img.shape[2],
+                             img.stride(1) * es, codes[img.dtype])
+        a = np.asarray(img)
+        codes = {np.dtype(np.uint8): LEM_IMG_U8, np.dtype(np.float16): LEM_IMG_F16, np.dtype(np.float32): LEM_IMG_F32}
+        if a.dtype not in codes:
+            a = a.astype(np.uint8)
+        a = np.ascontiguousarray(a)
         self._keep.append(a)
-        return lem_image(a.ctypes.data, a.shape[0], a.shape[1], 3 * a.shape[1], 0)
+        return lem_image(a.ctypes.data, a.shape[0], a.shape[1], a.strides[0], 0, a.shape[2], a.strides[1],
+                         codes[a.dtype])
 
     def close(self):
         if getattr(self, "h", None):

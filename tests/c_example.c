@@ -13,7 +13,8 @@ int example(const uint8_t *left_rgb, const uint8_t *right_rgb, int H, int W, flo
     lem_params p;
     lem_default_params(&p);
     p.disp_max = 60.0;
-    lem_image L = {left_rgb, H, W, 3 * W, 0}, R = {right_rgb, H, W, 3 * W, 0}; /* host images */
+    /* host images, packed 8-bit RGB */
+    lem_image L = {left_rgb, H, W, 3 * W, 0, 3, 3, LEM_IMG_U8}, R = {right_rgb, H, W, 3 * W, 0, 3, 3, LEM_IMG_U8};
     lem_handle *h = NULL;
     if (lem_create(&L, &R, &p, &h) != LEM_OK) {
         fprintf(stderr, "%s\n", lem_last_error(NULL));

@@ -120,6 +120,34 @@ def test_parameter_checks_of_the_later_options(L):
         assert not h.value
 
 
+def test_image_layout_checks_without_touching_the_gpu(L):
+    """lem_image's element type, channel count, pixel stride and alignment are checked
+    before any GPU work: an unknown dtype, 2 or 17 channels and a float pointer or stride
+    that is not a multiple of 4 bytes are LEM_ERR_ARG; a pixel stride shorter than its
+    channels or a row stride shorter than the row is LEM_ERR_SHAPE; dataflow must be 0/1."""
+    lib = L.lib()
+    a = np.zeros((32, 40, 4), np.float32)
+    base = a.ctypes.data
+    p = L.lem_default_params(gf_radius=2)
+    h = C.c_void_p()
+
+    def rc(im, prm=p):
+        return lib.lem_create(C.byref(im), C.byref(im), C.byref(prm), C.byref(h))
+
+    f32 = L.LEM_IMG_F32
+    assert rc(L.lem_image(base, 32, 40, 640, 0, 4, 16, 7)) == L.LEM_ERR_ARG           # dtype
+    assert rc(L.lem_image(base, 32, 40, 640, 0, 2, 16, f32)) == L.LEM_ERR_ARG         # channels
+    assert rc(L.lem_image(base, 32, 40, 640, 0, 17, 16, f32)) == L.LEM_ERR_ARG
+    assert rc(L.lem_image(base + 2, 32, 40, 640, 0, 4, 16, f32)) == L.LEM_ERR_ARG     # alignment
+    assert rc(L.lem_image(base, 32, 40, 642, 0, 4, 16, f32)) == L.LEM_ERR_ARG
+    assert rc(L.lem_image(base, 32, 40, 640, 0, 4, 12, f32)) == L.LEM_ERR_SHAPE       # stride_px < 4 ch
+    assert rc(L.lem_image(base, 32, 40, 620, 0, 4, 16, f32)) == L.LEM_ERR_SHAPE       # stride_row < row
+    assert "stride_row" in L.lem_last_error(None)
+    assert rc(L.lem_image(base, 32, 40, 640, 0, 4, 16, f32), L.lem_default_params(gf_radius=2, dataflow=2)) \
+        == L.LEM_ERR_ARG
+    assert not h.value
+
+
 def test_c_example_compiles_and_links(L):
     """tests/c_example.c (the usage example the README shows) is valid C99 against
     include/lem.h and links with the in-tree liblem.so (compiled and linked only:
