@@ -677,25 +677,39 @@ def time_to_energy(lem, pair, stream, tuned, seed=21, n_plain=ITERS_PER_HANDLE, 
 def middlebury_timing(lem, stream, flush, steps=3):
     """The 450 x 375 Middlebury-V2-shaped pair (disparities 0-60) with the paper's
     schedule (sequential proposals, FP32 images): iterations 2 .. steps + 1, L2 flushed
-    before each, kernel times from the library's events."""
+    before each, kernel times from the library's events; once with the default launch
+    shape and group launches, once autotuned (after iteration 1) with dataflow launches
+    (the same labels)."""
     from synth import workload_pair
     pair = workload_pair("middlebury_450x375", 0)
-    g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=61, disp_max=60.0)
-    g.set_kernel_timing(True)
-    g.iterate(1, stats=False)
-    ts, kt = [], {}
-    for _ in range(steps):
-        ts.append(timed_iteration(lem, g, stream, flush))
-        for (l, k), (ms, n) in g.kernel_times().items():
-            kt[f"{k} level {l}"] = kt.get(f"{k} level {l}", 0.0) + ms
-    st = g.iterate(0)
-    evals = g.evals_per_iteration()
-    g.close()
-    t = sum(ts) / len(ts)
+
+    def one(**kw):
+        g = lem.Stereo(pair["left"], pair["right"], stream=stream, seed=61, disp_max=60.0, **kw)
+        g.set_kernel_timing(True)
+        g.iterate(1, stats=False)
+        tuned = None
+        if kw:
+            t = g.autotune(repeats=1)
+            tuned = [list(t.threads), list(t.gr_interval), list(t.strip_rows)]
+        ts, kt = [], {}
+        for _ in range(steps):
+            ts.append(timed_iteration(lem, g, stream, flush))
+            for (l, k), (ms, n) in g.kernel_times().items():
+                kt[f"{k} level {l}"] = kt.get(f"{k} level {l}", 0.0) + ms
+        st = g.iterate(0)
+        evals = g.evals_per_iteration()
+        g.close()
+        t = sum(ts) / len(ts)
+        out = {"ms_per_iteration": 1e3 * t, "evals_per_s": evals / t, "maxflow_limit": st.maxflow_limit,
+               "kernel_ms_per_iteration": {k: v / steps for k, v in kt.items()}}
+        if tuned:
+            out["launch_config"] = tuned
+        return out
+
     return {"workload": "middlebury_450x375 (disparity 0-60), FP32 images, sequential proposals",
-            "ms_per_iteration": 1e3 * t, "evals_per_s": evals / t, "maxflow_limit": st.maxflow_limit,
-            "kernel_ms_per_iteration": {k: v / steps for k, v in kt.items()},
-            "note": f"iterations 2-{steps + 1}, default launch configuration, L2 flushed between"}
+            "default": one(), "tuned_dataflow": one(work_queue=1, dataflow=1),
+            "note": f"iterations 2-{steps + 1}, L2 flushed between; default = group launches with the default launch "
+                    f"configuration, tuned_dataflow = dataflow launches autotuned after iteration 1"}
 
 
 def run_lem(args):

@@ -353,8 +353,9 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
 /* n_iters outer iterations of Algorithm 1 (every level, all 16 groups),
  * continuing from the handle's iteration counter.  With params.use_graph the
  * first call runs one iteration directly and captures one iteration (48
- * launches and the increment of a device-side iteration index) as a CUDA
- * graph on a private stream; later iterations replay that graph on the
+ * group launches, or with params.dataflow 3 level launches and the memsets of
+ * their done flags, and the increment of a device-side iteration index) as a
+ * CUDA graph on a private stream; later iterations replay that graph on the
  * handle's stream (a handle with a level on the multi-CTA path always launches
  * directly).  stats may be NULL (no synchronisation); when given, the call
  * synchronises and fills all fields (energy after the last iteration).
@@ -434,10 +435,9 @@ int lem_get_kernel_times(lem_handle *h, lem_kernel_times *out);
  * fixed array of about 96 KiB in the library's device memory, which every GPU
  * that loads the library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with that
- * device current) and keeps it for the life of the process; make that first
- * call before any stream capture.  A cudaDeviceReset unloads the array, so
- * this entry point must not be called after a device reset in the same
- * process.  Every call shares the array and overwrites it (the counters are
+ * device current) and keeps it for the life of the process.  A
+ * cudaDeviceReset unloads the array, so this entry point must not be called
+ * after a device reset in the same process.  Every call shares the array and overwrites it (the counters are
  * cleared first), so calls whose work overlaps on the GPU race: order them on
  * one stream, or synchronise between them.
  *
