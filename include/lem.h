@@ -588,16 +588,19 @@ int64_t lem_cnn_num_params(void);
 int lem_cnn_get_params(lem_cnn *net, float *host);
 int lem_cnn_set_params(lem_cnn *net, const float *host);
 /* Forward pass: x DEVICE (H4*W4*7 floats), y DEVICE (H4*W4*3 floats).
- * Errors: LEM_ERR_ARG, LEM_ERR_OOM, LEM_ERR_CUDA. */
+ * Errors: LEM_ERR_ARG (also W4 > 1605: a convolution tile stages three rows of
+ * the padded grid in shared memory), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *y);
 /* Loss and gradients over n_images inputs x (DEVICE, n*H4*W4*7) with targets
  * t (DEVICE, n*H4*W4*3): loss = mean over images and pixels of
  * sum_c scale_c |y_c - t_c|.  scale: HOST, 3 floats.  loss: HOST float or NULL;
  * grads: HOST array in the lem_cnn_get_params order, or NULL.  All images go
- * through each layer together (one launch per layer and pass), so the network
- * holds activations for n*H4*W4 pixels (about 1.3 KB each; grown on demand,
- * kept until lem_cnn_destroy).  Synchronises the stream.  Errors: LEM_ERR_ARG
- * (also when n*H4*W4*32 exceeds 2^31 - 1), LEM_ERR_OOM, LEM_ERR_CUDA. */
+ * through each layer together (one launch per layer and pass) on one
+ * zero-padded grid, so the network holds activations for about
+ * n*(H4+2)*(W4+2) positions (1.25 KB each; grown on demand, cleared when the
+ * shape changes, kept until lem_cnn_destroy).  Synchronises the stream.
+ * Errors: LEM_ERR_ARG (also when the grid exceeds 2^31 / 32 positions or
+ * W4 > 1605), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_gradients(lem_cnn *net, const float *x, const float *t, int n_images, int H4, int W4,
                       const float *scale, float *loss, float *grads);
 /* lem_cnn_gradients, then one Adam step (beta 0.9 / 0.999, eps 1e-8, rate lr). */

@@ -6,15 +6,18 @@
 //
 // Convolutions are implicit GEMMs on the tensor cores (BF16 operands, FP32
 // accumulation):
-//   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = 128 pixels, N = Cout, K = 9 Cin)
-//                on tcgen05.mma with the accumulator in tensor memory
+//   forward      Y[p][o]   = sum_k Xpatch[p][k] W[k][o]        (M = 128 positions, N = Cout, K = 9 Cin)
+//                on tcgen05.mma with the accumulator in tensor memory; the input
+//                band is staged by the bulk-copy engine and each tap's A operand
+//                is that band seen from a shifted shared-memory descriptor
 //   input grad   dX        = the same kernel with flipped, transposed weights
 //   weight grad  dW^T[k][o] = sum_p Xpatch[p][k] dZ[p][o]     (M = 9 Cin, N = Cout, K = pixels)
 //                on tcgen05.mma: each CTA accumulates its pixel range in tensor
 //                memory and writes a partial sum; a second kernel adds the
 //                partials in a fixed order, so gradients are bit-reproducible
-// Activations are BF16, NHWC, channels padded to a multiple of 16; the weights
-// have an FP32 master copy updated by Adam.
+// Activations live on a zero-padded grid (see Geo below): BF16 in 8-channel
+// blocks, channels padded to a multiple of 16; the weights have an FP32 master
+// copy updated by Adam.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,17 +40,16 @@ constexpr int kRealCin[kLayers] = {7, 32, 32, 32, 32, 32};
 constexpr int kRealCout[kLayers] = {32, 32, 32, 32, 32, 3};
 constexpr int kTileP = 128;  // pixels per CTA
 
-typedef __nv_bfloat16 bf16;
-
-__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// element index of (row, k) in a rows x K bf16 matrix stored in the K-major
+// no-swizzle core-matrix layout (8 rows x 8 elements = 128 contiguous bytes per
+// core matrix, core matrix (row / 8, k / 8) at (row / 8 * K / 8 + k / 8) * 64):
+// the weights are kept in global memory in this order, so one bulk copy makes
+// the tensor cores' B operand
+__host__ __device__ __forceinline__ size_t cm_index(int row, int k, int K) {
+    return ((size_t)(row >> 3) * (K >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
+
+typedef __nv_bfloat16 bf16;
 
 // ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor core) helpers.  Operands sit in shared memory
@@ -141,90 +143,162 @@ constexpr int kConvThreads = 128;       // 4 warps: warp w reads TMEM lanes 32w 
 constexpr int kMmaWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
 static_assert(kConvThreads == kTileP, "one thread per pixel row of the tile");
 
-// Y = conv3x3(X) (+ bias) for 128 pixels per CTA as one 128 x COUT x 9CIN GEMM
-// on the tensor cores: the pixels' 3x3 patches (A, 128 x K) and the weights
-// (B, COUT x K, both K-major) are staged in shared memory, one thread issues
-// K/16 tcgen05.mma into a TMEM accumulator, and each warp reads its 32 rows
-// back for the epilogue.
-// B images of H x W pixels are stacked row after row; a patch never reaches
-// across an image's border (zero padding as for a single image).
-//   X  : B*H*W*CIN bf16;  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]);
-//   Z  : optional fp32 pre-activation B*H*W*COUT;  Y : optional bf16 output (ReLU if relu)
+// ---------------------------------------------------------------------------
+// Activation layout.  B images of H x W pixels sit in one zero-padded grid:
+// each image gets a zero row above and below and a zero column left and right,
+// so a pixel's 3x3 neighbourhood is the positions q + dy (W + 2) + dx around
+// its position q, and the images follow one another row after row.  G guard
+// positions before and after the grid keep every shifted read in the buffer.
+//   bf16 tensors (layer inputs, output gradients): channel-blocked, 8 channels
+//     (16 bytes) per position and block, block c8 of position q at
+//     (c8 * Ptot + q) * 8 elements;
+//   fp32 tensors (pre-activations, input gradients): C values per position at
+//     q * C.
+// Only interior positions are ever written; the rest stay zero (the buffers
+// are cleared whenever the geometry changes).
+// ---------------------------------------------------------------------------
+struct Geo {
+    int B, H, W;    // images and their size
+    int Wp;         // W + 2
+    int64_t G;      // guard positions before the grid (= Wp + 1)
+    int64_t P;      // positions of the grid, B (H + 2) Wp
+    int64_t tiles;  // 128-position tiles covering the grid
+    int64_t Ptot;   // G + 128 tiles + G
+};
+inline Geo make_geo(int B, int H, int W) {
+    Geo g;
+    g.B = B;
+    g.H = H;
+    g.W = W;
+    g.Wp = W + 2;
+    g.G = g.Wp + 1;
+    g.P = (int64_t)B * (H + 2) * g.Wp;
+    g.tiles = (g.P + 127) / 128;
+    g.Ptot = g.G + 128 * g.tiles + g.G;
+    return g;
+}
+// position of interior pixel p (0 .. B H W - 1, images one after the other, row-major)
+__host__ __device__ __forceinline__ int64_t pos_of(const Geo &g, int64_t p) {
+    const int64_t x = p % g.W, r = p / g.W;  // r: row over all images
+    const int64_t b = r / g.H, y = r - b * g.H;
+    return g.G + (b * (g.H + 2) + y + 1) * g.Wp + x + 1;
+}
+// whether grid position q holds a pixel (not padding or guard)
+__device__ __forceinline__ bool interior(const Geo &g, int64_t q) {
+    const int64_t t = q - g.G;
+    if (t < 0 || t >= g.P) return false;
+    const int64_t r = t / g.Wp, x = t - r * g.Wp;
+    const int64_t y = r % (g.H + 2);
+    return x >= 1 && x <= g.W && y >= 1 && y <= g.H;
+}
+
+// Y = conv3x3(X) (+ bias) as an implicit GEMM on the tensor cores, 128 grid
+// positions per CTA (M = 128, N = COUT, K = 9 CIN), with no patch gathering:
+// one thread copies, per 8-channel block, the positions q0 - G .. q0 + 127 + G
+// of X into shared memory with the bulk-copy engine (cp.async.bulk, completion
+// on an mbarrier); each block's run of 16-byte positions is a column of 8-row
+// core matrices of the K-major no-swizzle layout, so the A operand of tap
+// (dy, dx) is the same shared memory seen from an offset of dy (W + 2) + dx
+// positions.  The weights (B, COUT x 9CIN), kept in global memory in that
+// layout, come with the same copies; one thread issues the 9 CIN / 16
+// tcgen05.mma into a TMEM accumulator and each
+// warp reads its 32 rows back for the epilogue, which writes interior
+// positions only.
+//   X  : bf16, channel-blocked (CIN / 8 blocks);  Bt : COUT x (9 CIN) bf16 (row o holds W[k][o]) in the
+//        core-matrix order of cm_index;
+//   Z  : optional fp32 pre-activation, COUT per position;  Y : optional bf16 output, channel-blocked
+//        (ReLU if relu)
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int W, int B, const bf16 *Bt,
-                                                       const float *bias, float *Z, bf16 *Y, int relu) {
+__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, Geo g, const bf16 *Bt, const float *bias,
+                                                       float *Z, bf16 *Y, int relu) {
     constexpr int K = 9 * CIN, KC = K / 8, CH = CIN / 8;
     extern __shared__ __align__(128) unsigned char sm_raw[];
-    unsigned char *As = sm_raw;                          // 128 x K, core-matrix layout
-    unsigned char *Bs = sm_raw + (size_t)kTileP * K * 2; // COUT x K, core-matrix layout
-    __shared__ __align__(8) uint64_t mbar;
+    const int span = 128 + 2 * (int)g.G;                   // positions staged per block
+    const uint32_t SA = ((uint32_t)span * 16u + 127u) & ~127u;  // bytes per block in shared memory
+    unsigned char *Bs = sm_raw;                            // COUT x K, core-matrix layout
+    unsigned char *As = sm_raw + (size_t)COUT * K * 2;     // CH blocks of SA bytes
+    __shared__ __align__(8) uint64_t mbar_ld, mbar_mma;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = H * W * B, p0 = blockIdx.x * kTileP;
+    const int64_t q0 = g.G + (int64_t)blockIdx.x * kTileP;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_ld)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_mma)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    // weights: row o, k chunk c -> core matrix (o/8, c), row o%8
-    for (int q = tid; q < COUT * KC; q += kConvThreads) {
-        const int o = q / KC, c = q - o * KC;
-        *reinterpret_cast<uint4 *>(Bs + ((o >> 3) * KC + c) * 128 + (o & 7) * 16) =
-            *reinterpret_cast<const uint4 *>(Bt + (size_t)o * K + c * 8);
-    }
-    // patches: one thread per pixel row r, k chunk c = tap * CH + c8
-    {
-        const int r = tid, p = p0 + r;
-        unsigned char *row = As + (size_t)(r >> 3) * KC * 128 + (r & 7) * 16;
-        const int u = p % W, y = p / W, v = y % H;  // row of the stacked images, row within the image
-        for (int c = 0; c < KC; ++c) {
-            const int tap = c / CH, c8 = c - tap * CH;
-            const int uu = u + tap % 3 - 1, dv = tap / 3 - 1;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (p < n && uu >= 0 && uu < W && v + dv >= 0 && v + dv < H)
-                val = *reinterpret_cast<const uint4 *>(X + ((size_t)(y + dv) * W + uu) * CIN + c8 * 8);
-            *reinterpret_cast<uint4 *>(row + c * 128) = val;
+        // bulk copies of the weights (already in core-matrix order) and of the CH
+        // blocks: positions q0 - G .. q0 + 127 + G (16 bytes each)
+        const uint32_t bytes = (uint32_t)span * 16u, wbytes = (uint32_t)(COUT * K * 2);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&mbar_ld)),
+                     "r"(bytes * CH + wbytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(Bs)),
+            "l"(Bt), "r"(wbytes), "r"(smem_u32(&mbar_ld))
+            : "memory");
+        for (int c = 0; c < CH; ++c) {
+            const bf16 *src = X + ((size_t)c * g.Ptot + (size_t)(q0 - g.G)) * 8;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(As + (size_t)c * SA)),
+                "l"(src), "r"(bytes), "r"(smem_u32(&mbar_ld))
+                : "memory");
         }
     }
-    // generic-proxy stores -> visible to the tensor core's async proxy
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __shared__ float s_bias[COUT];
+    if (tid < COUT) s_bias[tid] = bias ? bias[tid] : 0.f;
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tbase = tmem_base;
+    __shared__ int s_ok;
     if (tid == 0) {
-        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-        constexpr uint32_t idesc = idesc_bf16(kTileP, COUT);
+        s_ok = mbar_wait0(smem_u32(&mbar_ld), kMmaWaitLimit) ? 1 : 0;
+        if (s_ok) {
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            constexpr uint32_t idesc = idesc_bf16(kTileP, COUT);
 #pragma unroll 1
-        for (int kk = 0; kk < K / 16; ++kk) {
-            // K step kk covers core-matrix columns 2kk, 2kk+1
-            const uint64_t ad = smem_desc(a0 + kk * 256, 128, KC * 128);
-            const uint64_t bd = smem_desc(b0 + kk * 256, 128, KC * 128);
-            mma_tc(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            for (int t = 0; t < 9; ++t) {
+                const int shift = (t / 3 - 1) * g.Wp + (t % 3 - 1);
+                const uint32_t at = a0 + (uint32_t)((int)g.G + shift) * 16u;
+#pragma unroll 1
+                for (int j = 0; j < CH / 2; ++j) {
+                    // K step: channels 16j .. 16j + 15 of tap t = blocks 2j, 2j + 1
+                    const uint64_t ad = smem_desc(at + (uint32_t)(2 * j) * SA, SA, 128);
+                    const uint64_t bd = smem_desc(b0 + (uint32_t)(t * (CH / 2) + j) * 256, 128, KC * 128);
+                    mma_tc(tbase, ad, bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar_mma))
+                         : "memory");
+        } else {
+            atomicAdd(&g_mma_timeouts, 1u);
+            // the copies may still be in flight: one more bounded wait before the
+            // CTA's shared memory can be handed on
+            mbar_wait0(smem_u32(&mbar_ld), kMmaWaitLimit);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         smem_u32(&mbar))
-                     : "memory");
     }
-    const bool ok = mbar_wait0(smem_u32(&mbar), kMmaWaitLimit);
+    __syncthreads();
+    const bool ok = s_ok && mbar_wait0(smem_u32(&mbar_mma), kMmaWaitLimit);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
         float acc[COUT];
         tmem_load_row<COUT>(tbase + ((uint32_t)(warp * 32) << 16), acc);
-        const int p = p0 + warp * 32 + lane;
-        if (p < n) {
+        const int64_t q = q0 + warp * 32 + lane;
+        if (interior(g, q)) {
 #pragma unroll
-            for (int o = 0; o < COUT; ++o) acc[o] += bias ? bias[o] : 0.f;
+            for (int o = 0; o < COUT; ++o) acc[o] += s_bias[o];
             if (Z) {
-                float4 *z4 = reinterpret_cast<float4 *>(Z + (size_t)p * COUT);
+                float4 *z4 = reinterpret_cast<float4 *>(Z + (size_t)q * COUT);
 #pragma unroll
                 for (int o = 0; o < COUT; o += 4) z4[o / 4] = make_float4(acc[o], acc[o + 1], acc[o + 2], acc[o + 3]);
             }
             if (Y) {
-                uint4 *y4 = reinterpret_cast<uint4 *>(Y + (size_t)p * COUT);
 #pragma unroll
                 for (int o = 0; o < COUT; o += 8) {
                     __nv_bfloat162 h[4];
@@ -234,14 +308,15 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
                         const float x1 = relu ? fmaxf(acc[o + 2 * j + 1], 0.f) : acc[o + 2 * j + 1];
                         h[j] = __floats2bfloat162_rn(x0, x1);
                     }
-                    y4[o / 8] = *reinterpret_cast<uint4 *>(h);
+                    *reinterpret_cast<uint4 *>(Y + ((size_t)(o / 8) * g.Ptot + (size_t)q) * 8) =
+                        *reinterpret_cast<uint4 *>(h);
                 }
             }
         }
-    } else if (tid == 0) {
+    } else if (tid == 0 && s_ok) {
         atomicAdd(&g_mma_timeouts, 1u);
         // give the MMAs in flight one more bounded chance before TMEM is freed
-        mbar_wait0(smem_u32(&mbar), kMmaWaitLimit);
+        mbar_wait0(smem_u32(&mbar_mma), kMmaWaitLimit);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -257,10 +332,12 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *X, int H, int
 // across the tiles).  The CTA then writes its partial dW (COUT x 9CIN, the
 // layout of gW) and bias partial (sum of dZ over its pixels, in pixel order) to
 // part / partb at its index; k_wgrad_reduce adds the partials in index order.
-//   X  : B*H*W*CIN bf16 (B stacked images, as in k_conv);  dZ : B*H*W*COUT bf16
+// The pixels are the interior pixels of the grid in order; a patch reads the
+// zero padding beyond its image's border.
+//   X  : bf16, channel-blocked (CIN / 8 blocks);  dZ : bf16, channel-blocked (COUT / 8 blocks)
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const bf16 *dZ, int H, int W, int B,
-                                                           int tiles_per_cta, float *part, float *partb) {
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const bf16 *dZ, Geo g, int tiles_per_cta,
+                                                           float *part, float *partb) {
     constexpr int K = 9 * CIN, MT = (K + 127) / 128, MP = MT * 128, PC = kTileP / 8, CH = CIN / 8;
     constexpr int TC = MT * COUT <= 32 ? 32 : (MT * COUT <= 64 ? 64 : (MT * COUT <= 128 ? 128 : 256));
     extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -270,7 +347,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const 
     __shared__ uint32_t tmem_base;
     __shared__ float s_db[COUT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = H * W * B;
+    const int n = g.H * g.W * g.B;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                      "r"(TC));
@@ -298,13 +375,12 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const 
             // thread r: pixel r of the tile; its patch values are column r of A,
             // its output gradient column r of B
             const int r = tid, p = p0 + r;
-            const int u = p % W, y = p / W, v = y % H;  // as in k_conv
+            const int64_t q = p < n ? pos_of(g, p) : 0;  // neighbours outside the image read zero padding
             for (int c = 0; c < 9 * CH; ++c) {
                 const int tap = c / CH, c8 = c - tap * CH;
-                const int uu = u + tap % 3 - 1, dv = tap / 3 - 1;
+                const int64_t qs = q + (tap / 3 - 1) * g.Wp + (tap % 3 - 1);
                 uint4 val = make_uint4(0, 0, 0, 0);
-                if (p < n && uu >= 0 && uu < W && v + dv >= 0 && v + dv < H)
-                    val = *reinterpret_cast<const uint4 *>(X + ((size_t)(y + dv) * W + uu) * CIN + c8 * 8);
+                if (p < n) val = *reinterpret_cast<const uint4 *>(X + ((size_t)c8 * g.Ptot + (size_t)qs) * 8);
                 const bf16 *e = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -316,7 +392,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const bf16 *X, const 
 #pragma unroll
             for (int c8 = 0; c8 < COUT / 8; ++c8) {
                 uint4 val = make_uint4(0, 0, 0, 0);
-                if (p < n) val = *reinterpret_cast<const uint4 *>(dZ + (size_t)p * COUT + c8 * 8);
+                if (p < n) val = *reinterpret_cast<const uint4 *>(dZ + ((size_t)c8 * g.Ptot + (size_t)q) * 8);
                 const bf16 *e = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -397,29 +473,35 @@ __global__ void k_wgrad_reduce(const float *part, const float *partb, int G, int
     }
 }
 
-// dZprev = dX * (Zprev > 0) as bf16 (ReLU backward); channels padded
-__global__ void k_relu_back(const float *dX, const float *Zprev, int count, bf16 *dZ) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    dZ[i] = __float2bfloat16_rn(Zprev[i] > 0.f ? dX[i] : 0.f);
+// dZprev = dX * (Zprev > 0) as bf16 (ReLU backward) at every position of the
+// grid (zero where Zprev is: padding and guards); dX, Zprev fp32 with C values
+// per position, dZ channel-blocked
+__global__ void k_relu_back(const float *dX, const float *Zprev, int C, int64_t Ptot, bf16 *dZ) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ptot * C) return;
+    const int64_t q = i / C;
+    const int c = (int)(i - q * C);
+    dZ[((size_t)(c >> 3) * Ptot + (size_t)q) * 8 + (c & 7)] = __float2bfloat16_rn(Zprev[i] > 0.f ? dX[i] : 0.f);
 }
 
-// L1 loss on (d, a, b): out is H*W*16 fp32 (channels 0..2 used), target H*W*3;
-// writes d loss / d out (bf16, padded channels zero) and accumulates the loss
-__global__ void k_l1_loss(const float *out, const float *target, int n, float s0, float s1, float s2, float inv_n,
-                          bf16 *dout, float *loss) {
+// L1 loss on (d, a, b) over the n interior pixels: out holds 16 fp32 values
+// per grid position (channels 0..2 used), target 3 per pixel; writes d loss /
+// d out (bf16, two channel blocks, padded channels zero) and accumulates the loss
+__global__ void k_l1_loss(const float *out, const float *target, Geo g, int n, float s0, float s1, float s2,
+                          float inv_n, bf16 *dout, float *loss) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.f;
     if (p < n) {
         const float sc[3] = {s0, s1, s2};
+        const int64_t q = pos_of(g, p);
         for (int c = 0; c < 16; ++c) {
             float gval = 0.f;
             if (c < 3) {
-                const float diff = out[(size_t)p * 16 + c] - target[(size_t)p * 3 + c];
+                const float diff = out[(size_t)q * 16 + c] - target[(size_t)p * 3 + c];
                 l += sc[c] * fabsf(diff);
                 gval = (diff > 0.f ? sc[c] : (diff < 0.f ? -sc[c] : 0.f)) * inv_n;
             }
-            dout[(size_t)p * 16 + c] = __float2bfloat16_rn(gval);
+            dout[((size_t)(c >> 3) * g.Ptot + (size_t)q) * 8 + (c & 7)] = __float2bfloat16_rn(gval);
         }
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
@@ -428,7 +510,7 @@ __global__ void k_l1_loss(const float *out, const float *target, int n, float s0
 
 // Adam on the fp32 master weights of one layer (real channels only), then the
 // bf16 copies: forward Bt[o][k] and input-gradient Bf[c][k'] (flipped taps,
-// roles of channels swapped).
+// roles of channels swapped), both in the core-matrix order of cm_index.
 //   w: (3,3,Cin,Cout) real sizes, fp32;  gW: dW in the padded GEMM layout COUT x 9CIN
 __global__ void k_adam(float *w, float *m, float *v, const float *gW, int ci, int co, int CIN, int COUT, float lr,
                        float b1, float b2, float eps, float c1, float c2, bf16 *Bt, bf16 *Bf) {
@@ -442,8 +524,8 @@ __global__ void k_adam(float *w, float *m, float *v, const float *gW, int ci, in
     v[idx] = vv;
     const float wn = w[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
     w[idx] = wn;
-    Bt[(size_t)o * 9 * CIN + tap * CIN + c] = __float2bfloat16_rn(wn);
-    if (Bf) Bf[(size_t)c * 9 * COUT + (8 - tap) * COUT + o] = __float2bfloat16_rn(wn);
+    Bt[cm_index(o, tap * CIN + c, 9 * CIN)] = __float2bfloat16_rn(wn);
+    if (Bf) Bf[cm_index(c, (8 - tap) * COUT + o, 9 * COUT)] = __float2bfloat16_rn(wn);
 }
 
 __global__ void k_adam_bias(float *b, float *m, float *v, const float *g, int co, float lr, float b1, float b2,
@@ -462,29 +544,34 @@ __global__ void k_pack_weights(const float *w, int ci, int co, int CIN, int COUT
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 9 * ci * co) return;
     const int o = idx % co, c = (idx / co) % ci, tap = idx / (co * ci);
-    Bt[(size_t)o * 9 * CIN + tap * CIN + c] = __float2bfloat16_rn(w[idx]);
-    if (Bf) Bf[(size_t)c * 9 * COUT + (8 - tap) * COUT + o] = __float2bfloat16_rn(w[idx]);
+    Bt[cm_index(o, tap * CIN + c, 9 * CIN)] = __float2bfloat16_rn(w[idx]);
+    if (Bf) Bf[cm_index(c, (8 - tap) * COUT + o, 9 * COUT)] = __float2bfloat16_rn(w[idx]);
 }
 
-// quarter-resolution input: x (fp32, H4*W4*7: R,G,B of left, R,G,B of right /255,
-// disparity / dmax) -> bf16 padded to 16 channels
-__global__ void k_pack_input(const float *x, int n, bf16 *X) {
+// quarter-resolution input: x (fp32, 7 values per pixel: R,G,B of left, R,G,B
+// of right /255, disparity / dmax) of the n interior pixels -> bf16, two
+// channel blocks (channels 7..15 zero)
+__global__ void k_pack_input(const float *x, Geo g, int n, bf16 *X) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * 16) return;
     const int p = i / 16, c = i % 16;
-    X[i] = __float2bfloat16_rn(c < 7 ? x[(size_t)p * 7 + c] : 0.f);
+    const int64_t q = pos_of(g, p);
+    X[((size_t)(c >> 3) * g.Ptot + (size_t)q) * 8 + (c & 7)] = __float2bfloat16_rn(c < 7 ? x[(size_t)p * 7 + c] : 0.f);
 }
 
-// network output (pre-activation of the last layer, 16 padded channels) -> y (3 channels)
-__global__ void k_take3(const float *z, int n, float *y) {
+// network output (pre-activation of the last layer, 16 values per grid
+// position) -> y (3 channels per interior pixel)
+__global__ void k_take3(const float *z, Geo g, int n, float *y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * 3) return;
-    y[i] = z[(size_t)(i / 3) * 16 + i % 3];
+    y[i] = z[(size_t)pos_of(g, i / 3) * 16 + i % 3];
 }
 
+// shared memory of k_conv: the weights and CIN / 8 blocks of 128 + 2 G positions
 template <int CIN, int COUT>
-size_t conv_smem() {
-    return (size_t)2 * 9 * CIN * (kTileP + COUT);
+size_t conv_smem(const Geo &g) {
+    const size_t SA = ((size_t)(128 + 2 * g.G) * 16 + 127) & ~(size_t)127;
+    return (size_t)2 * 9 * CIN * COUT + (size_t)(CIN / 8) * SA;
 }
 constexpr int kWgParts = 148;  // most CTAs (partial sums) of one weight-gradient launch
 
@@ -494,27 +581,27 @@ size_t wgrad_smem() {
 }
 
 template <int CIN, int COUT>
-cudaError_t conv(const bf16 *X, int H, int W, int B, const bf16 *Bt, const float *bias, float *Z, bf16 *Y,
-                 int relu, cudaStream_t st) {
-    const size_t sm = conv_smem<CIN, COUT>();
+cudaError_t conv(const bf16 *X, const Geo &g, const bf16 *Bt, const float *bias, float *Z, bf16 *Y, int relu,
+                 cudaStream_t st) {
+    const size_t sm = conv_smem<CIN, COUT>(g);
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int nb = (H * W * B + kTileP - 1) / kTileP;
-    k_conv<CIN, COUT><<<nb, kConvThreads, sm, st>>>(X, H, W, B, Bt, bias, Z, Y, relu);
+    k_conv<CIN, COUT><<<(unsigned)g.tiles, kConvThreads, sm, st>>>(X, g, Bt, bias, Z, Y, relu);
     return cudaGetLastError();
 }
 
 // part: kWgParts * COUT * 9CIN floats, partb: kWgParts * COUT floats (scratch)
 template <int CIN, int COUT>
-cudaError_t wgrad(const bf16 *X, const bf16 *dZ, int H, int W, int B, float *dW, float *dB, float *part,
-                  float *partb, cudaStream_t st) {
+cudaError_t wgrad(const bf16 *X, const bf16 *dZ, const Geo &g, float *dW, float *dB, float *part, float *partb,
+                  cudaStream_t st) {
     const size_t sm = wgrad_smem<CIN, COUT>();
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int tiles = (H * W * B + kTileP - 1) / kTileP;
+    const int tiles = (g.H * g.W * g.B + kTileP - 1) / kTileP;
     const int per = (tiles + kWgParts - 1) / kWgParts;
     const int G = (tiles + per - 1) / per;
-    k_wgrad_tc<CIN, COUT><<<G, kConvThreads, sm, st>>>(X, dZ, H, W, B, per, part, partb);
+    k_wgrad_tc<CIN, COUT><<<G, kConvThreads, sm, st>>>(X, dZ, g, per, part, partb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int KK = COUT * 9 * CIN;
     k_wgrad_reduce<<<(KK + COUT + 255) / 256, 256, 0, st>>>(part, partb, G, KK, COUT, dW, dB);
@@ -532,14 +619,15 @@ struct lem_cnn {
     bf16 *Bt[kLayers] = {}, *Bf[kLayers] = {};    // forward / input-gradient GEMM layouts
     float *gW[kLayers] = {}, *gB[kLayers] = {};   // gradients (padded GEMM layout)
     float *wpart = nullptr, *wpartb = nullptr;    // per-CTA partials of the weight gradient
-    // activations of up to cap pixels (all images of a training step, stacked)
-    size_t cap = 0;
-    bf16 *act[kLayers + 1] = {};                  // layer inputs (bf16), act[0] = packed input
-    float *pre[kLayers] = {};                     // pre-activations (fp32)
-    bf16 *dz = nullptr;                           // d loss / d pre-activation (bf16, 32 ch)
-    float *dx = nullptr;                          // d loss / d layer input (fp32, 32 ch)
+    // activations on the zero-padded grid of the current geometry (all images
+    // of a training step), for up to cap grid positions
+    int64_t cap = 0;
+    int geoB = 0, geoH = 0, geoW = 0;             // geometry the buffers were last cleared for
+    bf16 *act[kLayers] = {};                      // layer inputs (bf16, channel-blocked), act[0] = packed input
+    float *pre[kLayers] = {};                     // pre-activations (fp32, Cout per position)
+    bf16 *dz = nullptr;                           // d loss / d pre-activation (bf16, 32 ch, channel-blocked)
+    float *dx = nullptr;                          // d loss / d layer input (fp32, 32 per position)
     float *loss = nullptr;
-    float *xin = nullptr, *tgt = nullptr;         // staging of an input / target
     int step = 0;
     std::string err;
 };
@@ -561,65 +649,71 @@ int cnn_fail(lem_cnn *net, cudaError_t e, const char *what) {
 
 size_t nweights(int l) { return (size_t)9 * kRealCin[l] * kRealCout[l]; }
 
-int ensure_capacity(lem_cnn *net, size_t npix) {
-    if (npix <= net->cap) return LEM_OK;
-    // pointers are cleared as they are freed, so a failed allocation below
-    // leaves nothing dangling for a later call or lem_cnn_destroy
-    auto drop = [](auto *&p) {
-        cudaFree(p);
-        p = nullptr;
-    };
-    net->cap = 0;
-    for (int l = 0; l <= kLayers; ++l) drop(net->act[l]);
-    for (int l = 0; l < kLayers; ++l) drop(net->pre[l]);
-    drop(net->dz);
-    drop(net->dx);
-    drop(net->xin);
-    drop(net->tgt);
-    for (int l = 0; l <= kLayers; ++l) {
-        const int c = l == 0 ? kCin[0] : kCout[l - 1];
-        CNN_CUDA(net, cudaMalloc(&net->act[l], sizeof(bf16) * npix * c));
+// Buffers for the grid of B images of H x W: allocated for at least its
+// positions, and cleared whenever the geometry changes, so that every padding
+// and guard position reads zero (the kernels write interior positions only).
+int ensure_geometry(lem_cnn *net, const Geo &g) {
+    if (g.Ptot > net->cap) {
+        // pointers are cleared as they are freed, so a failed allocation below
+        // leaves nothing dangling for a later call or lem_cnn_destroy
+        auto drop = [](auto *&p) {
+            cudaFree(p);
+            p = nullptr;
+        };
+        net->cap = 0;
+        net->geoB = net->geoH = net->geoW = 0;
+        for (int l = 0; l < kLayers; ++l) drop(net->act[l]);
+        for (int l = 0; l < kLayers; ++l) drop(net->pre[l]);
+        drop(net->dz);
+        drop(net->dx);
+        for (int l = 0; l < kLayers; ++l) CNN_CUDA(net, cudaMalloc(&net->act[l], sizeof(bf16) * g.Ptot * kCin[l]));
+        for (int l = 0; l < kLayers; ++l) CNN_CUDA(net, cudaMalloc(&net->pre[l], sizeof(float) * g.Ptot * kCout[l]));
+        CNN_CUDA(net, cudaMalloc(&net->dz, sizeof(bf16) * g.Ptot * 32));
+        CNN_CUDA(net, cudaMalloc(&net->dx, sizeof(float) * g.Ptot * 32));
+        net->cap = g.Ptot;
     }
-    for (int l = 0; l < kLayers; ++l) CNN_CUDA(net, cudaMalloc(&net->pre[l], sizeof(float) * npix * kCout[l]));
-    CNN_CUDA(net, cudaMalloc(&net->dz, sizeof(bf16) * npix * 32));
-    CNN_CUDA(net, cudaMalloc(&net->dx, sizeof(float) * npix * 32));
-    CNN_CUDA(net, cudaMalloc(&net->xin, sizeof(float) * npix * 7));
-    CNN_CUDA(net, cudaMalloc(&net->tgt, sizeof(float) * npix * 3));
-    net->cap = npix;
+    if (net->geoB != g.B || net->geoH != g.H || net->geoW != g.W) {
+        for (int l = 0; l < kLayers; ++l) {
+            CNN_CUDA(net, cudaMemsetAsync(net->act[l], 0, sizeof(bf16) * g.Ptot * kCin[l], net->st));
+            CNN_CUDA(net, cudaMemsetAsync(net->pre[l], 0, sizeof(float) * g.Ptot * kCout[l], net->st));
+        }
+        CNN_CUDA(net, cudaMemsetAsync(net->dz, 0, sizeof(bf16) * g.Ptot * 32, net->st));
+        CNN_CUDA(net, cudaMemsetAsync(net->dx, 0, sizeof(float) * g.Ptot * 32, net->st));
+        net->geoB = g.B;
+        net->geoH = g.H;
+        net->geoW = g.W;
+    }
     return LEM_OK;
 }
 
-cudaError_t forward(lem_cnn *net, int H4, int W4, int B) {
+cudaError_t forward(lem_cnn *net, const Geo &g) {
     cudaStream_t st = net->st;
-    cudaError_t e = conv<16, 32>(net->act[0], H4, W4, B, net->Bt[0], net->b[0], net->pre[0], net->act[1], 1, st);
+    cudaError_t e = conv<16, 32>(net->act[0], g, net->Bt[0], net->b[0], net->pre[0], net->act[1], 1, st);
     for (int l = 1; l < 5 && e == cudaSuccess; ++l)
-        e = conv<32, 32>(net->act[l], H4, W4, B, net->Bt[l], net->b[l], net->pre[l], net->act[l + 1], 1, st);
-    if (e == cudaSuccess) e = conv<32, 16>(net->act[5], H4, W4, B, net->Bt[5], net->b[5], net->pre[5], nullptr, 0, st);
+        e = conv<32, 32>(net->act[l], g, net->Bt[l], net->b[l], net->pre[l], net->act[l + 1], 1, st);
+    if (e == cudaSuccess) e = conv<32, 16>(net->act[5], g, net->Bt[5], net->b[5], net->pre[5], nullptr, 0, st);
     return e;
 }
 
-// backward of B stacked images from d loss / d output (in net->dz, 16
-// channels); accumulates into gW / gB
-cudaError_t backward(lem_cnn *net, int H4, int W4, int B) {
+// backward over the grid from d loss / d output (in net->dz, 16 channels);
+// accumulates into gW / gB
+cudaError_t backward(lem_cnn *net, const Geo &g) {
     cudaStream_t st = net->st;
-    const int n = H4 * W4 * B;
     cudaError_t e = cudaSuccess;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         // weight gradient of layer l: input act[l], output gradient dz
-        if (l == 5)
-            e = wgrad<32, 16>(net->act[5], net->dz, H4, W4, B, net->gW[5], net->gB[5], net->wpart, net->wpartb, st);
-        else if (l == 0)
-            e = wgrad<16, 32>(net->act[0], net->dz, H4, W4, B, net->gW[0], net->gB[0], net->wpart, net->wpartb, st);
-        else
-            e = wgrad<32, 32>(net->act[l], net->dz, H4, W4, B, net->gW[l], net->gB[l], net->wpart, net->wpartb, st);
+        if (l == 5) e = wgrad<32, 16>(net->act[5], net->dz, g, net->gW[5], net->gB[5], net->wpart, net->wpartb, st);
+        else if (l == 0) e = wgrad<16, 32>(net->act[0], net->dz, g, net->gW[0], net->gB[0], net->wpart, net->wpartb, st);
+        else e = wgrad<32, 32>(net->act[l], net->dz, g, net->gW[l], net->gB[l], net->wpart, net->wpartb, st);
         if (e != cudaSuccess || l == 0) break;
         // input gradient: conv of dz with the flipped, transposed weights
-        if (l == 5) e = conv<16, 32>(net->dz, H4, W4, B, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
-        else e = conv<32, 32>(net->dz, H4, W4, B, net->Bf[l], nullptr, net->dx, nullptr, 0, st);
+        if (l == 5) e = conv<16, 32>(net->dz, g, net->Bf[5], nullptr, net->dx, nullptr, 0, st);
+        else e = conv<32, 32>(net->dz, g, net->Bf[l], nullptr, net->dx, nullptr, 0, st);
         if (e != cudaSuccess) break;
-        // ReLU of layer l-1
-        const int cnt = n * kCout[l - 1];
-        k_relu_back<<<(cnt + 255) / 256, 256, 0, st>>>(net->dx, net->pre[l - 1], cnt, net->dz);
+        // ReLU of layer l-1, over every grid position (padding stays zero)
+        const int C = kCout[l - 1];
+        const int64_t cnt = g.Ptot * C;
+        k_relu_back<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(net->dx, net->pre[l - 1], C, g.Ptot, net->dz);
         e = cudaGetLastError();
     }
     return e;
@@ -727,14 +821,12 @@ int lem_cnn_destroy(lem_cnn *net) {
         cudaFree(net->Bt[l]);
         cudaFree(net->Bf[l]);
     }
-    for (int l = 0; l <= kLayers; ++l) cudaFree(net->act[l]);
+    for (int l = 0; l < kLayers; ++l) cudaFree(net->act[l]);
     cudaFree(net->dz);
     cudaFree(net->dx);
     cudaFree(net->loss);
     cudaFree(net->wpart);
     cudaFree(net->wpartb);
-    cudaFree(net->xin);
-    cudaFree(net->tgt);
     delete net;
     return LEM_OK;
 }
@@ -775,13 +867,15 @@ int lem_cnn_set_params(lem_cnn *net, const float *host) {
 
 int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
     if (!net || !x || !out || H4 < 1 || W4 < 1) return LEM_ERR_ARG;
+    const Geo g = make_geo(1, H4, W4);
+    if (conv_smem<32, 32>(g) > 227 * 1024 || g.Ptot * 32 > (int64_t)INT32_MAX) return LEM_ERR_ARG;
     const size_t n = (size_t)H4 * W4;
-    int rc = ensure_capacity(net, n);
+    int rc = ensure_geometry(net, g);
     if (rc != LEM_OK) return rc;
-    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, (int)n, net->act[0]);
+    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, g, (int)n, net->act[0]);
     CNN_CUDA(net, cudaGetLastError());
-    CNN_CUDA(net, forward(net, H4, W4, 1));
-    k_take3<<<(int)((n * 3 + 255) / 256), 256, 0, net->st>>>(net->pre[5], (int)n, out);
+    CNN_CUDA(net, forward(net, g));
+    k_take3<<<(int)((n * 3 + 255) / 256), 256, 0, net->st>>>(net->pre[5], g, (int)n, out);
     CNN_CUDA(net, cudaGetLastError());
     return LEM_OK;
 }
@@ -789,11 +883,13 @@ int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
 int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_images, int H4, int W4,
                       const float *scale, float *loss, float *grads) {
     if (!net || !x || !target || n_images < 1 || H4 < 1 || W4 < 1 || !scale) return LEM_ERR_ARG;
-    // all images go through each layer in one launch: the batch is stacked as
-    // one (n_images * H4) x W4 grid whose patches stop at each image's border
+    // all images go through each layer in one launch: the batch is one grid of
+    // n_images zero-padded images whose 3x3 neighbourhoods stop at each image's border
+    const Geo g = make_geo(n_images, H4, W4);
     const size_t n = (size_t)H4 * W4 * n_images;
-    if (n * 32 > (size_t)INT32_MAX) return LEM_ERR_ARG;
-    int rc = ensure_capacity(net, n);
+    if (conv_smem<32, 32>(g) > 227 * 1024 || g.Ptot * 32 > (int64_t)INT32_MAX || n * 16 > (size_t)INT32_MAX)
+        return LEM_ERR_ARG;
+    int rc = ensure_geometry(net, g);
     if (rc != LEM_OK) return rc;
     for (int l = 0; l < kLayers; ++l) {
         CNN_CUDA(net, cudaMemsetAsync(net->gW[l], 0, sizeof(float) * kCout[l] * 9 * kCin[l], net->st));
@@ -801,13 +897,13 @@ int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_i
     }
     CNN_CUDA(net, cudaMemsetAsync(net->loss, 0, sizeof(float), net->st));
     const float inv_n = 1.f / (float)n;
-    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, (int)n, net->act[0]);
+    k_pack_input<<<(int)((n * 16 + 255) / 256), 256, 0, net->st>>>(x, g, (int)n, net->act[0]);
     CNN_CUDA(net, cudaGetLastError());
-    CNN_CUDA(net, forward(net, H4, W4, n_images));
-    k_l1_loss<<<(int)((n + 255) / 256), 256, 0, net->st>>>(net->pre[5], target, (int)n, scale[0], scale[1], scale[2],
-                                                         inv_n, net->dz, net->loss);
+    CNN_CUDA(net, forward(net, g));
+    k_l1_loss<<<(int)((n + 255) / 256), 256, 0, net->st>>>(net->pre[5], target, g, (int)n, scale[0], scale[1],
+                                                         scale[2], inv_n, net->dz, net->loss);
     CNN_CUDA(net, cudaGetLastError());
-    CNN_CUDA(net, backward(net, H4, W4, n_images));
+    CNN_CUDA(net, backward(net, g));
     if (loss) CNN_CUDA(net, cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, net->st));
     if (grads) {
         // real-channel gradients in the (3,3,ci,co) + bias order of lem_cnn_get_params
