@@ -588,7 +588,7 @@ int64_t lem_cnn_num_params(void);
 int lem_cnn_get_params(lem_cnn *net, float *host);
 int lem_cnn_set_params(lem_cnn *net, const float *host);
 /* Forward pass: x DEVICE (H4*W4*7 floats), y DEVICE (H4*W4*3 floats).
- * Errors: LEM_ERR_ARG (also W4 > 1605: a convolution tile stages three rows of
+ * Errors: LEM_ERR_ARG (also W4 > 1597: a convolution tile stages three rows of
  * the padded grid in shared memory), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *y);
 /* Loss and gradients over n_images inputs x (DEVICE, n*H4*W4*7) with targets
@@ -600,7 +600,7 @@ int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *y);
  * n*(H4+2)*(W4+2) positions (1.25 KB each; grown on demand, cleared when the
  * shape changes, kept until lem_cnn_destroy).  Synchronises the stream.
  * Errors: LEM_ERR_ARG (also when the grid exceeds 2^31 / 32 positions or
- * W4 > 1605), LEM_ERR_OOM, LEM_ERR_CUDA. */
+ * W4 > 1597), LEM_ERR_OOM, LEM_ERR_CUDA. */
 int lem_cnn_gradients(lem_cnn *net, const float *x, const float *t, int n_images, int H4, int W4,
                       const float *scale, float *loss, float *grads);
 /* lem_cnn_gradients, then one Adam step (beta 0.9 / 0.999, eps 1e-8, rate lr). */

@@ -567,7 +567,10 @@ __global__ void k_take3(const float *z, Geo g, int n, float *y) {
     y[i] = z[(size_t)pos_of(g, i / 3) * 16 + i % 3];
 }
 
-// shared memory of k_conv: the weights and CIN / 8 blocks of 128 + 2 G positions
+// shared memory of k_conv: the weights and CIN / 8 blocks of 128 + 2 G positions;
+// at most 226 KB of the 227 KB a CTA may have, the rest for its static shared
+// variables (grids up to 1597 columns)
+constexpr size_t kConvSmemMax = 226 * 1024;
 template <int CIN, int COUT>
 size_t conv_smem(const Geo &g) {
     const size_t SA = ((size_t)(128 + 2 * g.G) * 16 + 127) & ~(size_t)127;
@@ -584,7 +587,7 @@ template <int CIN, int COUT>
 cudaError_t conv(const bf16 *X, const Geo &g, const bf16 *Bt, const float *bias, float *Z, bf16 *Y, int relu,
                  cudaStream_t st) {
     const size_t sm = conv_smem<CIN, COUT>(g);
-    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (sm > kConvSmemMax) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_conv<CIN, COUT><<<(unsigned)g.tiles, kConvThreads, sm, st>>>(X, g, Bt, bias, Z, Y, relu);
@@ -868,7 +871,7 @@ int lem_cnn_set_params(lem_cnn *net, const float *host) {
 int lem_cnn_forward(lem_cnn *net, const float *x, int H4, int W4, float *out) {
     if (!net || !x || !out || H4 < 1 || W4 < 1) return LEM_ERR_ARG;
     const Geo g = make_geo(1, H4, W4);
-    if (conv_smem<32, 32>(g) > 227 * 1024 || g.Ptot * 32 > (int64_t)INT32_MAX) return LEM_ERR_ARG;
+    if (conv_smem<32, 32>(g) > kConvSmemMax || g.Ptot * 32 > (int64_t)INT32_MAX) return LEM_ERR_ARG;
     const size_t n = (size_t)H4 * W4;
     int rc = ensure_geometry(net, g);
     if (rc != LEM_OK) return rc;
@@ -887,7 +890,7 @@ int lem_cnn_gradients(lem_cnn *net, const float *x, const float *target, int n_i
     // n_images zero-padded images whose 3x3 neighbourhoods stop at each image's border
     const Geo g = make_geo(n_images, H4, W4);
     const size_t n = (size_t)H4 * W4 * n_images;
-    if (conv_smem<32, 32>(g) > 227 * 1024 || g.Ptot * 32 > (int64_t)INT32_MAX || n * 16 > (size_t)INT32_MAX)
+    if (conv_smem<32, 32>(g) > kConvSmemMax || g.Ptot * 32 > (int64_t)INT32_MAX || n * 16 > (size_t)INT32_MAX)
         return LEM_ERR_ARG;
     int rc = ensure_geometry(net, g);
     if (rc != LEM_OK) return rc;

@@ -99,6 +99,30 @@ def test_forward_matches_oracle(torch_cuda, H4, W4):
     assert np.abs(y - ref).max() <= 4 * FWD_TOL * np.abs(ref).max()
 
 
+def test_forward_across_grid_shapes_and_at_the_widest_grid(torch_cuda):
+    """The activations live on a zero-padded grid that is cleared when its shape changes:
+    forward passes at alternating shapes (a wide one first, so that stale values would sit in
+    the padding of the narrow ones) each match the bfloat16-storage model, up to the widest
+    grid a convolution tile's shared memory holds (W4 = 1597); one column more is refused
+    before any GPU work."""
+    torch = torch_cuda
+    from paper_1603_08328_gb300.lem import LemError, ProposalNet
+    params = _params(4)
+    net = ProposalNet(seed=0)
+    net.set_params(_flat(params))
+    rng = np.random.default_rng(44)
+    for H4, W4 in [(3, 1597), (9, 7), (5, 130), (9, 7), (2, 1597)]:
+        x = rng.uniform(0.0, 1.0, size=(H4, W4, 7)).astype(np.float32)
+        y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        net.sync_check()
+        emu, _, _ = cnn.forward(_f64(params), x.astype(np.float64), store="bf16")
+        e = _nerr(y, emu)
+        print(f"forward {H4}x{W4}: normalised error {e:.2e} (bf16 storage)")
+        assert e <= EMU_TOL
+    with pytest.raises(LemError):
+        net.forward(torch.zeros((2, 1598, 7), dtype=torch.float32, device="cuda"))
+
+
 def test_gradients_match_oracle(torch_cuda):
     """Loss and every layer's weight and bias gradient over two images against the FP64
     backward pass.  Targets are kept at least 0.3 away from the outputs so that the L1 sign
