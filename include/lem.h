@@ -233,9 +233,9 @@ int lem_v3_params(lem_params *p, int width);
  * (Eq. gf), the contrast weights lambda*max(w_pq, eps) of the 4 forward
  * neighbours (Eq. smweight), draws the random initial labels (Sec. 3.4:
  * random disparity in [disp_min, disp_max] and random unit normal) and fills
- * the cost cache phi_p(f_p).  left/right: same height and width, any layout
- * and element type lem_image describes (converted to packed 8-bit RGB on the
- * device first).
+ * the cost cache phi_p(f_p).  left/right: same height and width, each at
+ * least one regression window (2 gf_radius + 1 pixels), any layout and element
+ * type lem_image describes (converted to packed 8-bit RGB on the device first).
  * Errors: LEM_ERR_ARG (null pointers, bad parameters, an unknown dtype, fewer
  * than 3 or more than 16 channels, a pointer or stride that is not a multiple
  * of the element size), LEM_ERR_SHAPE (sizes, strides), LEM_ERR_OOM,

@@ -145,6 +145,9 @@ def test_image_layout_checks_without_touching_the_gpu(L):
     assert "stride_row" in L.lem_last_error(None)
     assert rc(L.lem_image(base, 32, 40, 640, 0, 4, 16, f32), L.lem_default_params(gf_radius=2, dataflow=2)) \
         == L.LEM_ERR_ARG
+    # one regression window (2 r' + 1 = 5 pixels) is the smallest image side
+    assert rc(L.lem_image(base, 4, 40, 640, 0, 4, 16, f32)) == L.LEM_ERR_SHAPE
+    assert rc(L.lem_image(base, 32, 4, 640, 0, 4, 16, f32)) == L.LEM_ERR_SHAPE
     assert not h.value
 
 
