@@ -208,6 +208,8 @@ typedef struct {
                                    neighbour after the wait limit (about 2 s) and moved anyway;
                                    nonzero means the labels are not valid (reported by
                                    lem_expand_iteration as LEM_ERR_CUDA when stats are read) */
+    double ms;             /* lem_expand_iteration: GPU time of the iterations of this call (CUDA
+                              events on the handle's stream around them); 0 from other calls  */
 } lem_stats;
 
 typedef struct lem_handle lem_handle;

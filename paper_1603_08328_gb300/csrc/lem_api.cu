@@ -71,6 +71,7 @@ struct lem_handle {
     int kn_last = 0;   // events of the last iteration issued (direct or captured)
     int kn_graph = 0;  // events of the captured iteration
     bool capturing = false;
+    cudaEvent_t it_ev[2] = {nullptr, nullptr};  // around the iterations of a lem_expand_iteration call
     lem::Counters last{};  // device counters at the previous stats read
     std::string err;
 };
@@ -341,6 +342,8 @@ void free_handle(lem_handle *h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
     for (cudaEvent_t e : h->kev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->it_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -953,6 +956,11 @@ int lem_expand_group(lem_handle *h, int iter, int level, int group, lem_stats *s
 int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
     if (!h) return fail(nullptr, LEM_ERR_ARG, "handle is NULL");
     if (n_iters < 0) return fail(h, LEM_ERR_ARG, "n_iters < 0");
+    if (stats) {
+        for (cudaEvent_t &e : h->it_ev)
+            if (!e) LEM_CUDA(h, cudaEventCreate(&e));
+        LEM_CUDA(h, cudaEventRecord(h->it_ev[0], h->st));
+    }
     int done = 0;
     // cooperative launches of the multi-CTA levels run directly, never as a graph
     const bool graph_ok = !(h->grid_level[0] || h->grid_level[1] || h->grid_level[2]);
@@ -984,10 +992,14 @@ int lem_expand_iteration(lem_handle *h, int n_iters, lem_stats *stats) {
         ++h->iter;
     }
     if (stats) {
+        LEM_CUDA(h, cudaEventRecord(h->it_ev[1], h->st));
         long long eq = 0;
         int rc = run_energy(h, &eq);
         if (rc != LEM_OK) return rc;
         if ((rc = read_counters(h, stats)) != LEM_OK) return rc;
+        float ms = 0.f;
+        LEM_CUDA(h, cudaEventElapsedTime(&ms, h->it_ev[0], h->it_ev[1]));
+        stats->ms = ms;
         stats->energy_q = eq;
         stats->energy = (double)eq / h->p.quant_scale;
         if (stats->dep_waits_given_up > 0)

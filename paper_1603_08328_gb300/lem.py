@@ -77,7 +77,8 @@ class lem_stats(C.Structure):
     _fields_ = [("energy_q", C.c_int64), ("energy", C.c_double), ("evals", C.c_int64), ("accepted", C.c_int64),
                 ("maxflow_limit", C.c_int64), ("fp64_inverses", C.c_int32), ("iterations", C.c_int32),
                 ("pr_rounds", C.c_int64), ("pr_global_relabels", C.c_int64), ("pr_bfs_levels", C.c_int64),
-                ("accepted_by_kind", C.c_int64 * 4), ("dep_waits_given_up", C.c_int64)]
+                ("accepted_by_kind", C.c_int64 * 4), ("dep_waits_given_up", C.c_int64),
+                ("ms", C.c_double)]
 
 
 _lib = None

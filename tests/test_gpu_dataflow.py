@@ -89,13 +89,16 @@ def test_dataflow_headline_1500x1000(torch_cuda):
 
 
 def test_dataflow_level_launches_are_timed_per_level(torch_cuda):
-    """With kernel timing on, a dataflow iteration records one expansion launch per level."""
+    """With kernel timing on, a dataflow iteration records one expansion launch per level, and
+    the call's stats carry the GPU time of its iterations."""
     from paper_1603_08328_gb300.lem import Stereo
     pair = workload_pair("middlebury_450x375", 5)
     g = Stereo(pair["left"], pair["right"], disp_max=60.0, seed=2, dataflow=1, work_queue=1)
     g.set_kernel_timing(True)
-    g.iterate(2)
+    st = g.iterate(2)
     kt = g.kernel_times()
     for lvl in range(3):
         ms, launches = kt[(lvl, "k_expand_group")]
         assert launches == 1 and ms > 0.0
+    # lem_stats.ms: the GPU time of both iterations of the call, at least the last one's kernels
+    assert st.ms >= sum(kt[(lvl, "k_expand_group")][0] for lvl in range(3)) > 0.0
