@@ -132,9 +132,6 @@ __device__ __forceinline__ float dd_eval(const DDCoef &d, float u, float v) {
     lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fmul_rn(d.al, u), __fmul_rn(d.bl, v)), d.cl));
     return __fadd_rn(s2, lo);
 }
-__device__ __forceinline__ float disp_diff(const float4 &f1, const float4 &f2, float u, float v) {
-    return dd_eval(dd_coef(f1, f2), u, v);
-}
 
 // Q(wl min(pb, tau)) for psi-bar pb = |D1| + |D2| (Eq. smooth, Eq. smooth_phi),
 // Q(x) = rne(S x)
@@ -1069,35 +1066,6 @@ __device__ __forceinline__ T warp_at(const T (&p)[NC], int m) {
         if (j == blk) v = t;
     }
     return m < 0 ? (T)0 : v;
-}
-
-// raw cost of left pixel (x, y) for the plane whose row warp offset is (Ib, Fb)
-// (row_offset), also returning the left pixel
-__device__ __forceinline__ float raw_cost(const DevPlanes &P, const KParams &kp, size_t rowb, int x, int Rx0,
-                                          float sh, float sl, int Ib, float Fb, float oma, float4 &l) {
-    const int W = P.W, fmt = P.fmt;
-    l = load_px(P.L, rowb + x, fmt);
-    const float dx = (float)(x - Rx0);
-    const float g = __fmaf_rn(sh, dx, __fmaf_rn(sl, dx, Fb));
-    const float gf = floorf(g);
-    float t = g - gf;
-    int i0 = Ib + (int)gf;
-    if (i0 < 0) {
-        i0 = 0;
-        t = 0.f;
-    } else if (i0 >= W - 1) {
-        i0 = W - 1;
-        t = 0.f;
-    }
-    const int i1 = min(i0 + 1, W - 1);
-    const float4 r0 = load_px(P.R, rowb + i0, fmt), r1 = load_px(P.R, rowb + i1, fmt);
-    const float rr = fmaf(t, r1.x - r0.x, r0.x);
-    const float rg = fmaf(t, r1.y - r0.y, r0.y);
-    const float rb = fmaf(t, r1.z - r0.z, r0.z);
-    const float rd = fmaf(t, r1.w - r0.w, r0.w);
-    const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
-    const float gd = fabsf(l.w - rd);
-    return rho_mix(col, gd, kp, oma);
 }
 
 __device__ __forceinline__ int yEndOf(int Ry0, int Rh, int r) { return Ry0 + Rh + 2 * r; }
