@@ -552,40 +552,51 @@ __global__ void k_init_labels(int H, int W, unsigned long long seed, double dmin
 // A3 + A4: data term of one label over one region, through M
 // ---------------------------------------------------------------------------
 // sum of count values base[0], base[stride], ... with four independent partial sums
-__device__ __forceinline__ float strided_sum(const float *base, int stride, int count) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+// The window sums of the guided filter keep four channels of a pixel together
+// (one float4 per pixel), so one 16-byte shared load feeds four sums; every
+// channel is summed exactly as a scalar sum would be.
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+// sum of `count` values at base, base + stride, ... in four interleaved partial
+// sums, ((a0 + a1) + (a2 + a3)) per channel
+__device__ __forceinline__ float4 strided_sum4(const float4 *base, int stride, int count) {
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     int i = 0;
     for (; i + 4 <= count; i += 4) {
-        a0 += base[i * stride];
-        a1 += base[(i + 1) * stride];
-        a2 += base[(i + 2) * stride];
-        a3 += base[(i + 3) * stride];
+        a0 = add4(a0, base[i * stride]);
+        a1 = add4(a1, base[(i + 1) * stride]);
+        a2 = add4(a2, base[(i + 2) * stride]);
+        a3 = add4(a3, base[(i + 3) * stride]);
     }
-    for (; i < count; ++i) a0 += base[i * stride];
-    return (a0 + a1) + (a2 + a3);
+    for (; i < count; ++i) a0 = add4(a0, base[i * stride]);
+    return add4(add4(a0, a1), add4(a2, a3));
 }
 __device__ __forceinline__ int ring_next(int s, int RS) { return s + 1 == RS ? 0 : s + 1; }
 // the same over `count` consecutive rows of a ring of RS rows (row pitch rs) from
-// slot s0, with the same association as strided_sum over those rows in order
+// slot s0, with the same association as strided_sum4 over those rows in order
 // (wherever the ring wraps)
-__device__ __forceinline__ float ring_sum(const float *base, int rs, int RS, int s0, int count) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+__device__ __forceinline__ float4 ring_sum4(const float4 *base, int rs, int RS, int s0, int count) {
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     int i = 0, s = s0;
     for (; i + 4 <= count; i += 4) {
-        a0 += base[s * rs];
+        a0 = add4(a0, base[s * rs]);
         s = ring_next(s, RS);
-        a1 += base[s * rs];
+        a1 = add4(a1, base[s * rs]);
         s = ring_next(s, RS);
-        a2 += base[s * rs];
+        a2 = add4(a2, base[s * rs]);
         s = ring_next(s, RS);
-        a3 += base[s * rs];
+        a3 = add4(a3, base[s * rs]);
         s = ring_next(s, RS);
     }
     for (; i < count; ++i) {
-        a0 += base[s * rs];
+        a0 = add4(a0, base[s * rs]);
         s = ring_next(s, RS);
     }
-    return (a0 + a1) + (a2 + a3);
+    return add4(add4(a0, a1), add4(a2, a3));
 }
 
 // Thread layout of one pipeline stage over an R x C item grid: threads form
@@ -638,7 +649,8 @@ __device__ __forceinline__ void row_offset(float sh, float sl, float lb, float l
 // which keeps the covariance differences small in flat areas.
 //
 // Strip pipeline: M rows enter a ring of T + 2r' rows of the four channels
-// (rho, (I - c) rho); every T rows of K (R grown by r') get vertical then
+// (rho, (I - c) rho), kept together per pixel as one float4 so that a 16-byte
+// shared load serves the four window sums; every T rows of K (R grown by r') get vertical then
 // horizontal window sums and their a_k, b_k, which enter a second ring of
 // T + 2r' + 4 rows; every T rows of R get the window means of a_k, b_k and phi.
 // Every sliding window sum restarts at rows Ky0 + 4m, Ry0 + 4m and columns
@@ -654,10 +666,11 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
     const int Ky0 = max(0, Ry0 - r), Ky1 = min(H, Ry0 + Rh + r);
     const int Mw = Mx1 - Mx0, Kw = Kx1 - Kx0;
     const int RS = T + 2 * r, RSA = RS + 4;
-    float *Xr = sm;                          // [RS][4][Mw]  raw-cost channels of M rows (ring)
-    float *Vb = Xr + (size_t)RS * 4 * Mw;    // [T][4][Mw]   vertical sums (also [T][4][Kw])
-    float *Bb = Vb + (size_t)T * 4 * Mw;     // [T][4][Kw]   box sums      (also [T][4][Rw])
-    float *ABr = Bb + (size_t)T * 4 * Kw;    // [RSA][4][Kw] a_k, b_k of K rows (ring)
+    // four channels per pixel in one float4 (16 bytes)
+    float4 *Xr = reinterpret_cast<float4 *>(sm);  // [RS][Mw]  (rho, (I - c) rho) of M rows (ring)
+    float4 *Vb = Xr + (size_t)RS * Mw;            // [T][Mw]   vertical sums (also [T][Kw])
+    float4 *Bb = Vb + (size_t)T * Mw;             // [T][Kw]   box sums      (also [T][Rw])
+    float4 *ABr = Bb + (size_t)T * Kw;            // [RSA][Kw] (a_k, b_k) of K rows (ring)
 
     const int fmt = P.fmt;
     const float4 cen4 = load_px(P.L, (size_t)(Ry0 + Rh / 2) * W + (Rx0 + Rw / 2), fmt);
@@ -670,9 +683,9 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
     const float oma = 1.0f - kp.alpha_grad;
 
     // stage layouts (fixed for the call)
-    const Grid2 gM(Mw), gK(Kw), gR(Rw), gV(4 * Mw), gV2(4 * Kw);
+    const Grid2 gM(Mw), gK(Kw), gR(Rw), gV(Mw), gV2(Kw);
     const int nchK = (Kw + 7) >> 3, nchR = (Rw + 3) >> 2;
-    const Grid2 gH(4 * nchK), gH2(4 * nchR);
+    const Grid2 gH(nchK), gH2(nchR);
 
     int mNext = My0, kNext = Ky0;
     int mSlot = 0;  // ring slot of row mNext in Xr
@@ -697,7 +710,7 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                         float Fb;
                         row_offset(sh, sl, lb, lc, Rx0, y, Ib, Fb);
                         const size_t rowb = (size_t)y * W;
-                        float *o = Xr + (size_t)slot * 4 * Mw;
+                        float4 *o = Xr + (size_t)slot * Mw;
                         for (int xc = gM.tc; xc < Mw; xc += gM.cpr) {
                             const int x = Mx0 + xc;
                             const float4 l = load_px(P.L, rowb + x, fmt);
@@ -722,10 +735,9 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                             const float col = fabsf(l.x - rr) + fabsf(l.y - rg) + fabsf(l.z - rb);
                             const float gd = fabsf(l.w - rd);
                             const float rho = rho_mix(col, gd, kp, oma);
-                            o[xc] = rho;
-                            o[Mw + xc] = __fmul_rn(__fmaf_rn(l.x, inv255, -cr), rho);
-                            o[2 * Mw + xc] = __fmul_rn(__fmaf_rn(l.y, inv255, -cg), rho);
-                            o[3 * Mw + xc] = __fmul_rn(__fmaf_rn(l.z, inv255, -cb), rho);
+                            o[xc] = make_float4(rho, __fmul_rn(__fmaf_rn(l.x, inv255, -cr), rho),
+                                                __fmul_rn(__fmaf_rn(l.y, inv255, -cg), rho),
+                                                __fmul_rn(__fmaf_rn(l.z, inv255, -cb), rho));
                         }
                     }
                 }
@@ -735,32 +747,32 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                 __syncthreads();
             }
             // vertical window sums of the 4 channels for K rows [k0, k1): item =
-            // (channel x M column) by group of 4 consecutive output rows
+            // M column by group of 4 consecutive output rows
             {
                 const int ng = (k1 - k0 + 3) >> 2;
-                const int rs = 4 * Mw;
+                const int rs = Mw;
                 if (gV.tr < gV.rpp) {
-                    for (int cc = gV.tc; cc < 4 * Mw; cc += gV.cpr) {
-                        const float *X = Xr + cc;  // cc = ch * Mw + col
-                        float *V = Vb + cc;
+                    for (int cc = gV.tc; cc < Mw; cc += gV.cpr) {
+                        const float4 *X = Xr + cc;
+                        float4 *V = Vb + cc;
                         for (int grp = gV.tr; grp < ng; grp += gV.rpp) {
                             const int ky0 = k0 + 4 * grp, ky1 = min(k1, ky0 + 4);
                             const int ylo = max(0, ky0 - r), yhi = min(H - 1, ky0 + r);
                             // slot of row ylo: rows mNext - RS .. mNext - 1 are in the ring
                             int sIn = mSlot - (mNext - ylo);
                             if (sIn < 0) sIn += RS;
-                            float sm = ring_sum(X, rs, RS, sIn, yhi - ylo + 1);
+                            float4 sm = ring_sum4(X, rs, RS, sIn, yhi - ylo + 1);
                             V[(ky0 - k0) * rs] = sm;
                             int sA = sIn + (yhi - ylo + 1);  // slot of row yhi + 1
                             if (sA >= RS) sA -= RS;
                             int sO = sIn;                    // slot of row ylo
                             for (int ky = ky0 + 1; ky < ky1; ++ky) {
                                 if (ky + r <= H - 1) {
-                                    sm += X[sA * rs];
+                                    sm = add4(sm, X[sA * rs]);
                                     sA = ring_next(sA, RS);
                                 }
                                 if (ky - r - 1 >= 0) {
-                                    sm -= X[sO * rs];
+                                    sm = sub4(sm, X[sO * rs]);
                                     sO = ring_next(sO, RS);
                                 }
                                 V[(ky - k0) * rs] = sm;
@@ -770,20 +782,19 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                 }
             }
             __syncthreads();
-            // horizontal window sums at K columns, 8 outputs per item
+            // horizontal window sums at K columns, 8 outputs (of 4 channels) per item
             if (gH.tr < gH.rpp) {
-                for (int cc = gH.tc; cc < 4 * nchK; cc += gH.cpr) {
-                    const int ch = cc / nchK, chunk = cc - ch * nchK;
+                for (int chunk = gH.tc; chunk < nchK; chunk += gH.cpr) {
                     const int kx0 = Kx0 + chunk * 8, kx1 = min(Kx1, kx0 + 8);
                     const int xlo = max(0, kx0 - r), xhi = min(W - 1, kx0 + r);
                     for (int row = gH.tr; row < k1 - k0; row += gH.rpp) {
-                        const float *V = Vb + row * 4 * Mw + ch * Mw - Mx0;
-                        float *B = Bb + row * 4 * Kw + ch * Kw - Kx0;
-                        float sm = strided_sum(V + xlo, 1, xhi - xlo + 1);
+                        const float4 *V = Vb + row * Mw - Mx0;
+                        float4 *B = Bb + row * Kw - Kx0;
+                        float4 sm = strided_sum4(V + xlo, 1, xhi - xlo + 1);
                         B[kx0] = sm;
                         for (int kx = kx0 + 1; kx < kx1; ++kx) {
-                            if (kx + r <= W - 1) sm += V[kx + r];
-                            if (kx - r - 1 >= 0) sm -= V[kx - r - 1];
+                            if (kx + r <= W - 1) sm = add4(sm, V[kx + r]);
+                            if (kx - r - 1 >= 0) sm = sub4(sm, V[kx - r - 1]);
                             B[kx] = sm;
                         }
                     }
@@ -797,27 +808,25 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                     const int ny = min(H - 1, ky + r) - max(0, ky - r) + 1;
                     int slot = kSlot + row;
                     if (slot >= RSA) slot -= RSA;
-                    float *A = ABr + slot * 4 * Kw;
-                    const float *B = Bb + row * 4 * Kw;
+                    float4 *A = ABr + slot * Kw;
+                    const float4 *B = Bb + row * Kw;
                     const float4 *G = P.gst + 3 * ((size_t)ky * W + Kx0);
                     for (int col = gK.tc; col < Kw; col += gK.cpr) {
                         const int kx = Kx0 + col;
                         const float n = (float)((min(W - 1, kx + r) - max(0, kx - r) + 1) * ny);
                         const float inv = 1.0f / n;
-                        const float mr = B[col] * inv;
+                        const float4 bs = B[col];
+                        const float mr = bs.x * inv;
                         const float4 g0 = G[3 * col], g1 = G[3 * col + 1], g2 = G[3 * col + 2];
                         const float u0 = g0.x - cr, u1 = g0.y - cg, u2 = g0.z - cb;
-                        const float v0 = B[Kw + col] * inv - u0 * mr;
-                        const float v1 = B[2 * Kw + col] * inv - u1 * mr;
-                        const float v2 = B[3 * Kw + col] * inv - u2 * mr;
+                        const float v0 = bs.y * inv - u0 * mr;
+                        const float v1 = bs.z * inv - u1 * mr;
+                        const float v2 = bs.w * inv - u2 * mr;
                         const float a0 = g0.w * v0 + g1.x * v1 + g1.y * v2;
                         const float a1 = g1.x * v0 + g1.z * v1 + g1.w * v2;
                         const float a2 = g1.y * v0 + g1.w * v1 + g2.x * v2;
                         const float bk = mr - (a0 * u0 + a1 * u1 + a2 * u2);
-                        A[col] = a0;
-                        A[Kw + col] = a1;
-                        A[2 * Kw + col] = a2;
-                        A[3 * Kw + col] = bk;
+                        A[col] = make_float4(a0, a1, a2, bk);
                     }
                 }
             }
@@ -829,28 +838,28 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
         // window means of a_k, b_k at p: vertical sums over K rows, every K column
         {
             const int ng = (p1 - p0 + 3) >> 2;
-            const int rs = 4 * Kw;
+            const int rs = Kw;
             if (gV2.tr < gV2.rpp) {
-                for (int cc = gV2.tc; cc < 4 * Kw; cc += gV2.cpr) {
-                    const float *A = ABr + cc;
-                    float *V = Vb + cc;
+                for (int cc = gV2.tc; cc < Kw; cc += gV2.cpr) {
+                    const float4 *A = ABr + cc;
+                    float4 *V = Vb + cc;
                     for (int grp = gV2.tr; grp < ng; grp += gV2.rpp) {
                         const int py0 = p0 + 4 * grp, py1 = min(p1, py0 + 4);
                         const int ylo = max(0, py0 - r), yhi = min(H - 1, py0 + r);
                         int sIn = kSlot - (kNext - ylo);
                         if (sIn < 0) sIn += RSA;
-                        float sm = ring_sum(A, rs, RSA, sIn, yhi - ylo + 1);
+                        float4 sm = ring_sum4(A, rs, RSA, sIn, yhi - ylo + 1);
                         V[(py0 - p0) * rs] = sm;
                         int sA = sIn + (yhi - ylo + 1);
                         if (sA >= RSA) sA -= RSA;
                         int sO = sIn;
                         for (int py = py0 + 1; py < py1; ++py) {
                             if (py + r <= H - 1) {
-                                sm += A[sA * rs];
+                                sm = add4(sm, A[sA * rs]);
                                 sA = ring_next(sA, RSA);
                             }
                             if (py - r - 1 >= 0) {
-                                sm -= A[sO * rs];
+                                sm = sub4(sm, A[sO * rs]);
                                 sO = ring_next(sO, RSA);
                             }
                             V[(py - p0) * rs] = sm;
@@ -861,18 +870,17 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
         }
         __syncthreads();
         if (gH2.tr < gH2.rpp) {
-            for (int cc = gH2.tc; cc < 4 * nchR; cc += gH2.cpr) {
-                const int ch = cc / nchR, chunk = cc - ch * nchR;
+            for (int chunk = gH2.tc; chunk < nchR; chunk += gH2.cpr) {
                 const int px0 = Rx0 + chunk * 4, px1 = min(Rx0 + Rw, px0 + 4);
                 const int xlo = max(0, px0 - r), xhi = min(W - 1, px0 + r);
                 for (int row = gH2.tr; row < p1 - p0; row += gH2.rpp) {
-                    const float *V = Vb + row * 4 * Kw + ch * Kw - Kx0;
-                    float *B = Bb + row * 4 * Rw + ch * Rw - Rx0;
-                    float sm = strided_sum(V + xlo, 1, xhi - xlo + 1);
+                    const float4 *V = Vb + row * Kw - Kx0;
+                    float4 *B = Bb + row * Rw - Rx0;
+                    float4 sm = strided_sum4(V + xlo, 1, xhi - xlo + 1);
                     B[px0] = sm;
                     for (int px = px0 + 1; px < px1; ++px) {
-                        if (px + r <= W - 1) sm += V[px + r];
-                        if (px - r - 1 >= 0) sm -= V[px - r - 1];
+                        if (px + r <= W - 1) sm = add4(sm, V[px + r]);
+                        if (px - r - 1 >= 0) sm = sub4(sm, V[px - r - 1]);
                         B[px] = sm;
                     }
                 }
@@ -883,7 +891,7 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
             for (int row = gR.tr; row < p1 - p0; row += gR.rpp) {
                 const int py = p0 + row;
                 const int ny = min(H - 1, py + r) - max(0, py - r) + 1;
-                const float *B = Bb + row * 4 * Rw;
+                const float4 *B = Bb + row * Rw;
                 const size_t rowb = (size_t)py * W;
                 for (int col = gR.tc; col < Rw; col += gR.cpr) {
                     const int px = Rx0 + col;
@@ -891,9 +899,8 @@ __device__ void region_unary_gf(const DevPlanes &P, const KParams &kp, int Rx0, 
                     const float4 l = load_px(P.L, rowb + px, fmt);
                     const float gu = __fmaf_rn(l.x, inv255, -cr), gv = __fmaf_rn(l.y, inv255, -cg);
                     const float gw = __fmaf_rn(l.z, inv255, -cb);
-                    const float phi =
-                        __fmaf_rn(B[col], gu, __fmaf_rn(B[Rw + col], gv, __fmaf_rn(B[2 * Rw + col], gw, B[3 * Rw + col]))) /
-                        n;
+                    const float4 b4 = B[col];
+                    const float phi = __fmaf_rn(b4.x, gu, __fmaf_rn(b4.y, gv, __fmaf_rn(b4.z, gw, b4.w))) / n;
                     out[(size_t)row * pitch + (p0 - Ry0) * (size_t)pitch + col] = phi;
                 }
             }
