@@ -1552,21 +1552,19 @@ __device__ void clamp_terminals(int n, int w, int h, const int *res, int *v) {
     }
 }
 
-// Global relabel of a region of at most 32 x 32 nodes by one warp (all 32
-// lanes of warp 0 call it): lane y keeps row y's residual bitplanes and BFS
-// words in registers and a BFS level moves frontier rows between lanes with
-// shuffles, so no level needs a CTA barrier.  Same result as global_relabel:
-// exact distances to the sink in hh (kInf where the sink cannot be reached);
-// returns whether a node with excess can reach it.
-__device__ __noinline__ bool warp_relabel(int n, int w, int h, const int *res, const int *v, uint16_t *hh,
-                                          int *levels) {
-    const int lane = threadIdx.x & 31;
+// Global relabel of a region of at most 32 x 32 nodes (called by every thread of
+// the CTA): the warps build the residual bitplanes and the BFS seeds one row each
+// (lane = column) into shared memory; warp 0 then keeps row y's planes and BFS
+// words in lane y and moves frontier rows between lanes with shuffles, so no BFS
+// level needs a CTA barrier; every thread then checks its nodes for excess that
+// can reach the sink.  Same result as global_relabel: exact distances to the sink
+// in hh (kInf where the sink cannot be reached).
+//   bits: 9 h words (8 planes and the seeds, row-indexed)
+__device__ __noinline__ bool small_relabel(int n, int w, int h, const int *res, const int *v, uint16_t *hh,
+                                           uint32_t *bits, int *levels) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const uint32_t full = 0xffffffffu;
-    const uint32_t rowmask = w >= 32 ? full : ((1u << w) - 1u);
-    uint32_t M[8], F = 0u, VIS = 0u;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) M[k] = 0u;
-    for (int y = 0; y < h; ++y) {
+    for (int y = warp; y < h; y += nwarp) {
         const bool in = lane < w;
         const int i = y * w + lane;
 #pragma unroll
@@ -1574,47 +1572,52 @@ __device__ __noinline__ bool warp_relabel(int n, int w, int h, const int *res, c
             bool p = false;
             if (in) p = res[k * n + i] > 0;
             const uint32_t m = __ballot_sync(full, p);
-            if (lane == y) M[k] = m;
+            if (lane == 0) bits[k * h + y] = m;
         }
         bool seed = false;
         if (in) seed = v[i] < 0;
         const uint32_t m = __ballot_sync(full, seed);
-        if (lane == y) {
-            F = m;
-            VIS = m;
-        }
+        if (lane == 0) bits[8 * h + y] = m;
         if (in) hh[i] = seed ? 1 : kInf;
     }
-    __syncwarp();
-    int level = 1;
-    for (;;) {
-        const uint32_t up = __shfl_up_sync(full, F, 1), dn = __shfl_down_sync(full, F, 1);
-        const uint32_t rows[3] = {lane > 0 ? up : 0u, F, lane + 1 < h ? dn : 0u};  // dy = -1, 0, +1
-        uint32_t cand = 0u;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t rowmask = w >= 32 ? full : ((1u << w) - 1u);
+        uint32_t M[8], F = 0u;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t r = rows[dir_dy(k) + 1];
-            const int dx = dir_dx(k);
-            cand |= M[k] & (dx > 0 ? (r >> 1) : (dx < 0 ? (r << 1) : r));
+        for (int k = 0; k < 8; ++k) M[k] = lane < h ? bits[k * h + lane] : 0u;
+        if (lane < h) F = bits[8 * h + lane];
+        uint32_t VIS = F;
+        int level = 1;
+        for (;;) {
+            const uint32_t up = __shfl_up_sync(full, F, 1), dn = __shfl_down_sync(full, F, 1);
+            const uint32_t rows[3] = {lane > 0 ? up : 0u, F, lane + 1 < h ? dn : 0u};  // dy = -1, 0, +1
+            uint32_t cand = 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t r = rows[dir_dy(k) + 1];
+                const int dx = dir_dx(k);
+                cand |= M[k] & (dx > 0 ? (r >> 1) : (dx < 0 ? (r << 1) : r));
+            }
+            cand &= ~VIS & rowmask;
+            if (lane >= h) cand = 0u;
+            VIS |= cand;
+            F = cand;
+            uint32_t c = cand;
+            while (c) {
+                const int b = __ffs(c) - 1;
+                c &= c - 1;
+                hh[lane * w + b] = (uint16_t)(level + 1);
+            }
+            if (!__any_sync(full, cand != 0u)) break;
+            ++level;
         }
-        cand &= ~VIS & rowmask;
-        if (lane >= h) cand = 0u;
-        VIS |= cand;
-        F = cand;
-        uint32_t c = cand;
-        while (c) {
-            const int b = __ffs(c) - 1;
-            c &= c - 1;
-            hh[lane * w + b] = (uint16_t)(level + 1);
-        }
-        if (!__any_sync(full, cand != 0u)) break;
-        ++level;
+        *levels += level;
     }
-    __syncwarp();
-    *levels += level;
+    __syncthreads();
     int act = 0;
-    for (int i = lane; i < n; i += 32) act |= (v[i] > 0 && hh[i] != kInf);
-    return __any_sync(full, act) != 0;
+    for (int i = tid; i < n; i += blockDim.x) act |= (v[i] > 0 && hh[i] != kInf);
+    return __syncthreads_or(act) != 0;
 }
 
 struct CutCount {
@@ -1668,21 +1671,18 @@ __device__ __forceinline__ void push_node(int n, int w, int *res, int *v, uint16
 //   list: n 16-bit entries; shares storage with the relabel's bitplanes
 __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
                            int gr_interval, CutCount &cc) {
-    __shared__ int s_cnt;
-    __shared__ int s_act;
+    // active-node counters of even and odd rounds: a round zeroes the other one, so
+    // no barrier is needed to reset the counter at the start of a round
+    __shared__ int s_cnt2[2];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     uint16_t *list = (uint16_t *)bits;
-    // regions of at most 32 x 32 nodes: the relabel runs on warp 0 alone
+    // regions of at most 32 x 32 nodes: the BFS levels of the relabel run on warp 0
     const bool small = w <= 32 && h <= 32;
     auto relabel = [&]() -> bool {
         if (!small) return global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
-        if (tid < 32) {
-            const bool a = warp_relabel(n, w, h, res, v, hh, &cc.levels);
-            if (tid == 0) s_act = a ? 1 : 0;
-        }
-        __syncthreads();
-        return s_act != 0;
+        return small_relabel(n, w, h, res, v, hh, bits, &cc.levels);
     };
+    if (tid == 0) s_cnt2[0] = 0;
     bool act = relabel();
     ++cc.relabels;
     int rounds = 0;
@@ -1717,10 +1717,10 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
             cc.rounds += rounds;
             return LEM_ERR_MAXFLOW_LIMIT;
         }
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
+        int *s_cnt = s_cnt2 + (rounds & 1);
         // four consecutive nodes per thread (one 16-byte load of v, one 8-byte
-        // load of hh), warp-aggregated appends
+        // load of hh); a warp appends its active nodes with one atomic, placed by
+        // four ballots (list order within a warp: first nodes, then second, ...)
         for (int base = 0; base < n; base += 4 * nt) {
             const int i0 = base + 4 * tid;
             bool a0 = false, a1 = false, a2 = false, a3 = false;
@@ -1736,25 +1736,28 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
                 a1 = i0 + 1 < n && v[i0 + 1] > 0 && hh[i0 + 1] != kInf;
                 a2 = i0 + 2 < n && v[i0 + 2] > 0 && hh[i0 + 2] != kInf;
             }
-            const int c = (int)a0 + (int)a1 + (int)a2 + (int)a3;
-            int incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t m0 = __ballot_sync(0xffffffffu, a0), m1 = __ballot_sync(0xffffffffu, a1);
+            const uint32_t m2 = __ballot_sync(0xffffffffu, a2), m3 = __ballot_sync(0xffffffffu, a3);
+            const int c0 = __popc(m0), c1 = __popc(m1), c2 = __popc(m2), c3 = __popc(m3);
+            const int tot = c0 + c1 + c2 + c3;
             if (tot == 0) continue;
             int pos = 0;
-            if (lane == 31) pos = atomicAdd(&s_cnt, tot);
-            pos = __shfl_sync(0xffffffffu, pos, 31) + incl - c;
-            if (a0) list[pos++] = (uint16_t)i0;
-            if (a1) list[pos++] = (uint16_t)(i0 + 1);
-            if (a2) list[pos++] = (uint16_t)(i0 + 2);
-            if (a3) list[pos] = (uint16_t)(i0 + 3);
+            if (lane == 0) pos = atomicAdd(s_cnt, tot);
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            const uint32_t lt = (1u << lane) - 1u;
+            if (a0) list[pos + __popc(m0 & lt)] = (uint16_t)i0;
+            pos += c0;
+            if (a1) list[pos + __popc(m1 & lt)] = (uint16_t)(i0 + 1);
+            pos += c1;
+            if (a2) list[pos + __popc(m2 & lt)] = (uint16_t)(i0 + 2);
+            pos += c2;
+            if (a3) list[pos + __popc(m3 & lt)] = (uint16_t)(i0 + 3);
         }
         __syncthreads();
-        const int cnt = s_cnt;
+        const int cnt = *s_cnt;
+        // the other counter is free until the next round's compaction (after the
+        // barrier that ends this round)
+        if (tid == 0) s_cnt2[(rounds & 1) ^ 1] = 0;
         for (int q = tid; q < cnt; q += nt) {
             const int i = list[q];
             push_node(n, w, res, v, hh, i, v[i], hh[i]);
