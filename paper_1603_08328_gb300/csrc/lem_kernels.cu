@@ -1627,7 +1627,10 @@ struct CutCount {
 // One push of node i with e > 0 excess at height hu: along admissible edges (to
 // a neighbour one level lower) as far as the residual capacities allow, then,
 // with excess left and no admissible edge, a relabel from the heights read here.
-// All loads come first (independent), the pushes are decided in registers, and
+// All loads come first and are independent: the eight neighbour heights are read
+// together with the residuals, at indices clamped to the region (a direction
+// that leaves the region has no residual capacity, so what is read there is
+// never used).  The pushes are decided in registers, and
 // the updates are fire-and-forget shared atomics (a neighbour may push into i's
 // reverse edges or excess at the same time; it only ever adds).  A stale
 // height read only costs extra rounds: the global relabel restores exact
@@ -1637,7 +1640,9 @@ __device__ __forceinline__ void push_node(int n, int w, int *res, int *v, uint16
 #pragma unroll
     for (int k = 0; k < 8; ++k) r[k] = res[k * n + i];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? (int)hh[i + dir_off(k, w)] : (int)kInf;
+    for (int k = 0; k < 8; ++k) hn[k] = (int)hh[min(max(i + dir_off(k, w), 0), n - 1)];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) hn[k] = r[k] > 0 ? hn[k] : (int)kInf;
     int left = e, mh = kInf;
     int d[8];
 #pragma unroll
