@@ -1329,6 +1329,14 @@ __device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *
     long long cst = 0;
     int ncl = 0;
     const float4 wp = P.wfw[(size_t)pv * W + pu];
+    // the eight neighbours' labels, loaded together before any is used (coordinates
+    // clamped to the image; a direction that leaves the image is skipped below)
+    float4 fqa[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int qu = min(max(pu + dir_dx(k), 0), W - 1), qv = min(max(pv + dir_dy(k), 0), H - 1);
+        fqa[k] = lab[(size_t)qv * W + qu];
+    }
     // psi(f_p, alpha) on every pair of p: its coefficient differences and its value
     // at p are shared by the 8 neighbours (the term of a backward pair (q, p) with
     // alpha at q is psi(f_p, alpha) on the same pair: each label is evaluated at
@@ -1346,12 +1354,12 @@ __device__ void build_node(const DevPlanes &P, const KParams &kp, const float4 *
         const float wl = fwd ? comp(wp, d) : comp(P.wfw[(size_t)qv * W + qu], d);
         const bool qin = qu >= x0 && qu < x0 + w && qv >= y0 && qv < y0 + h;
         if (!qin) {
-            const float4 fq = lab[(size_t)qv * W + qu];
+            const float4 fq = fqa[k];
             const DDCoef dpq = dd_coef(fp, fq), daq = dd_coef(al, fq);
             U0 += q_of(wl, kp.tau_dis, kp.S, dd_eval(dpq, fu, fv), dd_eval(dpq, gu, gv));
             U1 += q_of(wl, kp.tau_dis, kp.S, dd_eval(daq, fu, fv), dd_eval(daq, gu, gv));
         } else if (fwd) {
-            const float4 fq = lab[(size_t)qv * W + qu];
+            const float4 fq = fqa[k];
             const DDCoef dpq = dd_coef(fp, fq), daq = dd_coef(al, fq);
             int A = q_of(wl, kp.tau_dis, kp.S, dd_eval(dpq, fu, fv), dd_eval(dpq, gu, gv));
             const int B = q_of(wl, kp.tau_dis, kp.S, dpa_p, dd_eval(dpa, gu, gv));
@@ -1471,27 +1479,30 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
             const int y = rw.y, wi = rw.x;
             const uint32_t vis = VIS[word];
             uint32_t cand = 0;
-            if (~vis) {
+            {
                 // frontier words of rows y-1, y, y+1 around column word wi, shifted by
                 // dx = -1, 0, +1: sh[dy+1][dx+1] holds, at bit b, the frontier bit of
-                // node (x + dx, y + dy) for the node x at bit b
-                uint32_t sh[3][3];
+                // node (x + dx, y + dy) for the node x at bit b.  Every load is issued
+                // at once, at indices clamped to the grid; words outside it count as 0.
+                uint32_t sh[3][3], pl[8];
+                const int wl = max(wi - 1, 0), wr = min(wi + 1, WPR - 1);
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     const int yy = y + r - 1;
-                    uint32_t c = 0, lw = 0, rw2 = 0;
-                    if (yy >= 0 && yy < h) {
-                        const uint32_t *F = Fc + yy * WPR;
-                        c = F[wi];
-                        lw = wi > 0 ? F[wi - 1] : 0u;
-                        rw2 = wi + 1 < WPR ? F[wi + 1] : 0u;
-                    }
+                    const bool rin = yy >= 0 && yy < h;
+                    const uint32_t *F = Fc + min(max(yy, 0), h - 1) * WPR;
+                    uint32_t c = F[wi], lw = F[wl], rw2 = F[wr];
+                    if (!rin) c = lw = rw2 = 0u;
+                    if (wi == 0) lw = 0u;
+                    if (wi + 1 >= WPR) rw2 = 0u;
                     sh[r][0] = (c << 1) | (lw >> 31);  // dx = -1
                     sh[r][1] = c;                       // dx = 0
                     sh[r][2] = (c >> 1) | (rw2 << 31);  // dx = +1
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) cand |= M[k * NW + word] & sh[dir_dy(k) + 1][dir_dx(k) + 1];
+                for (int k = 0; k < 8; ++k) pl[k] = M[k * NW + word];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) cand |= pl[k] & sh[dir_dy(k) + 1][dir_dx(k) + 1];
                 // only bits of nodes inside the row can be reached
                 const int tail = w - wi * 32;
                 cand &= ~vis & (tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u));
@@ -1519,6 +1530,13 @@ __device__ bool global_relabel(int n, int w, int h, const int *res, const int *v
     int act = 0;
     for (int i = tid; i < n; i += nt) act |= (v[i] > 0 && hh[i] != kInf);
     return __syncthreads_or(act) != 0;
+}
+
+// The same as a separate function: kernels of up to 256 threads call it, so
+// that its code does not take part in their register allocation.
+__device__ __noinline__ bool global_relabel_outlined(int n, int w, int h, const int *res, const int *v, uint16_t *hh,
+                                                     uint32_t *bits, int *levels) {
+    return global_relabel(n, w, h, res, v, hh, bits, levels);
 }
 
 // Terminal reduction before the max-flow: a node's excess beyond what its
@@ -1674,6 +1692,7 @@ __device__ __forceinline__ void push_node(int n, int w, int *res, int *v, uint16
 // finite height) into a list each round, so warps only run the push path for
 // nodes that have work.
 //   list: n 16-bit entries; shares storage with the relabel's bitplanes
+template <bool kOutline = false>
 __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, uint32_t *bits, int max_rounds,
                            int gr_interval, CutCount &cc) {
     // active-node counters of even and odd rounds: a round zeroes the other one, so
@@ -1684,7 +1703,9 @@ __device__ int cta_maxflow(int n, int w, int h, int *res, int *v, uint16_t *hh, 
     // regions of at most 32 x 32 nodes: the BFS levels of the relabel run on warp 0
     const bool small = w <= 32 && h <= 32;
     auto relabel = [&]() -> bool {
-        if (!small) return global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
+        if (!small)
+            return kOutline ? global_relabel_outlined(n, w, h, res, v, hh, bits, &cc.levels)
+                            : global_relabel(n, w, h, res, v, hh, bits, &cc.levels);
         return small_relabel(n, w, h, res, v, hh, bits, &cc.levels);
     };
     if (tid == 0) s_cnt2[0] = 0;
@@ -1912,6 +1933,7 @@ __global__ void __launch_bounds__(NT, 1) k_mincut_batch(KParams kp, const int4 *
 // data term phi_p(al) is in `phi` (image plane, row pitch W): graph, terminal
 // reduction, CTA min-cut, commit of the minimal sink side.  All threads call
 // it; it ends with a barrier.
+template <bool kOutline = false>
 __device__ void expand_move(const DevPlanes &P, const KParams &kp, float4 *lab, const float *phi, float4 al, int x0,
                             int y0, int w, int h, const CutSmem &cs, CutCount &cc, long long &acc, long long &hits) {
     const int n = w * h, W = P.W;
@@ -1927,7 +1949,7 @@ __device__ void expand_move(const DevPlanes &P, const KParams &kp, float4 *lab, 
     __syncthreads();
     clamp_terminals(n, w, h, cs.res, cs.v);
     __syncthreads();
-    const int st = cta_maxflow(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
+    const int st = cta_maxflow<kOutline>(n, w, h, cs.res, cs.v, cs.hh, cs.bits, kp.max_rounds, kp.gr_interval, cc);
     if (st == LEM_OK) {
         RowCol rm(threadIdx.x, blockDim.x, w);
         for (int j = threadIdx.x; j < n; j += blockDim.x, rm.next()) {
@@ -2115,7 +2137,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
         }
         region_unary(P, kp, x0, y0, w, h, a1.x, a1.y, a1.z, smf, phiA + (size_t)y0 * W + x0, W);
         cluster_sync_all();
-        expand_move(P, kp, lab, phiA, a1, x0, y0, w, h, cs, cc, acck[0], hits);
+        expand_move<(NT <= 256)>(P, kp, lab, phiA, a1, x0, y0, w, h, cs, cc, acck[0], hits);
         if (threadIdx.x == 0) {
             const float4 a2 = propose(lab, W, st2, cx0, cy0, cw, chh, false, 0.0, 0.0, 0.0, 0.0);
             s_alpha[1] = a2;
@@ -2131,7 +2153,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
         const int src = s_src;
         if (src == 2)  // (not reachable: the first move sets f_r2 to alpha_1 or keeps it)
             region_unary(P, kp, x0, y0, w, h, a2.x, a2.y, a2.z, smf, phiA + (size_t)y0 * W + x0, W);
-        expand_move(P, kp, lab, src == 1 ? phiB : phiA, a2, x0, y0, w, h, cs, cc, acck[0], hits);
+        expand_move<(NT <= 256)>(P, kp, lab, src == 1 ? phiB : phiA, a2, x0, y0, w, h, cs, cc, acck[0], hits);
     } else {
         // outer perturbation sizes of this iteration, copied into Algorithm 2
         double rd = 0.5 * (kp.disp_max - kp.disp_min) * ldexp(1.0, -iter);
@@ -2171,7 +2193,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 3 : 1))
                 const float4 al = s_alpha[t - t0];
                 region_unary(P, kp, x0, y0, w, h, al.x, al.y, al.z, smf, phiA + (size_t)y0 * W + x0, W);
                 // (region_unary ends with a barrier; its shared memory is reused below)
-                expand_move(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acck[proposal_kind(lv, kc, t)], hits);
+                expand_move<(NT <= 256)>(P, kp, lab, phiA, al, x0, y0, w, h, cs, cc, acck[proposal_kind(lv, kc, t)],
+                                         hits);
             }
         }
         if (done) mark_region_done(done, item.w + cj * nx + ci);
