@@ -164,8 +164,8 @@ def _random_graph(rng, w, h, tmax=200000, cap=131072):
     return tcap, ncap
 
 
-@pytest.mark.parametrize("shape", [(1, 1), (16, 1), (1, 16), (4, 4), (15, 15), (45, 45), (75, 75), (75, 13),
-                                   (1, 375), (113, 49), (450, 12)])
+@pytest.mark.parametrize("shape", [(1, 1), (16, 1), (1, 16), (4, 4), (15, 15), (32, 1), (1, 32), (31, 29), (32, 32),
+                                   (33, 32), (64, 7), (45, 45), (75, 75), (75, 13), (1, 375), (113, 49), (450, 12)])
 def test_mincut_batch_random_graphs_bit_exact(mid, shape):
     g, _, _ = mid
     w, h = shape
